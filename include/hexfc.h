@@ -1,0 +1,262 @@
+/*
+ * hexfc.h -- C ABI of the GB300 focus+context hex-mesh renderer.
+ *
+ * The library renders every face of a hexahedral mesh into per-pixel fragment
+ * lists, shades each fragment in the focus+context edge/face style, sorts
+ * each list by depth and blends it front to back ("Interactive Focus+Context
+ * Rendering for Hexahedral Mesh Inspection", Neuhauser, Wang, Westermann:
+ * Section "Method Overview", Section "Focus+Context" Eqs. 1-4, Section
+ * "GPU Implementation").
+ *
+ * Conventions for every entry point
+ *   - Host pointers are read during the call only; the caller keeps ownership.
+ *   - Device pointers (marked "device") are caller-owned CUDA allocations on
+ *     the context's device; the library writes them on the given stream.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - The library owns the resident mesh buffers and the fragment buffers; they
+ *     live until hexfc_destroy.
+ *   - No C++ exception crosses this boundary; every failure is a status < 0.
+ *   - A context is not thread-safe: calls on one context must be serialised.
+ */
+#ifndef HEXFC_H
+#define HEXFC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t hexfc_status;
+
+enum {
+    HEXFC_OK = 0,
+    HEXFC_ERR_ARG = -1,       /* a pointer, size or parameter is invalid */
+    HEXFC_ERR_OOM = -2,       /* device allocation failed, or the fragment total exceeds the budget */
+    HEXFC_ERR_OVERFLOW = -3,  /* a per-pixel list exceeds HEXFC_MAX_LIST */
+    HEXFC_ERR_CUDA = -4,      /* a CUDA runtime call or kernel launch failed */
+    HEXFC_ERR_TIMEOUT = -5,   /* reserved: a bounded device-side wait ran out */
+    HEXFC_ERR_MESH = -6,      /* the mesh is malformed (index out of range, non-finite vertex) */
+    HEXFC_ERR_STATE = -7      /* call out of order (no mesh, no view, no previous render) */
+};
+
+/* Longest per-pixel fragment list the sort/composite pass accepts. */
+#define HEXFC_MAX_LIST 8192
+
+typedef struct hexfc_ctx hexfc_ctx;
+
+/*
+ * Camera (Section "Results and Analysis": timings along camera paths).
+ * eye/target/up in world units; fovy_deg > 0 selects a perspective camera with
+ * that vertical field of view, fovy_deg == 0 an orthographic camera whose view
+ * height is 2*ortho_half_h world units. Fragments are kept for
+ * znear < depth < zfar (depth along the view direction); triangles with a
+ * vertex outside that range, or outside +-16384 px, are not drawn.
+ * width x height pixels, row 0 at the top, pixel centres at (x+.5, y+.5).
+ */
+typedef struct hexfc_view {
+    double eye[3];
+    double target[3];
+    double up[3];
+    double fovy_deg;
+    double ortho_half_h;
+    double znear, zfar;
+    int32_t width, height;
+} hexfc_view;
+
+enum { HEXFC_LENS_SCREEN = 0, HEXFC_LENS_SPHERE = 1 };
+
+/*
+ * Focus lens (Section "Focus+Context": circular screen-space lens with centre
+ * and radius, focus = 1 - smoothstep(0.7, 1, dist); Section "Evaluation":
+ * object-space lens). SCREEN: center[0..1] in pixels, radius in pixels.
+ * SPHERE: center in world units, radius in world units, dist measured from the
+ * fragment's world position.
+ */
+typedef struct hexfc_lens {
+    int32_t mode;
+    int32_t pad;
+    double center[3];
+    double radius;
+} hexfc_lens;
+
+/*
+ * Style constants (Section "GPU Implementation": all constants of Eqs. 1-3
+ * are shader parameters). w_base: minimum edge width in pixels (Eq. 1);
+ * lod, delta: LoD level and importance threshold of Eq. 1; s: accentuation
+ * of Eq. 2; alpha_min..alpha_max: face opacity transfer function (Eq. 3's
+ * alpha_hat); tf_lo..tf_hi: importance range mapped to the blue-to-red colour
+ * table; bg: background colour (Section "Contextual Volume Rendering");
+ * accent_beta: brightening of accentuated edges (Section "Blending Focus and
+ * Context"); halo_scale, darken: halo width and edge darkening of the focus
+ * edges; g_min, g_max: clamp of the depth-dependent width factor.
+ */
+typedef struct hexfc_style {
+    float w_base;
+    int32_t lod;
+    float delta;
+    float s;
+    float alpha_min, alpha_max;
+    float tf_lo, tf_hi;
+    float bg[3];
+    float accent_beta;
+    float halo_scale;
+    float darken;
+    float g_min, g_max;
+} hexfc_style;
+
+/* Per-frame statistics of the last hexfc_render* call. */
+typedef struct hexfc_frame_stats {
+    uint64_t fragments;      /* fragments generated (sum of list lengths) */
+    uint64_t bin_entries;    /* (triangle, tile) pairs after binning */
+    uint32_t max_list;       /* longest per-pixel list */
+    uint32_t long_lists;     /* pixels handled by the long-list path */
+    uint32_t width, height;
+    uint32_t kernel_launches;  /* kernels this call launched */
+    uint32_t covered_pixels;   /* reserved (0) */
+} hexfc_frame_stats;
+
+/* Stages timed by HEXFC_OPT_STAGE_TIMING (CUDA events on the render stream).
+ * GAP stages are the host round trips that read the bin and fragment totals. */
+enum {
+    HEXFC_STAGE_VERTEX = 0,   /* vertex projection */
+    HEXFC_STAGE_FACE = 1,     /* face setup and tile counts */
+    HEXFC_STAGE_TILE_SCAN = 2,
+    HEXFC_STAGE_GAP1 = 3,
+    HEXFC_STAGE_BIN = 4,      /* bin fill */
+    HEXFC_STAGE_COUNT = 5,    /* per-pixel fragment count */
+    HEXFC_STAGE_SCAN = 6,     /* pixel prefix scan */
+    HEXFC_STAGE_GAP2 = 7,
+    HEXFC_STAGE_FILL = 8,     /* fragment fill and shading */
+    HEXFC_STAGE_COMPOSITE = 9,/* sort and composite (both list paths) */
+    HEXFC_N_STAGES = 10
+};
+
+enum {
+    HEXFC_METRIC_SCALED_JACOBIAN = 0,
+    HEXFC_METRIC_JACOBIAN_RATIO = 1,
+    HEXFC_METRIC_IMPORTANCE = 2   /* clamp(1 - scaled Jacobian, 0, 1) */
+};
+
+/* Fills *style with the defaults (w_base 2, lod 1, delta 0.5, s 1.5, alpha
+ * 0.1..0.6, tf 0..1, black background, accent 0.2, halo 0.5, darken 0.25,
+ * g 0.5..2). Never fails. */
+void hexfc_style_default(hexfc_style* style);
+
+/* Create a context on CUDA device `device`. frag_budget_bytes caps the
+ * fragment buffers (24 bytes per fragment); 0 means no cap beyond free memory.
+ * Errors: ARG (out == NULL), CUDA (bad device). */
+hexfc_status hexfc_create(hexfc_ctx** out, int device, uint64_t frag_budget_bytes);
+
+/* Free everything the context owns. Accepts NULL. */
+void hexfc_destroy(hexfc_ctx* ctx);
+
+/*
+ * Upload a hexahedral mesh and keep it resident on the device (Section "GPU
+ * Implementation": all data required for rendering is kept on the GPU).
+ *   verts            host, n_verts*3 float, xyz
+ *   cells            host, n_cells*8 int32, VTK hexahedron corner order
+ *   cell_scalar      host, n_cells float per-cell importance, or NULL: the
+ *                    importance is computed on the device as
+ *                    HEXFC_METRIC_IMPORTANCE (Section "Introduction")
+ *   cell_edge_level  host, n_cells*12 uint8 LoD level per cell edge, edge order
+ *                    01 12 23 30 45 56 67 74 04 15 26 37 (Section "Level of
+ *                    Detail Structure": each edge carries the highest level
+ *                    at which it still exists), or NULL for level 0
+ * Builds the unique faces (each geometric face once, canonical corner order,
+ * face id = rank of its sorted vertex ids) and unique edges on the host, and
+ * the per-vertex / per-edge importance (max over incident cells, Section
+ * "Method Overview") on the device. *mesh_id_out receives the mesh handle.
+ * Errors: ARG, MESH (index out of range, non-finite vertex, n_cells == 0),
+ * OOM, CUDA. Synchronous.
+ */
+hexfc_status hexfc_upload_mesh(hexfc_ctx* ctx, const float* verts, int64_t n_verts,
+                               const int32_t* cells, int64_t n_cells, const float* cell_scalar,
+                               const uint8_t* cell_edge_level, int32_t* mesh_id_out);
+
+/*
+ * Per-cell quality from the Jacobian of the cube-to-cell map (Section
+ * "Introduction"; Section "Results and Analysis": per-cell scaled Jacobian
+ * ratio). metric: HEXFC_METRIC_*; the 8 corners and the cell centre are
+ * sampled. out: device, n_cells float. Errors: ARG, STATE (bad mesh), CUDA.
+ */
+hexfc_status hexfc_cell_quality(hexfc_ctx* ctx, int32_t mesh, int32_t metric, float* out,
+                                void* stream);
+
+/*
+ * Replace the mesh's per-cell importance with `cell_importance` (device,
+ * n_cells float) and recompute the per-vertex and per-edge maxima on the
+ * device (Section "Method Overview"). Errors: ARG, STATE, CUDA.
+ */
+hexfc_status hexfc_set_cell_importance(hexfc_ctx* ctx, int32_t mesh, const float* cell_importance,
+                                       void* stream);
+
+/* Number of unique faces / edges of a mesh (for sizing and statistics). */
+hexfc_status hexfc_mesh_info(hexfc_ctx* ctx, int32_t mesh, int64_t* n_faces, int64_t* n_edges);
+
+/* Set the camera. Errors: ARG (NULL, width/height outside 1..16384,
+ * znear >= zfar, degenerate basis). */
+hexfc_status hexfc_set_view(hexfc_ctx* ctx, const hexfc_view* view);
+
+/* Set the focus lens (radius > 0). Errors: ARG. */
+hexfc_status hexfc_set_lens(hexfc_ctx* ctx, const hexfc_lens* lens);
+
+/* Set the style constants. Errors: ARG (w_base < 0, tf_hi == tf_lo, g_min > g_max). */
+hexfc_status hexfc_set_style(hexfc_ctx* ctx, const hexfc_style* style);
+
+/*
+ * Render one frame of `mesh` with the current view, lens and style into
+ * out_rgba (device, height*width*4 float, row-major, row 0 at the top,
+ * straight RGB over the background plus accumulated alpha).
+ * Steps, all on `stream`: vertex projection to 16.8 fixed point and 24-bit
+ * depth; triangle setup and tile binning; per-pixel fragment count; prefix
+ * scan; fragment fill with Eqs. 1-4; per-pixel depth sort and front-to-back
+ * composite. The call waits once for the fragment total (to size the buffers);
+ * the image is complete when `stream` reaches the end of the call.
+ * stats (host, nullable) receives the frame statistics.
+ * Errors: ARG, STATE (no view), OOM (fragments exceed the budget; stats still
+ * filled), OVERFLOW (a list longer than HEXFC_MAX_LIST), CUDA.
+ */
+hexfc_status hexfc_render(hexfc_ctx* ctx, int32_t mesh, float* out_rgba, hexfc_frame_stats* stats,
+                          void* stream);
+
+/* As hexfc_render, with the image copied into out_rgba_host (host,
+ * height*width*4 float) before the call returns. */
+hexfc_status hexfc_render_host(hexfc_ctx* ctx, int32_t mesh, float* out_rgba_host,
+                               hexfc_frame_stats* stats, void* stream);
+
+/*
+ * Parity hook: the fragment lists of the last render for `n` listed pixels
+ * (px[i], py[i], host). counts (host, n) receives each list length; keys
+ * (host, cap) and rgba (host, cap*4 float) receive the lists concatenated in
+ * the order of the pixel list, each sorted ascending by key =
+ * (z24 << 32) | (2*face_id + triangle), rgba premultiplied (Eq. 4).
+ * keys/rgba may be NULL. Errors: ARG, STATE (no previous render),
+ * OVERFLOW (total > cap; counts still filled), CUDA. Synchronous.
+ */
+hexfc_status hexfc_debug_pixels(hexfc_ctx* ctx, const int32_t* px, const int32_t* py, int64_t n,
+                                uint32_t* counts, uint64_t* keys, float* rgba, uint64_t cap);
+
+/* Tuning and test options. */
+enum {
+    HEXFC_OPT_REVERSE_BIN_ORDER = 1, /* 1: process faces in reverse id order when binning (test hook) */
+    HEXFC_OPT_STAGE_TIMING = 2       /* 1: record CUDA events around every stage of hexfc_render* */
+};
+hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value);
+
+/*
+ * Accumulated stage times (milliseconds, summed over frames) since the last
+ * reset, for frames rendered with HEXFC_OPT_STAGE_TIMING on. ms: host array of
+ * HEXFC_N_STAGES doubles; *frames: number of frames summed. Waits for the last
+ * timed frame to finish. reset != 0 clears the sums afterwards. Errors: ARG, CUDA.
+ */
+hexfc_status hexfc_stage_times(hexfc_ctx* ctx, double* ms, uint64_t* frames, int32_t reset);
+
+/* Static string for a status code. Never NULL. */
+const char* hexfc_status_string(hexfc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HEXFC_H */

@@ -1,0 +1,663 @@
+// C ABI of the hexfc library: context, resident meshes, camera/lens/style,
+// and the per-frame orchestration of the kernels on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hexfc_internal.cuh"
+#include "mesh_host.h"
+
+using namespace hexfc;
+
+struct hexfc_ctx {
+    int device = 0;
+    uint64_t budget = 0;
+    std::vector<DevMesh*> meshes;
+    bool have_view = false;
+    hexfc_view view{};
+    CamParams cam{};
+    double zref = 1.0;
+    hexfc_lens lens{};
+    hexfc_style style{};
+    FrameBufs fb;
+    int reverse_bins = 0;
+    // last render
+    bool have_frame = false;
+    int last_W = 0, last_H = 0, last_tiles_x = 0, last_tiles_y = 0;
+    hexfc_frame_stats last{};
+    float* d_out = nullptr;   // image buffer of hexfc_render_host
+    int64_t d_out_cap = 0;
+    // stage timing: events of the frame in flight, sums over completed frames
+    bool timing = false;
+    cudaEvent_t ev[2][HEXFC_N_STAGES + 1] = {};   // two frames: the one in flight and the previous one
+    bool ev_pending[2] = {false, false};
+    int ev_cur = 0;
+    double stage_ms[HEXFC_N_STAGES] = {};
+    uint64_t timed_frames = 0;
+};
+
+namespace {
+
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) {                \
+            (void)cudaGetLastError();           \
+            return HEXFC_ERR_CUDA;              \
+        }                                       \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+hexfc_status dalloc(T** p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? HEXFC_ERR_OOM : HEXFC_ERR_CUDA;
+    }
+    return HEXFC_OK;
+}
+
+template <typename T>
+void dfree(T*& p)
+{
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+// Grow a device array to hold at least n elements (contents are not kept).
+template <typename T>
+hexfc_status ensure(T** p, int64_t* cap, int64_t n)
+{
+    if (*p && *cap >= n) return HEXFC_OK;
+    dfree(*p);
+    int64_t want = n + n / 4 + 1024;
+    hexfc_status st = dalloc(p, (size_t)want);
+    *cap = st == HEXFC_OK ? want : 0;
+    return st;
+}
+
+void free_mesh(DevMesh* m)
+{
+    if (!m) return;
+    dfree(m->verts); dfree(m->cells); dfree(m->cell_edges); dfree(m->cell_imp);
+    dfree(m->vkey); dfree(m->ekey); dfree(m->vimp); dfree(m->eattr); dfree(m->elevel);
+    dfree(m->fverts); dfree(m->fedges); dfree(m->fimp); dfree(m->fpx); dfree(m->fpy); dfree(m->fpz);
+    delete m;
+}
+
+void free_frame(FrameBufs& f)
+{
+    dfree(f.vproj); dfree(f.ved); dfree(f.fx); dfree(f.fy); dfree(f.fz); dfree(f.fed); dfree(f.fflags);
+    dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.bins); dfree(f.cnt); dfree(f.off);
+    dfree(f.part); dfree(f.part_max); dfree(f.long_q); dfree(f.key); dfree(f.rgba); dfree(f.scal);
+    if (f.h_scal) cudaFreeHost(f.h_scal);
+    f = FrameBufs{};
+}
+
+DevMesh* get_mesh(hexfc_ctx* ctx, int32_t id)
+{
+    if (!ctx || id < 0 || id >= (int32_t)ctx->meshes.size()) return nullptr;
+    return ctx->meshes[(size_t)id];
+}
+
+// Stage events: record boundary k of the current frame (no-op without timing).
+void mark(hexfc_ctx* ctx, int k, cudaStream_t s)
+{
+    if (ctx->timing) cudaEventRecord(ctx->ev[ctx->ev_cur][k], s);
+}
+
+// Add the stage times of event set `set` if it holds a recorded frame.
+void collect_set(hexfc_ctx* ctx, int set)
+{
+    if (!ctx->ev_pending[set]) return;
+    ctx->ev_pending[set] = false;
+    if (cudaEventSynchronize(ctx->ev[set][HEXFC_N_STAGES]) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    for (int k = 0; k < HEXFC_N_STAGES; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev[set][k], ctx->ev[set][k + 1]) == cudaSuccess) ctx->stage_ms[k] += ms;
+        else (void)cudaGetLastError();
+    }
+    ++ctx->timed_frames;
+}
+
+// The previous frame's events are complete once the stream has passed any later point.
+void collect(hexfc_ctx* ctx) { collect_set(ctx, ctx->ev_cur ^ 1); }
+
+// Camera basis and projection constants, evaluated in double in a fixed order
+// (the host compiler is run without floating-point contraction).
+bool make_camera(const hexfc_view* v, CamParams& c, double& zref)
+{
+    double f[3] = {v->target[0] - v->eye[0], v->target[1] - v->eye[1], v->target[2] - v->eye[2]};
+    double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    if (!(fl > 0.0)) return false;
+    for (int d = 0; d < 3; ++d) c.F[d] = f[d] / fl;
+    double r[3] = {c.F[1] * v->up[2] - c.F[2] * v->up[1], c.F[2] * v->up[0] - c.F[0] * v->up[2],
+                   c.F[0] * v->up[1] - c.F[1] * v->up[0]};
+    double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (!(rl > 0.0)) return false;
+    for (int d = 0; d < 3; ++d) c.R[d] = r[d] / rl;
+    c.U[0] = c.R[1] * c.F[2] - c.R[2] * c.F[1];
+    c.U[1] = c.R[2] * c.F[0] - c.R[0] * c.F[2];
+    c.U[2] = c.R[0] * c.F[1] - c.R[1] * c.F[0];
+    for (int d = 0; d < 3; ++d) c.eye[d] = v->eye[d];
+    c.W = v->width;
+    c.H = v->height;
+    c.cx = (double)v->width * 0.5;
+    c.cy = (double)v->height * 0.5;
+    c.znear = v->znear;
+    c.zfar = v->zfar;
+    c.ortho = !(v->fovy_deg > 0.0);
+    if (c.ortho) {
+        if (!(v->ortho_half_h > 0.0)) return false;
+        c.scale = ((double)v->height * 0.5) / v->ortho_half_h;
+        c.focal = 0.0;
+    } else {
+        if (!(v->fovy_deg < 180.0)) return false;
+        c.focal = ((double)v->height * 0.5) / std::tan(v->fovy_deg * (3.14159265358979323846 / 180.0) * 0.5);
+        c.scale = 0.0;
+    }
+    c.zf_over = v->zfar / (v->zfar - v->znear);
+    zref = fl;
+    return true;
+}
+
+ShadeParams make_shade(const hexfc_ctx* ctx)
+{
+    ShadeParams sp{};
+    const hexfc_style& s = ctx->style;
+    sp.lens_mode = ctx->lens.mode;
+    for (int d = 0; d < 3; ++d) sp.lens_c[d] = (float)ctx->lens.center[d];
+    sp.lens_inv_r = (float)(1.0 / ctx->lens.radius);
+    sp.w_base = s.w_base;
+    sp.lod = s.lod;
+    sp.delta = s.delta;
+    sp.s = s.s;
+    sp.alpha_min = s.alpha_min;
+    sp.alpha_span = s.alpha_max - s.alpha_min;
+    sp.tf_lo = s.tf_lo;
+    sp.tf_inv = (float)(1.0 / ((double)s.tf_hi - (double)s.tf_lo));
+    for (int d = 0; d < 3; ++d) sp.bg[d] = s.bg[d];
+    sp.accent_beta = s.accent_beta;
+    sp.halo_scale = s.halo_scale;
+    sp.darken = s.darken;
+    sp.g_min = s.g_min;
+    sp.g_max = s.g_max;
+    sp.zref = (float)ctx->zref;
+    sp.ortho = ctx->cam.ortho;
+    return sp;
+}
+
+// Bins, counts, scan, fill and composite of one frame (everything but the output copy).
+hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_stats* stats, cudaStream_t s)
+{
+    FrameBufs& fb = ctx->fb;
+    const int W = ctx->view.width, H = ctx->view.height;
+    const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
+    const int64_t n_tiles = (int64_t)tiles_x * tiles_y;
+    const int64_t n_pix = n_tiles * kTilePix;
+    hexfc_status st;
+    if (!fb.vproj || fb.v_cap < m->n_verts) {
+        int64_t c1 = 0;
+        dfree(fb.ved);
+        if ((st = ensure(&fb.vproj, &fb.v_cap, m->n_verts)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.ved, &c1, fb.v_cap)) != HEXFC_OK) return st;
+    }
+    if (!fb.fx || fb.f_cap < m->n_faces) {
+        int64_t c1 = 0, c2 = 0, c3 = 0, c4 = 0;
+        dfree(fb.fy); dfree(fb.fz); dfree(fb.fed); dfree(fb.fflags);
+        if ((st = ensure(&fb.fx, &fb.f_cap, m->n_faces)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.fy, &c1, fb.f_cap)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.fz, &c2, fb.f_cap)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.fed, &c3, fb.f_cap)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.fflags, &c4, fb.f_cap)) != HEXFC_OK) return st;
+    }
+    if (!fb.tile_cnt || fb.t_cap < n_tiles + 1) {
+        int64_t c1 = 0, c2 = 0;
+        dfree(fb.tile_off); dfree(fb.tile_cur);
+        if ((st = ensure(&fb.tile_cnt, &fb.t_cap, n_tiles + 1)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.tile_off, &c1, fb.t_cap)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.tile_cur, &c2, fb.t_cap)) != HEXFC_OK) return st;
+    }
+    if (!fb.cnt || fb.p_cap < n_pix + 1) {
+        int64_t c1 = 0, c2 = 0;
+        dfree(fb.off); dfree(fb.long_q);
+        if ((st = ensure(&fb.cnt, &fb.p_cap, n_pix + 1)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.off, &c1, fb.p_cap)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.long_q, &c2, fb.p_cap)) != HEXFC_OK) return st;
+    }
+    int64_t nparts = scan_partials_needed(std::max<int64_t>(n_pix, n_tiles)) + 1;
+    if (!fb.part || fb.part_cap < 2 * nparts) {
+        int64_t c1 = 0;
+        dfree(fb.part_max);
+        if ((st = ensure(&fb.part, &fb.part_cap, 2 * nparts)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.part_max, &c1, fb.part_cap)) != HEXFC_OK) return st;
+    }
+    if (!fb.scal) {
+        if ((st = dalloc(&fb.scal, 16)) != HEXFC_OK) return st;
+        CK(cudaMallocHost((void**)&fb.h_scal, 16 * sizeof(uint64_t)));
+    }
+
+    if (ctx->timing && !ctx->ev[0][0])
+        for (auto& set : ctx->ev)
+            for (auto& e : set) CK(cudaEventCreate(&e));
+    ctx->ev_cur ^= 1;
+    uint32_t launches = 0;
+    mark(ctx, 0, s);
+    CK(cudaMemsetAsync(fb.tile_cnt, 0, sizeof(uint32_t) * (size_t)n_tiles, s));
+    CK(cudaMemsetAsync(fb.tile_cur, 0, sizeof(uint32_t) * (size_t)n_tiles, s));
+    CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * 16, s));
+    CK(launch_vertex_setup(*m, ctx->cam, fb, s));
+    mark(ctx, 1, s);
+    CK(launch_face_setup(*m, ctx->cam, ctx->style.lod, ctx->style.delta, fb, tiles_x, tiles_y, s));
+    mark(ctx, 2, s);
+    CK(scan_u32_to_u64(fb.tile_cnt, fb.tile_off, n_tiles, fb.part, fb.part_max, fb.scal + 8, 0xFFFFFFFFu, s));
+    mark(ctx, 3, s);
+    launches += 5;
+    CK(cudaMemcpyAsync(fb.h_scal + 8, fb.scal + 8, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    collect(ctx);
+    const uint64_t n_bins = fb.h_scal[8];
+    if ((st = ensure(&fb.bins, &fb.bin_cap, (int64_t)n_bins)) != HEXFC_OK) return st;
+    mark(ctx, 4, s);
+    CK(launch_bin_fill(*m, fb, tiles_x, W, H, ctx->reverse_bins, s));
+    mark(ctx, 5, s);
+    CK(launch_count(fb, tiles_x, tiles_y, W, H, s));
+    mark(ctx, 6, s);
+    CK(scan_u32_to_u64(fb.cnt, fb.off, n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
+    mark(ctx, 7, s);
+    launches += 5;
+    CK(cudaMemcpyAsync(fb.h_scal, fb.scal, 3 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint64_t total = fb.h_scal[0];
+    const uint32_t max_list = (uint32_t)fb.h_scal[1];
+    const uint32_t n_long = (uint32_t)fb.h_scal[2];
+    hexfc_frame_stats fs{};
+    fs.fragments = total;
+    fs.bin_entries = n_bins;
+    fs.max_list = max_list;
+    fs.long_lists = n_long;
+    fs.width = (uint32_t)W;
+    fs.height = (uint32_t)H;
+    fs.kernel_launches = launches;
+    ctx->last = fs;
+    if (stats) *stats = fs;
+    ctx->have_frame = false;
+    if (max_list > HEXFC_MAX_LIST) return HEXFC_ERR_OVERFLOW;
+    if (ctx->budget && total * 24ull > ctx->budget) return HEXFC_ERR_OOM;
+    if (!fb.key || fb.frag_cap < (int64_t)total) {
+        int64_t c1 = 0;
+        dfree(fb.rgba);
+        if ((st = ensure(&fb.key, &fb.frag_cap, (int64_t)total)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.rgba, &c1, fb.frag_cap)) != HEXFC_OK) return st;
+    }
+    ShadeParams sp = make_shade(ctx);
+    mark(ctx, 8, s);
+    CK(launch_fill(*m, fb, sp, tiles_x, tiles_y, W, H, s));
+    mark(ctx, 9, s);
+    CK(launch_composite(fb, sp, tiles_x, tiles_y, W, H, out, n_long, s));
+    mark(ctx, 10, s);
+    ctx->ev_pending[ctx->ev_cur] = ctx->timing;
+    launches += 2 + (n_long > 0 ? 1 : 0);
+    ctx->last.kernel_launches = launches;
+    if (stats) stats->kernel_launches = launches;
+    ctx->have_frame = true;
+    ctx->last_W = W;
+    ctx->last_H = H;
+    ctx->last_tiles_x = tiles_x;
+    ctx->last_tiles_y = tiles_y;
+    return HEXFC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hexfc_style_default(hexfc_style* s)
+{
+    if (!s) return;
+    s->w_base = 2.f;
+    s->lod = 1;
+    s->delta = 0.5f;
+    s->s = 1.5f;
+    s->alpha_min = 0.1f;
+    s->alpha_max = 0.6f;
+    s->tf_lo = 0.f;
+    s->tf_hi = 1.f;
+    s->bg[0] = s->bg[1] = s->bg[2] = 0.f;
+    s->accent_beta = 0.2f;
+    s->halo_scale = 0.5f;
+    s->darken = 0.25f;
+    s->g_min = 0.5f;
+    s->g_max = 2.f;
+}
+
+hexfc_status hexfc_create(hexfc_ctx** out, int device, uint64_t frag_budget_bytes)
+{
+    if (!out) return HEXFC_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        (void)cudaGetLastError();
+        return HEXFC_ERR_CUDA;
+    }
+    hexfc_ctx* c = new (std::nothrow) hexfc_ctx();
+    if (!c) return HEXFC_ERR_OOM;
+    c->device = device;
+    c->budget = frag_budget_bytes;
+    hexfc_style_default(&c->style);
+    c->lens.mode = HEXFC_LENS_SCREEN;
+    c->lens.radius = 1.0;
+    *out = c;
+    return HEXFC_OK;
+}
+
+void hexfc_destroy(hexfc_ctx* ctx)
+{
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    for (DevMesh* m : ctx->meshes) free_mesh(m);
+    free_frame(ctx->fb);
+    dfree(ctx->d_out);
+    for (auto& set : ctx->ev)
+        for (auto& e : set)
+            if (e) cudaEventDestroy(e);
+    delete ctx;
+}
+
+hexfc_status hexfc_upload_mesh(hexfc_ctx* ctx, const float* verts, int64_t n_verts, const int32_t* cells,
+                               int64_t n_cells, const float* cell_scalar, const uint8_t* cell_edge_level,
+                               int32_t* mesh_id_out)
+{
+    if (!ctx || !verts || !cells || !mesh_id_out || n_verts <= 0) return HEXFC_ERR_ARG;
+    if (n_cells <= 0) return HEXFC_ERR_MESH;
+    if (n_verts >= (1ll << 31) || n_cells >= (1ll << 27)) return HEXFC_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    HostTables t;
+    if (build_host_tables(verts, n_verts, cells, n_cells, cell_edge_level, t) != 0) return HEXFC_ERR_MESH;
+    if (2 * t.n_faces >= (1ll << 32)) return HEXFC_ERR_ARG;
+    DevMesh* m = new (std::nothrow) DevMesh();
+    if (!m) return HEXFC_ERR_OOM;
+    m->n_verts = n_verts;
+    m->n_cells = n_cells;
+    m->n_faces = t.n_faces;
+    m->n_edges = t.n_edges;
+    hexfc_status st = HEXFC_OK;
+    auto A = [&](hexfc_status s2) { if (st == HEXFC_OK) st = s2; };
+    A(dalloc(&m->verts, 3 * (size_t)n_verts));
+    A(dalloc(&m->cells, 8 * (size_t)n_cells));
+    A(dalloc(&m->cell_edges, 12 * (size_t)n_cells));
+    A(dalloc(&m->cell_imp, (size_t)n_cells));
+    A(dalloc(&m->vkey, (size_t)n_verts));
+    A(dalloc(&m->ekey, (size_t)t.n_edges));
+    A(dalloc(&m->vimp, (size_t)n_verts));
+    A(dalloc(&m->eattr, (size_t)t.n_edges));
+    A(dalloc(&m->elevel, (size_t)t.n_edges));
+    A(dalloc(&m->fverts, (size_t)t.n_faces));
+    A(dalloc(&m->fedges, (size_t)t.n_faces));
+    A(dalloc(&m->fimp, (size_t)t.n_faces));
+    A(dalloc(&m->fpx, (size_t)t.n_faces));
+    A(dalloc(&m->fpy, (size_t)t.n_faces));
+    A(dalloc(&m->fpz, (size_t)t.n_faces));
+    if (st != HEXFC_OK) {
+        free_mesh(m);
+        return st;
+    }
+    cudaError_t e = cudaSuccess;
+    auto H2D = [&](void* d, const void* h, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice);
+    };
+    H2D(m->verts, verts, sizeof(float) * 3 * (size_t)n_verts);
+    H2D(m->cells, cells, sizeof(int32_t) * 8 * (size_t)n_cells);
+    H2D(m->cell_edges, t.cell_edges.data(), sizeof(int32_t) * t.cell_edges.size());
+    H2D(m->elevel, t.elevel.data(), t.elevel.size());
+    H2D(m->fverts, t.fverts.data(), sizeof(int32_t) * t.fverts.size());
+    H2D(m->fedges, t.fedges.data(), sizeof(int32_t) * t.fedges.size());
+    if (cell_scalar) H2D(m->cell_imp, cell_scalar, sizeof(float) * (size_t)n_cells);
+    if (e == cudaSuccess && !cell_scalar) e = launch_cell_quality(*m, HEXFC_METRIC_IMPORTANCE, m->cell_imp, 0);
+    if (e == cudaSuccess) e = launch_importance(*m, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        free_mesh(m);
+        return HEXFC_ERR_CUDA;
+    }
+    ctx->meshes.push_back(m);
+    *mesh_id_out = (int32_t)(ctx->meshes.size() - 1);
+    return HEXFC_OK;
+}
+
+hexfc_status hexfc_cell_quality(hexfc_ctx* ctx, int32_t mesh, int32_t metric, float* out, void* stream)
+{
+    if (!ctx || !out || metric < 0 || metric > 2) return HEXFC_ERR_ARG;
+    DevMesh* m = get_mesh(ctx, mesh);
+    if (!m) return HEXFC_ERR_STATE;
+    DeviceGuard g(ctx->device);
+    CK(launch_cell_quality(*m, metric, out, (cudaStream_t)stream));
+    return HEXFC_OK;
+}
+
+hexfc_status hexfc_set_cell_importance(hexfc_ctx* ctx, int32_t mesh, const float* cell_importance, void* stream)
+{
+    if (!ctx || !cell_importance) return HEXFC_ERR_ARG;
+    DevMesh* m = get_mesh(ctx, mesh);
+    if (!m) return HEXFC_ERR_STATE;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(m->cell_imp, cell_importance, sizeof(float) * (size_t)m->n_cells, cudaMemcpyDeviceToDevice, s));
+    CK(launch_importance(*m, s));
+    return HEXFC_OK;
+}
+
+hexfc_status hexfc_mesh_info(hexfc_ctx* ctx, int32_t mesh, int64_t* n_faces, int64_t* n_edges)
+{
+    DevMesh* m = get_mesh(ctx, mesh);
+    if (!m) return ctx ? HEXFC_ERR_STATE : HEXFC_ERR_ARG;
+    if (n_faces) *n_faces = m->n_faces;
+    if (n_edges) *n_edges = m->n_edges;
+    return HEXFC_OK;
+}
+
+hexfc_status hexfc_set_view(hexfc_ctx* ctx, const hexfc_view* v)
+{
+    if (!ctx || !v) return HEXFC_ERR_ARG;
+    if (v->width < 1 || v->height < 1 || v->width > 16384 || v->height > 16384) return HEXFC_ERR_ARG;
+    if (!(v->znear < v->zfar) || !std::isfinite(v->znear) || !std::isfinite(v->zfar)) return HEXFC_ERR_ARG;
+    if (!(v->fovy_deg >= 0.0)) return HEXFC_ERR_ARG;
+    CamParams c{};
+    double zref = 1.0;
+    if (!make_camera(v, c, zref)) return HEXFC_ERR_ARG;
+    ctx->view = *v;
+    ctx->cam = c;
+    ctx->zref = zref;
+    ctx->have_view = true;
+    return HEXFC_OK;
+}
+
+hexfc_status hexfc_set_lens(hexfc_ctx* ctx, const hexfc_lens* l)
+{
+    if (!ctx || !l) return HEXFC_ERR_ARG;
+    if (l->mode != HEXFC_LENS_SCREEN && l->mode != HEXFC_LENS_SPHERE) return HEXFC_ERR_ARG;
+    if (!(l->radius > 0.0) || !std::isfinite(l->radius)) return HEXFC_ERR_ARG;
+    ctx->lens = *l;
+    return HEXFC_OK;
+}
+
+hexfc_status hexfc_set_style(hexfc_ctx* ctx, const hexfc_style* s)
+{
+    if (!ctx || !s) return HEXFC_ERR_ARG;
+    if (!(s->w_base >= 0.f) || s->tf_hi == s->tf_lo || !(s->g_min <= s->g_max)) return HEXFC_ERR_ARG;
+    ctx->style = *s;
+    return HEXFC_OK;
+}
+
+hexfc_status hexfc_render(hexfc_ctx* ctx, int32_t mesh, float* out_rgba, hexfc_frame_stats* stats, void* stream)
+{
+    if (!ctx || !out_rgba) return HEXFC_ERR_ARG;
+    DevMesh* m = get_mesh(ctx, mesh);
+    if (!m || !ctx->have_view) return HEXFC_ERR_STATE;
+    DeviceGuard g(ctx->device);
+    return render_frame(ctx, m, out_rgba, stats, (cudaStream_t)stream);
+}
+
+hexfc_status hexfc_render_host(hexfc_ctx* ctx, int32_t mesh, float* out_rgba_host, hexfc_frame_stats* stats,
+                               void* stream)
+{
+    if (!ctx || !out_rgba_host) return HEXFC_ERR_ARG;
+    DevMesh* m = get_mesh(ctx, mesh);
+    if (!m || !ctx->have_view) return HEXFC_ERR_STATE;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = sizeof(float) * 4 * (size_t)ctx->view.width * (size_t)ctx->view.height;
+    hexfc_status st = ensure(&ctx->d_out, &ctx->d_out_cap, (int64_t)(bytes / sizeof(float)));
+    if (st != HEXFC_OK) return st;
+    float* d_out = ctx->d_out;
+    st = render_frame(ctx, m, d_out, stats, s);
+    if (st == HEXFC_OK) {
+        cudaError_t e = cudaMemcpyAsync(out_rgba_host, d_out, bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            st = HEXFC_ERR_CUDA;
+        }
+    }
+    return st;
+}
+
+hexfc_status hexfc_debug_pixels(hexfc_ctx* ctx, const int32_t* px, const int32_t* py, int64_t n, uint32_t* counts,
+                                uint64_t* keys, float* rgba, uint64_t cap)
+{
+    if (!ctx || !px || !py || !counts || n < 0) return HEXFC_ERR_ARG;
+    if (!ctx->have_frame) return HEXFC_ERR_STATE;
+    for (int64_t i = 0; i < n; ++i)
+        if (px[i] < 0 || py[i] < 0 || px[i] >= ctx->last_W || py[i] >= ctx->last_H) return HEXFC_ERR_ARG;
+    if (n == 0) return HEXFC_OK;
+    DeviceGuard g(ctx->device);
+    FrameBufs& fb = ctx->fb;
+    int32_t *d_px = nullptr, *d_py = nullptr;
+    uint32_t* d_cnt = nullptr;
+    uint64_t* d_off = nullptr;
+    uint64_t* d_keys = nullptr;
+    float4* d_rgba = nullptr;
+    hexfc_status st = HEXFC_OK;
+    auto cleanup = [&]() {
+        dfree(d_px); dfree(d_py); dfree(d_cnt); dfree(d_off); dfree(d_keys); dfree(d_rgba);
+    };
+    if ((st = dalloc(&d_px, (size_t)n)) != HEXFC_OK || (st = dalloc(&d_py, (size_t)n)) != HEXFC_OK ||
+        (st = dalloc(&d_cnt, (size_t)n)) != HEXFC_OK || (st = dalloc(&d_off, (size_t)n)) != HEXFC_OK) {
+        cleanup();
+        return st;
+    }
+    cudaError_t e = cudaMemcpy(d_px, px, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_py, py, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_debug_gather(fb, d_px, d_py, n, nullptr, ctx->last_tiles_x, ctx->last_W, ctx->last_H, nullptr,
+                                nullptr, d_cnt, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(counts, d_cnt, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        cleanup();
+        return HEXFC_ERR_CUDA;
+    }
+    std::vector<uint64_t> hoff((size_t)n);
+    uint64_t total = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        hoff[(size_t)i] = total;
+        total += counts[i];
+    }
+    if (!keys && !rgba) {
+        cleanup();
+        return HEXFC_OK;
+    }
+    if (total > cap) {
+        cleanup();
+        return HEXFC_ERR_OVERFLOW;
+    }
+    if ((st = dalloc(&d_keys, (size_t)total)) != HEXFC_OK || (st = dalloc(&d_rgba, (size_t)total)) != HEXFC_OK) {
+        cleanup();
+        return st;
+    }
+    e = cudaMemcpy(d_off, hoff.data(), sizeof(uint64_t) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_debug_gather(fb, d_px, d_py, n, d_off, ctx->last_tiles_x, ctx->last_W, ctx->last_H, d_keys, d_rgba,
+                                nullptr, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && keys) e = cudaMemcpy(keys, d_keys, sizeof(uint64_t) * total, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && rgba) e = cudaMemcpy(rgba, d_rgba, sizeof(float4) * total, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && fb.scal) {
+        uint64_t errflag = 0;
+        e = cudaMemcpy(&errflag, fb.scal + 5, sizeof(uint64_t), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && errflag) st = HEXFC_ERR_CUDA;
+    }
+    cleanup();
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HEXFC_ERR_CUDA;
+    }
+    return st;
+}
+
+hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value)
+{
+    if (!ctx) return HEXFC_ERR_ARG;
+    switch (option) {
+    case HEXFC_OPT_REVERSE_BIN_ORDER: ctx->reverse_bins = value != 0; return HEXFC_OK;
+    case HEXFC_OPT_STAGE_TIMING: ctx->timing = value != 0; return HEXFC_OK;
+    default: return HEXFC_ERR_ARG;
+    }
+}
+
+hexfc_status hexfc_stage_times(hexfc_ctx* ctx, double* ms, uint64_t* frames, int32_t reset)
+{
+    if (!ctx || !ms || !frames) return HEXFC_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    collect_set(ctx, ctx->ev_cur ^ 1);
+    collect_set(ctx, ctx->ev_cur);
+    for (int k = 0; k < HEXFC_N_STAGES; ++k) ms[k] = ctx->stage_ms[k];
+    *frames = ctx->timed_frames;
+    if (reset) {
+        for (double& v : ctx->stage_ms) v = 0.0;
+        ctx->timed_frames = 0;
+    }
+    return HEXFC_OK;
+}
+
+const char* hexfc_status_string(hexfc_status s)
+{
+    switch (s) {
+    case HEXFC_OK: return "ok";
+    case HEXFC_ERR_ARG: return "invalid argument";
+    case HEXFC_ERR_OOM: return "out of memory or fragment budget exceeded";
+    case HEXFC_ERR_OVERFLOW: return "per-pixel list or output capacity exceeded";
+    case HEXFC_ERR_CUDA: return "CUDA error";
+    case HEXFC_ERR_TIMEOUT: return "device wait timed out";
+    case HEXFC_ERR_MESH: return "malformed mesh";
+    case HEXFC_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

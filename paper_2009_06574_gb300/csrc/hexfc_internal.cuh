@@ -1,0 +1,121 @@
+// Internal declarations of the hexfc CUDA library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hexfc.h"
+
+namespace hexfc {
+
+constexpr int kTile = 16;                 // raster tile edge in pixels
+constexpr int kTilePix = kTile * kTile;   // pixels (= threads) per tile CTA
+constexpr int kWarpSortMax = 256;         // longest list sorted in registers by one warp
+constexpr uint64_t kPadKey = ~0ull;
+
+// Camera constants of the vertex stage (double, evaluated without FMA).
+struct CamParams {
+    double eye[3], R[3], U[3], F[3];
+    double focal, scale, cx, cy, znear, zfar, zf_over;
+    int ortho, W, H;
+};
+
+// Focus+context constants of the fragment stage (float).
+struct ShadeParams {
+    int lens_mode;
+    float lens_c[3];
+    float lens_inv_r;
+    float w_base;
+    int lod;
+    float delta, s;
+    float alpha_min, alpha_span;   // alpha_hat = alpha_min + alpha_span * t
+    float tf_lo, tf_inv;           // t = clamp((imp - tf_lo) * tf_inv, 0, 1)
+    float bg[3];
+    float accent_beta, halo_scale, darken, g_min, g_max;
+    float zref;
+    int ortho;
+};
+
+// Resident mesh (device pointers), see hexfc_upload_mesh.
+struct DevMesh {
+    int64_t n_verts = 0, n_cells = 0, n_faces = 0, n_edges = 0;
+    float* verts = nullptr;        // [V*3]
+    int32_t* cells = nullptr;      // [C*8]
+    int32_t* cell_edges = nullptr; // [C*12] unique edge id per cell edge
+    float* cell_imp = nullptr;     // [C]
+    int32_t* vkey = nullptr;       // [V] ordered-int max of incident importance
+    int32_t* ekey = nullptr;       // [E]
+    float* vimp = nullptr;         // [V]
+    float* eattr = nullptr;        // [E]
+    uint8_t* elevel = nullptr;     // [E]
+    int4* fverts = nullptr;        // [F] canonical corners
+    int4* fedges = nullptr;        // [F] unique edge id of local edge k = (c_k, c_k+1)
+    float4* fimp = nullptr;        // [F] corner importance
+    float4* fpx = nullptr;         // [F] corner world x (y, z below)
+    float4* fpy = nullptr;
+    float4* fpz = nullptr;
+};
+
+// Per-frame buffers owned by the context.
+struct FrameBufs {
+    // vertex stage
+    int4* vproj = nullptr;   // {X, Y, z24, valid}
+    float* ved = nullptr;    // eye depth
+    int64_t v_cap = 0;
+    // face stage
+    int4* fx = nullptr;      // corner X (16.8)
+    int4* fy = nullptr;      // corner Y (16.8)
+    uint4* fz = nullptr;     // corner z24
+    float4* fed = nullptr;   // corner eye depth
+    uint32_t* fflags = nullptr;  // bits 0-3 focus-visible edges, 4-7 context-visible, 8-9 triangle valid
+    int64_t f_cap = 0;
+    // tiles
+    uint32_t* tile_cnt = nullptr;   // [T+1]
+    uint64_t* tile_off = nullptr;   // [T+1]
+    uint32_t* tile_cur = nullptr;   // [T]
+    int64_t t_cap = 0;
+    uint32_t* bins = nullptr;       // face2tri ids grouped by tile
+    int64_t bin_cap = 0;
+    // pixels (tile-major)
+    uint32_t* cnt = nullptr;        // [P]
+    uint64_t* off = nullptr;        // [P]
+    int64_t p_cap = 0;
+    uint64_t* part = nullptr;       // scan partials
+    uint32_t* part_max = nullptr;
+    int64_t part_cap = 0;
+    uint32_t* long_q = nullptr;     // queue of pixels with long lists
+    // fragments
+    uint64_t* key = nullptr;
+    float4* rgba = nullptr;
+    int64_t frag_cap = 0;
+    // small device scalars: [0] total fragments, [1] max list, [2] long lists, [3] long queue cursor,
+    // [4] bin total, [5] error flags
+    uint64_t* scal = nullptr;
+    uint64_t* h_scal = nullptr;     // pinned mirror
+};
+
+// ---- launches (each returns cudaGetLastError()) -----------------------------------------
+cudaError_t launch_cell_quality(const DevMesh& m, int metric, float* out, cudaStream_t s);
+cudaError_t launch_importance(const DevMesh& m, cudaStream_t s);
+
+cudaError_t launch_vertex_setup(const DevMesh& m, const CamParams& cam, FrameBufs& fb, cudaStream_t s);
+cudaError_t launch_face_setup(const DevMesh& m, const CamParams& cam, int lod, float delta,
+                              FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_t s);
+cudaError_t launch_bin_fill(const DevMesh& m, FrameBufs& fb, int tiles_x, int W, int H, int reverse,
+                            cudaStream_t s);
+cudaError_t launch_count(FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, cudaStream_t s);
+cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x,
+                        int tiles_y, int W, int H, cudaStream_t s);
+cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W,
+                             int H, float* out, uint32_t n_long, cudaStream_t s);
+cudaError_t launch_debug_gather(FrameBufs& fb, const int32_t* d_px, const int32_t* d_py, int64_t n,
+                                const uint64_t* d_dst_off, int tiles_x, int W, int H,
+                                uint64_t* d_keys, float4* d_rgba, uint32_t* d_counts,
+                                cudaStream_t s);
+
+// scans
+cudaError_t scan_u32_to_u64(const uint32_t* in, uint64_t* out, int64_t n, uint64_t* part,
+                            uint32_t* part_max, uint64_t* total_and_max, uint32_t long_threshold,
+                            cudaStream_t s);
+int64_t scan_partials_needed(int64_t n);
+
+}  // namespace hexfc

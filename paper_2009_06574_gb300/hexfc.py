@@ -1,0 +1,341 @@
+"""Python binding of the hexfc C ABI (include/hexfc.h).
+
+Argument marshalling only: every step of the renderer runs in the CUDA
+library. The functions keep the C names (hexfc_create, hexfc_upload_mesh,
+hexfc_set_view, hexfc_set_lens, hexfc_set_style, hexfc_render, ...); the
+`Renderer` class is a small convenience wrapper around one context. Device
+buffers are torch CUDA tensors; streams are torch CUDA streams. If the
+library cannot be built or loaded, every call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+HEXFC_OK = 0
+HEXFC_ERR_ARG = -1
+HEXFC_ERR_OOM = -2
+HEXFC_ERR_OVERFLOW = -3
+HEXFC_ERR_CUDA = -4
+HEXFC_ERR_TIMEOUT = -5
+HEXFC_ERR_MESH = -6
+HEXFC_ERR_STATE = -7
+HEXFC_MAX_LIST = 8192
+HEXFC_LENS_SCREEN = 0
+HEXFC_LENS_SPHERE = 1
+HEXFC_METRIC_SCALED_JACOBIAN = 0
+HEXFC_METRIC_JACOBIAN_RATIO = 1
+HEXFC_METRIC_IMPORTANCE = 2
+HEXFC_OPT_REVERSE_BIN_ORDER = 1
+HEXFC_OPT_STAGE_TIMING = 2
+STAGES = ["vertex", "face", "tile_scan", "gap1", "bin", "count", "scan", "gap2", "fill", "composite"]
+
+# every symbol include/hexfc.h declares
+EXPORTS = ["hexfc_style_default", "hexfc_create", "hexfc_destroy", "hexfc_upload_mesh", "hexfc_cell_quality",
+           "hexfc_set_cell_importance", "hexfc_mesh_info", "hexfc_set_view", "hexfc_set_lens",
+           "hexfc_set_style", "hexfc_render", "hexfc_render_host", "hexfc_debug_pixels", "hexfc_set_option",
+           "hexfc_stage_times", "hexfc_status_string"]
+
+
+class HexfcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+        self.status = status
+
+
+class hexfc_view(C.Structure):
+    _fields_ = [("eye", C.c_double * 3), ("target", C.c_double * 3), ("up", C.c_double * 3),
+                ("fovy_deg", C.c_double), ("ortho_half_h", C.c_double), ("znear", C.c_double),
+                ("zfar", C.c_double), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class hexfc_lens(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("pad", C.c_int32), ("center", C.c_double * 3), ("radius", C.c_double)]
+
+
+class hexfc_style(C.Structure):
+    _fields_ = [("w_base", C.c_float), ("lod", C.c_int32), ("delta", C.c_float), ("s", C.c_float),
+                ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("tf_lo", C.c_float), ("tf_hi", C.c_float),
+                ("bg", C.c_float * 3), ("accent_beta", C.c_float), ("halo_scale", C.c_float),
+                ("darken", C.c_float), ("g_min", C.c_float), ("g_max", C.c_float)]
+
+
+class hexfc_frame_stats(C.Structure):
+    _fields_ = [("fragments", C.c_uint64), ("bin_entries", C.c_uint64), ("max_list", C.c_uint32),
+                ("long_lists", C.c_uint32), ("width", C.c_uint32), ("height", C.c_uint32),
+                ("kernel_launches", C.c_uint32), ("covered_pixels", C.c_uint32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load (building first if missing or stale) the CUDA library."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+            sig = {
+                "hexfc_style_default": (None, [C.POINTER(hexfc_style)]),
+                "hexfc_create": (i32, [C.POINTER(vp), C.c_int, u64]),
+                "hexfc_destroy": (None, [vp]),
+                "hexfc_upload_mesh": (i32, [vp, vp, i64, vp, i64, vp, vp, C.POINTER(i32)]),
+                "hexfc_cell_quality": (i32, [vp, i32, i32, vp, vp]),
+                "hexfc_set_cell_importance": (i32, [vp, i32, vp, vp]),
+                "hexfc_mesh_info": (i32, [vp, i32, C.POINTER(i64), C.POINTER(i64)]),
+                "hexfc_set_view": (i32, [vp, C.POINTER(hexfc_view)]),
+                "hexfc_set_lens": (i32, [vp, C.POINTER(hexfc_lens)]),
+                "hexfc_set_style": (i32, [vp, C.POINTER(hexfc_style)]),
+                "hexfc_render": (i32, [vp, i32, vp, C.POINTER(hexfc_frame_stats), vp]),
+                "hexfc_render_host": (i32, [vp, i32, vp, C.POINTER(hexfc_frame_stats), vp]),
+                "hexfc_debug_pixels": (i32, [vp, vp, vp, i64, vp, vp, vp, u64]),
+                "hexfc_set_option": (i32, [vp, i32, i64]),
+                "hexfc_stage_times": (i32, [vp, vp, C.POINTER(u64), i32]),
+                "hexfc_status_string": (C.c_char_p, [i32]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return load().hexfc_status_string(int(s)).decode()
+
+
+def _check(status: int, what: str):
+    if status != HEXFC_OK:
+        raise HexfcError(status, what)
+
+
+def _np_ptr(a):
+    return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def make_view(v) -> hexfc_view:
+    o = hexfc_view()
+    o.eye[:] = [float(x) for x in v.eye]
+    o.target[:] = [float(x) for x in v.target]
+    o.up[:] = [float(x) for x in v.up]
+    o.fovy_deg, o.ortho_half_h = float(v.fovy_deg), float(v.ortho_half_h)
+    o.znear, o.zfar = float(v.znear), float(v.zfar)
+    o.width, o.height = int(v.width), int(v.height)
+    return o
+
+
+def make_lens(l) -> hexfc_lens:
+    o = hexfc_lens()
+    o.mode = int(l.mode)
+    c = list(l.center) + [0.0] * (3 - len(l.center))
+    o.center[:] = [float(x) for x in c[:3]]
+    o.radius = float(l.radius)
+    return o
+
+
+def make_style(s) -> hexfc_style:
+    o = hexfc_style()
+    load().hexfc_style_default(C.byref(o))
+    if s is None:
+        return o
+    for name, _ in hexfc_style._fields_:
+        if not hasattr(s, name):
+            continue
+        if name == "bg":
+            o.bg[:] = [float(x) for x in s.bg]
+        elif name == "lod":
+            o.lod = int(s.lod)
+        else:
+            setattr(o, name, float(getattr(s, name)))
+    return o
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(int(stream.cuda_stream))
+
+
+class Renderer:
+    """One hexfc context on one CUDA device."""
+
+    def __init__(self, device: int = 0, frag_budget_bytes: int = 0):
+        L = load()
+        h = C.c_void_p()
+        _check(L.hexfc_create(C.byref(h), int(device), int(frag_budget_bytes)), "hexfc_create")
+        self._h = h
+        self.device = device
+        self.view = None
+        self.last_stats = None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.hexfc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- meshes
+    def upload_mesh(self, verts, cells, cell_scalar=None, cell_edge_level=None) -> int:
+        v = np.ascontiguousarray(verts, dtype=np.float32)
+        c = np.ascontiguousarray(cells, dtype=np.int32)
+        s = np.ascontiguousarray(cell_scalar, dtype=np.float32) if cell_scalar is not None else None
+        l = np.ascontiguousarray(cell_edge_level, dtype=np.uint8) if cell_edge_level is not None else None
+        mid = C.c_int32(-1)
+        _check(load().hexfc_upload_mesh(self._h, _np_ptr(v), v.shape[0], _np_ptr(c), c.shape[0], _np_ptr(s),
+                                        _np_ptr(l), C.byref(mid)), "hexfc_upload_mesh")
+        return mid.value
+
+    def mesh_info(self, mesh: int):
+        nf, ne = C.c_int64(0), C.c_int64(0)
+        _check(load().hexfc_mesh_info(self._h, int(mesh), C.byref(nf), C.byref(ne)), "hexfc_mesh_info")
+        return nf.value, ne.value
+
+    def cell_quality(self, mesh: int, metric: int, out, stream=None):
+        """out: torch float32 CUDA tensor of n_cells."""
+        _check(load().hexfc_cell_quality(self._h, int(mesh), int(metric), C.c_void_p(out.data_ptr()),
+                                         _stream_ptr(stream)), "hexfc_cell_quality")
+        return out
+
+    def set_cell_importance(self, mesh: int, cell_importance, stream=None):
+        _check(load().hexfc_set_cell_importance(self._h, int(mesh), C.c_void_p(cell_importance.data_ptr()),
+                                                _stream_ptr(stream)), "hexfc_set_cell_importance")
+
+    # ---- state
+    def set_view(self, view):
+        self.view = view
+        v = make_view(view)
+        _check(load().hexfc_set_view(self._h, C.byref(v)), "hexfc_set_view")
+
+    def set_lens(self, lens):
+        l = make_lens(lens)
+        _check(load().hexfc_set_lens(self._h, C.byref(l)), "hexfc_set_lens")
+
+    def set_style(self, style):
+        s = make_style(style)
+        _check(load().hexfc_set_style(self._h, C.byref(s)), "hexfc_set_style")
+
+    def set_option(self, option: int, value: int):
+        _check(load().hexfc_set_option(self._h, int(option), int(value)), "hexfc_set_option")
+
+    def stage_times(self, reset: bool = True):
+        """Summed per-stage milliseconds and the number of timed frames."""
+        ms = np.zeros(len(STAGES), dtype=np.float64)
+        n = C.c_uint64(0)
+        _check(load().hexfc_stage_times(self._h, _np_ptr(ms), C.byref(n), int(bool(reset))), "hexfc_stage_times")
+        return dict(zip(STAGES, ms.tolist())), n.value
+
+    # ---- frames
+    def render(self, mesh: int, out, stream=None, check: bool = True):
+        """out: torch float32 CUDA tensor [H, W, 4]. Returns the status."""
+        st = hexfc_frame_stats()
+        r = load().hexfc_render(self._h, int(mesh), C.c_void_p(out.data_ptr()), C.byref(st), _stream_ptr(stream))
+        self.last_stats = st.as_dict()
+        if check:
+            _check(r, "hexfc_render")
+        return r
+
+    def render_host(self, mesh: int, out: np.ndarray, stream=None, check: bool = True):
+        """out: numpy float32 [H, W, 4] (ideally pinned)."""
+        assert out.dtype == np.float32 and out.flags["C_CONTIGUOUS"]
+        st = hexfc_frame_stats()
+        r = load().hexfc_render_host(self._h, int(mesh), _np_ptr(out), C.byref(st), _stream_ptr(stream))
+        self.last_stats = st.as_dict()
+        if check:
+            _check(r, "hexfc_render_host")
+        return r
+
+    def render_host_ptr(self, mesh: int, host_ptr: int, stream=None):
+        st = hexfc_frame_stats()
+        r = load().hexfc_render_host(self._h, int(mesh), C.c_void_p(host_ptr), C.byref(st), _stream_ptr(stream))
+        self.last_stats = st.as_dict()
+        _check(r, "hexfc_render_host")
+
+    def debug_pixels(self, px, py, fragments: bool = True):
+        """Sorted fragment lists of the last frame for the listed pixels:
+        dict(counts, offsets, keys, rgba)."""
+        px = np.ascontiguousarray(px, dtype=np.int32)
+        py = np.ascontiguousarray(py, dtype=np.int32)
+        n = px.shape[0]
+        counts = np.zeros(n, dtype=np.uint32)
+        L = load()
+        _check(L.hexfc_debug_pixels(self._h, _np_ptr(px), _np_ptr(py), n, _np_ptr(counts), None, None, 0),
+               "hexfc_debug_pixels")
+        off = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum(counts, out=off[1:])
+        out = {"counts": counts, "offsets": off}
+        if fragments:
+            tot = int(off[-1])
+            keys = np.zeros(max(tot, 1), dtype=np.uint64)
+            rgba = np.zeros((max(tot, 1), 4), dtype=np.float32)
+            _check(L.hexfc_debug_pixels(self._h, _np_ptr(px), _np_ptr(py), n, _np_ptr(counts), _np_ptr(keys),
+                                        _np_ptr(rgba), tot), "hexfc_debug_pixels")
+            out["keys"] = keys[:tot]
+            out["rgba"] = rgba[:tot]
+        return out
+
+
+# C-named module-level wrappers (thin): the same calls as include/hexfc.h
+def hexfc_create(device: int = 0, frag_budget_bytes: int = 0) -> Renderer:
+    return Renderer(device, frag_budget_bytes)
+
+
+def hexfc_destroy(r: Renderer):
+    r.close()
+
+
+def hexfc_upload_mesh(r: Renderer, verts, cells, cell_scalar=None, cell_edge_level=None) -> int:
+    return r.upload_mesh(verts, cells, cell_scalar, cell_edge_level)
+
+
+def hexfc_cell_quality(r: Renderer, mesh: int, metric: int, out, stream=None):
+    return r.cell_quality(mesh, metric, out, stream)
+
+
+def hexfc_set_cell_importance(r: Renderer, mesh: int, cell_importance, stream=None):
+    return r.set_cell_importance(mesh, cell_importance, stream)
+
+
+def hexfc_set_view(r: Renderer, view):
+    return r.set_view(view)
+
+
+def hexfc_set_lens(r: Renderer, lens):
+    return r.set_lens(lens)
+
+
+def hexfc_set_style(r: Renderer, style):
+    return r.set_style(style)
+
+
+def hexfc_render(r: Renderer, mesh: int, out, stream=None):
+    return r.render(mesh, out, stream)
+
+
+def hexfc_render_host(r: Renderer, mesh: int, out, stream=None):
+    return r.render_host(mesh, out, stream)
+
+
+def hexfc_debug_pixels(r: Renderer, px, py):
+    return r.debug_pixels(px, py)

@@ -286,10 +286,12 @@ def grid64_orbit_1080p() -> Workload:
     """64^3 warped+jittered grid (262,144 cells), 1920x1080, 60 deg FOV, 120-frame
     orbit with a Lissajous sphere lens, face alpha 0.1-0.6."""
     return Workload("grid64_warp0.3_jitter0.1_orbit120_1920x1080", 64, 0.1, 0.3, 2, 1920, 1080,
-                    120, Style(w_base=2.0, lod=4, delta=0.5, alpha_min=0.1, alpha_max=0.6))
+                    120, Style(w_base=2.0, lod=4, delta=0.08, alpha_min=0.1, alpha_max=0.6, tf_lo=0.0,
+                               tf_hi=0.15))
 
 
 def grid128_orbit_4k() -> Workload:
     """128^3 warped grid (2.1M cells) at 3840x2160 (the cubic128-sized case)."""
     return Workload("grid128_warp0.3_jitter0.1_orbit500_3840x2160", 128, 0.1, 0.3, 4, 3840, 2160,
-                    500, Style(w_base=2.0, lod=5, delta=0.5, alpha_min=0.1, alpha_max=0.6))
+                    500, Style(w_base=2.0, lod=5, delta=0.08, alpha_min=0.1, alpha_max=0.6, tf_lo=0.0,
+                               tf_hi=0.15))

@@ -1,0 +1,76 @@
+"""Parity between the CUDA renderer and the CPU oracle on the same inputs.
+
+Counts and sorted keys must match bit for bit. Per-fragment RGBA (FP32 on the
+GPU, FP64 in the oracle) and the composited image must agree within TOL. A
+fragment whose discrete decision (edge / halo / accentuation threshold) lies
+within the oracle's tie margin may have taken either side on the GPU: it is
+accepted only if it matches one of the oracle's own alternatives (the oracle
+evaluated with that decision flipped), and the pixel's expected colour is then
+recomposited by the oracle from the accepted alternatives.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+import oracle
+
+TOL = 1e-5
+
+
+def _subsets(bits: int):
+    idx = [b for b in range(4) if bits & (1 << b)]
+    for r in range(1, len(idx) + 1):
+        for combo in itertools.combinations(idx, r):
+            yield sum(1 << b for b in combo)
+
+
+def compare_lists(gpu: dict, orc: dict, om: "oracle.Mesh", view, lens, style, px, py, tol: float = TOL,
+                  gpu_image=None):
+    """gpu: Renderer.debug_pixels(...) output; orc: oracle.Mesh.render(...) output for
+    the same pixels. gpu_image: [npix, 4] GPU pixels in the same order (optional).
+    Returns a dict of statistics; raises AssertionError on a mismatch."""
+    cg, co = gpu["counts"].astype(np.int64), orc["counts"].astype(np.int64)
+    bad = np.nonzero(cg != co)[0]
+    assert len(bad) == 0, f"count mismatch at {len(bad)} pixels, first {bad[:5]}: gpu {cg[bad[:5]]} oracle {co[bad[:5]]}"
+    kg, ko = gpu["keys"], orc["keys"]
+    assert kg.shape == ko.shape
+    kb = np.nonzero(kg != ko)[0]
+    assert len(kb) == 0, f"key mismatch at {len(kb)} fragments, first {kb[:5]}: {kg[kb[:5]]} vs {ko[kb[:5]]}"
+    rg = gpu["rgba"].astype(np.float64)
+    ro = orc["rgba"].copy()
+    err = np.abs(rg - ro).max(axis=1) if len(rg) else np.zeros(0)
+    tie = orc["tie"]
+    off = orc["offsets"]
+    pix_of = np.repeat(np.arange(len(cg)), cg)
+    n_alt = 0
+    for j in np.nonzero(err > tol)[0]:
+        ok = False
+        if tie[j]:
+            i = pix_of[j]
+            f2t = int(ko[j]) & 0xFFFFFFFF
+            for flip in _subsets(int(tie[j])):
+                alt = om.shade(view, lens, style, int(px[i]), int(py[i]), f2t, flip)
+                assert alt is not None
+                if np.abs(alt[0] - rg[j]).max() <= tol:
+                    ro[j] = alt[0]
+                    ok = True
+                    n_alt += 1
+                    break
+        assert ok, (f"fragment {j} (pixel {px[pix_of[j]]},{py[pix_of[j]]}, key {int(ko[j]):#x}, tie {tie[j]}): "
+                    f"gpu {rg[j]} oracle {orc['rgba'][j]} err {err[j]:.3g}")
+    stats = {"pixels": int(len(cg)), "fragments": int(len(kg)), "max_frag_err": float(err.max()) if len(err) else 0.0,
+             "tie_fragments": int(np.count_nonzero(tie)), "accepted_alternatives": n_alt}
+    if gpu_image is not None:
+        exp = orc["image"].copy()
+        if n_alt:
+            touched = np.unique(pix_of[np.nonzero(err > tol)[0]])
+            for i in touched:
+                exp[i] = oracle.composite(ro[off[i]:off[i + 1]], style.bg)
+        ie = np.abs(gpu_image.astype(np.float64) - exp).max(axis=1)
+        worst = int(np.argmax(ie)) if len(ie) else 0
+        stats["max_pixel_err"] = float(ie.max()) if len(ie) else 0.0
+        assert stats["max_pixel_err"] <= tol, (f"pixel ({px[worst]},{py[worst]}) gpu {gpu_image[worst]} "
+                                               f"oracle {exp[worst]} err {ie[worst]:.3g}")
+    return stats

@@ -1,0 +1,277 @@
+"""GPU parity: the CUDA renderer (through the C ABI) against the CPU oracle.
+
+Counts and sorted keys bit-exact; fragment RGBA and image within 1e-5
+(FP32 shading against FP64); near-tie decisions resolved as in parity.py.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_06574_gb300 import synth
+
+from parity import TOL, compare_lists
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_06574_gb300 import hexfc
+    hexfc.load()
+    return hexfc
+
+
+def render_both(hx, mesh, view, lens, style, px=None, py=None, scalar=None):
+    scalar = mesh.cell_scalar if scalar is None else scalar
+    r = hx.Renderer(0)
+    mid = r.upload_mesh(mesh.verts, mesh.cells, scalar, mesh.edge_level)
+    r.set_view(view)
+    r.set_lens(lens)
+    r.set_style(style)
+    out = torch.zeros((view.height, view.width, 4), dtype=torch.float32, device="cuda")
+    r.render(mid, out)
+    torch.cuda.synchronize()
+    if px is None:
+        yy, xx = np.meshgrid(np.arange(view.height), np.arange(view.width), indexing="ij")
+        px, py = xx.ravel().astype(np.int32), yy.ravel().astype(np.int32)
+    g = r.debug_pixels(px, py)
+    img = out.cpu().numpy()[py, px]
+    om = oracle.Mesh(mesh.verts, mesh.cells, scalar, mesh.edge_level)
+    o = om.render(view, lens, style, px, py)
+    stats = compare_lists(g, o, om, view, lens, style, px, py, gpu_image=img)
+    stats["gpu_stats"] = r.last_stats
+    r.close()
+    return stats, out
+
+
+def test_small_ortho_full_frame(hx):
+    """4^3 jittered grid, 256x256 orthographic, sphere lens r=0.3 at the centre."""
+    w = synth.grid4_ortho_256()
+    st, _ = render_both(hx, w.mesh(), w.view(0), w.lens(0), w.style)
+    assert st["fragments"] > 100000
+    assert st["gpu_stats"]["fragments"] == st["fragments"]
+
+
+@pytest.mark.parametrize("frame", [0, 17, 40, 77])
+@pytest.mark.parametrize("lens_mode", [synth.LENS_SPHERE, synth.LENS_SCREEN])
+def test_perspective_orbit_ragged(hx, frame, lens_mode):
+    """8^3 warped grid on the orbit at 250x190 (ragged tiles), both lens modes."""
+    mesh = synth.hex_grid(8, jitter=0.1, warp_amp=0.3, seed=2)
+    view = synth.orbit_view(frame, 120, 250, 190)
+    if lens_mode == synth.LENS_SPHERE:
+        lens = synth.lissajous_lens(frame, 120)
+    else:
+        lens = synth.Lens(mode=synth.LENS_SCREEN, center=(120.0, 90.0, 0.0), radius=70.0)
+    style = synth.Style(w_base=1.5, lod=2, delta=0.6, s=1.5)
+    st, _ = render_both(hx, mesh, view, lens, style)
+    assert st["fragments"] > 1000
+
+
+@pytest.mark.parametrize("style_kw", [dict(s=3.0, alpha_min=0.0, alpha_max=1.0),
+                                      dict(bg=(1.0, 1.0, 1.0), w_base=3.0, lod=1, delta=0.3),
+                                      dict(w_base=0.0, lod=100, delta=2.0),
+                                      dict(tf_lo=0.2, tf_hi=0.7, g_min=1.0, g_max=1.0, halo_scale=1.0)])
+def test_style_variants(hx, style_kw):
+    mesh = synth.hex_grid(6, jitter=0.15, warp_amp=0.2, seed=5)
+    view = synth.orbit_view(33, 120, 160, 120, radius=1.6)
+    st, _ = render_both(hx, mesh, view, synth.lissajous_lens(33, 120, radius=0.4), synth.Style(**style_kw))
+
+
+def test_axis_aligned_cube(hx):
+    v = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0], [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]],
+                 np.float32) - 0.5
+    mesh = synth.HexMesh(v, np.arange(8, dtype=np.int32).reshape(1, 8), np.array([0.5], np.float32),
+                         np.zeros((1, 12), np.uint8))
+    view = synth.View(eye=(0, 0, 5.0), fovy_deg=0.0, ortho_half_h=1.0, znear=1.0, zfar=9.0, width=64, height=64)
+    st, _ = render_both(hx, mesh, view, synth.Lens(mode=0, center=(32, 32, 0), radius=10.0), synth.Style())
+    assert st["fragments"] == 2 * 32 * 32
+
+
+def test_long_lists(hx):
+    """A 1x1x300 column of cells seen along its axis: 301 fragments per pixel,
+    past the register sort (256), through the shared-memory path."""
+    nz = 300
+    xs = np.array([-0.2, 0.2], np.float32)
+    verts = np.array([(x, y, z) for z in np.linspace(-0.5, 0.5, nz + 1) for y in xs for x in xs], np.float32)
+    cells = []
+    for k in range(nz):
+        b = 4 * k
+        cells.append([b, b + 1, b + 3, b + 2, b + 4, b + 5, b + 7, b + 6])
+    cells = np.array(cells, np.int32)
+    scalar = (np.arange(nz, dtype=np.float32) % 7) / 7.0
+    mesh = synth.HexMesh(verts, cells, scalar, np.zeros((nz, 12), np.uint8))
+    view = synth.View(eye=(0.0, 0.0, 3.0), fovy_deg=0.0, ortho_half_h=0.5, znear=0.5, zfar=5.0, width=40, height=40)
+    style = synth.Style(alpha_min=0.05, alpha_max=0.3)
+    st, _ = render_both(hx, mesh, view, synth.Lens(mode=0, center=(20, 20, 0), radius=12.0), style)
+    assert st["gpu_stats"]["max_list"] == nz + 1
+    assert st["gpu_stats"]["long_lists"] > 100
+
+
+def test_empty_frame_is_background(hx):
+    mesh = synth.hex_grid(4, jitter=0.1, seed=1)
+    view = synth.View(eye=(0, 0, 3.0), target=(0, 0, 6.0), fovy_deg=45.0, znear=0.1, zfar=10.0, width=70, height=50)
+    style = synth.Style(bg=(0.25, 0.5, 0.75))
+    st, out = render_both(hx, mesh, view, synth.Lens(), style)
+    assert st["fragments"] == 0
+    img = out.cpu().numpy()
+    assert np.all(img[..., :3] == np.array([0.25, 0.5, 0.75], np.float32))
+    assert np.all(img[..., 3] == 0)
+
+
+def test_tiny_viewport(hx):
+    mesh = synth.hex_grid(3, jitter=0.1, seed=3)
+    view = synth.orbit_view(5, 120, 1, 1, radius=2.0)
+    render_both(hx, mesh, view, synth.lissajous_lens(5, 120), synth.Style())
+
+
+def test_full_size_sampled(hx):
+    """64^3 warped grid at 1920x1080 (one orbit frame): sampled pixels and a
+    crop against the oracle, in the launch configuration of the benchmark."""
+    w = synth.grid64_orbit_1080p()
+    mesh = w.mesh()
+    rng = np.random.default_rng(11)
+    n = 384
+    px = rng.integers(0, w.width, n).astype(np.int32)
+    py = rng.integers(0, w.height, n).astype(np.int32)
+    cy, cx = np.meshgrid(np.arange(500, 516), np.arange(900, 916), indexing="ij")
+    px = np.concatenate([px, cx.ravel().astype(np.int32)])
+    py = np.concatenate([py, cy.ravel().astype(np.int32)])
+    st, _ = render_both(hx, mesh, w.view(7), w.lens(7), w.style, px, py)
+    assert st["fragments"] > 10000
+
+
+def test_quality_matches_oracle(hx):
+    mesh = synth.hex_grid(12, jitter=0.3, warp_amp=0.4, seed=9)
+    r = hx.Renderer(0)
+    mid = r.upload_mesh(mesh.verts, mesh.cells, mesh.cell_scalar, mesh.edge_level)
+    for metric in (0, 1, 2):
+        out = torch.zeros(mesh.n_cells, dtype=torch.float32, device="cuda")
+        r.cell_quality(mid, metric, out)
+        torch.cuda.synchronize()
+        ref = oracle.cell_quality(mesh.verts, mesh.cells, metric)
+        assert np.allclose(out.cpu().numpy(), ref, atol=2e-6, rtol=1e-5), metric
+    r.close()
+
+
+def test_importance_update_equals_upload(hx):
+    """Setting the importance on the device gives the same image as uploading it."""
+    mesh = synth.hex_grid(6, jitter=0.1, warp_amp=0.2, seed=4)
+    view = synth.orbit_view(12, 120, 128, 96)
+    r = hx.Renderer(0)
+    a = r.upload_mesh(mesh.verts, mesh.cells, mesh.cell_scalar, mesh.edge_level)
+    b = r.upload_mesh(mesh.verts, mesh.cells, np.zeros(mesh.n_cells, np.float32), mesh.edge_level)
+    r.set_view(view)
+    r.set_lens(synth.lissajous_lens(12, 120))
+    r.set_style(synth.Style())
+    r.set_cell_importance(b, torch.from_numpy(mesh.cell_scalar).cuda())
+    oa = torch.zeros((96, 128, 4), device="cuda")
+    ob = torch.zeros((96, 128, 4), device="cuda")
+    r.render(a, oa)
+    r.render(b, ob)
+    torch.cuda.synchronize()
+    assert torch.equal(oa, ob)
+    r.close()
+
+
+def test_order_invariance(hx):
+    """Permuted cells and reversed binning give bit-identical keys and images."""
+    mesh = synth.hex_grid(6, jitter=0.2, warp_amp=0.2, seed=8)
+    perm = np.random.default_rng(3).permutation(mesh.n_cells)
+    view = synth.orbit_view(50, 120, 96, 96)
+    outs, keys = [], []
+    for cells, sc, lv, rev in [(mesh.cells, mesh.cell_scalar, mesh.edge_level, 0),
+                               (mesh.cells[perm], mesh.cell_scalar[perm], mesh.edge_level[perm], 1)]:
+        r = hx.Renderer(0)
+        mid = r.upload_mesh(mesh.verts, cells, sc, lv)
+        r.set_option(hx.HEXFC_OPT_REVERSE_BIN_ORDER, rev)
+        r.set_view(view)
+        r.set_lens(synth.lissajous_lens(50, 120))
+        r.set_style(synth.Style())
+        o = torch.zeros((96, 96, 4), device="cuda")
+        r.render(mid, o)
+        torch.cuda.synchronize()
+        yy, xx = np.meshgrid(np.arange(96), np.arange(96), indexing="ij")
+        keys.append(r.debug_pixels(xx.ravel(), yy.ravel())["keys"])
+        outs.append(o.cpu().numpy())
+        r.close()
+    assert np.array_equal(keys[0], keys[1])
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_render_host_matches_device(hx):
+    w = synth.grid4_ortho_256()
+    mesh = w.mesh()
+    r = hx.Renderer(0)
+    mid = r.upload_mesh(mesh.verts, mesh.cells, mesh.cell_scalar, mesh.edge_level)
+    r.set_view(w.view(0))
+    r.set_lens(w.lens(0))
+    r.set_style(w.style)
+    d = torch.zeros((256, 256, 4), device="cuda")
+    r.render(mid, d)
+    h = np.zeros((256, 256, 4), np.float32)
+    r.render_host(mid, h)
+    assert np.array_equal(d.cpu().numpy(), h)
+    r.close()
+
+
+def test_error_codes(hx):
+    r = hx.Renderer(0)
+    mesh = synth.hex_grid(2)
+    bad = mesh.cells.copy()
+    bad[0, 0] = 10 ** 6
+    with pytest.raises(hx.HexfcError) as e:
+        r.upload_mesh(mesh.verts, bad)
+    assert e.value.status == hx.HEXFC_ERR_MESH
+    nanv = mesh.verts.copy()
+    nanv[3, 1] = np.nan
+    with pytest.raises(hx.HexfcError) as e:
+        r.upload_mesh(nanv, mesh.cells)
+    assert e.value.status == hx.HEXFC_ERR_MESH
+    mid = r.upload_mesh(mesh.verts, mesh.cells)
+    out = torch.zeros((8, 8, 4), device="cuda")
+    with pytest.raises(hx.HexfcError) as e:
+        r.render(mid, out)
+    assert e.value.status == hx.HEXFC_ERR_STATE
+    with pytest.raises(hx.HexfcError) as e:
+        r.set_view(synth.View(width=0))
+    assert e.value.status == hx.HEXFC_ERR_ARG
+    with pytest.raises(hx.HexfcError) as e:
+        r.set_lens(synth.Lens(radius=0.0))
+    assert e.value.status == hx.HEXFC_ERR_ARG
+    r.close()
+    # fragment budget smaller than the frame
+    r = hx.Renderer(0, frag_budget_bytes=24 * 100)
+    mid = r.upload_mesh(mesh.verts, mesh.cells)
+    r.set_view(synth.orbit_view(0, 120, 64, 64, radius=2.0))
+    out = torch.zeros((64, 64, 4), device="cuda")
+    st = r.render(mid, out, check=False)
+    assert st == hx.HEXFC_ERR_OOM
+    assert r.last_stats["fragments"] > 100
+    r.close()
+
+
+def test_list_overflow_status(hx):
+    """More than HEXFC_MAX_LIST fragments in one pixel is reported, not drawn."""
+    nz = 4200  # seen along its axis the column gives nz+1 fragments per pixel
+    xs = np.array([-0.2, 0.2], np.float32)
+    verts = np.array([(x, y, z) for z in np.linspace(-0.5, 0.5, nz + 1) for y in xs for x in xs], np.float32)
+    cells = np.array([[4 * k, 4 * k + 1, 4 * k + 3, 4 * k + 2, 4 * k + 4, 4 * k + 5, 4 * k + 7, 4 * k + 6]
+                      for k in range(nz)], np.int32)
+    r = hx.Renderer(0)
+    mid = r.upload_mesh(verts, cells, np.full(nz, 0.5, np.float32))
+    # two coincident copies of the column double the list length past 8192
+    verts2 = np.concatenate([verts, verts])
+    cells2 = np.concatenate([cells, cells + len(verts)])
+    mid2 = r.upload_mesh(verts2, cells2, np.full(2 * nz, 0.5, np.float32))
+    r.set_view(synth.View(eye=(0.0, 0.0, 3.0), fovy_deg=0.0, ortho_half_h=0.5, znear=0.5, zfar=5.0, width=8,
+                          height=8))
+    out = torch.zeros((8, 8, 4), device="cuda")
+    assert r.render(mid, out, check=False) == hx.HEXFC_OK
+    assert r.last_stats["max_list"] == nz + 1
+    assert r.render(mid2, out, check=False) == hx.HEXFC_ERR_OVERFLOW
+    r.close()
