@@ -120,6 +120,7 @@ class ClockSampler:
 def workload_by_name(name):
     from paper_2009_06574_gb300 import synth
     return {"grid64_orbit_1080p": synth.grid64_orbit_1080p, "grid4_ortho_256": synth.grid4_ortho_256,
+            "grid64_orbit_540p": synth.grid64_orbit_540p,
             "grid128_orbit_4k": synth.grid128_orbit_4k}[name]()
 
 

@@ -283,12 +283,13 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
     if ((st = ensure(&fb.bins, &fb.bin_cap, (int64_t)n_bins)) != HEXFC_OK) return st;
     mark(ctx, 4, s);
     CK(launch_bin_fill(*m, fb, tiles_x, W, H, ctx->reverse_bins, s));
+    CK(launch_bin_sort(fb, tiles_x, tiles_y, s));
     mark(ctx, 5, s);
     CK(launch_count(fb, tiles_x, tiles_y, W, H, s));
     mark(ctx, 6, s);
     CK(scan_u32_to_u64(fb.cnt, fb.off, n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
     mark(ctx, 7, s);
-    launches += 5;
+    launches += 6;
     CK(cudaMemcpyAsync(fb.h_scal, fb.scal, 3 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const uint64_t total = fb.h_scal[0];

@@ -102,6 +102,7 @@ cudaError_t launch_face_setup(const DevMesh& m, const CamParams& cam, int lod, f
                               FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_t s);
 cudaError_t launch_bin_fill(const DevMesh& m, FrameBufs& fb, int tiles_x, int W, int H, int reverse,
                             cudaStream_t s);
+cudaError_t launch_bin_sort(FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_t s);
 cudaError_t launch_count(FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, cudaStream_t s);
 cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x,
                         int tiles_y, int W, int H, cudaStream_t s);

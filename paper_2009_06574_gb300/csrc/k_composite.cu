@@ -3,68 +3,25 @@
 // alpha-blended in visibility order; Section "GPU Implementation": per-pixel
 // fragment lists resolved by a sorting pass).
 //
-// The paper sorts with a per-pixel priority queue; here a list of n <= 256
-// fragments is sorted by one warp with a bitonic network held in registers
-// (32*M slots, M = 1, 2, 4 or 8 per lane), carrying the fragment's index in
-// its list; longer lists (up to HEXFC_MAX_LIST) go to a block-wide bitonic
-// sort in shared memory. Keys are unique within a pixel (depth, face,
-// triangle), so the order is unique. Compositing is an ordered reduction of
-// (colour, transmittance) pairs, (C1,T1)(C2,T2) = (C1 + T1 C2, T1 T2), which
-// equals the sequential front-to-back blend.
+// The paper sorts with a per-pixel priority queue. Here the fill pass visits
+// each tile's triangles in depth order, so nearly every list arrives sorted:
+// one warp stages a list (<= 256 fragments) in shared memory with cp.async
+// while it resolves the previous one, checks the order with one comparison
+// per element and a vote, and only an out-of-order list is sorted, by a
+// warp-wide bitonic network over (key, index) in shared memory. Lists longer
+// than 256 (up to HEXFC_MAX_LIST) are sorted by a whole block. Keys are
+// unique within a pixel (depth, face, triangle), so the order is unique.
+// Compositing is an ordered reduction of (colour, transmittance) pairs,
+// (C1,T1)(C2,T2) = (C1 + T1 C2, T1 T2), equal to the sequential
+// front-to-back blend.
 #include "hexfc_internal.cuh"
 
 namespace hexfc {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m)
-{
-    uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
-    lo = __shfl_xor_sync(kFull, lo, m);
-    hi = __shfl_xor_sync(kFull, hi, m);
-    return ((uint64_t)hi << 32) | lo;
-}
-
-// Bitonic sort of 32*M (key, idx) pairs across a warp, blocked layout: after
-// the call lane L holds ranks L*M .. L*M+M-1 in k[0..M-1].
-template <int M>
-__device__ __forceinline__ void warp_bitonic(uint64_t (&k)[M], uint32_t (&v)[M], int lane)
-{
-#pragma unroll
-    for (int size = 2; size <= 32 * M; size <<= 1) {
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            if (stride >= M) {
-                const int ls = stride / M;
-#pragma unroll
-                for (int j = 0; j < M; ++j) {
-                    int i = lane * M + j;
-                    uint64_t ok = shfl_xor_u64(k[j], ls);
-                    uint32_t ov = __shfl_xor_sync(kFull, v[j], ls);
-                    bool up = (i & size) == 0;
-                    bool lower = (i & stride) == 0;
-                    bool take = (lower == up) ? (ok < k[j]) : (ok > k[j]);
-                    if (take) { k[j] = ok; v[j] = ov; }
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < M; ++j) {
-                    if ((j & stride) == 0) {
-                        const int jj = j | stride;
-                        int i = lane * M + j;
-                        bool up = (i & size) == 0;
-                        bool sw = up ? (k[j] > k[jj]) : (k[j] < k[jj]);
-                        if (sw) {
-                            uint64_t tk = k[j]; k[j] = k[jj]; k[jj] = tk;
-                            uint32_t tv = v[j]; v[j] = v[jj]; v[jj] = tv;
-                        }
-                    }
-                }
-            }
-        }
-    }
-}
+constexpr int kWarpList = kWarpSortMax;   // per-warp staging capacity (fragments)
+constexpr int kWarps = kTilePix / 32;     // warps per composite block
 
 struct CT { float r, g, b, t; };  // premultiplied colour and transmittance
 
@@ -87,43 +44,89 @@ __device__ __forceinline__ CT warp_ordered_reduce(CT c, int lane)
     return c;
 }
 
-// Load, sort and (optionally) composite one pixel list with one warp.
-template <int M>
-__device__ __forceinline__ CT warp_pixel(const uint64_t* __restrict__ key, const float4* __restrict__ rgba,
-                                         uint64_t base, uint32_t n, int lane, uint64_t* out_key, float4* out_rgba)
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
 {
-    uint64_t k[M];
-    uint32_t v[M];
-#pragma unroll
-    for (int j = 0; j < M; ++j) {  // striped, coalesced load; the network does not care where keys start
-        uint32_t i = j * 32 + lane;
-        k[j] = i < n ? key[base + i] : kPadKey;
-        v[j] = i;
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Per-warp staging buffer of one list.
+struct WarpBuf {
+    uint64_t key[kWarpList];
+    float4 rgba[kWarpList];
+    uint16_t idx[kWarpList];
+};
+
+__device__ __forceinline__ void stage_list(WarpBuf& b, const uint64_t* __restrict__ key,
+                                           const float4* __restrict__ rgba, uint64_t base, uint32_t n, int lane)
+{
+    for (uint32_t i = lane; i < n; i += 32) {
+        cp_async8(&b.key[i], key + base + i);
+        cp_async16(&b.rgba[i], rgba + base + i);
     }
-    warp_bitonic<M>(k, v, lane);
+}
+
+// Resolve one staged list (n <= kWarpList) with one warp: sort if needed and
+// composite front to back. If out_key is given, the sorted list is written.
+__device__ CT warp_resolve(WarpBuf& b, uint32_t n, int lane, uint64_t* out_key, float4* out_rgba)
+{
+    if (n == 0) return CT{0.f, 0.f, 0.f, 1.f};
+    const uint32_t M = (n + 31) / 32;
+    const uint32_t i0 = lane * M;
+    bool inv = false;
+    for (uint32_t j = 0; j < M; ++j) {
+        uint32_t i = i0 + j;
+        if (i + 1 < n && b.key[i + 1] < b.key[i]) inv = true;
+    }
+    const bool sorted = !__any_sync(kFull, inv);
+    if (!sorted) {
+        // bitonic network over (key, idx), padded to a power of two >= 32
+        uint32_t np2 = 32;
+        while (np2 < n) np2 <<= 1;
+        for (uint32_t i = lane; i < np2; i += 32) {
+            if (i >= n) b.key[i] = kPadKey;
+            b.idx[i] = (uint16_t)i;
+        }
+        __syncwarp();
+        for (uint32_t size = 2; size <= np2; size <<= 1)
+            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+                for (uint32_t t = lane; t < np2 / 2; t += 32) {
+                    uint32_t i = 2 * stride * (t / stride) + (t % stride);
+                    uint32_t p = i + stride;
+                    bool up = (i & size) == 0;
+                    uint64_t a = b.key[i], c = b.key[p];
+                    if (up ? (a > c) : (a < c)) {
+                        b.key[i] = c;
+                        b.key[p] = a;
+                        uint16_t ti = b.idx[i];
+                        b.idx[i] = b.idx[p];
+                        b.idx[p] = ti;
+                    }
+                }
+                __syncwarp();
+            }
+    }
     CT c{0.f, 0.f, 0.f, 1.f};
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-        uint32_t rank = lane * M + j;
-        if (rank < n) {
-            float4 f = rgba[base + v[j]];
+    for (uint32_t j = 0; j < M; ++j) {
+        uint32_t r = i0 + j;
+        if (r < n) {
+            float4 f = b.rgba[sorted ? r : b.idx[r]];
             c = ct_over(c, CT{f.x, f.y, f.z, 1.f - f.w});
             if (out_key) {
-                out_key[rank] = k[j];
-                out_rgba[rank] = f;
+                out_key[r] = b.key[r];
+                out_rgba[r] = f;
             }
         }
     }
     return warp_ordered_reduce(c, lane);
-}
-
-__device__ __forceinline__ CT warp_pixel_any(const uint64_t* __restrict__ key, const float4* __restrict__ rgba,
-                                             uint64_t base, uint32_t n, int lane, uint64_t* ok, float4* orgba)
-{
-    if (n <= 32) return warp_pixel<1>(key, rgba, base, n, lane, ok, orgba);
-    if (n <= 64) return warp_pixel<2>(key, rgba, base, n, lane, ok, orgba);
-    if (n <= 128) return warp_pixel<4>(key, rgba, base, n, lane, ok, orgba);
-    return warp_pixel<8>(key, rgba, base, n, lane, ok, orgba);
 }
 
 __device__ __forceinline__ void tile_pixel(int64_t q, int tiles_x, int& x, int& y)
@@ -134,27 +137,55 @@ __device__ __forceinline__ void tile_pixel(int64_t q, int tiles_x, int& x, int& 
     y = (int)(tile / tiles_x) * kTile + local / kTile;
 }
 
-__global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ off,
-                                                   const uint64_t* __restrict__ key, const float4* __restrict__ rgba,
-                                                   int64_t n_pix, int tiles_x, int W, int H, float bg0, float bg1,
-                                                   float bg2, float4* __restrict__ out, uint32_t* __restrict__ long_q,
-                                                   unsigned long long* __restrict__ long_cursor)
+// One block per tile; warp w resolves pixels 32w .. 32w+31 of the tile, staging
+// the next list while it resolves the current one.
+__global__ void __launch_bounds__(kTilePix) k_composite(const uint32_t* __restrict__ cnt,
+                                                        const uint64_t* __restrict__ off,
+                                                        const uint64_t* __restrict__ key,
+                                                        const float4* __restrict__ rgba, int tiles_x, int W, int H,
+                                                        float bg0, float bg1, float bg2, float4* __restrict__ out,
+                                                        uint32_t* __restrict__ long_q,
+                                                        unsigned long long* __restrict__ long_cursor)
 {
-    int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (q >= n_pix) return;
-    int x, y;
-    tile_pixel(q, tiles_x, x, y);
-    if (x >= W || y >= H) return;
-    uint32_t n = cnt[q];
-    if (n > (uint32_t)kWarpSortMax) {
-        if (lane == 0) long_q[atomicAdd(long_cursor, 1ull)] = (uint32_t)q;
-        return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    WarpBuf* bufs = reinterpret_cast<WarpBuf*>(smem);
+    __shared__ uint32_t s_cnt[kTilePix];
+    __shared__ uint64_t s_off[kTilePix];
+    const int tile = blockIdx.x;
+    const int64_t q0 = (int64_t)tile * kTilePix;
+    s_cnt[threadIdx.x] = cnt[q0 + threadIdx.x];
+    s_off[threadIdx.x] = off[q0 + threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpBuf* wb = bufs + 2 * warp;
+    const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
+    auto len_of = [&](int p) -> uint32_t {
+        uint32_t n = s_cnt[p];
+        return n <= (uint32_t)kWarpList ? n : 0u;
+    };
+    int p = warp * 32;
+    stage_list(wb[0], key, rgba, s_off[p], len_of(p), lane);
+    cp_async_commit();
+    for (int i = 0; i < 32; ++i, ++p) {
+        if (i + 1 < 32) {
+            stage_list(wb[(i + 1) & 1], key, rgba, s_off[p + 1], len_of(p + 1), lane);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp();
+        const int x = px0 + (p & (kTile - 1)), y = py0 + p / kTile;
+        const uint32_t n = s_cnt[p];
+        if (n > (uint32_t)kWarpList) {
+            if (lane == 0) long_q[atomicAdd(long_cursor, 1ull)] = (uint32_t)(q0 + p);
+        } else if (x < W && y < H) {
+            CT c = warp_resolve(wb[i & 1], n, lane, nullptr, nullptr);
+            if (lane == 0)
+                out[(int64_t)y * W + x] = make_float4(c.r + c.t * bg0, c.g + c.t * bg1, c.b + c.t * bg2, 1.f - c.t);
+        }
+        __syncwarp();
     }
-    CT c{0.f, 0.f, 0.f, 1.f};
-    if (n > 0) c = warp_pixel_any(key, rgba, off[q], n, lane, nullptr, nullptr);
-    if (lane == 0)
-        out[(int64_t)y * W + x] = make_float4(c.r + c.t * bg0, c.g + c.t * bg1, c.b + c.t * bg2, 1.f - c.t);
 }
 
 // Block-wide bitonic sort of a long list in shared memory (n <= HEXFC_MAX_LIST).
@@ -225,21 +256,29 @@ __global__ void __launch_bounds__(1024) k_composite_long(const uint32_t* __restr
         out[(int64_t)y * W + x] = make_float4(c.r + c.t * bg0, c.g + c.t * bg1, c.b + c.t * bg2, 1.f - c.t);
 }
 
-// Debug: sorted lists of requested pixels, written at d_dst_off[i] (warp per pixel).
-__global__ void k_debug_short(const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ off,
-                              const uint64_t* __restrict__ key, const float4* __restrict__ rgba,
-                              const int32_t* __restrict__ px, const int32_t* __restrict__ py, int64_t n_req,
-                              const uint64_t* __restrict__ dst_off, int tiles_x, int W, int H,
-                              uint64_t* __restrict__ out_key, float4* __restrict__ out_rgba)
+// Debug: sorted lists of requested pixels written at dst_off[i], by the same
+// resolve routines as the composite (one warp per pixel for n <= 256).
+__global__ void __launch_bounds__(256) k_debug_short(const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ off,
+                                                     const uint64_t* __restrict__ key,
+                                                     const float4* __restrict__ rgba, const int32_t* __restrict__ px,
+                                                     const int32_t* __restrict__ py, int64_t n_req,
+                                                     const uint64_t* __restrict__ dst_off, int tiles_x,
+                                                     uint64_t* __restrict__ out_key, float4* __restrict__ out_rgba)
 {
+    extern __shared__ __align__(16) unsigned char smem[];
+    WarpBuf& b = reinterpret_cast<WarpBuf*>(smem)[threadIdx.x >> 5];
     int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (i >= n_req) return;
     int x = px[i], y = py[i];
     int64_t q = ((int64_t)(y / kTile) * tiles_x + x / kTile) * kTilePix + (y % kTile) * kTile + (x % kTile);
     uint32_t n = cnt[q];
-    if (n == 0 || n > (uint32_t)kWarpSortMax) return;
-    (void)warp_pixel_any(key, rgba, off[q], n, lane, out_key + dst_off[i], out_rgba + dst_off[i]);
+    if (n == 0 || n > (uint32_t)kWarpList) return;
+    stage_list(b, key, rgba, off[q], n, lane);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+    (void)warp_resolve(b, n, lane, out_key + dst_off[i], out_rgba + dst_off[i]);
 }
 
 __global__ void __launch_bounds__(1024) k_debug_long(const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ off,
@@ -255,7 +294,7 @@ __global__ void __launch_bounds__(1024) k_debug_long(const uint32_t* __restrict_
     int x = px[i], y = py[i];
     int64_t q = ((int64_t)(y / kTile) * tiles_x + x / kTile) * kTilePix + (y % kTile) * kTile + (x % kTile);
     uint32_t n = cnt[q];
-    if (n <= (uint32_t)kWarpSortMax) return;
+    if (n <= (uint32_t)kWarpList) return;
     (void)block_composite(key, rgba, off[q], n, s_k, s_v, out_key + dst_off[i], out_rgba + dst_off[i]);
 }
 
@@ -271,17 +310,18 @@ __global__ void k_debug_counts(const uint32_t* __restrict__ cnt, const int32_t* 
 }
 
 constexpr size_t kLongSmem = (size_t)HEXFC_MAX_LIST * (sizeof(uint64_t) + sizeof(uint32_t));
+constexpr size_t kCompositeSmem = 2 * kWarps * sizeof(WarpBuf);
 
 }  // namespace
 
 cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W, int H, float* out,
                              uint32_t n_long, cudaStream_t s)
 {
-    int64_t n_pix = (int64_t)tiles_x * tiles_y * kTilePix;
-    unsigned blocks = (unsigned)((n_pix * 32 + 255) / 256);
     float4* o4 = reinterpret_cast<float4*>(out);
-    k_composite<<<blocks, 256, 0, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, n_pix, tiles_x, W, H, sp.bg[0], sp.bg[1],
-                                       sp.bg[2], o4, fb.long_q, reinterpret_cast<unsigned long long*>(fb.scal + 3));
+    cudaFuncSetAttribute(k_composite, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCompositeSmem);
+    k_composite<<<(unsigned)(tiles_x * tiles_y), kTilePix, kCompositeSmem, s>>>(
+        fb.cnt, fb.off, fb.key, fb.rgba, tiles_x, W, H, sp.bg[0], sp.bg[1], sp.bg[2], o4, fb.long_q,
+        reinterpret_cast<unsigned long long*>(fb.scal + 3));
     if (n_long > 0) {
         cudaFuncSetAttribute(k_composite_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSmem);
         k_composite_long<<<n_long, 1024, kLongSmem, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, fb.long_q, tiles_x, W,
@@ -294,13 +334,17 @@ cudaError_t launch_debug_gather(FrameBufs& fb, const int32_t* d_px, const int32_
                                 const uint64_t* d_dst_off, int tiles_x, int W, int H, uint64_t* d_keys,
                                 float4* d_rgba, uint32_t* d_counts, cudaStream_t s)
 {
+    (void)W;
+    (void)H;
     if (n <= 0) return cudaSuccess;
     if (d_counts) {
         k_debug_counts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(fb.cnt, d_px, d_py, n, tiles_x, d_counts);
         return cudaGetLastError();
     }
-    k_debug_short<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, d_px, d_py, n,
-                                                                 d_dst_off, tiles_x, W, H, d_keys, d_rgba);
+    const size_t dsm = 8 * sizeof(WarpBuf);
+    cudaFuncSetAttribute(k_debug_short, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+    k_debug_short<<<(unsigned)((n * 32 + 255) / 256), 256, dsm, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, d_px, d_py, n,
+                                                                    d_dst_off, tiles_x, d_keys, d_rgba);
     cudaFuncSetAttribute(k_debug_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSmem);
     k_debug_long<<<(unsigned)n, 1024, kLongSmem, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, d_px, d_py, d_dst_off,
                                                       tiles_x, d_keys, d_rgba);

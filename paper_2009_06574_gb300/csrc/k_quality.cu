@@ -80,7 +80,7 @@ __device__ __forceinline__ int32_t f2key(float f)
 }
 __device__ __forceinline__ float key2f(int32_t k) { return __int_as_float(k >= 0 ? k : (k ^ 0x7FFFFFFF)); }
 
-__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v)
+__global__ void k_init_keys(int32_t* p, int64_t n, int32_t v)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
@@ -143,8 +143,8 @@ cudaError_t launch_cell_quality(const DevMesh& m, int metric, float* out, cudaSt
 
 cudaError_t launch_importance(const DevMesh& m, cudaStream_t s)
 {
-    k_fill_i32<<<grid_for(m.n_verts, 256), 256, 0, s>>>(m.vkey, m.n_verts, INT32_MIN);
-    k_fill_i32<<<grid_for(m.n_edges, 256), 256, 0, s>>>(m.ekey, m.n_edges, INT32_MIN);
+    k_init_keys<<<grid_for(m.n_verts, 256), 256, 0, s>>>(m.vkey, m.n_verts, INT32_MIN);
+    k_init_keys<<<grid_for(m.n_edges, 256), 256, 0, s>>>(m.ekey, m.n_edges, INT32_MIN);
     k_importance_scatter<<<grid_for(m.n_cells, 256), 256, 0, s>>>(m.cells, m.cell_edges, m.cell_imp,
                                                                    m.n_cells, m.vkey, m.ekey);
     k_key_to_float<<<grid_for(m.n_verts, 256), 256, 0, s>>>(m.vkey, m.vimp, m.n_verts);

@@ -15,7 +15,7 @@
 // Section "GPU Implementation"), and the fragment shader computes focus from
 // the lens, the edge distance to the four face edges ignoring invisible ones,
 // and Eqs. 1-4 (Section "Focus+Context").
-#include "raster_common.cuh"
+#include "shade.cuh"
 
 namespace hexfc {
 namespace {
@@ -146,17 +146,64 @@ __global__ void k_bin_fill(const int4* __restrict__ fx, const int4* __restrict__
     }
 }
 
+// ------------------------------------------------------------------ bin order
+
+constexpr int kBinSortMax = 4096;   // longer tile lists keep their arrival order
+
+// Orders each tile's list by triangle depth (sum of the three window depths,
+// then 2*face+tri). Any order gives the same fragments; depth order makes
+// the fill write almost every per-pixel list already sorted front to back.
+__global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ tile_off, uint32_t* __restrict__ bins,
+                                                  const uint4* __restrict__ fz)
+{
+    __shared__ uint64_t s_k[kBinSortMax];
+    const int tile = blockIdx.x;
+    const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];
+    const uint32_t n = (uint32_t)(end - beg);
+    if (n < 2 || n > (uint32_t)kBinSortMax) return;
+    uint32_t np2 = 2;
+    while (np2 < n) np2 <<= 1;
+    for (uint32_t i = threadIdx.x; i < np2; i += blockDim.x) {
+        uint64_t k = ~0ull;
+        if (i < n) {
+            uint32_t f2t = bins[beg + i];
+            uint4 z = fz[f2t >> 1];
+            uint64_t zs = (uint64_t)z.x + ((f2t & 1) ? (uint64_t)z.z + z.w : (uint64_t)z.y + z.z);
+            k = (zs << 32) | f2t;
+        }
+        s_k[i] = k;
+    }
+    __syncthreads();
+    for (uint32_t size = 2; size <= np2; size <<= 1)
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (uint32_t i = threadIdx.x; i < np2; i += blockDim.x) {
+                uint32_t p = i ^ stride;
+                if (p > i) {
+                    uint64_t a = s_k[i], b = s_k[p];
+                    bool up = (i & size) == 0;
+                    if (up ? (a > b) : (a < b)) { s_k[i] = b; s_k[p] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) bins[beg + i] = (uint32_t)s_k[i];
+}
+
 // ------------------------------------------------------------------ raster per tile
 
-// Triangle data staged in shared memory for one chunk of a tile's list.
-struct TriS {
-    int32_t X[3], Y[3];
-    int16_t bx0, by0, bx1, by1;
-    uint32_t meta;   // bits 0-2 top-left of the edge opposite vertex k
+constexpr int kChunk = 32;   // triangles staged per step (one coverage bit each)
+
+// Coverage data of one staged triangle.
+struct TriC {
+    int32_t X[3], Y[3];   // wound to positive area (16.8)
+    uint32_t meta;        // bit k: top-left rule owns the edge opposite vertex k
+    int16_t lx0, ly0;     // box of covered pixel centres, tile-local
+    int16_t bw, bh;       // box size, 0 when the triangle misses the tile
+    float inv_bw;
 };
 
-__device__ __forceinline__ void stage_tri(const int4* __restrict__ fx, const int4* __restrict__ fy,
-                                          uint32_t f2t, int W, int H, TriS& s, TriGeom& t)
+__device__ __forceinline__ void stage_cov(const int4* __restrict__ fx, const int4* __restrict__ fy, uint32_t f2t,
+                                          int W, int H, int px0, int py0, TriC& c, TriGeom& t)
 {
     uint32_t f = f2t >> 1, tri = f2t & 1;
     int4 a = fx[f], b = fy[f];
@@ -165,28 +212,59 @@ __device__ __forceinline__ void stage_tri(const int4* __restrict__ fx, const int
     uint32_t meta = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        s.X[k] = t.X[k];
-        s.Y[k] = t.Y[k];
+        c.X[k] = t.X[k];
+        c.Y[k] = t.Y[k];
         int a0 = (k + 1) % 3, b0 = (k + 2) % 3;
         meta |= (top_left(t.X[a0], t.Y[a0], t.X[b0], t.Y[b0]) ? 1u : 0u) << k;
     }
-    s.bx0 = (int16_t)t.bx0; s.by0 = (int16_t)t.by0; s.bx1 = (int16_t)t.bx1; s.by1 = (int16_t)t.by1;
-    s.meta = meta;
+    c.meta = meta;
+    int x0 = max(t.bx0, px0), x1 = min(t.bx1, px0 + kTile - 1);
+    int y0 = max(t.by0, py0), y1 = min(t.by1, py0 + kTile - 1);
+    if (!t.valid || x0 > x1 || y0 > y1) {
+        c.lx0 = c.ly0 = 0;
+        c.bw = c.bh = 0;
+        c.inv_bw = 0.f;
+    } else {
+        c.lx0 = (int16_t)(x0 - px0);
+        c.ly0 = (int16_t)(y0 - py0);
+        c.bw = (int16_t)(x1 - x0 + 1);
+        c.bh = (int16_t)(y1 - y0 + 1);
+        c.inv_bw = 1.f / (float)c.bw;
+    }
 }
 
-// Exact coverage of sample (sx, sy) (16.8) by a staged triangle; barycentric weights out.
-__device__ __forceinline__ bool covers(const TriS& s, int px, int py, int32_t sx, int32_t sy, int64_t l[3])
+// Exact coverage of sample (sx, sy); l[k] = weight of vertex k (sums to the area).
+__device__ __forceinline__ bool cover_sample(const TriC& c, int32_t sx, int32_t sy, int64_t l[3])
 {
-    if (px < s.bx0 || px > s.bx1 || py < s.by0 || py > s.by1) return false;
     bool in = true;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         int a = (k + 1) % 3, b = (k + 2) % 3;
-        int64_t e = edge_fn(s.X[a], s.Y[a], s.X[b], s.Y[b], sx, sy);
+        int64_t e = edge_fn(c.X[a], c.Y[a], c.X[b], c.Y[b], sx, sy);
         l[k] = e;
-        in = in && (e > 0 || (e == 0 && ((s.meta >> k) & 1u)));
+        in = in && (e > 0 || (e == 0 && ((c.meta >> k) & 1u)));
     }
     return in;
+}
+
+// Coverage of one chunk: a warp walks each triangle's box (clipped to the
+// tile), one sample per lane, and sets bit j of the covered pixels' masks.
+__device__ __forceinline__ void raster_chunk(const TriC* s_c, int m, int px0, int py0, uint32_t* s_mask)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = warp; j < m; j += kTilePix / 32) {
+        const TriC& c = s_c[j];
+        const int area = (int)c.bw * (int)c.bh;
+        for (int idx = lane; idx < area; idx += 32) {
+            // exact for idx < 256, bw <= 16: the quotient is never within 1/32 of an integer
+            int ry = (int)(((float)idx + 0.5f) * c.inv_bw);
+            int rx = idx - ry * c.bw;
+            int lx = c.lx0 + rx, ly = c.ly0 + ry;
+            int64_t l[3];
+            if (cover_sample(c, 256 * (px0 + lx) + 128, 256 * (py0 + ly) + 128, l))
+                atomicOr(s_mask + ly * kTile + lx, 1u << j);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__ tile_off,
@@ -194,141 +272,88 @@ __global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__
                                                     const int4* __restrict__ fx, const int4* __restrict__ fy,
                                                     int tiles_x, int W, int H, uint32_t* __restrict__ cnt)
 {
-    __shared__ TriS s_tri[kTilePix];
-    int tile = blockIdx.x;
-    int tx = tile % tiles_x, ty = tile / tiles_x;
-    int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    int py = ty * kTile + (threadIdx.x / kTile);
-    int32_t sx = 256 * px + 128, sy = 256 * py + 128;
-    uint64_t beg = tile_off[tile], end = tile_off[tile + 1];
+    __shared__ TriC s_c[kChunk];
+    __shared__ uint32_t s_mask[kTilePix];
+    const int tile = blockIdx.x;
+    const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
+    const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];
+    s_mask[threadIdx.x] = 0;
     uint32_t n = 0;
-    for (uint64_t base = beg; base < end; base += kTilePix) {
-        uint64_t i = base + threadIdx.x;
-        if (i < end) {
+    for (uint64_t base = beg; base < end; base += kChunk) {
+        if (threadIdx.x < kChunk && base + threadIdx.x < end) {
             TriGeom t;
-            stage_tri(fx, fy, bins[i], W, H, s_tri[threadIdx.x], t);
+            stage_cov(fx, fy, bins[base + threadIdx.x], W, H, px0, py0, s_c[threadIdx.x], t);
         }
         __syncthreads();
-        int m = (int)min((uint64_t)kTilePix, end - base);
-        for (int j = 0; j < m; ++j) {
-            int64_t l[3];
-            n += covers(s_tri[j], px, py, sx, sy, l) ? 1u : 0u;
-        }
+        raster_chunk(s_c, (int)min((uint64_t)kChunk, end - base), px0, py0, s_mask);
         __syncthreads();
+        n += __popc(s_mask[threadIdx.x]);
+        s_mask[threadIdx.x] = 0;
     }
     cnt[(int64_t)tile * kTilePix + threadIdx.x] = n;
 }
 
 // ------------------------------------------------------------------ fill + shade
 
-struct TriShade {
-    int32_t FX[4], FY[4];   // face corners (16.8)
-    uint32_t z[3];          // window depth of the triangle's vertices (wound order)
-    float ed[3], imp[3], P[3][3];
-    int64_t area;
-    uint32_t f2t;
-    uint32_t masks;         // bits 0-3 focus-visible, 4-7 context-visible face edges
-};
-
-__device__ __forceinline__ float smoothstepf(float e0, float e1, float x)
+// Exclusive scan of one value per thread of a kTilePix-thread block.
+__device__ __forceinline__ uint32_t block_scan_tile(uint32_t v, uint32_t* s_w, uint32_t& total)
 {
-    float t = fminf(fmaxf((x - e0) / (e1 - e0), 0.f), 1.f);
-    return t * t * (3.f - 2.f * t);
-}
-
-// Distance in pixels from sample (sx, sy) to segment a-b; exact integer
-// deltas (16.8), one float rounding at the end of each branch.
-__device__ __forceinline__ float seg_dist(int32_t sx, int32_t sy, int32_t ax, int32_t ay, int32_t bx, int32_t by)
-{
-    int64_t px = sx - ax, py = sy - ay;
-    int64_t ex = (int64_t)bx - ax, ey = (int64_t)by - ay;
-    int64_t len2 = ex * ex + ey * ey;
-    int64_t dot = px * ex + py * ey;
-    float d;
-    if (len2 == 0 || dot <= 0) {
-        d = sqrtf((float)(px * px + py * py));
-    } else if (dot >= len2) {
-        int64_t qx = sx - bx, qy = sy - by;
-        d = sqrtf((float)(qx * qx + qy * qy));
-    } else {
-        float cr = (float)(px * ey - py * ex);
-        d = fabsf(cr) / sqrtf((float)len2);
-    }
-    return d * (1.f / 256.f);
-}
-
-// Eqs. 1-4 for one fragment (Section "Focus+Context"); returns premultiplied RGBA.
-__device__ float4 shade_fragment(const TriShade& t, const int64_t l[3], int px, int py, int32_t sx, int32_t sy,
-                                 const ShadeParams& sp)
-{
-    float inv_a = 1.f / (float)t.area;
-    float lam[3] = {(float)l[0] * inv_a, (float)l[1] * inv_a, (float)l[2] * inv_a};
-    float b[3], z_eye;
-    if (sp.ortho) {
-        b[0] = lam[0]; b[1] = lam[1]; b[2] = lam[2];
-        z_eye = lam[0] * t.ed[0] + lam[1] * t.ed[1] + lam[2] * t.ed[2];
-    } else {  // perspective-correct interpolation
-        float q0 = lam[0] / t.ed[0], q1 = lam[1] / t.ed[1], q2 = lam[2] / t.ed[2];
-        float Q = q0 + q1 + q2;
-        float iQ = 1.f / Q;
-        b[0] = q0 * iQ; b[1] = q1 * iQ; b[2] = q2 * iQ;
-        z_eye = iQ;
-    }
-    float t_imp = b[0] * t.imp[0] + b[1] * t.imp[1] + b[2] * t.imp[2];
-    // lens distance, normalised to 1 at the lens border
-    float dist;
-    if (sp.lens_mode == HEXFC_LENS_SCREEN) {
-        float dx = ((float)px + 0.5f) - sp.lens_c[0], dy = ((float)py + 0.5f) - sp.lens_c[1];
-        dist = sqrtf(dx * dx + dy * dy) * sp.lens_inv_r;
-    } else {
-        float Px = b[0] * t.P[0][0] + b[1] * t.P[1][0] + b[2] * t.P[2][0];
-        float Py = b[0] * t.P[0][1] + b[1] * t.P[1][1] + b[2] * t.P[2][1];
-        float Pz = b[0] * t.P[0][2] + b[1] * t.P[1][2] + b[2] * t.P[2][2];
-        float dx = Px - sp.lens_c[0], dy = Py - sp.lens_c[1], dz = Pz - sp.lens_c[2];
-        dist = sqrtf(dx * dx + dy * dy + dz * dz) * sp.lens_inv_r;
-    }
-    float focus = 1.f - smoothstepf(0.7f, 1.f, dist);
-    // distances to the face edges: all, visible in focus, visible in context
-    float d_a = INFINITY, d_f = INFINITY, d_c = INFINITY;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        int k1 = (k + 1) & 3;
-        float d = seg_dist(sx, sy, t.FX[k], t.FY[k], t.FX[k1], t.FY[k1]);
-        d_a = fminf(d_a, d);
-        if ((t.masks >> k) & 1u) d_f = fminf(d_f, d);
-        if ((t.masks >> (4 + k)) & 1u) d_c = fminf(d_c, d);
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
-    float g = 1.f;
-    if (!sp.ortho) g = fminf(fmaxf(sp.zref / z_eye, sp.g_min), sp.g_max);
-    // Eq. 1 with the depth-dependent width, halo band of the focus edges
-    float w = (1.f + 0.3f * focus) * sp.w_base * g;
-    bool e_focus = d_f <= w, e_context = d_c <= w;
-    float h = sp.halo_scale * sp.w_base * focus * g;
-    float alpha_e = (float)e_context + focus * ((float)e_focus - (float)e_context);
-    bool halo = !e_focus && (d_f <= w + h) && focus > 0.f;
-    if (halo) alpha_e = focus;
-    // colour table and Eq. 2
-    float tt = fminf(fmaxf((t_imp - sp.tf_lo) * sp.tf_inv, 0.f), 1.f);
-    float ctf[3] = {tt, 0.f, 1.f - tt};
-    float dk = 1.f - sp.darken * focus;
-    bool accent = d_a <= (2.f / 3.f) * sp.w_base;
-    float s_e = accent ? sp.s : 1.f;
-    float cf[3], ce[3];
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    uint32_t pre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kTilePix / 32; ++w) {
+        uint32_t sw = s_w[w];
+        pre += w < warp ? sw : 0u;
+        tot += sw;
+    }
+    total = tot;
+    return pre + x - v;
+}
+
+__device__ __forceinline__ void stage_shade(const int4* __restrict__ fx, const int4* __restrict__ fy,
+                                            const uint4* __restrict__ fz, const float4* __restrict__ fed,
+                                            const uint32_t* __restrict__ fflags, const float4* __restrict__ fimp,
+                                            const float4* __restrict__ fpx, const float4* __restrict__ fpy,
+                                            const float4* __restrict__ fpz, uint32_t f2t, const TriGeom& t,
+                                            TriShade& S)
+{
+    uint32_t f = f2t >> 1;
+    int4 a = fx[f], b = fy[f];
+    S.FX[0] = a.x; S.FX[1] = a.y; S.FX[2] = a.z; S.FX[3] = a.w;
+    S.FY[0] = b.x; S.FY[1] = b.y; S.FY[2] = b.z; S.FY[3] = b.w;
+    uint4 z4 = fz[f];
+    float4 e4 = fed[f], i4 = fimp[f], x4 = fpx[f], y4 = fpy[f], w4 = fpz[f];
+    uint32_t zz[4] = {z4.x, z4.y, z4.z, z4.w};
+    float ee[4] = {e4.x, e4.y, e4.z, e4.w}, ii[4] = {i4.x, i4.y, i4.z, i4.w};
+    float xx[4] = {x4.x, x4.y, x4.z, x4.w}, yy[4] = {y4.x, y4.y, y4.z, y4.w}, ww[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        ce[k] = halo ? 1.f : ctf[k] * dk;
-        cf[k] = s_e > 1.f ? ctf[k] + sp.accent_beta * (1.f - ctf[k]) : ctf[k];
+        int c = t.vi[k];
+        // select corner c without dynamic register indexing
+        S.z[k] = c == 0 ? zz[0] : c == 1 ? zz[1] : c == 2 ? zz[2] : zz[3];
+        S.ed[k] = c == 0 ? ee[0] : c == 1 ? ee[1] : c == 2 ? ee[2] : ee[3];
+        S.imp[k] = c == 0 ? ii[0] : c == 1 ? ii[1] : c == 2 ? ii[2] : ii[3];
+        S.P[k][0] = c == 0 ? xx[0] : c == 1 ? xx[1] : c == 2 ? xx[2] : xx[3];
+        S.P[k][1] = c == 0 ? yy[0] : c == 1 ? yy[1] : c == 2 ? yy[2] : yy[3];
+        S.P[k][2] = c == 0 ? ww[0] : c == 1 ? ww[1] : c == 2 ? ww[2] : ww[3];
     }
-    // Eq. 3 and Eq. 4
-    float ahat = sp.alpha_min + sp.alpha_span * tt;
-    float dc = fminf(dist, 1.f);
-    float dc2 = dc * dc;
-    float af = fminf(s_e * (ahat * (dc2 * dc2)), 1.f);
-    float wf = (1.f - alpha_e) * af;
-    return make_float4(alpha_e * ce[0] + wf * cf[0], alpha_e * ce[1] + wf * cf[1], alpha_e * ce[2] + wf * cf[2],
-                       alpha_e + wf);
+    S.area = t.area;
+    S.f2t = f2t;
+    S.masks = fflags[f] & 0xFFu;
 }
 
+// Per tile: coverage of each chunk as per-pixel bit masks; the covered
+// samples are compacted into a queue (pixel-major, in list order) so that the
+// shading runs on every lane; each fragment is written at its pixel's offset
+// plus its rank in the pixel's list (the rank the count pass sized).
 __global__ void __launch_bounds__(kTilePix) k_fill(const uint64_t* __restrict__ tile_off,
                                                    const uint32_t* __restrict__ bins,
                                                    const int4* __restrict__ fx, const int4* __restrict__ fy,
@@ -340,65 +365,62 @@ __global__ void __launch_bounds__(kTilePix) k_fill(const uint64_t* __restrict__ 
                                                    const uint64_t* __restrict__ off, uint64_t* __restrict__ key,
                                                    float4* __restrict__ rgba, uint64_t* __restrict__ err)
 {
-    __shared__ TriS s_tri[kTilePix];
-    __shared__ TriShade s_sh[kTilePix];
-    int tile = blockIdx.x;
-    int tx = tile % tiles_x, ty = tile / tiles_x;
-    int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    int py = ty * kTile + (threadIdx.x / kTile);
-    int32_t sx = 256 * px + 128, sy = 256 * py + 128;
-    uint64_t beg = tile_off[tile], end = tile_off[tile + 1];
-    uint64_t o = off[(int64_t)tile * kTilePix + threadIdx.x];
-    const uint64_t o_end = off[(int64_t)tile * kTilePix + threadIdx.x + 1];
+    __shared__ TriC s_c[kChunk];
+    __shared__ TriShade s_sh[kChunk];
+    __shared__ uint32_t s_mask[kTilePix];
+    __shared__ uint32_t s_q[kChunk * kTilePix];
+    __shared__ uint64_t s_base[kTilePix];
+    __shared__ uint32_t s_len[kTilePix];
+    __shared__ uint32_t s_w[kTilePix / 32];
+    const int tile = blockIdx.x;
+    const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
+    const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];
+    {
+        const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;
+        uint64_t o0 = off[q];
+        s_base[threadIdx.x] = o0;
+        s_len[threadIdx.x] = (uint32_t)(off[q + 1] - o0);
+        s_mask[threadIdx.x] = 0;
+    }
+    uint32_t k_run = 0;
     bool bad = false;
-    for (uint64_t base = beg; base < end; base += kTilePix) {
-        uint64_t i = base + threadIdx.x;
-        if (i < end) {
-            uint32_t f2t = bins[i];
+    for (uint64_t base = beg; base < end; base += kChunk) {
+        if (threadIdx.x < kChunk && base + threadIdx.x < end) {
+            uint32_t f2t = bins[base + threadIdx.x];
             TriGeom t;
-            stage_tri(fx, fy, f2t, W, H, s_tri[threadIdx.x], t);
-            uint32_t f = f2t >> 1;
-            TriShade& S = s_sh[threadIdx.x];
-            int4 a = fx[f], b = fy[f];
-            S.FX[0] = a.x; S.FX[1] = a.y; S.FX[2] = a.z; S.FX[3] = a.w;
-            S.FY[0] = b.x; S.FY[1] = b.y; S.FY[2] = b.z; S.FY[3] = b.w;
-            uint4 z4 = fz[f];
-            float4 e4 = fed[f], i4 = fimp[f], x4 = fpx[f], y4 = fpy[f], w4 = fpz[f];
-            uint32_t zz[4] = {z4.x, z4.y, z4.z, z4.w};
-            float ee[4] = {e4.x, e4.y, e4.z, e4.w}, ii[4] = {i4.x, i4.y, i4.z, i4.w};
-            float xx[4] = {x4.x, x4.y, x4.z, x4.w}, yy[4] = {y4.x, y4.y, y4.z, y4.w}, ww[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                int c = t.vi[k];
-                // select corner c without dynamic register indexing
-                uint32_t zc = c == 0 ? zz[0] : c == 1 ? zz[1] : c == 2 ? zz[2] : zz[3];
-                float ec = c == 0 ? ee[0] : c == 1 ? ee[1] : c == 2 ? ee[2] : ee[3];
-                float ic = c == 0 ? ii[0] : c == 1 ? ii[1] : c == 2 ? ii[2] : ii[3];
-                float xc = c == 0 ? xx[0] : c == 1 ? xx[1] : c == 2 ? xx[2] : xx[3];
-                float yc = c == 0 ? yy[0] : c == 1 ? yy[1] : c == 2 ? yy[2] : yy[3];
-                float wc = c == 0 ? ww[0] : c == 1 ? ww[1] : c == 2 ? ww[2] : ww[3];
-                S.z[k] = zc; S.ed[k] = ec; S.imp[k] = ic;
-                S.P[k][0] = xc; S.P[k][1] = yc; S.P[k][2] = wc;
-            }
-            S.area = t.area;
-            S.f2t = f2t;
-            S.masks = fflags[f] & 0xFFu;
+            stage_cov(fx, fy, f2t, W, H, px0, py0, s_c[threadIdx.x], t);
+            stage_shade(fx, fy, fz, fed, fflags, fimp, fpx, fpy, fpz, f2t, t, s_sh[threadIdx.x]);
         }
         __syncthreads();
-        int m = (int)min((uint64_t)kTilePix, end - base);
-        for (int j = 0; j < m; ++j) {
+        raster_chunk(s_c, (int)min((uint64_t)kChunk, end - base), px0, py0, s_mask);
+        __syncthreads();
+        uint32_t mk = s_mask[threadIdx.x];
+        s_mask[threadIdx.x] = 0;
+        uint32_t total;
+        uint32_t r = block_scan_tile(__popc(mk), s_w, total);
+        while (mk) {
+            uint32_t j = __ffs(mk) - 1;
+            mk &= mk - 1;
+            s_q[r++] = j | ((uint32_t)threadIdx.x << 5) | (k_run++ << 13);
+        }
+        __syncthreads();
+        for (uint32_t e = threadIdx.x; e < total; e += kTilePix) {
+            const uint32_t qe = s_q[e];
+            const uint32_t j = qe & 31u, p = (qe >> 5) & 255u, kk = qe >> 13;
+            const int px = px0 + (int)(p & (kTile - 1)), py = py0 + (int)(p / kTile);
+            const int32_t sx = 256 * px + 128, sy = 256 * py + 128;
             int64_t l[3];
-            if (!covers(s_tri[j], px, py, sx, sy, l)) continue;
+            (void)cover_sample(s_c[j], sx, sy, l);
             const TriShade& S = s_sh[j];
             uint32_t z = sample_depth(S.z[0], S.z[1], S.z[2], l[1], l[2], S.area, bad);
             float4 c = shade_fragment(S, l, px, py, sx, sy, sp);
-            if (o < o_end) {  // the count pass sized this list; never write past it
+            if (kk < s_len[p]) {  // the count pass sized this list; never write past it
+                const uint64_t o = s_base[p] + kk;
                 key[o] = ((uint64_t)z << 32) | (uint64_t)S.f2t;
                 rgba[o] = c;
             } else {
                 bad = true;
             }
-            ++o;
         }
         __syncthreads();
     }
@@ -428,6 +450,12 @@ cudaError_t launch_bin_fill(const DevMesh& m, FrameBufs& fb, int tiles_x, int W,
 {
     k_bin_fill<<<grid_for(m.n_faces, 256), 256, 0, s>>>(fb.fx, fb.fy, fb.fflags, m.n_faces, W, H, tiles_x, reverse,
                                                          fb.tile_off, fb.tile_cur, fb.bins);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_sort(FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_t s)
+{
+    k_bin_sort<<<(unsigned)(tiles_x * tiles_y), 256, 0, s>>>(fb.tile_off, fb.bins, fb.fz);
     return cudaGetLastError();
 }
 

@@ -43,9 +43,10 @@ __device__ __forceinline__ void tri_setup(const int32_t FX[4], const int32_t FY[
 {
     int i1 = tri == 0 ? 1 : 2, i2 = tri == 0 ? 2 : 3;
     t.vi[0] = 0; t.vi[1] = i1; t.vi[2] = i2;
+    // selects instead of FX[i1]: no dynamic register indexing
     t.X[0] = FX[0]; t.Y[0] = FY[0];
-    t.X[1] = FX[i1]; t.Y[1] = FY[i1];
-    t.X[2] = FX[i2]; t.Y[2] = FY[i2];
+    t.X[1] = tri == 0 ? FX[1] : FX[2]; t.Y[1] = tri == 0 ? FY[1] : FY[2];
+    t.X[2] = tri == 0 ? FX[2] : FX[3]; t.Y[2] = tri == 0 ? FY[2] : FY[3];
     int64_t a = edge_fn(t.X[0], t.Y[0], t.X[1], t.Y[1], t.X[2], t.Y[2]);
     if (a < 0) {
         int32_t tx = t.X[1], ty = t.Y[1];

@@ -290,6 +290,14 @@ def grid64_orbit_1080p() -> Workload:
                                tf_hi=0.15))
 
 
+def grid64_orbit_540p() -> Workload:
+    """The 64^3 orbit workload at 960x540 (a quarter of the pixels; for profiling)."""
+    w = grid64_orbit_1080p()
+    w.name = "grid64_warp0.3_jitter0.1_orbit120_960x540"
+    w.width, w.height = 960, 540
+    return w
+
+
 def grid128_orbit_4k() -> Workload:
     """128^3 warped grid (2.1M cells) at 3840x2160 (the cubic128-sized case)."""
     return Workload("grid128_warp0.3_jitter0.1_orbit500_3840x2160", 128, 0.1, 0.3, 4, 3840, 2160,
