@@ -256,6 +256,40 @@ hexfc_status hexfc_stage_times(hexfc_ctx* ctx, double* ms, uint64_t* frames, int
 /* Static string for a status code. Never NULL. */
 const char* hexfc_status_string(hexfc_status s);
 
+/* Size of the fixed device scratch array used by hexfc_render_noalloc. */
+#define HEXFC_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * hexfc_render without any memory allocation. The paper has no counterpart:
+ * this entry point exists for callers that cannot let a library allocate, for
+ * example an application that reserves all device memory for its own
+ * allocator or a fixed budget up front, or a frame loop that must not stall
+ * on cudaMalloc/cudaFree, which can synchronise the device.
+ *
+ * Same inputs, output and result as hexfc_render (the same kernels), but every
+ * per-frame buffer (projected vertices, face records, tile bins, counts,
+ * offsets, fragment lists) is carved from one file-scope device array of
+ * HEXFC_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU loading the library holds
+ * until the process exits. The call makes no cudaMalloc, cudaFree or
+ * cudaMallocHost; the mesh must already be uploaded, and out_rgba (device,
+ * height*width*4 float) is the caller's.
+ *
+ * - The first call on a device looks up the array's device address (with that
+ *   device current) and keeps it; make that first call before any stream
+ *   capture on that device.
+ * - All calls share the one array and it keeps the last call's contents (the
+ *   counters that must start at zero are cleared on the stream). Calls whose
+ *   work overlaps on the GPU (other streams, other threads, other contexts of
+ *   the same process on the same device) race on it: serialise them.
+ * - It waits on `stream` twice, like hexfc_render; stage timing is not recorded
+ *   and hexfc_debug_pixels keeps referring to the last hexfc_render* frame.
+ * Errors: ARG, STATE (no view or bad mesh), OVERFLOW (the frame needs more
+ * than HEXFC_NOALLOC_SCRATCH_BYTES, or a list longer than HEXFC_MAX_LIST;
+ * nothing is drawn, stats is filled as far as known), CUDA.
+ */
+hexfc_status hexfc_render_noalloc(hexfc_ctx* ctx, int32_t mesh, float* out_rgba, hexfc_frame_stats* stats,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

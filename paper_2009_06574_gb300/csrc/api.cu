@@ -662,3 +662,135 @@ const char* hexfc_status_string(hexfc_status s)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Rendering without any allocation (no counterpart in the paper).
+//
+// Every per-frame buffer of hexfc_render_noalloc lives in one fixed device
+// array of HEXFC_NOALLOC_SCRATCH_BYTES, defined here at file scope. Each GPU
+// that loads this library holds it until the process exits. In host code the
+// array's name is only a host-side stand-in, never a device address, so the
+// first call on a device (with that device current) looks the address up with
+// cudaGetSymbolAddress and remembers it for that device.
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HEXFC_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on `device` (current); nullptr on failure.
+void* noalloc_scratch(int device)
+{
+    if (device < 0 || device >= kMaxDevices) return nullptr;
+    if (!g_noalloc_ptr[device]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        g_noalloc_ptr[device] = p;
+    }
+    return g_noalloc_ptr[device];
+}
+
+// Bump carving of the scratch array in 256-byte aligned pieces.
+struct Arena {
+    unsigned char* base;
+    size_t used, cap;
+    template <typename T>
+    T* take(size_t n)
+    {
+        size_t off = (used + 255) & ~(size_t)255;
+        size_t bytes = (n == 0 ? 1 : n) * sizeof(T);
+        if (off > cap || bytes > cap - off) return nullptr;
+        used = off + bytes;
+        return reinterpret_cast<T*>(base + off);
+    }
+};
+
+hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_stats* stats, cudaStream_t s)
+{
+    unsigned char* scratch = static_cast<unsigned char*>(noalloc_scratch(ctx->device));
+    if (!scratch) return HEXFC_ERR_CUDA;
+    const int W = ctx->view.width, H = ctx->view.height;
+    const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
+    const int64_t n_tiles = (int64_t)tiles_x * tiles_y;
+    const int64_t n_pix = n_tiles * kTilePix;
+    const int64_t nparts = scan_partials_needed(std::max<int64_t>(n_pix, n_tiles)) + 1;
+    Arena a{scratch, 0, (size_t)HEXFC_NOALLOC_SCRATCH_BYTES};
+    FrameBufs fb;
+    fb.vproj = a.take<int4>((size_t)m->n_verts);
+    fb.ved = a.take<float>((size_t)m->n_verts);
+    fb.fx = a.take<int4>((size_t)m->n_faces);
+    fb.fy = a.take<int4>((size_t)m->n_faces);
+    fb.fz = a.take<uint4>((size_t)m->n_faces);
+    fb.fed = a.take<float4>((size_t)m->n_faces);
+    fb.fflags = a.take<uint32_t>((size_t)m->n_faces);
+    fb.tile_cnt = a.take<uint32_t>((size_t)n_tiles + 1);
+    fb.tile_off = a.take<uint64_t>((size_t)n_tiles + 1);
+    fb.tile_cur = a.take<uint32_t>((size_t)n_tiles + 1);
+    fb.cnt = a.take<uint32_t>((size_t)n_pix + 1);
+    fb.off = a.take<uint64_t>((size_t)n_pix + 1);
+    fb.long_q = a.take<uint32_t>((size_t)n_pix + 1);
+    fb.part = a.take<uint64_t>(2 * (size_t)nparts);
+    fb.part_max = a.take<uint32_t>(2 * (size_t)nparts);
+    fb.scal = a.take<uint64_t>(16);
+    if (!fb.vproj || !fb.ved || !fb.fx || !fb.fy || !fb.fz || !fb.fed || !fb.fflags || !fb.tile_cnt ||
+        !fb.tile_off || !fb.tile_cur || !fb.cnt || !fb.off || !fb.long_q || !fb.part || !fb.part_max || !fb.scal)
+        return HEXFC_ERR_OVERFLOW;
+    // the array keeps the previous call's contents: clear what must start at zero
+    CK(cudaMemsetAsync(fb.tile_cnt, 0, sizeof(uint32_t) * (size_t)n_tiles, s));
+    CK(cudaMemsetAsync(fb.tile_cur, 0, sizeof(uint32_t) * (size_t)n_tiles, s));
+    CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * 16, s));
+    CK(launch_vertex_setup(*m, ctx->cam, fb, s));
+    CK(launch_face_setup(*m, ctx->cam, ctx->style.lod, ctx->style.delta, fb, tiles_x, tiles_y, s));
+    CK(scan_u32_to_u64(fb.tile_cnt, fb.tile_off, n_tiles, fb.part, fb.part_max, fb.scal + 8, 0xFFFFFFFFu, s));
+    uint64_t h[16] = {};  // pageable host copy of the totals (no pinned allocation)
+    CK(cudaMemcpyAsync(h + 8, fb.scal + 8, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint64_t n_bins = h[8];
+    fb.bins = a.take<uint32_t>((size_t)n_bins);
+    hexfc_frame_stats fs{};
+    fs.bin_entries = n_bins;
+    fs.width = (uint32_t)W;
+    fs.height = (uint32_t)H;
+    if (!fb.bins) {
+        if (stats) *stats = fs;
+        return HEXFC_ERR_OVERFLOW;
+    }
+    CK(launch_bin_fill(*m, fb, tiles_x, W, H, ctx->reverse_bins, s));
+    CK(launch_bin_sort(fb, tiles_x, tiles_y, s));
+    CK(launch_count(fb, tiles_x, tiles_y, W, H, s));
+    CK(scan_u32_to_u64(fb.cnt, fb.off, n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
+    CK(cudaMemcpyAsync(h, fb.scal, 3 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint64_t total = h[0];
+    const uint32_t n_long = (uint32_t)h[2];
+    fs.fragments = total;
+    fs.max_list = (uint32_t)h[1];
+    fs.long_lists = n_long;
+    fs.kernel_launches = 12 + (n_long > 0 ? 1u : 0u);
+    if (stats) *stats = fs;
+    if (fs.max_list > HEXFC_MAX_LIST) return HEXFC_ERR_OVERFLOW;
+    fb.key = a.take<uint64_t>((size_t)total);
+    fb.rgba = a.take<float4>((size_t)total);
+    if (!fb.key || !fb.rgba) return HEXFC_ERR_OVERFLOW;
+    ShadeParams sp = make_shade(ctx);
+    CK(launch_fill(*m, fb, sp, tiles_x, tiles_y, W, H, s));
+    CK(launch_composite(fb, sp, tiles_x, tiles_y, W, H, out, n_long, s));
+    return HEXFC_OK;
+}
+
+}  // namespace
+
+extern "C" hexfc_status hexfc_render_noalloc(hexfc_ctx* ctx, int32_t mesh, float* out_rgba,
+                                             hexfc_frame_stats* stats, void* stream)
+{
+    if (!ctx || !out_rgba) return HEXFC_ERR_ARG;
+    DevMesh* m = get_mesh(ctx, mesh);
+    if (!m || !ctx->have_view) return HEXFC_ERR_STATE;
+    DeviceGuard g(ctx->device);
+    return render_frame_noalloc(ctx, m, out_rgba, stats, (cudaStream_t)stream);
+}

@@ -26,6 +26,7 @@ HEXFC_ERR_TIMEOUT = -5
 HEXFC_ERR_MESH = -6
 HEXFC_ERR_STATE = -7
 HEXFC_MAX_LIST = 8192
+HEXFC_NOALLOC_SCRATCH_BYTES = 32 << 20
 HEXFC_LENS_SCREEN = 0
 HEXFC_LENS_SPHERE = 1
 HEXFC_METRIC_SCALED_JACOBIAN = 0
@@ -39,7 +40,7 @@ STAGES = ["vertex", "face", "tile_scan", "gap1", "bin", "count", "scan", "gap2",
 EXPORTS = ["hexfc_style_default", "hexfc_create", "hexfc_destroy", "hexfc_upload_mesh", "hexfc_cell_quality",
            "hexfc_set_cell_importance", "hexfc_mesh_info", "hexfc_set_view", "hexfc_set_lens",
            "hexfc_set_style", "hexfc_render", "hexfc_render_host", "hexfc_debug_pixels", "hexfc_set_option",
-           "hexfc_stage_times", "hexfc_status_string"]
+           "hexfc_stage_times", "hexfc_status_string", "hexfc_render_noalloc"]
 
 
 class HexfcError(RuntimeError):
@@ -107,6 +108,7 @@ def load():
                 "hexfc_set_option": (i32, [vp, i32, i64]),
                 "hexfc_stage_times": (i32, [vp, vp, C.POINTER(u64), i32]),
                 "hexfc_status_string": (C.c_char_p, [i32]),
+                "hexfc_render_noalloc": (i32, [vp, i32, vp, C.POINTER(hexfc_frame_stats), vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -254,6 +256,17 @@ class Renderer:
         self.last_stats = st.as_dict()
         if check:
             _check(r, "hexfc_render")
+        return r
+
+    def render_noalloc(self, mesh: int, out, stream=None, check: bool = True):
+        """Like render, with every per-frame buffer in the library's fixed scratch
+        array (no allocation). out: torch float32 CUDA tensor [H, W, 4]."""
+        st = hexfc_frame_stats()
+        r = load().hexfc_render_noalloc(self._h, int(mesh), C.c_void_p(out.data_ptr()), C.byref(st),
+                                        _stream_ptr(stream))
+        self.last_stats = st.as_dict()
+        if check:
+            _check(r, "hexfc_render_noalloc")
         return r
 
     def render_host(self, mesh: int, out: np.ndarray, stream=None, check: bool = True):
