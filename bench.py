@@ -335,7 +335,8 @@ def run_ours(args, rank, world, local_rank):
                    "height": w.height, "frames": w.n_frames,
                    "l2": "not flushed: per-frame working set (fragment lists) far larger than L2",
                    "parallelism": f"replicas x{world}"},
-        "fragments_per_s": F * fps, "fragments_per_frame": F,
+        "fragments_per_s": F * fps, "fragments_per_frame": F, "bins_per_frame": bins,
+        "kernels_gbs": {k: round(algo[k] / (kernel_stages[k] / 1000.0) / 1e9, 1) for k in algo},
         "stage_ms": {k: round(v, 4) for k, v in per_frame.items()},
         "roofline": {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": float(traffic) if traffic else None,

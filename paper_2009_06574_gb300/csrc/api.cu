@@ -108,7 +108,8 @@ void free_mesh(DevMesh* m)
 void free_frame(FrameBufs& f)
 {
     dfree(f.vproj); dfree(f.ved); dfree(f.fx); dfree(f.fy); dfree(f.fz); dfree(f.fed); dfree(f.fflags);
-    dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.bins); dfree(f.cnt); dfree(f.off);
+    dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.bins); dfree(f.masks); dfree(f.cnt);
+    dfree(f.off);
     dfree(f.part); dfree(f.part_max); dfree(f.long_q); dfree(f.key); dfree(f.rgba); dfree(f.scal);
     if (f.h_scal) cudaFreeHost(f.h_scal);
     f = FrameBufs{};
@@ -273,15 +274,18 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
     mark(ctx, 1, s);
     CK(launch_face_setup(*m, ctx->cam, ctx->style.lod, ctx->style.delta, fb, tiles_x, tiles_y, s));
     mark(ctx, 2, s);
-    CK(scan_u32_to_u64(fb.tile_cnt, fb.tile_off, n_tiles, fb.part, fb.part_max, fb.scal + 8, 0xFFFFFFFFu, s));
+    CK(scan_u32_to_u64(fb.tile_cnt, fb.tile_off, n_tiles, fb.part, fb.part_max, fb.scal + 8, 0xFFFFFFFFu, s,
+                       (uint32_t)kChunk));
     mark(ctx, 3, s);
     launches += 5;
     CK(cudaMemcpyAsync(fb.h_scal + 8, fb.scal + 8, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     collect(ctx);
-    const uint64_t n_bins = fb.h_scal[8];
+    const uint64_t n_bins = fb.h_scal[8];   // padded to whole chunks per tile
     if ((st = ensure(&fb.bins, &fb.bin_cap, (int64_t)n_bins)) != HEXFC_OK) return st;
+    if ((st = ensure(&fb.masks, &fb.mask_cap, (int64_t)n_bins * (kTilePix / kChunk))) != HEXFC_OK) return st;
     mark(ctx, 4, s);
+    CK(cudaMemsetAsync(fb.bins, 0xFF, sizeof(uint32_t) * (size_t)n_bins, s));   // padding slots = kPadBin
     CK(launch_bin_fill(*m, fb, tiles_x, W, H, ctx->reverse_bins, s));
     CK(launch_bin_sort(fb, tiles_x, tiles_y, s));
     mark(ctx, 5, s);
@@ -746,20 +750,23 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * 16, s));
     CK(launch_vertex_setup(*m, ctx->cam, fb, s));
     CK(launch_face_setup(*m, ctx->cam, ctx->style.lod, ctx->style.delta, fb, tiles_x, tiles_y, s));
-    CK(scan_u32_to_u64(fb.tile_cnt, fb.tile_off, n_tiles, fb.part, fb.part_max, fb.scal + 8, 0xFFFFFFFFu, s));
+    CK(scan_u32_to_u64(fb.tile_cnt, fb.tile_off, n_tiles, fb.part, fb.part_max, fb.scal + 8, 0xFFFFFFFFu, s,
+                       (uint32_t)kChunk));
     uint64_t h[16] = {};  // pageable host copy of the totals (no pinned allocation)
     CK(cudaMemcpyAsync(h + 8, fb.scal + 8, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const uint64_t n_bins = h[8];
     fb.bins = a.take<uint32_t>((size_t)n_bins);
+    fb.masks = a.take<uint32_t>((size_t)n_bins * (kTilePix / kChunk));
     hexfc_frame_stats fs{};
     fs.bin_entries = n_bins;
     fs.width = (uint32_t)W;
     fs.height = (uint32_t)H;
-    if (!fb.bins) {
+    if (!fb.bins || !fb.masks) {
         if (stats) *stats = fs;
         return HEXFC_ERR_OVERFLOW;
     }
+    CK(cudaMemsetAsync(fb.bins, 0xFF, sizeof(uint32_t) * (size_t)n_bins, s));   // padding slots = kPadBin
     CK(launch_bin_fill(*m, fb, tiles_x, W, H, ctx->reverse_bins, s));
     CK(launch_bin_sort(fb, tiles_x, tiles_y, s));
     CK(launch_count(fb, tiles_x, tiles_y, W, H, s));
@@ -774,7 +781,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fs.kernel_launches = 12 + (n_long > 0 ? 1u : 0u);
     if (stats) *stats = fs;
     if (fs.max_list > HEXFC_MAX_LIST) return HEXFC_ERR_OVERFLOW;
-    fb.key = a.take<uint64_t>((size_t)total);
+    fb.key = a.take<uint64_t>((size_t)total + 2);   // the composite widens key copies to 16-byte boundaries
     fb.rgba = a.take<float4>((size_t)total);
     if (!fb.key || !fb.rgba) return HEXFC_ERR_OVERFLOW;
     ShadeParams sp = make_shade(ctx);

@@ -11,6 +11,8 @@ constexpr int kTile = 16;                 // raster tile edge in pixels
 constexpr int kTilePix = kTile * kTile;   // pixels (= threads) per tile CTA
 constexpr int kWarpSortMax = 256;         // longest list sorted in registers by one warp
 constexpr uint64_t kPadKey = ~0ull;
+constexpr int kChunk = 32;                // triangles per raster chunk (one coverage bit each)
+constexpr uint32_t kPadBin = 0xFFFFFFFFu; // empty slot: tile lists are padded to whole chunks
 
 // Camera constants of the vertex stage (double, evaluated without FMA).
 struct CamParams {
@@ -73,8 +75,10 @@ struct FrameBufs {
     uint64_t* tile_off = nullptr;   // [T+1]
     uint32_t* tile_cur = nullptr;   // [T]
     int64_t t_cap = 0;
-    uint32_t* bins = nullptr;       // face2tri ids grouped by tile
+    uint32_t* bins = nullptr;       // face2tri ids grouped by tile, each tile padded to whole chunks
     int64_t bin_cap = 0;
+    uint32_t* masks = nullptr;      // per chunk of a tile list: 256 per-pixel coverage masks
+    int64_t mask_cap = 0;
     // pixels (tile-major)
     uint32_t* cnt = nullptr;        // [P]
     uint64_t* off = nullptr;        // [P]
@@ -116,7 +120,7 @@ cudaError_t launch_debug_gather(FrameBufs& fb, const int32_t* d_px, const int32_
 // scans
 cudaError_t scan_u32_to_u64(const uint32_t* in, uint64_t* out, int64_t n, uint64_t* part,
                             uint32_t* part_max, uint64_t* total_and_max, uint32_t long_threshold,
-                            cudaStream_t s);
+                            cudaStream_t s, uint32_t round_to = 0);
 int64_t scan_partials_needed(int64_t n);
 
 }  // namespace hexfc

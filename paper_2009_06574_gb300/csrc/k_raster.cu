@@ -151,8 +151,9 @@ __global__ void k_bin_fill(const int4* __restrict__ fx, const int4* __restrict__
 constexpr int kBinSortMax = 4096;   // longer tile lists keep their arrival order
 
 // Orders each tile's list by triangle depth (sum of the three window depths,
-// then 2*face+tri). Any order gives the same fragments; depth order makes
-// the fill write almost every per-pixel list already sorted front to back.
+// then 2*face+tri); the padding slots (kPadBin) go last. Any order gives the
+// same fragments; depth order makes the fill write almost every per-pixel list
+// already sorted front to back.
 __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ tile_off, uint32_t* __restrict__ bins,
                                                   const uint4* __restrict__ fz)
 {
@@ -167,9 +168,11 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
         uint64_t k = ~0ull;
         if (i < n) {
             uint32_t f2t = bins[beg + i];
-            uint4 z = fz[f2t >> 1];
-            uint64_t zs = (uint64_t)z.x + ((f2t & 1) ? (uint64_t)z.z + z.w : (uint64_t)z.y + z.z);
-            k = (zs << 32) | f2t;
+            if (f2t != kPadBin) {
+                uint4 z = fz[f2t >> 1];
+                uint64_t zs = (uint64_t)z.x + ((f2t & 1) ? (uint64_t)z.z + z.w : (uint64_t)z.y + z.z);
+                k = (zs << 32) | f2t;
+            }
         }
         s_k[i] = k;
     }
@@ -186,61 +189,70 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
             }
             __syncthreads();
         }
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) bins[beg + i] = (uint32_t)s_k[i];
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        uint64_t k = s_k[i];
+        bins[beg + i] = k == ~0ull ? kPadBin : (uint32_t)k;
+    }
 }
 
 // ------------------------------------------------------------------ raster per tile
 
-constexpr int kChunk = 32;   // triangles staged per step (one coverage bit each)
-
-// Coverage data of one staged triangle.
+// Coverage data of one staged triangle: its three edge functions at the first
+// sample of its box (clipped to the tile) and their per-pixel steps, exact.
 struct TriC {
-    int32_t X[3], Y[3];   // wound to positive area (16.8)
-    uint32_t meta;        // bit k: top-left rule owns the edge opposite vertex k
+    int64_t e0[3];        // edge function opposite vertex k at the box origin sample
+    int32_t dx[3], dy[3]; // edge vector (b - a) of that edge, 16.8
+    uint32_t meta;        // bit k: top-left rule owns edge k
     int16_t lx0, ly0;     // box of covered pixel centres, tile-local
     int16_t bw, bh;       // box size, 0 when the triangle misses the tile
     float inv_bw;
 };
 
-__device__ __forceinline__ void stage_cov(const int4* __restrict__ fx, const int4* __restrict__ fy, uint32_t f2t,
-                                          int W, int H, int px0, int py0, TriC& c, TriGeom& t)
+__device__ __forceinline__ void empty_cov(TriC& c)
 {
-    uint32_t f = f2t >> 1, tri = f2t & 1;
-    int4 a = fx[f], b = fy[f];
+    c.lx0 = c.ly0 = 0;
+    c.bw = c.bh = 0;
+    c.inv_bw = 0.f;
+}
+
+__device__ __forceinline__ void stage_cov(int4 a, int4 b, uint32_t f2t, int W, int H, int px0, int py0, TriC& c,
+                                          TriGeom& t)
+{
     int32_t X[4] = {a.x, a.y, a.z, a.w}, Y[4] = {b.x, b.y, b.z, b.w};
-    tri_setup(X, Y, (int)tri, W, H, t);
-    uint32_t meta = 0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        c.X[k] = t.X[k];
-        c.Y[k] = t.Y[k];
-        int a0 = (k + 1) % 3, b0 = (k + 2) % 3;
-        meta |= (top_left(t.X[a0], t.Y[a0], t.X[b0], t.Y[b0]) ? 1u : 0u) << k;
-    }
-    c.meta = meta;
+    tri_setup(X, Y, (int)(f2t & 1), W, H, t);
     int x0 = max(t.bx0, px0), x1 = min(t.bx1, px0 + kTile - 1);
     int y0 = max(t.by0, py0), y1 = min(t.by1, py0 + kTile - 1);
     if (!t.valid || x0 > x1 || y0 > y1) {
-        c.lx0 = c.ly0 = 0;
-        c.bw = c.bh = 0;
-        c.inv_bw = 0.f;
-    } else {
-        c.lx0 = (int16_t)(x0 - px0);
-        c.ly0 = (int16_t)(y0 - py0);
-        c.bw = (int16_t)(x1 - x0 + 1);
-        c.bh = (int16_t)(y1 - y0 + 1);
-        c.inv_bw = 1.f / (float)c.bw;
+        empty_cov(c);
+        return;
     }
+    const int32_t sx = 256 * x0 + 128, sy = 256 * y0 + 128;
+    uint32_t meta = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int ia = (k + 1) % 3, ib = (k + 2) % 3;
+        c.e0[k] = edge_fn(t.X[ia], t.Y[ia], t.X[ib], t.Y[ib], sx, sy);
+        c.dx[k] = t.X[ib] - t.X[ia];
+        c.dy[k] = t.Y[ib] - t.Y[ia];
+        meta |= (top_left(t.X[ia], t.Y[ia], t.X[ib], t.Y[ib]) ? 1u : 0u) << k;
+    }
+    c.meta = meta;
+    c.lx0 = (int16_t)(x0 - px0);
+    c.ly0 = (int16_t)(y0 - py0);
+    c.bw = (int16_t)(x1 - x0 + 1);
+    c.bh = (int16_t)(y1 - y0 + 1);
+    c.inv_bw = 1.f / (float)c.bw;
 }
 
-// Exact coverage of sample (sx, sy); l[k] = weight of vertex k (sums to the area).
-__device__ __forceinline__ bool cover_sample(const TriC& c, int32_t sx, int32_t sy, int64_t l[3])
+// Exact coverage of the sample (rx, ry) pixels from the box origin;
+// l[k] = edge function k = weight of vertex k (they sum to the area).
+__device__ __forceinline__ bool cover_at(const TriC& c, int rx, int ry, int64_t l[3])
 {
+    const int32_t sx = rx << 8, sy = ry << 8;
     bool in = true;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        int a = (k + 1) % 3, b = (k + 2) % 3;
-        int64_t e = edge_fn(c.X[a], c.Y[a], c.X[b], c.Y[b], sx, sy);
+        int64_t e = c.e0[k] + (int64_t)c.dx[k] * sy - (int64_t)c.dy[k] * sx;
         l[k] = e;
         in = in && (e > 0 || (e == 0 && ((c.meta >> k) & 1u)));
     }
@@ -249,46 +261,65 @@ __device__ __forceinline__ bool cover_sample(const TriC& c, int32_t sx, int32_t 
 
 // Coverage of one chunk: a warp walks each triangle's box (clipped to the
 // tile), one sample per lane, and sets bit j of the covered pixels' masks.
-__device__ __forceinline__ void raster_chunk(const TriC* s_c, int m, int px0, int py0, uint32_t* s_mask)
+__device__ __forceinline__ void raster_chunk(const TriC* s_c, int px0, int py0, uint32_t* s_mask)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int j = warp; j < m; j += kTilePix / 32) {
+    (void)px0;
+    (void)py0;
+    for (int j = warp; j < kChunk; j += kTilePix / 32) {
         const TriC& c = s_c[j];
         const int area = (int)c.bw * (int)c.bh;
         for (int idx = lane; idx < area; idx += 32) {
             // exact for idx < 256, bw <= 16: the quotient is never within 1/32 of an integer
             int ry = (int)(((float)idx + 0.5f) * c.inv_bw);
             int rx = idx - ry * c.bw;
-            int lx = c.lx0 + rx, ly = c.ly0 + ry;
             int64_t l[3];
-            if (cover_sample(c, 256 * (px0 + lx) + 128, 256 * (py0 + ly) + 128, l))
-                atomicOr(s_mask + ly * kTile + lx, 1u << j);
+            if (cover_at(c, rx, ry, l)) atomicOr(s_mask + (c.ly0 + ry) * kTile + c.lx0 + rx, 1u << j);
         }
     }
 }
 
+// Per tile: coverage of every chunk of 32 triangles as per-pixel bit masks;
+// the masks are kept for the fill pass and their bit counts are the per-pixel
+// list lengths.
 __global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__ tile_off,
                                                     const uint32_t* __restrict__ bins,
                                                     const int4* __restrict__ fx, const int4* __restrict__ fy,
-                                                    int tiles_x, int W, int H, uint32_t* __restrict__ cnt)
+                                                    int tiles_x, int W, int H, uint32_t* __restrict__ cnt,
+                                                    uint32_t* __restrict__ masks)
 {
     __shared__ TriC s_c[kChunk];
     __shared__ uint32_t s_mask[kTilePix];
     const int tile = blockIdx.x;
     const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
-    const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];
+    const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
     s_mask[threadIdx.x] = 0;
     uint32_t n = 0;
+    // the staging warp loads chunk c+1 while the block rasterises chunk c
+    uint32_t f2t_n = kPadBin;
+    int4 a_n = make_int4(0, 0, 0, 0), b_n = a_n;
+    if (threadIdx.x < kChunk && beg < end) {
+        f2t_n = bins[beg + threadIdx.x];
+        if (f2t_n != kPadBin) { a_n = fx[f2t_n >> 1]; b_n = fy[f2t_n >> 1]; }
+    }
     for (uint64_t base = beg; base < end; base += kChunk) {
-        if (threadIdx.x < kChunk && base + threadIdx.x < end) {
+        if (threadIdx.x < kChunk) {
             TriGeom t;
-            stage_cov(fx, fy, bins[base + threadIdx.x], W, H, px0, py0, s_c[threadIdx.x], t);
+            if (f2t_n != kPadBin) stage_cov(a_n, b_n, f2t_n, W, H, px0, py0, s_c[threadIdx.x], t);
+            else empty_cov(s_c[threadIdx.x]);
+            f2t_n = kPadBin;
+            if (base + kChunk < end) {
+                f2t_n = bins[base + kChunk + threadIdx.x];
+                if (f2t_n != kPadBin) { a_n = fx[f2t_n >> 1]; b_n = fy[f2t_n >> 1]; }
+            }
         }
         __syncthreads();
-        raster_chunk(s_c, (int)min((uint64_t)kChunk, end - base), px0, py0, s_mask);
+        raster_chunk(s_c, px0, py0, s_mask);
         __syncthreads();
-        n += __popc(s_mask[threadIdx.x]);
+        uint32_t mk = s_mask[threadIdx.x];
         s_mask[threadIdx.x] = 0;
+        n += __popc(mk);
+        masks[(base / kChunk) * kTilePix + threadIdx.x] = mk;
     }
     cnt[(int64_t)tile * kTilePix + threadIdx.x] = n;
 }
@@ -318,17 +349,25 @@ __device__ __forceinline__ uint32_t block_scan_tile(uint32_t v, uint32_t* s_w, u
     return pre + x - v;
 }
 
-__device__ __forceinline__ void stage_shade(const int4* __restrict__ fx, const int4* __restrict__ fy,
-                                            const uint4* __restrict__ fz, const float4* __restrict__ fed,
-                                            const uint32_t* __restrict__ fflags, const float4* __restrict__ fimp,
-                                            const float4* __restrict__ fpx, const float4* __restrict__ fpy,
-                                            const float4* __restrict__ fpz, uint32_t f2t, const TriGeom& t,
-                                            TriShade& S)
+__device__ __forceinline__ void stage_shade(const int4 a, const int4 b, const uint4* __restrict__ fz,
+                                            const float4* __restrict__ fed, const uint32_t* __restrict__ fflags,
+                                            const float4* __restrict__ fimp, const float4* __restrict__ fpx,
+                                            const float4* __restrict__ fpy, const float4* __restrict__ fpz,
+                                            uint32_t f2t, const TriGeom& t, TriShade& S)
 {
     uint32_t f = f2t >> 1;
-    int4 a = fx[f], b = fy[f];
     S.FX[0] = a.x; S.FX[1] = a.y; S.FX[2] = a.z; S.FX[3] = a.w;
     S.FY[0] = b.x; S.FY[1] = b.y; S.FY[2] = b.z; S.FY[3] = b.w;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int k1 = (k + 1) & 3;
+        int32_t ex = S.FX[k1] - S.FX[k], ey = S.FY[k1] - S.FY[k];
+        S.ex[k] = ex;
+        S.ey[k] = ey;
+        int64_t l2 = (int64_t)ex * ex + (int64_t)ey * ey;
+        S.len2[k] = l2;
+        S.inv_len[k] = l2 > 0 ? rsqrtf((float)l2) : 0.f;
+    }
     uint4 z4 = fz[f];
     float4 e4 = fed[f], i4 = fimp[f], x4 = fpx[f], y4 = fpy[f], w4 = fpz[f];
     uint32_t zz[4] = {z4.x, z4.y, z4.z, z4.w};
@@ -339,23 +378,28 @@ __device__ __forceinline__ void stage_shade(const int4* __restrict__ fx, const i
         int c = t.vi[k];
         // select corner c without dynamic register indexing
         S.z[k] = c == 0 ? zz[0] : c == 1 ? zz[1] : c == 2 ? zz[2] : zz[3];
-        S.ed[k] = c == 0 ? ee[0] : c == 1 ? ee[1] : c == 2 ? ee[2] : ee[3];
+        float ed = c == 0 ? ee[0] : c == 1 ? ee[1] : c == 2 ? ee[2] : ee[3];
+        S.ed[k] = ed;
+        S.inv_ed[k] = 1.f / ed;
         S.imp[k] = c == 0 ? ii[0] : c == 1 ? ii[1] : c == 2 ? ii[2] : ii[3];
         S.P[k][0] = c == 0 ? xx[0] : c == 1 ? xx[1] : c == 2 ? xx[2] : xx[3];
         S.P[k][1] = c == 0 ? yy[0] : c == 1 ? yy[1] : c == 2 ? yy[2] : yy[3];
         S.P[k][2] = c == 0 ? ww[0] : c == 1 ? ww[1] : c == 2 ? ww[2] : ww[3];
     }
     S.area = t.area;
+    S.inv_area = 1.f / (float)t.area;
     S.f2t = f2t;
     S.masks = fflags[f] & 0xFFu;
 }
 
-// Per tile: coverage of each chunk as per-pixel bit masks; the covered
-// samples are compacted into a queue (pixel-major, in list order) so that the
-// shading runs on every lane; each fragment is written at its pixel's offset
-// plus its rank in the pixel's list (the rank the count pass sized).
+// Per tile: the coverage masks of the count pass give, chunk by chunk, each
+// pixel's covered triangles; the covered samples are compacted into a queue
+// (pixel-major, in list order) so that the shading runs on every lane, and
+// each fragment is written at its pixel's offset plus its rank in the pixel's
+// list (the rank the count pass sized).
 __global__ void __launch_bounds__(kTilePix) k_fill(const uint64_t* __restrict__ tile_off,
                                                    const uint32_t* __restrict__ bins,
+                                                   const uint32_t* __restrict__ masks,
                                                    const int4* __restrict__ fx, const int4* __restrict__ fy,
                                                    const uint4* __restrict__ fz, const float4* __restrict__ fed,
                                                    const uint32_t* __restrict__ fflags,
@@ -367,37 +411,37 @@ __global__ void __launch_bounds__(kTilePix) k_fill(const uint64_t* __restrict__ 
 {
     __shared__ TriC s_c[kChunk];
     __shared__ TriShade s_sh[kChunk];
-    __shared__ uint32_t s_mask[kTilePix];
     __shared__ uint32_t s_q[kChunk * kTilePix];
     __shared__ uint64_t s_base[kTilePix];
     __shared__ uint32_t s_len[kTilePix];
     __shared__ uint32_t s_w[kTilePix / 32];
     const int tile = blockIdx.x;
     const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
-    const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];
+    const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
     {
         const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;
         uint64_t o0 = off[q];
         s_base[threadIdx.x] = o0;
         s_len[threadIdx.x] = (uint32_t)(off[q + 1] - o0);
-        s_mask[threadIdx.x] = 0;
     }
     uint32_t k_run = 0;
     bool bad = false;
     for (uint64_t base = beg; base < end; base += kChunk) {
-        if (threadIdx.x < kChunk && base + threadIdx.x < end) {
+        uint32_t mk = masks[(base / kChunk) * kTilePix + threadIdx.x];
+        if (threadIdx.x < kChunk) {
             uint32_t f2t = bins[base + threadIdx.x];
-            TriGeom t;
-            stage_cov(fx, fy, f2t, W, H, px0, py0, s_c[threadIdx.x], t);
-            stage_shade(fx, fy, fz, fed, fflags, fimp, fpx, fpy, fpz, f2t, t, s_sh[threadIdx.x]);
+            if (f2t != kPadBin) {
+                TriGeom t;
+                int4 a = fx[f2t >> 1], b = fy[f2t >> 1];
+                stage_cov(a, b, f2t, W, H, px0, py0, s_c[threadIdx.x], t);
+                if (s_c[threadIdx.x].bw > 0)
+                    stage_shade(a, b, fz, fed, fflags, fimp, fpx, fpy, fpz, f2t, t, s_sh[threadIdx.x]);
+            } else {
+                empty_cov(s_c[threadIdx.x]);
+            }
         }
-        __syncthreads();
-        raster_chunk(s_c, (int)min((uint64_t)kChunk, end - base), px0, py0, s_mask);
-        __syncthreads();
-        uint32_t mk = s_mask[threadIdx.x];
-        s_mask[threadIdx.x] = 0;
         uint32_t total;
-        uint32_t r = block_scan_tile(__popc(mk), s_w, total);
+        uint32_t r = block_scan_tile(__popc(mk), s_w, total);   // contains a block barrier
         while (mk) {
             uint32_t j = __ffs(mk) - 1;
             mk &= mk - 1;
@@ -407,17 +451,18 @@ __global__ void __launch_bounds__(kTilePix) k_fill(const uint64_t* __restrict__ 
         for (uint32_t e = threadIdx.x; e < total; e += kTilePix) {
             const uint32_t qe = s_q[e];
             const uint32_t j = qe & 31u, p = (qe >> 5) & 255u, kk = qe >> 13;
-            const int px = px0 + (int)(p & (kTile - 1)), py = py0 + (int)(p / kTile);
-            const int32_t sx = 256 * px + 128, sy = 256 * py + 128;
+            const int lx = (int)(p & (kTile - 1)), ly = (int)(p / kTile);
+            const int px = px0 + lx, py = py0 + ly;
+            const TriC& c = s_c[j];
             int64_t l[3];
-            (void)cover_sample(s_c[j], sx, sy, l);
+            (void)cover_at(c, lx - c.lx0, ly - c.ly0, l);
             const TriShade& S = s_sh[j];
-            uint32_t z = sample_depth(S.z[0], S.z[1], S.z[2], l[1], l[2], S.area, bad);
-            float4 c = shade_fragment(S, l, px, py, sx, sy, sp);
+            uint32_t z = sample_depth_fast(S.z[0], S.z[1], S.z[2], l[1], l[2], S.area, S.inv_area, bad);
+            float4 col = shade_fragment(S, l, px, py, 256 * px + 128, 256 * py + 128, sp);
             if (kk < s_len[p]) {  // the count pass sized this list; never write past it
                 const uint64_t o = s_base[p] + kk;
                 key[o] = ((uint64_t)z << 32) | (uint64_t)S.f2t;
-                rgba[o] = c;
+                rgba[o] = col;
             } else {
                 bad = true;
             }
@@ -462,16 +507,16 @@ cudaError_t launch_bin_sort(FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_
 cudaError_t launch_count(FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, cudaStream_t s)
 {
     k_count<<<(unsigned)(tiles_x * tiles_y), kTilePix, 0, s>>>(fb.tile_off, fb.bins, fb.fx, fb.fy, tiles_x, W, H,
-                                                                fb.cnt);
+                                                                fb.cnt, fb.masks);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W,
                         int H, cudaStream_t s)
 {
-    k_fill<<<(unsigned)(tiles_x * tiles_y), kTilePix, 0, s>>>(fb.tile_off, fb.bins, fb.fx, fb.fy, fb.fz, fb.fed,
-                                                               fb.fflags, m.fimp, m.fpx, m.fpy, m.fpz, tiles_x, W, H,
-                                                               sp, fb.off, fb.key, fb.rgba, fb.scal + 5);
+    k_fill<<<(unsigned)(tiles_x * tiles_y), kTilePix, 0, s>>>(fb.tile_off, fb.bins, fb.masks, fb.fx, fb.fy, fb.fz,
+                                                               fb.fed, fb.fflags, m.fimp, m.fpx, m.fpy, m.fpz, tiles_x,
+                                                               W, H, sp, fb.off, fb.key, fb.rgba, fb.scal + 5);
     return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
 // Exclusive prefix scan of uint32 counts into uint64 offsets, with the total,
-// the maximum and the number of entries above a threshold. Three phases:
+// the maximum and the number of entries above a threshold (each count can be
+// rounded up to a power of two first). Three phases:
 // per-block reduce, scan of the block partials in one block, per-block
 // down-sweep. It replaces the global append counter of per-pixel linked lists
 // (Section "GPU Implementation") by exact offsets, so that every pixel's
@@ -62,7 +63,7 @@ __device__ __forceinline__ uint64_t warp_sum(uint64_t v)
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n,
                                                               uint64_t* __restrict__ part,
                                                               uint32_t* __restrict__ part_max,
-                                                              uint32_t long_thr)
+                                                              uint32_t long_thr, uint32_t round_mask)
 {
     __shared__ uint64_t s_sum[32], s_long[32];
     __shared__ uint32_t s_max[32];
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         int64_t i = base + k;
-        uint32_t v = i < n ? in[i] : 0u;
+        uint32_t v = i < n ? ((in[i] + round_mask) & ~round_mask) : 0u;
         sum += v;
         mx = max(mx, v);
         nlong += v > long_thr ? 1u : 0u;
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partials(uint64_t* __rest
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ in, int64_t n,
                                                             const uint64_t* __restrict__ part,
                                                             uint64_t* __restrict__ out,
-                                                            const uint64_t* __restrict__ scal)
+                                                            const uint64_t* __restrict__ scal, uint32_t round_mask)
 {
     int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         int64_t i = base + k;
-        v[k] = i < n ? in[i] : 0u;
+        v[k] = i < n ? ((in[i] + round_mask) & ~round_mask) : 0u;
         local += v[k];
     }
     uint64_t tot;
@@ -166,13 +167,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
 int64_t scan_partials_needed(int64_t n) { return (n + kScanChunk - 1) / kScanChunk; }
 
 cudaError_t scan_u32_to_u64(const uint32_t* in, uint64_t* out, int64_t n, uint64_t* part,
-                            uint32_t* part_max, uint64_t* scal, uint32_t long_thr, cudaStream_t s)
+                            uint32_t* part_max, uint64_t* scal, uint32_t long_thr, cudaStream_t s,
+                            uint32_t round_to)
 {
     int64_t nb = scan_partials_needed(n);
     if (nb < 1) nb = 1;
-    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part, part_max, long_thr);
+    const uint32_t rm = round_to > 1 ? round_to - 1 : 0u;   // round_to: 0/1 or a power of two
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part, part_max, long_thr, rm);
     k_scan_partials<<<1, kScanThreads, 0, s>>>(part, part_max, nb, scal);
-    k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part, out, scal);
+    k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part, out, scal, rm);
     return cudaGetLastError();
 }
 

@@ -86,6 +86,19 @@ __device__ __forceinline__ int64_t floor_div_est(int64_t n, int64_t a, bool& bad
     return q;
 }
 
+// floor(n / a) as floor_div_est, from a float reciprocal of a (a > 0, |n / a| < 2^25).
+__device__ __forceinline__ int64_t floor_div_rcp(int64_t n, int64_t a, float inv_a, bool& bad)
+{
+    int64_t q = (int64_t)floorf((float)n * inv_a);
+    int64_t r = n - q * a;
+#pragma unroll 1
+    for (int it = 0; it < 16 && r < 0; ++it) { --q; r += a; }
+#pragma unroll 1
+    for (int it = 0; it < 16 && r >= a; ++it) { ++q; r -= a; }
+    if (r < 0 || r >= a) bad = true;
+    return q;
+}
+
 // Per-sample depth: z0 + floor((l1 (z1 - z0) + l2 (z2 - z0)) / area), exact.
 __device__ __forceinline__ uint32_t sample_depth(uint32_t z0, uint32_t z1, uint32_t z2, int64_t l1, int64_t l2,
                                                  int64_t area, bool& bad)
@@ -108,6 +121,16 @@ __device__ __forceinline__ uint32_t sample_depth(uint32_t z0, uint32_t z1, uint3
         q = (int64_t)qq;
     }
     return (uint32_t)((int64_t)z0 + q);
+}
+
+// sample_depth with a precomputed float reciprocal of the area (same result).
+__device__ __forceinline__ uint32_t sample_depth_fast(uint32_t z0, uint32_t z1, uint32_t z2, int64_t l1, int64_t l2,
+                                                      int64_t area, float inv_area, bool& bad)
+{
+    if (area >= (1ll << 38)) return sample_depth(z0, z1, z2, l1, l2, area, bad);
+    const int64_t d1 = (int64_t)z1 - (int64_t)z0, d2 = (int64_t)z2 - (int64_t)z0;
+    // |l| <= area < 2^38 and |d| < 2^24: the numerator fits in int64
+    return (uint32_t)((int64_t)z0 + floor_div_rcp(l1 * d1 + l2 * d2, area, inv_area, bad));
 }
 
 }  // namespace hexfc
