@@ -110,7 +110,7 @@ void free_frame(FrameBufs& f)
     dfree(f.vproj); dfree(f.ved); dfree(f.fx); dfree(f.fy); dfree(f.fz); dfree(f.fed); dfree(f.fflags);
     dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.bins); dfree(f.masks); dfree(f.cnt);
     dfree(f.off);
-    dfree(f.part); dfree(f.part_max); dfree(f.long_q); dfree(f.key); dfree(f.rgba); dfree(f.scal);
+    dfree(f.part); dfree(f.part_max); dfree(f.long_q); dfree(f.fix_q); dfree(f.key); dfree(f.rgba); dfree(f.scal);
     if (f.h_scal) cudaFreeHost(f.h_scal);
     f = FrameBufs{};
 }
@@ -244,10 +244,12 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
     }
     if (!fb.cnt || fb.p_cap < n_pix + 1) {
         int64_t c1 = 0, c2 = 0;
-        dfree(fb.off); dfree(fb.long_q);
+        int64_t c3 = 0;
+        dfree(fb.off); dfree(fb.long_q); dfree(fb.fix_q);
         if ((st = ensure(&fb.cnt, &fb.p_cap, n_pix + 1)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.off, &c1, fb.p_cap)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.long_q, &c2, fb.p_cap)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.fix_q, &c3, fb.p_cap)) != HEXFC_OK) return st;
     }
     int64_t nparts = scan_partials_needed(std::max<int64_t>(n_pix, n_tiles)) + 1;
     if (!fb.part || fb.part_cap < 2 * nparts) {
@@ -269,7 +271,10 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
     mark(ctx, 0, s);
     CK(cudaMemsetAsync(fb.tile_cnt, 0, sizeof(uint32_t) * (size_t)n_tiles, s));
     CK(cudaMemsetAsync(fb.tile_cur, 0, sizeof(uint32_t) * (size_t)n_tiles, s));
-    CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * 16, s));
+    // scal[5] (device error bits) is kept across frames so that errors of the
+    // last passes of a frame are reported by the next call
+    CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * 5, s));
+    CK(cudaMemsetAsync(fb.scal + 6, 0, sizeof(uint64_t) * 10, s));
     CK(launch_vertex_setup(*m, ctx->cam, fb, s));
     mark(ctx, 1, s);
     CK(launch_face_setup(*m, ctx->cam, ctx->style.lod, ctx->style.delta, fb, tiles_x, tiles_y, s));
@@ -294,8 +299,13 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
     CK(scan_u32_to_u64(fb.cnt, fb.off, n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
     mark(ctx, 7, s);
     launches += 6;
-    CK(cudaMemcpyAsync(fb.h_scal, fb.scal, 3 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(fb.h_scal, fb.scal, 6 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (fb.h_scal[5] != 0) {  // a bounded device wait ran out, or an exactness check failed
+        const uint64_t bits = fb.h_scal[5];
+        CK(cudaMemsetAsync(fb.scal + 5, 0, sizeof(uint64_t), s));
+        return (bits & 6ull) ? HEXFC_ERR_TIMEOUT : HEXFC_ERR_CUDA;
+    }
     const uint64_t total = fb.h_scal[0];
     const uint32_t max_list = (uint32_t)fb.h_scal[1];
     const uint32_t n_long = (uint32_t)fb.h_scal[2];
@@ -325,7 +335,7 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
     CK(launch_composite(fb, sp, tiles_x, tiles_y, W, H, out, n_long, s));
     mark(ctx, 10, s);
     ctx->ev_pending[ctx->ev_cur] = ctx->timing;
-    launches += 2 + (n_long > 0 ? 1 : 0);
+    launches += 3 + (n_long > 0 ? 1 : 0);
     ctx->last.kernel_launches = launches;
     if (stats) stats->kernel_launches = launches;
     ctx->have_frame = true;
@@ -738,11 +748,13 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fb.cnt = a.take<uint32_t>((size_t)n_pix + 1);
     fb.off = a.take<uint64_t>((size_t)n_pix + 1);
     fb.long_q = a.take<uint32_t>((size_t)n_pix + 1);
+    fb.fix_q = a.take<uint32_t>((size_t)n_pix + 1);
     fb.part = a.take<uint64_t>(2 * (size_t)nparts);
     fb.part_max = a.take<uint32_t>(2 * (size_t)nparts);
     fb.scal = a.take<uint64_t>(16);
     if (!fb.vproj || !fb.ved || !fb.fx || !fb.fy || !fb.fz || !fb.fed || !fb.fflags || !fb.tile_cnt ||
-        !fb.tile_off || !fb.tile_cur || !fb.cnt || !fb.off || !fb.long_q || !fb.part || !fb.part_max || !fb.scal)
+        !fb.tile_off || !fb.tile_cur || !fb.cnt || !fb.off || !fb.long_q || !fb.fix_q || !fb.part || !fb.part_max ||
+        !fb.scal)
         return HEXFC_ERR_OVERFLOW;
     // the array keeps the previous call's contents: clear what must start at zero
     CK(cudaMemsetAsync(fb.tile_cnt, 0, sizeof(uint32_t) * (size_t)n_tiles, s));
@@ -771,14 +783,15 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     CK(launch_bin_sort(fb, tiles_x, tiles_y, s));
     CK(launch_count(fb, tiles_x, tiles_y, W, H, s));
     CK(scan_u32_to_u64(fb.cnt, fb.off, n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
-    CK(cudaMemcpyAsync(h, fb.scal, 3 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h, fb.scal, 6 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (h[5] != 0) return (h[5] & 6ull) ? HEXFC_ERR_TIMEOUT : HEXFC_ERR_CUDA;
     const uint64_t total = h[0];
     const uint32_t n_long = (uint32_t)h[2];
     fs.fragments = total;
     fs.max_list = (uint32_t)h[1];
     fs.long_lists = n_long;
-    fs.kernel_launches = 12 + (n_long > 0 ? 1u : 0u);
+    fs.kernel_launches = 14 + (n_long > 0 ? 1u : 0u);
     if (stats) *stats = fs;
     if (fs.max_list > HEXFC_MAX_LIST) return HEXFC_ERR_OVERFLOW;
     fb.key = a.take<uint64_t>((size_t)total + 2);   // the composite widens key copies to 16-byte boundaries

@@ -87,12 +87,13 @@ struct FrameBufs {
     uint32_t* part_max = nullptr;
     int64_t part_cap = 0;
     uint32_t* long_q = nullptr;     // queue of pixels with long lists
+    uint32_t* fix_q = nullptr;      // queue of pixels whose list arrived out of order
     // fragments
     uint64_t* key = nullptr;
     float4* rgba = nullptr;
     int64_t frag_cap = 0;
     // small device scalars: [0] total fragments, [1] max list, [2] long lists, [3] long queue cursor,
-    // [4] bin total, [5] error flags
+    // [4] out-of-order queue cursor, [5] error bits (kept across frames), [8..10] tile scan totals
     uint64_t* scal = nullptr;
     uint64_t* h_scal = nullptr;     // pinned mirror
 };

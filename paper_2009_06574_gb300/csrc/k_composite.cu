@@ -3,20 +3,20 @@
 // alpha-blended in visibility order; Section "GPU Implementation": per-pixel
 // fragment lists resolved by a sorting pass).
 //
-// A tile's lists are one contiguous range of the fragment buffers (pixels in
-// tile-major order). The composite streams that range through shared memory
-// with bulk asynchronous copies (cp.async.bulk, completion on an mbarrier) in
-// segments of consecutive pixels, two segments in flight, while the warps
-// resolve the pixels of the segment that has landed. The paper sorts with a
-// per-pixel priority queue; here the fill pass visits each tile's triangles in
-// depth order, so nearly every list arrives sorted: one comparison per element
-// and a vote confirm it, and only an out-of-order list is sorted, by a
-// warp-wide bitonic network over (key, index) in registers. Lists longer
-// than 256 (up to HEXFC_MAX_LIST) are sorted by a whole block. Keys are unique
-// within a pixel (depth, face, triangle), so the order is unique. Compositing
-// is an ordered reduction of (colour, transmittance) pairs,
-// (C1,T1)(C2,T2) = (C1 + T1 C2, T1 T2), equal to the sequential blend.
+// The paper sorts with a per-pixel priority queue. Here the fill pass visits
+// each tile's triangles in depth order, so every list arrives sorted or nearly
+// sorted. One thread per pixel streams its list front to back through a small
+// sorted window in registers (the lists of a warp's 32 pixels are one
+// contiguous range, tile-major order) and checks the order of what it blends;
+// a list the window cannot sort is resolved by the whole warp: a bitonic
+// network over (key, index) in registers. Lists longer than 256 (up to
+// HEXFC_MAX_LIST) are sorted by a whole block in shared memory. Keys are
+// unique within a pixel (depth, face, triangle), so the order is unique.
+// The warp-wide resolve composites as an ordered reduction of (colour,
+// transmittance) pairs, (C1,T1)(C2,T2) = (C1 + T1 C2, T1 T2), equal to the
+// sequential front-to-back blend.
 #include "hexfc_internal.cuh"
+#include "pipeline.cuh"
 
 namespace hexfc {
 namespace {
@@ -24,9 +24,6 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpList = kWarpSortMax;   // longest list a warp resolves
 constexpr int kWarps = kTilePix / 32;     // warps per composite block
-constexpr int kSegCap = 1024;             // segment target (fragments); a segment spans < kSegCap + kWarpList
-constexpr int kStageFrags = kSegCap + kWarpList + 2;   // +2: key copies are widened to 16-byte boundaries
-constexpr uint32_t kWaitLimit = 1u << 26; // bounded mbarrier waits
 
 struct CT { float r, g, b, t; };  // premultiplied colour and transmittance
 
@@ -51,8 +48,6 @@ __device__ __forceinline__ CT warp_ordered_reduce(CT c, int lane)
 
 // ---------------------------------------------------------------- async copies
 
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
@@ -63,42 +58,6 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-// Waits for phase `parity` of the barrier to complete; false if the bound
-// (about half a second of SM clock, or kWaitLimit polls) ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
-{
-    const unsigned a = smem_addr(bar);
-    const long long t0 = clock64();
-    for (uint32_t it = 0; it < kWaitLimit && clock64() - t0 < (1ll << 30); ++it) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-__device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, unsigned bytes, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-            smem_addr(smem)),
-        "l"(gmem), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------- resolve
 
@@ -223,18 +182,9 @@ __device__ __forceinline__ void tile_pixel(int64_t q, int tiles_x, int& x, int& 
     y = (int)(tile / tiles_x) * kTile + local / kTile;
 }
 
-// Shared memory of the composite block.
-struct StageBuf {
-    uint64_t key[kStageFrags];
-    float4 rgba[kStageFrags];
-};
-struct WarpList {  // fallback staging of one list per warp
+struct WarpList {  // staging of one list per warp (debug gather)
     uint64_t key[kWarpList];
     float4 rgba[kWarpList];
-};
-union CompositeSmem {
-    StageBuf stage[2];
-    WarpList warp[kWarps];
 };
 
 __device__ __forceinline__ float4 finish(CT c, float bg0, float bg1, float bg2)
@@ -242,125 +192,110 @@ __device__ __forceinline__ float4 finish(CT c, float bg0, float bg1, float bg2)
     return make_float4(c.r + c.t * bg0, c.g + c.t * bg1, c.b + c.t * bg2, 1.f - c.t);
 }
 
-// One block per tile. Segment k of the tile holds the pixels whose lists end
-// in ((k-1) kSegCap, k kSegCap] fragments from the tile's start; it is copied
-// whole into stage k % 2 and resolved by the 8 warps, pixel by pixel.
-__global__ void __launch_bounds__(kTilePix) k_composite(const uint32_t* __restrict__ cnt,
-                                                        const uint64_t* __restrict__ off,
-                                                        const uint64_t* __restrict__ key,
-                                                        const float4* __restrict__ rgba, int tiles_x, int W, int H,
-                                                        float bg0, float bg1, float bg2, float4* __restrict__ out,
-                                                        uint32_t* __restrict__ long_q,
-                                                        unsigned long long* __restrict__ long_cursor,
-                                                        unsigned long long* __restrict__ err)
-{
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    CompositeSmem& sm = *reinterpret_cast<CompositeSmem*>(smem_raw);
-    __shared__ uint32_t s_cnt[kTilePix];
-    __shared__ uint64_t s_off[kTilePix + 1];
-    __shared__ uint16_t s_first[kTilePix * kWarpList / kSegCap + 2];   // first pixel of each segment (+ end)
-    __shared__ __align__(8) uint64_t s_bar[2];
-    const int tile = blockIdx.x;
-    const int64_t q0 = (int64_t)tile * kTilePix;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
-    const uint32_t n_me = cnt[q0 + threadIdx.x];
-    s_cnt[threadIdx.x] = n_me;
-    s_off[threadIdx.x] = off[q0 + threadIdx.x];
-    if (threadIdx.x == 0) s_off[kTilePix] = off[q0 + kTilePix];
-    const int has_long = __syncthreads_or(n_me > (uint32_t)kWarpList);
+// One thread per pixel (tile-major order, so a warp's 32 lists are one
+// contiguous range): the lane streams its list through a sorted window of
+// kWin (key, colour) pairs in registers and blends the smallest pair each time
+// the window overflows, so a list whose elements sit at most kWin - 1 places
+// from their sorted position comes out sorted. The blend checks that the keys
+// it consumes increase; a list that breaks that is queued for the warp-wide
+// resolve of k_composite_fix, and lists longer than 256 for the block-wide
+// sort of k_composite_long.
+constexpr int kWin = 4;
 
-    if (has_long) {
-        // rare: a list longer than 256 in this tile; warp by warp, one list at a time
-        for (int p = warp; p < kTilePix; p += kWarps) {
-            const uint32_t n = s_cnt[p];
-            const int x = px0 + (p & (kTile - 1)), y = py0 + p / kTile;
-            if (n > (uint32_t)kWarpList) {
-                if (lane == 0) long_q[atomicAdd(long_cursor, 1ull)] = (uint32_t)(q0 + p);
-                continue;
-            }
-            WarpList& b = sm.warp[warp];
-            for (uint32_t i = lane; i < n; i += 32) {
-                cp_async8(&b.key[i], key + s_off[p] + i);
-                cp_async16(&b.rgba[i], rgba + s_off[p] + i);
-            }
-            cp_async_commit();
-            cp_async_wait_all();
-            __syncwarp();
-            CT c = warp_resolve(b.key, b.rgba, n, lane, nullptr, nullptr);
-            if (lane == 0 && x < W && y < H) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
-            __syncwarp();
-        }
+struct KC {
+    uint64_t k;
+    float4 c;
+};
+
+__device__ __forceinline__ void kc_sort2(KC& a, KC& b)  // (a, b) -> (min, max)
+{
+    const bool sw = b.k < a.k;
+    const KC lo = sw ? b : a, hi = sw ? a : b;
+    a = lo;
+    b = hi;
+}
+
+__device__ __forceinline__ void blend_checked(CT& c, uint64_t& last, bool& ok, const KC& e)
+{
+    ok = ok && e.k > last;
+    last = e.k;
+    c = ct_over(c, CT{e.c.x, e.c.y, e.c.z, 1.f - e.c.w});
+}
+
+__global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ cnt,
+                                                   const uint64_t* __restrict__ off,
+                                                   const uint64_t* __restrict__ key,
+                                                   const float4* __restrict__ rgba, int64_t n_pix, int tiles_x,
+                                                   int W, int H, float bg0, float bg1, float bg2,
+                                                   float4* __restrict__ out, uint32_t* __restrict__ long_q,
+                                                   unsigned long long* __restrict__ long_cursor,
+                                                   uint32_t* __restrict__ fix_q,
+                                                   unsigned long long* __restrict__ fix_cursor)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_pix) return;
+    int x, y;
+    tile_pixel(q, tiles_x, x, y);
+    if (x >= W || y >= H) return;
+    const uint32_t n = cnt[q];
+    if (n > (uint32_t)kWarpList) {
+        long_q[atomicAdd(long_cursor, 1ull)] = (uint32_t)q;
         return;
     }
+    const uint64_t* kp = key + off[q];
+    const float4* rp = rgba + off[q];
+    CT c{0.f, 0.f, 0.f, 1.f};
+    bool ok = true;
+    uint64_t last = 0;   // keys are > 0 unless depth and face id are both 0, which the check then flags
+    // window w[0] <= w[1] <= w[2] <= w[3], filled from the first kWin elements
+    const uint64_t kPad = ~0ull;
+    KC w0{kPad, {}}, w1{kPad, {}}, w2{kPad, {}}, w3{kPad, {}};
+    const uint32_t pre = n < (uint32_t)kWin ? n : (uint32_t)kWin;
+    if (pre > 0) w0 = KC{kp[0], rp[0]};
+    if (pre > 1) w1 = KC{kp[1], rp[1]};
+    if (pre > 2) w2 = KC{kp[2], rp[2]};
+    if (pre > 3) w3 = KC{kp[3], rp[3]};
+    kc_sort2(w0, w1); kc_sort2(w2, w3); kc_sort2(w0, w2); kc_sort2(w1, w3); kc_sort2(w1, w2);
+    for (uint32_t i = kWin; i < n; ++i) {
+        KC e{kp[i], rp[i]};
+        if (e.k < w0.k) {          // smaller than the whole window: blend it at once
+            blend_checked(c, last, ok, e);
+        } else {                   // blend the window's minimum, insert e
+            blend_checked(c, last, ok, w0);
+            w0 = w1; w1 = w2; w2 = w3; w3 = e;
+            kc_sort2(w2, w3);
+            kc_sort2(w1, w2);
+            kc_sort2(w0, w1);
+        }
+    }
+    if (pre > 0) blend_checked(c, last, ok, w0);
+    if (pre > 1) blend_checked(c, last, ok, w1);
+    if (pre > 2) blend_checked(c, last, ok, w2);
+    if (pre > 3) blend_checked(c, last, ok, w3);
+    if (ok) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
+    else fix_q[atomicAdd(fix_cursor, 1ull)] = (uint32_t)q;
+}
 
-    // segments: pixel p belongs to segment (rel_end(p) - 1) / kSegCap
-    const uint64_t base = s_off[0];
-    const uint64_t total = s_off[kTilePix] - base;
-    const uint32_t n_seg = total == 0 ? 1u : (uint32_t)((total - 1) / kSegCap) + 1u;
-    {
-        const int p = threadIdx.x;
-        const uint64_t re = s_off[p + 1] - base;
-        const uint32_t sg = re > 0 ? (uint32_t)((re - 1) / kSegCap) : 0u;
-        uint32_t sp = 0;
-        if (p > 0) {
-            const uint64_t rp = s_off[p] - base;
-            sp = rp > 0 ? (uint32_t)((rp - 1) / kSegCap) : 0u;
-        }
-        if (p == 0) s_first[0] = 0;
-        else if (sg != sp) s_first[sg] = (uint16_t)p;
-        if (p == 0) s_first[n_seg] = kTilePix;
-        if (p == 0) {
-            mbar_init(&s_bar[0], 1);
-            mbar_init(&s_bar[1], 1);
-            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        }
+// Out-of-order lists (n <= 256): one warp each, sorted in registers.
+__global__ void __launch_bounds__(256) k_composite_fix(const uint32_t* __restrict__ cnt,
+                                                       const uint64_t* __restrict__ off,
+                                                       const uint64_t* __restrict__ key,
+                                                       const float4* __restrict__ rgba, int tiles_x, int W,
+                                                       float bg0, float bg1, float bg2, float4* __restrict__ out,
+                                                       const uint32_t* __restrict__ fix_q,
+                                                       const unsigned long long* __restrict__ fix_cursor)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t n_fix = *fix_cursor;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < n_fix; w += warps) {
+        const uint32_t q = fix_q[w];
+        int x, y;
+        tile_pixel(q, tiles_x, x, y);
+        const uint64_t b = off[q];
+        CT c = warp_resolve(key + b, rgba + b, cnt[q], lane, nullptr, nullptr);
+        if (lane == 0) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
     }
-    __syncthreads();
-
-    // producer: thread 0 copies segment k into stage k % 2
-    auto issue = [&](uint32_t k) {
-        const uint32_t p_a = s_first[k], p_b = s_first[k + 1];
-        const uint64_t f0 = s_off[p_a], f1 = s_off[p_b];
-        StageBuf& st = sm.stage[k & 1];
-        if (f1 == f0) {  // nothing to copy: complete the phase by a plain arrive
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(&s_bar[k & 1])) : "memory");
-            return;
-        }
-        const uint64_t k0 = f0 & ~1ull, k1 = (f1 + 1) & ~1ull;   // 16-byte aligned key range
-        const unsigned kb = (unsigned)((k1 - k0) * sizeof(uint64_t));
-        const unsigned rb = (unsigned)((f1 - f0) * sizeof(float4));
-        mbar_expect_tx(&s_bar[k & 1], kb + rb);
-        bulk_g2s(st.key, key + k0, kb, &s_bar[k & 1]);
-        bulk_g2s(st.rgba, rgba + f0, rb, &s_bar[k & 1]);
-    };
-    if (threadIdx.x == 0) {
-        issue(0);
-        if (n_seg > 1) issue(1);
-    }
-    bool timed_out = false;
-    for (uint32_t k = 0; k < n_seg; ++k) {
-        const uint32_t sidx = k & 1;
-        if (!mbar_wait(&s_bar[sidx], (k >> 1) & 1)) timed_out = true;
-        StageBuf& st = sm.stage[sidx];
-        const uint32_t p_a = s_first[k], p_b = s_first[k + 1];
-        const uint64_t kbase = s_off[p_a] & ~1ull, rbase = s_off[p_a];
-        for (uint32_t p = p_a + warp; p < p_b; p += kWarps) {
-            const uint32_t n = s_cnt[p];
-            const int x = px0 + (int)(p & (kTile - 1)), y = py0 + (int)(p / kTile);
-            CT c{0.f, 0.f, 0.f, 1.f};
-            if (n > 0 && !timed_out)
-                c = warp_resolve(st.key + (s_off[p] - kbase), st.rgba + (s_off[p] - rbase), n, lane, nullptr,
-                                 nullptr);
-            if (lane == 0 && x < W && y < H) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
-        }
-        __syncthreads();  // stage sidx is free again
-        if (threadIdx.x == 0 && k + 2 < n_seg) {
-            fence_proxy_async();  // order the warps' shared-memory accesses before the async overwrite
-            issue(k + 2);
-        }
-    }
-    if (timed_out && threadIdx.x == 0) atomicOr(err, 2ull);
 }
 
 // ---------------------------------------------------------------- long lists
@@ -491,7 +426,7 @@ __global__ void k_debug_counts(const uint32_t* __restrict__ cnt, const int32_t* 
 }
 
 constexpr size_t kLongSmem = (size_t)HEXFC_MAX_LIST * (sizeof(uint64_t) + sizeof(uint32_t));
-constexpr size_t kCompositeSmem = sizeof(CompositeSmem);
+constexpr unsigned kFixBlocks = 4 * 152;   // persistent: warps stride over the queue of out-of-order lists
 
 }  // namespace
 
@@ -499,10 +434,14 @@ cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, 
                              uint32_t n_long, cudaStream_t s)
 {
     float4* o4 = reinterpret_cast<float4*>(out);
-    cudaFuncSetAttribute(k_composite, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCompositeSmem);
-    k_composite<<<(unsigned)(tiles_x * tiles_y), kTilePix, kCompositeSmem, s>>>(
-        fb.cnt, fb.off, fb.key, fb.rgba, tiles_x, W, H, sp.bg[0], sp.bg[1], sp.bg[2], o4, fb.long_q,
-        reinterpret_cast<unsigned long long*>(fb.scal + 3), reinterpret_cast<unsigned long long*>(fb.scal + 5));
+    const int64_t n_pix = (int64_t)tiles_x * tiles_y * kTilePix;
+    unsigned long long* long_cursor = reinterpret_cast<unsigned long long*>(fb.scal + 3);
+    unsigned long long* fix_cursor = reinterpret_cast<unsigned long long*>(fb.scal + 4);
+    k_composite<<<(unsigned)((n_pix + 255) / 256), 256, 0, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, n_pix, tiles_x, W, H,
+                                                              sp.bg[0], sp.bg[1], sp.bg[2], o4, fb.long_q,
+                                                              long_cursor, fb.fix_q, fix_cursor);
+    k_composite_fix<<<kFixBlocks, 256, 0, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, tiles_x, W, sp.bg[0], sp.bg[1],
+                                               sp.bg[2], o4, fb.fix_q, fix_cursor);
     if (n_long > 0) {
         cudaFuncSetAttribute(k_composite_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSmem);
         k_composite_long<<<n_long, 1024, kLongSmem, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, fb.long_q, tiles_x, W,

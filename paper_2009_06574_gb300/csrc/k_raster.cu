@@ -15,6 +15,7 @@
 // Section "GPU Implementation"), and the fragment shader computes focus from
 // the lens, the edge distance to the four face edges ignoring invisible ones,
 // and Eqs. 1-4 (Section "Focus+Context").
+#include "pipeline.cuh"
 #include "shade.cuh"
 
 namespace hexfc {
@@ -197,33 +198,30 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
 
 // ------------------------------------------------------------------ raster per tile
 
-// Coverage data of one staged triangle: its three edge functions at the first
-// sample of its box (clipped to the tile) and their per-pixel steps, exact.
-struct TriC {
-    int64_t e0[3];        // edge function opposite vertex k at the box origin sample
-    int32_t dx[3], dy[3]; // edge vector (b - a) of that edge, 16.8
-    uint32_t meta;        // bit k: top-left rule owns edge k
-    int16_t lx0, ly0;     // box of covered pixel centres, tile-local
-    int16_t bw, bh;       // box size, 0 when the triangle misses the tile
-    float inv_bw;
+// Coverage data of the kChunk triangles of one chunk (structure of arrays):
+// each triangle's three edge functions at the first sample of its box
+// (clipped to the tile) and the edge vectors that step them, exact.
+struct CovSoA {
+    int64_t e0[3][kChunk];          // edge function opposite vertex k at the box origin sample
+    int32_t dx[3][kChunk], dy[3][kChunk];  // edge vector (b - a) of that edge, 16.8
+    uint32_t meta[kChunk];          // bit k: top-left rule owns edge k
+    int32_t box[kChunk];            // lx0 | ly0 << 8 | bw << 16 | bh << 24 (tile-local); bw = bh = 0: misses the tile
 };
 
-__device__ __forceinline__ void empty_cov(TriC& c)
-{
-    c.lx0 = c.ly0 = 0;
-    c.bw = c.bh = 0;
-    c.inv_bw = 0.f;
-}
+__device__ __forceinline__ int box_lx0(int b) { return b & 255; }
+__device__ __forceinline__ int box_ly0(int b) { return (b >> 8) & 255; }
+__device__ __forceinline__ int box_bw(int b) { return (b >> 16) & 255; }
+__device__ __forceinline__ int box_bh(int b) { return (b >> 24) & 255; }
 
-__device__ __forceinline__ void stage_cov(int4 a, int4 b, uint32_t f2t, int W, int H, int px0, int py0, TriC& c,
-                                          TriGeom& t)
+__device__ __forceinline__ void stage_cov(int4 a, int4 b, uint32_t f2t, int W, int H, int px0, int py0, CovSoA& c,
+                                          int j, TriGeom& t)
 {
     int32_t X[4] = {a.x, a.y, a.z, a.w}, Y[4] = {b.x, b.y, b.z, b.w};
     tri_setup(X, Y, (int)(f2t & 1), W, H, t);
     int x0 = max(t.bx0, px0), x1 = min(t.bx1, px0 + kTile - 1);
     int y0 = max(t.by0, py0), y1 = min(t.by1, py0 + kTile - 1);
     if (!t.valid || x0 > x1 || y0 > y1) {
-        empty_cov(c);
+        c.box[j] = 0;
         return;
     }
     const int32_t sx = 256 * x0 + 128, sy = 256 * y0 + 128;
@@ -231,245 +229,304 @@ __device__ __forceinline__ void stage_cov(int4 a, int4 b, uint32_t f2t, int W, i
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         int ia = (k + 1) % 3, ib = (k + 2) % 3;
-        c.e0[k] = edge_fn(t.X[ia], t.Y[ia], t.X[ib], t.Y[ib], sx, sy);
-        c.dx[k] = t.X[ib] - t.X[ia];
-        c.dy[k] = t.Y[ib] - t.Y[ia];
+        c.e0[k][j] = edge_fn(t.X[ia], t.Y[ia], t.X[ib], t.Y[ib], sx, sy);
+        c.dx[k][j] = t.X[ib] - t.X[ia];
+        c.dy[k][j] = t.Y[ib] - t.Y[ia];
         meta |= (top_left(t.X[ia], t.Y[ia], t.X[ib], t.Y[ib]) ? 1u : 0u) << k;
     }
-    c.meta = meta;
-    c.lx0 = (int16_t)(x0 - px0);
-    c.ly0 = (int16_t)(y0 - py0);
-    c.bw = (int16_t)(x1 - x0 + 1);
-    c.bh = (int16_t)(y1 - y0 + 1);
-    c.inv_bw = 1.f / (float)c.bw;
+    c.meta[j] = meta;
+    c.box[j] = (x0 - px0) | ((y0 - py0) << 8) | ((x1 - x0 + 1) << 16) | ((y1 - y0 + 1) << 24);
 }
 
-// Exact coverage of the sample (rx, ry) pixels from the box origin;
-// l[k] = edge function k = weight of vertex k (they sum to the area).
-__device__ __forceinline__ bool cover_at(const TriC& c, int rx, int ry, int64_t l[3])
+// Exact coverage of the sample (rx, ry) pixels from the box origin of
+// triangle j; l[k] = edge function k = weight of vertex k (sum = the area).
+__device__ __forceinline__ bool cover_at(const CovSoA& c, int j, int rx, int ry, int64_t l[3])
 {
     const int32_t sx = rx << 8, sy = ry << 8;
+    const uint32_t meta = c.meta[j];
     bool in = true;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        int64_t e = c.e0[k] + (int64_t)c.dx[k] * sy - (int64_t)c.dy[k] * sx;
+        int64_t e = c.e0[k][j] + (int64_t)c.dx[k][j] * sy - (int64_t)c.dy[k][j] * sx;
         l[k] = e;
-        in = in && (e > 0 || (e == 0 && ((c.meta >> k) & 1u)));
+        in = in && (e > 0 || (e == 0 && ((meta >> k) & 1u)));
     }
     return in;
 }
 
-// Coverage of one chunk: a warp walks each triangle's box (clipped to the
-// tile), one sample per lane, and sets bit j of the covered pixels' masks.
-__device__ __forceinline__ void raster_chunk(const TriC* s_c, int px0, int py0, uint32_t* s_mask)
+// ------------------------------------------------------------------ tile pipelines
+//
+// k_count and k_fill run one block per tile: a producer warp stages each chunk
+// of 32 triangles of the tile's (depth-ordered) list into a ring of kRing
+// slots in shared memory, and eight consumer warps each own two rows of the
+// tile (32 pixels, one per lane). Slots are handed over with mbarriers (full:
+// the 32 producer lanes arrive; empty: the 8 consumer warps arrive), so the
+// warps drift apart by up to kRing chunks instead of meeting at a block
+// barrier for every chunk. Every wait is bounded; a wait that runs out sets an
+// error bit and ends the kernel's loops.
+
+constexpr int kRing = 4;
+constexpr int kConsumerWarps = kTilePix / 32;
+constexpr int kPipeThreads = kTilePix + 32;
+constexpr unsigned long long kErrWait = 4ull;
+
+struct CountSlot {
+    CovSoA c;
+    uint32_t wmask[kConsumerWarps];   // bit j: triangle j touches the two rows of consumer warp w
+};
+
+__device__ __forceinline__ void pipe_init(uint64_t* full, uint64_t* empty)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    (void)px0;
-    (void)py0;
-    for (int j = warp; j < kChunk; j += kTilePix / 32) {
-        const TriC& c = s_c[j];
-        const int area = (int)c.bw * (int)c.bh;
-        for (int idx = lane; idx < area; idx += 32) {
-            // exact for idx < 256, bw <= 16: the quotient is never within 1/32 of an integer
-            int ry = (int)(((float)idx + 0.5f) * c.inv_bw);
-            int rx = idx - ry * c.bw;
-            int64_t l[3];
-            if (cover_at(c, rx, ry, l)) atomicOr(s_mask + (c.ly0 + ry) * kTile + c.lx0 + rx, 1u << j);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kRing; ++s) {
+            mbar_init(&full[s], 32);
+            mbar_init(&empty[s], kConsumerWarps);
         }
+        mbar_init_fence();
     }
+    __syncthreads();
 }
 
-// Per tile: coverage of every chunk of 32 triangles as per-pixel bit masks;
-// the masks are kept for the fill pass and their bit counts are the per-pixel
-// list lengths.
-__global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__ tile_off,
-                                                    const uint32_t* __restrict__ bins,
-                                                    const int4* __restrict__ fx, const int4* __restrict__ fy,
-                                                    int tiles_x, int W, int H, uint32_t* __restrict__ cnt,
-                                                    uint32_t* __restrict__ masks)
+// Per tile: coverage of every chunk of 32 triangles as per-pixel bit masks,
+// one lane per pixel; the masks are kept for the fill pass and their bit
+// counts are the per-pixel list lengths.
+__global__ void __launch_bounds__(kPipeThreads) k_count(const uint64_t* __restrict__ tile_off,
+                                                        const uint32_t* __restrict__ bins,
+                                                        const int4* __restrict__ fx, const int4* __restrict__ fy,
+                                                        int tiles_x, int W, int H, uint32_t* __restrict__ cnt,
+                                                        uint32_t* __restrict__ masks,
+                                                        unsigned long long* __restrict__ err)
 {
-    __shared__ TriC s_c[kChunk];
-    __shared__ uint32_t s_mask[kTilePix];
+    __shared__ CountSlot s_ring[kRing];
+    __shared__ __align__(8) uint64_t s_full[kRing], s_empty[kRing];
     const int tile = blockIdx.x;
     const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
     const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
-    s_mask[threadIdx.x] = 0;
-    uint32_t n = 0;
-    // the staging warp loads chunk c+1 while the block rasterises chunk c
-    uint32_t f2t_n = kPadBin;
-    int4 a_n = make_int4(0, 0, 0, 0), b_n = a_n;
-    if (threadIdx.x < kChunk && beg < end) {
-        f2t_n = bins[beg + threadIdx.x];
-        if (f2t_n != kPadBin) { a_n = fx[f2t_n >> 1]; b_n = fy[f2t_n >> 1]; }
-    }
-    for (uint64_t base = beg; base < end; base += kChunk) {
-        if (threadIdx.x < kChunk) {
-            TriGeom t;
-            if (f2t_n != kPadBin) stage_cov(a_n, b_n, f2t_n, W, H, px0, py0, s_c[threadIdx.x], t);
-            else empty_cov(s_c[threadIdx.x]);
-            f2t_n = kPadBin;
-            if (base + kChunk < end) {
-                f2t_n = bins[base + kChunk + threadIdx.x];
-                if (f2t_n != kPadBin) { a_n = fx[f2t_n >> 1]; b_n = fy[f2t_n >> 1]; }
+    const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    pipe_init(s_full, s_empty);
+
+    if (warp == kConsumerWarps) {  // producer
+        uint32_t f2t = n_chunks > 0 ? bins[beg + lane] : kPadBin;
+        for (uint32_t c = 0; c < n_chunks; ++c) {
+            const int s = c % kRing;
+            const uint32_t f2t_next = c + 1 < n_chunks ? bins[beg + (uint64_t)(c + 1) * kChunk + lane] : kPadBin;
+            int4 a = make_int4(0, 0, 0, 0), b = a;
+            if (f2t != kPadBin) { a = fx[f2t >> 1]; b = fy[f2t >> 1]; }
+            if (!mbar_wait(&s_empty[s], ((c / kRing) & 1) ^ 1)) {
+                if (lane == 0) atomicOr(err, kErrWait);
+                break;
             }
+            CountSlot& S = s_ring[s];
+            TriGeom t;
+            if (f2t != kPadBin) stage_cov(a, b, f2t, W, H, px0, py0, S.c, lane, t);
+            else S.c.box[lane] = 0;
+            const int bx = S.c.box[lane], y0 = box_ly0(bx), bh = box_bh(bx);
+#pragma unroll
+            for (int w = 0; w < kConsumerWarps; ++w) {
+                const unsigned m = __ballot_sync(0xffffffffu, bh > 0 && y0 <= 2 * w + 1 && y0 + bh > 2 * w);
+                if (lane == 0) S.wmask[w] = m;
+            }
+            __syncwarp();
+            mbar_arrive(&s_full[s]);
+            f2t = f2t_next;
         }
-        __syncthreads();
-        raster_chunk(s_c, px0, py0, s_mask);
-        __syncthreads();
-        uint32_t mk = s_mask[threadIdx.x];
-        s_mask[threadIdx.x] = 0;
-        n += __popc(mk);
-        masks[(base / kChunk) * kTilePix + threadIdx.x] = mk;
+        return;
     }
-    cnt[(int64_t)tile * kTilePix + threadIdx.x] = n;
+    // consumers: lane = pixel (lx, ly) of rows 2*warp and 2*warp + 1
+    const int p = threadIdx.x, lx = p & (kTile - 1), ly = p / kTile;
+    uint32_t n = 0;
+    for (uint32_t c = 0; c < n_chunks; ++c) {
+        const int s = c % kRing;
+        if (!mbar_wait(&s_full[s], (c / kRing) & 1)) {
+            if (lane == 0) atomicOr(err, kErrWait);
+            break;
+        }
+        const CountSlot& S = s_ring[s];
+        uint32_t todo = S.wmask[warp], mk = 0;
+        while (todo) {
+            const int j = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int bx = S.c.box[j];
+            const int rx = lx - box_lx0(bx), ry = ly - box_ly0(bx);
+            int64_t l[3];
+            if (rx >= 0 && rx < box_bw(bx) && ry >= 0 && ry < box_bh(bx) && cover_at(S.c, j, rx, ry, l))
+                mk |= 1u << j;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_empty[s]);
+        n += __popc(mk);
+        masks[(beg / kChunk + c) * kTilePix + p] = mk;
+    }
+    cnt[(int64_t)tile * kTilePix + p] = n;
 }
 
 // ------------------------------------------------------------------ fill + shade
-
-// Exclusive scan of one value per thread of a kTilePix-thread block.
-__device__ __forceinline__ uint32_t block_scan_tile(uint32_t v, uint32_t* s_w, uint32_t& total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_w[warp] = x;
-    __syncthreads();
-    uint32_t pre = 0, tot = 0;
-#pragma unroll
-    for (int w = 0; w < kTilePix / 32; ++w) {
-        uint32_t sw = s_w[w];
-        pre += w < warp ? sw : 0u;
-        tot += sw;
-    }
-    total = tot;
-    return pre + x - v;
-}
 
 __device__ __forceinline__ void stage_shade(const int4 a, const int4 b, const uint4* __restrict__ fz,
                                             const float4* __restrict__ fed, const uint32_t* __restrict__ fflags,
                                             const float4* __restrict__ fimp, const float4* __restrict__ fpx,
                                             const float4* __restrict__ fpy, const float4* __restrict__ fpz,
-                                            uint32_t f2t, const TriGeom& t, TriShade& S)
+                                            uint32_t f2t, const TriGeom& t, ShadeSoA& S, int j)
 {
-    uint32_t f = f2t >> 1;
-    S.FX[0] = a.x; S.FX[1] = a.y; S.FX[2] = a.z; S.FX[3] = a.w;
-    S.FY[0] = b.x; S.FY[1] = b.y; S.FY[2] = b.z; S.FY[3] = b.w;
+    const uint32_t f = f2t >> 1;
+    const int32_t FX[4] = {a.x, a.y, a.z, a.w}, FY[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        int k1 = (k + 1) & 3;
-        int32_t ex = S.FX[k1] - S.FX[k], ey = S.FY[k1] - S.FY[k];
-        S.ex[k] = ex;
-        S.ey[k] = ey;
-        int64_t l2 = (int64_t)ex * ex + (int64_t)ey * ey;
-        S.len2[k] = l2;
-        S.inv_len[k] = l2 > 0 ? rsqrtf((float)l2) : 0.f;
+        const int k1 = (k + 1) & 3;
+        S.FX[k][j] = FX[k];
+        S.FY[k][j] = FY[k];
+        const int32_t ex = FX[k1] - FX[k], ey = FY[k1] - FY[k];
+        S.ex[k][j] = ex;
+        S.ey[k][j] = ey;
+        const int64_t l2 = (int64_t)ex * ex + (int64_t)ey * ey;
+        S.len2[k][j] = l2;
+        S.inv_len[k][j] = l2 > 0 ? rsqrtf((float)l2) : 0.f;
     }
-    uint4 z4 = fz[f];
-    float4 e4 = fed[f], i4 = fimp[f], x4 = fpx[f], y4 = fpy[f], w4 = fpz[f];
-    uint32_t zz[4] = {z4.x, z4.y, z4.z, z4.w};
-    float ee[4] = {e4.x, e4.y, e4.z, e4.w}, ii[4] = {i4.x, i4.y, i4.z, i4.w};
-    float xx[4] = {x4.x, x4.y, x4.z, x4.w}, yy[4] = {y4.x, y4.y, y4.z, y4.w}, ww[4] = {w4.x, w4.y, w4.z, w4.w};
+    const uint4 z4 = fz[f];
+    const float4 e4 = fed[f], i4 = fimp[f], x4 = fpx[f], y4 = fpy[f], w4 = fpz[f];
+    const uint32_t zz[4] = {z4.x, z4.y, z4.z, z4.w};
+    const float ee[4] = {e4.x, e4.y, e4.z, e4.w}, ii[4] = {i4.x, i4.y, i4.z, i4.w};
+    const float xx[4] = {x4.x, x4.y, x4.z, x4.w}, yy[4] = {y4.x, y4.y, y4.z, y4.w};
+    const float ww[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        int c = t.vi[k];
+        const int c = t.vi[k];
         // select corner c without dynamic register indexing
-        S.z[k] = c == 0 ? zz[0] : c == 1 ? zz[1] : c == 2 ? zz[2] : zz[3];
-        float ed = c == 0 ? ee[0] : c == 1 ? ee[1] : c == 2 ? ee[2] : ee[3];
-        S.ed[k] = ed;
-        S.inv_ed[k] = 1.f / ed;
-        S.imp[k] = c == 0 ? ii[0] : c == 1 ? ii[1] : c == 2 ? ii[2] : ii[3];
-        S.P[k][0] = c == 0 ? xx[0] : c == 1 ? xx[1] : c == 2 ? xx[2] : xx[3];
-        S.P[k][1] = c == 0 ? yy[0] : c == 1 ? yy[1] : c == 2 ? yy[2] : yy[3];
-        S.P[k][2] = c == 0 ? ww[0] : c == 1 ? ww[1] : c == 2 ? ww[2] : ww[3];
+        S.z[k][j] = c == 0 ? zz[0] : c == 1 ? zz[1] : c == 2 ? zz[2] : zz[3];
+        S.inv_ed[k][j] = 1.f / (c == 0 ? ee[0] : c == 1 ? ee[1] : c == 2 ? ee[2] : ee[3]);
+        S.imp[k][j] = c == 0 ? ii[0] : c == 1 ? ii[1] : c == 2 ? ii[2] : ii[3];
+        S.P[k][0][j] = c == 0 ? xx[0] : c == 1 ? xx[1] : c == 2 ? xx[2] : xx[3];
+        S.P[k][1][j] = c == 0 ? yy[0] : c == 1 ? yy[1] : c == 2 ? yy[2] : yy[3];
+        S.P[k][2][j] = c == 0 ? ww[0] : c == 1 ? ww[1] : c == 2 ? ww[2] : ww[3];
     }
-    S.area = t.area;
-    S.inv_area = 1.f / (float)t.area;
-    S.f2t = f2t;
-    S.masks = fflags[f] & 0xFFu;
+    S.area[j] = t.area;
+    S.inv_area[j] = 1.f / (float)t.area;
+    S.f2t[j] = f2t;
+    S.masks[j] = fflags[f] & 0xFFu;
 }
 
+struct FillSlot {
+    CovSoA c;
+    ShadeSoA sh;
+};
+
 // Per tile: the coverage masks of the count pass give, chunk by chunk, each
-// pixel's covered triangles; the covered samples are compacted into a queue
+// lane's covered triangles; a warp compacts its covered samples into a queue
 // (pixel-major, in list order) so that the shading runs on every lane, and
 // each fragment is written at its pixel's offset plus its rank in the pixel's
 // list (the rank the count pass sized).
-__global__ void __launch_bounds__(kTilePix) k_fill(const uint64_t* __restrict__ tile_off,
-                                                   const uint32_t* __restrict__ bins,
-                                                   const uint32_t* __restrict__ masks,
-                                                   const int4* __restrict__ fx, const int4* __restrict__ fy,
-                                                   const uint4* __restrict__ fz, const float4* __restrict__ fed,
-                                                   const uint32_t* __restrict__ fflags,
-                                                   const float4* __restrict__ fimp, const float4* __restrict__ fpx,
-                                                   const float4* __restrict__ fpy, const float4* __restrict__ fpz,
-                                                   int tiles_x, int W, int H, ShadeParams sp,
-                                                   const uint64_t* __restrict__ off, uint64_t* __restrict__ key,
-                                                   float4* __restrict__ rgba, uint64_t* __restrict__ err)
+__global__ void __launch_bounds__(kPipeThreads) k_fill(const uint64_t* __restrict__ tile_off,
+                                                       const uint32_t* __restrict__ bins,
+                                                       const uint32_t* __restrict__ masks,
+                                                       const int4* __restrict__ fx, const int4* __restrict__ fy,
+                                                       const uint4* __restrict__ fz, const float4* __restrict__ fed,
+                                                       const uint32_t* __restrict__ fflags,
+                                                       const float4* __restrict__ fimp, const float4* __restrict__ fpx,
+                                                       const float4* __restrict__ fpy, const float4* __restrict__ fpz,
+                                                       int tiles_x, int W, int H, ShadeParams sp,
+                                                       const uint64_t* __restrict__ off, uint64_t* __restrict__ key,
+                                                       float4* __restrict__ rgba,
+                                                       unsigned long long* __restrict__ err)
 {
-    __shared__ TriC s_c[kChunk];
-    __shared__ TriShade s_sh[kChunk];
-    __shared__ uint32_t s_q[kChunk * kTilePix];
+    extern __shared__ __align__(16) unsigned char fill_smem[];
+    FillSlot* s_ring = reinterpret_cast<FillSlot*>(fill_smem);                              // [kRing]
+    uint32_t* s_qall = reinterpret_cast<uint32_t*>(fill_smem + kRing * sizeof(FillSlot));  // [warps][kChunk*32]
     __shared__ uint64_t s_base[kTilePix];
     __shared__ uint32_t s_len[kTilePix];
-    __shared__ uint32_t s_w[kTilePix / 32];
+    __shared__ __align__(8) uint64_t s_full[kRing], s_empty[kRing];
     const int tile = blockIdx.x;
     const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
     const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
-    {
+    const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < kTilePix) {
         const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;
-        uint64_t o0 = off[q];
+        const uint64_t o0 = off[q];
         s_base[threadIdx.x] = o0;
         s_len[threadIdx.x] = (uint32_t)(off[q + 1] - o0);
     }
-    uint32_t k_run = 0;
-    bool bad = false;
-    for (uint64_t base = beg; base < end; base += kChunk) {
-        uint32_t mk = masks[(base / kChunk) * kTilePix + threadIdx.x];
-        if (threadIdx.x < kChunk) {
-            uint32_t f2t = bins[base + threadIdx.x];
+    pipe_init(s_full, s_empty);
+
+    if (warp == kConsumerWarps) {  // producer
+        uint32_t f2t = n_chunks > 0 ? bins[beg + lane] : kPadBin;
+        for (uint32_t c = 0; c < n_chunks; ++c) {
+            const int s = c % kRing;
+            const uint32_t f2t_next = c + 1 < n_chunks ? bins[beg + (uint64_t)(c + 1) * kChunk + lane] : kPadBin;
+            int4 a = make_int4(0, 0, 0, 0), b = a;
+            if (f2t != kPadBin) { a = fx[f2t >> 1]; b = fy[f2t >> 1]; }
+            if (!mbar_wait(&s_empty[s], ((c / kRing) & 1) ^ 1)) {
+                if (lane == 0) atomicOr(err, kErrWait);
+                break;
+            }
+            FillSlot& S = s_ring[s];
             if (f2t != kPadBin) {
                 TriGeom t;
-                int4 a = fx[f2t >> 1], b = fy[f2t >> 1];
-                stage_cov(a, b, f2t, W, H, px0, py0, s_c[threadIdx.x], t);
-                if (s_c[threadIdx.x].bw > 0)
-                    stage_shade(a, b, fz, fed, fflags, fimp, fpx, fpy, fpz, f2t, t, s_sh[threadIdx.x]);
+                stage_cov(a, b, f2t, W, H, px0, py0, S.c, lane, t);
+                if (S.c.box[lane] != 0) stage_shade(a, b, fz, fed, fflags, fimp, fpx, fpy, fpz, f2t, t, S.sh, lane);
             } else {
-                empty_cov(s_c[threadIdx.x]);
+                S.c.box[lane] = 0;
             }
+            mbar_arrive(&s_full[s]);
+            f2t = f2t_next;
         }
-        uint32_t total;
-        uint32_t r = block_scan_tile(__popc(mk), s_w, total);   // contains a block barrier
+        return;
+    }
+    // consumers: lane = pixel of rows 2*warp and 2*warp + 1
+    const int p = threadIdx.x;
+    uint32_t* q = s_qall + warp * (kChunk * 32);
+    uint32_t k_run = 0;
+    bool bad = false;
+    uint32_t mk_next = n_chunks > 0 ? masks[(beg / kChunk) * kTilePix + p] : 0u;
+    for (uint32_t c = 0; c < n_chunks; ++c) {
+        const int s = c % kRing;
+        uint32_t mk = mk_next;
+        if (c + 1 < n_chunks) mk_next = masks[(beg / kChunk + c + 1) * kTilePix + p];
+        if (!mbar_wait(&s_full[s], (c / kRing) & 1)) {
+            if (lane == 0) atomicOr(err, kErrWait);
+            break;
+        }
+        // warp-wide exclusive scan of the hit counts
+        const uint32_t h = __popc(mk);
+        uint32_t incl = h;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t r = incl - h;
         while (mk) {
-            uint32_t j = __ffs(mk) - 1;
+            const uint32_t j = __ffs(mk) - 1;
             mk &= mk - 1;
-            s_q[r++] = j | ((uint32_t)threadIdx.x << 5) | (k_run++ << 13);
+            q[r++] = j | ((uint32_t)lane << 5) | (k_run++ << 10);
         }
-        __syncthreads();
-        for (uint32_t e = threadIdx.x; e < total; e += kTilePix) {
-            const uint32_t qe = s_q[e];
-            const uint32_t j = qe & 31u, p = (qe >> 5) & 255u, kk = qe >> 13;
-            const int lx = (int)(p & (kTile - 1)), ly = (int)(p / kTile);
+        __syncwarp();
+        const FillSlot& S = s_ring[s];
+        for (uint32_t e = lane; e < total; e += 32) {
+            const uint32_t qe = q[e];
+            const int j = (int)(qe & 31u);
+            const uint32_t pl = warp * 32 + ((qe >> 5) & 31u), kk = qe >> 10;
+            const int lx = (int)(pl & (kTile - 1)), ly = (int)(pl / kTile);
             const int px = px0 + lx, py = py0 + ly;
-            const TriC& c = s_c[j];
+            const int bx = S.c.box[j];
             int64_t l[3];
-            (void)cover_at(c, lx - c.lx0, ly - c.ly0, l);
-            const TriShade& S = s_sh[j];
-            uint32_t z = sample_depth_fast(S.z[0], S.z[1], S.z[2], l[1], l[2], S.area, S.inv_area, bad);
-            float4 col = shade_fragment(S, l, px, py, 256 * px + 128, 256 * py + 128, sp);
-            if (kk < s_len[p]) {  // the count pass sized this list; never write past it
-                const uint64_t o = s_base[p] + kk;
-                key[o] = ((uint64_t)z << 32) | (uint64_t)S.f2t;
+            (void)cover_at(S.c, j, lx - box_lx0(bx), ly - box_ly0(bx), l);
+            const uint32_t z = sample_depth_fast(S.sh.z[0][j], S.sh.z[1][j], S.sh.z[2][j], l[1], l[2], S.sh.area[j],
+                                                 S.sh.inv_area[j], bad);
+            const float4 col = shade_fragment(S.sh, j, l, px, py, 256 * px + 128, 256 * py + 128, sp);
+            if (kk < s_len[pl]) {  // the count pass sized this list; never write past it
+                const uint64_t o = s_base[pl] + kk;
+                key[o] = ((uint64_t)z << 32) | (uint64_t)S.sh.f2t[j];
                 rgba[o] = col;
             } else {
                 bad = true;
             }
         }
-        __syncthreads();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_empty[s]);
     }
-    if (bad) atomicOr(reinterpret_cast<unsigned long long*>(err), 1ull);
+    if (bad) atomicOr(err, 1ull);
 }
 
 }  // namespace
@@ -506,17 +563,20 @@ cudaError_t launch_bin_sort(FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_
 
 cudaError_t launch_count(FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, cudaStream_t s)
 {
-    k_count<<<(unsigned)(tiles_x * tiles_y), kTilePix, 0, s>>>(fb.tile_off, fb.bins, fb.fx, fb.fy, tiles_x, W, H,
-                                                                fb.cnt, fb.masks);
+    k_count<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, 0, s>>>(
+        fb.tile_off, fb.bins, fb.fx, fb.fy, tiles_x, W, H, fb.cnt, fb.masks,
+        reinterpret_cast<unsigned long long*>(fb.scal + 5));
     return cudaGetLastError();
 }
 
 cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W,
                         int H, cudaStream_t s)
 {
-    k_fill<<<(unsigned)(tiles_x * tiles_y), kTilePix, 0, s>>>(fb.tile_off, fb.bins, fb.masks, fb.fx, fb.fy, fb.fz,
-                                                               fb.fed, fb.fflags, m.fimp, m.fpx, m.fpy, m.fpz, tiles_x,
-                                                               W, H, sp, fb.off, fb.key, fb.rgba, fb.scal + 5);
+    const size_t smem = kRing * sizeof(FillSlot) + (size_t)kConsumerWarps * kChunk * 32 * sizeof(uint32_t);
+    cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_fill<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, smem, s>>>(
+        fb.tile_off, fb.bins, fb.masks, fb.fx, fb.fy, fb.fz, fb.fed, fb.fflags, m.fimp, m.fpx, m.fpy, m.fpz, tiles_x,
+        W, H, sp, fb.off, fb.key, fb.rgba, reinterpret_cast<unsigned long long*>(fb.scal + 5));
     return cudaGetLastError();
 }
 

@@ -5,63 +5,69 @@
 
 namespace hexfc {
 
-// Per-triangle shading inputs staged in shared memory (wound vertex order).
-struct TriShade {
-    int32_t FX[4], FY[4];   // face corners (16.8)
-    int32_t ex[4], ey[4];   // face edge vectors corner k -> k+1 (16.8)
-    int64_t len2[4];        // their squared lengths, exact
-    float inv_len[4];       // 1 / length
-    uint32_t z[3];          // window depth of the triangle's vertices
-    float ed[3], inv_ed[3]; // eye depth and its reciprocal
-    float imp[3], P[3][3];  // vertex importance and world position
-    int64_t area;           // twice the area (16.8 squared)
-    float inv_area;
-    uint32_t f2t;
-    uint32_t masks;         // bits 0-3 focus-visible, 4-7 context-visible face edges
+// Shading inputs of the kChunk triangles of one chunk, structure of arrays
+// (element j = triangle j, vertices in wound order), so that lanes reading
+// different triangles touch different shared-memory banks.
+struct ShadeSoA {
+    int32_t FX[4][kChunk], FY[4][kChunk];   // face corners (16.8)
+    int32_t ex[4][kChunk], ey[4][kChunk];   // face edge vectors corner k -> k+1 (16.8)
+    int64_t len2[4][kChunk];                // their squared lengths, exact
+    float inv_len[4][kChunk];               // 1 / length
+    uint32_t z[3][kChunk];                  // window depth of the triangle's vertices
+    float inv_ed[3][kChunk];                // 1 / eye depth
+    float imp[3][kChunk];                   // vertex importance
+    float P[3][3][kChunk];                  // world position P[vertex][axis]
+    int64_t area[kChunk];                   // twice the area (16.8 squared)
+    float inv_area[kChunk];
+    uint32_t f2t[kChunk];
+    uint32_t masks[kChunk];                 // bits 0-3 focus-visible, 4-7 context-visible face edges
 };
 
 // Squared distance (in 1/256-pixel units squared) from sample (sx, sy) to face
-// edge k of S: exact integer tests pick the closest feature (an end point or
-// the segment's interior), one float rounding for the value.
-__device__ __forceinline__ float seg_dist2(const TriShade& S, int k, int32_t sx, int32_t sy)
+// edge k of triangle j: exact integer tests pick the closest feature (an end
+// point or the segment's interior), one float rounding for the value.
+__device__ __forceinline__ float seg_dist2(const ShadeSoA& S, int j, int k, int32_t sx, int32_t sy)
 {
-    const int32_t px = sx - S.FX[k], py = sy - S.FY[k];
-    const int64_t dot = (int64_t)px * S.ex[k] + (int64_t)py * S.ey[k];
-    if (S.len2[k] == 0 || dot <= 0) return (float)((int64_t)px * px + (int64_t)py * py);
-    if (dot >= S.len2[k]) {
-        const int32_t qx = px - S.ex[k], qy = py - S.ey[k];
+    const int32_t px = sx - S.FX[k][j], py = sy - S.FY[k][j];
+    const int32_t ex = S.ex[k][j], ey = S.ey[k][j];
+    const int64_t len2 = S.len2[k][j];
+    const int64_t dot = (int64_t)px * ex + (int64_t)py * ey;
+    if (len2 == 0 || dot <= 0) return (float)((int64_t)px * px + (int64_t)py * py);
+    if (dot >= len2) {
+        const int32_t qx = px - ex, qy = py - ey;
         return (float)((int64_t)qx * qx + (int64_t)qy * qy);
     }
-    const float cr = (float)((int64_t)px * S.ey[k] - (int64_t)py * S.ex[k]) * S.inv_len[k];
+    const float cr = (float)((int64_t)px * ey - (int64_t)py * ex) * S.inv_len[k][j];
     return cr * cr;
 }
 
-// Eqs. 1-4 for one fragment; l[k] are the exact barycentric weights (sum =
-// area). Returns the premultiplied RGBA of Eq. 4.
-__device__ __forceinline__ float4 shade_fragment(const TriShade& t, const int64_t l[3], int px, int py, int32_t sx,
-                                                 int32_t sy, const ShadeParams& sp)
+// Eqs. 1-4 for one fragment of triangle j; l[k] are the exact barycentric
+// weights (sum = area). Returns the premultiplied RGBA of Eq. 4.
+__device__ __forceinline__ float4 shade_fragment(const ShadeSoA& t, int j, const int64_t l[3], int px, int py,
+                                                 int32_t sx, int32_t sy, const ShadeParams& sp)
 {
-    const float lam0 = (float)l[0] * t.inv_area, lam1 = (float)l[1] * t.inv_area, lam2 = (float)l[2] * t.inv_area;
+    const float ia = t.inv_area[j];
+    const float lam0 = (float)l[0] * ia, lam1 = (float)l[1] * ia, lam2 = (float)l[2] * ia;
     float b0, b1, b2, g = 1.f;
     if (sp.ortho) {
         b0 = lam0; b1 = lam1; b2 = lam2;
     } else {  // perspective-correct interpolation: weights lam_k / w_k, renormalised
-        const float q0 = lam0 * t.inv_ed[0], q1 = lam1 * t.inv_ed[1], q2 = lam2 * t.inv_ed[2];
+        const float q0 = lam0 * t.inv_ed[0][j], q1 = lam1 * t.inv_ed[1][j], q2 = lam2 * t.inv_ed[2][j];
         const float Q = q0 + q1 + q2;   // 1 / eye depth of the fragment
         const float iQ = __frcp_rn(Q);
         b0 = q0 * iQ; b1 = q1 * iQ; b2 = q2 * iQ;
         g = fminf(fmaxf(sp.zref * Q, sp.g_min), sp.g_max);   // depth factor z_ref / z_eye
     }
-    const float t_imp = b0 * t.imp[0] + b1 * t.imp[1] + b2 * t.imp[2];
+    const float t_imp = b0 * t.imp[0][j] + b1 * t.imp[1][j] + b2 * t.imp[2][j];
     // lens distance, normalised to 1 at the lens border
     float dist;
     if (sp.lens_mode == HEXFC_LENS_SCREEN) {
         const float dx = ((float)px + 0.5f) - sp.lens_c[0], dy = ((float)py + 0.5f) - sp.lens_c[1];
         dist = sqrtf(dx * dx + dy * dy) * sp.lens_inv_r;
     } else {
-        const float Px = b0 * t.P[0][0] + b1 * t.P[1][0] + b2 * t.P[2][0];
-        const float Py = b0 * t.P[0][1] + b1 * t.P[1][1] + b2 * t.P[2][1];
-        const float Pz = b0 * t.P[0][2] + b1 * t.P[1][2] + b2 * t.P[2][2];
+        const float Px = b0 * t.P[0][0][j] + b1 * t.P[1][0][j] + b2 * t.P[2][0][j];
+        const float Py = b0 * t.P[0][1][j] + b1 * t.P[1][1][j] + b2 * t.P[2][1][j];
+        const float Pz = b0 * t.P[0][2][j] + b1 * t.P[1][2][j] + b2 * t.P[2][2][j];
         const float dx = Px - sp.lens_c[0], dy = Py - sp.lens_c[1], dz = Pz - sp.lens_c[2];
         dist = sqrtf(dx * dx + dy * dy + dz * dz) * sp.lens_inv_r;
     }
@@ -69,13 +75,14 @@ __device__ __forceinline__ float4 shade_fragment(const TriShade& t, const int64_
     const float st = fminf(fmaxf((dist - 0.7f) * (1.f / 0.3f), 0.f), 1.f);
     const float focus = 1.f - st * st * (3.f - 2.f * st);
     // distances to the face edges: all, visible in focus, visible in context
+    const uint32_t masks = t.masks[j];
     float a2 = INFINITY, f2 = INFINITY, c2 = INFINITY;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const float d2 = seg_dist2(t, k, sx, sy);
+        const float d2 = seg_dist2(t, j, k, sx, sy);
         a2 = fminf(a2, d2);
-        if ((t.masks >> k) & 1u) f2 = fminf(f2, d2);
-        if ((t.masks >> (4 + k)) & 1u) c2 = fminf(c2, d2);
+        if ((masks >> k) & 1u) f2 = fminf(f2, d2);
+        if ((masks >> (4 + k)) & 1u) c2 = fminf(c2, d2);
     }
     const float d_a = sqrtf(a2) * (1.f / 256.f), d_f = sqrtf(f2) * (1.f / 256.f), d_c = sqrtf(c2) * (1.f / 256.f);
     // Eq. 1 with the depth-dependent width, halo band of the focus edges
