@@ -254,14 +254,14 @@ __device__ __forceinline__ bool cover_at(const CovSoA& c, int j, int rx, int ry,
     return in;
 }
 
-// ------------------------------------------------------------------ tile pipelines
+// ------------------------------------------------------------------ tile passes
 //
-// k_count and k_fill run one block per tile: a producer warp stages each chunk
-// of 32 triangles of the tile's (depth-ordered) list into a ring of kRing
-// slots in shared memory, and eight consumer warps each own two rows of the
-// tile (32 pixels, one per lane). Slots are handed over with mbarriers (full:
-// the 32 producer lanes arrive; empty: the 8 consumer warps arrive), so the
-// warps drift apart by up to kRing chunks instead of meeting at a block
+// k_fill runs one block per tile as a pipeline: a producer warp stages each
+// chunk of 32 triangles of the tile's (depth-ordered) list into a ring of
+// kRing slots in shared memory, and eight consumer warps each own two rows of
+// the tile (32 pixels, one per lane). Slots are handed over with mbarriers
+// (full: the 32 producer lanes arrive; empty: the 8 consumer warps arrive), so
+// the warps drift apart by up to kRing chunks instead of meeting at a block
 // barrier for every chunk. Every wait is bounded; a wait that runs out sets an
 // error bit and ends the kernel's loops.
 
@@ -269,11 +269,6 @@ constexpr int kRing = 4;
 constexpr int kConsumerWarps = kTilePix / 32;
 constexpr int kPipeThreads = kTilePix + 32;
 constexpr unsigned long long kErrWait = 4ull;
-
-struct CountSlot {
-    CovSoA c;
-    uint32_t wmask[kConsumerWarps];   // bit j: triangle j touches the two rows of consumer warp w
-};
 
 __device__ __forceinline__ void pipe_init(uint64_t* full, uint64_t* empty)
 {
@@ -287,78 +282,74 @@ __device__ __forceinline__ void pipe_init(uint64_t* full, uint64_t* empty)
     __syncthreads();
 }
 
-// Per tile: coverage of every chunk of 32 triangles as per-pixel bit masks,
-// one lane per pixel; the masks are kept for the fill pass and their bit
-// counts are the per-pixel list lengths.
-__global__ void __launch_bounds__(kPipeThreads) k_count(const uint64_t* __restrict__ tile_off,
-                                                        const uint32_t* __restrict__ bins,
-                                                        const int4* __restrict__ fx, const int4* __restrict__ fy,
-                                                        int tiles_x, int W, int H, uint32_t* __restrict__ cnt,
-                                                        uint32_t* __restrict__ masks,
-                                                        unsigned long long* __restrict__ err)
+// Per tile: coverage of every chunk of 32 triangles as per-pixel bit masks;
+// the masks are kept for the fill pass and their bit counts are the
+// per-pixel list lengths. Warp w takes chunks w, w + 8, ... of the tile's list
+// on its own: its 32 lanes stage the chunk's triangles, then walk each
+// triangle's box (clipped to the tile) one sample per lane, setting bit j of
+// the covered pixels in the warp's private masks. No block barrier until the
+// per-pixel totals are summed at the end.
+struct CountWarp {
+    CovSoA c;
+    uint32_t mask[kTilePix];
+    uint32_t count[kTilePix];
+};
+
+__global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__ tile_off,
+                                                    const uint32_t* __restrict__ bins,
+                                                    const int4* __restrict__ fx, const int4* __restrict__ fy,
+                                                    int tiles_x, int W, int H, uint32_t* __restrict__ cnt,
+                                                    uint32_t* __restrict__ masks)
 {
-    __shared__ CountSlot s_ring[kRing];
-    __shared__ __align__(8) uint64_t s_full[kRing], s_empty[kRing];
+    __shared__ CountWarp s_w[kConsumerWarps];
     const int tile = blockIdx.x;
     const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
     const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
     const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    pipe_init(s_full, s_empty);
-
-    if (warp == kConsumerWarps) {  // producer
-        uint32_t f2t = n_chunks > 0 ? bins[beg + lane] : kPadBin;
-        for (uint32_t c = 0; c < n_chunks; ++c) {
-            const int s = c % kRing;
-            const uint32_t f2t_next = c + 1 < n_chunks ? bins[beg + (uint64_t)(c + 1) * kChunk + lane] : kPadBin;
-            int4 a = make_int4(0, 0, 0, 0), b = a;
-            if (f2t != kPadBin) { a = fx[f2t >> 1]; b = fy[f2t >> 1]; }
-            if (!mbar_wait(&s_empty[s], ((c / kRing) & 1) ^ 1)) {
-                if (lane == 0) atomicOr(err, kErrWait);
-                break;
-            }
-            CountSlot& S = s_ring[s];
-            TriGeom t;
-            if (f2t != kPadBin) stage_cov(a, b, f2t, W, H, px0, py0, S.c, lane, t);
-            else S.c.box[lane] = 0;
-            const int bx = S.c.box[lane], y0 = box_ly0(bx), bh = box_bh(bx);
-#pragma unroll
-            for (int w = 0; w < kConsumerWarps; ++w) {
-                const unsigned m = __ballot_sync(0xffffffffu, bh > 0 && y0 <= 2 * w + 1 && y0 + bh > 2 * w);
-                if (lane == 0) S.wmask[w] = m;
-            }
-            __syncwarp();
-            mbar_arrive(&s_full[s]);
-            f2t = f2t_next;
-        }
-        return;
+    CountWarp& me = s_w[warp];
+    for (int i = lane; i < kTilePix; i += 32) {
+        me.mask[i] = 0;
+        me.count[i] = 0;
     }
-    // consumers: lane = pixel (lx, ly) of rows 2*warp and 2*warp + 1
-    const int p = threadIdx.x, lx = p & (kTile - 1), ly = p / kTile;
-    uint32_t n = 0;
-    for (uint32_t c = 0; c < n_chunks; ++c) {
-        const int s = c % kRing;
-        if (!mbar_wait(&s_full[s], (c / kRing) & 1)) {
-            if (lane == 0) atomicOr(err, kErrWait);
-            break;
-        }
-        const CountSlot& S = s_ring[s];
-        uint32_t todo = S.wmask[warp], mk = 0;
-        while (todo) {
-            const int j = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int bx = S.c.box[j];
-            const int rx = lx - box_lx0(bx), ry = ly - box_ly0(bx);
-            int64_t l[3];
-            if (rx >= 0 && rx < box_bw(bx) && ry >= 0 && ry < box_bh(bx) && cover_at(S.c, j, rx, ry, l))
-                mk |= 1u << j;
+    __syncwarp();
+    for (uint32_t c = warp; c < n_chunks; c += kConsumerWarps) {
+        const uint32_t f2t = bins[beg + (uint64_t)c * kChunk + lane];
+        if (f2t != kPadBin) {
+            TriGeom t;
+            stage_cov(fx[f2t >> 1], fy[f2t >> 1], f2t, W, H, px0, py0, me.c, lane, t);
+        } else {
+            me.c.box[lane] = 0;
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&s_empty[s]);
-        n += __popc(mk);
-        masks[(beg / kChunk + c) * kTilePix + p] = mk;
+        for (int j = 0; j < kChunk; ++j) {
+            const int bx = me.c.box[j];
+            const int bw = box_bw(bx), area = bw * box_bh(bx);
+            if (area == 0) continue;
+            const int lx0 = box_lx0(bx), ly0 = box_ly0(bx);
+            const float inv_bw = __frcp_rn((float)bw);
+            for (int idx = lane; idx < area; idx += 32) {
+                // exact for idx < 256, bw <= 16: the quotient is never within 1/32 of an integer
+                const int ry = (int)(((float)idx + 0.5f) * inv_bw);
+                const int rx = idx - ry * bw;
+                int64_t l[3];
+                if (cover_at(me.c, j, rx, ry, l)) atomicOr(&me.mask[(ly0 + ry) * kTile + lx0 + rx], 1u << j);
+            }
+        }
+        __syncwarp();
+        for (int i = lane; i < kTilePix; i += 32) {
+            const uint32_t m = me.mask[i];
+            me.mask[i] = 0;
+            masks[(beg / kChunk + c) * kTilePix + i] = m;
+            me.count[i] += __popc(m);
+        }
+        __syncwarp();
     }
-    cnt[(int64_t)tile * kTilePix + p] = n;
+    __syncthreads();
+    uint32_t n = 0;
+#pragma unroll
+    for (int w = 0; w < kConsumerWarps; ++w) n += s_w[w].count[threadIdx.x];
+    cnt[(int64_t)tile * kTilePix + threadIdx.x] = n;
 }
 
 // ------------------------------------------------------------------ fill + shade
@@ -374,14 +365,14 @@ __device__ __forceinline__ void stage_shade(const int4 a, const int4 b, const ui
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int k1 = (k + 1) & 3;
-        S.FX[k][j] = FX[k];
-        S.FY[k][j] = FY[k];
+        S.FX[k][j] = (float)FX[k];   // |coordinate| <= 2^22: exact
+        S.FY[k][j] = (float)FY[k];
         const int32_t ex = FX[k1] - FX[k], ey = FY[k1] - FY[k];
-        S.ex[k][j] = ex;
-        S.ey[k][j] = ey;
-        const int64_t l2 = (int64_t)ex * ex + (int64_t)ey * ey;
+        S.ex[k][j] = (float)ex;
+        S.ey[k][j] = (float)ey;
+        const float l2 = (float)((int64_t)ex * ex + (int64_t)ey * ey);
         S.len2[k][j] = l2;
-        S.inv_len[k][j] = l2 > 0 ? rsqrtf((float)l2) : 0.f;
+        S.inv_len[k][j] = l2 > 0.f ? rsqrtf(l2) : 0.f;
     }
     const uint4 z4 = fz[f];
     const float4 e4 = fed[f], i4 = fimp[f], x4 = fpx[f], y4 = fpy[f], w4 = fpz[f];
@@ -510,11 +501,13 @@ __global__ void __launch_bounds__(kPipeThreads) k_fill(const uint64_t* __restric
             const int lx = (int)(pl & (kTile - 1)), ly = (int)(pl / kTile);
             const int px = px0 + lx, py = py0 + ly;
             const int bx = S.c.box[j];
-            int64_t l[3];
-            (void)cover_at(S.c, j, lx - box_lx0(bx), ly - box_ly0(bx), l);
-            const uint32_t z = sample_depth_fast(S.sh.z[0][j], S.sh.z[1][j], S.sh.z[2][j], l[1], l[2], S.sh.area[j],
+            // exact weights of vertices 1 and 2 (edge functions opposite them)
+            const int32_t sxr = (lx - box_lx0(bx)) << 8, syr = (ly - box_ly0(bx)) << 8;
+            const int64_t l1 = S.c.e0[1][j] + (int64_t)S.c.dx[1][j] * syr - (int64_t)S.c.dy[1][j] * sxr;
+            const int64_t l2 = S.c.e0[2][j] + (int64_t)S.c.dx[2][j] * syr - (int64_t)S.c.dy[2][j] * sxr;
+            const uint32_t z = sample_depth_fast(S.sh.z[0][j], S.sh.z[1][j], S.sh.z[2][j], l1, l2, S.sh.area[j],
                                                  S.sh.inv_area[j], bad);
-            const float4 col = shade_fragment(S.sh, j, l, px, py, 256 * px + 128, 256 * py + 128, sp);
+            const float4 col = shade_fragment(S.sh, j, l1, l2, px, py, sp);
             if (kk < s_len[pl]) {  // the count pass sized this list; never write past it
                 const uint64_t o = s_base[pl] + kk;
                 key[o] = ((uint64_t)z << 32) | (uint64_t)S.sh.f2t[j];
@@ -563,9 +556,8 @@ cudaError_t launch_bin_sort(FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_
 
 cudaError_t launch_count(FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, cudaStream_t s)
 {
-    k_count<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, 0, s>>>(
-        fb.tile_off, fb.bins, fb.fx, fb.fy, tiles_x, W, H, fb.cnt, fb.masks,
-        reinterpret_cast<unsigned long long*>(fb.scal + 5));
+    k_count<<<(unsigned)(tiles_x * tiles_y), kTilePix, 0, s>>>(fb.tile_off, fb.bins, fb.fx, fb.fy, tiles_x, W, H,
+                                                                fb.cnt, fb.masks);
     return cudaGetLastError();
 }
 

@@ -7,11 +7,12 @@ namespace hexfc {
 
 // Shading inputs of the kChunk triangles of one chunk, structure of arrays
 // (element j = triangle j, vertices in wound order), so that lanes reading
-// different triangles touch different shared-memory banks.
+// different triangles touch different shared-memory banks. Coordinates are in
+// 1/256-pixel units; integers below 2^24 are exact in float.
 struct ShadeSoA {
-    int32_t FX[4][kChunk], FY[4][kChunk];   // face corners (16.8)
-    int32_t ex[4][kChunk], ey[4][kChunk];   // face edge vectors corner k -> k+1 (16.8)
-    int64_t len2[4][kChunk];                // their squared lengths, exact
+    float FX[4][kChunk], FY[4][kChunk];     // face corners
+    float ex[4][kChunk], ey[4][kChunk];     // face edge vectors corner k -> k+1
+    float len2[4][kChunk];                  // their squared lengths
     float inv_len[4][kChunk];               // 1 / length
     uint32_t z[3][kChunk];                  // window depth of the triangle's vertices
     float inv_ed[3][kChunk];                // 1 / eye depth
@@ -23,31 +24,32 @@ struct ShadeSoA {
     uint32_t masks[kChunk];                 // bits 0-3 focus-visible, 4-7 context-visible face edges
 };
 
-// Squared distance (in 1/256-pixel units squared) from sample (sx, sy) to face
-// edge k of triangle j: exact integer tests pick the closest feature (an end
-// point or the segment's interior), one float rounding for the value.
-__device__ __forceinline__ float seg_dist2(const ShadeSoA& S, int j, int k, int32_t sx, int32_t sy)
+// Squared distance (1/256-pixel units squared) from sample (sx, sy) to face
+// edge k of triangle j: the closest point of the segment (an end point or the
+// foot of the perpendicular), chosen without branches.
+__device__ __forceinline__ float seg_dist2(const ShadeSoA& S, int j, int k, float sx, float sy)
 {
-    const int32_t px = sx - S.FX[k][j], py = sy - S.FY[k][j];
-    const int32_t ex = S.ex[k][j], ey = S.ey[k][j];
-    const int64_t len2 = S.len2[k][j];
-    const int64_t dot = (int64_t)px * ex + (int64_t)py * ey;
-    if (len2 == 0 || dot <= 0) return (float)((int64_t)px * px + (int64_t)py * py);
-    if (dot >= len2) {
-        const int32_t qx = px - ex, qy = py - ey;
-        return (float)((int64_t)qx * qx + (int64_t)qy * qy);
-    }
-    const float cr = (float)((int64_t)px * ey - (int64_t)py * ex) * S.inv_len[k][j];
-    return cr * cr;
+    const float px = sx - S.FX[k][j], py = sy - S.FY[k][j];   // exact: both are integers < 2^24
+    const float ex = S.ex[k][j], ey = S.ey[k][j];
+    const float dot = fmaf(px, ex, py * ey);
+    const float da = fmaf(px, px, py * py);
+    const float qx = px - ex, qy = py - ey;
+    const float db = fmaf(qx, qx, qy * qy);
+    const float cr = fmaf(px, ey, -py * ex) * S.inv_len[k][j];
+    const float dp = cr * cr;
+    return dot <= 0.f ? da : (dot >= S.len2[k][j] ? db : dp);
 }
 
-// Eqs. 1-4 for one fragment of triangle j; l[k] are the exact barycentric
-// weights (sum = area). Returns the premultiplied RGBA of Eq. 4.
-__device__ __forceinline__ float4 shade_fragment(const ShadeSoA& t, int j, const int64_t l[3], int px, int py,
-                                                 int32_t sx, int32_t sy, const ShadeParams& sp)
+__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
+// Eqs. 1-4 for one fragment of triangle j at pixel (px, py); l1, l2 are the
+// exact barycentric weights of vertices 1 and 2 (of a total equal to the
+// area). Returns the premultiplied RGBA of Eq. 4.
+__device__ __forceinline__ float4 shade_fragment(const ShadeSoA& t, int j, int64_t l1, int64_t l2, int px, int py,
+                                                 const ShadeParams& sp)
 {
-    const float ia = t.inv_area[j];
-    const float lam0 = (float)l[0] * ia, lam1 = (float)l[1] * ia, lam2 = (float)l[2] * ia;
+    const float lam1 = (float)l1 * t.inv_area[j], lam2 = (float)l2 * t.inv_area[j];
+    const float lam0 = 1.f - lam1 - lam2;
     float b0, b1, b2, g = 1.f;
     if (sp.ortho) {
         b0 = lam0; b1 = lam1; b2 = lam2;
@@ -63,28 +65,31 @@ __device__ __forceinline__ float4 shade_fragment(const ShadeSoA& t, int j, const
     float dist;
     if (sp.lens_mode == HEXFC_LENS_SCREEN) {
         const float dx = ((float)px + 0.5f) - sp.lens_c[0], dy = ((float)py + 0.5f) - sp.lens_c[1];
-        dist = sqrtf(dx * dx + dy * dy) * sp.lens_inv_r;
+        dist = fast_sqrt(dx * dx + dy * dy) * sp.lens_inv_r;
     } else {
         const float Px = b0 * t.P[0][0][j] + b1 * t.P[1][0][j] + b2 * t.P[2][0][j];
         const float Py = b0 * t.P[0][1][j] + b1 * t.P[1][1][j] + b2 * t.P[2][1][j];
         const float Pz = b0 * t.P[0][2][j] + b1 * t.P[1][2][j] + b2 * t.P[2][2][j];
         const float dx = Px - sp.lens_c[0], dy = Py - sp.lens_c[1], dz = Pz - sp.lens_c[2];
-        dist = sqrtf(dx * dx + dy * dy + dz * dz) * sp.lens_inv_r;
+        dist = fast_sqrt(dx * dx + dy * dy + dz * dz) * sp.lens_inv_r;
     }
     // focus = 1 - smoothstep(0.7, 1, dist)
     const float st = fminf(fmaxf((dist - 0.7f) * (1.f / 0.3f), 0.f), 1.f);
     const float focus = 1.f - st * st * (3.f - 2.f * st);
     // distances to the face edges: all, visible in focus, visible in context
     const uint32_t masks = t.masks[j];
+    const float sx = (float)(256 * px + 128), sy = (float)(256 * py + 128);
     float a2 = INFINITY, f2 = INFINITY, c2 = INFINITY;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const float d2 = seg_dist2(t, j, k, sx, sy);
         a2 = fminf(a2, d2);
-        if ((masks >> k) & 1u) f2 = fminf(f2, d2);
-        if ((masks >> (4 + k)) & 1u) c2 = fminf(c2, d2);
+        f2 = ((masks >> k) & 1u) ? fminf(f2, d2) : f2;
+        c2 = ((masks >> (4 + k)) & 1u) ? fminf(c2, d2) : c2;
     }
-    const float d_a = sqrtf(a2) * (1.f / 256.f), d_f = sqrtf(f2) * (1.f / 256.f), d_c = sqrtf(c2) * (1.f / 256.f);
+    const float d_a = fast_sqrt(a2) * (1.f / 256.f);
+    const float d_f = f2 < INFINITY ? fast_sqrt(f2) * (1.f / 256.f) : INFINITY;
+    const float d_c = c2 < INFINITY ? fast_sqrt(c2) * (1.f / 256.f) : INFINITY;
     // Eq. 1 with the depth-dependent width, halo band of the focus edges
     const float w = (1.f + 0.3f * focus) * sp.w_base * g;
     const bool e_focus = d_f <= w, e_context = d_c <= w;
