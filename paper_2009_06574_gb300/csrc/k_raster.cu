@@ -150,50 +150,86 @@ __global__ void k_bin_fill(const int4* __restrict__ fx, const int4* __restrict__
 // ------------------------------------------------------------------ bin order
 
 constexpr int kBinSortMax = 4096;   // longer tile lists keep their arrival order
+constexpr int kDepthBuckets = 2048;
 
-// Orders each tile's list by triangle depth (sum of the three window depths,
-// then 2*face+tri); the padding slots (kPadBin) go last. Any order gives the
-// same fragments; depth order makes the fill write almost every per-pixel list
-// already sorted front to back.
-__global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ tile_off, uint32_t* __restrict__ bins,
+// Orders each tile's list front to back by a counting sort of the triangles
+// into kDepthBuckets buckets of their depth (sum of the three window depths)
+// over the tile's depth range; the padding slots stay at the end. Any order
+// gives the same fragments; this one makes the fill write every per-pixel list
+// sorted or nearly sorted (order within a bucket is arbitrary).
+__global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ tile_off,
+                                                  const uint32_t* __restrict__ tile_cnt, uint32_t* __restrict__ bins,
                                                   const uint4* __restrict__ fz)
 {
-    __shared__ uint64_t s_k[kBinSortMax];
+    __shared__ uint32_t s_hist[kDepthBuckets];
+    __shared__ uint16_t s_b[kBinSortMax];
+    __shared__ uint32_t s_out[kBinSortMax];
+    __shared__ uint32_t s_red[2][8];
     const int tile = blockIdx.x;
-    const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];
-    const uint32_t n = (uint32_t)(end - beg);
+    const uint64_t beg = tile_off[tile];
+    const uint32_t n = tile_cnt[tile];   // real entries; the rest of the padded list is kPadBin
     if (n < 2 || n > (uint32_t)kBinSortMax) return;
-    uint32_t np2 = 2;
-    while (np2 < n) np2 <<= 1;
-    for (uint32_t i = threadIdx.x; i < np2; i += blockDim.x) {
-        uint64_t k = ~0ull;
-        if (i < n) {
-            uint32_t f2t = bins[beg + i];
-            if (f2t != kPadBin) {
-                uint4 z = fz[f2t >> 1];
-                uint64_t zs = (uint64_t)z.x + ((f2t & 1) ? (uint64_t)z.z + z.w : (uint64_t)z.y + z.z);
-                k = (zs << 32) | f2t;
-            }
-        }
-        s_k[i] = k;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto zsum = [&](uint32_t f2t) -> uint32_t {
+        const uint4 z = fz[f2t >> 1];
+        return z.x + ((f2t & 1) ? z.z + z.w : z.y + z.z);   // < 3 * 2^24
+    };
+    // depth range of the tile's triangles
+    uint32_t zmin = 0xFFFFFFFFu, zmax = 0;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint32_t zs = zsum(bins[beg + i]);
+        zmin = min(zmin, zs);
+        zmax = max(zmax, zs);
+    }
+    for (int i = threadIdx.x; i < kDepthBuckets; i += blockDim.x) s_hist[i] = 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        zmin = min(zmin, __shfl_xor_sync(0xffffffffu, zmin, o));
+        zmax = max(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
+    }
+    if (lane == 0) { s_red[0][warp] = zmin; s_red[1][warp] = zmax; }
+    __syncthreads();
+    zmin = s_red[0][0];
+    zmax = s_red[1][0];
+    for (int w = 1; w < 8; ++w) { zmin = min(zmin, s_red[0][w]); zmax = max(zmax, s_red[1][w]); }
+    const float scale = (float)kDepthBuckets / (float)(zmax - zmin + 1);
+    // histogram
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const int b = min((int)((float)(zsum(bins[beg + i]) - zmin) * scale), kDepthBuckets - 1);
+        s_b[i] = (uint16_t)b;
+        atomicAdd(&s_hist[b], 1u);
     }
     __syncthreads();
-    for (uint32_t size = 2; size <= np2; size <<= 1)
-        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-            for (uint32_t i = threadIdx.x; i < np2; i += blockDim.x) {
-                uint32_t p = i ^ stride;
-                if (p > i) {
-                    uint64_t a = s_k[i], b = s_k[p];
-                    bool up = (i & size) == 0;
-                    if (up ? (a > b) : (a < b)) { s_k[i] = b; s_k[p] = a; }
-                }
-            }
-            __syncthreads();
+    // exclusive scan of the histogram: 8 buckets per thread
+    {
+        uint32_t v[kDepthBuckets / 256], sum = 0;
+#pragma unroll
+        for (int k = 0; k < kDepthBuckets / 256; ++k) {
+            v[k] = s_hist[threadIdx.x * (kDepthBuckets / 256) + k];
+            sum += v[k];
         }
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        uint64_t k = s_k[i];
-        bins[beg + i] = k == ~0ull ? kPadBin : (uint32_t)k;
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        __syncthreads();   // everyone has read s_hist
+        if (lane == 31) s_red[0][warp] = incl;
+        __syncthreads();
+        uint32_t base = incl - sum;
+        for (int w = 0; w < warp; ++w) base += s_red[0][w];
+#pragma unroll
+        for (int k = 0; k < kDepthBuckets / 256; ++k) {
+            s_hist[threadIdx.x * (kDepthBuckets / 256) + k] = base;
+            base += v[k];
+        }
     }
+    __syncthreads();
+    // scatter (arbitrary order inside a bucket), then write back
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) s_out[atomicAdd(&s_hist[s_b[i]], 1u)] = bins[beg + i];
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) bins[beg + i] = s_out[i];
 }
 
 // ------------------------------------------------------------------ raster per tile
@@ -265,7 +301,7 @@ __device__ __forceinline__ bool cover_at(const CovSoA& c, int j, int rx, int ry,
 // barrier for every chunk. Every wait is bounded; a wait that runs out sets an
 // error bit and ends the kernel's loops.
 
-constexpr int kRing = 4;
+constexpr int kRing = 3;
 constexpr int kConsumerWarps = kTilePix / 32;
 constexpr int kPipeThreads = kTilePix + 32;
 constexpr unsigned long long kErrWait = 4ull;
@@ -407,7 +443,7 @@ struct FillSlot {
 // (pixel-major, in list order) so that the shading runs on every lane, and
 // each fragment is written at its pixel's offset plus its rank in the pixel's
 // list (the rank the count pass sized).
-__global__ void __launch_bounds__(kPipeThreads) k_fill(const uint64_t* __restrict__ tile_off,
+__global__ void __launch_bounds__(kPipeThreads, 4) k_fill(const uint64_t* __restrict__ tile_off,
                                                        const uint32_t* __restrict__ bins,
                                                        const uint32_t* __restrict__ masks,
                                                        const int4* __restrict__ fx, const int4* __restrict__ fy,
@@ -468,11 +504,14 @@ __global__ void __launch_bounds__(kPipeThreads) k_fill(const uint64_t* __restric
     uint32_t* q = s_qall + warp * (kChunk * 32);
     uint32_t k_run = 0;
     bool bad = false;
-    uint32_t mk_next = n_chunks > 0 ? masks[(beg / kChunk) * kTilePix + p] : 0u;
+    // masks of the next two chunks are in flight while this one is shaded
+    uint32_t mk_a = n_chunks > 0 ? masks[(beg / kChunk) * kTilePix + p] : 0u;
+    uint32_t mk_b = n_chunks > 1 ? masks[(beg / kChunk + 1) * kTilePix + p] : 0u;
     for (uint32_t c = 0; c < n_chunks; ++c) {
         const int s = c % kRing;
-        uint32_t mk = mk_next;
-        if (c + 1 < n_chunks) mk_next = masks[(beg / kChunk + c + 1) * kTilePix + p];
+        uint32_t mk = mk_a;
+        mk_a = mk_b;
+        if (c + 2 < n_chunks) mk_b = masks[(beg / kChunk + c + 2) * kTilePix + p];
         if (!mbar_wait(&s_full[s], (c / kRing) & 1)) {
             if (lane == 0) atomicOr(err, kErrWait);
             break;
@@ -550,7 +589,7 @@ cudaError_t launch_bin_fill(const DevMesh& m, FrameBufs& fb, int tiles_x, int W,
 
 cudaError_t launch_bin_sort(FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_t s)
 {
-    k_bin_sort<<<(unsigned)(tiles_x * tiles_y), 256, 0, s>>>(fb.tile_off, fb.bins, fb.fz);
+    k_bin_sort<<<(unsigned)(tiles_x * tiles_y), 256, 0, s>>>(fb.tile_off, fb.tile_cnt, fb.bins, fb.fz);
     return cudaGetLastError();
 }
 
