@@ -108,7 +108,7 @@ void free_mesh(DevMesh* m)
 void free_frame(FrameBufs& f)
 {
     dfree(f.vproj); dfree(f.ved); dfree(f.fx); dfree(f.fy); dfree(f.fz); dfree(f.fed); dfree(f.fflags);
-    dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.bins); dfree(f.masks); dfree(f.cnt);
+    dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.tile_order); dfree(f.bins); dfree(f.masks); dfree(f.cnt);
     dfree(f.off);
     dfree(f.part); dfree(f.part_max); dfree(f.long_q); dfree(f.fix_q); dfree(f.key); dfree(f.rgba); dfree(f.scal);
     if (f.h_scal) cudaFreeHost(f.h_scal);
@@ -237,10 +237,12 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
     }
     if (!fb.tile_cnt || fb.t_cap < n_tiles + 1) {
         int64_t c1 = 0, c2 = 0;
-        dfree(fb.tile_off); dfree(fb.tile_cur);
+        int64_t c3 = 0;
+        dfree(fb.tile_off); dfree(fb.tile_cur); dfree(fb.tile_order);
         if ((st = ensure(&fb.tile_cnt, &fb.t_cap, n_tiles + 1)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.tile_off, &c1, fb.t_cap)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.tile_cur, &c2, fb.t_cap)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.tile_order, &c3, fb.t_cap)) != HEXFC_OK) return st;
     }
     if (!fb.cnt || fb.p_cap < n_pix + 1) {
         int64_t c1 = 0, c2 = 0;
@@ -293,12 +295,13 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
     CK(cudaMemsetAsync(fb.bins, 0xFF, sizeof(uint32_t) * (size_t)n_bins, s));   // padding slots = kPadBin
     CK(launch_bin_fill(*m, fb, tiles_x, W, H, ctx->reverse_bins, s));
     CK(launch_bin_sort(fb, tiles_x, tiles_y, s));
+    CK(launch_tile_order(fb, n_tiles, s));
     mark(ctx, 5, s);
     CK(launch_count(fb, tiles_x, tiles_y, W, H, s));
     mark(ctx, 6, s);
     CK(scan_u32_to_u64(fb.cnt, fb.off, n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
     mark(ctx, 7, s);
-    launches += 6;
+    launches += 7;
     CK(cudaMemcpyAsync(fb.h_scal, fb.scal, 6 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (fb.h_scal[5] != 0) {  // a bounded device wait ran out, or an exactness check failed
@@ -745,6 +748,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fb.tile_cnt = a.take<uint32_t>((size_t)n_tiles + 1);
     fb.tile_off = a.take<uint64_t>((size_t)n_tiles + 1);
     fb.tile_cur = a.take<uint32_t>((size_t)n_tiles + 1);
+    fb.tile_order = a.take<uint32_t>((size_t)n_tiles + 1);
     fb.cnt = a.take<uint32_t>((size_t)n_pix + 1);
     fb.off = a.take<uint64_t>((size_t)n_pix + 1);
     fb.long_q = a.take<uint32_t>((size_t)n_pix + 1);
@@ -753,7 +757,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fb.part_max = a.take<uint32_t>(2 * (size_t)nparts);
     fb.scal = a.take<uint64_t>(16);
     if (!fb.vproj || !fb.ved || !fb.fx || !fb.fy || !fb.fz || !fb.fed || !fb.fflags || !fb.tile_cnt ||
-        !fb.tile_off || !fb.tile_cur || !fb.cnt || !fb.off || !fb.long_q || !fb.fix_q || !fb.part || !fb.part_max ||
+        !fb.tile_off || !fb.tile_cur || !fb.tile_order || !fb.cnt || !fb.off || !fb.long_q || !fb.fix_q || !fb.part || !fb.part_max ||
         !fb.scal)
         return HEXFC_ERR_OVERFLOW;
     // the array keeps the previous call's contents: clear what must start at zero
@@ -781,6 +785,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     CK(cudaMemsetAsync(fb.bins, 0xFF, sizeof(uint32_t) * (size_t)n_bins, s));   // padding slots = kPadBin
     CK(launch_bin_fill(*m, fb, tiles_x, W, H, ctx->reverse_bins, s));
     CK(launch_bin_sort(fb, tiles_x, tiles_y, s));
+    CK(launch_tile_order(fb, n_tiles, s));
     CK(launch_count(fb, tiles_x, tiles_y, W, H, s));
     CK(scan_u32_to_u64(fb.cnt, fb.off, n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
     CK(cudaMemcpyAsync(h, fb.scal, 6 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
@@ -791,7 +796,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fs.fragments = total;
     fs.max_list = (uint32_t)h[1];
     fs.long_lists = n_long;
-    fs.kernel_launches = 14 + (n_long > 0 ? 1u : 0u);
+    fs.kernel_launches = 15 + (n_long > 0 ? 1u : 0u);
     if (stats) *stats = fs;
     if (fs.max_list > HEXFC_MAX_LIST) return HEXFC_ERR_OVERFLOW;
     fb.key = a.take<uint64_t>((size_t)total + 2);   // the composite widens key copies to 16-byte boundaries

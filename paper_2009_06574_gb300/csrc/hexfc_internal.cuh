@@ -74,6 +74,7 @@ struct FrameBufs {
     uint32_t* tile_cnt = nullptr;   // [T+1]
     uint64_t* tile_off = nullptr;   // [T+1]
     uint32_t* tile_cur = nullptr;   // [T]
+    uint32_t* tile_order = nullptr; // [T] tiles by decreasing chunk count
     int64_t t_cap = 0;
     uint32_t* bins = nullptr;       // face2tri ids grouped by tile, each tile padded to whole chunks
     int64_t bin_cap = 0;
@@ -108,6 +109,7 @@ cudaError_t launch_face_setup(const DevMesh& m, const CamParams& cam, int lod, f
 cudaError_t launch_bin_fill(const DevMesh& m, FrameBufs& fb, int tiles_x, int W, int H, int reverse,
                             cudaStream_t s);
 cudaError_t launch_bin_sort(FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_t s);
+cudaError_t launch_tile_order(FrameBufs& fb, int n_tiles, cudaStream_t s);
 cudaError_t launch_count(FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, cudaStream_t s);
 cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x,
                         int tiles_y, int W, int H, cudaStream_t s);

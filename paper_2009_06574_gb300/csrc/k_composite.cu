@@ -46,19 +46,6 @@ __device__ __forceinline__ CT warp_ordered_reduce(CT c, int lane)
     return c;
 }
 
-// ---------------------------------------------------------------- async copies
-
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 // ---------------------------------------------------------------- resolve
 
 __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m)
@@ -392,7 +379,7 @@ __global__ void __launch_bounds__(256) k_debug_short(const uint32_t* __restrict_
         cp_async16(&b.rgba[e], rgba + off[q] + e);
     }
     cp_async_commit();
-    cp_async_wait_all();
+    cp_async_wait<0>();
     __syncwarp();
     (void)warp_resolve(b.key, b.rgba, n, lane, out_key + dst_off[i], out_rgba + dst_off[i]);
 }

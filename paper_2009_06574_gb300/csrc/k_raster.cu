@@ -232,6 +232,77 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) bins[beg + i] = s_out[i];
 }
 
+// ------------------------------------------------------------------ tile order
+
+constexpr int kOrderBuckets = 4096;   // chunk counts above kOrderBuckets - 1 share the first class
+
+// Rank of lane's value among the lanes of the warp holding the same value, and
+// how many hold it, so that one lane per value does the shared-memory atomic.
+__device__ __forceinline__ uint32_t warp_add_same(uint32_t* s, uint32_t b, bool active)
+{
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    if (!active) return 0;
+    const unsigned peers = __match_any_sync(act, b);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&s[b], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+}
+
+// The tiles in decreasing order of their number of chunks (a counting sort),
+// so that the per-tile passes start the longest tiles first and the shortest
+// ones fill the tail of the launch. Order inside a class is arbitrary; no
+// result depends on it. One block.
+__global__ void __launch_bounds__(1024) k_tile_order(const uint64_t* __restrict__ tile_off, int n_tiles,
+                                                     uint32_t* __restrict__ order)
+{
+    __shared__ uint32_t s_hist[kOrderBuckets];
+    __shared__ uint32_t s_warp[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto cls = [&](int t) -> uint32_t {
+        const uint64_t nc = (tile_off[t + 1] - tile_off[t]) / kChunk;
+        return (uint32_t)(kOrderBuckets - 1) - (uint32_t)min(nc, (uint64_t)(kOrderBuckets - 1));
+    };
+    for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) s_hist[i] = 0;
+    __syncthreads();
+    for (int t0 = 0; t0 < n_tiles; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        warp_add_same(s_hist, t < n_tiles ? cls(t) : 0u, t < n_tiles);
+    }
+    __syncthreads();
+    // exclusive scan of the histogram: kOrderBuckets / 1024 classes per thread
+    constexpr int kPer = kOrderBuckets / 1024;
+    uint32_t v[kPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        v[k] = s_hist[threadIdx.x * kPer + k];
+        sum += v[k];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t base = incl - sum;
+    for (int w = 0; w < warp; ++w) base += s_warp[w];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        s_hist[threadIdx.x * kPer + k] = base;
+        base += v[k];
+    }
+    __syncthreads();
+    for (int t0 = 0; t0 < n_tiles; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        const uint32_t slot = warp_add_same(s_hist, t < n_tiles ? cls(t) : 0u, t < n_tiles);
+        if (t < n_tiles) order[slot] = (uint32_t)t;
+    }
+}
+
 // ------------------------------------------------------------------ raster per tile
 
 // Coverage data of the kChunk triangles of one chunk (structure of arrays):
@@ -327,18 +398,65 @@ __device__ __forceinline__ void pipe_init(uint64_t* full, uint64_t* empty)
 // per-pixel totals are summed at the end.
 struct CountWarp {
     CovSoA c;
+    // float copies of the edge functions: E ~ e0f + fa*rx + fb*ry, and a bound on the
+    // float error; outside the bound the float sign is the exact sign
+    float e0f[3][kChunk], fa[3][kChunk], fb[3][kChunk], tol[3][kChunk];
     uint32_t mask[kTilePix];
     uint32_t count[kTilePix];
 };
 
+// Float version of triangle j's edge functions in the warp's staging slot.
+// The float evaluation fmaf(fa, rx, fmaf(fb, ry, e0f)) has three roundings of
+// magnitudes at most |e0| + 15 (|fa| + |fb|); tol is twice that bound.
+__device__ __forceinline__ void stage_fast(CountWarp& me, int j)
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float e0 = (float)me.c.e0[k][j];
+        const float fa = -256.f * (float)me.c.dy[k][j];   // exact: |dy| < 2^24
+        const float fb = 256.f * (float)me.c.dx[k][j];
+        me.e0f[k][j] = e0;
+        me.fa[k][j] = fa;
+        me.fb[k][j] = fb;
+        me.tol[k][j] = ldexpf(fabsf(e0) + 16.f * (fabsf(fa) + fabsf(fb)), -21);
+    }
+}
+
+// Coverage of sample (rx, ry) of triangle j: decided in float when every edge
+// value is outside its error bound (or one is clearly negative), else exactly.
+__device__ __forceinline__ bool cover_fast(const CountWarp& me, int j, int rx, int ry)
+{
+    const float frx = (float)rx, fry = (float)ry;
+    bool all_pos = true, any_neg = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float e = fmaf(me.fa[k][j], frx, fmaf(me.fb[k][j], fry, me.e0f[k][j]));
+        const float t = me.tol[k][j];
+        all_pos = all_pos && e > t;
+        any_neg = any_neg || e < -t;
+    }
+    if (all_pos) return true;
+    if (any_neg) return false;
+    int64_t l[3];
+    return cover_at(me.c, j, rx, ry, l);
+}
+
+// Per tile: coverage of every chunk of 32 triangles as per-pixel bit masks;
+// the masks are kept for the fill pass and their bit counts are the
+// per-pixel list lengths. Warp w takes chunks w, w + 8, ... of the tile's list
+// on its own: its 32 lanes stage the chunk's triangles, then walk each
+// triangle's box (clipped to the tile) one sample per lane, setting bit j of
+// the covered pixels in the warp's private masks. No block barrier until the
+// per-pixel totals are summed at the end.
 __global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__ tile_off,
                                                     const uint32_t* __restrict__ bins,
                                                     const int4* __restrict__ fx, const int4* __restrict__ fy,
-                                                    int tiles_x, int W, int H, uint32_t* __restrict__ cnt,
-                                                    uint32_t* __restrict__ masks)
+                                                    const uint32_t* __restrict__ order, int tiles_x, int W, int H,
+                                                    uint32_t* __restrict__ cnt, uint32_t* __restrict__ masks)
 {
-    __shared__ CountWarp s_w[kConsumerWarps];
-    const int tile = blockIdx.x;
+    extern __shared__ __align__(16) unsigned char count_smem[];
+    CountWarp* s_w = reinterpret_cast<CountWarp*>(count_smem);   // [kConsumerWarps]
+    const int tile = (int)order[blockIdx.x];
     const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
     const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
     const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
@@ -349,14 +467,20 @@ __global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__
         me.count[i] = 0;
     }
     __syncwarp();
+    uint32_t f2t = warp < (int)n_chunks ? bins[beg + (uint64_t)warp * kChunk + lane] : kPadBin;
     for (uint32_t c = warp; c < n_chunks; c += kConsumerWarps) {
-        const uint32_t f2t = bins[beg + (uint64_t)c * kChunk + lane];
+        int4 a = make_int4(0, 0, 0, 0), b = a;
+        if (f2t != kPadBin) { a = fx[f2t >> 1]; b = fy[f2t >> 1]; }
+        const uint32_t f2t_next =
+            c + kConsumerWarps < n_chunks ? bins[beg + (uint64_t)(c + kConsumerWarps) * kChunk + lane] : kPadBin;
         if (f2t != kPadBin) {
             TriGeom t;
-            stage_cov(fx[f2t >> 1], fy[f2t >> 1], f2t, W, H, px0, py0, me.c, lane, t);
+            stage_cov(a, b, f2t, W, H, px0, py0, me.c, lane, t);
+            if (me.c.box[lane] != 0) stage_fast(me, lane);
         } else {
             me.c.box[lane] = 0;
         }
+        f2t = f2t_next;
         __syncwarp();
         for (int j = 0; j < kChunk; ++j) {
             const int bx = me.c.box[j];
@@ -368,8 +492,7 @@ __global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__
                 // exact for idx < 256, bw <= 16: the quotient is never within 1/32 of an integer
                 const int ry = (int)(((float)idx + 0.5f) * inv_bw);
                 const int rx = idx - ry * bw;
-                int64_t l[3];
-                if (cover_at(me.c, j, rx, ry, l)) atomicOr(&me.mask[(ly0 + ry) * kTile + lx0 + rx], 1u << j);
+                if (cover_fast(me, j, rx, ry)) atomicOr(&me.mask[(ly0 + ry) * kTile + lx0 + rx], 1u << j);
             }
         }
         __syncwarp();
@@ -390,14 +513,34 @@ __global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__
 
 // ------------------------------------------------------------------ fill + shade
 
-__device__ __forceinline__ void stage_shade(const int4 a, const int4 b, const uint4* __restrict__ fz,
-                                            const float4* __restrict__ fed, const uint32_t* __restrict__ fflags,
-                                            const float4* __restrict__ fimp, const float4* __restrict__ fpx,
-                                            const float4* __restrict__ fpy, const float4* __restrict__ fpz,
-                                            uint32_t f2t, const TriGeom& t, ShadeSoA& S, int j)
+// Raw per-face records of one triangle, fetched asynchronously by the producer.
+struct RawFace {
+    int4 fx, fy;
+    uint4 fz;
+    float4 fed, fimp, fpx, fpy, fpz;
+    uint32_t flags, pad[3];
+};
+
+__device__ __forceinline__ void raw_fetch(RawFace& r, uint32_t f, const int4* __restrict__ fx,
+                                          const int4* __restrict__ fy, const uint4* __restrict__ fz,
+                                          const float4* __restrict__ fed, const uint32_t* __restrict__ fflags,
+                                          const float4* __restrict__ fimp, const float4* __restrict__ fpx,
+                                          const float4* __restrict__ fpy, const float4* __restrict__ fpz)
 {
-    const uint32_t f = f2t >> 1;
-    const int32_t FX[4] = {a.x, a.y, a.z, a.w}, FY[4] = {b.x, b.y, b.z, b.w};
+    cp_async16(&r.fx, fx + f);
+    cp_async16(&r.fy, fy + f);
+    cp_async16(&r.fz, fz + f);
+    cp_async16(&r.fed, fed + f);
+    cp_async16(&r.fimp, fimp + f);
+    cp_async16(&r.fpx, fpx + f);
+    cp_async16(&r.fpy, fpy + f);
+    cp_async16(&r.fpz, fpz + f);
+    cp_async4(&r.flags, fflags + f);
+}
+
+__device__ __forceinline__ void stage_shade(const RawFace& r, uint32_t f2t, const TriGeom& t, ShadeSoA& S, int j)
+{
+    const int32_t FX[4] = {r.fx.x, r.fx.y, r.fx.z, r.fx.w}, FY[4] = {r.fy.x, r.fy.y, r.fy.z, r.fy.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int k1 = (k + 1) & 3;
@@ -406,16 +549,14 @@ __device__ __forceinline__ void stage_shade(const int4 a, const int4 b, const ui
         const int32_t ex = FX[k1] - FX[k], ey = FY[k1] - FY[k];
         S.ex[k][j] = (float)ex;
         S.ey[k][j] = (float)ey;
-        const float l2 = (float)((int64_t)ex * ex + (int64_t)ey * ey);
+        const float l2 = u64_to_f32((uint64_t)((int64_t)ex * ex + (int64_t)ey * ey));
         S.len2[k][j] = l2;
         S.inv_len[k][j] = l2 > 0.f ? rsqrtf(l2) : 0.f;
     }
-    const uint4 z4 = fz[f];
-    const float4 e4 = fed[f], i4 = fimp[f], x4 = fpx[f], y4 = fpy[f], w4 = fpz[f];
-    const uint32_t zz[4] = {z4.x, z4.y, z4.z, z4.w};
-    const float ee[4] = {e4.x, e4.y, e4.z, e4.w}, ii[4] = {i4.x, i4.y, i4.z, i4.w};
-    const float xx[4] = {x4.x, x4.y, x4.z, x4.w}, yy[4] = {y4.x, y4.y, y4.z, y4.w};
-    const float ww[4] = {w4.x, w4.y, w4.z, w4.w};
+    const uint32_t zz[4] = {r.fz.x, r.fz.y, r.fz.z, r.fz.w};
+    const float ee[4] = {r.fed.x, r.fed.y, r.fed.z, r.fed.w}, ii[4] = {r.fimp.x, r.fimp.y, r.fimp.z, r.fimp.w};
+    const float xx[4] = {r.fpx.x, r.fpx.y, r.fpx.z, r.fpx.w}, yy[4] = {r.fpy.x, r.fpy.y, r.fpy.z, r.fpy.w};
+    const float ww[4] = {r.fpz.x, r.fpz.y, r.fpz.z, r.fpz.w};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int c = t.vi[k];
@@ -427,10 +568,12 @@ __device__ __forceinline__ void stage_shade(const int4 a, const int4 b, const ui
         S.P[k][1][j] = c == 0 ? yy[0] : c == 1 ? yy[1] : c == 2 ? yy[2] : yy[3];
         S.P[k][2][j] = c == 0 ? ww[0] : c == 1 ? ww[1] : c == 2 ? ww[2] : ww[3];
     }
+    S.dz[0][j] = (float)(int32_t)(S.z[1][j] - S.z[0][j]);
+    S.dz[1][j] = (float)(int32_t)(S.z[2][j] - S.z[0][j]);
     S.area[j] = t.area;
-    S.inv_area[j] = 1.f / (float)t.area;
+    S.inv_area[j] = 1.f / u64_to_f32((uint64_t)t.area);
     S.f2t[j] = f2t;
-    S.masks[j] = fflags[f] & 0xFFu;
+    S.masks[j] = r.flags & 0xFFu;
 }
 
 struct FillSlot {
@@ -438,31 +581,42 @@ struct FillSlot {
     ShadeSoA sh;
 };
 
+constexpr int kQCap = 512;   // queue entries per consumer warp; larger chunks are shaded in windows
+
+__host__ __device__ constexpr size_t fill_smem_bytes()
+{
+    return kRing * sizeof(FillSlot) + 2 * kChunk * sizeof(RawFace) + (size_t)kConsumerWarps * kQCap * sizeof(uint32_t);
+}
+
 // Per tile: the coverage masks of the count pass give, chunk by chunk, each
 // lane's covered triangles; a warp compacts its covered samples into a queue
 // (pixel-major, in list order) so that the shading runs on every lane, and
 // each fragment is written at its pixel's offset plus its rank in the pixel's
-// list (the rank the count pass sized).
+// list (the rank the count pass sized). The producer fetches the raw face
+// records of chunk c+1 with cp.async while it sets up chunk c.
 __global__ void __launch_bounds__(kPipeThreads, 4) k_fill(const uint64_t* __restrict__ tile_off,
-                                                       const uint32_t* __restrict__ bins,
-                                                       const uint32_t* __restrict__ masks,
-                                                       const int4* __restrict__ fx, const int4* __restrict__ fy,
-                                                       const uint4* __restrict__ fz, const float4* __restrict__ fed,
-                                                       const uint32_t* __restrict__ fflags,
-                                                       const float4* __restrict__ fimp, const float4* __restrict__ fpx,
-                                                       const float4* __restrict__ fpy, const float4* __restrict__ fpz,
-                                                       int tiles_x, int W, int H, ShadeParams sp,
-                                                       const uint64_t* __restrict__ off, uint64_t* __restrict__ key,
-                                                       float4* __restrict__ rgba,
-                                                       unsigned long long* __restrict__ err)
+                                                          const uint32_t* __restrict__ bins,
+                                                          const uint32_t* __restrict__ masks,
+                                                          const int4* __restrict__ fx, const int4* __restrict__ fy,
+                                                          const uint4* __restrict__ fz, const float4* __restrict__ fed,
+                                                          const uint32_t* __restrict__ fflags,
+                                                          const float4* __restrict__ fimp,
+                                                          const float4* __restrict__ fpx,
+                                                          const float4* __restrict__ fpy,
+                                                          const float4* __restrict__ fpz,
+                                                          const uint32_t* __restrict__ order, int tiles_x, int W,
+                                                          int H, ShadeParams sp, const uint64_t* __restrict__ off,
+                                                          uint64_t* __restrict__ key, float4* __restrict__ rgba,
+                                                          unsigned long long* __restrict__ err)
 {
     extern __shared__ __align__(16) unsigned char fill_smem[];
-    FillSlot* s_ring = reinterpret_cast<FillSlot*>(fill_smem);                              // [kRing]
-    uint32_t* s_qall = reinterpret_cast<uint32_t*>(fill_smem + kRing * sizeof(FillSlot));  // [warps][kChunk*32]
+    FillSlot* s_ring = reinterpret_cast<FillSlot*>(fill_smem);                                   // [kRing]
+    RawFace* s_raw = reinterpret_cast<RawFace*>(fill_smem + kRing * sizeof(FillSlot));          // [2][kChunk]
+    uint32_t* s_qall = reinterpret_cast<uint32_t*>(s_raw + 2 * kChunk);                         // [warps][kQCap]
     __shared__ uint64_t s_base[kTilePix];
     __shared__ uint32_t s_len[kTilePix];
     __shared__ __align__(8) uint64_t s_full[kRing], s_empty[kRing];
-    const int tile = blockIdx.x;
+    const int tile = (int)order[blockIdx.x];
     const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
     const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
     const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
@@ -476,32 +630,44 @@ __global__ void __launch_bounds__(kPipeThreads, 4) k_fill(const uint64_t* __rest
     pipe_init(s_full, s_empty);
 
     if (warp == kConsumerWarps) {  // producer
-        uint32_t f2t = n_chunks > 0 ? bins[beg + lane] : kPadBin;
+        uint32_t f2t_c = n_chunks > 0 ? bins[beg + lane] : kPadBin;
+        uint32_t f2t_n = n_chunks > 1 ? bins[beg + kChunk + lane] : kPadBin;
+        if (f2t_c != kPadBin) raw_fetch(s_raw[lane], f2t_c >> 1, fx, fy, fz, fed, fflags, fimp, fpx, fpy, fpz);
+        cp_async_commit();
         for (uint32_t c = 0; c < n_chunks; ++c) {
             const int s = c % kRing;
-            const uint32_t f2t_next = c + 1 < n_chunks ? bins[beg + (uint64_t)(c + 1) * kChunk + lane] : kPadBin;
-            int4 a = make_int4(0, 0, 0, 0), b = a;
-            if (f2t != kPadBin) { a = fx[f2t >> 1]; b = fy[f2t >> 1]; }
+            uint32_t f2t_nn = kPadBin;
+            if (c + 1 < n_chunks) {
+                if (f2t_n != kPadBin)
+                    raw_fetch(s_raw[((c + 1) & 1) * kChunk + lane], f2t_n >> 1, fx, fy, fz, fed, fflags, fimp, fpx,
+                              fpy, fpz);
+                if (c + 2 < n_chunks) f2t_nn = bins[beg + (uint64_t)(c + 2) * kChunk + lane];
+            }
+            cp_async_commit();
+            cp_async_wait<1>();   // this lane's copies of chunk c have landed
             if (!mbar_wait(&s_empty[s], ((c / kRing) & 1) ^ 1)) {
                 if (lane == 0) atomicOr(err, kErrWait);
                 break;
             }
             FillSlot& S = s_ring[s];
-            if (f2t != kPadBin) {
+            if (f2t_c != kPadBin) {
+                const RawFace& r = s_raw[(c & 1) * kChunk + lane];
                 TriGeom t;
-                stage_cov(a, b, f2t, W, H, px0, py0, S.c, lane, t);
-                if (S.c.box[lane] != 0) stage_shade(a, b, fz, fed, fflags, fimp, fpx, fpy, fpz, f2t, t, S.sh, lane);
+                stage_cov(r.fx, r.fy, f2t_c, W, H, px0, py0, S.c, lane, t);
+                if (S.c.box[lane] != 0) stage_shade(r, f2t_c, t, S.sh, lane);
             } else {
                 S.c.box[lane] = 0;
             }
             mbar_arrive(&s_full[s]);
-            f2t = f2t_next;
+            f2t_c = f2t_n;
+            f2t_n = f2t_nn;
         }
+        cp_async_wait<0>();
         return;
     }
     // consumers: lane = pixel of rows 2*warp and 2*warp + 1
     const int p = threadIdx.x;
-    uint32_t* q = s_qall + warp * (kChunk * 32);
+    uint32_t* q = s_qall + warp * kQCap;
     uint32_t k_run = 0;
     bool bad = false;
     // masks of the next two chunks are in flight while this one is shaded
@@ -509,7 +675,7 @@ __global__ void __launch_bounds__(kPipeThreads, 4) k_fill(const uint64_t* __rest
     uint32_t mk_b = n_chunks > 1 ? masks[(beg / kChunk + 1) * kTilePix + p] : 0u;
     for (uint32_t c = 0; c < n_chunks; ++c) {
         const int s = c % kRing;
-        uint32_t mk = mk_a;
+        const uint32_t mk = mk_a;
         mk_a = mk_b;
         if (c + 2 < n_chunks) mk_b = masks[(beg / kChunk + c + 2) * kTilePix + p];
         if (!mbar_wait(&s_full[s], (c / kRing) & 1)) {
@@ -525,37 +691,46 @@ __global__ void __launch_bounds__(kPipeThreads, 4) k_fill(const uint64_t* __rest
             if (lane >= o) incl += y;
         }
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        uint32_t r = incl - h;
-        while (mk) {
-            const uint32_t j = __ffs(mk) - 1;
-            mk &= mk - 1;
-            q[r++] = j | ((uint32_t)lane << 5) | (k_run++ << 10);
-        }
-        __syncwarp();
+        const uint32_t r0 = incl - h;
         const FillSlot& S = s_ring[s];
-        for (uint32_t e = lane; e < total; e += 32) {
-            const uint32_t qe = q[e];
-            const int j = (int)(qe & 31u);
-            const uint32_t pl = warp * 32 + ((qe >> 5) & 31u), kk = qe >> 10;
-            const int lx = (int)(pl & (kTile - 1)), ly = (int)(pl / kTile);
-            const int px = px0 + lx, py = py0 + ly;
-            const int bx = S.c.box[j];
-            // exact weights of vertices 1 and 2 (edge functions opposite them)
-            const int32_t sxr = (lx - box_lx0(bx)) << 8, syr = (ly - box_ly0(bx)) << 8;
-            const int64_t l1 = S.c.e0[1][j] + (int64_t)S.c.dx[1][j] * syr - (int64_t)S.c.dy[1][j] * sxr;
-            const int64_t l2 = S.c.e0[2][j] + (int64_t)S.c.dx[2][j] * syr - (int64_t)S.c.dy[2][j] * sxr;
-            const uint32_t z = sample_depth_fast(S.sh.z[0][j], S.sh.z[1][j], S.sh.z[2][j], l1, l2, S.sh.area[j],
-                                                 S.sh.inv_area[j], bad);
-            const float4 col = shade_fragment(S.sh, j, l1, l2, px, py, sp);
-            if (kk < s_len[pl]) {  // the count pass sized this list; never write past it
-                const uint64_t o = s_base[pl] + kk;
-                key[o] = ((uint64_t)z << 32) | (uint64_t)S.sh.f2t[j];
-                rgba[o] = col;
-            } else {
-                bad = true;
+        for (uint32_t w0 = 0; w0 < total; w0 += kQCap) {
+            uint32_t m2 = mk, r = r0, t = 0;
+            while (m2) {
+                const uint32_t j = __ffs(m2) - 1;
+                m2 &= m2 - 1;
+                if (r >= w0 && r < w0 + kQCap) q[r - w0] = j | ((uint32_t)lane << 5) | ((k_run + t) << 10);
+                ++r;
+                ++t;
             }
+            __syncwarp();
+            const uint32_t nq = min((uint32_t)kQCap, total - w0);
+            for (uint32_t e = lane; e < nq; e += 32) {
+                const uint32_t qe = q[e];
+                const int j = (int)(qe & 31u);
+                const uint32_t pl = warp * 32 + ((qe >> 5) & 31u), kk = qe >> 10;
+                const int lx = (int)(pl & (kTile - 1)), ly = (int)(pl / kTile);
+                const int px = px0 + lx, py = py0 + ly;
+                const int bx = S.c.box[j];
+                // exact weights of vertices 1 and 2 (edge functions opposite them)
+                const int32_t sxr = (lx - box_lx0(bx)) << 8, syr = (ly - box_ly0(bx)) << 8;
+                const int64_t l1 = S.c.e0[1][j] + (int64_t)S.c.dx[1][j] * syr - (int64_t)S.c.dy[1][j] * sxr;
+                const int64_t l2 = S.c.e0[2][j] + (int64_t)S.c.dx[2][j] * syr - (int64_t)S.c.dy[2][j] * sxr;
+                const float ia = S.sh.inv_area[j];
+                const float lam1 = u64_to_f32((uint64_t)l1) * ia, lam2 = u64_to_f32((uint64_t)l2) * ia;
+                const uint32_t z = sample_depth_lam(S.sh.z[0][j], S.sh.z[1][j], S.sh.z[2][j], l1, l2, S.sh.area[j],
+                                                    lam1, lam2, S.sh.dz[0][j], S.sh.dz[1][j], bad);
+                const float4 col = shade_fragment(S.sh, j, lam1, lam2, px, py, sp);
+                if (kk < s_len[pl]) {  // the count pass sized this list; never write past it
+                    const uint64_t o = s_base[pl] + kk;
+                    key[o] = ((uint64_t)z << 32) | (uint64_t)S.sh.f2t[j];
+                    rgba[o] = col;
+                } else {
+                    bad = true;
+                }
+            }
+            __syncwarp();
         }
-        __syncwarp();
+        k_run += h;
         if (lane == 0) mbar_arrive(&s_empty[s]);
     }
     if (bad) atomicOr(err, 1ull);
@@ -593,21 +768,29 @@ cudaError_t launch_bin_sort(FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_
     return cudaGetLastError();
 }
 
+cudaError_t launch_tile_order(FrameBufs& fb, int n_tiles, cudaStream_t s)
+{
+    k_tile_order<<<1, 1024, 0, s>>>(fb.tile_off, n_tiles, fb.tile_order);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_count(FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, cudaStream_t s)
 {
-    k_count<<<(unsigned)(tiles_x * tiles_y), kTilePix, 0, s>>>(fb.tile_off, fb.bins, fb.fx, fb.fy, tiles_x, W, H,
-                                                                fb.cnt, fb.masks);
+    const size_t smem = kConsumerWarps * sizeof(CountWarp);
+    cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_count<<<(unsigned)(tiles_x * tiles_y), kTilePix, smem, s>>>(fb.tile_off, fb.bins, fb.fx, fb.fy, fb.tile_order,
+                                                                   tiles_x, W, H, fb.cnt, fb.masks);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W,
                         int H, cudaStream_t s)
 {
-    const size_t smem = kRing * sizeof(FillSlot) + (size_t)kConsumerWarps * kChunk * 32 * sizeof(uint32_t);
+    const size_t smem = fill_smem_bytes();
     cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_fill<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, smem, s>>>(
-        fb.tile_off, fb.bins, fb.masks, fb.fx, fb.fy, fb.fz, fb.fed, fb.fflags, m.fimp, m.fpx, m.fpy, m.fpz, tiles_x,
-        W, H, sp, fb.off, fb.key, fb.rgba, reinterpret_cast<unsigned long long*>(fb.scal + 5));
+        fb.tile_off, fb.bins, fb.masks, fb.fx, fb.fy, fb.fz, fb.fed, fb.fflags, m.fimp, m.fpx, m.fpy, m.fpz,
+        fb.tile_order, tiles_x, W, H, sp, fb.off, fb.key, fb.rgba, reinterpret_cast<unsigned long long*>(fb.scal + 5));
     return cudaGetLastError();
 }
 

@@ -86,17 +86,22 @@ __device__ __forceinline__ int64_t floor_div_est(int64_t n, int64_t a, bool& bad
     return q;
 }
 
-// floor(n / a) as floor_div_est, from a float reciprocal of a (a > 0, |n / a| < 2^25).
-__device__ __forceinline__ int64_t floor_div_rcp(int64_t n, int64_t a, float inv_a, bool& bad)
+// Integer to float conversions on the FP32/integer pipes: the 64-bit
+// conversion instructions run on the FP64 unit, which is narrow on this part.
+// 2^23 + k for k < 2^23 is exactly the float with mantissa bits k.
+__device__ __forceinline__ float u16_to_f32(uint32_t k)   // k < 2^23, exact
 {
-    int64_t q = (int64_t)floorf((float)n * inv_a);
-    int64_t r = n - q * a;
-#pragma unroll 1
-    for (int it = 0; it < 16 && r < 0; ++it) { --q; r += a; }
-#pragma unroll 1
-    for (int it = 0; it < 16 && r >= a; ++it) { ++q; r -= a; }
-    if (r < 0 || r >= a) bad = true;
-    return q;
+    return __int_as_float(0x4B000000 | (int)k) - 8388608.f;
+}
+// Correctly rounded: one rounding of hi * 2^16 + lo, both exact.
+__device__ __forceinline__ float u32_to_f32_rn(uint32_t x)
+{
+    return fmaf(u16_to_f32(x >> 16), 65536.f, u16_to_f32(x & 0xFFFFu));
+}
+// 0 <= v < 2^55: correctly rounded below 2^32, else within 0.75 ulp.
+__device__ __forceinline__ float u64_to_f32(uint64_t v)
+{
+    return fmaf(u16_to_f32((uint32_t)(v >> 32)), 4294967296.f, u32_to_f32_rn((uint32_t)v));
 }
 
 // Per-sample depth: z0 + floor((l1 (z1 - z0) + l2 (z2 - z0)) / area), exact.
@@ -123,14 +128,26 @@ __device__ __forceinline__ uint32_t sample_depth(uint32_t z0, uint32_t z1, uint3
     return (uint32_t)((int64_t)z0 + q);
 }
 
-// sample_depth with a precomputed float reciprocal of the area (same result).
-__device__ __forceinline__ uint32_t sample_depth_fast(uint32_t z0, uint32_t z1, uint32_t z2, int64_t l1, int64_t l2,
-                                                      int64_t area, float inv_area, bool& bad)
+// sample_depth for a covered sample (l0, l1, l2 >= 0), from the float
+// barycentric weights lam1 ~ l1 / area, lam2 ~ l2 / area and the float depth
+// deltas dz1, dz2 (same result). With lam within 5 ulp and 0 <= lam <= 1,
+// |d| < 2^24, the float estimate is within 8 of the quotient; the integer
+// remainder then corrects it.
+__device__ __forceinline__ uint32_t sample_depth_lam(uint32_t z0, uint32_t z1, uint32_t z2, int64_t l1, int64_t l2,
+                                                     int64_t area, float lam1, float lam2, float dz1, float dz2,
+                                                     bool& bad)
 {
     if (area >= (1ll << 38)) return sample_depth(z0, z1, z2, l1, l2, area, bad);
-    const int64_t d1 = (int64_t)z1 - (int64_t)z0, d2 = (int64_t)z2 - (int64_t)z0;
+    const int32_t d1 = (int32_t)(z1 - z0), d2 = (int32_t)(z2 - z0);
+    int64_t q = __float2int_rd(fmaf(lam1, dz1, lam2 * dz2));
     // |l| <= area < 2^38 and |d| < 2^24: the numerator fits in int64
-    return (uint32_t)((int64_t)z0 + floor_div_rcp(l1 * d1 + l2 * d2, area, inv_area, bad));
+    int64_t r = l1 * d1 + l2 * d2 - q * area;
+#pragma unroll 1
+    for (int it = 0; it < 16 && r < 0; ++it) { --q; r += area; }
+#pragma unroll 1
+    for (int it = 0; it < 16 && r >= area; ++it) { ++q; r -= area; }
+    if (r < 0 || r >= area) bad = true;
+    return (uint32_t)((int64_t)z0 + q);
 }
 
 }  // namespace hexfc

@@ -15,6 +15,7 @@ struct ShadeSoA {
     float len2[4][kChunk];                  // their squared lengths
     float inv_len[4][kChunk];               // 1 / length
     uint32_t z[3][kChunk];                  // window depth of the triangle's vertices
+    float dz[2][kChunk];                    // z[1] - z[0], z[2] - z[0] (exact: |d| < 2^24)
     float inv_ed[3][kChunk];                // 1 / eye depth
     float imp[3][kChunk];                   // vertex importance
     float P[3][3][kChunk];                  // world position P[vertex][axis]
@@ -42,13 +43,12 @@ __device__ __forceinline__ float seg_dist2(const ShadeSoA& S, int j, int k, floa
 
 __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 
-// Eqs. 1-4 for one fragment of triangle j at pixel (px, py); l1, l2 are the
-// exact barycentric weights of vertices 1 and 2 (of a total equal to the
-// area). Returns the premultiplied RGBA of Eq. 4.
-__device__ __forceinline__ float4 shade_fragment(const ShadeSoA& t, int j, int64_t l1, int64_t l2, int px, int py,
+// Eqs. 1-4 for one fragment of triangle j at pixel (px, py); lam1, lam2 are
+// the screen-space barycentric weights of vertices 1 and 2. Returns the
+// premultiplied RGBA of Eq. 4.
+__device__ __forceinline__ float4 shade_fragment(const ShadeSoA& t, int j, float lam1, float lam2, int px, int py,
                                                  const ShadeParams& sp)
 {
-    const float lam1 = (float)l1 * t.inv_area[j], lam2 = (float)l2 * t.inv_area[j];
     const float lam0 = 1.f - lam1 - lam2;
     float b0, b1, b2, g = 1.f;
     if (sp.ortho) {
