@@ -101,13 +101,13 @@ void free_mesh(DevMesh* m)
     if (!m) return;
     dfree(m->verts); dfree(m->cells); dfree(m->cell_edges); dfree(m->cell_imp);
     dfree(m->vkey); dfree(m->ekey); dfree(m->vimp); dfree(m->eattr); dfree(m->elevel);
-    dfree(m->fverts); dfree(m->fedges); dfree(m->fimp); dfree(m->fpx); dfree(m->fpy); dfree(m->fpz);
+    dfree(m->fverts); dfree(m->fedges); dfree(m->frec);
     delete m;
 }
 
 void free_frame(FrameBufs& f)
 {
-    dfree(f.vproj); dfree(f.ved); dfree(f.fx); dfree(f.fy); dfree(f.fz); dfree(f.fed); dfree(f.fflags);
+    dfree(f.vproj); dfree(f.ved); dfree(f.tzsum);
     dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.tile_order); dfree(f.bins); dfree(f.masks); dfree(f.cnt);
     dfree(f.off);
     dfree(f.part); dfree(f.part_max); dfree(f.long_q); dfree(f.fix_q); dfree(f.key); dfree(f.rgba); dfree(f.scal);
@@ -208,6 +208,8 @@ ShadeParams make_shade(const hexfc_ctx* ctx)
     sp.g_max = s.g_max;
     sp.zref = (float)ctx->zref;
     sp.ortho = ctx->cam.ortho;
+    const float acc = 256.f * (2.f / 3.f) * s.w_base;
+    sp.accent_r2 = acc * acc;
     return sp;
 }
 
@@ -226,15 +228,7 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
         if ((st = ensure(&fb.vproj, &fb.v_cap, m->n_verts)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.ved, &c1, fb.v_cap)) != HEXFC_OK) return st;
     }
-    if (!fb.fx || fb.f_cap < m->n_faces) {
-        int64_t c1 = 0, c2 = 0, c3 = 0, c4 = 0;
-        dfree(fb.fy); dfree(fb.fz); dfree(fb.fed); dfree(fb.fflags);
-        if ((st = ensure(&fb.fx, &fb.f_cap, m->n_faces)) != HEXFC_OK) return st;
-        if ((st = ensure(&fb.fy, &c1, fb.f_cap)) != HEXFC_OK) return st;
-        if ((st = ensure(&fb.fz, &c2, fb.f_cap)) != HEXFC_OK) return st;
-        if ((st = ensure(&fb.fed, &c3, fb.f_cap)) != HEXFC_OK) return st;
-        if ((st = ensure(&fb.fflags, &c4, fb.f_cap)) != HEXFC_OK) return st;
-    }
+    if ((st = ensure(&fb.tzsum, &fb.f_cap, 2 * m->n_faces)) != HEXFC_OK) return st;
     if (!fb.tile_cnt || fb.t_cap < n_tiles + 1) {
         int64_t c1 = 0, c2 = 0;
         int64_t c3 = 0;
@@ -294,10 +288,10 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
     mark(ctx, 4, s);
     CK(cudaMemsetAsync(fb.bins, 0xFF, sizeof(uint32_t) * (size_t)n_bins, s));   // padding slots = kPadBin
     CK(launch_bin_fill(*m, fb, tiles_x, W, H, ctx->reverse_bins, s));
-    CK(launch_bin_sort(fb, tiles_x, tiles_y, s));
+    CK(launch_bin_sort(*m, fb, tiles_x, tiles_y, s));
     CK(launch_tile_order(fb, n_tiles, s));
     mark(ctx, 5, s);
-    CK(launch_count(fb, tiles_x, tiles_y, W, H, s));
+    CK(launch_count(*m, fb, tiles_x, tiles_y, W, H, s));
     mark(ctx, 6, s);
     CK(scan_u32_to_u64(fb.cnt, fb.off, n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
     mark(ctx, 7, s);
@@ -436,10 +430,7 @@ hexfc_status hexfc_upload_mesh(hexfc_ctx* ctx, const float* verts, int64_t n_ver
     A(dalloc(&m->elevel, (size_t)t.n_edges));
     A(dalloc(&m->fverts, (size_t)t.n_faces));
     A(dalloc(&m->fedges, (size_t)t.n_faces));
-    A(dalloc(&m->fimp, (size_t)t.n_faces));
-    A(dalloc(&m->fpx, (size_t)t.n_faces));
-    A(dalloc(&m->fpy, (size_t)t.n_faces));
-    A(dalloc(&m->fpz, (size_t)t.n_faces));
+    A(dalloc(&m->frec, (size_t)t.n_faces));
     if (st != HEXFC_OK) {
         free_mesh(m);
         return st;
@@ -740,11 +731,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     FrameBufs fb;
     fb.vproj = a.take<int4>((size_t)m->n_verts);
     fb.ved = a.take<float>((size_t)m->n_verts);
-    fb.fx = a.take<int4>((size_t)m->n_faces);
-    fb.fy = a.take<int4>((size_t)m->n_faces);
-    fb.fz = a.take<uint4>((size_t)m->n_faces);
-    fb.fed = a.take<float4>((size_t)m->n_faces);
-    fb.fflags = a.take<uint32_t>((size_t)m->n_faces);
+    fb.tzsum = a.take<uint32_t>(2 * (size_t)m->n_faces);
     fb.tile_cnt = a.take<uint32_t>((size_t)n_tiles + 1);
     fb.tile_off = a.take<uint64_t>((size_t)n_tiles + 1);
     fb.tile_cur = a.take<uint32_t>((size_t)n_tiles + 1);
@@ -756,7 +743,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fb.part = a.take<uint64_t>(2 * (size_t)nparts);
     fb.part_max = a.take<uint32_t>(2 * (size_t)nparts);
     fb.scal = a.take<uint64_t>(16);
-    if (!fb.vproj || !fb.ved || !fb.fx || !fb.fy || !fb.fz || !fb.fed || !fb.fflags || !fb.tile_cnt ||
+    if (!fb.vproj || !fb.ved || !fb.tzsum || !fb.tile_cnt ||
         !fb.tile_off || !fb.tile_cur || !fb.tile_order || !fb.cnt || !fb.off || !fb.long_q || !fb.fix_q || !fb.part || !fb.part_max ||
         !fb.scal)
         return HEXFC_ERR_OVERFLOW;
@@ -784,9 +771,9 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     }
     CK(cudaMemsetAsync(fb.bins, 0xFF, sizeof(uint32_t) * (size_t)n_bins, s));   // padding slots = kPadBin
     CK(launch_bin_fill(*m, fb, tiles_x, W, H, ctx->reverse_bins, s));
-    CK(launch_bin_sort(fb, tiles_x, tiles_y, s));
+    CK(launch_bin_sort(*m, fb, tiles_x, tiles_y, s));
     CK(launch_tile_order(fb, n_tiles, s));
-    CK(launch_count(fb, tiles_x, tiles_y, W, H, s));
+    CK(launch_count(*m, fb, tiles_x, tiles_y, W, H, s));
     CK(scan_u32_to_u64(fb.cnt, fb.off, n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
     CK(cudaMemcpyAsync(h, fb.scal, 6 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

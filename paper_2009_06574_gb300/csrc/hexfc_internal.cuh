@@ -35,7 +35,25 @@ struct ShadeParams {
     float accent_beta, halo_scale, darken, g_min, g_max;
     float zref;
     int ortho;
+    float accent_r2;   // (256 * 2/3 * w_base)^2: accentuation radius squared, 1/256-pixel units
 };
+
+// One face in one 128-byte line. The face stage of every frame rewrites the
+// first half (window corners, depths, edge flags, eye depths); the static half
+// (corner importance and world position) is rewritten when importance changes.
+struct __align__(128) FaceRec {
+    int4 X, Y;            // corner window position, 16.8 fixed point
+    uint4 Z;              // bits 0-23: corner window depth (z24); Z.x bits 24-31: edge flags
+                          // (bits 0-3 visible in focus, 4-7 visible in context); Z.y bits 24-25:
+                          // triangle 0 / 1 drawn
+    float4 ed;            // corner eye depth
+    float4 imp;           // corner importance
+    float4 px, py, pz;    // corner world position
+};
+static_assert(sizeof(FaceRec) == 128, "one line per face");
+constexpr uint32_t kZ24 = 0xFFFFFFu;
+__host__ __device__ inline uint32_t face_edge_flags(const uint4& z) { return z.x >> 24; }
+__host__ __device__ inline uint32_t face_tris(const uint4& z) { return (z.y >> 24) & 3u; }
 
 // Resident mesh (device pointers), see hexfc_upload_mesh.
 struct DevMesh {
@@ -51,10 +69,7 @@ struct DevMesh {
     uint8_t* elevel = nullptr;     // [E]
     int4* fverts = nullptr;        // [F] canonical corners
     int4* fedges = nullptr;        // [F] unique edge id of local edge k = (c_k, c_k+1)
-    float4* fimp = nullptr;        // [F] corner importance
-    float4* fpx = nullptr;         // [F] corner world x (y, z below)
-    float4* fpy = nullptr;
-    float4* fpz = nullptr;
+    FaceRec* frec = nullptr;       // [F] face records (the per-frame half is scratch of the current frame)
 };
 
 // Per-frame buffers owned by the context.
@@ -63,12 +78,8 @@ struct FrameBufs {
     int4* vproj = nullptr;   // {X, Y, z24, valid}
     float* ved = nullptr;    // eye depth
     int64_t v_cap = 0;
-    // face stage
-    int4* fx = nullptr;      // corner X (16.8)
-    int4* fy = nullptr;      // corner Y (16.8)
-    uint4* fz = nullptr;     // corner z24
-    float4* fed = nullptr;   // corner eye depth
-    uint32_t* fflags = nullptr;  // bits 0-3 focus-visible edges, 4-7 context-visible, 8-9 triangle valid
+    // faces
+    uint32_t* tzsum = nullptr;      // [2F] per triangle (2 face + tri): sum of its window depths
     int64_t f_cap = 0;
     // tiles
     uint32_t* tile_cnt = nullptr;   // [T+1]
@@ -108,9 +119,10 @@ cudaError_t launch_face_setup(const DevMesh& m, const CamParams& cam, int lod, f
                               FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_t s);
 cudaError_t launch_bin_fill(const DevMesh& m, FrameBufs& fb, int tiles_x, int W, int H, int reverse,
                             cudaStream_t s);
-cudaError_t launch_bin_sort(FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_t s);
+cudaError_t launch_bin_sort(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_t s);
 cudaError_t launch_tile_order(FrameBufs& fb, int n_tiles, cudaStream_t s);
-cudaError_t launch_count(FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, cudaStream_t s);
+cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int W, int H,
+                         cudaStream_t s);
 cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x,
                         int tiles_y, int W, int H, cudaStream_t s);
 cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W,

@@ -23,7 +23,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpList = kWarpSortMax;   // longest list a warp resolves
-constexpr int kWarps = kTilePix / 32;     // warps per composite block
 
 struct CT { float r, g, b, t; };  // premultiplied colour and transmittance
 

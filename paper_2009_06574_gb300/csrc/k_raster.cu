@@ -70,10 +70,8 @@ __device__ __forceinline__ void tile_range(const TriGeom& t, int& tx0, int& ty0,
 __global__ void k_face_setup(const int4* __restrict__ fverts, const int4* __restrict__ fedges,
                              const uint8_t* __restrict__ elevel, const float* __restrict__ eattr,
                              const int4* __restrict__ vproj, const float* __restrict__ ved, int64_t n_faces,
-                             int lod, float delta, int W, int H, int tiles_x,
-                             int4* __restrict__ fx, int4* __restrict__ fy, uint4* __restrict__ fz,
-                             float4* __restrict__ fed, uint32_t* __restrict__ fflags,
-                             uint32_t* __restrict__ tile_cnt)
+                             int lod, float delta, int W, int H, int tiles_x, FaceRec* __restrict__ frec,
+                             uint32_t* __restrict__ tzsum, uint32_t* __restrict__ tile_cnt)
 {
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= n_faces) return;
@@ -91,7 +89,7 @@ __global__ void k_face_setup(const int4* __restrict__ fverts, const int4* __rest
     }
     int4 e = fedges[f];
     int eid[4] = {e.x, e.y, e.z, e.w};
-    uint32_t flags = 0;
+    uint32_t flags = 0, tris = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         bool vis_c = (int)elevel[eid[k]] >= lod;
@@ -106,34 +104,35 @@ __global__ void k_face_setup(const int4* __restrict__ fverts, const int4* __rest
         TriGeom t;
         tri_setup(X, Y, tri, W, H, t);
         if (!t.valid) continue;
-        flags |= 1u << (8 + tri);
+        tris |= 1u << tri;
         int tx0, ty0, tx1, ty1;
         tile_range(t, tx0, ty0, tx1, ty1);
         for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(tile_cnt + ty * tiles_x + tx, 1u);
     }
-    fx[f] = make_int4(X[0], X[1], X[2], X[3]);
-    fy[f] = make_int4(Y[0], Y[1], Y[2], Y[3]);
-    fz[f] = make_uint4(Z[0], Z[1], Z[2], Z[3]);
-    fed[f] = make_float4(E[0], E[1], E[2], E[3]);
-    fflags[f] = flags;
+    FaceRec& r = frec[f];   // the per-frame half of the line
+    r.X = make_int4(X[0], X[1], X[2], X[3]);
+    r.Y = make_int4(Y[0], Y[1], Y[2], Y[3]);
+    r.Z = make_uint4((Z[0] & kZ24) | (flags << 24), (Z[1] & kZ24) | (tris << 24), Z[2] & kZ24, Z[3] & kZ24);
+    r.ed = make_float4(E[0], E[1], E[2], E[3]);
+    const uint32_t z0 = Z[0] & kZ24, z1 = Z[1] & kZ24, z2 = Z[2] & kZ24, z3 = Z[3] & kZ24;
+    reinterpret_cast<uint2*>(tzsum)[f] = make_uint2(z0 + z1 + z2, z0 + z2 + z3);   // < 3 * 2^24
 }
 
-__global__ void k_bin_fill(const int4* __restrict__ fx, const int4* __restrict__ fy,
-                           const uint32_t* __restrict__ fflags, int64_t n_faces, int W, int H, int tiles_x,
+__global__ void k_bin_fill(const FaceRec* __restrict__ frec, int64_t n_faces, int W, int H, int tiles_x,
                            int reverse, const uint64_t* __restrict__ tile_off, uint32_t* __restrict__ tile_cur,
                            uint32_t* __restrict__ bins)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_faces) return;
     int64_t f = reverse ? (n_faces - 1 - i) : i;
-    uint32_t flags = fflags[f];
-    if ((flags & (3u << 8)) == 0) return;
-    int4 a = fx[f], b = fy[f];
+    const uint32_t tris = face_tris(frec[f].Z);
+    if (tris == 0) return;
+    int4 a = frec[f].X, b = frec[f].Y;
     int32_t X[4] = {a.x, a.y, a.z, a.w}, Y[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
     for (int tri = 0; tri < 2; ++tri) {
-        if (!(flags & (1u << (8 + tri)))) continue;
+        if (!(tris & (1u << tri))) continue;
         TriGeom t;
         tri_setup(X, Y, tri, W, H, t);
         int tx0, ty0, tx1, ty1;
@@ -159,7 +158,7 @@ constexpr int kDepthBuckets = 2048;
 // sorted or nearly sorted (order within a bucket is arbitrary).
 __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ tile_off,
                                                   const uint32_t* __restrict__ tile_cnt, uint32_t* __restrict__ bins,
-                                                  const uint4* __restrict__ fz)
+                                                  const uint32_t* __restrict__ tzsum)
 {
     __shared__ uint32_t s_hist[kDepthBuckets];
     __shared__ uint16_t s_b[kBinSortMax];
@@ -170,10 +169,7 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
     const uint32_t n = tile_cnt[tile];   // real entries; the rest of the padded list is kPadBin
     if (n < 2 || n > (uint32_t)kBinSortMax) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    auto zsum = [&](uint32_t f2t) -> uint32_t {
-        const uint4 z = fz[f2t >> 1];
-        return z.x + ((f2t & 1) ? z.z + z.w : z.y + z.z);   // < 3 * 2^24
-    };
+    auto zsum = [&](uint32_t f2t) -> uint32_t { return tzsum[f2t]; };   // sum of the triangle's window depths
     // depth range of the tile's triangles
     uint32_t zmin = 0xFFFFFFFFu, zmax = 0;
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -365,12 +361,12 @@ __device__ __forceinline__ bool cover_at(const CovSoA& c, int j, int rx, int ry,
 //
 // k_fill runs one block per tile as a pipeline: a producer warp stages each
 // chunk of 32 triangles of the tile's (depth-ordered) list into a ring of
-// kRing slots in shared memory, and eight consumer warps each own two rows of
-// the tile (32 pixels, one per lane). Slots are handed over with mbarriers
-// (full: the 32 producer lanes arrive; empty: the 8 consumer warps arrive), so
-// the warps drift apart by up to kRing chunks instead of meeting at a block
-// barrier for every chunk. Every wait is bounded; a wait that runs out sets an
-// error bit and ends the kernel's loops.
+// kRing slots in shared memory, while the eight consumer warps shade the
+// covered samples of earlier chunks. Slots are handed over with mbarriers
+// (full: the 32 producer lanes arrive; empty: one consumer thread arrives once
+// no queued sample refers to the slot), so the producer runs up to kRing
+// chunks ahead. Every wait is bounded; a wait that runs out sets an error bit
+// and ends the kernel's loops.
 
 constexpr int kRing = 3;
 constexpr int kConsumerWarps = kTilePix / 32;
@@ -382,7 +378,7 @@ __device__ __forceinline__ void pipe_init(uint64_t* full, uint64_t* empty)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kRing; ++s) {
             mbar_init(&full[s], 32);
-            mbar_init(&empty[s], kConsumerWarps);
+            mbar_init(&empty[s], 1);
         }
         mbar_init_fence();
     }
@@ -450,7 +446,7 @@ __device__ __forceinline__ bool cover_fast(const CountWarp& me, int j, int rx, i
 // per-pixel totals are summed at the end.
 __global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__ tile_off,
                                                     const uint32_t* __restrict__ bins,
-                                                    const int4* __restrict__ fx, const int4* __restrict__ fy,
+                                                    const FaceRec* __restrict__ frec,
                                                     const uint32_t* __restrict__ order, int tiles_x, int W, int H,
                                                     uint32_t* __restrict__ cnt, uint32_t* __restrict__ masks)
 {
@@ -470,7 +466,7 @@ __global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__
     uint32_t f2t = warp < (int)n_chunks ? bins[beg + (uint64_t)warp * kChunk + lane] : kPadBin;
     for (uint32_t c = warp; c < n_chunks; c += kConsumerWarps) {
         int4 a = make_int4(0, 0, 0, 0), b = a;
-        if (f2t != kPadBin) { a = fx[f2t >> 1]; b = fy[f2t >> 1]; }
+        if (f2t != kPadBin) { a = frec[f2t >> 1].X; b = frec[f2t >> 1].Y; }
         const uint32_t f2t_next =
             c + kConsumerWarps < n_chunks ? bins[beg + (uint64_t)(c + kConsumerWarps) * kChunk + lane] : kPadBin;
         if (f2t != kPadBin) {
@@ -513,67 +509,61 @@ __global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__
 
 // ------------------------------------------------------------------ fill + shade
 
-// Raw per-face records of one triangle, fetched asynchronously by the producer.
-struct RawFace {
-    int4 fx, fy;
-    uint4 fz;
-    float4 fed, fimp, fpx, fpy, fpz;
-    uint32_t flags, pad[3];
-};
-
-__device__ __forceinline__ void raw_fetch(RawFace& r, uint32_t f, const int4* __restrict__ fx,
-                                          const int4* __restrict__ fy, const uint4* __restrict__ fz,
-                                          const float4* __restrict__ fed, const uint32_t* __restrict__ fflags,
-                                          const float4* __restrict__ fimp, const float4* __restrict__ fpx,
-                                          const float4* __restrict__ fpy, const float4* __restrict__ fpz)
+// Producer lane: fetch face record f (one line) into shared memory.
+__device__ __forceinline__ void rec_fetch(FaceRec& r, const FaceRec* __restrict__ frec, uint32_t f)
 {
-    cp_async16(&r.fx, fx + f);
-    cp_async16(&r.fy, fy + f);
-    cp_async16(&r.fz, fz + f);
-    cp_async16(&r.fed, fed + f);
-    cp_async16(&r.fimp, fimp + f);
-    cp_async16(&r.fpx, fpx + f);
-    cp_async16(&r.fpy, fpy + f);
-    cp_async16(&r.fpz, fpz + f);
-    cp_async4(&r.flags, fflags + f);
+    const int4* src = reinterpret_cast<const int4*>(frec + f);
+    int4* dst = reinterpret_cast<int4*>(&r);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) cp_async16(dst + k, src + k);
 }
 
-__device__ __forceinline__ void stage_shade(const RawFace& r, uint32_t f2t, const TriGeom& t, ShadeSoA& S, int j)
+__device__ __forceinline__ void stage_shade(const FaceRec& r, uint32_t f2t, const TriGeom& t, bool ortho,
+                                            ShadeSoA& S, int j)
 {
-    const int32_t FX[4] = {r.fx.x, r.fx.y, r.fx.z, r.fx.w}, FY[4] = {r.fy.x, r.fy.y, r.fy.z, r.fy.w};
+    const int32_t FX[4] = {r.X.x, r.X.y, r.X.z, r.X.w}, FY[4] = {r.Y.x, r.Y.y, r.Y.z, r.Y.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int k1 = (k + 1) & 3;
         S.FX[k][j] = (float)FX[k];   // |coordinate| <= 2^22: exact
         S.FY[k][j] = (float)FY[k];
         const int32_t ex = FX[k1] - FX[k], ey = FY[k1] - FY[k];
-        S.ex[k][j] = (float)ex;
-        S.ey[k][j] = (float)ey;
         const float l2 = u64_to_f32((uint64_t)((int64_t)ex * ex + (int64_t)ey * ey));
-        S.len2[k][j] = l2;
-        S.inv_len[k][j] = l2 > 0.f ? rsqrtf(l2) : 0.f;
+        S.inv_len2[k][j] = l2 > 0.f ? 1.f / l2 : 0.f;
     }
-    const uint32_t zz[4] = {r.fz.x, r.fz.y, r.fz.z, r.fz.w};
-    const float ee[4] = {r.fed.x, r.fed.y, r.fed.z, r.fed.w}, ii[4] = {r.fimp.x, r.fimp.y, r.fimp.z, r.fimp.w};
-    const float xx[4] = {r.fpx.x, r.fpx.y, r.fpx.z, r.fpx.w}, yy[4] = {r.fpy.x, r.fpy.y, r.fpy.z, r.fpy.w};
-    const float ww[4] = {r.fpz.x, r.fpz.y, r.fpz.z, r.fpz.w};
+    const uint32_t zz[4] = {r.Z.x & kZ24, r.Z.y & kZ24, r.Z.z & kZ24, r.Z.w & kZ24};
+    const float ee[4] = {r.ed.x, r.ed.y, r.ed.z, r.ed.w}, ii[4] = {r.imp.x, r.imp.y, r.imp.z, r.imp.w};
+    const float xx[4] = {r.px.x, r.px.y, r.px.z, r.px.w}, yy[4] = {r.py.x, r.py.y, r.py.z, r.py.w};
+    const float ww[4] = {r.pz.x, r.pz.y, r.pz.z, r.pz.w};
+    float q[3], a[3], P[3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int c = t.vi[k];
         // select corner c without dynamic register indexing
         S.z[k][j] = c == 0 ? zz[0] : c == 1 ? zz[1] : c == 2 ? zz[2] : zz[3];
-        S.inv_ed[k][j] = 1.f / (c == 0 ? ee[0] : c == 1 ? ee[1] : c == 2 ? ee[2] : ee[3]);
-        S.imp[k][j] = c == 0 ? ii[0] : c == 1 ? ii[1] : c == 2 ? ii[2] : ii[3];
-        S.P[k][0][j] = c == 0 ? xx[0] : c == 1 ? xx[1] : c == 2 ? xx[2] : xx[3];
-        S.P[k][1][j] = c == 0 ? yy[0] : c == 1 ? yy[1] : c == 2 ? yy[2] : yy[3];
-        S.P[k][2][j] = c == 0 ? ww[0] : c == 1 ? ww[1] : c == 2 ? ww[2] : ww[3];
+        q[k] = ortho ? 1.f : 1.f / (c == 0 ? ee[0] : c == 1 ? ee[1] : c == 2 ? ee[2] : ee[3]);
+        a[k] = (c == 0 ? ii[0] : c == 1 ? ii[1] : c == 2 ? ii[2] : ii[3]) * q[k];
+        P[k][0] = (c == 0 ? xx[0] : c == 1 ? xx[1] : c == 2 ? xx[2] : xx[3]) * q[k];
+        P[k][1] = (c == 0 ? yy[0] : c == 1 ? yy[1] : c == 2 ? yy[2] : yy[3]) * q[k];
+        P[k][2] = (c == 0 ? ww[0] : c == 1 ? ww[1] : c == 2 ? ww[2] : ww[3]) * q[k];
     }
     S.dz[0][j] = (float)(int32_t)(S.z[1][j] - S.z[0][j]);
     S.dz[1][j] = (float)(int32_t)(S.z[2][j] - S.z[0][j]);
+    S.q0[j] = q[0];
+    S.a0[j] = a[0];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        S.dq[k][j] = q[k + 1] - q[0];
+        S.da[k][j] = a[k + 1] - a[0];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) S.dp[k][d][j] = P[k + 1][d] - P[0][d];
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) S.p0[d][j] = P[0][d];
     S.area[j] = t.area;
     S.inv_area[j] = 1.f / u64_to_f32((uint64_t)t.area);
     S.f2t[j] = f2t;
-    S.masks[j] = r.flags & 0xFFu;
+    S.masks[j] = face_edge_flags(r.Z);
 }
 
 struct FillSlot {
@@ -581,40 +571,58 @@ struct FillSlot {
     ShadeSoA sh;
 };
 
-constexpr int kQCap = 512;   // queue entries per consumer warp; larger chunks are shaded in windows
+// Block queue of covered samples: entry = j | pixel << 5 | ring slot << 13 | rank << 15.
+constexpr int kQCap = 2048;            // entries (a power of two)
+constexpr int kQWin = 896;             // entries queued per window: leftovers + 2 windows fit in kQCap
+constexpr uint32_t kNoRank = 0x1FFFFu;   // rank of a sample beyond its list (never written)
+static_assert(kTilePix + 2 * kQWin <= kQCap, "queue windows");
+static_assert(kRing <= 4, "two bits of ring slot");
+
+constexpr size_t kRawOff = (kRing * sizeof(FillSlot) + 127) & ~(size_t)127;   // face records: 128-aligned
 
 __host__ __device__ constexpr size_t fill_smem_bytes()
 {
-    return kRing * sizeof(FillSlot) + 2 * kChunk * sizeof(RawFace) + (size_t)kConsumerWarps * kQCap * sizeof(uint32_t);
+    return kRawOff + 2 * kChunk * sizeof(FaceRec) + (size_t)kQCap * sizeof(uint32_t);
 }
 
+// Barrier 1 among the consumer warps only (the producer never joins it); the
+// non-aligned forms, since lanes may arrive apart. True on every consumer if
+// `p` holds on any of them.
+__device__ __forceinline__ bool consumers_sync_or(bool p)
+{
+    int r;
+    asm volatile(
+        "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n barrier.red.or.pred b, 1, %2, a;\n selp.s32 %0, 1, 0, b;\n}\n"
+        : "=r"(r)
+        : "r"((int)p), "n"(kTilePix)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void consumers_sync() { asm volatile("barrier.sync 1, %0;\n" ::"n"(kTilePix) : "memory"); }
+
 // Per tile: the coverage masks of the count pass give, chunk by chunk, each
-// lane's covered triangles; a warp compacts its covered samples into a queue
-// (pixel-major, in list order) so that the shading runs on every lane, and
-// each fragment is written at its pixel's offset plus its rank in the pixel's
-// list (the rank the count pass sized). The producer fetches the raw face
-// records of chunk c+1 with cp.async while it sets up chunk c.
-__global__ void __launch_bounds__(kPipeThreads, 4) k_fill(const uint64_t* __restrict__ tile_off,
+// pixel's covered triangles; the consumers compact the chunk's covered samples
+// into one queue (pixel-major, in list order) and shade it 256 samples at a
+// time, so that every lane has work, and each fragment is written at its
+// pixel's offset plus its rank in the pixel's list (the rank the count pass
+// sized). The producer fetches the face records of chunk c+1 with cp.async
+// while it sets up chunk c.
+__global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __restrict__ tile_off,
                                                           const uint32_t* __restrict__ bins,
                                                           const uint32_t* __restrict__ masks,
-                                                          const int4* __restrict__ fx, const int4* __restrict__ fy,
-                                                          const uint4* __restrict__ fz, const float4* __restrict__ fed,
-                                                          const uint32_t* __restrict__ fflags,
-                                                          const float4* __restrict__ fimp,
-                                                          const float4* __restrict__ fpx,
-                                                          const float4* __restrict__ fpy,
-                                                          const float4* __restrict__ fpz,
+                                                          const FaceRec* __restrict__ frec,
                                                           const uint32_t* __restrict__ order, int tiles_x, int W,
                                                           int H, ShadeParams sp, const uint64_t* __restrict__ off,
                                                           uint64_t* __restrict__ key, float4* __restrict__ rgba,
                                                           unsigned long long* __restrict__ err)
 {
-    extern __shared__ __align__(16) unsigned char fill_smem[];
-    FillSlot* s_ring = reinterpret_cast<FillSlot*>(fill_smem);                                   // [kRing]
-    RawFace* s_raw = reinterpret_cast<RawFace*>(fill_smem + kRing * sizeof(FillSlot));          // [2][kChunk]
-    uint32_t* s_qall = reinterpret_cast<uint32_t*>(s_raw + 2 * kChunk);                         // [warps][kQCap]
+    extern __shared__ __align__(128) unsigned char fill_smem[];
+    FillSlot* s_ring = reinterpret_cast<FillSlot*>(fill_smem);                                    // [kRing]
+    FaceRec* s_raw = reinterpret_cast<FaceRec*>(fill_smem + kRawOff);                            // [2][kChunk]
+    uint32_t* s_q = reinterpret_cast<uint32_t*>(s_raw + 2 * kChunk);                             // [kQCap]
     __shared__ uint64_t s_base[kTilePix];
     __shared__ uint32_t s_len[kTilePix];
+    __shared__ uint32_t s_wsum[kConsumerWarps];
     __shared__ __align__(8) uint64_t s_full[kRing], s_empty[kRing];
     const int tile = (int)order[blockIdx.x];
     const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
@@ -632,15 +640,13 @@ __global__ void __launch_bounds__(kPipeThreads, 4) k_fill(const uint64_t* __rest
     if (warp == kConsumerWarps) {  // producer
         uint32_t f2t_c = n_chunks > 0 ? bins[beg + lane] : kPadBin;
         uint32_t f2t_n = n_chunks > 1 ? bins[beg + kChunk + lane] : kPadBin;
-        if (f2t_c != kPadBin) raw_fetch(s_raw[lane], f2t_c >> 1, fx, fy, fz, fed, fflags, fimp, fpx, fpy, fpz);
+        if (f2t_c != kPadBin) rec_fetch(s_raw[lane], frec, f2t_c >> 1);
         cp_async_commit();
         for (uint32_t c = 0; c < n_chunks; ++c) {
             const int s = c % kRing;
             uint32_t f2t_nn = kPadBin;
             if (c + 1 < n_chunks) {
-                if (f2t_n != kPadBin)
-                    raw_fetch(s_raw[((c + 1) & 1) * kChunk + lane], f2t_n >> 1, fx, fy, fz, fed, fflags, fimp, fpx,
-                              fpy, fpz);
+                if (f2t_n != kPadBin) rec_fetch(s_raw[((c + 1) & 1) * kChunk + lane], frec, f2t_n >> 1);
                 if (c + 2 < n_chunks) f2t_nn = bins[beg + (uint64_t)(c + 2) * kChunk + lane];
             }
             cp_async_commit();
@@ -651,10 +657,10 @@ __global__ void __launch_bounds__(kPipeThreads, 4) k_fill(const uint64_t* __rest
             }
             FillSlot& S = s_ring[s];
             if (f2t_c != kPadBin) {
-                const RawFace& r = s_raw[(c & 1) * kChunk + lane];
+                const FaceRec& r = s_raw[(c & 1) * kChunk + lane];
                 TriGeom t;
-                stage_cov(r.fx, r.fy, f2t_c, W, H, px0, py0, S.c, lane, t);
-                if (S.c.box[lane] != 0) stage_shade(r, f2t_c, t, S.sh, lane);
+                stage_cov(r.X, r.Y, f2t_c, W, H, px0, py0, S.c, lane, t);
+                if (S.c.box[lane] != 0) stage_shade(r, f2t_c, t, sp.ortho != 0, S.sh, lane);
             } else {
                 S.c.box[lane] = 0;
             }
@@ -665,11 +671,36 @@ __global__ void __launch_bounds__(kPipeThreads, 4) k_fill(const uint64_t* __rest
         cp_async_wait<0>();
         return;
     }
-    // consumers: lane = pixel of rows 2*warp and 2*warp + 1
+    // consumers: thread p owns pixel p of the tile for the queue; any thread shades any entry
     const int p = threadIdx.x;
-    uint32_t* q = s_qall + warp * kQCap;
     uint32_t k_run = 0;
     bool bad = false;
+    // Queue positions are absolute counts (modulo kQCap): entries [head, tail) are
+    // queued. Only whole rounds of kTilePix entries are shaded; the rest waits
+    // for the next chunk unless it would keep an older chunk's slot (then it is
+    // shaded as a partial round), so at most the newest chunk's slot is held.
+    uint32_t head = 0, tail = 0, released = 0;
+    auto shade_entry = [&](uint32_t qe) {
+        const uint32_t kk = qe >> 15;
+        if (kk == kNoRank) return;
+        const int j = (int)(qe & 31u);
+        const uint32_t pl = (qe >> 5) & 255u;
+        const FillSlot& S = s_ring[(qe >> 13) & 3u];
+        const int lx = (int)(pl & (kTile - 1)), ly = (int)(pl / kTile);
+        const int bx = S.c.box[j];
+        // exact weights of vertices 1 and 2 (edge functions opposite them)
+        const int32_t sxr = (lx - box_lx0(bx)) << 8, syr = (ly - box_ly0(bx)) << 8;
+        const int64_t l1 = S.c.e0[1][j] + (int64_t)S.c.dx[1][j] * syr - (int64_t)S.c.dy[1][j] * sxr;
+        const int64_t l2 = S.c.e0[2][j] + (int64_t)S.c.dx[2][j] * syr - (int64_t)S.c.dy[2][j] * sxr;
+        const float ia = S.sh.inv_area[j];
+        const float lam1 = u64_to_f32((uint64_t)l1) * ia, lam2 = u64_to_f32((uint64_t)l2) * ia;
+        const uint32_t z = sample_depth_lam(S.sh.z[0][j], S.sh.z[1][j], S.sh.z[2][j], l1, l2, S.sh.area[j], lam1,
+                                            lam2, S.sh.dz[0][j], S.sh.dz[1][j], bad);
+        const float4 col = shade_fragment(S.sh, j, lam1, lam2, px0 + lx, py0 + ly, sp);
+        const uint64_t o = s_base[pl] + kk;
+        key[o] = ((uint64_t)z << 32) | (uint64_t)S.sh.f2t[j];
+        rgba[o] = col;
+    };
     // masks of the next two chunks are in flight while this one is shaded
     uint32_t mk_a = n_chunks > 0 ? masks[(beg / kChunk) * kTilePix + p] : 0u;
     uint32_t mk_b = n_chunks > 1 ? masks[(beg / kChunk + 1) * kTilePix + p] : 0u;
@@ -678,61 +709,61 @@ __global__ void __launch_bounds__(kPipeThreads, 4) k_fill(const uint64_t* __rest
         const uint32_t mk = mk_a;
         mk_a = mk_b;
         if (c + 2 < n_chunks) mk_b = masks[(beg / kChunk + c + 2) * kTilePix + p];
-        if (!mbar_wait(&s_full[s], (c / kRing) & 1)) {
-            if (lane == 0) atomicOr(err, kErrWait);
-            break;
-        }
-        // warp-wide exclusive scan of the hit counts
+        const bool ok = mbar_wait(&s_full[s], (c / kRing) & 1);
+        // block-wide exclusive scan of the hit counts (warp scan + the warp totals)
         const uint32_t h = __popc(mk);
         uint32_t incl = h;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        const uint32_t r0 = incl - h;
-        const FillSlot& S = s_ring[s];
-        for (uint32_t w0 = 0; w0 < total; w0 += kQCap) {
+        if (lane == 31) s_wsum[warp] = incl;
+        if (consumers_sync_or(!ok)) {   // every consumer leaves together
+            if (p == 0) atomicOr(err, kErrWait);
+            break;
+        }
+        // every entry queued before this chunk has been shaded by all threads,
+        // except leftovers of chunk c - 1: release the slots of the chunks before
+        const uint32_t rel_to = head == tail ? c : c - 1;
+        if (p == 0)
+            for (uint32_t r = released; r < rel_to; ++r) mbar_arrive(&s_empty[r % kRing]);
+        released = max(released, rel_to);
+        uint32_t r0 = incl - h, total = 0;
+#pragma unroll
+        for (int w = 0; w < kConsumerWarps; ++w) {
+            const uint32_t v = s_wsum[w];
+            r0 += w < warp ? v : 0u;
+            total += v;
+        }
+        const bool fits = k_run + h <= s_len[p];   // the count pass sized this list
+        bad = bad || !fits;
+        const uint32_t chunk_start = tail;
+        for (uint32_t w0 = 0; w0 < total; w0 += kQWin) {
             uint32_t m2 = mk, r = r0, t = 0;
             while (m2) {
                 const uint32_t j = __ffs(m2) - 1;
                 m2 &= m2 - 1;
-                if (r >= w0 && r < w0 + kQCap) q[r - w0] = j | ((uint32_t)lane << 5) | ((k_run + t) << 10);
+                if (r >= w0 && r < w0 + kQWin)
+                    s_q[(tail + r - w0) & (kQCap - 1)] =
+                        j | ((uint32_t)p << 5) | ((uint32_t)s << 13) | ((fits ? k_run + t : kNoRank) << 15);
                 ++r;
                 ++t;
             }
-            __syncwarp();
-            const uint32_t nq = min((uint32_t)kQCap, total - w0);
-            for (uint32_t e = lane; e < nq; e += 32) {
-                const uint32_t qe = q[e];
-                const int j = (int)(qe & 31u);
-                const uint32_t pl = warp * 32 + ((qe >> 5) & 31u), kk = qe >> 10;
-                const int lx = (int)(pl & (kTile - 1)), ly = (int)(pl / kTile);
-                const int px = px0 + lx, py = py0 + ly;
-                const int bx = S.c.box[j];
-                // exact weights of vertices 1 and 2 (edge functions opposite them)
-                const int32_t sxr = (lx - box_lx0(bx)) << 8, syr = (ly - box_ly0(bx)) << 8;
-                const int64_t l1 = S.c.e0[1][j] + (int64_t)S.c.dx[1][j] * syr - (int64_t)S.c.dy[1][j] * sxr;
-                const int64_t l2 = S.c.e0[2][j] + (int64_t)S.c.dx[2][j] * syr - (int64_t)S.c.dy[2][j] * sxr;
-                const float ia = S.sh.inv_area[j];
-                const float lam1 = u64_to_f32((uint64_t)l1) * ia, lam2 = u64_to_f32((uint64_t)l2) * ia;
-                const uint32_t z = sample_depth_lam(S.sh.z[0][j], S.sh.z[1][j], S.sh.z[2][j], l1, l2, S.sh.area[j],
-                                                    lam1, lam2, S.sh.dz[0][j], S.sh.dz[1][j], bad);
-                const float4 col = shade_fragment(S.sh, j, lam1, lam2, px, py, sp);
-                if (kk < s_len[pl]) {  // the count pass sized this list; never write past it
-                    const uint64_t o = s_base[pl] + kk;
-                    key[o] = ((uint64_t)z << 32) | (uint64_t)S.sh.f2t[j];
-                    rgba[o] = col;
-                } else {
-                    bad = true;
-                }
-            }
-            __syncwarp();
+            consumers_sync();   // the window's entries are queued
+            tail += min((uint32_t)kQWin, total - w0);
+            const uint32_t rounds = (tail - head) / kTilePix;
+            for (uint32_t i = 0; i < rounds; ++i) shade_entry(s_q[(head + i * kTilePix + p) & (kQCap - 1)]);
+            head += rounds * kTilePix;
+        }
+        if (head < chunk_start) {   // leftovers of an older chunk: shade them all now
+            if (p < tail - head) shade_entry(s_q[(head + p) & (kQCap - 1)]);
+            head = tail;
         }
         k_run += h;
-        if (lane == 0) mbar_arrive(&s_empty[s]);
     }
+    // the last leftovers (the producer is done; no slot is released any more)
+    if (head < tail && p < tail - head) shade_entry(s_q[(head + p) & (kQCap - 1)]);
     if (bad) atomicOr(err, 1ull);
 }
 
@@ -750,21 +781,22 @@ cudaError_t launch_face_setup(const DevMesh& m, const CamParams& cam, int lod, f
     (void)tiles_y;
     k_face_setup<<<grid_for(m.n_faces, 256), 256, 0, s>>>(m.fverts, m.fedges, m.elevel, m.eattr, fb.vproj,
                                                            fb.ved, m.n_faces, lod, delta, cam.W, cam.H, tiles_x,
-                                                           fb.fx, fb.fy, fb.fz, fb.fed, fb.fflags, fb.tile_cnt);
+                                                           m.frec, fb.tzsum, fb.tile_cnt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bin_fill(const DevMesh& m, FrameBufs& fb, int tiles_x, int W, int H, int reverse,
                             cudaStream_t s)
 {
-    k_bin_fill<<<grid_for(m.n_faces, 256), 256, 0, s>>>(fb.fx, fb.fy, fb.fflags, m.n_faces, W, H, tiles_x, reverse,
+    k_bin_fill<<<grid_for(m.n_faces, 256), 256, 0, s>>>(m.frec, m.n_faces, W, H, tiles_x, reverse,
                                                          fb.tile_off, fb.tile_cur, fb.bins);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_sort(FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_t s)
+cudaError_t launch_bin_sort(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_t s)
 {
-    k_bin_sort<<<(unsigned)(tiles_x * tiles_y), 256, 0, s>>>(fb.tile_off, fb.tile_cnt, fb.bins, fb.fz);
+    (void)m;
+    k_bin_sort<<<(unsigned)(tiles_x * tiles_y), 256, 0, s>>>(fb.tile_off, fb.tile_cnt, fb.bins, fb.tzsum);
     return cudaGetLastError();
 }
 
@@ -774,11 +806,11 @@ cudaError_t launch_tile_order(FrameBufs& fb, int n_tiles, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_count(FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, cudaStream_t s)
+cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, cudaStream_t s)
 {
     const size_t smem = kConsumerWarps * sizeof(CountWarp);
     cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_count<<<(unsigned)(tiles_x * tiles_y), kTilePix, smem, s>>>(fb.tile_off, fb.bins, fb.fx, fb.fy, fb.tile_order,
+    k_count<<<(unsigned)(tiles_x * tiles_y), kTilePix, smem, s>>>(fb.tile_off, fb.bins, m.frec, fb.tile_order,
                                                                    tiles_x, W, H, fb.cnt, fb.masks);
     return cudaGetLastError();
 }
@@ -789,8 +821,8 @@ cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, 
     const size_t smem = fill_smem_bytes();
     cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_fill<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, smem, s>>>(
-        fb.tile_off, fb.bins, fb.masks, fb.fx, fb.fy, fb.fz, fb.fed, fb.fflags, m.fimp, m.fpx, m.fpy, m.fpz,
-        fb.tile_order, tiles_x, W, H, sp, fb.off, fb.key, fb.rgba, reinterpret_cast<unsigned long long*>(fb.scal + 5));
+        fb.tile_off, fb.bins, fb.masks, m.frec, fb.tile_order, tiles_x, W, H, sp, fb.off, fb.key, fb.rgba,
+        reinterpret_cast<unsigned long long*>(fb.scal + 5));
     return cudaGetLastError();
 }
 

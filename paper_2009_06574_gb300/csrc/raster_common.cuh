@@ -86,22 +86,13 @@ __device__ __forceinline__ int64_t floor_div_est(int64_t n, int64_t a, bool& bad
     return q;
 }
 
-// Integer to float conversions on the FP32/integer pipes: the 64-bit
-// conversion instructions run on the FP64 unit, which is narrow on this part.
-// 2^23 + k for k < 2^23 is exactly the float with mantissa bits k.
-__device__ __forceinline__ float u16_to_f32(uint32_t k)   // k < 2^23, exact
-{
-    return __int_as_float(0x4B000000 | (int)k) - 8388608.f;
-}
-// Correctly rounded: one rounding of hi * 2^16 + lo, both exact.
-__device__ __forceinline__ float u32_to_f32_rn(uint32_t x)
-{
-    return fmaf(u16_to_f32(x >> 16), 65536.f, u16_to_f32(x & 0xFFFFu));
-}
-// 0 <= v < 2^55: correctly rounded below 2^32, else within 0.75 ulp.
+// 0 <= v < 2^55 to float through 32-bit conversions (the 64-bit conversion
+// instructions run on the FP64 unit, which is narrow on this part): correctly
+// rounded below 2^32, else within 0.75 ulp (one rounding of hi * 2^32 + lo,
+// lo rounded first).
 __device__ __forceinline__ float u64_to_f32(uint64_t v)
 {
-    return fmaf(u16_to_f32((uint32_t)(v >> 32)), 4294967296.f, u32_to_f32_rn((uint32_t)v));
+    return fmaf((float)(uint32_t)(v >> 32), 4294967296.f, (float)(uint32_t)v);
 }
 
 // Per-sample depth: z0 + floor((l1 (z1 - z0) + l2 (z2 - z0)) / area), exact.
