@@ -28,10 +28,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# per-fragment / per-pixel / per-face algorithmic bytes of the kernels
+# Algorithmic bytes of the kernels: what the method must move, counted once
+# (a fragment record written by the fill and read by the composite, a face
+# record read once per frame), independent of how the kernels tile the work.
 FRAG_BYTES = 24          # 8 B key + 16 B premultiplied RGBA
-FACE_FRAME_BYTES = 68    # per-frame face record: X[4], Y[4], z24[4], eye depth[4], flags
-FACE_STATIC_BYTES = 64   # corner importance[4], world position[4][3]
+FACE_FRAME_BYTES = 64    # per-frame half of a face record: X[4], Y[4], z24[4] + flags, eye depth[4]
+FACE_STATIC_BYTES = 64   # static half: corner importance[4], world position[4][3]
 
 
 def parse_args():
@@ -200,6 +202,24 @@ def run_reference(args, rank, world):
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def replica_frames(rank: int, world: int, n_frames: int, start: int, count: int) -> list:
+    """Frames of the orbit a replica renders: rank r starts r/world of the way
+    along the path, so the replicas draw different views (weak scaling)."""
+    f0 = (rank * n_frames) // max(world, 1)
+    return [(f0 + start + i) % n_frames for i in range(count)]
+
+
+def reduce_replicas(ms: float, frag_sum: float, e2e_s: float, device) -> tuple:
+    """Job totals over the replicas: the slowest rank's timed span (device ms)
+    and end-to-end wall time, and the sum of the fragments drawn."""
+    import torch
+    t = torch.tensor([ms, e2e_s], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    fs = torch.tensor([frag_sum], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(fs)
+    return float(t[0].item()), float(fs.item()), float(t[1].item())
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -216,12 +236,10 @@ def run_ours(args, rank, world, local_rank):
     out = torch.empty((w.height, w.width, 4), dtype=torch.float32, device=dev)
     imp = torch.empty(mesh.n_cells, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    frame0 = rank * 7919  # replicas render different frames of the orbit
-
     frags = []
 
     def step(i):
-        f = (frame0 + i) % w.n_frames
+        f = replica_frames(rank, world, w.n_frames, i, 1)[0]
         r.set_view(w.view(f))
         r.set_lens(w.lens(f))
         r.cell_quality(mid, hexfc.HEXFC_METRIC_IMPORTANCE, imp, stream)
@@ -265,37 +283,31 @@ def run_ours(args, rank, world, local_rank):
     stage_ms, n_timed = r.stage_times(reset=True)
     r.set_option(hexfc.HEXFC_OPT_STAGE_TIMING, 0)
     frag_sum = float(sum(frags))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        fs = torch.tensor([frag_sum], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(fs)
-        frag_sum = float(fs.item())
 
     # ---- end to end through the C ABI with host buffers (image copied back every frame)
-    e2e = None
-    if rank == 0 or world > 1:
-        host = torch.empty((w.height, w.width, 4), dtype=torch.float32, pin_memory=True)
-        host_np = host.numpy()
-        ne = max(1, min(args.e2e_steps, args.steps))
-        for i in range(2):
-            r.set_view(w.view(i)); r.set_lens(w.lens(i))
-            r.render_host(mid, host_np, stream)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(ne):
-            f = (frame0 + i) % w.n_frames
-            r.set_view(w.view(f))
-            r.set_lens(w.lens(f))
-            r.cell_quality(mid, hexfc.HEXFC_METRIC_IMPORTANCE, imp, stream)
-            r.set_cell_importance(mid, imp, stream)
-            r.render_host(mid, host_np, stream)
-        torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        e2e = {"value": world * ne / te if world > 1 else ne / te, "unit": "frames/s",
-               "h2d_bytes_per_step": int(C_sizeof_view_lens()),
-               "d2h_bytes_per_step": int(w.width * w.height * 16 + 32)}
+    host = torch.empty((w.height, w.width, 4), dtype=torch.float32, pin_memory=True)
+    host_np = host.numpy()
+    ne = max(1, min(args.e2e_steps, args.steps))
+    for i in range(2):
+        r.set_view(w.view(i)); r.set_lens(w.lens(i))
+        r.render_host(mid, host_np, stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for f in replica_frames(rank, world, w.n_frames, 0, ne):
+        r.set_view(w.view(f))
+        r.set_lens(w.lens(f))
+        r.cell_quality(mid, hexfc.HEXFC_METRIC_IMPORTANCE, imp, stream)
+        r.set_cell_importance(mid, imp, stream)
+        r.render_host(mid, host_np, stream)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    if world > 1:
+        ms, frag_sum, te = reduce_replicas(ms, frag_sum, te, dev)
+    e2e = {"value": world * ne / te, "unit": "frames/s",
+           "h2d_bytes_per_step": int(C_sizeof_view_lens()),
+           "d2h_bytes_per_step": int(w.width * w.height * 16 + 32)}
 
     if rank != 0:
         return
