@@ -56,7 +56,7 @@ class _Style(C.Structure):
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("tf_lo", C.c_float),
                 ("tf_hi", C.c_float), ("bg", C.c_float * 3), ("accent_beta", C.c_float),
                 ("halo_scale", C.c_float), ("darken", C.c_float), ("g_min", C.c_float),
-                ("g_max", C.c_float)]
+                ("g_max", C.c_float), ("desat", C.c_float)]
 
 
 def _view(v) -> _View:

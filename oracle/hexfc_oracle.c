@@ -59,6 +59,11 @@
  *      fragment (s_e > 1) brightens its face colour by accent_beta.
  *   R11 s_e alpha_f is clamped to 1 in Eq. 4; colours are premultiplied.
  *   R12 output = C + (1 - A) bg, alpha = A.
+ *   R16 depth cue (Section "Evaluation": fragments in the focus region that
+ *      lie further from the camera are slightly desaturated): with strength
+ *      desat (0 = off, the default), k = desat focus clamp(1 - g, 0, 1) and
+ *      the Eq. 4 colour moves towards its luma y = 0.299 R + 0.587 G +
+ *      0.114 B by k; opacity unchanged.
  *
  * Near-tie bookkeeping: a discrete decision of R8/R9 whose two sides differ by
  * less than ORC_TIE_MARGIN pixels is reported in a per-fragment bit mask, and
@@ -101,6 +106,7 @@ typedef struct {
     float alpha_min, alpha_max, tf_lo, tf_hi;
     float bg[3];
     float accent_beta, halo_scale, darken, g_min, g_max;
+    float desat;          /* depth cue strength (R16), 0 = off */
 } orc_style;
 
 /* ----------------------------------------------------------------- quality */
@@ -645,6 +651,14 @@ void orc_fc_shade(const orc_style* st, double dist, double d_f, double d_c, doub
     if (af > 1.0) af = 1.0;
     for (int k = 0; k < 3; ++k) rgba[k] = alpha_e * ce[k] + (1.0 - alpha_e) * af * cf[k];
     rgba[3] = alpha_e + (1.0 - alpha_e) * af;
+    /* depth cue of Section "Evaluation" (R16): fragments in focus and beyond
+     * the reference depth (g < 1) lose part of their saturation; the colour
+     * moves towards its Rec. 601 luma, opacity unchanged */
+    double kd = (double)st->desat * focus * clamp01(1.0 - g);
+    if (kd > 0.0) {
+        double y = 0.299 * rgba[0] + 0.587 * rgba[1] + 0.114 * rgba[2];
+        for (int k = 0; k < 3; ++k) rgba[k] = rgba[k] + kd * (y - rgba[k]);
+    }
 }
 
 typedef struct {

@@ -216,6 +216,7 @@ class Style:
     darken: float = 0.25
     g_min: float = 0.5
     g_max: float = 2.0
+    desat: float = 0.0
 
 
 def orbit_view(frame: int, n_frames: int, width: int, height: int, radius: float = 1.2,

@@ -133,6 +133,51 @@ def test_fc_closed_forms(name, inp, exp):
     assert np.allclose(rgba, exp, atol=1e-12), (name, rgba, exp)
 
 
+def _cue_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "fc_depth_cue.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            lhs, rhs = line.split("|")
+            t = lhs.split()
+            rows.append((t[0], [float(x) for x in t[1:]], [float(x) for x in rhs.split()]))
+    return rows
+
+
+@pytest.mark.parametrize("name,inp,exp", _cue_rows(), ids=[r[0] for r in _cue_rows()])
+def test_fc_depth_cue(name, inp, exp):
+    dist, d_f, d_c, d_a, g, t_imp, s, desat = inp
+    st = synth.Style(w_base=2.0, s=s, alpha_min=0.1, alpha_max=0.6, tf_lo=0.0, tf_hi=1.0,
+                     accent_beta=0.2, halo_scale=0.5, darken=0.25, desat=desat)
+    rgba, _ = oracle.fc_shade(st, dist, d_f, d_c, d_a, g, t_imp)
+    assert np.allclose(rgba, exp, atol=1e-12), (name, rgba, exp)
+
+
+def test_depth_cue_invariants():
+    """The cue only moves a colour along the grey axis: luma and opacity are
+    kept, desat = 0 changes nothing, in front of the reference depth (g >= 1)
+    or out of focus nothing changes, and full strength in full focus at
+    g <= 0 gives pure grey."""
+    rng = np.random.default_rng(7)
+    luma = np.array([0.299, 0.587, 0.114])
+    for _ in range(400):
+        dist, g, t = rng.uniform(0, 1.2), rng.uniform(0.2, 2.0), rng.uniform()
+        d_f, d_c, d_a = rng.uniform(0, 6, 3)
+        d_c = max(d_c, d_f)
+        d_a = min(d_a, d_f)
+        base, _ = oracle.fc_shade(synth.Style(), dist, d_f, d_c, d_a, g, t)
+        cued, _ = oracle.fc_shade(synth.Style(desat=rng.uniform(0.1, 1.0)), dist, d_f, d_c, d_a, g, t)
+        assert cued[3] == base[3]
+        assert float(luma @ cued[:3]) == pytest.approx(float(luma @ base[:3]), abs=1e-14)
+        if g >= 1.0 or dist >= 1.0:
+            assert np.array_equal(cued, base)
+    grey, _ = oracle.fc_shade(synth.Style(desat=1.0), 0.5, math.inf, math.inf, 9.0, 0.0, 1.0)
+    assert grey[3] > 0.0
+    assert grey[0] == pytest.approx(grey[1], abs=1e-15) and grey[1] == pytest.approx(grey[2], abs=1e-15)
+
+
 def test_fc_special_cases():
     rng = np.random.default_rng(0)
     st = synth.Style(w_base=2.0, s=1.5)
