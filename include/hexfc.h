@@ -90,7 +90,10 @@ typedef struct hexfc_lens {
  * table; bg: background colour (Section "Contextual Volume Rendering");
  * accent_beta: brightening of accentuated edges (Section "Blending Focus and
  * Context"); halo_scale, darken: halo width and edge darkening of the focus
- * edges; g_min, g_max: clamp of the depth-dependent width factor.
+ * edges; g_min, g_max: clamp of the depth-dependent width factor; desat:
+ * strength of the depth cue of Section "Evaluation" (fragments in focus
+ * beyond the reference depth are desaturated by desat * focus * clamp(1 - g,
+ * 0, 1) towards their luma; 0 = off, the default).
  */
 typedef struct hexfc_style {
     float w_base;
@@ -104,6 +107,7 @@ typedef struct hexfc_style {
     float halo_scale;
     float darken;
     float g_min, g_max;
+    float desat;
 } hexfc_style;
 
 /* Per-frame statistics of the last hexfc_render* call. */
@@ -202,7 +206,7 @@ hexfc_status hexfc_set_view(hexfc_ctx* ctx, const hexfc_view* view);
 /* Set the focus lens (radius > 0). Errors: ARG. */
 hexfc_status hexfc_set_lens(hexfc_ctx* ctx, const hexfc_lens* lens);
 
-/* Set the style constants. Errors: ARG (w_base < 0, tf_hi == tf_lo, g_min > g_max). */
+/* Set the style constants. Errors: ARG (w_base < 0, tf_hi == tf_lo, g_min > g_max, desat outside [0, 1]). */
 hexfc_status hexfc_set_style(hexfc_ctx* ctx, const hexfc_style* style);
 
 /*

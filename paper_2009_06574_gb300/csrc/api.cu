@@ -208,6 +208,7 @@ ShadeParams make_shade(const hexfc_ctx* ctx)
     sp.g_max = s.g_max;
     sp.zref = (float)ctx->zref;
     sp.ortho = ctx->cam.ortho;
+    sp.desat = s.desat;
     const float acc = 256.f * (2.f / 3.f) * s.w_base;
     sp.accent_r2 = acc * acc;
     return sp;
@@ -364,6 +365,7 @@ void hexfc_style_default(hexfc_style* s)
     s->darken = 0.25f;
     s->g_min = 0.5f;
     s->g_max = 2.f;
+    s->desat = 0.f;
 }
 
 hexfc_status hexfc_create(hexfc_ctx** out, int device, uint64_t frag_budget_bytes)
@@ -519,6 +521,7 @@ hexfc_status hexfc_set_style(hexfc_ctx* ctx, const hexfc_style* s)
 {
     if (!ctx || !s) return HEXFC_ERR_ARG;
     if (!(s->w_base >= 0.f) || s->tf_hi == s->tf_lo || !(s->g_min <= s->g_max)) return HEXFC_ERR_ARG;
+    if (!(s->desat >= 0.f && s->desat <= 1.f)) return HEXFC_ERR_ARG;
     ctx->style = *s;
     return HEXFC_OK;
 }

@@ -36,6 +36,7 @@ struct ShadeParams {
     float zref;
     int ortho;
     float accent_r2;   // (256 * 2/3 * w_base)^2: accentuation radius squared, 1/256-pixel units
+    float desat;       // depth cue strength (0 = off)
 };
 
 // One face in one 128-byte line. The face stage of every frame rewrites the

@@ -106,8 +106,18 @@ __device__ __forceinline__ float4 shade_fragment(const ShadeSoA& t, int j, float
     const float dc2 = dc * dc;
     const float af = fminf(s_e * (ahat * (dc2 * dc2)), 1.f);
     const float wf = (1.f - alpha_e) * af;
-    return make_float4(alpha_e * ce[0] + wf * cf[0], alpha_e * ce[1] + wf * cf[1], alpha_e * ce[2] + wf * cf[2],
-                       alpha_e + wf);
+    float4 c = make_float4(alpha_e * ce[0] + wf * cf[0], alpha_e * ce[1] + wf * cf[1], alpha_e * ce[2] + wf * cf[2],
+                           alpha_e + wf);
+    // depth cue (Section "Evaluation"): in focus and beyond the reference
+    // depth, the colour moves towards its luma; opacity unchanged
+    if (sp.desat > 0.f) {
+        const float k = sp.desat * focus * fminf(fmaxf(1.f - g, 0.f), 1.f);
+        const float y = 0.299f * c.x + 0.587f * c.y + 0.114f * c.z;
+        c.x = fmaf(k, y - c.x, c.x);
+        c.y = fmaf(k, y - c.y, c.y);
+        c.z = fmaf(k, y - c.z, c.z);
+    }
+    return c;
 }
 
 }  // namespace hexfc

@@ -63,7 +63,8 @@ class hexfc_style(C.Structure):
     _fields_ = [("w_base", C.c_float), ("lod", C.c_int32), ("delta", C.c_float), ("s", C.c_float),
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("tf_lo", C.c_float), ("tf_hi", C.c_float),
                 ("bg", C.c_float * 3), ("accent_beta", C.c_float), ("halo_scale", C.c_float),
-                ("darken", C.c_float), ("g_min", C.c_float), ("g_max", C.c_float)]
+                ("darken", C.c_float), ("g_min", C.c_float), ("g_max", C.c_float),
+                ("desat", C.c_float)]
 
 
 class hexfc_frame_stats(C.Structure):

@@ -73,6 +73,7 @@ def test_perspective_orbit_ragged(hx, frame, lens_mode):
 
 
 @pytest.mark.parametrize("style_kw", [dict(s=3.0, alpha_min=0.0, alpha_max=1.0),
+                                      dict(desat=0.8, g_min=0.25, tf_hi=0.6),
                                       dict(bg=(1.0, 1.0, 1.0), w_base=3.0, lod=1, delta=0.3),
                                       dict(w_base=0.0, lod=100, delta=2.0),
                                       dict(tf_lo=0.2, tf_hi=0.7, g_min=1.0, g_max=1.0, halo_scale=1.0)])
@@ -243,6 +244,10 @@ def test_error_codes(hx):
     with pytest.raises(hx.HexfcError) as e:
         r.set_lens(synth.Lens(radius=0.0))
     assert e.value.status == hx.HEXFC_ERR_ARG
+    for bad_style in (synth.Style(desat=1.5), synth.Style(w_base=-1.0), synth.Style(g_min=3.0)):
+        with pytest.raises(hx.HexfcError) as e:
+            r.set_style(bad_style)
+        assert e.value.status == hx.HEXFC_ERR_ARG
     r.close()
     # fragment budget smaller than the frame
     r = hx.Renderer(0, frag_budget_bytes=24 * 100)
