@@ -180,6 +180,31 @@ hexfc_status hexfc_upload_mesh(hexfc_ctx* ctx, const float* verts, int64_t n_ver
                                const uint8_t* cell_edge_level, int32_t* mesh_id_out);
 
 /*
+ * Serving support (no counterpart in the paper; used to render many requests
+ * at once on one GPU with one context per concurrent frame).
+ *
+ * hexfc_share_mesh: make mesh `mesh` of context src available in context dst
+ * (same device) without a copy; *mesh_id_out receives its handle in dst. A
+ * mesh stays resident until every context holding it is destroyed. Rendering
+ * and quality evaluation only read a resident mesh, so contexts may render a
+ * shared mesh at the same time from different host threads;
+ * hexfc_set_cell_importance rewrites it for every holder and must not overlap
+ * a render of it. Errors: ARG (NULL pointer, different devices), STATE (no
+ * such mesh in src), OOM.
+ *
+ * hexfc_frame_memory: *bytes = device memory held by the context's per-frame
+ * buffers (they grow to the largest frame rendered and are reused).
+ * Errors: ARG.
+ *
+ * hexfc_trim: free the context's per-frame buffers (the next render allocates
+ * them again). Call only when no render of this context is in flight.
+ * Errors: ARG.
+ */
+hexfc_status hexfc_share_mesh(hexfc_ctx* dst, const hexfc_ctx* src, int32_t mesh, int32_t* mesh_id_out);
+hexfc_status hexfc_frame_memory(const hexfc_ctx* ctx, uint64_t* bytes);
+hexfc_status hexfc_trim(hexfc_ctx* ctx);
+
+/*
  * Per-cell quality from the Jacobian of the cube-to-cell map (Section
  * "Introduction"; Section "Results and Analysis": per-cell scaled Jacobian
  * ratio). metric: HEXFC_METRIC_*; the 8 corners and the cell centre are

@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -15,7 +16,7 @@ using namespace hexfc;
 struct hexfc_ctx {
     int device = 0;
     uint64_t budget = 0;
-    std::vector<DevMesh*> meshes;
+    std::vector<std::shared_ptr<DevMesh>> meshes;   // resident meshes, possibly shared with other contexts
     bool have_view = false;
     hexfc_view view{};
     CamParams cam{};
@@ -101,13 +102,13 @@ void free_mesh(DevMesh* m)
     if (!m) return;
     dfree(m->verts); dfree(m->cells); dfree(m->cell_edges); dfree(m->cell_imp);
     dfree(m->vkey); dfree(m->ekey); dfree(m->vimp); dfree(m->eattr); dfree(m->elevel);
-    dfree(m->fverts); dfree(m->fedges); dfree(m->frec);
+    dfree(m->fverts); dfree(m->fedges); dfree(m->fstat);
     delete m;
 }
 
 void free_frame(FrameBufs& f)
 {
-    dfree(f.vproj); dfree(f.ved); dfree(f.tzsum);
+    dfree(f.vproj); dfree(f.ved); dfree(f.fframe); dfree(f.tzsum);
     dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.tile_order); dfree(f.bins); dfree(f.masks); dfree(f.cnt);
     dfree(f.off);
     dfree(f.part); dfree(f.part_max); dfree(f.long_q); dfree(f.fix_q); dfree(f.key); dfree(f.rgba); dfree(f.scal);
@@ -118,7 +119,7 @@ void free_frame(FrameBufs& f)
 DevMesh* get_mesh(hexfc_ctx* ctx, int32_t id)
 {
     if (!ctx || id < 0 || id >= (int32_t)ctx->meshes.size()) return nullptr;
-    return ctx->meshes[(size_t)id];
+    return ctx->meshes[(size_t)id].get();
 }
 
 // Stage events: record boundary k of the current frame (no-op without timing).
@@ -229,7 +230,12 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
         if ((st = ensure(&fb.vproj, &fb.v_cap, m->n_verts)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.ved, &c1, fb.v_cap)) != HEXFC_OK) return st;
     }
-    if ((st = ensure(&fb.tzsum, &fb.f_cap, 2 * m->n_faces)) != HEXFC_OK) return st;
+    if (!fb.fframe || fb.f_cap < m->n_faces) {
+        int64_t c1 = 0;
+        dfree(fb.tzsum);
+        if ((st = ensure(&fb.fframe, &fb.f_cap, m->n_faces)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.tzsum, &c1, 2 * fb.f_cap)) != HEXFC_OK) return st;
+    }
     if (!fb.tile_cnt || fb.t_cap < n_tiles + 1) {
         int64_t c1 = 0, c2 = 0;
         int64_t c3 = 0;
@@ -393,7 +399,7 @@ void hexfc_destroy(hexfc_ctx* ctx)
     if (!ctx) return;
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
-    for (DevMesh* m : ctx->meshes) free_mesh(m);
+    ctx->meshes.clear();   // a mesh is freed with its last holder
     free_frame(ctx->fb);
     dfree(ctx->d_out);
     for (auto& set : ctx->ev)
@@ -432,7 +438,7 @@ hexfc_status hexfc_upload_mesh(hexfc_ctx* ctx, const float* verts, int64_t n_ver
     A(dalloc(&m->elevel, (size_t)t.n_edges));
     A(dalloc(&m->fverts, (size_t)t.n_faces));
     A(dalloc(&m->fedges, (size_t)t.n_faces));
-    A(dalloc(&m->frec, (size_t)t.n_faces));
+    A(dalloc(&m->fstat, (size_t)t.n_faces));
     if (st != HEXFC_OK) {
         free_mesh(m);
         return st;
@@ -456,8 +462,61 @@ hexfc_status hexfc_upload_mesh(hexfc_ctx* ctx, const float* verts, int64_t n_ver
         free_mesh(m);
         return HEXFC_ERR_CUDA;
     }
-    ctx->meshes.push_back(m);
+    const int dev = ctx->device;
+    try {
+        ctx->meshes.emplace_back(m, [dev](DevMesh* p) {
+            DeviceGuard g2(dev);
+            free_mesh(p);
+        });
+    } catch (...) {
+        free_mesh(m);
+        return HEXFC_ERR_OOM;
+    }
     *mesh_id_out = (int32_t)(ctx->meshes.size() - 1);
+    return HEXFC_OK;
+}
+
+hexfc_status hexfc_frame_memory(const hexfc_ctx* ctx, uint64_t* bytes)
+{
+    if (!ctx || !bytes) return HEXFC_ERR_ARG;
+    const FrameBufs& f = ctx->fb;
+    uint64_t b = 0;
+    b += (uint64_t)f.v_cap * (sizeof(int4) + sizeof(float));
+    b += (uint64_t)f.f_cap * (sizeof(FaceFrame) + 2 * sizeof(uint32_t));
+    b += (uint64_t)f.t_cap * (3 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t));
+    b += (uint64_t)f.bin_cap * sizeof(uint32_t) + (uint64_t)f.mask_cap * sizeof(uint32_t);
+    b += (uint64_t)f.p_cap * (3 * sizeof(uint32_t) + sizeof(uint64_t));
+    b += (uint64_t)f.part_cap * (sizeof(uint64_t) + sizeof(uint32_t));
+    b += (uint64_t)f.frag_cap * (sizeof(uint64_t) + sizeof(float4));
+    b += (uint64_t)ctx->d_out_cap * sizeof(float);
+    *bytes = b;
+    return HEXFC_OK;
+}
+
+hexfc_status hexfc_trim(hexfc_ctx* ctx)
+{
+    if (!ctx) return HEXFC_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    uint64_t* pinned = ctx->fb.h_scal;
+    ctx->fb.h_scal = nullptr;   // the pinned mirror is small: keep it
+    free_frame(ctx->fb);
+    ctx->fb.h_scal = pinned;
+    dfree(ctx->d_out);
+    ctx->d_out_cap = 0;
+    ctx->have_frame = false;
+    return HEXFC_OK;
+}
+
+hexfc_status hexfc_share_mesh(hexfc_ctx* dst, const hexfc_ctx* src, int32_t mesh, int32_t* mesh_id_out)
+{
+    if (!dst || !src || !mesh_id_out || dst->device != src->device) return HEXFC_ERR_ARG;
+    if (mesh < 0 || mesh >= (int32_t)src->meshes.size()) return HEXFC_ERR_STATE;
+    try {
+        dst->meshes.push_back(src->meshes[(size_t)mesh]);
+    } catch (...) {
+        return HEXFC_ERR_OOM;
+    }
+    *mesh_id_out = (int32_t)(dst->meshes.size() - 1);
     return HEXFC_OK;
 }
 
@@ -734,6 +793,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     FrameBufs fb;
     fb.vproj = a.take<int4>((size_t)m->n_verts);
     fb.ved = a.take<float>((size_t)m->n_verts);
+    fb.fframe = a.take<FaceFrame>((size_t)m->n_faces);
     fb.tzsum = a.take<uint32_t>(2 * (size_t)m->n_faces);
     fb.tile_cnt = a.take<uint32_t>((size_t)n_tiles + 1);
     fb.tile_off = a.take<uint64_t>((size_t)n_tiles + 1);
@@ -746,7 +806,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fb.part = a.take<uint64_t>(2 * (size_t)nparts);
     fb.part_max = a.take<uint32_t>(2 * (size_t)nparts);
     fb.scal = a.take<uint64_t>(16);
-    if (!fb.vproj || !fb.ved || !fb.tzsum || !fb.tile_cnt ||
+    if (!fb.vproj || !fb.ved || !fb.fframe || !fb.tzsum || !fb.tile_cnt ||
         !fb.tile_off || !fb.tile_cur || !fb.tile_order || !fb.cnt || !fb.off || !fb.long_q || !fb.fix_q || !fb.part || !fb.part_max ||
         !fb.scal)
         return HEXFC_ERR_OVERFLOW;

@@ -39,19 +39,23 @@ struct ShadeParams {
     float desat;       // depth cue strength (0 = off)
 };
 
-// One face in one 128-byte line. The face stage of every frame rewrites the
-// first half (window corners, depths, edge flags, eye depths); the static half
-// (corner importance and world position) is rewritten when importance changes.
-struct __align__(128) FaceRec {
+// A face as two 64-byte records: the per-frame one (window corners, depths,
+// edge flags, eye depths), written by the face stage of every frame into the
+// rendering context's buffers, and the static one (corner importance and world
+// position), owned by the mesh and rewritten only when importance changes, so
+// that contexts can render one resident mesh at the same time.
+struct __align__(64) FaceFrame {
     int4 X, Y;            // corner window position, 16.8 fixed point
     uint4 Z;              // bits 0-23: corner window depth (z24); Z.x bits 24-31: edge flags
                           // (bits 0-3 visible in focus, 4-7 visible in context); Z.y bits 24-25:
                           // triangle 0 / 1 drawn
     float4 ed;            // corner eye depth
+};
+struct __align__(64) FaceStatic {
     float4 imp;           // corner importance
     float4 px, py, pz;    // corner world position
 };
-static_assert(sizeof(FaceRec) == 128, "one line per face");
+static_assert(sizeof(FaceFrame) == 64 && sizeof(FaceStatic) == 64, "two sectors each");
 constexpr uint32_t kZ24 = 0xFFFFFFu;
 __host__ __device__ inline uint32_t face_edge_flags(const uint4& z) { return z.x >> 24; }
 __host__ __device__ inline uint32_t face_tris(const uint4& z) { return (z.y >> 24) & 3u; }
@@ -70,7 +74,7 @@ struct DevMesh {
     uint8_t* elevel = nullptr;     // [E]
     int4* fverts = nullptr;        // [F] canonical corners
     int4* fedges = nullptr;        // [F] unique edge id of local edge k = (c_k, c_k+1)
-    FaceRec* frec = nullptr;       // [F] face records (the per-frame half is scratch of the current frame)
+    FaceStatic* fstat = nullptr;   // [F] static face records
 };
 
 // Per-frame buffers owned by the context.
@@ -80,6 +84,7 @@ struct FrameBufs {
     float* ved = nullptr;    // eye depth
     int64_t v_cap = 0;
     // faces
+    FaceFrame* fframe = nullptr;    // [F] per-frame face records
     uint32_t* tzsum = nullptr;      // [2F] per triangle (2 face + tri): sum of its window depths
     int64_t f_cap = 0;
     // tiles

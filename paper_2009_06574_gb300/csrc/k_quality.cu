@@ -107,9 +107,9 @@ __global__ void k_key_to_float(const int32_t* __restrict__ key, float* __restric
     out[i] = (k == INT32_MIN) ? 0.f : key2f(k);   // an unreferenced vertex gets 0
 }
 
-// Static half of the face records: importance and world position of the 4 corners.
+// Static face records: importance and world position of the 4 corners.
 __global__ void k_face_static(const int4* __restrict__ fverts, const float* __restrict__ vimp,
-                              const float* __restrict__ verts, int64_t n_faces, FaceRec* __restrict__ frec)
+                              const float* __restrict__ verts, int64_t n_faces, FaceStatic* __restrict__ fstat)
 {
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= n_faces) return;
@@ -123,7 +123,7 @@ __global__ void k_face_static(const int4* __restrict__ fverts, const float* __re
         y[k] = verts[3 * (int64_t)id[k] + 1];
         z[k] = verts[3 * (int64_t)id[k] + 2];
     }
-    FaceRec& r = frec[f];
+    FaceStatic& r = fstat[f];
     r.imp = make_float4(im[0], im[1], im[2], im[3]);
     r.px = make_float4(x[0], x[1], x[2], x[3]);
     r.py = make_float4(y[0], y[1], y[2], y[3]);
@@ -149,7 +149,7 @@ cudaError_t launch_importance(const DevMesh& m, cudaStream_t s)
                                                                    m.n_cells, m.vkey, m.ekey);
     k_key_to_float<<<grid_for(m.n_verts, 256), 256, 0, s>>>(m.vkey, m.vimp, m.n_verts);
     k_key_to_float<<<grid_for(m.n_edges, 256), 256, 0, s>>>(m.ekey, m.eattr, m.n_edges);
-    k_face_static<<<grid_for(m.n_faces, 256), 256, 0, s>>>(m.fverts, m.vimp, m.verts, m.n_faces, m.frec);
+    k_face_static<<<grid_for(m.n_faces, 256), 256, 0, s>>>(m.fverts, m.vimp, m.verts, m.n_faces, m.fstat);
     return cudaGetLastError();
 }
 

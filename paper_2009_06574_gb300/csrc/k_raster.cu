@@ -70,7 +70,7 @@ __device__ __forceinline__ void tile_range(const TriGeom& t, int& tx0, int& ty0,
 __global__ void k_face_setup(const int4* __restrict__ fverts, const int4* __restrict__ fedges,
                              const uint8_t* __restrict__ elevel, const float* __restrict__ eattr,
                              const int4* __restrict__ vproj, const float* __restrict__ ved, int64_t n_faces,
-                             int lod, float delta, int W, int H, int tiles_x, FaceRec* __restrict__ frec,
+                             int lod, float delta, int W, int H, int tiles_x, FaceFrame* __restrict__ fframe,
                              uint32_t* __restrict__ tzsum, uint32_t* __restrict__ tile_cnt)
 {
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -110,7 +110,7 @@ __global__ void k_face_setup(const int4* __restrict__ fverts, const int4* __rest
         for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(tile_cnt + ty * tiles_x + tx, 1u);
     }
-    FaceRec& r = frec[f];   // the per-frame half of the line
+    FaceFrame& r = fframe[f];
     r.X = make_int4(X[0], X[1], X[2], X[3]);
     r.Y = make_int4(Y[0], Y[1], Y[2], Y[3]);
     r.Z = make_uint4((Z[0] & kZ24) | (flags << 24), (Z[1] & kZ24) | (tris << 24), Z[2] & kZ24, Z[3] & kZ24);
@@ -119,16 +119,16 @@ __global__ void k_face_setup(const int4* __restrict__ fverts, const int4* __rest
     reinterpret_cast<uint2*>(tzsum)[f] = make_uint2(z0 + z1 + z2, z0 + z2 + z3);   // < 3 * 2^24
 }
 
-__global__ void k_bin_fill(const FaceRec* __restrict__ frec, int64_t n_faces, int W, int H, int tiles_x,
+__global__ void k_bin_fill(const FaceFrame* __restrict__ fframe, int64_t n_faces, int W, int H, int tiles_x,
                            int reverse, const uint64_t* __restrict__ tile_off, uint32_t* __restrict__ tile_cur,
                            uint32_t* __restrict__ bins)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_faces) return;
     int64_t f = reverse ? (n_faces - 1 - i) : i;
-    const uint32_t tris = face_tris(frec[f].Z);
+    const uint32_t tris = face_tris(fframe[f].Z);
     if (tris == 0) return;
-    int4 a = frec[f].X, b = frec[f].Y;
+    int4 a = fframe[f].X, b = fframe[f].Y;
     int32_t X[4] = {a.x, a.y, a.z, a.w}, Y[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
     for (int tri = 0; tri < 2; ++tri) {
@@ -446,7 +446,7 @@ __device__ __forceinline__ bool cover_fast(const CountWarp& me, int j, int rx, i
 // per-pixel totals are summed at the end.
 __global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__ tile_off,
                                                     const uint32_t* __restrict__ bins,
-                                                    const FaceRec* __restrict__ frec,
+                                                    const FaceFrame* __restrict__ fframe,
                                                     const uint32_t* __restrict__ order, int tiles_x, int W, int H,
                                                     uint32_t* __restrict__ cnt, uint32_t* __restrict__ masks)
 {
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__
     uint32_t f2t = warp < (int)n_chunks ? bins[beg + (uint64_t)warp * kChunk + lane] : kPadBin;
     for (uint32_t c = warp; c < n_chunks; c += kConsumerWarps) {
         int4 a = make_int4(0, 0, 0, 0), b = a;
-        if (f2t != kPadBin) { a = frec[f2t >> 1].X; b = frec[f2t >> 1].Y; }
+        if (f2t != kPadBin) { a = fframe[f2t >> 1].X; b = fframe[f2t >> 1].Y; }
         const uint32_t f2t_next =
             c + kConsumerWarps < n_chunks ? bins[beg + (uint64_t)(c + kConsumerWarps) * kChunk + lane] : kPadBin;
         if (f2t != kPadBin) {
@@ -509,18 +509,31 @@ __global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__
 
 // ------------------------------------------------------------------ fill + shade
 
-// Producer lane: fetch face record f (one line) into shared memory.
-__device__ __forceinline__ void rec_fetch(FaceRec& r, const FaceRec* __restrict__ frec, uint32_t f)
+// Both records of a face, staged side by side by the producer.
+struct __align__(128) RawFace {
+    FaceFrame fr;
+    FaceStatic st;
+};
+
+// Producer lane: fetch the records of face f into shared memory.
+__device__ __forceinline__ void rec_fetch(RawFace& r, const FaceFrame* __restrict__ fframe,
+                                          const FaceStatic* __restrict__ fstat, uint32_t f)
 {
-    const int4* src = reinterpret_cast<const int4*>(frec + f);
+    const int4* a = reinterpret_cast<const int4*>(fframe + f);
+    const int4* b = reinterpret_cast<const int4*>(fstat + f);
     int4* dst = reinterpret_cast<int4*>(&r);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) cp_async16(dst + k, src + k);
+    for (int k = 0; k < 4; ++k) {
+        cp_async16(dst + k, a + k);
+        cp_async16(dst + 4 + k, b + k);
+    }
 }
 
-__device__ __forceinline__ void stage_shade(const FaceRec& r, uint32_t f2t, const TriGeom& t, bool ortho,
+__device__ __forceinline__ void stage_shade(const RawFace& rf, uint32_t f2t, const TriGeom& t, bool ortho,
                                             ShadeSoA& S, int j)
 {
+    const FaceFrame& r = rf.fr;
+    const FaceStatic& fs = rf.st;
     const int32_t FX[4] = {r.X.x, r.X.y, r.X.z, r.X.w}, FY[4] = {r.Y.x, r.Y.y, r.Y.z, r.Y.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -532,9 +545,9 @@ __device__ __forceinline__ void stage_shade(const FaceRec& r, uint32_t f2t, cons
         S.inv_len2[k][j] = l2 > 0.f ? 1.f / l2 : 0.f;
     }
     const uint32_t zz[4] = {r.Z.x & kZ24, r.Z.y & kZ24, r.Z.z & kZ24, r.Z.w & kZ24};
-    const float ee[4] = {r.ed.x, r.ed.y, r.ed.z, r.ed.w}, ii[4] = {r.imp.x, r.imp.y, r.imp.z, r.imp.w};
-    const float xx[4] = {r.px.x, r.px.y, r.px.z, r.px.w}, yy[4] = {r.py.x, r.py.y, r.py.z, r.py.w};
-    const float ww[4] = {r.pz.x, r.pz.y, r.pz.z, r.pz.w};
+    const float ee[4] = {r.ed.x, r.ed.y, r.ed.z, r.ed.w}, ii[4] = {fs.imp.x, fs.imp.y, fs.imp.z, fs.imp.w};
+    const float xx[4] = {fs.px.x, fs.px.y, fs.px.z, fs.px.w}, yy[4] = {fs.py.x, fs.py.y, fs.py.z, fs.py.w};
+    const float ww[4] = {fs.pz.x, fs.pz.y, fs.pz.z, fs.pz.w};
     float q[3], a[3], P[3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -582,7 +595,7 @@ constexpr size_t kRawOff = (kRing * sizeof(FillSlot) + 127) & ~(size_t)127;   //
 
 __host__ __device__ constexpr size_t fill_smem_bytes()
 {
-    return kRawOff + 2 * kChunk * sizeof(FaceRec) + (size_t)kQCap * sizeof(uint32_t);
+    return kRawOff + 2 * kChunk * sizeof(RawFace) + (size_t)kQCap * sizeof(uint32_t);
 }
 
 // Barrier 1 among the consumer warps only (the producer never joins it); the
@@ -610,7 +623,8 @@ __device__ __forceinline__ void consumers_sync() { asm volatile("barrier.sync 1,
 __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __restrict__ tile_off,
                                                           const uint32_t* __restrict__ bins,
                                                           const uint32_t* __restrict__ masks,
-                                                          const FaceRec* __restrict__ frec,
+                                                          const FaceFrame* __restrict__ fframe,
+                                                          const FaceStatic* __restrict__ fstat,
                                                           const uint32_t* __restrict__ order, int tiles_x, int W,
                                                           int H, ShadeParams sp, const uint64_t* __restrict__ off,
                                                           uint64_t* __restrict__ key, float4* __restrict__ rgba,
@@ -618,7 +632,7 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __rest
 {
     extern __shared__ __align__(128) unsigned char fill_smem[];
     FillSlot* s_ring = reinterpret_cast<FillSlot*>(fill_smem);                                    // [kRing]
-    FaceRec* s_raw = reinterpret_cast<FaceRec*>(fill_smem + kRawOff);                            // [2][kChunk]
+    RawFace* s_raw = reinterpret_cast<RawFace*>(fill_smem + kRawOff);                            // [2][kChunk]
     uint32_t* s_q = reinterpret_cast<uint32_t*>(s_raw + 2 * kChunk);                             // [kQCap]
     __shared__ uint64_t s_base[kTilePix];
     __shared__ uint32_t s_len[kTilePix];
@@ -640,13 +654,13 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __rest
     if (warp == kConsumerWarps) {  // producer
         uint32_t f2t_c = n_chunks > 0 ? bins[beg + lane] : kPadBin;
         uint32_t f2t_n = n_chunks > 1 ? bins[beg + kChunk + lane] : kPadBin;
-        if (f2t_c != kPadBin) rec_fetch(s_raw[lane], frec, f2t_c >> 1);
+        if (f2t_c != kPadBin) rec_fetch(s_raw[lane], fframe, fstat, f2t_c >> 1);
         cp_async_commit();
         for (uint32_t c = 0; c < n_chunks; ++c) {
             const int s = c % kRing;
             uint32_t f2t_nn = kPadBin;
             if (c + 1 < n_chunks) {
-                if (f2t_n != kPadBin) rec_fetch(s_raw[((c + 1) & 1) * kChunk + lane], frec, f2t_n >> 1);
+                if (f2t_n != kPadBin) rec_fetch(s_raw[((c + 1) & 1) * kChunk + lane], fframe, fstat, f2t_n >> 1);
                 if (c + 2 < n_chunks) f2t_nn = bins[beg + (uint64_t)(c + 2) * kChunk + lane];
             }
             cp_async_commit();
@@ -657,9 +671,9 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __rest
             }
             FillSlot& S = s_ring[s];
             if (f2t_c != kPadBin) {
-                const FaceRec& r = s_raw[(c & 1) * kChunk + lane];
+                const RawFace& r = s_raw[(c & 1) * kChunk + lane];
                 TriGeom t;
-                stage_cov(r.X, r.Y, f2t_c, W, H, px0, py0, S.c, lane, t);
+                stage_cov(r.fr.X, r.fr.Y, f2t_c, W, H, px0, py0, S.c, lane, t);
                 if (S.c.box[lane] != 0) stage_shade(r, f2t_c, t, sp.ortho != 0, S.sh, lane);
             } else {
                 S.c.box[lane] = 0;
@@ -781,14 +795,14 @@ cudaError_t launch_face_setup(const DevMesh& m, const CamParams& cam, int lod, f
     (void)tiles_y;
     k_face_setup<<<grid_for(m.n_faces, 256), 256, 0, s>>>(m.fverts, m.fedges, m.elevel, m.eattr, fb.vproj,
                                                            fb.ved, m.n_faces, lod, delta, cam.W, cam.H, tiles_x,
-                                                           m.frec, fb.tzsum, fb.tile_cnt);
+                                                           fb.fframe, fb.tzsum, fb.tile_cnt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bin_fill(const DevMesh& m, FrameBufs& fb, int tiles_x, int W, int H, int reverse,
                             cudaStream_t s)
 {
-    k_bin_fill<<<grid_for(m.n_faces, 256), 256, 0, s>>>(m.frec, m.n_faces, W, H, tiles_x, reverse,
+    k_bin_fill<<<grid_for(m.n_faces, 256), 256, 0, s>>>(fb.fframe, m.n_faces, W, H, tiles_x, reverse,
                                                          fb.tile_off, fb.tile_cur, fb.bins);
     return cudaGetLastError();
 }
@@ -810,7 +824,7 @@ cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles
 {
     const size_t smem = kConsumerWarps * sizeof(CountWarp);
     cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_count<<<(unsigned)(tiles_x * tiles_y), kTilePix, smem, s>>>(fb.tile_off, fb.bins, m.frec, fb.tile_order,
+    k_count<<<(unsigned)(tiles_x * tiles_y), kTilePix, smem, s>>>(fb.tile_off, fb.bins, fb.fframe, fb.tile_order,
                                                                    tiles_x, W, H, fb.cnt, fb.masks);
     return cudaGetLastError();
 }
@@ -821,7 +835,7 @@ cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, 
     const size_t smem = fill_smem_bytes();
     cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_fill<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, smem, s>>>(
-        fb.tile_off, fb.bins, fb.masks, m.frec, fb.tile_order, tiles_x, W, H, sp, fb.off, fb.key, fb.rgba,
+        fb.tile_off, fb.bins, fb.masks, fb.fframe, m.fstat, fb.tile_order, tiles_x, W, H, sp, fb.off, fb.key, fb.rgba,
         reinterpret_cast<unsigned long long*>(fb.scal + 5));
     return cudaGetLastError();
 }

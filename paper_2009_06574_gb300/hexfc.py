@@ -40,7 +40,8 @@ STAGES = ["vertex", "face", "tile_scan", "gap1", "bin", "count", "scan", "gap2",
 EXPORTS = ["hexfc_style_default", "hexfc_create", "hexfc_destroy", "hexfc_upload_mesh", "hexfc_cell_quality",
            "hexfc_set_cell_importance", "hexfc_mesh_info", "hexfc_set_view", "hexfc_set_lens",
            "hexfc_set_style", "hexfc_render", "hexfc_render_host", "hexfc_debug_pixels", "hexfc_set_option",
-           "hexfc_stage_times", "hexfc_status_string", "hexfc_render_noalloc"]
+           "hexfc_stage_times", "hexfc_status_string", "hexfc_render_noalloc", "hexfc_share_mesh",
+           "hexfc_frame_memory", "hexfc_trim"]
 
 
 class HexfcError(RuntimeError):
@@ -110,6 +111,9 @@ def load():
                 "hexfc_stage_times": (i32, [vp, vp, C.POINTER(u64), i32]),
                 "hexfc_status_string": (C.c_char_p, [i32]),
                 "hexfc_render_noalloc": (i32, [vp, i32, vp, C.POINTER(hexfc_frame_stats), vp]),
+                "hexfc_share_mesh": (i32, [vp, vp, i32, C.POINTER(i32)]),
+                "hexfc_frame_memory": (i32, [vp, C.POINTER(u64)]),
+                "hexfc_trim": (i32, [vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -209,6 +213,22 @@ class Renderer:
         _check(load().hexfc_upload_mesh(self._h, _np_ptr(v), v.shape[0], _np_ptr(c), c.shape[0], _np_ptr(s),
                                         _np_ptr(l), C.byref(mid)), "hexfc_upload_mesh")
         return mid.value
+
+    def share_mesh(self, src: "Renderer", mesh: int) -> int:
+        """Make mesh `mesh` of renderer `src` (same device) resident here too, without a copy."""
+        mid = C.c_int32(-1)
+        _check(load().hexfc_share_mesh(self._h, src._h, int(mesh), C.byref(mid)), "hexfc_share_mesh")
+        return mid.value
+
+    def frame_memory(self) -> int:
+        """Device bytes held by this context's per-frame buffers."""
+        b = C.c_uint64(0)
+        _check(load().hexfc_frame_memory(self._h, C.byref(b)), "hexfc_frame_memory")
+        return b.value
+
+    def trim(self):
+        """Free the per-frame buffers (no render of this context may be in flight)."""
+        _check(load().hexfc_trim(self._h), "hexfc_trim")
 
     def mesh_info(self, mesh: int):
         nf, ne = C.c_int64(0), C.c_int64(0)

@@ -1,0 +1,255 @@
+"""Continuous-batching frame server over the hexfc C ABI.
+
+Requests (mesh, camera, lens, style, resolution) arrive at any time; each is
+admitted into a free slot as soon as one is free and the device memory the
+in-flight frames need stays within a budget, so frames of different requests
+run on the GPU at the same time (one context and one CUDA stream per slot,
+each driven by its own host thread; the ABI calls release the interpreter
+lock). Meshes are uploaded once and shared by all slots.
+
+Admission by memory: a slot's per-frame buffers grow to the largest frame it
+has drawn and are reused. The server keeps, per (mesh, width, height), the
+largest footprint seen; a frame of a kind never drawn before is admitted only
+when nothing else is in flight, which measures it. A request is admitted when
+the held buffers of every slot, with the chosen slot raised to the request's
+footprint, fit the budget; idle slots release their buffers (largest first)
+when that makes room. Requests start in arrival order (no overtaking).
+
+The renderer is injected (`renderer_factory`), so the scheduling logic is
+tested on the CPU with a stand-in; the default is `hexfc.Renderer`.
+"""
+from __future__ import annotations
+
+import dataclasses
+import threading
+import time
+from collections import deque
+from typing import Any, Callable, Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Request:
+    mesh: str
+    view: Any          # synth.View (carries width and height)
+    lens: Any          # synth.Lens
+    style: Any = None  # synth.Style or None for the defaults
+
+
+@dataclasses.dataclass
+class Result:
+    ticket: int
+    request: Request
+    status: int = 0
+    image: Optional[np.ndarray] = None   # [H, W, 4] float32
+    stats: Optional[dict] = None
+    slot: int = -1
+    t_submit: float = 0.0
+    t_admit: float = 0.0     # admitted into a slot (arrival order)
+    t_start: float = 0.0     # the slot's thread began the frame
+    t_done: float = 0.0
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_submit
+
+
+class _Slot:
+    def __init__(self, index: int, renderer, stream):
+        self.index = index
+        self.r = renderer
+        self.stream = stream
+        self.busy = False
+        self.held = 0          # bytes of per-frame buffers the slot holds now
+        self.reserved = 0      # bytes admitted for the frame in flight
+        self.mesh_ids = {}     # mesh name -> id in this slot's context
+        self.job = None
+
+
+class Server:
+    def __init__(self, device: int = 0, slots: int = 4, mem_budget_bytes: int = 120 << 30,
+                 renderer_factory: Optional[Callable[[int], Any]] = None,
+                 stream_factory: Optional[Callable[[int], Any]] = None):
+        if renderer_factory is None:
+            from . import hexfc
+
+            def renderer_factory(dev, budget=mem_budget_bytes):
+                return hexfc.Renderer(dev, frag_budget_bytes=budget)
+        if stream_factory is None:
+            def stream_factory(dev):
+                import torch
+                return torch.cuda.Stream(device=dev)
+        self.device = device
+        self.budget = int(mem_budget_bytes)
+        self._lock = threading.Lock()
+        self._cv = threading.Condition(self._lock)
+        self._queue: deque = deque()
+        self._results = {}
+        self._footprint = {}          # (mesh, W, H) -> bytes
+        self._meshes = {}             # names of the resident meshes
+        self._next_ticket = 0
+        self._closing = False
+        self._alone = None            # slot drawing an unmeasured kind of frame (nothing runs beside it)
+        self.peak_reserved = 0        # largest admitted total, for tests and reports
+        self.max_in_flight = 0
+        self._slots = [_Slot(i, renderer_factory(device), stream_factory(device)) for i in range(slots)]
+        self._threads = [threading.Thread(target=self._work, args=(s,), daemon=True) for s in self._slots]
+        for t in self._threads:
+            t.start()
+
+    # ---- meshes
+    def add_mesh(self, name: str, verts, cells, cell_scalar=None, cell_edge_level=None):
+        """Upload once (slot 0) and share the resident mesh with every slot."""
+        with self._lock:
+            s0 = self._slots[0]
+            mid = s0.r.upload_mesh(verts, cells, cell_scalar, cell_edge_level)
+            s0.mesh_ids[name] = mid
+            for s in self._slots[1:]:
+                s.mesh_ids[name] = s.r.share_mesh(s0.r, mid)
+            self._meshes[name] = True
+
+    # ---- requests
+    def submit(self, req: Request) -> int:
+        with self._cv:
+            if self._closing:
+                raise RuntimeError("server closed")
+            if req.mesh not in self._meshes:
+                raise KeyError(req.mesh)
+            t = self._next_ticket
+            self._next_ticket += 1
+            self._results[t] = Result(ticket=t, request=req, t_submit=time.perf_counter())
+            self._queue.append(t)
+            self._admit()
+            return t
+
+    def result(self, ticket: int, timeout: Optional[float] = None) -> Result:
+        deadline = None if timeout is None else time.perf_counter() + timeout
+        with self._cv:
+            while self._results[ticket].t_done == 0.0:
+                left = None if deadline is None else deadline - time.perf_counter()
+                if left is not None and left <= 0:
+                    raise TimeoutError(f"ticket {ticket}")
+                self._cv.wait(left)
+            return self._results.pop(ticket)
+
+    def close(self):
+        with self._cv:
+            self._closing = True
+            self._cv.notify_all()
+        for t in self._threads:
+            t.join()
+        for s in self._slots:
+            s.r.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- admission (called with the lock held)
+    def _key(self, req: Request):
+        return (req.mesh, int(req.view.width), int(req.view.height))
+
+    def _admit(self):
+        while self._queue and self._alone is None:
+            t = self._queue[0]
+            req = self._results[t].request
+            idle = [s for s in self._slots if not s.busy]
+            if not idle:
+                return
+            in_flight = any(s.busy for s in self._slots)
+            need = self._footprint.get(self._key(req))
+            if need is None and in_flight:
+                return          # an unmeasured kind of frame runs alone
+            slot = self._place(idle, need if need is not None else 0, exclusive=need is None)
+            if slot is None:
+                return
+            self._queue.popleft()
+            slot.busy = True
+            slot.reserved = max(slot.held, need or 0)
+            slot.job = t
+            if need is None:
+                self._alone = slot
+            self._results[t].t_admit = time.perf_counter()
+            self.peak_reserved = max(self.peak_reserved, self._total())
+            self.max_in_flight = max(self.max_in_flight, sum(s.busy for s in self._slots))
+            self._cv.notify_all()
+
+    def _total(self) -> int:
+        return sum(s.reserved if s.busy else s.held for s in self._slots)
+
+    def _others(self, slot) -> int:
+        return sum(o.reserved if o.busy else o.held for o in self._slots if o is not slot)
+
+    def _trim(self, slot):
+        if slot.held:
+            slot.r.trim()
+            slot.held = 0
+
+    def _place(self, idle, need: int, exclusive: bool):
+        """The idle slot for a frame of footprint `need`, releasing idle
+        buffers if that makes it fit the budget; None if it cannot start now."""
+        if exclusive:
+            # unmeasured frame, nothing in flight: give it the whole budget
+            s = max(idle, key=lambda o: o.held)
+            for o in idle:
+                if o is not s:
+                    self._trim(o)
+            return s
+        # best fit: the smallest slot that already holds enough, else the largest
+        s = min(idle, key=lambda o: (0, o.held) if o.held >= need else (1, -o.held))
+        for o in sorted((o for o in idle if o is not s), key=lambda o: -o.held):
+            if self._others(s) + max(s.held, need) <= self.budget:
+                break
+            self._trim(o)
+        if self._others(s) + max(s.held, need) <= self.budget:
+            return s
+        return None
+
+    # ---- workers
+    def _work(self, slot: _Slot):
+        while True:
+            with self._cv:
+                while slot.job is None and not self._closing:
+                    self._cv.wait()
+                if slot.job is None:
+                    return
+                res = self._results[slot.job]
+            req = res.request
+            res.t_start = time.perf_counter()
+            res.slot = slot.index
+            img = np.empty((int(req.view.height), int(req.view.width), 4), dtype=np.float32)
+            status = 0
+            try:
+                slot.r.set_view(req.view)
+                slot.r.set_lens(req.lens)
+                slot.r.set_style(req.style)
+                status = slot.r.render_host(slot.mesh_ids[req.mesh], img, slot.stream, check=False)
+            except Exception:   # an argument the library rejected
+                status = -1
+            held = slot.r.frame_memory()
+            with self._cv:
+                res.status = int(status)
+                res.image = img if status == 0 else None
+                res.stats = dict(slot.r.last_stats) if slot.r.last_stats else None
+                res.t_done = time.perf_counter()
+                key = self._key(req)
+                if status == 0:
+                    self._footprint[key] = max(self._footprint.get(key, 0), held)
+                slot.held = held
+                slot.reserved = 0
+                slot.busy = False
+                slot.job = None
+                if self._alone is slot:
+                    self._alone = None
+                self._admit()
+                self._cv.notify_all()
+
+
+def percentile(values, q: float) -> float:
+    v = np.sort(np.asarray(values, dtype=np.float64))
+    if v.size == 0:
+        return float("nan")
+    return float(np.percentile(v, q))
