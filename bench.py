@@ -419,7 +419,11 @@ def run_serving(args, rank, world):
     th = threading.Thread(target=feed)
     th.start()
     th.join()
-    out = [srv.result(t, timeout=3600) for t in tickets]
+    out = []
+    for t in tickets:   # a server hands images on and drops them: their buffers are reused
+        r = srv.result(t, timeout=3600)
+        r.image = None
+        out.append(r)
     t_end = max(r.t_done for r in out)
     peak, in_flight = srv.peak_reserved, srv.max_in_flight
     srv.close()

@@ -23,6 +23,7 @@ from __future__ import annotations
 import dataclasses
 import threading
 import time
+import weakref
 from collections import deque
 from typing import Any, Callable, Optional
 
@@ -55,6 +56,36 @@ class Result:
         return self.t_done - self.t_submit
 
 
+class _HostImage(np.ndarray):
+    """A result image viewing a pooled page-locked buffer; the buffer goes
+    back to the pool when the last view of it is gone."""
+
+
+class _BufferPool:
+    """Page-locked image buffers, recycled: a frame's image is copied from the
+    device straight into the buffer the result then owns (no second copy)."""
+
+    def __init__(self, factory):
+        self._factory = factory
+        self._free = {}
+        self._lock = threading.Lock()
+
+    def take(self, shape):
+        n = int(np.prod(shape))
+        with self._lock:
+            lst = self._free.get(n)
+            raw = lst.pop() if lst else None
+        if raw is None:
+            raw = self._factory(n)
+        img = raw[:n].reshape(shape).view(_HostImage)
+        weakref.finalize(img, self._give_back, n, raw)
+        return img
+
+    def _give_back(self, n, raw):
+        with self._lock:
+            self._free.setdefault(n, []).append(raw)
+
+
 class _Slot:
     def __init__(self, index: int, renderer, stream):
         self.index = index
@@ -70,7 +101,8 @@ class _Slot:
 class Server:
     def __init__(self, device: int = 0, slots: int = 4, mem_budget_bytes: int = 120 << 30,
                  renderer_factory: Optional[Callable[[int], Any]] = None,
-                 stream_factory: Optional[Callable[[int], Any]] = None):
+                 stream_factory: Optional[Callable[[int], Any]] = None,
+                 host_buffer_factory: Optional[Callable[[int], np.ndarray]] = None):
         if renderer_factory is None:
             from . import hexfc
 
@@ -80,6 +112,11 @@ class Server:
             def stream_factory(dev):
                 import torch
                 return torch.cuda.Stream(device=dev)
+        if host_buffer_factory is None:
+            def host_buffer_factory(n_floats):   # page-locked: the image copy is a DMA
+                import torch
+                return torch.empty(n_floats, dtype=torch.float32, pin_memory=True).numpy()
+        self._pool = _BufferPool(host_buffer_factory)
         self.device = device
         self.budget = int(mem_budget_bytes)
         self._lock = threading.Lock()
@@ -220,7 +257,7 @@ class Server:
             req = res.request
             res.t_start = time.perf_counter()
             res.slot = slot.index
-            img = np.empty((int(req.view.height), int(req.view.width), 4), dtype=np.float32)
+            img = self._pool.take((int(req.view.height), int(req.view.width), 4))
             status = 0
             try:
                 slot.r.set_view(req.view)
@@ -229,10 +266,12 @@ class Server:
                 status = slot.r.render_host(slot.mesh_ids[req.mesh], img, slot.stream, check=False)
             except Exception:   # an argument the library rejected
                 status = -1
+            if status != 0:
+                img = None
             held = slot.r.frame_memory()
             with self._cv:
                 res.status = int(status)
-                res.image = img if status == 0 else None
+                res.image = img
                 res.stats = dict(slot.r.last_stats) if slot.r.last_stats else None
                 res.t_done = time.perf_counter()
                 key = self._key(req)

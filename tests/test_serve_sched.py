@@ -80,7 +80,8 @@ class FakeRenderer:
 def make_server(slots, budget, footprint, duration, ledger):
     return serve.Server(0, slots=slots, mem_budget_bytes=budget,
                         renderer_factory=lambda dev: FakeRenderer(dev, ledger, footprint, duration),
-                        stream_factory=lambda dev: None)
+                        stream_factory=lambda dev: None,
+                        host_buffer_factory=lambda n: np.empty(n, np.float32))
 
 
 def grid(n):
