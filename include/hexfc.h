@@ -201,6 +201,39 @@ hexfc_status hexfc_upload_mesh(hexfc_ctx* ctx, const float* verts, int64_t n_ver
  * Errors: ARG.
  */
 hexfc_status hexfc_share_mesh(hexfc_ctx* dst, const hexfc_ctx* src, int32_t mesh, int32_t* mesh_id_out);
+
+/*
+ * Batched frames (no counterpart in the paper): many views of one or several
+ * resident meshes, each with its own camera, lens, style and output, in one
+ * call. The frame's three phases (geometry up to the bin total; binning,
+ * depth order and coverage count up to the fragment total; fill and
+ * composite) run for all items at once: each phase is captured as one CUDA
+ * graph with the items on their own streams, and the executable graph of a
+ * phase is reused (updated in place) when only parameters changed. The host
+ * waits twice per batch instead of twice per frame.
+ *   items[i].mesh      mesh handle of ctx
+ *   items[i].view, .lens, .style   as for hexfc_set_view / _lens / _style
+ *                      (the context's own view, lens and style are unchanged)
+ *   items[i].out_rgba  device, height*width*4 float, row-major (as hexfc_render)
+ *   stats, item_status host arrays of n, or NULL: per-item statistics and status
+ * The context owns one set of frame buffers per item position (grown and
+ * reused). Work is ordered after earlier work on `stream`, and later work on
+ * `stream` sees the images. Errors: ARG (a NULL output or an invalid view,
+ * lens or style), STATE (unknown mesh) before anything runs; OOM, CUDA; the
+ * first failing item's status (OVERFLOW, OOM, TIMEOUT) otherwise, the other
+ * items drawn.
+ */
+typedef struct hexfc_batch_item {
+    int32_t mesh;
+    int32_t pad;
+    hexfc_view view;
+    hexfc_lens lens;
+    hexfc_style style;
+    float* out_rgba;
+} hexfc_batch_item;
+
+hexfc_status hexfc_render_batch(hexfc_ctx* ctx, int32_t n, const hexfc_batch_item* items,
+                                hexfc_frame_stats* stats, hexfc_status* item_status, void* stream);
 hexfc_status hexfc_frame_memory(const hexfc_ctx* ctx, uint64_t* bytes);
 hexfc_status hexfc_trim(hexfc_ctx* ctx);
 
@@ -270,7 +303,10 @@ hexfc_status hexfc_debug_pixels(hexfc_ctx* ctx, const int32_t* px, const int32_t
 /* Tuning and test options. */
 enum {
     HEXFC_OPT_REVERSE_BIN_ORDER = 1, /* 1: process faces in reverse id order when binning (test hook) */
-    HEXFC_OPT_STAGE_TIMING = 2       /* 1: record CUDA events around every stage of hexfc_render* */
+    HEXFC_OPT_STAGE_TIMING = 2,      /* 1: record CUDA events around every stage of hexfc_render* */
+    HEXFC_OPT_DEPTH_BUCKETS = 3,     /* buckets of the per-tile depth order of the triangles: a power of
+                                        two in 256..4096 (default 2048) */
+    HEXFC_OPT_COMPOSITE_WINDOW = 4   /* sorted window of the per-pixel resolve: 4 (default) or 8 */
 };
 hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value);
 

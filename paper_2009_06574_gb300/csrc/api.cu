@@ -25,6 +25,8 @@ struct hexfc_ctx {
     hexfc_style style{};
     FrameBufs fb;
     int reverse_bins = 0;
+    int depth_buckets = 2048;   // HEXFC_OPT_DEPTH_BUCKETS
+    int window = 4;             // HEXFC_OPT_COMPOSITE_WINDOW
     // last render
     bool have_frame = false;
     int last_W = 0, last_H = 0, last_tiles_x = 0, last_tiles_y = 0;
@@ -38,6 +40,18 @@ struct hexfc_ctx {
     int ev_cur = 0;
     double stage_ms[HEXFC_N_STAGES] = {};
     uint64_t timed_frames = 0;
+    // batched frames (hexfc_render_batch): buffers and stream per item, an
+    // origin stream for the captures, and one executable graph per phase
+    struct BatchSlot {
+        FrameBufs fb;
+        cudaStream_t stream = nullptr;
+        cudaEvent_t done = nullptr;
+    };
+    std::vector<std::unique_ptr<BatchSlot>> batch;
+    cudaStream_t origin = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph_exec[3] = {nullptr, nullptr, nullptr};
+    uint64_t graph_instantiations = 0, graph_updates = 0;
 };
 
 namespace {
@@ -186,13 +200,12 @@ bool make_camera(const hexfc_view* v, CamParams& c, double& zref)
     return true;
 }
 
-ShadeParams make_shade(const hexfc_ctx* ctx)
+ShadeParams make_shade_params(const hexfc_lens& lens, const hexfc_style& s, double zref, int ortho)
 {
     ShadeParams sp{};
-    const hexfc_style& s = ctx->style;
-    sp.lens_mode = ctx->lens.mode;
-    for (int d = 0; d < 3; ++d) sp.lens_c[d] = (float)ctx->lens.center[d];
-    sp.lens_inv_r = (float)(1.0 / ctx->lens.radius);
+    sp.lens_mode = lens.mode;
+    for (int d = 0; d < 3; ++d) sp.lens_c[d] = (float)lens.center[d];
+    sp.lens_inv_r = (float)(1.0 / lens.radius);
     sp.w_base = s.w_base;
     sp.lod = s.lod;
     sp.delta = s.delta;
@@ -207,22 +220,98 @@ ShadeParams make_shade(const hexfc_ctx* ctx)
     sp.darken = s.darken;
     sp.g_min = s.g_min;
     sp.g_max = s.g_max;
-    sp.zref = (float)ctx->zref;
-    sp.ortho = ctx->cam.ortho;
+    sp.zref = (float)zref;
+    sp.ortho = ortho;
     sp.desat = s.desat;
     const float acc = 256.f * (2.f / 3.f) * s.w_base;
     sp.accent_r2 = acc * acc;
     return sp;
 }
 
-// Bins, counts, scan, fill and composite of one frame (everything but the output copy).
-hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_stats* stats, cudaStream_t s)
+ShadeParams make_shade(const hexfc_ctx* ctx)
 {
-    FrameBufs& fb = ctx->fb;
-    const int W = ctx->view.width, H = ctx->view.height;
-    const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
-    const int64_t n_tiles = (int64_t)tiles_x * tiles_y;
-    const int64_t n_pix = n_tiles * kTilePix;
+    return make_shade_params(ctx->lens, ctx->style, ctx->zref, ctx->cam.ortho);
+}
+
+bool valid_view(const hexfc_view* v, CamParams& c, double& zref)
+{
+    if (v->width < 1 || v->height < 1 || v->width > 16384 || v->height > 16384) return false;
+    if (!(v->znear < v->zfar) || !std::isfinite(v->znear) || !std::isfinite(v->zfar)) return false;
+    if (!(v->fovy_deg >= 0.0)) return false;
+    return make_camera(v, c, zref);
+}
+
+bool valid_lens(const hexfc_lens* l)
+{
+    if (l->mode != HEXFC_LENS_SCREEN && l->mode != HEXFC_LENS_SPHERE) return false;
+    return l->radius > 0.0 && std::isfinite(l->radius);
+}
+
+bool valid_style(const hexfc_style* s)
+{
+    if (!(s->w_base >= 0.f) || s->tf_hi == s->tf_lo || !(s->g_min <= s->g_max)) return false;
+    return s->desat >= 0.f && s->desat <= 1.f;
+}
+
+// One frame: its mesh, camera and style constants, its buffers, and what the
+// host learns between the three phases. Phase 1 (geometry: vertices, face
+// records, per-tile triangle counts and their scan) ends with the bin total;
+// phase 2 (binning, depth order, tile order, coverage count, pixel scan) ends
+// with the fragment total; phase 3 draws (fill and composite). The host reads
+// the totals between phases to size the next phase's buffers.
+struct FrameJob {
+    FrameBufs* fb = nullptr;
+    DevMesh* m = nullptr;
+    CamParams cam{};
+    ShadeParams sp{};
+    int lod = 0;
+    float delta = 0.f;
+    int W = 0, H = 0, tiles_x = 0, tiles_y = 0;
+    int64_t n_tiles = 0, n_pix = 0;
+    int reverse = 0;
+    int buckets = 2048, window = 4;
+    uint64_t budget = 0;
+    float* out = nullptr;
+    hexfc_ctx* timing = nullptr;   // stage events of the single-frame path
+    uint32_t launches = 0;
+    uint64_t n_bins = 0, total = 0;
+    uint32_t max_list = 0, n_long = 0;
+    hexfc_frame_stats fs{};
+};
+
+void job_mark(const FrameJob& j, int k, cudaStream_t s)
+{
+    if (j.timing) mark(j.timing, k, s);
+}
+
+FrameJob make_job(hexfc_ctx* ctx, FrameBufs* fb, DevMesh* m, float* out)
+{
+    FrameJob j;
+    j.fb = fb;
+    j.m = m;
+    j.cam = ctx->cam;
+    j.sp = make_shade(ctx);
+    j.lod = ctx->style.lod;
+    j.delta = ctx->style.delta;
+    j.W = ctx->view.width;
+    j.H = ctx->view.height;
+    j.tiles_x = (j.W + kTile - 1) / kTile;
+    j.tiles_y = (j.H + kTile - 1) / kTile;
+    j.n_tiles = (int64_t)j.tiles_x * j.tiles_y;
+    j.n_pix = j.n_tiles * kTilePix;
+    j.reverse = ctx->reverse_bins;
+    j.buckets = ctx->depth_buckets;
+    j.window = ctx->window;
+    j.budget = ctx->budget;
+    j.out = out;
+    return j;
+}
+
+// Buffers whose size follows from the mesh and the view.
+hexfc_status job_alloc(FrameJob& j)
+{
+    FrameBufs& fb = *j.fb;
+    const DevMesh* m = j.m;
     hexfc_status st;
     if (!fb.vproj || fb.v_cap < m->n_verts) {
         int64_t c1 = 0;
@@ -236,25 +325,23 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
         if ((st = ensure(&fb.fframe, &fb.f_cap, m->n_faces)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.tzsum, &c1, 2 * fb.f_cap)) != HEXFC_OK) return st;
     }
-    if (!fb.tile_cnt || fb.t_cap < n_tiles + 1) {
-        int64_t c1 = 0, c2 = 0;
-        int64_t c3 = 0;
+    if (!fb.tile_cnt || fb.t_cap < j.n_tiles + 1) {
+        int64_t c1 = 0, c2 = 0, c3 = 0;
         dfree(fb.tile_off); dfree(fb.tile_cur); dfree(fb.tile_order);
-        if ((st = ensure(&fb.tile_cnt, &fb.t_cap, n_tiles + 1)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.tile_cnt, &fb.t_cap, j.n_tiles + 1)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.tile_off, &c1, fb.t_cap)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.tile_cur, &c2, fb.t_cap)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.tile_order, &c3, fb.t_cap)) != HEXFC_OK) return st;
     }
-    if (!fb.cnt || fb.p_cap < n_pix + 1) {
-        int64_t c1 = 0, c2 = 0;
-        int64_t c3 = 0;
+    if (!fb.cnt || fb.p_cap < j.n_pix + 1) {
+        int64_t c1 = 0, c2 = 0, c3 = 0;
         dfree(fb.off); dfree(fb.long_q); dfree(fb.fix_q);
-        if ((st = ensure(&fb.cnt, &fb.p_cap, n_pix + 1)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.cnt, &fb.p_cap, j.n_pix + 1)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.off, &c1, fb.p_cap)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.long_q, &c2, fb.p_cap)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.fix_q, &c3, fb.p_cap)) != HEXFC_OK) return st;
     }
-    int64_t nparts = scan_partials_needed(std::max<int64_t>(n_pix, n_tiles)) + 1;
+    const int64_t nparts = scan_partials_needed(std::max<int64_t>(j.n_pix, j.n_tiles)) + 1;
     if (!fb.part || fb.part_cap < 2 * nparts) {
         int64_t c1 = 0;
         dfree(fb.part_max);
@@ -265,88 +352,192 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
         if ((st = dalloc(&fb.scal, 16)) != HEXFC_OK) return st;
         CK(cudaMallocHost((void**)&fb.h_scal, 16 * sizeof(uint64_t)));
     }
+    return HEXFC_OK;
+}
 
-    if (ctx->timing && !ctx->ev[0][0])
-        for (auto& set : ctx->ev)
-            for (auto& e : set) CK(cudaEventCreate(&e));
-    ctx->ev_cur ^= 1;
-    uint32_t launches = 0;
-    mark(ctx, 0, s);
-    CK(cudaMemsetAsync(fb.tile_cnt, 0, sizeof(uint32_t) * (size_t)n_tiles, s));
-    CK(cudaMemsetAsync(fb.tile_cur, 0, sizeof(uint32_t) * (size_t)n_tiles, s));
+hexfc_status job_phase1(FrameJob& j, cudaStream_t s)
+{
+    FrameBufs& fb = *j.fb;
+    job_mark(j, 0, s);
+    CK(cudaMemsetAsync(fb.tile_cnt, 0, sizeof(uint32_t) * (size_t)j.n_tiles, s));
+    CK(cudaMemsetAsync(fb.tile_cur, 0, sizeof(uint32_t) * (size_t)j.n_tiles, s));
     // scal[5] (device error bits) is kept across frames so that errors of the
     // last passes of a frame are reported by the next call
     CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * 5, s));
     CK(cudaMemsetAsync(fb.scal + 6, 0, sizeof(uint64_t) * 10, s));
-    CK(launch_vertex_setup(*m, ctx->cam, fb, s));
-    mark(ctx, 1, s);
-    CK(launch_face_setup(*m, ctx->cam, ctx->style.lod, ctx->style.delta, fb, tiles_x, tiles_y, s));
-    mark(ctx, 2, s);
-    CK(scan_u32_to_u64(fb.tile_cnt, fb.tile_off, n_tiles, fb.part, fb.part_max, fb.scal + 8, 0xFFFFFFFFu, s,
+    CK(launch_vertex_setup(*j.m, j.cam, fb, s));
+    job_mark(j, 1, s);
+    CK(launch_face_setup(*j.m, j.cam, j.lod, j.delta, fb, j.tiles_x, j.tiles_y, s));
+    job_mark(j, 2, s);
+    CK(scan_u32_to_u64(fb.tile_cnt, fb.tile_off, j.n_tiles, fb.part, fb.part_max, fb.scal + 8, 0xFFFFFFFFu, s,
                        (uint32_t)kChunk));
-    mark(ctx, 3, s);
-    launches += 5;
+    job_mark(j, 3, s);
+    j.launches = 5;
     CK(cudaMemcpyAsync(fb.h_scal + 8, fb.scal + 8, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    collect(ctx);
-    const uint64_t n_bins = fb.h_scal[8];   // padded to whole chunks per tile
-    if ((st = ensure(&fb.bins, &fb.bin_cap, (int64_t)n_bins)) != HEXFC_OK) return st;
-    if ((st = ensure(&fb.masks, &fb.mask_cap, (int64_t)n_bins * (kTilePix / kChunk))) != HEXFC_OK) return st;
-    mark(ctx, 4, s);
-    CK(cudaMemsetAsync(fb.bins, 0xFF, sizeof(uint32_t) * (size_t)n_bins, s));   // padding slots = kPadBin
-    CK(launch_bin_fill(*m, fb, tiles_x, W, H, ctx->reverse_bins, s));
-    CK(launch_bin_sort(*m, fb, tiles_x, tiles_y, s));
-    CK(launch_tile_order(fb, n_tiles, s));
-    mark(ctx, 5, s);
-    CK(launch_count(*m, fb, tiles_x, tiles_y, W, H, s));
-    mark(ctx, 6, s);
-    CK(scan_u32_to_u64(fb.cnt, fb.off, n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
-    mark(ctx, 7, s);
-    launches += 7;
+    return HEXFC_OK;
+}
+
+// After phase 1 has completed: bins and masks for the bin total.
+hexfc_status job_read1(FrameJob& j)
+{
+    FrameBufs& fb = *j.fb;
+    hexfc_status st;
+    j.n_bins = fb.h_scal[8];   // padded to whole chunks per tile
+    if ((st = ensure(&fb.bins, &fb.bin_cap, (int64_t)j.n_bins)) != HEXFC_OK) return st;
+    if ((st = ensure(&fb.masks, &fb.mask_cap, (int64_t)j.n_bins * (kTilePix / kChunk))) != HEXFC_OK) return st;
+    return HEXFC_OK;
+}
+
+hexfc_status job_phase2(FrameJob& j, cudaStream_t s)
+{
+    FrameBufs& fb = *j.fb;
+    job_mark(j, 4, s);
+    CK(cudaMemsetAsync(fb.bins, 0xFF, sizeof(uint32_t) * (size_t)j.n_bins, s));   // padding slots = kPadBin
+    CK(launch_bin_fill(*j.m, fb, j.tiles_x, j.W, j.H, j.reverse, s));
+    CK(launch_bin_sort(*j.m, fb, j.tiles_x, j.tiles_y, j.buckets, s));
+    CK(launch_tile_order(fb, j.n_tiles, s));
+    job_mark(j, 5, s);
+    CK(launch_count(*j.m, fb, j.tiles_x, j.tiles_y, j.W, j.H, s));
+    job_mark(j, 6, s);
+    CK(scan_u32_to_u64(fb.cnt, fb.off, j.n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
+    job_mark(j, 7, s);
+    j.launches += 7;
     CK(cudaMemcpyAsync(fb.h_scal, fb.scal, 6 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    return HEXFC_OK;
+}
+
+// After phase 2 has completed: device error bits, totals, limits, fragment buffers.
+hexfc_status job_read2(FrameJob& j, cudaStream_t s)
+{
+    FrameBufs& fb = *j.fb;
+    hexfc_status st;
     if (fb.h_scal[5] != 0) {  // a bounded device wait ran out, or an exactness check failed
         const uint64_t bits = fb.h_scal[5];
         CK(cudaMemsetAsync(fb.scal + 5, 0, sizeof(uint64_t), s));
         return (bits & 6ull) ? HEXFC_ERR_TIMEOUT : HEXFC_ERR_CUDA;
     }
-    const uint64_t total = fb.h_scal[0];
-    const uint32_t max_list = (uint32_t)fb.h_scal[1];
-    const uint32_t n_long = (uint32_t)fb.h_scal[2];
-    hexfc_frame_stats fs{};
-    fs.fragments = total;
-    fs.bin_entries = n_bins;
-    fs.max_list = max_list;
-    fs.long_lists = n_long;
-    fs.width = (uint32_t)W;
-    fs.height = (uint32_t)H;
-    fs.kernel_launches = launches;
-    ctx->last = fs;
-    if (stats) *stats = fs;
-    ctx->have_frame = false;
-    if (max_list > HEXFC_MAX_LIST) return HEXFC_ERR_OVERFLOW;
-    if (ctx->budget && total * 24ull > ctx->budget) return HEXFC_ERR_OOM;
-    if (!fb.key || fb.frag_cap < (int64_t)total) {
+    j.total = fb.h_scal[0];
+    j.max_list = (uint32_t)fb.h_scal[1];
+    j.n_long = (uint32_t)fb.h_scal[2];
+    hexfc_frame_stats& fs = j.fs;
+    fs = hexfc_frame_stats{};
+    fs.fragments = j.total;
+    fs.bin_entries = j.n_bins;
+    fs.max_list = j.max_list;
+    fs.long_lists = j.n_long;
+    fs.width = (uint32_t)j.W;
+    fs.height = (uint32_t)j.H;
+    fs.kernel_launches = j.launches;
+    if (j.max_list > HEXFC_MAX_LIST) return HEXFC_ERR_OVERFLOW;
+    if (j.budget && j.total * 24ull > j.budget) return HEXFC_ERR_OOM;
+    if (!fb.key || fb.frag_cap < (int64_t)j.total) {
         int64_t c1 = 0;
         dfree(fb.rgba);
-        if ((st = ensure(&fb.key, &fb.frag_cap, (int64_t)total)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.key, &fb.frag_cap, (int64_t)j.total)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.rgba, &c1, fb.frag_cap)) != HEXFC_OK) return st;
     }
-    ShadeParams sp = make_shade(ctx);
-    mark(ctx, 8, s);
-    CK(launch_fill(*m, fb, sp, tiles_x, tiles_y, W, H, s));
-    mark(ctx, 9, s);
-    CK(launch_composite(fb, sp, tiles_x, tiles_y, W, H, out, n_long, s));
-    mark(ctx, 10, s);
+    return HEXFC_OK;
+}
+
+hexfc_status job_phase3(FrameJob& j, cudaStream_t s)
+{
+    FrameBufs& fb = *j.fb;
+    job_mark(j, 8, s);
+    CK(launch_fill(*j.m, fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, s));
+    job_mark(j, 9, s);
+    CK(launch_composite(fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, j.out, j.n_long, j.window, s));
+    job_mark(j, 10, s);
+    j.launches += 3 + (j.n_long > 0 ? 1 : 0);
+    j.fs.kernel_launches = j.launches;
+    return HEXFC_OK;
+}
+
+// Bins, counts, scan, fill and composite of one frame (everything but the output copy).
+hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_stats* stats, cudaStream_t s)
+{
+    FrameJob j = make_job(ctx, &ctx->fb, m, out);
+    hexfc_status st;
+    if ((st = job_alloc(j)) != HEXFC_OK) return st;
+    if (ctx->timing && !ctx->ev[0][0])
+        for (auto& set : ctx->ev)
+            for (auto& e : set) CK(cudaEventCreate(&e));
+    ctx->ev_cur ^= 1;
+    j.timing = ctx;
+    if ((st = job_phase1(j, s)) != HEXFC_OK) return st;
+    CK(cudaStreamSynchronize(s));
+    collect(ctx);
+    if ((st = job_read1(j)) != HEXFC_OK) return st;
+    if ((st = job_phase2(j, s)) != HEXFC_OK) return st;
+    CK(cudaStreamSynchronize(s));
+    ctx->have_frame = false;
+    st = job_read2(j, s);
+    ctx->last = j.fs;
+    if (stats) *stats = j.fs;
+    if (st != HEXFC_OK) return st;
+    if ((st = job_phase3(j, s)) != HEXFC_OK) return st;
     ctx->ev_pending[ctx->ev_cur] = ctx->timing;
-    launches += 3 + (n_long > 0 ? 1 : 0);
-    ctx->last.kernel_launches = launches;
-    if (stats) stats->kernel_launches = launches;
+    ctx->last.kernel_launches = j.launches;
+    if (stats) stats->kernel_launches = j.launches;
     ctx->have_frame = true;
-    ctx->last_W = W;
-    ctx->last_H = H;
-    ctx->last_tiles_x = tiles_x;
-    ctx->last_tiles_y = tiles_y;
+    ctx->last_W = j.W;
+    ctx->last_H = j.H;
+    ctx->last_tiles_x = j.tiles_x;
+    ctx->last_tiles_y = j.tiles_y;
+    return HEXFC_OK;
+}
+
+// Capture `body(i, stream_i)` for the listed items, each on its own stream
+// forked from the context's origin stream and joined back, as one graph;
+// reuse the phase's executable graph when only parameters changed.
+template <typename F>
+hexfc_status batch_graph(hexfc_ctx* ctx, int phase, const std::vector<int>& items, F&& body)
+{
+    cudaStream_t o = ctx->origin;
+    if (cudaStreamBeginCapture(o, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HEXFC_ERR_CUDA;
+    }
+    hexfc_status st = HEXFC_OK;
+    bool ok = cudaEventRecord(ctx->ev_in, o) == cudaSuccess;
+    for (int i : items) {
+        auto& b = *ctx->batch[(size_t)i];
+        ok = ok && cudaStreamWaitEvent(b.stream, ctx->ev_in, 0) == cudaSuccess;
+        if (ok && st == HEXFC_OK) st = body(i, b.stream);
+        ok = ok && cudaEventRecord(b.done, b.stream) == cudaSuccess;   // join, also after a failure
+        ok = ok && cudaStreamWaitEvent(o, b.done, 0) == cudaSuccess;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(o, &g);
+    if (!ok || ec != cudaSuccess || st != HEXFC_OK || !g) {
+        (void)cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        return st != HEXFC_OK ? st : HEXFC_ERR_CUDA;
+    }
+    cudaGraphExec_t& ex = ctx->graph_exec[phase];
+    if (ex) {
+        cudaGraphExecUpdateResultInfo info{};
+        if (cudaGraphExecUpdate(ex, g, &info) == cudaSuccess) {
+            ++ctx->graph_updates;
+        } else {   // another shape of graph: build it anew
+            (void)cudaGetLastError();
+            cudaGraphExecDestroy(ex);
+            ex = nullptr;
+        }
+    }
+    if (!ex) {
+        if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+            (void)cudaGetLastError();
+            ex = nullptr;
+            cudaGraphDestroy(g);
+            return HEXFC_ERR_CUDA;
+        }
+        ++ctx->graph_instantiations;
+    }
+    cudaGraphDestroy(g);
+    if (cudaGraphLaunch(ex, o) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HEXFC_ERR_CUDA;
+    }
     return HEXFC_OK;
 }
 
@@ -390,6 +581,14 @@ hexfc_status hexfc_create(hexfc_ctx** out, int device, uint64_t frag_budget_byte
     hexfc_style_default(&c->style);
     c->lens.mode = HEXFC_LENS_SCREEN;
     c->lens.radius = 1.0;
+    {
+        DeviceGuard g(device);
+        if (prepare_raster_kernels() != cudaSuccess || prepare_composite_kernels() != cudaSuccess) {
+            (void)cudaGetLastError();
+            delete c;
+            return HEXFC_ERR_CUDA;
+        }
+    }
     *out = c;
     return HEXFC_OK;
 }
@@ -401,6 +600,16 @@ void hexfc_destroy(hexfc_ctx* ctx)
     cudaDeviceSynchronize();
     ctx->meshes.clear();   // a mesh is freed with its last holder
     free_frame(ctx->fb);
+    for (auto& b : ctx->batch) {
+        free_frame(b->fb);
+        if (b->stream) cudaStreamDestroy(b->stream);
+        if (b->done) cudaEventDestroy(b->done);
+    }
+    for (auto& g : ctx->graph_exec)
+        if (g) cudaGraphExecDestroy(g);
+    if (ctx->origin) cudaStreamDestroy(ctx->origin);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     dfree(ctx->d_out);
     for (auto& set : ctx->ev)
         for (auto& e : set)
@@ -476,6 +685,94 @@ hexfc_status hexfc_upload_mesh(hexfc_ctx* ctx, const float* verts, int64_t n_ver
     return HEXFC_OK;
 }
 
+hexfc_status hexfc_render_batch(hexfc_ctx* ctx, int32_t n, const hexfc_batch_item* items,
+                                hexfc_frame_stats* stats, hexfc_status* item_status, void* stream)
+{
+    if (!ctx || n < 0 || (n > 0 && !items)) return HEXFC_ERR_ARG;
+    std::vector<CamParams> cams((size_t)n);
+    std::vector<double> zrefs((size_t)n, 1.0);
+    for (int32_t i = 0; i < n; ++i) {
+        const hexfc_batch_item& it = items[i];
+        if (!it.out_rgba || !valid_lens(&it.lens) || !valid_style(&it.style)) return HEXFC_ERR_ARG;
+        if (!valid_view(&it.view, cams[(size_t)i], zrefs[(size_t)i])) return HEXFC_ERR_ARG;
+        if (!get_mesh(ctx, it.mesh)) return HEXFC_ERR_STATE;
+    }
+    if (n == 0) return HEXFC_OK;
+    DeviceGuard g(ctx->device);
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (!ctx->origin) {
+        CK(cudaStreamCreateWithFlags(&ctx->origin, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
+    }
+    while ((int32_t)ctx->batch.size() < n) {
+        std::unique_ptr<hexfc_ctx::BatchSlot> b(new (std::nothrow) hexfc_ctx::BatchSlot());
+        if (!b) return HEXFC_ERR_OOM;
+        CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming));
+        ctx->batch.push_back(std::move(b));
+    }
+    std::vector<FrameJob> jobs((size_t)n);
+    std::vector<hexfc_status> res((size_t)n, HEXFC_OK);
+    std::vector<int> live;
+    hexfc_status st;
+    for (int32_t i = 0; i < n; ++i) {
+        const hexfc_batch_item& it = items[i];
+        FrameJob& j = jobs[(size_t)i];
+        j.fb = &ctx->batch[(size_t)i]->fb;
+        j.m = get_mesh(ctx, it.mesh);
+        j.cam = cams[(size_t)i];
+        j.sp = make_shade_params(it.lens, it.style, zrefs[(size_t)i], j.cam.ortho);
+        j.lod = it.style.lod;
+        j.delta = it.style.delta;
+        j.W = it.view.width;
+        j.H = it.view.height;
+        j.tiles_x = (j.W + kTile - 1) / kTile;
+        j.tiles_y = (j.H + kTile - 1) / kTile;
+        j.n_tiles = (int64_t)j.tiles_x * j.tiles_y;
+        j.n_pix = j.n_tiles * kTilePix;
+        j.reverse = ctx->reverse_bins;
+        j.buckets = ctx->depth_buckets;
+        j.window = ctx->window;
+        j.budget = ctx->budget;
+        j.out = it.out_rgba;
+        if ((st = job_alloc(j)) != HEXFC_OK) return st;
+        live.push_back(i);
+    }
+    // the batch starts after the caller's earlier work on its stream
+    CK(cudaEventRecord(ctx->ev_out, s));
+    CK(cudaStreamWaitEvent(ctx->origin, ctx->ev_out, 0));
+    if ((st = batch_graph(ctx, 0, live, [&](int i, cudaStream_t si) { return job_phase1(jobs[(size_t)i], si); })) !=
+        HEXFC_OK)
+        return st;
+    CK(cudaStreamSynchronize(ctx->origin));
+    for (int i : live)
+        if ((st = job_read1(jobs[(size_t)i])) != HEXFC_OK) return st;
+    if ((st = batch_graph(ctx, 1, live, [&](int i, cudaStream_t si) { return job_phase2(jobs[(size_t)i], si); })) !=
+        HEXFC_OK)
+        return st;
+    CK(cudaStreamSynchronize(ctx->origin));
+    std::vector<int> draw;
+    for (int i : live) {
+        res[(size_t)i] = job_read2(jobs[(size_t)i], ctx->batch[(size_t)i]->stream);
+        if (res[(size_t)i] == HEXFC_OK) draw.push_back(i);
+    }
+    if (!draw.empty() &&
+        (st = batch_graph(ctx, 2, draw, [&](int i, cudaStream_t si) { return job_phase3(jobs[(size_t)i], si); })) !=
+            HEXFC_OK)
+        return st;
+    // the caller's stream continues after the batch
+    CK(cudaEventRecord(ctx->ev_out, ctx->origin));
+    CK(cudaStreamWaitEvent(s, ctx->ev_out, 0));
+    hexfc_status first = HEXFC_OK;
+    for (int32_t i = 0; i < n; ++i) {
+        if (stats) stats[i] = jobs[(size_t)i].fs;
+        if (item_status) item_status[i] = res[(size_t)i];
+        if (first == HEXFC_OK) first = res[(size_t)i];
+    }
+    return first;
+}
+
 hexfc_status hexfc_frame_memory(const hexfc_ctx* ctx, uint64_t* bytes)
 {
     if (!ctx || !bytes) return HEXFC_ERR_ARG;
@@ -489,6 +786,16 @@ hexfc_status hexfc_frame_memory(const hexfc_ctx* ctx, uint64_t* bytes)
     b += (uint64_t)f.part_cap * (sizeof(uint64_t) + sizeof(uint32_t));
     b += (uint64_t)f.frag_cap * (sizeof(uint64_t) + sizeof(float4));
     b += (uint64_t)ctx->d_out_cap * sizeof(float);
+    for (const auto& bs : ctx->batch) {
+        const FrameBufs& g = bs->fb;
+        b += (uint64_t)g.v_cap * (sizeof(int4) + sizeof(float)) +
+             (uint64_t)g.f_cap * (sizeof(FaceFrame) + 2 * sizeof(uint32_t)) +
+             (uint64_t)g.t_cap * (3 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t)) +
+             (uint64_t)(g.bin_cap + g.mask_cap) * sizeof(uint32_t) +
+             (uint64_t)g.p_cap * (3 * sizeof(uint32_t) + sizeof(uint64_t)) +
+             (uint64_t)g.part_cap * (sizeof(uint64_t) + sizeof(uint32_t)) +
+             (uint64_t)g.frag_cap * (sizeof(uint64_t) + sizeof(float4));
+    }
     *bytes = b;
     return HEXFC_OK;
 }
@@ -501,6 +808,12 @@ hexfc_status hexfc_trim(hexfc_ctx* ctx)
     ctx->fb.h_scal = nullptr;   // the pinned mirror is small: keep it
     free_frame(ctx->fb);
     ctx->fb.h_scal = pinned;
+    for (auto& bs : ctx->batch) {
+        uint64_t* hp = bs->fb.h_scal;
+        bs->fb.h_scal = nullptr;
+        free_frame(bs->fb);
+        bs->fb.h_scal = hp;
+    }
     dfree(ctx->d_out);
     ctx->d_out_cap = 0;
     ctx->have_frame = false;
@@ -554,12 +867,9 @@ hexfc_status hexfc_mesh_info(hexfc_ctx* ctx, int32_t mesh, int64_t* n_faces, int
 hexfc_status hexfc_set_view(hexfc_ctx* ctx, const hexfc_view* v)
 {
     if (!ctx || !v) return HEXFC_ERR_ARG;
-    if (v->width < 1 || v->height < 1 || v->width > 16384 || v->height > 16384) return HEXFC_ERR_ARG;
-    if (!(v->znear < v->zfar) || !std::isfinite(v->znear) || !std::isfinite(v->zfar)) return HEXFC_ERR_ARG;
-    if (!(v->fovy_deg >= 0.0)) return HEXFC_ERR_ARG;
     CamParams c{};
     double zref = 1.0;
-    if (!make_camera(v, c, zref)) return HEXFC_ERR_ARG;
+    if (!valid_view(v, c, zref)) return HEXFC_ERR_ARG;
     ctx->view = *v;
     ctx->cam = c;
     ctx->zref = zref;
@@ -569,18 +879,14 @@ hexfc_status hexfc_set_view(hexfc_ctx* ctx, const hexfc_view* v)
 
 hexfc_status hexfc_set_lens(hexfc_ctx* ctx, const hexfc_lens* l)
 {
-    if (!ctx || !l) return HEXFC_ERR_ARG;
-    if (l->mode != HEXFC_LENS_SCREEN && l->mode != HEXFC_LENS_SPHERE) return HEXFC_ERR_ARG;
-    if (!(l->radius > 0.0) || !std::isfinite(l->radius)) return HEXFC_ERR_ARG;
+    if (!ctx || !l || !valid_lens(l)) return HEXFC_ERR_ARG;
     ctx->lens = *l;
     return HEXFC_OK;
 }
 
 hexfc_status hexfc_set_style(hexfc_ctx* ctx, const hexfc_style* s)
 {
-    if (!ctx || !s) return HEXFC_ERR_ARG;
-    if (!(s->w_base >= 0.f) || s->tf_hi == s->tf_lo || !(s->g_min <= s->g_max)) return HEXFC_ERR_ARG;
-    if (!(s->desat >= 0.f && s->desat <= 1.f)) return HEXFC_ERR_ARG;
+    if (!ctx || !s || !valid_style(s)) return HEXFC_ERR_ARG;
     ctx->style = *s;
     return HEXFC_OK;
 }
@@ -697,6 +1003,14 @@ hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value)
     switch (option) {
     case HEXFC_OPT_REVERSE_BIN_ORDER: ctx->reverse_bins = value != 0; return HEXFC_OK;
     case HEXFC_OPT_STAGE_TIMING: ctx->timing = value != 0; return HEXFC_OK;
+    case HEXFC_OPT_DEPTH_BUCKETS:
+        if (value < 256 || value > 4096 || (value & (value - 1)) != 0) return HEXFC_ERR_ARG;
+        ctx->depth_buckets = (int)value;
+        return HEXFC_OK;
+    case HEXFC_OPT_COMPOSITE_WINDOW:
+        if (value != 4 && value != 8) return HEXFC_ERR_ARG;
+        ctx->window = (int)value;
+        return HEXFC_OK;
     default: return HEXFC_ERR_ARG;
     }
 }
@@ -834,7 +1148,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     }
     CK(cudaMemsetAsync(fb.bins, 0xFF, sizeof(uint32_t) * (size_t)n_bins, s));   // padding slots = kPadBin
     CK(launch_bin_fill(*m, fb, tiles_x, W, H, ctx->reverse_bins, s));
-    CK(launch_bin_sort(*m, fb, tiles_x, tiles_y, s));
+    CK(launch_bin_sort(*m, fb, tiles_x, tiles_y, ctx->depth_buckets, s));
     CK(launch_tile_order(fb, n_tiles, s));
     CK(launch_count(*m, fb, tiles_x, tiles_y, W, H, s));
     CK(scan_u32_to_u64(fb.cnt, fb.off, n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
@@ -854,7 +1168,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     if (!fb.key || !fb.rgba) return HEXFC_ERR_OVERFLOW;
     ShadeParams sp = make_shade(ctx);
     CK(launch_fill(*m, fb, sp, tiles_x, tiles_y, W, H, s));
-    CK(launch_composite(fb, sp, tiles_x, tiles_y, W, H, out, n_long, s));
+    CK(launch_composite(fb, sp, tiles_x, tiles_y, W, H, out, n_long, ctx->window, s));
     return HEXFC_OK;
 }
 

@@ -125,14 +125,19 @@ cudaError_t launch_face_setup(const DevMesh& m, const CamParams& cam, int lod, f
                               FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_t s);
 cudaError_t launch_bin_fill(const DevMesh& m, FrameBufs& fb, int tiles_x, int W, int H, int reverse,
                             cudaStream_t s);
-cudaError_t launch_bin_sort(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_t s);
+// Kernel attributes (dynamic shared memory limits), once per device context.
+cudaError_t prepare_raster_kernels();
+cudaError_t prepare_composite_kernels();
+
+cudaError_t launch_bin_sort(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int buckets,
+                            cudaStream_t s);
 cudaError_t launch_tile_order(FrameBufs& fb, int n_tiles, cudaStream_t s);
 cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int W, int H,
                          cudaStream_t s);
 cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x,
                         int tiles_y, int W, int H, cudaStream_t s);
-cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W,
-                             int H, float* out, uint32_t n_long, cudaStream_t s);
+cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W, int H,
+                             float* out, uint32_t n_long, int window, cudaStream_t s);
 cudaError_t launch_debug_gather(FrameBufs& fb, const int32_t* d_px, const int32_t* d_py, int64_t n,
                                 const uint64_t* d_dst_off, int tiles_x, int W, int H,
                                 uint64_t* d_keys, float4* d_rgba, uint32_t* d_counts,

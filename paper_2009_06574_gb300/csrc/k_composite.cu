@@ -179,15 +179,14 @@ __device__ __forceinline__ float4 finish(CT c, float bg0, float bg1, float bg2)
 }
 
 // One thread per pixel (tile-major order, so a warp's 32 lists are one
-// contiguous range): the lane streams its list through a sorted window of
-// kWin (key, colour) pairs in registers and blends the smallest pair each time
-// the window overflows, so a list whose elements sit at most kWin - 1 places
-// from their sorted position comes out sorted. The blend checks that the keys
-// it consumes increase; a list that breaks that is queued for the warp-wide
+// contiguous range): the lane streams its list through a sorted window of KW
+// (key, colour) pairs in registers and blends the smallest pair each time the
+// window overflows, so a list whose elements sit at most KW - 1 places from
+// their sorted position comes out sorted. The blend checks that the keys it
+// consumes increase; a list that breaks that is queued for the warp-wide
 // resolve of k_composite_fix, and lists longer than 256 for the block-wide
-// sort of k_composite_long.
-constexpr int kWin = 4;
-
+// sort of k_composite_long. KW (4 or 8) trades registers for fewer queued
+// lists; the result does not depend on it.
 struct KC {
     uint64_t k;
     float4 c;
@@ -208,6 +207,7 @@ __device__ __forceinline__ void blend_checked(CT& c, uint64_t& last, bool& ok, c
     c = ct_over(c, CT{e.c.x, e.c.y, e.c.z, 1.f - e.c.w});
 }
 
+template <int KW>
 __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ cnt,
                                                    const uint64_t* __restrict__ off,
                                                    const uint64_t* __restrict__ key,
@@ -233,31 +233,32 @@ __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ 
     CT c{0.f, 0.f, 0.f, 1.f};
     bool ok = true;
     uint64_t last = 0;   // keys are > 0 unless depth and face id are both 0, which the check then flags
-    // window w[0] <= w[1] <= w[2] <= w[3], filled from the first kWin elements
+    // the window w[0] <= ... <= w[KW-1], filled from the first KW elements
     const uint64_t kPad = ~0ull;
-    KC w0{kPad, {}}, w1{kPad, {}}, w2{kPad, {}}, w3{kPad, {}};
-    const uint32_t pre = n < (uint32_t)kWin ? n : (uint32_t)kWin;
-    if (pre > 0) w0 = KC{kp[0], rp[0]};
-    if (pre > 1) w1 = KC{kp[1], rp[1]};
-    if (pre > 2) w2 = KC{kp[2], rp[2]};
-    if (pre > 3) w3 = KC{kp[3], rp[3]};
-    kc_sort2(w0, w1); kc_sort2(w2, w3); kc_sort2(w0, w2); kc_sort2(w1, w3); kc_sort2(w1, w2);
-    for (uint32_t i = kWin; i < n; ++i) {
-        KC e{kp[i], rp[i]};
-        if (e.k < w0.k) {          // smaller than the whole window: blend it at once
+    KC w[KW];
+    const uint32_t pre = n < (uint32_t)KW ? n : (uint32_t)KW;
+#pragma unroll
+    for (int k = 0; k < KW; ++k) w[k] = (uint32_t)k < pre ? KC{kp[k], rp[k]} : KC{kPad, {}};
+#pragma unroll
+    for (int pass = 0; pass < KW; ++pass)   // odd-even transposition sort
+#pragma unroll
+        for (int k = pass & 1; k + 1 < KW; k += 2) kc_sort2(w[k], w[k + 1]);
+    for (uint32_t i = KW; i < n; ++i) {
+        const KC e{kp[i], rp[i]};
+        if (e.k < w[0].k) {        // smaller than the whole window: blend it at once
             blend_checked(c, last, ok, e);
         } else {                   // blend the window's minimum, insert e
-            blend_checked(c, last, ok, w0);
-            w0 = w1; w1 = w2; w2 = w3; w3 = e;
-            kc_sort2(w2, w3);
-            kc_sort2(w1, w2);
-            kc_sort2(w0, w1);
+            blend_checked(c, last, ok, w[0]);
+#pragma unroll
+            for (int k = 0; k + 1 < KW; ++k) w[k] = w[k + 1];
+            w[KW - 1] = e;
+#pragma unroll
+            for (int k = KW - 1; k > 0; --k) kc_sort2(w[k - 1], w[k]);
         }
     }
-    if (pre > 0) blend_checked(c, last, ok, w0);
-    if (pre > 1) blend_checked(c, last, ok, w1);
-    if (pre > 2) blend_checked(c, last, ok, w2);
-    if (pre > 3) blend_checked(c, last, ok, w3);
+#pragma unroll
+    for (int k = 0; k < KW; ++k)
+        if ((uint32_t)k < pre) blend_checked(c, last, ok, w[k]);
     if (ok) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
     else fix_q[atomicAdd(fix_cursor, 1ull)] = (uint32_t)q;
 }
@@ -417,23 +418,31 @@ constexpr unsigned kFixBlocks = 4 * 152;   // persistent: warps stride over the 
 }  // namespace
 
 cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W, int H, float* out,
-                             uint32_t n_long, cudaStream_t s)
+                             uint32_t n_long, int window, cudaStream_t s)
 {
     float4* o4 = reinterpret_cast<float4*>(out);
     const int64_t n_pix = (int64_t)tiles_x * tiles_y * kTilePix;
     unsigned long long* long_cursor = reinterpret_cast<unsigned long long*>(fb.scal + 3);
     unsigned long long* fix_cursor = reinterpret_cast<unsigned long long*>(fb.scal + 4);
-    k_composite<<<(unsigned)((n_pix + 255) / 256), 256, 0, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, n_pix, tiles_x, W, H,
-                                                              sp.bg[0], sp.bg[1], sp.bg[2], o4, fb.long_q,
-                                                              long_cursor, fb.fix_q, fix_cursor);
+    const unsigned grid = (unsigned)((n_pix + 255) / 256);
+    if (window == 8)
+        k_composite<8><<<grid, 256, 0, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, n_pix, tiles_x, W, H, sp.bg[0], sp.bg[1],
+                                            sp.bg[2], o4, fb.long_q, long_cursor, fb.fix_q, fix_cursor);
+    else
+        k_composite<4><<<grid, 256, 0, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, n_pix, tiles_x, W, H, sp.bg[0], sp.bg[1],
+                                            sp.bg[2], o4, fb.long_q, long_cursor, fb.fix_q, fix_cursor);
     k_composite_fix<<<kFixBlocks, 256, 0, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, tiles_x, W, sp.bg[0], sp.bg[1],
                                                sp.bg[2], o4, fb.fix_q, fix_cursor);
     if (n_long > 0) {
-        cudaFuncSetAttribute(k_composite_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSmem);
         k_composite_long<<<n_long, 1024, kLongSmem, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, fb.long_q, tiles_x, W,
                                                          sp.bg[0], sp.bg[1], sp.bg[2], o4);
     }
     return cudaGetLastError();
+}
+
+cudaError_t prepare_composite_kernels()
+{
+    return cudaFuncSetAttribute(k_composite_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSmem);
 }
 
 cudaError_t launch_debug_gather(FrameBufs& fb, const int32_t* d_px, const int32_t* d_py, int64_t n,

@@ -149,18 +149,18 @@ __global__ void k_bin_fill(const FaceFrame* __restrict__ fframe, int64_t n_faces
 // ------------------------------------------------------------------ bin order
 
 constexpr int kBinSortMax = 4096;   // longer tile lists keep their arrival order
-constexpr int kDepthBuckets = 2048;
+constexpr int kDepthBucketsMax = 4096;
 
 // Orders each tile's list front to back by a counting sort of the triangles
-// into kDepthBuckets buckets of their depth (sum of the three window depths)
+// into nb buckets (a power of two, 256..kDepthBucketsMax) of their depth (sum of the three window depths)
 // over the tile's depth range; the padding slots stay at the end. Any order
 // gives the same fragments; this one makes the fill write every per-pixel list
 // sorted or nearly sorted (order within a bucket is arbitrary).
 __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ tile_off,
                                                   const uint32_t* __restrict__ tile_cnt, uint32_t* __restrict__ bins,
-                                                  const uint32_t* __restrict__ tzsum)
+                                                  const uint32_t* __restrict__ tzsum, int nb)
 {
-    __shared__ uint32_t s_hist[kDepthBuckets];
+    __shared__ uint32_t s_hist[kDepthBucketsMax];
     __shared__ uint16_t s_b[kBinSortMax];
     __shared__ uint32_t s_out[kBinSortMax];
     __shared__ uint32_t s_red[2][8];
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
         zmin = min(zmin, zs);
         zmax = max(zmax, zs);
     }
-    for (int i = threadIdx.x; i < kDepthBuckets; i += blockDim.x) s_hist[i] = 0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s_hist[i] = 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         zmin = min(zmin, __shfl_xor_sync(0xffffffffu, zmin, o));
@@ -188,20 +188,21 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
     zmin = s_red[0][0];
     zmax = s_red[1][0];
     for (int w = 1; w < 8; ++w) { zmin = min(zmin, s_red[0][w]); zmax = max(zmax, s_red[1][w]); }
-    const float scale = (float)kDepthBuckets / (float)(zmax - zmin + 1);
+    const float scale = (float)nb / (float)(zmax - zmin + 1);
     // histogram
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const int b = min((int)((float)(zsum(bins[beg + i]) - zmin) * scale), kDepthBuckets - 1);
+        const int b = min((int)((float)(zsum(bins[beg + i]) - zmin) * scale), nb - 1);
         s_b[i] = (uint16_t)b;
         atomicAdd(&s_hist[b], 1u);
     }
     __syncthreads();
-    // exclusive scan of the histogram: 8 buckets per thread
+    // exclusive scan of the histogram: nb / 256 buckets per thread
     {
-        uint32_t v[kDepthBuckets / 256], sum = 0;
+        const int per = nb / 256;
+        uint32_t v[kDepthBucketsMax / 256], sum = 0;
 #pragma unroll
-        for (int k = 0; k < kDepthBuckets / 256; ++k) {
-            v[k] = s_hist[threadIdx.x * (kDepthBuckets / 256) + k];
+        for (int k = 0; k < kDepthBucketsMax / 256; ++k) {
+            v[k] = k < per ? s_hist[threadIdx.x * per + k] : 0u;
             sum += v[k];
         }
         uint32_t incl = sum;
@@ -216,8 +217,8 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
         uint32_t base = incl - sum;
         for (int w = 0; w < warp; ++w) base += s_red[0][w];
 #pragma unroll
-        for (int k = 0; k < kDepthBuckets / 256; ++k) {
-            s_hist[threadIdx.x * (kDepthBuckets / 256) + k] = base;
+        for (int k = 0; k < kDepthBucketsMax / 256; ++k) {
+            if (k < per) s_hist[threadIdx.x * per + k] = base;
             base += v[k];
         }
     }
@@ -783,6 +784,15 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __rest
 
 }  // namespace
 
+cudaError_t prepare_raster_kernels()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kConsumerWarps * sizeof(CountWarp)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem_bytes());
+    return e;
+}
+
 cudaError_t launch_vertex_setup(const DevMesh& m, const CamParams& cam, FrameBufs& fb, cudaStream_t s)
 {
     k_vertex_setup<<<grid_for(m.n_verts, 256), 256, 0, s>>>(m.verts, m.n_verts, cam, fb.vproj, fb.ved);
@@ -807,10 +817,10 @@ cudaError_t launch_bin_fill(const DevMesh& m, FrameBufs& fb, int tiles_x, int W,
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_sort(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, cudaStream_t s)
+cudaError_t launch_bin_sort(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int buckets, cudaStream_t s)
 {
     (void)m;
-    k_bin_sort<<<(unsigned)(tiles_x * tiles_y), 256, 0, s>>>(fb.tile_off, fb.tile_cnt, fb.bins, fb.tzsum);
+    k_bin_sort<<<(unsigned)(tiles_x * tiles_y), 256, 0, s>>>(fb.tile_off, fb.tile_cnt, fb.bins, fb.tzsum, buckets);
     return cudaGetLastError();
 }
 
@@ -823,7 +833,6 @@ cudaError_t launch_tile_order(FrameBufs& fb, int n_tiles, cudaStream_t s)
 cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, cudaStream_t s)
 {
     const size_t smem = kConsumerWarps * sizeof(CountWarp);
-    cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_count<<<(unsigned)(tiles_x * tiles_y), kTilePix, smem, s>>>(fb.tile_off, fb.bins, fb.fframe, fb.tile_order,
                                                                    tiles_x, W, H, fb.cnt, fb.masks);
     return cudaGetLastError();
@@ -833,7 +842,6 @@ cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, 
                         int H, cudaStream_t s)
 {
     const size_t smem = fill_smem_bytes();
-    cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_fill<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, smem, s>>>(
         fb.tile_off, fb.bins, fb.masks, fb.fframe, m.fstat, fb.tile_order, tiles_x, W, H, sp, fb.off, fb.key, fb.rgba,
         reinterpret_cast<unsigned long long*>(fb.scal + 5));

@@ -34,6 +34,8 @@ HEXFC_METRIC_JACOBIAN_RATIO = 1
 HEXFC_METRIC_IMPORTANCE = 2
 HEXFC_OPT_REVERSE_BIN_ORDER = 1
 HEXFC_OPT_STAGE_TIMING = 2
+HEXFC_OPT_DEPTH_BUCKETS = 3
+HEXFC_OPT_COMPOSITE_WINDOW = 4
 STAGES = ["vertex", "face", "tile_scan", "gap1", "bin", "count", "scan", "gap2", "fill", "composite"]
 
 # every symbol include/hexfc.h declares
@@ -41,7 +43,7 @@ EXPORTS = ["hexfc_style_default", "hexfc_create", "hexfc_destroy", "hexfc_upload
            "hexfc_set_cell_importance", "hexfc_mesh_info", "hexfc_set_view", "hexfc_set_lens",
            "hexfc_set_style", "hexfc_render", "hexfc_render_host", "hexfc_debug_pixels", "hexfc_set_option",
            "hexfc_stage_times", "hexfc_status_string", "hexfc_render_noalloc", "hexfc_share_mesh",
-           "hexfc_frame_memory", "hexfc_trim"]
+           "hexfc_frame_memory", "hexfc_trim", "hexfc_render_batch"]
 
 
 class HexfcError(RuntimeError):
@@ -75,6 +77,11 @@ class hexfc_frame_stats(C.Structure):
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class hexfc_batch_item(C.Structure):
+    _fields_ = [("mesh", C.c_int32), ("pad", C.c_int32), ("view", hexfc_view), ("lens", hexfc_lens),
+                ("style", hexfc_style), ("out_rgba", C.c_void_p)]
 
 
 _lib = None
@@ -114,6 +121,7 @@ def load():
                 "hexfc_share_mesh": (i32, [vp, vp, i32, C.POINTER(i32)]),
                 "hexfc_frame_memory": (i32, [vp, C.POINTER(u64)]),
                 "hexfc_trim": (i32, [vp]),
+                "hexfc_render_batch": (i32, [vp, i32, vp, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -278,6 +286,25 @@ class Renderer:
         if check:
             _check(r, "hexfc_render")
         return r
+
+    def render_batch(self, items, stream=None, check: bool = True):
+        """items: list of (mesh, view, lens, style, out) with out a torch float32
+        CUDA tensor [H, W, 4]. Returns (status, per-item statuses, per-item stats)."""
+        n = len(items)
+        arr = (hexfc_batch_item * max(n, 1))()
+        for k, (mesh, view, lens, style, out) in enumerate(items):
+            arr[k].mesh = int(mesh)
+            arr[k].view = make_view(view)
+            arr[k].lens = make_lens(lens)
+            arr[k].style = make_style(style)
+            arr[k].out_rgba = C.c_void_p(out.data_ptr())
+        st = (hexfc_frame_stats * max(n, 1))()
+        ist = (C.c_int32 * max(n, 1))()
+        r = load().hexfc_render_batch(self._h, n, C.cast(arr, C.c_void_p), C.cast(st, C.c_void_p),
+                                      C.cast(ist, C.c_void_p), _stream_ptr(stream))
+        if check:
+            _check(r, "hexfc_render_batch")
+        return r, [int(ist[k]) for k in range(n)], [st[k].as_dict() for k in range(n)]
 
     def render_noalloc(self, mesh: int, out, stream=None, check: bool = True):
         """Like render, with every per-frame buffer in the library's fixed scratch
