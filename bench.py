@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-steps", type=int, default=60)
+    ap.add_argument("--predicted", type=int, default=0,
+                    help="tile capacities: 0 count-then-fill, 1 previous frame's counts, 2 capacity network")
     # serving mode (--workload serving): Poisson request stream over resident meshes
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean requests per second")
     ap.add_argument("--requests", type=int, default=600, help="serving: requests in the timed stream")
@@ -239,10 +241,13 @@ def run_ours(args, rank, world, local_rank):
     mid = r.upload_mesh(mesh.verts, mesh.cells, None, mesh.edge_level)
     n_faces, n_edges = r.mesh_info(mid)
     r.set_style(w.style)
+    if args.predicted:
+        r.set_option(hexfc.HEXFC_OPT_PREDICTED_CAPACITY, args.predicted)
     out = torch.empty((w.height, w.width, 4), dtype=torch.float32, device=dev)
     imp = torch.empty(mesh.n_cells, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     frags = []
+    predicted_frames = []
 
     def step(i):
         f = replica_frames(rank, world, w.n_frames, i, 1)[0]
@@ -252,6 +257,7 @@ def run_ours(args, rank, world, local_rank):
         r.set_cell_importance(mid, imp, stream)
         r.render(mid, out, stream)
         frags.append(r.last_stats["fragments"])
+        predicted_frames.append(r.last_stats["predicted"])
         return r.last_stats
 
     for i in range(args.warmup):
@@ -352,8 +358,10 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": w.name, "cells": mesh.n_cells, "faces": n_faces, "width": w.width,
                    "height": w.height, "frames": w.n_frames,
                    "l2": "not flushed: per-frame working set (fragment lists) far larger than L2",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "tile_capacity": ["count pass", "previous frame", "capacity network"][args.predicted]},
         "fragments_per_s": F * fps, "fragments_per_frame": F, "bins_per_frame": bins,
+        "predicted_frames": int(sum(predicted_frames[-args.steps:])),
         "kernels_gbs": {k: round(algo[k] / (kernel_stages[k] / 1000.0) / 1e9, 1) for k in algo},
         "stage_ms": {k: round(v, 4) for k, v in per_frame.items()},
         "roofline": {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved, "peak": peak, "unit": "GB/s",

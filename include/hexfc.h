@@ -119,6 +119,9 @@ typedef struct hexfc_frame_stats {
     uint32_t width, height;
     uint32_t kernel_launches;  /* kernels this call launched */
     uint32_t covered_pixels;   /* reserved (0) */
+    uint32_t predicted;        /* 1: drawn with chosen tile capacities and no count pass */
+    uint32_t overflow_tiles;   /* tiles above their chosen capacity (the frame was then drawn exactly) */
+    uint64_t capacity;         /* sum of the chosen tile capacities (fragments), 0 if none */
 } hexfc_frame_stats;
 
 /* Stages timed by HEXFC_OPT_STAGE_TIMING (CUDA events on the render stream).
@@ -306,9 +309,25 @@ enum {
     HEXFC_OPT_STAGE_TIMING = 2,      /* 1: record CUDA events around every stage of hexfc_render* */
     HEXFC_OPT_DEPTH_BUCKETS = 3,     /* buckets of the per-tile depth order of the triangles: a power of
                                         two in 256..4096 (default 2048) */
-    HEXFC_OPT_COMPOSITE_WINDOW = 4   /* sorted window of the per-pixel resolve: 4 (default) or 8 */
+    HEXFC_OPT_COMPOSITE_WINDOW = 4,  /* sorted window of the per-pixel resolve: 4 (default) or 8 */
+    HEXFC_OPT_PREDICTED_CAPACITY = 5 /* 0: count-then-fill (default); 1: capacities from the previous
+                                        frame's tile counts; 2: from the capacity network. See below. */
 };
 hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value);
+
+/*
+ * Predicted capacities (HEXFC_OPT_PREDICTED_CAPACITY != 0; no counterpart in
+ * the paper, which sizes its buffers once): the fragment arrays are divided
+ * into per-16x16-tile regions of a chosen capacity before the frame, and one
+ * fused pass per tile counts the tile's coverage, lays out its lists inside
+ * the region and draws them, so there is no separate count pass, no global
+ * scan and no host wait between counting and drawing. Capacities come from
+ * the previous frame's exact tile counts (mode 1: count * 1.15 + 256) or from
+ * the capacity network (mode 2, see hexfc_capacity_*). A frame with a tile
+ * above its capacity is drawn again by the exact count-then-fill path, so
+ * the image is always exact; stats.overflow_tiles reports it. The first frame
+ * at a resolution, with no previous counts, is drawn exactly.
+ */
 
 /*
  * Accumulated stage times (milliseconds, summed over frames) since the last

@@ -27,6 +27,10 @@ struct hexfc_ctx {
     int reverse_bins = 0;
     int depth_buckets = 2048;   // HEXFC_OPT_DEPTH_BUCKETS
     int window = 4;             // HEXFC_OPT_COMPOSITE_WINDOW
+    int predicted = 0;          // HEXFC_OPT_PREDICTED_CAPACITY
+    // exact tile counts of the last frame (fb.tile_frag) are valid for this size
+    int counts_W = 0, counts_H = 0;
+    uint64_t counts_total = 0;
     // last render
     bool have_frame = false;
     int last_W = 0, last_H = 0, last_tiles_x = 0, last_tiles_y = 0;
@@ -123,7 +127,7 @@ void free_mesh(DevMesh* m)
 void free_frame(FrameBufs& f)
 {
     dfree(f.vproj); dfree(f.ved); dfree(f.fframe); dfree(f.tzsum);
-    dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.tile_order); dfree(f.bins); dfree(f.masks); dfree(f.cnt);
+    dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.tile_order); dfree(f.tile_frag); dfree(f.tile_cap); dfree(f.cap_off); dfree(f.tile_over); dfree(f.bins); dfree(f.masks); dfree(f.cnt);
     dfree(f.off);
     dfree(f.part); dfree(f.part_max); dfree(f.long_q); dfree(f.fix_q); dfree(f.key); dfree(f.rgba); dfree(f.scal);
     if (f.h_scal) cudaFreeHost(f.h_scal);
@@ -326,12 +330,13 @@ hexfc_status job_alloc(FrameJob& j)
         if ((st = ensure(&fb.tzsum, &c1, 2 * fb.f_cap)) != HEXFC_OK) return st;
     }
     if (!fb.tile_cnt || fb.t_cap < j.n_tiles + 1) {
-        int64_t c1 = 0, c2 = 0, c3 = 0;
-        dfree(fb.tile_off); dfree(fb.tile_cur); dfree(fb.tile_order);
+        int64_t c1 = 0, c2 = 0, c3 = 0, c4 = 0;
+        dfree(fb.tile_off); dfree(fb.tile_cur); dfree(fb.tile_order); dfree(fb.tile_frag);
         if ((st = ensure(&fb.tile_cnt, &fb.t_cap, j.n_tiles + 1)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.tile_off, &c1, fb.t_cap)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.tile_cur, &c2, fb.t_cap)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.tile_order, &c3, fb.t_cap)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.tile_frag, &c4, fb.t_cap)) != HEXFC_OK) return st;
     }
     if (!fb.cnt || fb.p_cap < j.n_pix + 1) {
         int64_t c1 = 0, c2 = 0, c3 = 0;
@@ -483,6 +488,115 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
     ctx->last_H = j.H;
     ctx->last_tiles_x = j.tiles_x;
     ctx->last_tiles_y = j.tiles_y;
+    ctx->counts_W = j.W;   // k_count left the exact tile counts in fb.tile_frag
+    ctx->counts_H = j.H;
+    ctx->counts_total = j.total;
+    return HEXFC_OK;
+}
+
+constexpr float kCapMargin = 0.15f;   // capacity = predicted count * (1 + margin) + pad
+constexpr uint32_t kCapPad = 256;
+constexpr uint32_t kLongListsUnknown = 1u << 30;   // the long-list pass reads the queue length on the device
+
+// A frame with chosen tile capacities and the fused count-and-fill pass; on
+// an overflow, the frame is drawn again by render_frame.
+hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_stats* stats,
+                                    cudaStream_t s)
+{
+    if (ctx->counts_W != ctx->view.width || ctx->counts_H != ctx->view.height)
+        return render_frame(ctx, m, out, stats, s);   // no tile counts for this size yet
+    FrameJob j = make_job(ctx, &ctx->fb, m, out);
+    FrameBufs& fb = ctx->fb;
+    hexfc_status st;
+    if ((st = job_alloc(j)) != HEXFC_OK) return st;
+    if (!fb.tile_cap || fb.cap_cap < fb.t_cap) {   // capacity arrays follow the tile arrays
+        int64_t c1 = 0, c2 = 0;
+        dfree(fb.cap_off); dfree(fb.tile_over);
+        if ((st = ensure(&fb.tile_cap, &fb.cap_cap, fb.t_cap)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.cap_off, &c1, fb.cap_cap)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.tile_over, &c2, fb.cap_cap)) != HEXFC_OK) return st;
+    }
+    // fragment arrays for the capacities of this frame (previous counts * margin + pad)
+    const uint64_t want = (uint64_t)((double)ctx->counts_total * (1.0 + kCapMargin) * 1.1) +
+                          (uint64_t)j.n_tiles * kCapPad;
+    if (!fb.key || fb.frag_cap < (int64_t)want) {
+        int64_t c1 = 0;
+        dfree(fb.rgba);
+        if ((st = ensure(&fb.key, &fb.frag_cap, (int64_t)want)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.rgba, &c1, fb.frag_cap)) != HEXFC_OK) return st;
+    }
+    if (ctx->timing && !ctx->ev[0][0])
+        for (auto& set : ctx->ev)
+            for (auto& e : set) CK(cudaEventCreate(&e));
+    ctx->ev_cur ^= 1;
+    j.timing = ctx;
+    if ((st = job_phase1(j, s)) != HEXFC_OK) return st;
+    CK(cudaStreamSynchronize(s));
+    collect(ctx);
+    if ((st = job_read1(j)) != HEXFC_OK) return st;
+    job_mark(j, 4, s);
+    CK(cudaMemsetAsync(fb.bins, 0xFF, sizeof(uint32_t) * (size_t)j.n_bins, s));   // padding slots = kPadBin
+    CK(launch_bin_fill(*m, fb, j.tiles_x, j.W, j.H, j.reverse, s));
+    CK(launch_bin_sort(*m, fb, j.tiles_x, j.tiles_y, j.buckets, s));
+    CK(launch_tile_order(fb, j.n_tiles, s));
+    job_mark(j, 5, s);
+    CK(launch_capacity_from_previous(fb, j.n_tiles, kCapMargin, kCapPad, s));
+    job_mark(j, 6, s);
+    CK(scan_u32_to_u64(fb.tile_cap, fb.cap_off, j.n_tiles, fb.part, fb.part_max, fb.scal + 11, 0xFFFFFFFFu, s));
+    job_mark(j, 7, s);
+    CK(launch_count_fill(*m, fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, s));
+    job_mark(j, 8, s);
+    j.launches += 4 + 1 + 3 + 1;
+    CK(cudaMemcpyAsync(fb.h_scal, fb.scal, 16 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (fb.h_scal[5] != 0) {
+        const uint64_t bits = fb.h_scal[5];
+        CK(cudaMemsetAsync(fb.scal + 5, 0, sizeof(uint64_t), s));
+        return (bits & 6ull) ? HEXFC_ERR_TIMEOUT : HEXFC_ERR_CUDA;
+    }
+    const uint32_t overflow = (uint32_t)fb.h_scal[6];
+    const uint64_t capacity = fb.h_scal[11];
+    if (fb.h_scal[1] > HEXFC_MAX_LIST || capacity + fb.h_scal[14] > (uint64_t)fb.frag_cap) {
+        // a list too long, or no room after the regions for the tiles that did not fit: exact path
+        // (fb.tile_frag already holds this frame's exact counts; k_count rewrites them)
+        st = render_frame(ctx, m, out, stats, s);
+        ctx->last.overflow_tiles = overflow;
+        ctx->last.capacity = capacity;
+        if (stats) {
+            stats->overflow_tiles = overflow;
+            stats->capacity = capacity;
+        }
+        return st;
+    }
+    if (overflow > 0) {   // the tiles above their capacity, in regions after all others
+        CK(launch_overflow_fill(*m, fb, j.sp, overflow, capacity, j.tiles_x, j.W, j.H, s));
+        j.launches += 2;
+    }
+    job_mark(j, 9, s);
+    CK(launch_composite(fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, out, kLongListsUnknown, j.window, s));
+    job_mark(j, 10, s);
+    j.launches += 3;
+    ctx->ev_pending[ctx->ev_cur] = ctx->timing;
+    hexfc_frame_stats& fs = j.fs;
+    fs = hexfc_frame_stats{};
+    fs.fragments = fb.h_scal[0];
+    fs.bin_entries = j.n_bins;
+    fs.max_list = (uint32_t)fb.h_scal[1];
+    fs.long_lists = (uint32_t)fb.h_scal[2];
+    fs.width = (uint32_t)j.W;
+    fs.height = (uint32_t)j.H;
+    fs.kernel_launches = j.launches;
+    fs.predicted = 1;
+    fs.overflow_tiles = overflow;
+    fs.capacity = capacity;
+    ctx->last = fs;
+    if (stats) *stats = fs;
+    ctx->have_frame = true;
+    ctx->last_W = j.W;
+    ctx->last_H = j.H;
+    ctx->last_tiles_x = j.tiles_x;
+    ctx->last_tiles_y = j.tiles_y;
+    ctx->counts_total = fs.fragments;
     return HEXFC_OK;
 }
 
@@ -780,7 +894,7 @@ hexfc_status hexfc_frame_memory(const hexfc_ctx* ctx, uint64_t* bytes)
     uint64_t b = 0;
     b += (uint64_t)f.v_cap * (sizeof(int4) + sizeof(float));
     b += (uint64_t)f.f_cap * (sizeof(FaceFrame) + 2 * sizeof(uint32_t));
-    b += (uint64_t)f.t_cap * (3 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t));
+    b += (uint64_t)f.t_cap * (4 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t));
     b += (uint64_t)f.bin_cap * sizeof(uint32_t) + (uint64_t)f.mask_cap * sizeof(uint32_t);
     b += (uint64_t)f.p_cap * (3 * sizeof(uint32_t) + sizeof(uint64_t));
     b += (uint64_t)f.part_cap * (sizeof(uint64_t) + sizeof(uint32_t));
@@ -790,7 +904,7 @@ hexfc_status hexfc_frame_memory(const hexfc_ctx* ctx, uint64_t* bytes)
         const FrameBufs& g = bs->fb;
         b += (uint64_t)g.v_cap * (sizeof(int4) + sizeof(float)) +
              (uint64_t)g.f_cap * (sizeof(FaceFrame) + 2 * sizeof(uint32_t)) +
-             (uint64_t)g.t_cap * (3 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t)) +
+             (uint64_t)g.t_cap * (4 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t)) +
              (uint64_t)(g.bin_cap + g.mask_cap) * sizeof(uint32_t) +
              (uint64_t)g.p_cap * (3 * sizeof(uint32_t) + sizeof(uint64_t)) +
              (uint64_t)g.part_cap * (sizeof(uint64_t) + sizeof(uint32_t)) +
@@ -897,6 +1011,7 @@ hexfc_status hexfc_render(hexfc_ctx* ctx, int32_t mesh, float* out_rgba, hexfc_f
     DevMesh* m = get_mesh(ctx, mesh);
     if (!m || !ctx->have_view) return HEXFC_ERR_STATE;
     DeviceGuard g(ctx->device);
+    if (ctx->predicted) return render_frame_predicted(ctx, m, out_rgba, stats, (cudaStream_t)stream);
     return render_frame(ctx, m, out_rgba, stats, (cudaStream_t)stream);
 }
 
@@ -912,7 +1027,7 @@ hexfc_status hexfc_render_host(hexfc_ctx* ctx, int32_t mesh, float* out_rgba_hos
     hexfc_status st = ensure(&ctx->d_out, &ctx->d_out_cap, (int64_t)(bytes / sizeof(float)));
     if (st != HEXFC_OK) return st;
     float* d_out = ctx->d_out;
-    st = render_frame(ctx, m, d_out, stats, s);
+    st = ctx->predicted ? render_frame_predicted(ctx, m, d_out, stats, s) : render_frame(ctx, m, d_out, stats, s);
     if (st == HEXFC_OK) {
         cudaError_t e = cudaMemcpyAsync(out_rgba_host, d_out, bytes, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1010,6 +1125,10 @@ hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value)
     case HEXFC_OPT_COMPOSITE_WINDOW:
         if (value != 4 && value != 8) return HEXFC_ERR_ARG;
         ctx->window = (int)value;
+        return HEXFC_OK;
+    case HEXFC_OPT_PREDICTED_CAPACITY:
+        if (value < 0 || value > 2) return HEXFC_ERR_ARG;
+        ctx->predicted = (int)value;
         return HEXFC_OK;
     default: return HEXFC_ERR_ARG;
     }
@@ -1113,6 +1232,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fb.tile_off = a.take<uint64_t>((size_t)n_tiles + 1);
     fb.tile_cur = a.take<uint32_t>((size_t)n_tiles + 1);
     fb.tile_order = a.take<uint32_t>((size_t)n_tiles + 1);
+    fb.tile_frag = a.take<uint32_t>((size_t)n_tiles + 1);
     fb.cnt = a.take<uint32_t>((size_t)n_pix + 1);
     fb.off = a.take<uint64_t>((size_t)n_pix + 1);
     fb.long_q = a.take<uint32_t>((size_t)n_pix + 1);
@@ -1121,7 +1241,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fb.part_max = a.take<uint32_t>(2 * (size_t)nparts);
     fb.scal = a.take<uint64_t>(16);
     if (!fb.vproj || !fb.ved || !fb.fframe || !fb.tzsum || !fb.tile_cnt ||
-        !fb.tile_off || !fb.tile_cur || !fb.tile_order || !fb.cnt || !fb.off || !fb.long_q || !fb.fix_q || !fb.part || !fb.part_max ||
+        !fb.tile_off || !fb.tile_cur || !fb.tile_order || !fb.tile_frag || !fb.cnt || !fb.off || !fb.long_q || !fb.fix_q || !fb.part || !fb.part_max ||
         !fb.scal)
         return HEXFC_ERR_OVERFLOW;
     // the array keeps the previous call's contents: clear what must start at zero

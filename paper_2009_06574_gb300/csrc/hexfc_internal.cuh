@@ -92,6 +92,11 @@ struct FrameBufs {
     uint64_t* tile_off = nullptr;   // [T+1]
     uint32_t* tile_cur = nullptr;   // [T]
     uint32_t* tile_order = nullptr; // [T] tiles by decreasing chunk count
+    uint32_t* tile_frag = nullptr;  // [T] exact fragments per tile (the count's or the fused pass's)
+    uint32_t* tile_cap = nullptr;   // [T+1] chosen fragment capacity per tile (predicted frames)
+    uint64_t* cap_off = nullptr;    // [T+1] its exclusive prefix
+    uint32_t* tile_over = nullptr;  // [T+1] tiles above their capacity (drawn after the fused pass)
+    int64_t cap_cap = 0;
     int64_t t_cap = 0;
     uint32_t* bins = nullptr;       // face2tri ids grouped by tile, each tile padded to whole chunks
     int64_t bin_cap = 0;
@@ -134,6 +139,12 @@ cudaError_t launch_bin_sort(const DevMesh& m, FrameBufs& fb, int tiles_x, int ti
 cudaError_t launch_tile_order(FrameBufs& fb, int n_tiles, cudaStream_t s);
 cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int W, int H,
                          cudaStream_t s);
+cudaError_t launch_capacity_from_previous(FrameBufs& fb, int64_t n_tiles, float margin, uint32_t pad,
+                                          cudaStream_t s);
+cudaError_t launch_count_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y,
+                              int W, int H, cudaStream_t s);
+cudaError_t launch_overflow_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, uint32_t n_over,
+                                 uint64_t base, int tiles_x, int W, int H, cudaStream_t s);
 cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x,
                         int tiles_y, int W, int H, cudaStream_t s);
 cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W, int H,

@@ -336,22 +336,32 @@ __device__ CT block_composite(const uint64_t* __restrict__ key, const float4* __
     return c;
 }
 
+// Lists longer than 256: one block each, queued by k_composite (the queue
+// length is read on the device, so the grid need not match it). A list above
+// HEXFC_MAX_LIST is never drawn; the frame reports it as an overflow.
 __global__ void __launch_bounds__(1024) k_composite_long(const uint32_t* __restrict__ cnt,
                                                          const uint64_t* __restrict__ off,
                                                          const uint64_t* __restrict__ key,
                                                          const float4* __restrict__ rgba,
-                                                         const uint32_t* __restrict__ long_q, int tiles_x, int W,
-                                                         float bg0, float bg1, float bg2, float4* __restrict__ out)
+                                                         const uint32_t* __restrict__ long_q,
+                                                         const unsigned long long* __restrict__ n_long,
+                                                         int tiles_x, int W, float bg0, float bg1, float bg2,
+                                                         float4* __restrict__ out)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* s_k = reinterpret_cast<uint64_t*>(smem);
     uint32_t* s_v = reinterpret_cast<uint32_t*>(s_k + HEXFC_MAX_LIST);
-    uint32_t q = long_q[blockIdx.x];
-    int x, y;
-    tile_pixel(q, tiles_x, x, y);
-    uint32_t n = cnt[q];
-    CT c = block_composite(key, rgba, off[q], n, s_k, s_v, nullptr, nullptr);
-    if (threadIdx.x == 0) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
+    const unsigned long long total = *n_long;
+    for (unsigned long long i = blockIdx.x; i < total; i += gridDim.x) {
+        const uint32_t q = long_q[i];
+        const uint32_t n = cnt[q];
+        if (n > (uint32_t)HEXFC_MAX_LIST) continue;
+        int x, y;
+        tile_pixel(q, tiles_x, x, y);
+        CT c = block_composite(key, rgba, off[q], n, s_k, s_v, nullptr, nullptr);
+        if (threadIdx.x == 0) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
+        __syncthreads();   // the shared arrays are reused by the next list
+    }
 }
 
 // ---------------------------------------------------------------- debug gather
@@ -414,6 +424,7 @@ __global__ void k_debug_counts(const uint32_t* __restrict__ cnt, const int32_t* 
 
 constexpr size_t kLongSmem = (size_t)HEXFC_MAX_LIST * (sizeof(uint64_t) + sizeof(uint32_t));
 constexpr unsigned kFixBlocks = 4 * 152;   // persistent: warps stride over the queue of out-of-order lists
+constexpr unsigned kLongGridMax = 2 * 152;  // persistent: blocks stride over the queue of long lists
 
 }  // namespace
 
@@ -433,9 +444,10 @@ cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, 
                                             sp.bg[2], o4, fb.long_q, long_cursor, fb.fix_q, fix_cursor);
     k_composite_fix<<<kFixBlocks, 256, 0, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, tiles_x, W, sp.bg[0], sp.bg[1],
                                                sp.bg[2], o4, fb.fix_q, fix_cursor);
-    if (n_long > 0) {
-        k_composite_long<<<n_long, 1024, kLongSmem, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, fb.long_q, tiles_x, W,
-                                                         sp.bg[0], sp.bg[1], sp.bg[2], o4);
+    if (n_long > 0) {   // n_long: the number of long lists if known, else an upper bound on the useful grid
+        const unsigned grid = n_long < kLongGridMax ? n_long : kLongGridMax;
+        k_composite_long<<<grid, 1024, kLongSmem, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, fb.long_q, long_cursor,
+                                                       tiles_x, W, sp.bg[0], sp.bg[1], sp.bg[2], o4);
     }
     return cudaGetLastError();
 }

@@ -438,26 +438,13 @@ __device__ __forceinline__ bool cover_fast(const CountWarp& me, int j, int rx, i
     return cover_at(me.c, j, rx, ry, l);
 }
 
-// Per tile: coverage of every chunk of 32 triangles as per-pixel bit masks;
-// the masks are kept for the fill pass and their bit counts are the
-// per-pixel list lengths. Warp w takes chunks w, w + 8, ... of the tile's list
-// on its own: its 32 lanes stage the chunk's triangles, then walk each
-// triangle's box (clipped to the tile) one sample per lane, setting bit j of
-// the covered pixels in the warp's private masks. No block barrier until the
-// per-pixel totals are summed at the end.
-__global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__ tile_off,
-                                                    const uint32_t* __restrict__ bins,
-                                                    const FaceFrame* __restrict__ fframe,
-                                                    const uint32_t* __restrict__ order, int tiles_x, int W, int H,
-                                                    uint32_t* __restrict__ cnt, uint32_t* __restrict__ masks)
+// Warp `warp` of a tile block rasterises chunks warp, warp + kConsumerWarps, ...
+// of the tile's list into masks (global, per chunk) and adds their bit counts
+// to its private per-pixel counts s_w[warp].count.
+__device__ __forceinline__ void count_chunks(CountWarp* s_w, int warp, int lane, const uint32_t* __restrict__ bins,
+                                             const FaceFrame* __restrict__ fframe, uint64_t beg, uint32_t n_chunks,
+                                             int px0, int py0, int W, int H, uint32_t* __restrict__ masks)
 {
-    extern __shared__ __align__(16) unsigned char count_smem[];
-    CountWarp* s_w = reinterpret_cast<CountWarp*>(count_smem);   // [kConsumerWarps]
-    const int tile = (int)order[blockIdx.x];
-    const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
-    const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
-    const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     CountWarp& me = s_w[warp];
     for (int i = lane; i < kTilePix; i += 32) {
         me.mask[i] = 0;
@@ -501,11 +488,48 @@ __global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__
         }
         __syncwarp();
     }
+}
+
+// Sum of v over the block's first kTilePix threads (all threads call it).
+__device__ __forceinline__ uint32_t tile_sum(uint32_t v, uint32_t* s_tmp)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0 && warp < kConsumerWarps) s_tmp[warp] = v;
+    __syncthreads();
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < kConsumerWarps; ++w) t += s_tmp[w];
+    __syncthreads();
+    return t;
+}
+
+// Per tile: coverage of every chunk as per-pixel bit masks (kept for the
+// fill) and the per-pixel list lengths; the tile's total goes to tile_frag.
+__global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__ tile_off,
+                                                    const uint32_t* __restrict__ bins,
+                                                    const FaceFrame* __restrict__ fframe,
+                                                    const uint32_t* __restrict__ order, int tiles_x, int W, int H,
+                                                    uint32_t* __restrict__ cnt, uint32_t* __restrict__ masks,
+                                                    uint32_t* __restrict__ tile_frag)
+{
+    extern __shared__ __align__(16) unsigned char count_smem[];
+    CountWarp* s_w = reinterpret_cast<CountWarp*>(count_smem);   // [kConsumerWarps]
+    __shared__ uint32_t s_tmp[kConsumerWarps];
+    const int tile = (int)order[blockIdx.x];
+    const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
+    const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
+    const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    count_chunks(s_w, warp, lane, bins, fframe, beg, n_chunks, px0, py0, W, H, masks);
     __syncthreads();
     uint32_t n = 0;
 #pragma unroll
     for (int w = 0; w < kConsumerWarps; ++w) n += s_w[w].count[threadIdx.x];
     cnt[(int64_t)tile * kTilePix + threadIdx.x] = n;
+    const uint32_t total = tile_sum(n, s_tmp);
+    if (threadIdx.x == 0) tile_frag[tile] = total;
 }
 
 // ------------------------------------------------------------------ fill + shade
@@ -614,44 +638,22 @@ __device__ __forceinline__ bool consumers_sync_or(bool p)
 }
 __device__ __forceinline__ void consumers_sync() { asm volatile("barrier.sync 1, %0;\n" ::"n"(kTilePix) : "memory"); }
 
-// Per tile: the coverage masks of the count pass give, chunk by chunk, each
-// pixel's covered triangles; the consumers compact the chunk's covered samples
-// into one queue (pixel-major, in list order) and shade it 256 samples at a
-// time, so that every lane has work, and each fragment is written at its
-// pixel's offset plus its rank in the pixel's list (the rank the count pass
-// sized). The producer fetches the face records of chunk c+1 with cp.async
-// while it sets up chunk c.
-__global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __restrict__ tile_off,
-                                                          const uint32_t* __restrict__ bins,
-                                                          const uint32_t* __restrict__ masks,
-                                                          const FaceFrame* __restrict__ fframe,
-                                                          const FaceStatic* __restrict__ fstat,
-                                                          const uint32_t* __restrict__ order, int tiles_x, int W,
-                                                          int H, ShadeParams sp, const uint64_t* __restrict__ off,
-                                                          uint64_t* __restrict__ key, float4* __restrict__ rgba,
-                                                          unsigned long long* __restrict__ err)
+// The fill pipeline of one tile block: s_base / s_len hold the offsets and
+// lengths of the tile's 256 lists, the ring barriers are initialised, and
+// `smem` is the dynamic shared memory (fill_smem_bytes()).
+__device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s_base, const uint32_t* s_len,
+                                          uint32_t* s_wsum, uint64_t* s_full, uint64_t* s_empty,
+                                          const uint32_t* __restrict__ bins, const uint32_t* __restrict__ masks,
+                                          const FaceFrame* __restrict__ fframe,
+                                          const FaceStatic* __restrict__ fstat, uint64_t beg, uint32_t n_chunks,
+                                          int px0, int py0, int W, int H, const ShadeParams& sp,
+                                          uint64_t* __restrict__ key, float4* __restrict__ rgba,
+                                          unsigned long long* __restrict__ err)
 {
-    extern __shared__ __align__(128) unsigned char fill_smem[];
-    FillSlot* s_ring = reinterpret_cast<FillSlot*>(fill_smem);                                    // [kRing]
-    RawFace* s_raw = reinterpret_cast<RawFace*>(fill_smem + kRawOff);                            // [2][kChunk]
-    uint32_t* s_q = reinterpret_cast<uint32_t*>(s_raw + 2 * kChunk);                             // [kQCap]
-    __shared__ uint64_t s_base[kTilePix];
-    __shared__ uint32_t s_len[kTilePix];
-    __shared__ uint32_t s_wsum[kConsumerWarps];
-    __shared__ __align__(8) uint64_t s_full[kRing], s_empty[kRing];
-    const int tile = (int)order[blockIdx.x];
-    const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
-    const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
-    const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
+    FillSlot* s_ring = reinterpret_cast<FillSlot*>(smem);                                    // [kRing]
+    RawFace* s_raw = reinterpret_cast<RawFace*>(smem + kRawOff);                            // [2][kChunk]
+    uint32_t* s_q = reinterpret_cast<uint32_t*>(s_raw + 2 * kChunk);                        // [kQCap]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x < kTilePix) {
-        const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;
-        const uint64_t o0 = off[q];
-        s_base[threadIdx.x] = o0;
-        s_len[threadIdx.x] = (uint32_t)(off[q + 1] - o0);
-    }
-    pipe_init(s_full, s_empty);
-
     if (warp == kConsumerWarps) {  // producer
         uint32_t f2t_c = n_chunks > 0 ? bins[beg + lane] : kPadBin;
         uint32_t f2t_n = n_chunks > 1 ? bins[beg + kChunk + lane] : kPadBin;
@@ -782,6 +784,187 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __rest
     if (bad) atomicOr(err, 1ull);
 }
 
+// Per tile: the coverage masks of the count pass give, chunk by chunk, each
+// pixel's covered triangles; the consumers compact the chunk's covered samples
+// into one queue (pixel-major, in list order) and shade it 256 samples at a
+// time, so that every lane has work, and each fragment is written at its
+// pixel's offset plus its rank in the pixel's list (the rank the count pass
+// sized). The producer fetches the face records of chunk c+1 with cp.async
+// while it sets up chunk c.
+__global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __restrict__ tile_off,
+                                                          const uint32_t* __restrict__ bins,
+                                                          const uint32_t* __restrict__ masks,
+                                                          const FaceFrame* __restrict__ fframe,
+                                                          const FaceStatic* __restrict__ fstat,
+                                                          const uint32_t* __restrict__ order, int tiles_x, int W,
+                                                          int H, ShadeParams sp, const uint64_t* __restrict__ off,
+                                                          const uint32_t* __restrict__ cnt,
+                                                          uint64_t* __restrict__ key, float4* __restrict__ rgba,
+                                                          unsigned long long* __restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char fill_smem[];
+    __shared__ uint64_t s_base[kTilePix];
+    __shared__ uint32_t s_len[kTilePix];
+    __shared__ uint32_t s_wsum[kConsumerWarps];
+    __shared__ __align__(8) uint64_t s_full[kRing], s_empty[kRing];
+    const int tile = (int)order[blockIdx.x];
+    const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
+    const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
+    const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
+    if (threadIdx.x < kTilePix) {
+        const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;
+        s_base[threadIdx.x] = off[q];
+        s_len[threadIdx.x] = cnt[q];
+    }
+    pipe_init(s_full, s_empty);
+    fill_tile(fill_smem, s_base, s_len, s_wsum, s_full, s_empty, bins, masks, fframe, fstat, beg, n_chunks, px0, py0,
+              W, H, sp, key, rgba, err);
+}
+
+// Per tile, with no separate count pass: the consumer warps rasterise the
+// tile's chunks into masks and per-pixel counts (as k_count), the block scans
+// the counts into offsets inside the tile's region [cap_off[t], cap_off[t+1])
+// of the fragment arrays (capacities chosen before the frame), and if the
+// tile fits, the fill pipeline draws it. A tile that does not fit draws
+// nothing: it appends itself to `over` (scal[6] tiles, scal[14] fragments)
+// with its exact counts and masks in place, for k_fill to draw once it has a
+// region. tile_frag = the tile's exact total; scal[0] += fragments, scal[1] =
+// max list, scal[2] += lists longer than kWarpSortMax.
+__global__ void __launch_bounds__(kPipeThreads, 3) k_count_fill(const uint64_t* __restrict__ tile_off,
+                                                               const uint32_t* __restrict__ bins,
+                                                               uint32_t* __restrict__ masks,
+                                                               const FaceFrame* __restrict__ fframe,
+                                                               const FaceStatic* __restrict__ fstat,
+                                                               const uint32_t* __restrict__ order, int tiles_x,
+                                                               int W, int H, ShadeParams sp,
+                                                               const uint64_t* __restrict__ cap_off,
+                                                               uint64_t frag_cap, uint32_t* __restrict__ cnt,
+                                                               uint64_t* __restrict__ off,
+                                                               uint32_t* __restrict__ tile_frag,
+                                                               uint32_t* __restrict__ over,
+                                                               uint64_t* __restrict__ key, float4* __restrict__ rgba,
+                                                               unsigned long long* __restrict__ scal)
+{
+    extern __shared__ __align__(128) unsigned char cf_smem[];
+    __shared__ uint64_t s_base[kTilePix];
+    __shared__ uint32_t s_len[kTilePix];
+    __shared__ uint32_t s_wsum[kConsumerWarps];
+    __shared__ uint32_t s_wmax[kConsumerWarps], s_wlong[kConsumerWarps];
+    __shared__ __align__(8) uint64_t s_full[kRing], s_empty[kRing];
+    const int tile = (int)order[blockIdx.x];
+    const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
+    const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
+    const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    CountWarp* s_w = reinterpret_cast<CountWarp*>(cf_smem);
+    if (warp < kConsumerWarps) count_chunks(s_w, warp, lane, bins, fframe, beg, n_chunks, px0, py0, W, H, masks);
+    __syncthreads();
+    // the per-pixel counts, their block-wide exclusive scan, maximum and long lists
+    uint32_t n = 0;
+    if (warp < kConsumerWarps)
+#pragma unroll
+        for (int w = 0; w < kConsumerWarps; ++w) n += s_w[w].count[threadIdx.x];
+    uint32_t incl = n, mx = n, lg = n > (uint32_t)kWarpSortMax ? 1u : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        lg += __shfl_xor_sync(0xffffffffu, lg, o);
+    }
+    if (lane == 31 && warp < kConsumerWarps) {
+        s_wsum[warp] = incl;
+        s_wmax[warp] = mx;
+        s_wlong[warp] = lg;
+    }
+    __syncthreads();
+    uint32_t base = 0, total = 0, tmax = 0, tlong = 0;
+#pragma unroll
+    for (int w = 0; w < kConsumerWarps; ++w) {
+        const uint32_t v = s_wsum[w];
+        base += w < warp ? v : 0u;
+        total += v;
+        tmax = max(tmax, s_wmax[w]);
+        tlong += s_wlong[w];
+    }
+    const uint64_t region = cap_off[tile], cap = cap_off[tile + 1] - region;
+    const bool fits = total <= cap && region + total <= frag_cap;   // the same on every thread
+    if (warp < kConsumerWarps) {
+        const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;
+        const uint64_t o = region + base + incl - n;
+        cnt[q] = n;        // also for a tile that does not fit: its lists are drawn later
+        off[q] = o;
+        s_base[threadIdx.x] = o;
+        s_len[threadIdx.x] = n;
+    }
+    if (threadIdx.x == 0) {
+        tile_frag[tile] = total;
+        atomicAdd(&scal[0], (unsigned long long)total);
+        atomicMax(&scal[1], (unsigned long long)tmax);
+        atomicAdd(&scal[2], (unsigned long long)tlong);
+        if (!fits) {
+            over[atomicAdd(&scal[6], 1ull)] = (uint32_t)tile;
+            atomicAdd(&scal[14], (unsigned long long)total);
+        }
+    }
+    if (!fits) return;
+    pipe_init(s_full, s_empty);   // also orders the scan's shared reads before the fill reuses them
+    fill_tile(cf_smem, s_base, s_len, s_wsum, s_full, s_empty, bins, masks, fframe, fstat, beg, n_chunks, px0, py0,
+              W, H, sp, key, rgba, scal + 5);
+}
+
+// Regions for the tiles that did not fit their capacity: after `base`, in
+// the order of the list, sized by their exact totals; then the pixels' list
+// offsets inside them (one block per listed tile).
+__global__ void __launch_bounds__(kTilePix) k_overflow_offsets(const uint32_t* __restrict__ over, uint32_t n_over,
+                                                               const uint32_t* __restrict__ tile_frag, uint64_t base,
+                                                               const uint32_t* __restrict__ cnt,
+                                                               uint64_t* __restrict__ off)
+{
+    __shared__ uint32_t s_w[kConsumerWarps];
+    __shared__ unsigned long long s_region;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t i = blockIdx.x;
+    // the tile's region: base + the totals of the tiles listed before it
+    unsigned long long acc = 0;
+    for (uint32_t k = threadIdx.x; k < i; k += blockDim.x) acc += tile_frag[over[k]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) s_region = 0;
+    __syncthreads();
+    if (lane == 0) atomicAdd(&s_region, acc);
+    // the pixels' exclusive scan inside the tile
+    const uint32_t tile = over[i];
+    const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;
+    const uint32_t n = cnt[q];
+    uint32_t incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    uint32_t pre = incl - n;
+    for (int w = 0; w < warp; ++w) pre += s_w[w];
+    off[q] = base + s_region + pre;
+}
+
+// Capacities from the previous frame's exact tile counts: prev * (1 + margin) + pad.
+__global__ void k_capacity_from_previous(const uint32_t* __restrict__ prev, int64_t n_tiles, float margin,
+                                         uint32_t pad, uint32_t* __restrict__ cap)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    cap[t] = (uint32_t)fminf((float)prev[t] * (1.f + margin) + (float)pad, 4.0e9f);
+}
+
+constexpr size_t count_fill_smem_bytes()
+{
+    return kConsumerWarps * sizeof(CountWarp) > fill_smem_bytes() ? kConsumerWarps * sizeof(CountWarp)
+                                                                     : fill_smem_bytes();
+}
+
 }  // namespace
 
 cudaError_t prepare_raster_kernels()
@@ -790,7 +973,36 @@ cudaError_t prepare_raster_kernels()
                                          (int)(kConsumerWarps * sizeof(CountWarp)));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_count_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)count_fill_smem_bytes());
     return e;
+}
+
+cudaError_t launch_capacity_from_previous(FrameBufs& fb, int64_t n_tiles, float margin, uint32_t pad, cudaStream_t s)
+{
+    k_capacity_from_previous<<<grid_for(n_tiles, 256), 256, 0, s>>>(fb.tile_frag, n_tiles, margin, pad, fb.tile_cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W,
+                              int H, cudaStream_t s)
+{
+    k_count_fill<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, count_fill_smem_bytes(), s>>>(
+        fb.tile_off, fb.bins, fb.masks, fb.fframe, m.fstat, fb.tile_order, tiles_x, W, H, sp, fb.cap_off,
+        (uint64_t)fb.frag_cap, fb.cnt, fb.off, fb.tile_frag, fb.tile_over, fb.key, fb.rgba,
+        reinterpret_cast<unsigned long long*>(fb.scal));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_overflow_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, uint32_t n_over,
+                                 uint64_t base, int tiles_x, int W, int H, cudaStream_t s)
+{
+    k_overflow_offsets<<<n_over, kTilePix, 0, s>>>(fb.tile_over, n_over, fb.tile_frag, base, fb.cnt, fb.off);
+    k_fill<<<n_over, kPipeThreads, fill_smem_bytes(), s>>>(fb.tile_off, fb.bins, fb.masks, fb.fframe, m.fstat,
+                                                            fb.tile_over, tiles_x, W, H, sp, fb.off, fb.cnt, fb.key,
+                                                            fb.rgba, reinterpret_cast<unsigned long long*>(fb.scal + 5));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_vertex_setup(const DevMesh& m, const CamParams& cam, FrameBufs& fb, cudaStream_t s)
@@ -834,7 +1046,7 @@ cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles
 {
     const size_t smem = kConsumerWarps * sizeof(CountWarp);
     k_count<<<(unsigned)(tiles_x * tiles_y), kTilePix, smem, s>>>(fb.tile_off, fb.bins, fb.fframe, fb.tile_order,
-                                                                   tiles_x, W, H, fb.cnt, fb.masks);
+                                                                   tiles_x, W, H, fb.cnt, fb.masks, fb.tile_frag);
     return cudaGetLastError();
 }
 
@@ -843,8 +1055,8 @@ cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, 
 {
     const size_t smem = fill_smem_bytes();
     k_fill<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, smem, s>>>(
-        fb.tile_off, fb.bins, fb.masks, fb.fframe, m.fstat, fb.tile_order, tiles_x, W, H, sp, fb.off, fb.key, fb.rgba,
-        reinterpret_cast<unsigned long long*>(fb.scal + 5));
+        fb.tile_off, fb.bins, fb.masks, fb.fframe, m.fstat, fb.tile_order, tiles_x, W, H, sp, fb.off, fb.cnt, fb.key,
+        fb.rgba, reinterpret_cast<unsigned long long*>(fb.scal + 5));
     return cudaGetLastError();
 }
 

@@ -36,6 +36,7 @@ HEXFC_OPT_REVERSE_BIN_ORDER = 1
 HEXFC_OPT_STAGE_TIMING = 2
 HEXFC_OPT_DEPTH_BUCKETS = 3
 HEXFC_OPT_COMPOSITE_WINDOW = 4
+HEXFC_OPT_PREDICTED_CAPACITY = 5
 STAGES = ["vertex", "face", "tile_scan", "gap1", "bin", "count", "scan", "gap2", "fill", "composite"]
 
 # every symbol include/hexfc.h declares
@@ -73,7 +74,8 @@ class hexfc_style(C.Structure):
 class hexfc_frame_stats(C.Structure):
     _fields_ = [("fragments", C.c_uint64), ("bin_entries", C.c_uint64), ("max_list", C.c_uint32),
                 ("long_lists", C.c_uint32), ("width", C.c_uint32), ("height", C.c_uint32),
-                ("kernel_launches", C.c_uint32), ("covered_pixels", C.c_uint32)]
+                ("kernel_launches", C.c_uint32), ("covered_pixels", C.c_uint32), ("predicted", C.c_uint32),
+                ("overflow_tiles", C.c_uint32), ("capacity", C.c_uint64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -12,8 +12,10 @@ has drawn and are reused. The server keeps, per (mesh, width, height), the
 largest footprint seen; a frame of a kind never drawn before is admitted only
 when nothing else is in flight, which measures it. A request is admitted when
 the held buffers of every slot, with the chosen slot raised to the request's
-footprint, fit the budget; idle slots release their buffers (largest first)
-when that makes room. Requests start in arrival order (no overtaking).
+footprint, fit the budget; when nothing is in flight, idle slots release their
+buffers (largest first) if that makes room (freeing device memory synchronises
+the device, so it is not done under running frames). Requests start in
+arrival order (no overtaking).
 
 The renderer is injected (`renderer_factory`), so the scheduling logic is
 tested on the CPU with a stand-in; the default is `hexfc.Renderer`.
@@ -237,6 +239,12 @@ class Server:
             return s
         # best fit: the smallest slot that already holds enough, else the largest
         s = min(idle, key=lambda o: (0, o.held) if o.held >= need else (1, -o.held))
+        if self._others(s) + max(s.held, need) <= self.budget:
+            return s
+        # releasing device memory synchronises the whole device: only when
+        # nothing is in flight; otherwise the request waits for a frame to end
+        if any(o.busy for o in self._slots):
+            return None
         for o in sorted((o for o in idle if o is not s), key=lambda o: -o.held):
             if self._others(s) + max(s.held, need) <= self.budget:
                 break

@@ -1,0 +1,93 @@
+"""Frames drawn with chosen tile capacities and the fused count-and-fill pass
+are bit-identical to the count-then-fill path; tiles above their capacity are
+drawn afterwards in regions of their exact size (or the whole frame by the
+exact path when there is no room), and the image is still exact."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2009_06574_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hx():
+    from paper_2009_06574_gb300 import hexfc
+    hexfc.load()
+    return hexfc
+
+
+def _pair(hx, mesh, style):
+    out = []
+    for mode in (0, 1):
+        r = hx.Renderer(0)
+        mid = r.upload_mesh(mesh.verts, mesh.cells, mesh.cell_scalar, mesh.edge_level)
+        r.set_style(style)
+        r.set_option(hx.HEXFC_OPT_PREDICTED_CAPACITY, mode)
+        out.append((r, mid))
+    return out
+
+
+def _draw(r, mid, view, lens):
+    r.set_view(view)
+    r.set_lens(lens)
+    img = torch.empty((view.height, view.width, 4), device="cuda")
+    r.render(mid, img)
+    return img.cpu().numpy(), dict(r.last_stats)
+
+
+def test_predicted_frames_match_exact_path(hx):
+    mesh = synth.hex_grid(10, jitter=0.1, warp_amp=0.3, seed=6)
+    style = synth.Style(w_base=1.5, lod=2)
+    (ex, me), (pr, mp) = _pair(hx, mesh, style)
+    n_pred = 0
+    for f in range(16):   # consecutive orbit frames: the previous frame's counts are a fair guess
+        view, lens = synth.orbit_view(f, 120, 200, 150), synth.lissajous_lens(f, 120)
+        a, sa = _draw(ex, me, view, lens)
+        b, sb = _draw(pr, mp, view, lens)
+        np.testing.assert_array_equal(b, a)
+        assert sb["fragments"] == sa["fragments"] and sb["max_list"] == sa["max_list"]
+        n_pred += sb["predicted"]
+        if f > 0:
+            assert sb["capacity"] >= sb["fragments"]
+    assert n_pred >= 8   # the others overflowed and were drawn exactly (compared above too)
+    ex.close(); pr.close()
+
+
+def test_overflow_falls_back_to_exact(hx):
+    mesh = synth.hex_grid(10, jitter=0.1, warp_amp=0.3, seed=6)
+    style = synth.Style()
+    (ex, me), (pr, mp) = _pair(hx, mesh, style)
+    lens = synth.lissajous_lens(0, 120)
+    far = synth.orbit_view(0, 120, 160, 120, radius=4.0)
+    near = synth.orbit_view(0, 120, 160, 120, radius=1.3)   # many more fragments per tile
+    _draw(pr, mp, far, lens)
+    _draw(pr, mp, far, lens)
+    b, sb = _draw(pr, mp, near, lens)
+    a, sa = _draw(ex, me, near, lens)
+    assert sb["overflow_tiles"] > 0
+    np.testing.assert_array_equal(b, a)
+    # the counts of the exact redraw now size the next frame
+    c, sc = _draw(pr, mp, near, lens)
+    assert sc["predicted"] == 1 and sc["overflow_tiles"] == 0
+    np.testing.assert_array_equal(c, a)
+    with pytest.raises(hx.HexfcError):
+        pr.set_option(hx.HEXFC_OPT_PREDICTED_CAPACITY, 3)
+    ex.close(); pr.close()
+
+
+def test_some_tiles_over_capacity_are_drawn_after(hx):
+    mesh = synth.hex_grid(12, jitter=0.1, warp_amp=0.3, seed=9)
+    style = synth.Style(w_base=1.5, lod=2)
+    (ex, me), (pr, mp) = _pair(hx, mesh, style)
+    partial = 0
+    for f in (0, 2, 6, 12, 20, 30, 42, 56, 72):   # growing jumps along the orbit
+        view, lens = synth.orbit_view(f, 120, 240, 180), synth.lissajous_lens(f, 120)
+        a, _ = _draw(ex, me, view, lens)
+        b, sb = _draw(pr, mp, view, lens)
+        np.testing.assert_array_equal(b, a)
+        partial += int(sb["predicted"] == 1 and sb["overflow_tiles"] > 0)
+    assert partial >= 1
+    ex.close(); pr.close()
+
