@@ -330,6 +330,41 @@ hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value);
  */
 
 /*
+ * Tile-capacity network (no counterpart in the paper): per 16x16 tile, a
+ * 4 -> 64 -> 64 -> 1 ReLU network predicts y ~ log(1 + fragments) from the
+ * tile's previous-frame count, the depth range of its triangles, its screen
+ * distance to the lens and the camera's motion since the previous frame;
+ * the capacity is expm1(y) * 1.15 + 256. Weights are used in FP16 with FP32
+ * sums; training keeps FP32 master weights and Adam moments on the device.
+ * Every frame leaves its features and exact tile counts (from the count pass
+ * or the fused pass) for training. Parameters: HEXFC_CAPACITY_PARAMS floats,
+ * in the order W1 (64 x 4, row-major), b1 (64), W2 (64 x 64, row-major,
+ * W2[j][i] from hidden unit i of the first layer to unit j of the second),
+ * b2 (64), w3 (64), b3 (1).
+ *
+ * hexfc_capacity_reset: set weights from seed (scaled normal, biases 0,
+ *   b3 = 5) and clear the Adam state. Errors: ARG, OOM, CUDA.
+ * hexfc_capacity_set_weights / _get_weights: host array of n ==
+ *   HEXFC_CAPACITY_PARAMS floats (set also clears the Adam state).
+ *   Errors: ARG (n, non-finite), STATE (get before any weights), CUDA.
+ * hexfc_capacity_grad: loss (mean over the n rows of (y - log(1 + count))^2)
+ *   and its gradient for host features x (n x 4) and counts (n), with the
+ *   current weights (test hook). grad: host, HEXFC_CAPACITY_PARAMS floats.
+ *   Errors: ARG, STATE (no weights), OOM, CUDA. Synchronous.
+ * hexfc_capacity_train: `steps` Adam steps (rate lr) on the last frame's
+ *   features and exact tile counts, on `stream`; *loss (nullable) receives
+ *   the loss before the last step (the host waits when loss != NULL).
+ *   Errors: ARG, STATE (no weights or no frame yet), OOM, CUDA.
+ */
+#define HEXFC_CAPACITY_PARAMS 4545
+hexfc_status hexfc_capacity_reset(hexfc_ctx* ctx, uint64_t seed);
+hexfc_status hexfc_capacity_set_weights(hexfc_ctx* ctx, const float* w, int64_t n);
+hexfc_status hexfc_capacity_get_weights(hexfc_ctx* ctx, float* w, int64_t n);
+hexfc_status hexfc_capacity_grad(hexfc_ctx* ctx, const float* x, const uint32_t* counts, int64_t n, float* grad,
+                                 float* loss);
+hexfc_status hexfc_capacity_train(hexfc_ctx* ctx, int32_t steps, float lr, float* loss, void* stream);
+
+/*
  * Accumulated stage times (milliseconds, summed over frames) since the last
  * reset, for frames rendered with HEXFC_OPT_STAGE_TIMING on. ms: host array of
  * HEXFC_N_STAGES doubles; *frames: number of frames summed. Waits for the last

@@ -31,6 +31,11 @@ struct hexfc_ctx {
     // exact tile counts of the last frame (fb.tile_frag) are valid for this size
     int counts_W = 0, counts_H = 0;
     uint64_t counts_total = 0;
+    // tile-capacity network and the camera of the previous frame (its motion is a feature)
+    CapNet cap;
+    bool have_prev_cam = false;
+    double prev_eye[3] = {0, 0, 0}, prev_F[3] = {0, 0, 1};
+    int64_t feat_tiles = 0;   // tiles whose features and exact counts the last frame left for training
     // last render
     bool have_frame = false;
     int last_W = 0, last_H = 0, last_tiles_x = 0, last_tiles_y = 0;
@@ -127,7 +132,8 @@ void free_mesh(DevMesh* m)
 void free_frame(FrameBufs& f)
 {
     dfree(f.vproj); dfree(f.ved); dfree(f.fframe); dfree(f.tzsum);
-    dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.tile_order); dfree(f.tile_frag); dfree(f.tile_cap); dfree(f.cap_off); dfree(f.tile_over); dfree(f.bins); dfree(f.masks); dfree(f.cnt);
+    dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.tile_order); dfree(f.tile_frag); dfree(f.tile_cap); dfree(f.cap_off); dfree(f.tile_over); dfree(f.tile_zr); dfree(f.cap_x);
+    dfree(f.bins); dfree(f.masks); dfree(f.cnt);
     dfree(f.off);
     dfree(f.part); dfree(f.part_max); dfree(f.long_q); dfree(f.fix_q); dfree(f.key); dfree(f.rgba); dfree(f.scal);
     if (f.h_scal) cudaFreeHost(f.h_scal);
@@ -274,6 +280,8 @@ struct FrameJob {
     int64_t n_tiles = 0, n_pix = 0;
     int reverse = 0;
     int buckets = 2048, window = 4;
+    float lens_x = 0.f, lens_y = 0.f, inv_diag = 0.f, motion = 0.f;   // capacity-network features
+    bool prev_counts = false;   // fb.tile_frag holds the previous frame's counts for this tile grid
     uint64_t budget = 0;
     float* out = nullptr;
     hexfc_ctx* timing = nullptr;   // stage events of the single-frame path
@@ -286,6 +294,51 @@ struct FrameJob {
 void job_mark(const FrameJob& j, int k, cudaStream_t s)
 {
     if (j.timing) mark(j.timing, k, s);
+}
+
+// Per-frame constants of the capacity features: the lens centre on screen,
+// 1 / screen diagonal, and the camera's motion since the previous frame
+// (eye displacement / reference depth + angle between view directions).
+void feature_constants(const hexfc_ctx* ctx, const hexfc_view& v, const hexfc_lens& lens, const CamParams& c,
+                       double zref, FrameJob& j)
+{
+    double lx = lens.center[0], ly = lens.center[1];
+    if (lens.mode == HEXFC_LENS_SPHERE) {
+        const double dx = lens.center[0] - c.eye[0], dy = lens.center[1] - c.eye[1], dz = lens.center[2] - c.eye[2];
+        const double ex = dx * c.R[0] + dy * c.R[1] + dz * c.R[2], ey = dx * c.U[0] + dy * c.U[1] + dz * c.U[2];
+        const double ed = dx * c.F[0] + dy * c.F[1] + dz * c.F[2];
+        if (c.ortho) {
+            lx = c.cx + ex * c.scale;
+            ly = c.cy - ey * c.scale;
+        } else if (ed > c.znear) {
+            lx = c.cx + ex / ed * c.focal;
+            ly = c.cy - ey / ed * c.focal;
+        } else {
+            lx = ly = 1e9;   // behind the camera: far from every tile
+        }
+    }
+    j.lens_x = (float)lx;
+    j.lens_y = (float)ly;
+    j.inv_diag = (float)(1.0 / std::sqrt((double)v.width * v.width + (double)v.height * v.height));
+    double motion = 0.0;
+    if (ctx->have_prev_cam) {
+        double d2 = 0.0, dot = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            d2 += (c.eye[k] - ctx->prev_eye[k]) * (c.eye[k] - ctx->prev_eye[k]);
+            dot += c.F[k] * ctx->prev_F[k];
+        }
+        motion = std::sqrt(d2) / (zref > 0 ? zref : 1.0) + std::acos(std::fmin(1.0, std::fmax(-1.0, dot)));
+    }
+    j.motion = (float)motion;
+}
+
+void remember_camera(hexfc_ctx* ctx, const CamParams& c)
+{
+    for (int k = 0; k < 3; ++k) {
+        ctx->prev_eye[k] = c.eye[k];
+        ctx->prev_F[k] = c.F[k];
+    }
+    ctx->have_prev_cam = true;
 }
 
 FrameJob make_job(hexfc_ctx* ctx, FrameBufs* fb, DevMesh* m, float* out)
@@ -308,7 +361,19 @@ FrameJob make_job(hexfc_ctx* ctx, FrameBufs* fb, DevMesh* m, float* out)
     j.window = ctx->window;
     j.budget = ctx->budget;
     j.out = out;
+    feature_constants(ctx, ctx->view, ctx->lens, ctx->cam, ctx->zref, j);
+    j.prev_counts = fb == &ctx->fb && ctx->counts_W == j.W && ctx->counts_H == j.H;
     return j;
+}
+
+// Capacity features of the frame (before its count overwrites the previous counts).
+hexfc_status job_features(FrameJob& j, cudaStream_t s)
+{
+    FrameBufs& fb = *j.fb;
+    if (!j.prev_counts) CK(cudaMemsetAsync(fb.tile_frag, 0, sizeof(uint32_t) * (size_t)j.n_tiles, s));
+    CK(launch_cap_features(fb, j.n_tiles, j.tiles_x, j.lens_x, j.lens_y, j.inv_diag, j.motion, s));
+    j.launches += 1;
+    return HEXFC_OK;
 }
 
 // Buffers whose size follows from the mesh and the view.
@@ -330,13 +395,16 @@ hexfc_status job_alloc(FrameJob& j)
         if ((st = ensure(&fb.tzsum, &c1, 2 * fb.f_cap)) != HEXFC_OK) return st;
     }
     if (!fb.tile_cnt || fb.t_cap < j.n_tiles + 1) {
-        int64_t c1 = 0, c2 = 0, c3 = 0, c4 = 0;
-        dfree(fb.tile_off); dfree(fb.tile_cur); dfree(fb.tile_order); dfree(fb.tile_frag);
+        int64_t c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0, c6 = 0;
+        dfree(fb.tile_off); dfree(fb.tile_cur); dfree(fb.tile_order); dfree(fb.tile_frag); dfree(fb.tile_zr);
+        dfree(fb.cap_x);
         if ((st = ensure(&fb.tile_cnt, &fb.t_cap, j.n_tiles + 1)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.tile_off, &c1, fb.t_cap)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.tile_cur, &c2, fb.t_cap)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.tile_order, &c3, fb.t_cap)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.tile_frag, &c4, fb.t_cap)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.tile_zr, &c5, fb.t_cap)) != HEXFC_OK) return st;
+        if ((st = ensure(&fb.cap_x, &c6, 4 * fb.t_cap)) != HEXFC_OK) return st;
     }
     if (!fb.cnt || fb.p_cap < j.n_pix + 1) {
         int64_t c1 = 0, c2 = 0, c3 = 0;
@@ -401,6 +469,8 @@ hexfc_status job_phase2(FrameJob& j, cudaStream_t s)
     CK(launch_bin_fill(*j.m, fb, j.tiles_x, j.W, j.H, j.reverse, s));
     CK(launch_bin_sort(*j.m, fb, j.tiles_x, j.tiles_y, j.buckets, s));
     CK(launch_tile_order(fb, j.n_tiles, s));
+    hexfc_status fst = job_features(j, s);
+    if (fst != HEXFC_OK) return fst;
     job_mark(j, 5, s);
     CK(launch_count(*j.m, fb, j.tiles_x, j.tiles_y, j.W, j.H, s));
     job_mark(j, 6, s);
@@ -491,6 +561,8 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
     ctx->counts_W = j.W;   // k_count left the exact tile counts in fb.tile_frag
     ctx->counts_H = j.H;
     ctx->counts_total = j.total;
+    ctx->feat_tiles = j.n_tiles;
+    remember_camera(ctx, j.cam);
     return HEXFC_OK;
 }
 
@@ -503,6 +575,7 @@ constexpr uint32_t kLongListsUnknown = 1u << 30;   // the long-list pass reads t
 hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_stats* stats,
                                     cudaStream_t s)
 {
+    if (ctx->predicted == 2 && !ctx->cap.ready) return HEXFC_ERR_STATE;   // no network weights
     if (ctx->counts_W != ctx->view.width || ctx->counts_H != ctx->view.height)
         return render_frame(ctx, m, out, stats, s);   // no tile counts for this size yet
     FrameJob j = make_job(ctx, &ctx->fb, m, out);
@@ -539,8 +612,10 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     CK(launch_bin_fill(*m, fb, j.tiles_x, j.W, j.H, j.reverse, s));
     CK(launch_bin_sort(*m, fb, j.tiles_x, j.tiles_y, j.buckets, s));
     CK(launch_tile_order(fb, j.n_tiles, s));
+    if ((st = job_features(j, s)) != HEXFC_OK) return st;
     job_mark(j, 5, s);
-    CK(launch_capacity_from_previous(fb, j.n_tiles, kCapMargin, kCapPad, s));
+    if (ctx->predicted == 2) CK(launch_cap_forward(ctx->cap, fb, j.n_tiles, kCapMargin, kCapPad, s));
+    else CK(launch_capacity_from_previous(fb, j.n_tiles, kCapMargin, kCapPad, s));
     job_mark(j, 6, s);
     CK(scan_u32_to_u64(fb.tile_cap, fb.cap_off, j.n_tiles, fb.part, fb.part_max, fb.scal + 11, 0xFFFFFFFFu, s));
     job_mark(j, 7, s);
@@ -597,12 +672,65 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     ctx->last_tiles_x = j.tiles_x;
     ctx->last_tiles_y = j.tiles_y;
     ctx->counts_total = fs.fragments;
+    ctx->feat_tiles = j.n_tiles;
+    remember_camera(ctx, j.cam);
     return HEXFC_OK;
 }
 
 // Capture `body(i, stream_i)` for the listed items, each on its own stream
 // forked from the context's origin stream and joined back, as one graph;
 // reuse the phase's executable graph when only parameters changed.
+// Weights, moments and gradient of the capacity network (once).
+hexfc_status cap_alloc(CapNet& n)
+{
+    hexfc_status st = HEXFC_OK;
+    if (!n.w) {
+        if ((st = dalloc(&n.w, kCapParams)) != HEXFC_OK) return st;
+        if ((st = dalloc(&n.w16, kCapParams)) != HEXFC_OK) return st;
+        if ((st = dalloc(&n.m, kCapParams)) != HEXFC_OK) return st;
+        if ((st = dalloc(&n.v, kCapParams)) != HEXFC_OK) return st;
+        if ((st = dalloc(&n.grad, kCapParams + 1)) != HEXFC_OK) return st;
+    }
+    return st;
+}
+
+// Per-tile training buffers for n tiles.
+hexfc_status cap_train_buffers(CapNet& c, int64_t n)
+{
+    if (c.h1 && c.tiles >= n) return HEXFC_OK;
+    dfree(c.h1); dfree(c.h2); dfree(c.da1); dfree(c.da2); dfree(c.dy); dfree(c.x); dfree(c.t);
+    c.tiles = 0;
+    hexfc_status st;
+    const int64_t m = n + n / 4 + 256;
+    if ((st = dalloc(&c.h1, (size_t)(m * kCapHid))) != HEXFC_OK) return st;
+    if ((st = dalloc(&c.h2, (size_t)(m * kCapHid))) != HEXFC_OK) return st;
+    if ((st = dalloc(&c.da1, (size_t)(m * kCapHid))) != HEXFC_OK) return st;
+    if ((st = dalloc(&c.da2, (size_t)(m * kCapHid))) != HEXFC_OK) return st;
+    if ((st = dalloc(&c.dy, (size_t)m)) != HEXFC_OK) return st;
+    if ((st = dalloc(&c.x, (size_t)(4 * m))) != HEXFC_OK) return st;
+    if ((st = dalloc(&c.t, (size_t)m)) != HEXFC_OK) return st;
+    c.tiles = m;
+    return HEXFC_OK;
+}
+
+// Standard normal values from a splitmix64 stream (Box-Muller).
+struct NormalStream {
+    uint64_t s;
+    double next_u()
+    {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);   // (0, 1)
+    }
+    double next()
+    {
+        const double u1 = next_u(), u2 = next_u();
+        return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+    }
+};
+
 template <typename F>
 hexfc_status batch_graph(hexfc_ctx* ctx, int phase, const std::vector<int>& items, F&& body)
 {
@@ -721,6 +849,11 @@ void hexfc_destroy(hexfc_ctx* ctx)
     }
     for (auto& g : ctx->graph_exec)
         if (g) cudaGraphExecDestroy(g);
+    {
+        CapNet& n = ctx->cap;
+        dfree(n.w); dfree(n.w16); dfree(n.m); dfree(n.v); dfree(n.grad);
+        dfree(n.h1); dfree(n.h2); dfree(n.da1); dfree(n.da2); dfree(n.dy); dfree(n.x); dfree(n.t);
+    }
     if (ctx->origin) cudaStreamDestroy(ctx->origin);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
@@ -887,6 +1020,87 @@ hexfc_status hexfc_render_batch(hexfc_ctx* ctx, int32_t n, const hexfc_batch_ite
     return first;
 }
 
+hexfc_status hexfc_capacity_set_weights(hexfc_ctx* ctx, const float* w, int64_t n)
+{
+    if (!ctx || !w || n != kCapParams) return HEXFC_ERR_ARG;
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(w[i])) return HEXFC_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    CapNet& c = ctx->cap;
+    hexfc_status st;
+    if ((st = cap_alloc(c)) != HEXFC_OK) return st;
+    CK(cudaMemcpy(c.w, w, sizeof(float) * kCapParams, cudaMemcpyHostToDevice));
+    CK(cudaMemset(c.m, 0, sizeof(float) * kCapParams));
+    CK(cudaMemset(c.v, 0, sizeof(float) * kCapParams));
+    CK(launch_cap_to_half(c, 0));
+    CK(cudaDeviceSynchronize());
+    c.step = 0;
+    c.ready = true;
+    return HEXFC_OK;
+}
+
+hexfc_status hexfc_capacity_reset(hexfc_ctx* ctx, uint64_t seed)
+{
+    if (!ctx) return HEXFC_ERR_ARG;
+    std::vector<float> w((size_t)kCapParams, 0.f);
+    NormalStream rs{seed};
+    const int oW1 = 0, oB1 = kCapHid * kCapIn, oW2 = oB1 + kCapHid, oB2 = oW2 + kCapHid * kCapHid;
+    const int oW3 = oB2 + kCapHid, oB3 = oW3 + kCapHid;
+    for (int i = oW1; i < oB1; ++i) w[(size_t)i] = (float)(rs.next() * std::sqrt(2.0 / kCapIn));
+    for (int i = oW2; i < oB2; ++i) w[(size_t)i] = (float)(rs.next() * std::sqrt(2.0 / kCapHid));
+    for (int i = oW3; i < oB3; ++i) w[(size_t)i] = (float)(rs.next() * std::sqrt(1.0 / kCapHid));
+    w[(size_t)oB3] = 5.f;   // log(1 + count) of a few hundred fragments
+    return hexfc_capacity_set_weights(ctx, w.data(), kCapParams);
+}
+
+hexfc_status hexfc_capacity_get_weights(hexfc_ctx* ctx, float* w, int64_t n)
+{
+    if (!ctx || !w || n != kCapParams) return HEXFC_ERR_ARG;
+    if (!ctx->cap.ready) return HEXFC_ERR_STATE;
+    DeviceGuard g(ctx->device);
+    CK(cudaMemcpy(w, ctx->cap.w, sizeof(float) * kCapParams, cudaMemcpyDeviceToHost));
+    return HEXFC_OK;
+}
+
+hexfc_status hexfc_capacity_grad(hexfc_ctx* ctx, const float* x, const uint32_t* counts, int64_t n, float* grad,
+                                 float* loss)
+{
+    if (!ctx || !x || !counts || n < 1 || !grad) return HEXFC_ERR_ARG;
+    if (!ctx->cap.ready) return HEXFC_ERR_STATE;
+    DeviceGuard g(ctx->device);
+    CapNet& c = ctx->cap;
+    hexfc_status st;
+    if ((st = cap_train_buffers(c, n)) != HEXFC_OK) return st;
+    CK(cudaMemcpy(c.x, x, sizeof(float) * 4 * (size_t)n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c.t, counts, sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice));
+    CK(launch_cap_grad(c, c.x, c.t, n, 0));
+    CK(cudaMemcpy(grad, c.grad, sizeof(float) * kCapParams, cudaMemcpyDeviceToHost));
+    if (loss) CK(cudaMemcpy(loss, c.grad + kCapParams, sizeof(float), cudaMemcpyDeviceToHost));
+    return HEXFC_OK;
+}
+
+hexfc_status hexfc_capacity_train(hexfc_ctx* ctx, int32_t steps, float lr, float* loss, void* stream)
+{
+    if (!ctx || steps < 0 || !(lr > 0.f)) return HEXFC_ERR_ARG;
+    if (!ctx->cap.ready || ctx->feat_tiles == 0) return HEXFC_ERR_STATE;
+    DeviceGuard g(ctx->device);
+    CapNet& c = ctx->cap;
+    const cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = ctx->feat_tiles;
+    hexfc_status st;
+    if ((st = cap_train_buffers(c, n)) != HEXFC_OK) return st;
+    for (int32_t k = 0; k < steps; ++k) {
+        CK(launch_cap_grad(c, ctx->fb.cap_x, ctx->fb.tile_frag, n, s));
+        CK(launch_cap_adam(c, lr, s));
+    }
+    if (loss) {
+        if (steps == 0) CK(launch_cap_grad(c, ctx->fb.cap_x, ctx->fb.tile_frag, n, s));
+        CK(cudaMemcpyAsync(loss, c.grad + kCapParams, sizeof(float), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return HEXFC_OK;
+}
+
 hexfc_status hexfc_frame_memory(const hexfc_ctx* ctx, uint64_t* bytes)
 {
     if (!ctx || !bytes) return HEXFC_ERR_ARG;
@@ -894,7 +1108,7 @@ hexfc_status hexfc_frame_memory(const hexfc_ctx* ctx, uint64_t* bytes)
     uint64_t b = 0;
     b += (uint64_t)f.v_cap * (sizeof(int4) + sizeof(float));
     b += (uint64_t)f.f_cap * (sizeof(FaceFrame) + 2 * sizeof(uint32_t));
-    b += (uint64_t)f.t_cap * (4 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t));
+    b += (uint64_t)f.t_cap * (9 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t));
     b += (uint64_t)f.bin_cap * sizeof(uint32_t) + (uint64_t)f.mask_cap * sizeof(uint32_t);
     b += (uint64_t)f.p_cap * (3 * sizeof(uint32_t) + sizeof(uint64_t));
     b += (uint64_t)f.part_cap * (sizeof(uint64_t) + sizeof(uint32_t));
@@ -904,7 +1118,7 @@ hexfc_status hexfc_frame_memory(const hexfc_ctx* ctx, uint64_t* bytes)
         const FrameBufs& g = bs->fb;
         b += (uint64_t)g.v_cap * (sizeof(int4) + sizeof(float)) +
              (uint64_t)g.f_cap * (sizeof(FaceFrame) + 2 * sizeof(uint32_t)) +
-             (uint64_t)g.t_cap * (4 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t)) +
+             (uint64_t)g.t_cap * (9 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t)) +
              (uint64_t)(g.bin_cap + g.mask_cap) * sizeof(uint32_t) +
              (uint64_t)g.p_cap * (3 * sizeof(uint32_t) + sizeof(uint64_t)) +
              (uint64_t)g.part_cap * (sizeof(uint64_t) + sizeof(uint32_t)) +
@@ -1233,6 +1447,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fb.tile_cur = a.take<uint32_t>((size_t)n_tiles + 1);
     fb.tile_order = a.take<uint32_t>((size_t)n_tiles + 1);
     fb.tile_frag = a.take<uint32_t>((size_t)n_tiles + 1);
+    fb.tile_zr = a.take<float>((size_t)n_tiles + 1);
     fb.cnt = a.take<uint32_t>((size_t)n_pix + 1);
     fb.off = a.take<uint64_t>((size_t)n_pix + 1);
     fb.long_q = a.take<uint32_t>((size_t)n_pix + 1);
@@ -1241,7 +1456,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fb.part_max = a.take<uint32_t>(2 * (size_t)nparts);
     fb.scal = a.take<uint64_t>(16);
     if (!fb.vproj || !fb.ved || !fb.fframe || !fb.tzsum || !fb.tile_cnt ||
-        !fb.tile_off || !fb.tile_cur || !fb.tile_order || !fb.tile_frag || !fb.cnt || !fb.off || !fb.long_q || !fb.fix_q || !fb.part || !fb.part_max ||
+        !fb.tile_off || !fb.tile_cur || !fb.tile_order || !fb.tile_frag || !fb.tile_zr || !fb.cnt || !fb.off || !fb.long_q || !fb.fix_q || !fb.part || !fb.part_max ||
         !fb.scal)
         return HEXFC_ERR_OVERFLOW;
     // the array keeps the previous call's contents: clear what must start at zero

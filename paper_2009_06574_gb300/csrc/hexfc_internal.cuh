@@ -1,5 +1,6 @@
 // Internal declarations of the hexfc CUDA library (not part of the C ABI).
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -77,6 +78,28 @@ struct DevMesh {
     FaceStatic* fstat = nullptr;   // [F] static face records
 };
 
+// Tile-capacity network (4 -> 64 -> 64 -> 1): FP32 master weights, the FP16
+// copy the kernels use, Adam moments, and per-tile training values.
+constexpr int kCapIn = 4, kCapHid = 64;
+constexpr int kCapParams = kCapHid * kCapIn + kCapHid + kCapHid * kCapHid + kCapHid + kCapHid + 1;
+struct CapNet {
+    float* w = nullptr;
+    __half* w16 = nullptr;
+    float* m = nullptr;
+    float* v = nullptr;
+    float* grad = nullptr;        // [kCapParams + 1]; the last value is the loss
+    float* h1 = nullptr;          // [tiles * kCapHid] layer values and errors of a training pass
+    float* h2 = nullptr;
+    float* da1 = nullptr;
+    float* da2 = nullptr;
+    float* dy = nullptr;          // [tiles]
+    float* x = nullptr;           // [4 * tiles] features handed in by the caller
+    uint32_t* t = nullptr;        // [tiles] counts handed in by the caller
+    int64_t tiles = 0;            // capacity of the per-tile arrays
+    int64_t step = 0;             // Adam steps taken
+    bool ready = false;           // weights set
+};
+
 // Per-frame buffers owned by the context.
 struct FrameBufs {
     // vertex stage
@@ -93,6 +116,8 @@ struct FrameBufs {
     uint32_t* tile_cur = nullptr;   // [T]
     uint32_t* tile_order = nullptr; // [T] tiles by decreasing chunk count
     uint32_t* tile_frag = nullptr;  // [T] exact fragments per tile (the count's or the fused pass's)
+    float* tile_zr = nullptr;       // [T] depth range of the tile's triangles (fraction of the z24 sum range)
+    float* cap_x = nullptr;         // [4T] capacity-network features of the frame
     uint32_t* tile_cap = nullptr;   // [T+1] chosen fragment capacity per tile (predicted frames)
     uint64_t* cap_off = nullptr;    // [T+1] its exclusive prefix
     uint32_t* tile_over = nullptr;  // [T+1] tiles above their capacity (drawn after the fused pass)
@@ -145,6 +170,13 @@ cudaError_t launch_count_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams
                               int W, int H, cudaStream_t s);
 cudaError_t launch_overflow_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, uint32_t n_over,
                                  uint64_t base, int tiles_x, int W, int H, cudaStream_t s);
+cudaError_t launch_cap_features(FrameBufs& fb, int64_t n_tiles, int tiles_x, float lens_x, float lens_y,
+                                float inv_diag, float motion, cudaStream_t s);
+cudaError_t launch_cap_forward(const CapNet& net, FrameBufs& fb, int64_t n_tiles, float margin, uint32_t pad,
+                               cudaStream_t s);
+cudaError_t launch_cap_grad(CapNet& net, const float* X, const uint32_t* counts, int64_t n, cudaStream_t s);
+cudaError_t launch_cap_adam(CapNet& net, float lr, cudaStream_t s);
+cudaError_t launch_cap_to_half(CapNet& net, cudaStream_t s);
 cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x,
                         int tiles_y, int W, int H, cudaStream_t s);
 cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W, int H,

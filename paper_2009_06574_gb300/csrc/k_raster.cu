@@ -158,7 +158,8 @@ constexpr int kDepthBucketsMax = 4096;
 // sorted or nearly sorted (order within a bucket is arbitrary).
 __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ tile_off,
                                                   const uint32_t* __restrict__ tile_cnt, uint32_t* __restrict__ bins,
-                                                  const uint32_t* __restrict__ tzsum, int nb)
+                                                  const uint32_t* __restrict__ tzsum, int nb,
+                                                  float* __restrict__ tile_zr)
 {
     __shared__ uint32_t s_hist[kDepthBucketsMax];
     __shared__ uint16_t s_b[kBinSortMax];
@@ -167,7 +168,10 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
     const int tile = blockIdx.x;
     const uint64_t beg = tile_off[tile];
     const uint32_t n = tile_cnt[tile];   // real entries; the rest of the padded list is kPadBin
-    if (n < 2 || n > (uint32_t)kBinSortMax) return;
+    if (n < 2 || n > (uint32_t)kBinSortMax) {   // nothing to order; depth range 0 (or unknown: 1)
+        if (threadIdx.x == 0) tile_zr[tile] = n < 2 ? 0.f : 1.f;
+        return;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     auto zsum = [&](uint32_t f2t) -> uint32_t { return tzsum[f2t]; };   // sum of the triangle's window depths
     // depth range of the tile's triangles
@@ -189,6 +193,7 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
     zmax = s_red[1][0];
     for (int w = 1; w < 8; ++w) { zmin = min(zmin, s_red[0][w]); zmax = max(zmax, s_red[1][w]); }
     const float scale = (float)nb / (float)(zmax - zmin + 1);
+    if (threadIdx.x == 0) tile_zr[tile] = (float)(zmax - zmin) * (1.f / 50331648.f);   // of 3 * 2^24
     // histogram
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
         const int b = min((int)((float)(zsum(bins[beg + i]) - zmin) * scale), nb - 1);
@@ -1032,7 +1037,8 @@ cudaError_t launch_bin_fill(const DevMesh& m, FrameBufs& fb, int tiles_x, int W,
 cudaError_t launch_bin_sort(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int buckets, cudaStream_t s)
 {
     (void)m;
-    k_bin_sort<<<(unsigned)(tiles_x * tiles_y), 256, 0, s>>>(fb.tile_off, fb.tile_cnt, fb.bins, fb.tzsum, buckets);
+    k_bin_sort<<<(unsigned)(tiles_x * tiles_y), 256, 0, s>>>(fb.tile_off, fb.tile_cnt, fb.bins, fb.tzsum, buckets,
+                                                              fb.tile_zr);
     return cudaGetLastError();
 }
 

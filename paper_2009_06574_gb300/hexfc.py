@@ -37,6 +37,7 @@ HEXFC_OPT_STAGE_TIMING = 2
 HEXFC_OPT_DEPTH_BUCKETS = 3
 HEXFC_OPT_COMPOSITE_WINDOW = 4
 HEXFC_OPT_PREDICTED_CAPACITY = 5
+HEXFC_CAPACITY_PARAMS = 4545
 STAGES = ["vertex", "face", "tile_scan", "gap1", "bin", "count", "scan", "gap2", "fill", "composite"]
 
 # every symbol include/hexfc.h declares
@@ -44,7 +45,9 @@ EXPORTS = ["hexfc_style_default", "hexfc_create", "hexfc_destroy", "hexfc_upload
            "hexfc_set_cell_importance", "hexfc_mesh_info", "hexfc_set_view", "hexfc_set_lens",
            "hexfc_set_style", "hexfc_render", "hexfc_render_host", "hexfc_debug_pixels", "hexfc_set_option",
            "hexfc_stage_times", "hexfc_status_string", "hexfc_render_noalloc", "hexfc_share_mesh",
-           "hexfc_frame_memory", "hexfc_trim", "hexfc_render_batch"]
+           "hexfc_frame_memory", "hexfc_trim", "hexfc_render_batch", "hexfc_capacity_reset",
+           "hexfc_capacity_set_weights", "hexfc_capacity_get_weights", "hexfc_capacity_grad",
+           "hexfc_capacity_train"]
 
 
 class HexfcError(RuntimeError):
@@ -124,6 +127,11 @@ def load():
                 "hexfc_frame_memory": (i32, [vp, C.POINTER(u64)]),
                 "hexfc_trim": (i32, [vp]),
                 "hexfc_render_batch": (i32, [vp, i32, vp, vp, vp, vp]),
+                "hexfc_capacity_reset": (i32, [vp, u64]),
+                "hexfc_capacity_set_weights": (i32, [vp, vp, i64]),
+                "hexfc_capacity_get_weights": (i32, [vp, vp, i64]),
+                "hexfc_capacity_grad": (i32, [vp, vp, vp, i64, vp, vp]),
+                "hexfc_capacity_train": (i32, [vp, i32, C.c_float, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -307,6 +315,35 @@ class Renderer:
         if check:
             _check(r, "hexfc_render_batch")
         return r, [int(ist[k]) for k in range(n)], [st[k].as_dict() for k in range(n)]
+
+    # ---- tile-capacity network
+    def capacity_reset(self, seed: int = 0):
+        _check(load().hexfc_capacity_reset(self._h, int(seed)), "hexfc_capacity_reset")
+
+    def capacity_set_weights(self, w):
+        a = np.ascontiguousarray(w, dtype=np.float32)
+        _check(load().hexfc_capacity_set_weights(self._h, _np_ptr(a), a.size), "hexfc_capacity_set_weights")
+
+    def capacity_get_weights(self) -> np.ndarray:
+        a = np.zeros(HEXFC_CAPACITY_PARAMS, dtype=np.float32)
+        _check(load().hexfc_capacity_get_weights(self._h, _np_ptr(a), a.size), "hexfc_capacity_get_weights")
+        return a
+
+    def capacity_grad(self, x, counts):
+        """(loss, gradient) of the network on host features x [n, 4] and counts [n]."""
+        xa = np.ascontiguousarray(x, dtype=np.float32)
+        ca = np.ascontiguousarray(counts, dtype=np.uint32)
+        g = np.zeros(HEXFC_CAPACITY_PARAMS, dtype=np.float32)
+        loss = C.c_float(0.0)
+        _check(load().hexfc_capacity_grad(self._h, _np_ptr(xa), _np_ptr(ca), ca.size, _np_ptr(g), C.byref(loss)),
+               "hexfc_capacity_grad")
+        return float(loss.value), g
+
+    def capacity_train(self, steps: int, lr: float = 1e-3, stream=None, want_loss: bool = True):
+        loss = C.c_float(0.0)
+        _check(load().hexfc_capacity_train(self._h, int(steps), float(lr), C.byref(loss) if want_loss else None,
+                                           _stream_ptr(stream)), "hexfc_capacity_train")
+        return float(loss.value) if want_loss else None
 
     def render_noalloc(self, mesh: int, out, stream=None, check: bool = True):
         """Like render, with every per-frame buffer in the library's fixed scratch

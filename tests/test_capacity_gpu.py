@@ -1,0 +1,93 @@
+"""The tile-capacity network on the GPU: its forward/backward kernels give the
+oracle's loss and gradient (at the same FP16-rounded weights), training on the
+exact counts of rendered frames lowers the loss, and frames drawn with its
+capacities are bit-identical to the count-then-fill path."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import capacity_mlp as mlp
+from paper_2009_06574_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hx():
+    from paper_2009_06574_gb300 import hexfc
+    hexfc.load()
+    return hexfc
+
+
+def test_gradient_matches_oracle(hx):
+    r = hx.Renderer(0)
+    w = mlp.init(4).astype(np.float32)
+    r.capacity_set_weights(w)
+    np.testing.assert_array_equal(r.capacity_get_weights(), w)
+    w16 = w.astype(np.float16).astype(np.float64)     # the kernels use the FP16 copy
+    rng = np.random.default_rng(8)
+    n = 700
+    x = np.stack([rng.uniform(0, 1, n), rng.uniform(0, 0.5, n), rng.uniform(0, 1.5, n),
+                  np.full(n, 0.05)], axis=1).astype(np.float32)
+    counts = rng.integers(0, 20000, n).astype(np.uint32)
+    loss, g = r.capacity_grad(x, counts)
+    t = np.log1p(counts.astype(np.float64))
+    loss_o, g_o = mlp.grad(w16, x.astype(np.float64), t)
+    assert loss == pytest.approx(loss_o, rel=2e-4)
+    scale = np.abs(g_o).max()
+    np.testing.assert_allclose(g, g_o, rtol=2e-3, atol=2e-5 * scale)
+    with pytest.raises(hx.HexfcError):
+        r.capacity_set_weights(w[:-1])
+    r.close()
+
+
+def test_training_on_rendered_frames_lowers_the_loss(hx):
+    r = hx.Renderer(0)
+    m = synth.hex_grid(12, jitter=0.1, warp_amp=0.3, seed=3)
+    mid = r.upload_mesh(m.verts, m.cells, m.cell_scalar, m.edge_level)
+    r.capacity_reset(7)
+    out = torch.empty((180, 240, 4), device="cuda")
+    losses = []
+    for f in range(12):
+        r.set_view(synth.orbit_view(f, 120, 240, 180))
+        r.set_lens(synth.lissajous_lens(f, 120))
+        r.render(mid, out)
+        losses.append(r.capacity_train(30, lr=3e-3))
+    assert losses[-1] < 0.5 * losses[0]
+    first = r.capacity_train(0)
+    after = r.capacity_train(60, lr=3e-3)
+    assert after <= first
+    r.close()
+
+
+def test_network_capacities_draw_exact_frames(hx):
+    m = synth.hex_grid(10, jitter=0.1, warp_amp=0.3, seed=6)
+    style = synth.Style(w_base=1.5, lod=2)
+    ex, pr = hx.Renderer(0), hx.Renderer(0)
+    me = ex.upload_mesh(m.verts, m.cells, m.cell_scalar, m.edge_level)
+    mp = pr.upload_mesh(m.verts, m.cells, m.cell_scalar, m.edge_level)
+    for r in (ex, pr):
+        r.set_style(style)
+    pr.set_option(hx.HEXFC_OPT_PREDICTED_CAPACITY, 2)
+    view0 = synth.orbit_view(0, 120, 200, 150)
+    pr.set_view(view0)
+    out = torch.empty((150, 200, 4), device="cuda")
+    with pytest.raises(hx.HexfcError) as e:     # no weights yet
+        pr.render(mp, out)
+    assert e.value.status == hx.HEXFC_ERR_STATE
+    pr.capacity_reset(1)
+    n_pred = 0
+    for f in range(10):
+        view, lens = synth.orbit_view(f, 120, 200, 150), synth.lissajous_lens(f, 120)
+        imgs = []
+        for r, mid in ((ex, me), (pr, mp)):
+            r.set_view(view)
+            r.set_lens(lens)
+            o = torch.empty((150, 200, 4), device="cuda")
+            r.render(mid, o)
+            imgs.append(o.cpu().numpy())
+        np.testing.assert_array_equal(imgs[1], imgs[0])
+        n_pred += pr.last_stats["predicted"]
+        pr.capacity_train(20, lr=3e-3)
+    assert n_pred >= 5
+    ex.close(); pr.close()
