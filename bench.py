@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--slots", type=int, default=8, help="serving: frames in flight at most")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: device memory for frames")
     ap.add_argument("--serve-sizes", default="16,32,48,64,80,96,112,128", help="serving: grid sizes N")
+    ap.add_argument("--learned-n", type=int, default=128, help="learned capacity: grid size N")
+    ap.add_argument("--train-steps", type=int, default=8, help="learned capacity: Adam steps per training frame")
     return ap.parse_args()
 
 
@@ -523,6 +525,80 @@ def run_batch(args, rank, world):
     r.close()
 
 
+def run_learned(args, rank, world):
+    """Learned tile capacities: a warped 128^3 grid at 3840x2160 along a
+    500-frame camera and lens path. Frames 0-399 are drawn by count-then-fill
+    and the capacity network trains on each frame's exact tile counts; frames
+    400-499 are then drawn (timed) by count-then-fill, by the fused pass with
+    the network's capacities, and by the fused pass with the previous frame's
+    counts as capacities."""
+    import numpy as np
+    import torch
+    from paper_2009_06574_gb300 import hexfc, synth
+
+    if rank != 0:
+        return
+    n, (W, H), n_frames, n_train = args.learned_n, (3840, 2160), 500, 400
+    r = hexfc.Renderer(0)
+    m = synth.hex_grid(n, jitter=0.1, warp_amp=0.3, seed=100 + n)
+    mid = r.upload_mesh(m.verts, m.cells, None, m.edge_level)
+    r.set_style(synth.Style(w_base=2.0, lod=4, delta=0.08, tf_hi=0.15))
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def frame(f):
+        r.set_view(synth.orbit_view(f, n_frames, W, H))
+        r.set_lens(synth.lissajous_lens(f, n_frames))
+        r.render(mid, out, stream)
+        return r.last_stats
+
+    r.capacity_reset(1)
+    t0 = time.perf_counter()
+    losses = []
+    for f in range(n_train):
+        frame(f)
+        losses.append(r.capacity_train(args.train_steps, lr=2e-3, stream=stream))
+    train_s = time.perf_counter() - t0
+    res = {}
+    for name, mode in (("count_then_fill", 0), ("network", 2), ("previous_frame", 1)):
+        r.set_option(hexfc.HEXFC_OPT_PREDICTED_CAPACITY, mode)
+        frame(n_train - 2)
+        frame(n_train - 1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        e0.record(stream)
+        for f in range(n_train, n_frames):
+            stats.append(frame(f))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        frags = sum(st["fragments"] for st in stats)
+        pred = [st for st in stats if st["predicted"]]
+        res[name] = {
+            "frames_per_s": len(stats) / (ms / 1000.0), "ms_per_frame": ms / len(stats),
+            "fragments_per_s": frags / (ms / 1000.0),
+            "predicted_frames": len(pred), "exact_redraws": sum(1 for st in stats if st["capacity"] and not st["predicted"]),
+            "overflow_tiles_per_frame": float(np.mean([st["overflow_tiles"] for st in stats])),
+            "capacity_over_fragments": (float(np.mean([st["capacity"] / max(st["fragments"], 1) for st in pred]))
+                                        if pred else None),
+        }
+    r.set_option(hexfc.HEXFC_OPT_PREDICTED_CAPACITY, 0)
+    line = {
+        "metric": "frames/s, learned tile capacity vs count-then-fill (128^3, 3840x2160)",
+        "value": res["network"]["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "higher_is_better": True,
+        "impl": "ours", "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"grid{n}_orbit500_3840x2160_learned_capacity", "train_frames": n_train,
+                   "eval_frames": n_frames - n_train, "train_steps_per_frame": args.train_steps},
+        "modes": res,
+        "speedup_vs_count_then_fill": res["network"]["frames_per_s"] / res["count_then_fill"]["frames_per_s"],
+        "train_loss": {"first": losses[0], "after_100": losses[min(99, len(losses) - 1)], "last": losses[-1]},
+        "train_seconds": train_s,
+    }
+    print(json.dumps(line), flush=True)
+    r.close()
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", 0))
@@ -536,6 +612,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args, rank, world)
+        return
+    if args.workload == "learned":
+        run_learned(args, rank, world)
         return
     if world > 1:
         import torch
