@@ -403,8 +403,12 @@ struct CountWarp {
     // float copies of the edge functions: E ~ e0f + fa*rx + fb*ry, and a bound on the
     // float error; outside the bound the float sign is the exact sign
     float e0f[3][kChunk], fa[3][kChunk], fb[3][kChunk], tol[3][kChunk];
-    uint32_t mask[kTilePix];
-    uint32_t count[kTilePix];
+    // the chunk's samples as one sequence: triangle j's box samples start at
+    // start[j]; r2j maps the rank of a non-empty triangle to its index
+    uint32_t start[kChunk];
+    float inv_bw[kChunk];
+    uint8_t r2j[kChunk];
+    uint32_t mask[kTilePix];   // coverage bits of the chunk; after the last chunk, the warp's per-pixel counts
 };
 
 // Float version of triangle j's edge functions in the warp's staging slot.
@@ -444,16 +448,18 @@ __device__ __forceinline__ bool cover_fast(const CountWarp& me, int j, int rx, i
 }
 
 // Warp `warp` of a tile block rasterises chunks warp, warp + kConsumerWarps, ...
-// of the tile's list into masks (global, per chunk) and adds their bit counts
-// to its private per-pixel counts s_w[warp].count.
+// of the tile's list into masks (global, per chunk); its per-pixel counts are
+// left in s_w[warp].mask.
 __device__ __forceinline__ void count_chunks(CountWarp* s_w, int warp, int lane, const uint32_t* __restrict__ bins,
                                              const FaceFrame* __restrict__ fframe, uint64_t beg, uint32_t n_chunks,
                                              int px0, int py0, int W, int H, uint32_t* __restrict__ masks)
 {
     CountWarp& me = s_w[warp];
-    for (int i = lane; i < kTilePix; i += 32) {
-        me.mask[i] = 0;
-        me.count[i] = 0;
+    uint32_t count[kTilePix / 32];   // pixels lane + 32 k
+#pragma unroll
+    for (int k = 0; k < kTilePix / 32; ++k) {
+        me.mask[lane + 32 * k] = 0;
+        count[k] = 0;
     }
     __syncwarp();
     uint32_t f2t = warp < (int)n_chunks ? bins[beg + (uint64_t)warp * kChunk + lane] : kPadBin;
@@ -470,29 +476,54 @@ __device__ __forceinline__ void count_chunks(CountWarp* s_w, int warp, int lane,
             me.c.box[lane] = 0;
         }
         f2t = f2t_next;
+        // the box samples of the chunk's 32 triangles as one sequence, so that
+        // every round gives each lane a sample whatever the boxes' sizes
+        const int bx_l = me.c.box[lane];
+        const uint32_t area_l = (uint32_t)(box_bw(bx_l) * box_bh(bx_l));
+        uint32_t incl = area_l;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t start_l = incl - area_l, total = __shfl_sync(0xffffffffu, incl, 31);
+        const unsigned nonempty = __ballot_sync(0xffffffffu, area_l != 0);
+        me.start[lane] = start_l;
+        me.inv_bw[lane] = area_l ? __frcp_rn((float)box_bw(bx_l)) : 0.f;
+        if (area_l) me.r2j[__popc(nonempty & ((1u << lane) - 1u))] = (uint8_t)lane;
         __syncwarp();
-        for (int j = 0; j < kChunk; ++j) {
-            const int bx = me.c.box[j];
-            const int bw = box_bw(bx), area = bw * box_bh(bx);
-            if (area == 0) continue;
-            const int lx0 = box_lx0(bx), ly0 = box_ly0(bx);
-            const float inv_bw = __frcp_rn((float)bw);
-            for (int idx = lane; idx < area; idx += 32) {
-                // exact for idx < 256, bw <= 16: the quotient is never within 1/32 of an integer
-                const int ry = (int)(((float)idx + 0.5f) * inv_bw);
-                const int rx = idx - ry * bw;
-                if (cover_fast(me, j, rx, ry)) atomicOr(&me.mask[(ly0 + ry) * kTile + lx0 + rx], 1u << j);
+        for (uint32_t g = 0; g < total; g += 32) {
+            // triangles starting in [g, g + 32) (bit = offset) and those before g
+            const bool starts = area_l != 0 && start_l >= g && start_l < g + 32;
+            const uint32_t smask = __reduce_or_sync(0xffffffffu, starts ? 1u << (start_l - g) : 0u);
+            const int before = __popc(__ballot_sync(0xffffffffu, area_l != 0 && start_l < g));
+            const uint32_t idx = g + (uint32_t)lane;
+            if (idx < total) {
+                const int c = __popc(smask & (0xffffffffu >> (31 - lane)));   // starts in [g, idx]
+                const int j = me.r2j[c > 0 ? before + c - 1 : before - 1];
+                const int bx = me.c.box[j];
+                const int bw = box_bw(bx);
+                const int off = (int)(idx - me.start[j]);
+                // exact for off < 256, bw <= 16: the quotient is never within 1/32 of an integer
+                const int ry = (int)(((float)off + 0.5f) * me.inv_bw[j]);
+                const int rx = off - ry * bw;
+                if (cover_fast(me, j, rx, ry))
+                    atomicOr(&me.mask[(box_ly0(bx) + ry) * kTile + box_lx0(bx) + rx], 1u << j);
             }
         }
         __syncwarp();
-        for (int i = lane; i < kTilePix; i += 32) {
+#pragma unroll
+        for (int k = 0; k < kTilePix / 32; ++k) {
+            const int i = lane + 32 * k;
             const uint32_t m = me.mask[i];
             me.mask[i] = 0;
             masks[(beg / kChunk + c) * kTilePix + i] = m;
-            me.count[i] += __popc(m);
+            count[k] += __popc(m);
         }
         __syncwarp();
     }
+#pragma unroll
+    for (int k = 0; k < kTilePix / 32; ++k) me.mask[lane + 32 * k] = count[k];
 }
 
 // Sum of v over the block's first kTilePix threads (all threads call it).
@@ -512,7 +543,7 @@ __device__ __forceinline__ uint32_t tile_sum(uint32_t v, uint32_t* s_tmp)
 
 // Per tile: coverage of every chunk as per-pixel bit masks (kept for the
 // fill) and the per-pixel list lengths; the tile's total goes to tile_frag.
-__global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__ tile_off,
+__global__ void __launch_bounds__(kTilePix, 5) k_count(const uint64_t* __restrict__ tile_off,
                                                     const uint32_t* __restrict__ bins,
                                                     const FaceFrame* __restrict__ fframe,
                                                     const uint32_t* __restrict__ order, int tiles_x, int W, int H,
@@ -531,7 +562,7 @@ __global__ void __launch_bounds__(kTilePix) k_count(const uint64_t* __restrict__
     __syncthreads();
     uint32_t n = 0;
 #pragma unroll
-    for (int w = 0; w < kConsumerWarps; ++w) n += s_w[w].count[threadIdx.x];
+    for (int w = 0; w < kConsumerWarps; ++w) n += s_w[w].mask[threadIdx.x];
     cnt[(int64_t)tile * kTilePix + threadIdx.x] = n;
     const uint32_t total = tile_sum(n, s_tmp);
     if (threadIdx.x == 0) tile_frag[tile] = total;
@@ -868,7 +899,7 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_count_fill(const uint64_t* 
     uint32_t n = 0;
     if (warp < kConsumerWarps)
 #pragma unroll
-        for (int w = 0; w < kConsumerWarps; ++w) n += s_w[w].count[threadIdx.x];
+        for (int w = 0; w < kConsumerWarps; ++w) n += s_w[w].mask[threadIdx.x];
     uint32_t incl = n, mx = n, lg = n > (uint32_t)kWarpSortMax ? 1u : 0u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
