@@ -412,13 +412,14 @@ struct CountWarp {
 };
 
 // Float version of triangle j's edge functions in the warp's staging slot.
-// The float evaluation fmaf(fa, rx, fmaf(fb, ry, e0f)) has three roundings of
-// magnitudes at most |e0| + 15 (|fa| + |fb|); tol is twice that bound.
+// e0f is within 0.75 ulp of e0 and the float evaluation fmaf(fa, rx,
+// fmaf(fb, ry, e0f)) adds two roundings, all of magnitudes at most |e0| +
+// 15 (|fa| + |fb|): at most 3.5 units of 2^-24 of that, and tol allows 8.
 __device__ __forceinline__ void stage_fast(CountWarp& me, int j)
 {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float e0 = (float)me.c.e0[k][j];
+        const float e0 = i64_to_f32(me.c.e0[k][j]);
         const float fa = -256.f * (float)me.c.dy[k][j];   // exact: |dy| < 2^24
         const float fb = 256.f * (float)me.c.dx[k][j];
         me.e0f[k][j] = e0;

@@ -95,6 +95,13 @@ __device__ __forceinline__ float u64_to_f32(uint64_t v)
     return fmaf((float)(uint32_t)(v >> 32), 4294967296.f, (float)(uint32_t)v);
 }
 
+// |v| < 2^55 to float by sign and magnitude (u64_to_f32): within 0.75 ulp.
+__device__ __forceinline__ float i64_to_f32(int64_t v)
+{
+    const float m = u64_to_f32((uint64_t)(v < 0 ? -v : v));
+    return v < 0 ? -m : m;
+}
+
 // Per-sample depth: z0 + floor((l1 (z1 - z0) + l2 (z2 - z0)) / area), exact.
 __device__ __forceinline__ uint32_t sample_depth(uint32_t z0, uint32_t z1, uint32_t z2, int64_t l1, int64_t l2,
                                                  int64_t area, bool& bad)
