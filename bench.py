@@ -37,7 +37,7 @@ FRAG_BYTES = 24          # 8 B key + 16 B premultiplied RGBA
 # one pass, on the 1920x1080 bench frame), per fragment drawn, and the fill kernel's
 # sources it was taken on: the roofline reports it only while those sources are unchanged.
 FILL_DRAM = {"bytes_per_fragment": 42.12,
-             "sha256": "085ac33ba80cd5547a23f5a973a2360b3e70737c4bf09f8cc35045492a74db47",
+             "sha256": "299dd47dd2d2e36843d4e927eaf8a37a3bb10f07e678307f2f265c184c99ee80",
              "profile": "profiles/k_fill_dram_grid64_orbit_1080p.md"}
 FILL_SOURCES = ("csrc/k_raster.cu", "csrc/shade.cuh", "csrc/raster_common.cuh", "csrc/pipeline.cuh",
                 "csrc/hexfc_internal.cuh")

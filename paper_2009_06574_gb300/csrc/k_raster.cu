@@ -6,9 +6,15 @@
 //                   visibility masks of Eq. 1, triangle validity, and the
 //                   number of 16x16 tiles each triangle's box touches.
 //   k_bin_fill      per face: append 2*face+tri to the list of every touched tile.
-//   k_count         per tile (one thread per pixel): exact coverage count.
-//   k_fill          per tile: exact coverage again; every covered sample is
-//                   shaded with Eqs. 1-4 and written at its pixel's offset.
+//   k_bin_sort      per tile: counting sort of the tile's triangles by depth.
+//   k_tile_order    the tiles by decreasing work (for count and fill).
+//   k_count         per tile: exact coverage as per-chunk masks and per-pixel
+//                   counts.
+//   k_fill          per tile: every covered sample (from the masks) gets its
+//                   exact depth, is shaded with Eqs. 1-4 and written at its
+//                   pixel's offset plus its rank in the pixel's list.
+//   k_count_fill    per tile, with capacities chosen before the frame: count
+//                   and fill in one pass (no separate count, no global scan).
 //
 // Each face is drawn as two triangles (Section "Method Overview"; Section "GPU
 // Implementation"), all covered samples are kept (per-pixel fragment lists,
