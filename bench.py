@@ -64,6 +64,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-steps", type=int, default=60)
+    ap.add_argument("--no-4k", action="store_true", help="skip the secondary 3840x2160 measurement")
     ap.add_argument("--predicted", type=int, default=0,
                     help="tile capacities: 0 count-then-fill, 1 previous frame's counts, 2 capacity network")
     # serving mode (--workload serving): Poisson request stream over resident meshes
@@ -248,6 +249,36 @@ def reduce_replicas(ms: float, frag_sum: float, e2e_s: float, device) -> tuple:
     return float(t[0].item()), float(fs.item()), float(t[1].item())
 
 
+def secondary_4k(args, hexfc, torch, stream, steps: int = 12, warmup: int = 3):
+    """The metric's second size: the warped 128^3 grid at 3840x2160 along its
+    orbit (cell importance fixed at upload), device-timed frames/s and
+    fragments/s. Runs after the main measurement, outside its timed region."""
+    w = workload_by_name("grid128_orbit_4k")
+    mesh = w.mesh()
+    r = hexfc.Renderer(torch.cuda.current_device())
+    mid = r.upload_mesh(mesh.verts, mesh.cells, None, mesh.edge_level)
+    r.set_style(w.style)
+    out = torch.empty((w.height, w.width, 4), dtype=torch.float32, device="cuda")
+    frags = 0
+    for i in range(warmup + steps):
+        if i == warmup:
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        f = (i * 5) % w.n_frames
+        r.set_view(w.view(f))
+        r.set_lens(w.lens(f))
+        r.render(mid, out, stream)
+        if i >= warmup:
+            frags += r.last_stats["fragments"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    r.close()
+    return {"workload": w.name, "frames_per_s": steps / (ms / 1000.0), "ms_per_frame": ms / steps,
+            "fragments_per_frame": frags / steps, "fragments_per_s": frags / (ms / 1000.0), "steps": steps}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -363,6 +394,12 @@ def run_ours(args, rank, world, local_rank):
     traffic = None
     if dom == "fill" and fill_sources_sha256() == FILL_DRAM["sha256"]:
         traffic = FILL_DRAM["bytes_per_fragment"] * F
+    sec = None
+    if not args.no_4k:
+        try:
+            sec = secondary_4k(args, hexfc, torch, stream)
+        except Exception as e:   # the main line stands on its own
+            sec = {"workload": "grid128_orbit_4k", "failed": str(e)}
     cpu = None
     if not args.no_cpu_baseline:
         try:
@@ -391,6 +428,7 @@ def run_ours(args, rank, world, local_rank):
                      "traffic_source": FILL_DRAM["profile"] if traffic else None,
                      "peak_kind": peak_kind, "algorithmic_bytes": algo[dom]},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "secondary_4k": sec,
     }
     print(json.dumps(line), flush=True)
 
