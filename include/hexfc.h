@@ -308,7 +308,8 @@ enum {
     HEXFC_OPT_REVERSE_BIN_ORDER = 1, /* 1: process faces in reverse id order when binning (test hook) */
     HEXFC_OPT_STAGE_TIMING = 2,      /* 1: record CUDA events around every stage of hexfc_render* */
     HEXFC_OPT_DEPTH_BUCKETS = 3,     /* buckets of the per-tile depth order of the triangles: a power of
-                                        two in 256..4096 (default 2048) */
+                                        two in 256..4096 (default 2048), or 0 for no depth order (lists
+                                        in the faces' order: a test hook for the sorting passes) */
     HEXFC_OPT_COMPOSITE_WINDOW = 4,  /* sorted window of the per-pixel resolve: 4 (default) or 8 */
     HEXFC_OPT_PREDICTED_CAPACITY = 5 /* 0: count-then-fill (default); 1: capacities from the previous
                                         frame's tile counts; 2: from the capacity network. See below. */

@@ -184,9 +184,9 @@ __device__ __forceinline__ float4 finish(CT c, float bg0, float bg1, float bg2)
 // window overflows, so a list whose elements sit at most KW - 1 places from
 // their sorted position comes out sorted. The blend checks that the keys it
 // consumes increase; a list that breaks that is queued for the warp-wide
-// resolve of k_composite_fix, and lists longer than 256 for the block-wide
-// sort of k_composite_long. KW (4 or 8) trades registers for fewer queued
-// lists; the result does not depend on it.
+// resolve of k_composite_fix, or, if longer than 256, for the block-wide sort
+// of k_composite_long. KW (4 or 8) trades registers for fewer queued lists;
+// the result does not depend on it.
 struct KC {
     uint64_t k;
     float4 c;
@@ -224,10 +224,6 @@ __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ 
     tile_pixel(q, tiles_x, x, y);
     if (x >= W || y >= H) return;
     const uint32_t n = cnt[q];
-    if (n > (uint32_t)kWarpList) {
-        long_q[atomicAdd(long_cursor, 1ull)] = (uint32_t)q;
-        return;
-    }
     const uint64_t* kp = key + off[q];
     const float4* rp = rgba + off[q];
     CT c{0.f, 0.f, 0.f, 1.f};
@@ -260,6 +256,7 @@ __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ 
     for (int k = 0; k < KW; ++k)
         if ((uint32_t)k < pre) blend_checked(c, last, ok, w[k]);
     if (ok) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
+    else if (n > (uint32_t)kWarpList) long_q[atomicAdd(long_cursor, 1ull)] = (uint32_t)q;
     else fix_q[atomicAdd(fix_cursor, 1ull)] = (uint32_t)q;
 }
 

@@ -154,7 +154,7 @@ __global__ void k_bin_fill(const FaceFrame* __restrict__ fframe, int64_t n_faces
 
 // ------------------------------------------------------------------ bin order
 
-constexpr int kBinSortMax = 4096;   // longer tile lists keep their arrival order
+constexpr int kBinSortMax = 4096;   // longer tile lists are sorted through global scratch
 constexpr int kDepthBucketsMax = 4096;
 
 // Orders each tile's list front to back by a counting sort of the triangles
@@ -165,7 +165,7 @@ constexpr int kDepthBucketsMax = 4096;
 __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ tile_off,
                                                   const uint32_t* __restrict__ tile_cnt, uint32_t* __restrict__ bins,
                                                   const uint32_t* __restrict__ tzsum, int nb,
-                                                  float* __restrict__ tile_zr)
+                                                  float* __restrict__ tile_zr, uint32_t* __restrict__ tmp)
 {
     __shared__ uint32_t s_hist[kDepthBucketsMax];
     __shared__ uint16_t s_b[kBinSortMax];
@@ -174,10 +174,11 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
     const int tile = blockIdx.x;
     const uint64_t beg = tile_off[tile];
     const uint32_t n = tile_cnt[tile];   // real entries; the rest of the padded list is kPadBin
-    if (n < 2 || n > (uint32_t)kBinSortMax) {   // nothing to order; depth range 0 (or unknown: 1)
-        if (threadIdx.x == 0) tile_zr[tile] = n < 2 ? 0.f : 1.f;
+    if (n < 2) {   // nothing to order; depth range 0
+        if (threadIdx.x == 0) tile_zr[tile] = 0.f;
         return;
     }
+    const bool big = n > (uint32_t)kBinSortMax;   // buckets recomputed, scatter through tmp
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     auto zsum = [&](uint32_t f2t) -> uint32_t { return tzsum[f2t]; };   // sum of the triangle's window depths
     // depth range of the tile's triangles
@@ -200,10 +201,11 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
     for (int w = 1; w < 8; ++w) { zmin = min(zmin, s_red[0][w]); zmax = max(zmax, s_red[1][w]); }
     const float scale = (float)nb / (float)(zmax - zmin + 1);
     if (threadIdx.x == 0) tile_zr[tile] = (float)(zmax - zmin) * (1.f / 50331648.f);   // of 3 * 2^24
+    auto bucket = [&](uint32_t f2t) -> int { return min((int)((float)(zsum(f2t) - zmin) * scale), nb - 1); };
     // histogram
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const int b = min((int)((float)(zsum(bins[beg + i]) - zmin) * scale), nb - 1);
-        s_b[i] = (uint16_t)b;
+        const int b = bucket(bins[beg + i]);
+        if (!big) s_b[i] = (uint16_t)b;
         atomicAdd(&s_hist[b], 1u);
     }
     __syncthreads();
@@ -235,9 +237,14 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
     }
     __syncthreads();
     // scatter (arbitrary order inside a bucket), then write back
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) s_out[atomicAdd(&s_hist[s_b[i]], 1u)] = bins[beg + i];
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint32_t f2t = bins[beg + i];
+        const uint32_t slot = atomicAdd(&s_hist[big ? bucket(f2t) : (int)s_b[i]], 1u);
+        if (big) tmp[beg + slot] = f2t;
+        else s_out[slot] = f2t;
+    }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) bins[beg + i] = s_out[i];
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) bins[beg + i] = big ? tmp[beg + i] : s_out[i];
 }
 
 // ------------------------------------------------------------------ tile order
@@ -1075,8 +1082,10 @@ cudaError_t launch_bin_fill(const DevMesh& m, FrameBufs& fb, int tiles_x, int W,
 cudaError_t launch_bin_sort(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int buckets, cudaStream_t s)
 {
     (void)m;
+    if (buckets == 0)   // no depth order (lists keep the faces' arrival order); depth ranges unknown
+        return cudaMemsetAsync(fb.tile_zr, 0, sizeof(float) * (size_t)tiles_x * tiles_y, s);
     k_bin_sort<<<(unsigned)(tiles_x * tiles_y), 256, 0, s>>>(fb.tile_off, fb.tile_cnt, fb.bins, fb.tzsum, buckets,
-                                                              fb.tile_zr);
+                                                              fb.tile_zr, fb.bins_tmp);
     return cudaGetLastError();
 }
 

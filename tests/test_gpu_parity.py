@@ -26,9 +26,11 @@ def hx():
     return hexfc
 
 
-def render_both(hx, mesh, view, lens, style, px=None, py=None, scalar=None):
+def render_both(hx, mesh, view, lens, style, px=None, py=None, scalar=None, options=None):
     scalar = mesh.cell_scalar if scalar is None else scalar
     r = hx.Renderer(0)
+    for opt, val in (options or {}).items():
+        r.set_option(opt, val)
     mid = r.upload_mesh(mesh.verts, mesh.cells, scalar, mesh.edge_level)
     r.set_view(view)
     r.set_lens(lens)
@@ -93,9 +95,11 @@ def test_axis_aligned_cube(hx):
     assert st["fragments"] == 2 * 32 * 32
 
 
-def test_long_lists(hx):
+@pytest.mark.parametrize("depth_order", [True, False])
+def test_long_lists(hx, depth_order):
     """A 1x1x300 column of cells seen along its axis: 301 fragments per pixel,
-    past the register sort (256), through the shared-memory path."""
+    past the register sort (256): in depth order the lists stream through the
+    resolve window, without it (faces' order) through the shared-memory sort."""
     nz = 300
     xs = np.array([-0.2, 0.2], np.float32)
     verts = np.array([(x, y, z) for z in np.linspace(-0.5, 0.5, nz + 1) for y in xs for x in xs], np.float32)
@@ -108,9 +112,29 @@ def test_long_lists(hx):
     mesh = synth.HexMesh(verts, cells, scalar, np.zeros((nz, 12), np.uint8))
     view = synth.View(eye=(0.0, 0.0, 3.0), fovy_deg=0.0, ortho_half_h=0.5, znear=0.5, zfar=5.0, width=40, height=40)
     style = synth.Style(alpha_min=0.05, alpha_max=0.3)
-    st, _ = render_both(hx, mesh, view, synth.Lens(mode=0, center=(20, 20, 0), radius=12.0), style)
+    opts = {} if depth_order else {hx.HEXFC_OPT_DEPTH_BUCKETS: 0}
+    st, _ = render_both(hx, mesh, view, synth.Lens(mode=0, center=(20, 20, 0), radius=12.0), style, options=opts)
     assert st["gpu_stats"]["max_list"] == nz + 1
     assert st["gpu_stats"]["long_lists"] > 100
+
+
+def test_tiles_past_shared_sort(hx):
+    """A 16^3 grid drawn into 32x32 pixels (four tiles): the tiles list more
+    than 4096 triangles, so the per-tile depth order runs through global
+    scratch instead of shared memory."""
+    mesh = synth.hex_grid(16, jitter=0.1, warp_amp=0.2, seed=5)
+    view = synth.orbit_view(20, 120, 32, 32)
+    st, _ = render_both(hx, mesh, view, synth.lissajous_lens(20, 32), synth.Style(w_base=1.0))
+    assert st["gpu_stats"]["bin_entries"] > 4 * (4096 + 32)
+
+
+def test_without_depth_order(hx):
+    """Lists in the faces' order (no per-tile depth order): most lists go
+    through the warp-wide sort of the out-of-order pass; the result is the same."""
+    mesh = synth.hex_grid(8, jitter=0.1, warp_amp=0.3, seed=2)
+    view = synth.orbit_view(50, 120, 160, 120)
+    render_both(hx, mesh, view, synth.lissajous_lens(50, 120), synth.Style(w_base=1.5, lod=2),
+                options={hx.HEXFC_OPT_DEPTH_BUCKETS: 0})
 
 
 def test_empty_frame_is_background(hx):
