@@ -5,13 +5,19 @@
 //
 // The paper sorts with a per-pixel priority queue. Here the fill pass visits
 // each tile's triangles in depth order, so every list arrives sorted or nearly
-// sorted. One thread per pixel streams its list front to back through a small
-// sorted window in registers (the lists of a warp's 32 pixels are one
-// contiguous range, tile-major order) and checks the order of what it blends;
-// a list the window cannot sort is resolved by the whole warp: a bitonic
-// network over (key, index) in registers. Lists longer than 256 (up to
-// HEXFC_MAX_LIST) are sorted by a whole block in shared memory. Keys are
-// unique within a pixel (depth, face, triangle), so the order is unique.
+// sorted. Layout: the lists of a warp's 32 pixels (tile-major pixel order)
+// share one region of the fragment arrays, starting at the offset of the
+// group's first pixel, stored chunk-major: for each chunk of 32 triangles of
+// the tile list, the group's fragments of that chunk, pixel by pixel, each
+// pixel's in list order. A pixel finds its fragments of a chunk from the
+// chunk's coverage masks: its own bit count, after those of the lower pixels
+// of its group. One thread per pixel walks the chunks and streams its list
+// front to back through a small sorted window in registers, checking the
+// order of what it blends; a list the window cannot sort is gathered and
+// resolved by a whole warp: a bitonic network over (key, index) in registers.
+// Lists longer than 256 (up to HEXFC_MAX_LIST) are sorted by a whole block in
+// shared memory. Keys are unique within a pixel (depth, face, triangle), so
+// the order is unique.
 // The warp-wide resolve composites as an ordered reduction of (colour,
 // transmittance) pairs, (C1,T1)(C2,T2) = (C1 + T1 C2, T1 T2), equal to the
 // sequential front-to-back blend.
@@ -168,7 +174,32 @@ __device__ __forceinline__ void tile_pixel(int64_t q, int tiles_x, int& x, int& 
     y = (int)(tile / tiles_x) * kTile + local / kTile;
 }
 
-struct WarpList {  // staging of one list per warp (debug gather)
+// The fragments of pixel q, in list order, found by one whole warp (lane i
+// reads the masks of pixel i of q's group): f(i, e) for list element i at
+// fragment index e. Elements past `limit` are skipped.
+template <class F>
+__device__ __forceinline__ void list_walk(const uint64_t* __restrict__ tile_off, const uint32_t* __restrict__ masks,
+                                          const uint64_t* __restrict__ off, uint32_t q, int lane, uint32_t limit,
+                                          F&& f)
+{
+    const uint32_t tile = q / kTilePix, l = q & 31u, g0 = q - l;
+    const uint64_t cb = tile_off[tile] / kChunk, ce = tile_off[tile + 1] / kChunk;
+    const uint32_t* mp = masks + cb * kTilePix + (g0 % kTilePix) + lane;
+    uint64_t e = off[g0];
+    uint32_t k = 0;
+    for (uint64_t c = cb; c < ce; ++c, mp += kTilePix) {
+        const uint32_t h = __popc(*mp);
+        const uint32_t before = __reduce_add_sync(kFull, (uint32_t)lane < l ? h : 0u);
+        const uint32_t total = __reduce_add_sync(kFull, h);
+        const uint32_t hl = __shfl_sync(kFull, h, l);
+        for (uint32_t t = lane; t < hl; t += 32)
+            if (k + t < limit) f(k + t, e + before + t);
+        k += hl;
+        e += total;
+    }
+}
+
+struct WarpList {  // staging of one list per warp (out-of-order lists, debug gather)
     uint64_t key[kWarpList];
     float4 rgba[kWarpList];
 };
@@ -178,15 +209,17 @@ __device__ __forceinline__ float4 finish(CT c, float bg0, float bg1, float bg2)
     return make_float4(c.r + c.t * bg0, c.g + c.t * bg1, c.b + c.t * bg2, 1.f - c.t);
 }
 
-// One thread per pixel (tile-major order, so a warp's 32 lists are one
-// contiguous range): the lane streams its list through a sorted window of KW
-// (key, colour) pairs in registers and blends the smallest pair each time the
-// window overflows, so a list whose elements sit at most KW - 1 places from
-// their sorted position comes out sorted. The blend checks that the keys it
-// consumes increase; a list that breaks that is queued for the warp-wide
-// resolve of k_composite_fix, or, if longer than 256, for the block-wide sort
-// of k_composite_long. KW (4 or 8) trades registers for fewer queued lists;
-// the result does not depend on it.
+// One block per tile, one thread per pixel: the thread walks the tile's
+// chunks (its group's fragments of each chunk follow those of the chunks
+// before; its own come after those of the lower pixels of the group) and
+// streams its list through a sorted window of KW (key, colour) pairs in
+// registers, blending the smallest pair each time the window overflows, so a
+// list whose elements sit at most KW - 1 places from their sorted position
+// comes out sorted. The blend checks that the keys it consumes increase; a
+// list that breaks that is queued for the warp-wide resolve of
+// k_composite_fix, or, if longer than 256, for the block-wide sort of
+// k_composite_long. KW (4 or 8) trades registers for fewer queued lists; the
+// result does not depend on it.
 struct KC {
     uint64_t k;
     float4 c;
@@ -210,75 +243,106 @@ __device__ __forceinline__ void blend_checked(CT& c, uint64_t& last, bool& ok, c
 template <int KW>
 __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ cnt,
                                                    const uint64_t* __restrict__ off,
+                                                   const uint64_t* __restrict__ tile_off,
+                                                   const uint32_t* __restrict__ masks,
                                                    const uint64_t* __restrict__ key,
-                                                   const float4* __restrict__ rgba, int64_t n_pix, int tiles_x,
-                                                   int W, int H, float bg0, float bg1, float bg2,
-                                                   float4* __restrict__ out, uint32_t* __restrict__ long_q,
+                                                   const float4* __restrict__ rgba, int tiles_x, int W, int H,
+                                                   float bg0, float bg1, float bg2, float4* __restrict__ out,
+                                                   uint32_t* __restrict__ long_q,
                                                    unsigned long long* __restrict__ long_cursor,
                                                    uint32_t* __restrict__ fix_q,
                                                    unsigned long long* __restrict__ fix_cursor)
 {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n_pix) return;
-    int x, y;
-    tile_pixel(q, tiles_x, x, y);
-    if (x >= W || y >= H) return;
+    const int tile = blockIdx.x, lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;
+    const uint64_t cb = tile_off[tile] / kChunk;
+    const uint32_t n_chunks = (uint32_t)(tile_off[tile + 1] / kChunk - cb);
+    uint64_t e0 = off[q - lane];   // the group's region
     const uint32_t n = cnt[q];
-    const uint64_t* kp = key + off[q];
-    const float4* rp = rgba + off[q];
     CT c{0.f, 0.f, 0.f, 1.f};
     bool ok = true;
     uint64_t last = 0;   // keys are > 0 unless depth and face id are both 0, which the check then flags
-    // the window w[0] <= ... <= w[KW-1], filled from the first KW elements
+    // the window w[0] <= ... <= w[KW-1]; empty places hold the largest key
     const uint64_t kPad = ~0ull;
     KC w[KW];
-    const uint32_t pre = n < (uint32_t)KW ? n : (uint32_t)KW;
 #pragma unroll
-    for (int k = 0; k < KW; ++k) w[k] = (uint32_t)k < pre ? KC{kp[k], rp[k]} : KC{kPad, {}};
+    for (int k = 0; k < KW; ++k) w[k] = KC{kPad, {}};
+    uint32_t seen = 0;
+    const uint32_t* mp = masks + cb * kTilePix + threadIdx.x;
+    uint32_t mk_next = n_chunks > 0 ? mp[0] : 0u;
+    for (uint32_t ch = 0; ch < n_chunks; ++ch) {
+        const uint32_t m = mk_next;
+        if (ch + 1 < n_chunks) mk_next = mp[(uint64_t)(ch + 1) * kTilePix];
+        const uint32_t h = __popc(m);
+        uint32_t incl = h;
 #pragma unroll
-    for (int pass = 0; pass < KW; ++pass)   // odd-even transposition sort
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint64_t e = e0 + incl - h;
+        e0 += __shfl_sync(kFull, incl, 31);
+        for (uint32_t t = 0; t < h; ++t) {
+            const KC f{key[e + t], rgba[e + t]};
+            const bool full = seen >= (uint32_t)KW;
+            ++seen;
+            if (full && f.k < w[0].k) {   // smaller than the whole window: blend it at once
+                blend_checked(c, last, ok, f);
+            } else {                      // blend the window's minimum (once full), insert f
+                if (full) {
+                    blend_checked(c, last, ok, w[0]);
 #pragma unroll
-        for (int k = pass & 1; k + 1 < KW; k += 2) kc_sort2(w[k], w[k + 1]);
-    for (uint32_t i = KW; i < n; ++i) {
-        const KC e{kp[i], rp[i]};
-        if (e.k < w[0].k) {        // smaller than the whole window: blend it at once
-            blend_checked(c, last, ok, e);
-        } else {                   // blend the window's minimum, insert e
-            blend_checked(c, last, ok, w[0]);
+                    for (int k = 0; k + 1 < KW; ++k) w[k] = w[k + 1];
+                }
+                w[KW - 1] = f;
 #pragma unroll
-            for (int k = 0; k + 1 < KW; ++k) w[k] = w[k + 1];
-            w[KW - 1] = e;
-#pragma unroll
-            for (int k = KW - 1; k > 0; --k) kc_sort2(w[k - 1], w[k]);
+                for (int k = KW - 1; k > 0; --k) kc_sort2(w[k - 1], w[k]);
+            }
         }
     }
+    const uint32_t pre = seen < (uint32_t)KW ? seen : (uint32_t)KW;
 #pragma unroll
     for (int k = 0; k < KW; ++k)
         if ((uint32_t)k < pre) blend_checked(c, last, ok, w[k]);
+    ok = ok && seen == n;
+    int x, y;
+    tile_pixel(q, tiles_x, x, y);
+    if (x >= W || y >= H) return;
     if (ok) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
     else if (n > (uint32_t)kWarpList) long_q[atomicAdd(long_cursor, 1ull)] = (uint32_t)q;
     else fix_q[atomicAdd(fix_cursor, 1ull)] = (uint32_t)q;
 }
 
-// Out-of-order lists (n <= 256): one warp each, sorted in registers.
+// Out-of-order lists (n <= 256): one warp each, gathered into shared memory
+// and sorted in registers.
 __global__ void __launch_bounds__(256) k_composite_fix(const uint32_t* __restrict__ cnt,
                                                        const uint64_t* __restrict__ off,
+                                                       const uint64_t* __restrict__ tile_off,
+                                                       const uint32_t* __restrict__ masks,
                                                        const uint64_t* __restrict__ key,
                                                        const float4* __restrict__ rgba, int tiles_x, int W,
                                                        float bg0, float bg1, float bg2, float4* __restrict__ out,
                                                        const uint32_t* __restrict__ fix_q,
                                                        const unsigned long long* __restrict__ fix_cursor)
 {
+    extern __shared__ __align__(16) unsigned char smem[];
+    WarpList& b = reinterpret_cast<WarpList*>(smem)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const uint64_t n_fix = *fix_cursor;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < n_fix; w += warps) {
         const uint32_t q = fix_q[w];
+        const uint32_t n = min(cnt[q], (uint32_t)kWarpList);
+        list_walk(tile_off, masks, off, q, lane, n, [&](uint32_t i, uint64_t e) {
+            b.key[i] = key[e];
+            b.rgba[i] = rgba[e];
+        });
+        __syncwarp();
         int x, y;
         tile_pixel(q, tiles_x, x, y);
-        const uint64_t b = off[q];
-        CT c = warp_resolve(key + b, rgba + b, cnt[q], lane, nullptr, nullptr);
+        CT c = warp_resolve(b.key, b.rgba, n, lane, nullptr, nullptr);
         if (lane == 0) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
+        __syncwarp();   // the staging is reused by the warp's next list
     }
 }
 
@@ -307,12 +371,22 @@ __device__ void block_sort(uint64_t* s_k, uint32_t* s_v, uint32_t n, uint32_t np
         }
 }
 
-__device__ CT block_composite(const uint64_t* __restrict__ key, const float4* __restrict__ rgba, uint64_t base,
-                              uint32_t n, uint64_t* s_k, uint32_t* s_v, uint64_t* out_key, float4* out_rgba)
+// List of pixel q (n <= HEXFC_MAX_LIST elements): the first warp finds the
+// elements' fragment indices (relative to the group's region) in s_e, then the
+// block sorts (key, element) pairs and the first warp composites.
+__device__ CT block_composite(const uint64_t* __restrict__ tile_off, const uint32_t* __restrict__ masks,
+                              const uint64_t* __restrict__ off, const uint64_t* __restrict__ key,
+                              const float4* __restrict__ rgba, uint32_t q, uint32_t n, uint64_t* s_k, uint32_t* s_v,
+                              uint32_t* s_e, uint64_t* out_key, float4* out_rgba)
 {
     uint32_t np2 = 32;
     while (np2 < n) np2 <<= 1;
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) { s_k[i] = key[base + i]; s_v[i] = i; }
+    const uint64_t base = off[q - (q & 31u)];
+    if (threadIdx.x < 32)
+        list_walk(tile_off, masks, off, q, (int)threadIdx.x, n,
+                  [&](uint32_t i, uint64_t e) { s_e[i] = (uint32_t)(e - base); });
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) { s_k[i] = key[base + s_e[i]]; s_v[i] = i; }
     __syncthreads();
     block_sort(s_k, s_v, n, np2);
     // first warp: each lane composites a contiguous run of ranks, then an ordered reduction
@@ -323,7 +397,7 @@ __device__ CT block_composite(const uint64_t* __restrict__ key, const float4* __
         for (uint32_t j = 0; j < per; ++j) {
             uint32_t rank = lane * per + j;
             if (rank < n) {
-                float4 f = rgba[base + s_v[rank]];
+                float4 f = rgba[base + s_e[s_v[rank]]];
                 c = ct_over(c, CT{f.x, f.y, f.z, 1.f - f.w});
                 if (out_key) { out_key[rank] = s_k[rank]; out_rgba[rank] = f; }
             }
@@ -338,6 +412,8 @@ __device__ CT block_composite(const uint64_t* __restrict__ key, const float4* __
 // HEXFC_MAX_LIST is never drawn; the frame reports it as an overflow.
 __global__ void __launch_bounds__(1024) k_composite_long(const uint32_t* __restrict__ cnt,
                                                          const uint64_t* __restrict__ off,
+                                                         const uint64_t* __restrict__ tile_off,
+                                                         const uint32_t* __restrict__ masks,
                                                          const uint64_t* __restrict__ key,
                                                          const float4* __restrict__ rgba,
                                                          const uint32_t* __restrict__ long_q,
@@ -348,6 +424,7 @@ __global__ void __launch_bounds__(1024) k_composite_long(const uint32_t* __restr
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* s_k = reinterpret_cast<uint64_t*>(smem);
     uint32_t* s_v = reinterpret_cast<uint32_t*>(s_k + HEXFC_MAX_LIST);
+    uint32_t* s_e = s_v + HEXFC_MAX_LIST;
     const unsigned long long total = *n_long;
     for (unsigned long long i = blockIdx.x; i < total; i += gridDim.x) {
         const uint32_t q = long_q[i];
@@ -355,7 +432,7 @@ __global__ void __launch_bounds__(1024) k_composite_long(const uint32_t* __restr
         if (n > (uint32_t)HEXFC_MAX_LIST) continue;
         int x, y;
         tile_pixel(q, tiles_x, x, y);
-        CT c = block_composite(key, rgba, off[q], n, s_k, s_v, nullptr, nullptr);
+        CT c = block_composite(tile_off, masks, off, key, rgba, q, n, s_k, s_v, s_e, nullptr, nullptr);
         if (threadIdx.x == 0) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
         __syncthreads();   // the shared arrays are reused by the next list
     }
@@ -366,6 +443,8 @@ __global__ void __launch_bounds__(1024) k_composite_long(const uint32_t* __restr
 // Sorted lists of requested pixels written at dst_off[i], by the same resolve
 // routines as the composite (one warp per pixel for n <= 256).
 __global__ void __launch_bounds__(256) k_debug_short(const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ off,
+                                                     const uint64_t* __restrict__ tile_off,
+                                                     const uint32_t* __restrict__ masks,
                                                      const uint64_t* __restrict__ key,
                                                      const float4* __restrict__ rgba, const int32_t* __restrict__ px,
                                                      const int32_t* __restrict__ py, int64_t n_req,
@@ -381,17 +460,17 @@ __global__ void __launch_bounds__(256) k_debug_short(const uint32_t* __restrict_
     int64_t q = ((int64_t)(y / kTile) * tiles_x + x / kTile) * kTilePix + (y % kTile) * kTile + (x % kTile);
     uint32_t n = cnt[q];
     if (n == 0 || n > (uint32_t)kWarpList) return;
-    for (uint32_t e = lane; e < n; e += 32) {
-        cp_async8(&b.key[e], key + off[q] + e);
-        cp_async16(&b.rgba[e], rgba + off[q] + e);
-    }
-    cp_async_commit();
-    cp_async_wait<0>();
+    list_walk(tile_off, masks, off, (uint32_t)q, lane, n, [&](uint32_t k, uint64_t e) {
+        b.key[k] = key[e];
+        b.rgba[k] = rgba[e];
+    });
     __syncwarp();
     (void)warp_resolve(b.key, b.rgba, n, lane, out_key + dst_off[i], out_rgba + dst_off[i]);
 }
 
 __global__ void __launch_bounds__(1024) k_debug_long(const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ off,
+                                                     const uint64_t* __restrict__ tile_off,
+                                                     const uint32_t* __restrict__ masks,
                                                      const uint64_t* __restrict__ key, const float4* __restrict__ rgba,
                                                      const int32_t* __restrict__ px, const int32_t* __restrict__ py,
                                                      const uint64_t* __restrict__ dst_off, int tiles_x,
@@ -400,12 +479,14 @@ __global__ void __launch_bounds__(1024) k_debug_long(const uint32_t* __restrict_
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* s_k = reinterpret_cast<uint64_t*>(smem);
     uint32_t* s_v = reinterpret_cast<uint32_t*>(s_k + HEXFC_MAX_LIST);
+    uint32_t* s_e = s_v + HEXFC_MAX_LIST;
     int64_t i = blockIdx.x;
     int x = px[i], y = py[i];
     int64_t q = ((int64_t)(y / kTile) * tiles_x + x / kTile) * kTilePix + (y % kTile) * kTile + (x % kTile);
     uint32_t n = cnt[q];
-    if (n <= (uint32_t)kWarpList) return;
-    (void)block_composite(key, rgba, off[q], n, s_k, s_v, out_key + dst_off[i], out_rgba + dst_off[i]);
+    if (n <= (uint32_t)kWarpList || n > (uint32_t)HEXFC_MAX_LIST) return;
+    (void)block_composite(tile_off, masks, off, key, rgba, (uint32_t)q, n, s_k, s_v, s_e, out_key + dst_off[i],
+                          out_rgba + dst_off[i]);
 }
 
 __global__ void k_debug_counts(const uint32_t* __restrict__ cnt, const int32_t* __restrict__ px,
@@ -419,7 +500,8 @@ __global__ void k_debug_counts(const uint32_t* __restrict__ cnt, const int32_t* 
     out[i] = cnt[q];
 }
 
-constexpr size_t kLongSmem = (size_t)HEXFC_MAX_LIST * (sizeof(uint64_t) + sizeof(uint32_t));
+constexpr size_t kLongSmem = (size_t)HEXFC_MAX_LIST * (sizeof(uint64_t) + 2 * sizeof(uint32_t));
+constexpr size_t kFixSmem = 8 * sizeof(WarpList);
 constexpr unsigned kFixBlocks = 4 * 152;   // persistent: warps stride over the queue of out-of-order lists
 constexpr unsigned kLongGridMax = 2 * 152;  // persistent: blocks stride over the queue of long lists
 
@@ -432,26 +514,32 @@ cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, 
     const int64_t n_pix = (int64_t)tiles_x * tiles_y * kTilePix;
     unsigned long long* long_cursor = reinterpret_cast<unsigned long long*>(fb.scal + 3);
     unsigned long long* fix_cursor = reinterpret_cast<unsigned long long*>(fb.scal + 4);
-    const unsigned grid = (unsigned)((n_pix + 255) / 256);
+    const unsigned grid = (unsigned)(n_pix / kTilePix);
     if (window == 8)
-        k_composite<8><<<grid, 256, 0, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, n_pix, tiles_x, W, H, sp.bg[0], sp.bg[1],
-                                            sp.bg[2], o4, fb.long_q, long_cursor, fb.fix_q, fix_cursor);
+        k_composite<8><<<grid, 256, 0, s>>>(fb.cnt, fb.off, fb.tile_off, fb.masks, fb.key, fb.rgba, tiles_x, W, H,
+                                            sp.bg[0], sp.bg[1], sp.bg[2], o4, fb.long_q, long_cursor, fb.fix_q,
+                                            fix_cursor);
     else
-        k_composite<4><<<grid, 256, 0, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, n_pix, tiles_x, W, H, sp.bg[0], sp.bg[1],
-                                            sp.bg[2], o4, fb.long_q, long_cursor, fb.fix_q, fix_cursor);
-    k_composite_fix<<<kFixBlocks, 256, 0, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, tiles_x, W, sp.bg[0], sp.bg[1],
-                                               sp.bg[2], o4, fb.fix_q, fix_cursor);
+        k_composite<4><<<grid, 256, 0, s>>>(fb.cnt, fb.off, fb.tile_off, fb.masks, fb.key, fb.rgba, tiles_x, W, H,
+                                            sp.bg[0], sp.bg[1], sp.bg[2], o4, fb.long_q, long_cursor, fb.fix_q,
+                                            fix_cursor);
+    k_composite_fix<<<kFixBlocks, 256, kFixSmem, s>>>(fb.cnt, fb.off, fb.tile_off, fb.masks, fb.key, fb.rgba,
+                                                      tiles_x, W, sp.bg[0], sp.bg[1], sp.bg[2], o4, fb.fix_q,
+                                                      fix_cursor);
     if (n_long > 0) {   // n_long: the number of long lists if known, else an upper bound on the useful grid
         const unsigned grid = n_long < kLongGridMax ? n_long : kLongGridMax;
-        k_composite_long<<<grid, 1024, kLongSmem, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, fb.long_q, long_cursor,
-                                                       tiles_x, W, sp.bg[0], sp.bg[1], sp.bg[2], o4);
+        k_composite_long<<<grid, 1024, kLongSmem, s>>>(fb.cnt, fb.off, fb.tile_off, fb.masks, fb.key, fb.rgba,
+                                                       fb.long_q, long_cursor, tiles_x, W, sp.bg[0], sp.bg[1],
+                                                       sp.bg[2], o4);
     }
     return cudaGetLastError();
 }
 
 cudaError_t prepare_composite_kernels()
 {
-    return cudaFuncSetAttribute(k_composite_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_composite_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSmem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_composite_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixSmem);
 }
 
 cudaError_t launch_debug_gather(FrameBufs& fb, const int32_t* d_px, const int32_t* d_py, int64_t n,
@@ -467,11 +555,12 @@ cudaError_t launch_debug_gather(FrameBufs& fb, const int32_t* d_px, const int32_
     }
     const size_t dsm = 8 * sizeof(WarpList);
     cudaFuncSetAttribute(k_debug_short, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
-    k_debug_short<<<(unsigned)((n * 32 + 255) / 256), 256, dsm, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, d_px, d_py, n,
-                                                                    d_dst_off, tiles_x, d_keys, d_rgba);
+    k_debug_short<<<(unsigned)((n * 32 + 255) / 256), 256, dsm, s>>>(fb.cnt, fb.off, fb.tile_off, fb.masks, fb.key,
+                                                                    fb.rgba, d_px, d_py, n, d_dst_off, tiles_x,
+                                                                    d_keys, d_rgba);
     cudaFuncSetAttribute(k_debug_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSmem);
-    k_debug_long<<<(unsigned)n, 1024, kLongSmem, s>>>(fb.cnt, fb.off, fb.key, fb.rgba, d_px, d_py, d_dst_off,
-                                                      tiles_x, d_keys, d_rgba);
+    k_debug_long<<<(unsigned)n, 1024, kLongSmem, s>>>(fb.cnt, fb.off, fb.tile_off, fb.masks, fb.key, fb.rgba, d_px,
+                                                      d_py, d_dst_off, tiles_x, d_keys, d_rgba);
     return cudaGetLastError();
 }
 

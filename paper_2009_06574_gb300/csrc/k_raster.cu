@@ -382,9 +382,9 @@ __device__ __forceinline__ bool cover_at(const CovSoA& c, int j, int rx, int ry,
 // chunk of 32 triangles of the tile's (depth-ordered) list into a ring of
 // kRing slots in shared memory, while the eight consumer warps shade the
 // covered samples of earlier chunks. Slots are handed over with mbarriers
-// (full: the 32 producer lanes arrive; empty: one consumer thread arrives once
-// no queued sample refers to the slot), so the producer runs up to kRing
-// chunks ahead. Every wait is bounded; a wait that runs out sets an error bit
+// (full: the 32 producer lanes arrive; empty: lane 0 of each consumer warp
+// arrives once no sample in its warp's queue refers to the slot), so the
+// producer runs up to kRing chunks ahead. Every wait is bounded; a wait that runs out sets an error bit
 // and ends the kernel's loops.
 
 constexpr int kRing = 3;
@@ -397,7 +397,7 @@ __device__ __forceinline__ void pipe_init(uint64_t* full, uint64_t* empty)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kRing; ++s) {
             mbar_init(&full[s], 32);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);   // lane 0 of each consumer warp
         }
         mbar_init_fence();
     }
@@ -659,40 +659,24 @@ struct FillSlot {
     ShadeSoA sh;
 };
 
-// Block queue of covered samples: entry = j | pixel << 5 | ring slot << 13 | rank << 15.
-constexpr int kQCap = 2048;            // entries (a power of two)
-constexpr int kQWin = 896;             // entries queued per window: leftovers + 2 windows fit in kQCap
-constexpr uint32_t kNoRank = 0x1FFFFu;   // rank of a sample beyond its list (never written)
-static_assert(kTilePix + 2 * kQWin <= kQCap, "queue windows");
+// Warp queues of covered samples: entry = j | pixel << 5 | ring slot << 13 | counted << 15.
+constexpr int kWQ = 256;               // entries per consumer warp (a power of two)
+constexpr int kWQWin = kWQ - 32;       // entries queued per window: fewer than 32 leftovers + a window fit
+constexpr uint32_t kCounted = 1u << 15;  // the count pass sized the sample's list for it
 static_assert(kRing <= 4, "two bits of ring slot");
 
 constexpr size_t kRawOff = (kRing * sizeof(FillSlot) + 127) & ~(size_t)127;   // face records: 128-aligned
 
 __host__ __device__ constexpr size_t fill_smem_bytes()
 {
-    return kRawOff + 2 * kChunk * sizeof(RawFace) + (size_t)kQCap * sizeof(uint32_t);
+    return kRawOff + 2 * kChunk * sizeof(RawFace) + (size_t)kConsumerWarps * kWQ * sizeof(uint32_t);
 }
-
-// Barrier 1 among the consumer warps only (the producer never joins it); the
-// non-aligned forms, since lanes may arrive apart. True on every consumer if
-// `p` holds on any of them.
-__device__ __forceinline__ bool consumers_sync_or(bool p)
-{
-    int r;
-    asm volatile(
-        "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n barrier.red.or.pred b, 1, %2, a;\n selp.s32 %0, 1, 0, b;\n}\n"
-        : "=r"(r)
-        : "r"((int)p), "n"(kTilePix)
-        : "memory");
-    return r != 0;
-}
-__device__ __forceinline__ void consumers_sync() { asm volatile("barrier.sync 1, %0;\n" ::"n"(kTilePix) : "memory"); }
 
 // The fill pipeline of one tile block: s_base / s_len hold the offsets and
 // lengths of the tile's 256 lists, the ring barriers are initialised, and
 // `smem` is the dynamic shared memory (fill_smem_bytes()).
 __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s_base, const uint32_t* s_len,
-                                          uint32_t* s_wsum, uint64_t* s_full, uint64_t* s_empty,
+                                          uint64_t* s_full, uint64_t* s_empty,
                                           const uint32_t* __restrict__ bins, const uint32_t* __restrict__ masks,
                                           const FaceFrame* __restrict__ fframe,
                                           const FaceStatic* __restrict__ fstat, uint64_t beg, uint32_t n_chunks,
@@ -702,7 +686,6 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
 {
     FillSlot* s_ring = reinterpret_cast<FillSlot*>(smem);                                    // [kRing]
     RawFace* s_raw = reinterpret_cast<RawFace*>(smem + kRawOff);                            // [2][kChunk]
-    uint32_t* s_q = reinterpret_cast<uint32_t*>(s_raw + 2 * kChunk);                        // [kQCap]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == kConsumerWarps) {  // producer
         uint32_t f2t_c = n_chunks > 0 ? bins[beg + lane] : kPadBin;
@@ -738,18 +721,27 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
         cp_async_wait<0>();
         return;
     }
-    // consumers: thread p owns pixel p of the tile for the queue; any thread shades any entry
+    // consumers: warp w owns pixels 32w .. 32w + 31 and a private queue; each
+    // warp goes through the chunks on its own (no block barrier), so warps
+    // may be up to kRing chunks apart
     const int p = threadIdx.x;
+    uint32_t* s_q = reinterpret_cast<uint32_t*>(s_raw + 2 * kChunk) + warp * kWQ;   // [kWQ]
     uint32_t k_run = 0;
-    bool bad = false;
-    // Queue positions are absolute counts (modulo kQCap): entries [head, tail) are
-    // queued. Only whole rounds of kTilePix entries are shaded; the rest waits
-    // for the next chunk unless it would keep an older chunk's slot (then it is
+    bool bad = false, stalled = false;
+    // The warp's 32 lists are one region of the fragment arrays, from the
+    // offset of its first pixel; the region holds them chunk-major (fragment
+    // e of the warp's queue at region start + e), so every shading round
+    // writes 32 consecutive records.
+    const uint64_t w_beg = s_base[warp * 32];
+    const uint64_t w_end = w_beg + __reduce_add_sync(0xffffffffu, s_len[p]);
+    // Queue positions are absolute counts (modulo kWQ): entries [head, tail) are
+    // queued. Only whole rounds of 32 entries are shaded; the rest waits for
+    // the next chunk unless it would keep an older chunk's slot (then it is
     // shaded as a partial round), so at most the newest chunk's slot is held.
     uint32_t head = 0, tail = 0, released = 0;
-    auto shade_entry = [&](uint32_t qe) {
-        const uint32_t kk = qe >> 15;
-        if (kk == kNoRank) return;
+    auto shade_entry = [&](uint32_t qe, uint32_t e) {
+        const uint64_t o = w_beg + e;
+        if (!(qe & kCounted) || o >= w_end) return;
         const int j = (int)(qe & 31u);
         const uint32_t pl = (qe >> 5) & 255u;
         const FillSlot& S = s_ring[(qe >> 13) & 3u];
@@ -764,7 +756,6 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
         const uint32_t z = sample_depth_lam(S.sh.z[0][j], S.sh.z[1][j], S.sh.z[2][j], l1, l2, S.sh.area[j], lam1,
                                             lam2, S.sh.dz[0][j], S.sh.dz[1][j], bad);
         const float4 col = shade_fragment(S.sh, j, lam1, lam2, px0 + lx, py0 + ly, sp);
-        const uint64_t o = s_base[pl] + kk;
         key[o] = ((uint64_t)z << 32) | (uint64_t)S.sh.f2t[j];
         rgba[o] = col;
     };
@@ -776,8 +767,19 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
         const uint32_t mk = mk_a;
         mk_a = mk_b;
         if (c + 2 < n_chunks) mk_b = masks[(beg / kChunk + c + 2) * kTilePix + p];
-        const bool ok = mbar_wait(&s_full[s], (c / kRing) & 1);
-        // block-wide exclusive scan of the hit counts (warp scan + the warp totals)
+        // every entry of the chunks before c - 1 (and of c - 1 if nothing is
+        // left over) has been shaded by the whole warp: release their slots
+        __syncwarp();
+        const uint32_t rel_to = head == tail ? c : c - 1;
+        if (lane == 0)
+            for (uint32_t r = released; r < rel_to; ++r) mbar_arrive(&s_empty[r % kRing]);
+        released = max(released, rel_to);
+        if (!__all_sync(0xffffffffu, mbar_wait(&s_full[s], (c / kRing) & 1))) {
+            if (lane == 0) atomicOr(err, kErrWait);
+            stalled = true;
+            break;
+        }
+        // warp exclusive scan of the hit counts
         const uint32_t h = __popc(mk);
         uint32_t incl = h;
 #pragma unroll
@@ -785,62 +787,47 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        if (lane == 31) s_wsum[warp] = incl;
-        if (consumers_sync_or(!ok)) {   // every consumer leaves together
-            if (p == 0) atomicOr(err, kErrWait);
-            break;
-        }
-        // every entry queued before this chunk has been shaded by all threads,
-        // except leftovers of chunk c - 1: release the slots of the chunks before
-        const uint32_t rel_to = head == tail ? c : c - 1;
-        if (p == 0)
-            for (uint32_t r = released; r < rel_to; ++r) mbar_arrive(&s_empty[r % kRing]);
-        released = max(released, rel_to);
-        uint32_t r0 = incl - h, total = 0;
-#pragma unroll
-        for (int w = 0; w < kConsumerWarps; ++w) {
-            const uint32_t v = s_wsum[w];
-            r0 += w < warp ? v : 0u;
-            total += v;
-        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         const bool fits = k_run + h <= s_len[p];   // the count pass sized this list
         bad = bad || !fits;
         const uint32_t chunk_start = tail;
-        for (uint32_t w0 = 0; w0 < total; w0 += kQWin) {
-            uint32_t m2 = mk, r = r0, t = 0;
+        const uint32_t tag = ((uint32_t)p << 5) | ((uint32_t)s << 13) | (fits ? kCounted : 0u);
+        for (uint32_t w0 = 0; w0 < total; w0 += kWQWin) {
+            uint32_t m2 = mk, r = incl - h;
             while (m2) {
                 const uint32_t j = __ffs(m2) - 1;
                 m2 &= m2 - 1;
-                if (r >= w0 && r < w0 + kQWin)
-                    s_q[(tail + r - w0) & (kQCap - 1)] =
-                        j | ((uint32_t)p << 5) | ((uint32_t)s << 13) | ((fits ? k_run + t : kNoRank) << 15);
+                if (r >= w0 && r < w0 + kWQWin) s_q[(tail + r - w0) & (kWQ - 1)] = j | tag;
                 ++r;
-                ++t;
             }
-            consumers_sync();   // the window's entries are queued
-            tail += min((uint32_t)kQWin, total - w0);
-            const uint32_t rounds = (tail - head) / kTilePix;
-            for (uint32_t i = 0; i < rounds; ++i) shade_entry(s_q[(head + i * kTilePix + p) & (kQCap - 1)]);
-            head += rounds * kTilePix;
+            __syncwarp();   // the window's entries are queued
+            tail += min((uint32_t)kWQWin, total - w0);
+            const uint32_t rounds = (tail - head) / 32;
+            for (uint32_t i = 0; i < rounds; ++i) {
+                const uint32_t e = head + i * 32 + lane;
+                shade_entry(s_q[e & (kWQ - 1)], e);
+            }
+            head += rounds * 32;
+            __syncwarp();   // shaded entries are read before the next window overwrites them
         }
         if (head < chunk_start) {   // leftovers of an older chunk: shade them all now
-            if (p < tail - head) shade_entry(s_q[(head + p) & (kQCap - 1)]);
+            if (lane < tail - head) shade_entry(s_q[(head + lane) & (kWQ - 1)], head + lane);
             head = tail;
         }
         k_run += h;
     }
     // the last leftovers (the producer is done; no slot is released any more)
-    if (head < tail && p < tail - head) shade_entry(s_q[(head + p) & (kQCap - 1)]);
+    if (!stalled && lane < tail - head) shade_entry(s_q[(head + lane) & (kWQ - 1)], head + lane);
     if (bad) atomicOr(err, 1ull);
 }
 
 // Per tile: the coverage masks of the count pass give, chunk by chunk, each
-// pixel's covered triangles; the consumers compact the chunk's covered samples
-// into one queue (pixel-major, in list order) and shade it 256 samples at a
-// time, so that every lane has work, and each fragment is written at its
-// pixel's offset plus its rank in the pixel's list (the rank the count pass
-// sized). The producer fetches the face records of chunk c+1 with cp.async
-// while it sets up chunk c.
+// pixel's covered triangles; each consumer warp compacts its 32 pixels'
+// covered samples into its queue (pixel-major, in list order) and shades it
+// 32 samples at a time, so that every lane has work, writing the fragments in
+// queue order into the warp's region (the 32 lists the count pass sized):
+// chunk by chunk, pixel by pixel within a chunk. The producer fetches the face
+// records of chunk c+1 with cp.async while it sets up chunk c.
 __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __restrict__ tile_off,
                                                           const uint32_t* __restrict__ bins,
                                                           const uint32_t* __restrict__ masks,
@@ -855,7 +842,6 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __rest
     extern __shared__ __align__(128) unsigned char fill_smem[];
     __shared__ uint64_t s_base[kTilePix];
     __shared__ uint32_t s_len[kTilePix];
-    __shared__ uint32_t s_wsum[kConsumerWarps];
     __shared__ __align__(8) uint64_t s_full[kRing], s_empty[kRing];
     const int tile = (int)order[blockIdx.x];
     const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
@@ -867,7 +853,7 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __rest
         s_len[threadIdx.x] = cnt[q];
     }
     pipe_init(s_full, s_empty);
-    fill_tile(fill_smem, s_base, s_len, s_wsum, s_full, s_empty, bins, masks, fframe, fstat, beg, n_chunks, px0, py0,
+    fill_tile(fill_smem, s_base, s_len, s_full, s_empty, bins, masks, fframe, fstat, beg, n_chunks, px0, py0,
               W, H, sp, key, rgba, err);
 }
 
@@ -959,7 +945,7 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_count_fill(const uint64_t* 
     }
     if (!fits) return;
     pipe_init(s_full, s_empty);   // also orders the scan's shared reads before the fill reuses them
-    fill_tile(cf_smem, s_base, s_len, s_wsum, s_full, s_empty, bins, masks, fframe, fstat, beg, n_chunks, px0, py0,
+    fill_tile(cf_smem, s_base, s_len, s_full, s_empty, bins, masks, fframe, fstat, beg, n_chunks, px0, py0,
               W, H, sp, key, rgba, scal + 5);
 }
 
