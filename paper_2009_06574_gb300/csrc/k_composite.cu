@@ -282,12 +282,20 @@ __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ 
         }
         const uint64_t e = e0 + incl - h;
         e0 += __shfl_sync(kFull, incl, 31);
+        KC nx{};   // the next element is loaded while this one is placed
+        if (h > 0) nx = KC{key[e], rgba[e]};
         for (uint32_t t = 0; t < h; ++t) {
-            const KC f{key[e + t], rgba[e + t]};
+            const KC f = nx;
+            if (t + 1 < h) nx = KC{key[e + t + 1], rgba[e + t + 1]};
             const bool full = seen >= (uint32_t)KW;
             ++seen;
             if (full && f.k < w[0].k) {   // smaller than the whole window: blend it at once
                 blend_checked(c, last, ok, f);
+            } else if (full && f.k > w[KW - 1].k) {   // in order (the common case): append
+                blend_checked(c, last, ok, w[0]);
+#pragma unroll
+                for (int k = 0; k + 1 < KW; ++k) w[k] = w[k + 1];
+                w[KW - 1] = f;
             } else {                      // blend the window's minimum (once full), insert f
                 if (full) {
                     blend_checked(c, last, ok, w[0]);
