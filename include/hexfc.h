@@ -267,7 +267,8 @@ hexfc_status hexfc_set_view(hexfc_ctx* ctx, const hexfc_view* view);
 /* Set the focus lens (radius > 0). Errors: ARG. */
 hexfc_status hexfc_set_lens(hexfc_ctx* ctx, const hexfc_lens* lens);
 
-/* Set the style constants. Errors: ARG (w_base < 0, tf_hi == tf_lo, g_min > g_max, desat outside [0, 1]). */
+/* Set the style constants. Errors: ARG (w_base < 0, tf_hi == tf_lo, g_min < 0, g_min > g_max,
+ * halo_scale < 0, desat outside [0, 1]). */
 hexfc_status hexfc_set_style(hexfc_ctx* ctx, const hexfc_style* style);
 
 /*

@@ -259,7 +259,8 @@ bool valid_lens(const hexfc_lens* l)
 
 bool valid_style(const hexfc_style* s)
 {
-    if (!(s->w_base >= 0.f) || s->tf_hi == s->tf_lo || !(s->g_min <= s->g_max)) return false;
+    if (!(s->w_base >= 0.f) || s->tf_hi == s->tf_lo || !(s->g_min >= 0.f) || !(s->g_min <= s->g_max)) return false;
+    if (!(s->halo_scale >= 0.f)) return false;
     return s->desat >= 0.f && s->desat <= 1.f;
 }
 

@@ -604,7 +604,7 @@ __device__ __forceinline__ void rec_fetch(RawFace& r, const FaceFrame* __restric
     }
 }
 
-__device__ __forceinline__ void stage_shade(const RawFace& rf, uint32_t f2t, const TriGeom& t, bool ortho,
+__device__ __forceinline__ void stage_shade(const RawFace& rf, uint32_t f2t, const TriGeom& t, const ShadeParams& sp,
                                             ShadeSoA& S, int j)
 {
     const FaceFrame& r = rf.fr;
@@ -623,6 +623,7 @@ __device__ __forceinline__ void stage_shade(const RawFace& rf, uint32_t f2t, con
     const float ee[4] = {r.ed.x, r.ed.y, r.ed.z, r.ed.w}, ii[4] = {fs.imp.x, fs.imp.y, fs.imp.z, fs.imp.w};
     const float xx[4] = {fs.px.x, fs.px.y, fs.px.z, fs.px.w}, yy[4] = {fs.py.x, fs.py.y, fs.py.z, fs.py.w};
     const float ww[4] = {fs.pz.x, fs.pz.y, fs.pz.z, fs.pz.w};
+    const bool ortho = sp.ortho != 0;
     float q[3], a[3], P[3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -631,9 +632,10 @@ __device__ __forceinline__ void stage_shade(const RawFace& rf, uint32_t f2t, con
         S.z[k][j] = c == 0 ? zz[0] : c == 1 ? zz[1] : c == 2 ? zz[2] : zz[3];
         q[k] = ortho ? 1.f : 1.f / (c == 0 ? ee[0] : c == 1 ? ee[1] : c == 2 ? ee[2] : ee[3]);
         a[k] = (c == 0 ? ii[0] : c == 1 ? ii[1] : c == 2 ? ii[2] : ii[3]) * q[k];
-        P[k][0] = (c == 0 ? xx[0] : c == 1 ? xx[1] : c == 2 ? xx[2] : xx[3]) * q[k];
-        P[k][1] = (c == 0 ? yy[0] : c == 1 ? yy[1] : c == 2 ? yy[2] : yy[3]) * q[k];
-        P[k][2] = (c == 0 ? ww[0] : c == 1 ? ww[1] : c == 2 ? ww[2] : ww[3]) * q[k];
+        // offset from the sphere lens centre (unused by the screen lens)
+        P[k][0] = ((c == 0 ? xx[0] : c == 1 ? xx[1] : c == 2 ? xx[2] : xx[3]) - sp.lens_c[0]) * q[k];
+        P[k][1] = ((c == 0 ? yy[0] : c == 1 ? yy[1] : c == 2 ? yy[2] : yy[3]) - sp.lens_c[1]) * q[k];
+        P[k][2] = ((c == 0 ? ww[0] : c == 1 ? ww[1] : c == 2 ? ww[2] : ww[3]) - sp.lens_c[2]) * q[k];
     }
     S.dz[0][j] = (float)(int32_t)(S.z[1][j] - S.z[0][j]);
     S.dz[1][j] = (float)(int32_t)(S.z[2][j] - S.z[0][j]);
@@ -710,7 +712,7 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
                 const RawFace& r = s_raw[(c & 1) * kChunk + lane];
                 TriGeom t;
                 stage_cov(r.fr.X, r.fr.Y, f2t_c, W, H, px0, py0, S.c, lane, t);
-                if (S.c.box[lane] != 0) stage_shade(r, f2t_c, t, sp.ortho != 0, S.sh, lane);
+                if (S.c.box[lane] != 0) stage_shade(r, f2t_c, t, sp, S.sh, lane);
             } else {
                 S.c.box[lane] = 0;
             }

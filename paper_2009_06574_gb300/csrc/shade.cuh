@@ -23,14 +23,21 @@ struct ShadeSoA {
     float dz[2][kChunk];                    // z[1] - z[0], z[2] - z[0] (exact: |d| < 2^24)
     float q0[kChunk], dq[2][kChunk];        // 1 / eye depth
     float a0[kChunk], da[2][kChunk];        // importance / eye depth
-    float p0[3][kChunk], dp[2][3][kChunk];  // world position / eye depth
+    float p0[3][kChunk], dp[2][3][kChunk];  // (world position - sphere lens centre) / eye depth
     int64_t area[kChunk];                   // twice the area (16.8 squared)
     float inv_area[kChunk];
     uint32_t f2t[kChunk];
     uint32_t masks[kChunk];                 // bits 0-3 focus-visible, 4-7 context-visible face edges
 };
 
-__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+// Square root of x >= 0 (0 at 0), the hardware approximation (a few units in
+// the last place).
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // Eqs. 1-4 for one fragment of triangle j at pixel (px, py); lam1, lam2 are
 // the screen-space barycentric weights of vertices 1 and 2. Returns the
@@ -46,16 +53,16 @@ __device__ __forceinline__ float4 shade_fragment(const ShadeSoA& t, int j, float
     float dist;
     if (sp.lens_mode == HEXFC_LENS_SCREEN) {
         const float dx = ((float)px + 0.5f) - sp.lens_c[0], dy = ((float)py + 0.5f) - sp.lens_c[1];
-        dist = fast_sqrt(dx * dx + dy * dy) * sp.lens_inv_r;
+        dist = sqrt_approx(dx * dx + dy * dy) * sp.lens_inv_r;
     } else {
-        const float Px = fmaf(lam2, t.dp[1][0][j], fmaf(lam1, t.dp[0][0][j], t.p0[0][j])) * iQ;
-        const float Py = fmaf(lam2, t.dp[1][1][j], fmaf(lam1, t.dp[0][1][j], t.p0[1][j])) * iQ;
-        const float Pz = fmaf(lam2, t.dp[1][2][j], fmaf(lam1, t.dp[0][2][j], t.p0[2][j])) * iQ;
-        const float dx = Px - sp.lens_c[0], dy = Py - sp.lens_c[1], dz = Pz - sp.lens_c[2];
-        dist = fast_sqrt(dx * dx + dy * dy + dz * dz) * sp.lens_inv_r;
+        // the interpolated offset from the centre, P - C = D / Q (D affine in lam)
+        const float Dx = fmaf(lam2, t.dp[1][0][j], fmaf(lam1, t.dp[0][0][j], t.p0[0][j]));
+        const float Dy = fmaf(lam2, t.dp[1][1][j], fmaf(lam1, t.dp[0][1][j], t.p0[1][j]));
+        const float Dz = fmaf(lam2, t.dp[1][2][j], fmaf(lam1, t.dp[0][2][j], t.p0[2][j]));
+        dist = sqrt_approx(fmaf(Dx, Dx, fmaf(Dy, Dy, Dz * Dz))) * (iQ * sp.lens_inv_r);
     }
     // focus = 1 - smoothstep(0.7, 1, dist)
-    const float st = fminf(fmaxf((dist - 0.7f) * (1.f / 0.3f), 0.f), 1.f);
+    const float st = __saturatef((dist - 0.7f) * (1.f / 0.3f));
     const float focus = 1.f - st * st * (3.f - 2.f * st);
     // squared distances to the face edge segments: the closest point of edge k
     // is corner k + t e_k, t = clamp(v_k . e_k / |e_k|^2, 0, 1), with
@@ -79,35 +86,34 @@ __device__ __forceinline__ float4 shade_fragment(const ShadeSoA& t, int j, float
         vx = nx;
         vy = ny;
     }
-    // Eq. 1 with the depth-dependent width, halo band of the focus edges; the
-    // tests compare squared distances (1/256-pixel units)
-    const float w = (1.f + 0.3f * focus) * sp.w_base * g;
-    const float h = sp.halo_scale * sp.w_base * focus * g;
-    const float w256 = 256.f * w, wh256 = 256.f * (w + h);
-    const bool e_focus = f2 <= w256 * w256, e_context = c2 <= w256 * w256;
-    float alpha_e = (float)e_context + focus * ((float)e_focus - (float)e_context);
-    const bool halo = !e_focus && (f2 <= wh256 * wh256) && focus > 0.f;
-    if (halo) alpha_e = focus;
-    // colour table and Eq. 2
-    const float tt = fminf(fmaxf((t_imp - sp.tf_lo) * sp.tf_inv, 0.f), 1.f);
-    const float ctf[3] = {tt, 0.f, 1.f - tt};
-    const float dk = 1.f - sp.darken * focus;
+    // Eq. 1 with the depth-dependent width w, halo band h (focus edges); the
+    // tests compare squared distances in 1/256-pixel units. Edges visible in
+    // context are visible in focus too (c2 >= f2), so an edge in context
+    // (alpha 1) is one in focus, and an edge in focus or in the halo band has
+    // alpha = focus (in the band with focus 0 that is 0 as well).
+    const float wg = 256.f * sp.w_base * g;                      // >= 0: w_base, g_min, halo_scale >= 0
+    const float w256 = fmaf(0.3f * focus, wg, wg);
+    const float wh256 = fmaf((0.3f + sp.halo_scale) * focus, wg, wg);
+    const float w2 = w256 * w256;
+    const bool band = f2 <= wh256 * wh256;
+    const bool halo = band && f2 > w2 && focus > 0.f;
+    const float alpha_e = c2 <= w2 ? 1.f : (band ? focus : 0.f);
+    // colour table ctf = (t, 0, 1 - t); Eq. 2: accentuated faces (s_e = s > 1)
+    // move the face colour towards white by beta
+    const float tt = __saturatef((t_imp - sp.tf_lo) * sp.tf_inv);
     const bool accent = a2 <= sp.accent_r2;
     const float s_e = accent ? sp.s : 1.f;
-    float cf[3], ce[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        ce[k] = halo ? 1.f : ctf[k] * dk;
-        cf[k] = s_e > 1.f ? ctf[k] + sp.accent_beta * (1.f - ctf[k]) : ctf[k];
-    }
+    const float beta = s_e > 1.f ? sp.accent_beta : 0.f;
+    const float dk = fmaf(-sp.darken, focus, 1.f);
+    const float er = halo ? 1.f : tt * dk, eg = halo ? 1.f : 0.f, eb = halo ? 1.f : (1.f - tt) * dk;
     // Eq. 3 and Eq. 4
-    const float ahat = sp.alpha_min + sp.alpha_span * tt;
+    const float ahat = fmaf(sp.alpha_span, tt, sp.alpha_min);
     const float dc = fminf(dist, 1.f);
     const float dc2 = dc * dc;
     const float af = fminf(s_e * (ahat * (dc2 * dc2)), 1.f);
     const float wf = (1.f - alpha_e) * af;
-    float4 c = make_float4(alpha_e * ce[0] + wf * cf[0], alpha_e * ce[1] + wf * cf[1], alpha_e * ce[2] + wf * cf[2],
-                           alpha_e + wf);
+    float4 c = make_float4(fmaf(alpha_e, er, wf * fmaf(beta, 1.f - tt, tt)), fmaf(alpha_e, eg, wf * beta),
+                           fmaf(alpha_e, eb, wf * fmaf(beta, tt, 1.f - tt)), alpha_e + wf);
     // depth cue (Section "Evaluation"): in focus and beyond the reference
     // depth, the colour moves towards its luma; opacity unchanged
     if (sp.desat > 0.f) {

@@ -268,7 +268,8 @@ def test_error_codes(hx):
     with pytest.raises(hx.HexfcError) as e:
         r.set_lens(synth.Lens(radius=0.0))
     assert e.value.status == hx.HEXFC_ERR_ARG
-    for bad_style in (synth.Style(desat=1.5), synth.Style(w_base=-1.0), synth.Style(g_min=3.0)):
+    for bad_style in (synth.Style(desat=1.5), synth.Style(w_base=-1.0), synth.Style(g_min=3.0),
+                      synth.Style(g_min=-0.5), synth.Style(halo_scale=-0.1)):
         with pytest.raises(hx.HexfcError) as e:
             r.set_style(bad_style)
         assert e.value.status == hx.HEXFC_ERR_ARG
