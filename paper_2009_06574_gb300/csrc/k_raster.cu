@@ -413,13 +413,14 @@ __device__ __forceinline__ void pipe_init(uint64_t* full, uint64_t* empty)
 // per-pixel totals are summed at the end.
 struct CountWarp {
     CovSoA c;
-    // float copies of the edge functions: E ~ e0f + fa*rx + fb*ry, and a bound on the
-    // float error; outside the bound the float sign is the exact sign
-    float e0f[3][kChunk], fa[3][kChunk], fb[3][kChunk], tol[3][kChunk];
+    // float copies of the edge functions, (e0f, fa, fb, tol) per edge: E ~ e0f +
+    // fa*rx + fb*ry, and a bound on the float error; outside the bound the
+    // float sign is the exact sign (one 16-byte load per edge and sample)
+    float4 ef[3][kChunk];
     // the chunk's samples as one sequence: triangle j's box samples start at
-    // start[j]; r2j maps the rank of a non-empty triangle to its index
-    uint32_t start[kChunk];
-    float inv_bw[kChunk];
+    // seq[j].x (seq[j] = start, 1 / box width, box); r2j maps the rank of a
+    // non-empty triangle to its index
+    uint4 seq[kChunk];
     uint8_t r2j[kChunk];
     uint32_t mask[kTilePix];   // coverage bits of the chunk; after the last chunk, the warp's per-pixel counts
 };
@@ -435,10 +436,7 @@ __device__ __forceinline__ void stage_fast(CountWarp& me, int j)
         const float e0 = i64_to_f32(me.c.e0[k][j]);
         const float fa = -256.f * (float)me.c.dy[k][j];   // exact: |dy| < 2^24
         const float fb = 256.f * (float)me.c.dx[k][j];
-        me.e0f[k][j] = e0;
-        me.fa[k][j] = fa;
-        me.fb[k][j] = fb;
-        me.tol[k][j] = ldexpf(fabsf(e0) + 16.f * (fabsf(fa) + fabsf(fb)), -21);
+        me.ef[k][j] = make_float4(e0, fa, fb, ldexpf(fabsf(e0) + 16.f * (fabsf(fa) + fabsf(fb)), -21));
     }
 }
 
@@ -450,8 +448,9 @@ __device__ __forceinline__ bool cover_fast(const CountWarp& me, int j, int rx, i
     bool all_pos = true, any_neg = false;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float e = fmaf(me.fa[k][j], frx, fmaf(me.fb[k][j], fry, me.e0f[k][j]));
-        const float t = me.tol[k][j];
+        const float4 f = me.ef[k][j];
+        const float e = fmaf(f.y, frx, fmaf(f.z, fry, f.x));
+        const float t = f.w;
         all_pos = all_pos && e > t;
         any_neg = any_neg || e < -t;
     }
@@ -502,8 +501,8 @@ __device__ __forceinline__ void count_chunks(CountWarp* s_w, int warp, int lane,
         }
         const uint32_t start_l = incl - area_l, total = __shfl_sync(0xffffffffu, incl, 31);
         const unsigned nonempty = __ballot_sync(0xffffffffu, area_l != 0);
-        me.start[lane] = start_l;
-        me.inv_bw[lane] = area_l ? __frcp_rn((float)box_bw(bx_l)) : 0.f;
+        me.seq[lane] = make_uint4(start_l, __float_as_uint(area_l ? __frcp_rn((float)box_bw(bx_l)) : 0.f),
+                                  (uint32_t)bx_l, 0u);
         if (area_l) me.r2j[__popc(nonempty & ((1u << lane) - 1u))] = (uint8_t)lane;
         __syncwarp();
         for (uint32_t g = 0; g < total; g += 32) {
@@ -515,11 +514,12 @@ __device__ __forceinline__ void count_chunks(CountWarp* s_w, int warp, int lane,
             if (idx < total) {
                 const int c = __popc(smask & (0xffffffffu >> (31 - lane)));   // starts in [g, idx]
                 const int j = me.r2j[c > 0 ? before + c - 1 : before - 1];
-                const int bx = me.c.box[j];
+                const uint4 sq = me.seq[j];
+                const int bx = (int)sq.z;
                 const int bw = box_bw(bx);
-                const int off = (int)(idx - me.start[j]);
+                const int off = (int)(idx - sq.x);
                 // exact for off < 256, bw <= 16: the quotient is never within 1/32 of an integer
-                const int ry = (int)(((float)off + 0.5f) * me.inv_bw[j]);
+                const int ry = (int)(((float)off + 0.5f) * __uint_as_float(sq.y));
                 const int rx = off - ry * bw;
                 if (cover_fast(me, j, rx, ry))
                     atomicOr(&me.mask[(box_ly0(bx) + ry) * kTile + box_lx0(bx) + rx], 1u << j);
