@@ -36,9 +36,11 @@ enum {
     HEXFC_ERR_OOM = -2,       /* device allocation failed, or the fragment total exceeds the budget */
     HEXFC_ERR_OVERFLOW = -3,  /* a per-pixel list exceeds HEXFC_MAX_LIST */
     HEXFC_ERR_CUDA = -4,      /* a CUDA runtime call or kernel launch failed */
-    HEXFC_ERR_TIMEOUT = -5,   /* reserved: a bounded device-side wait ran out */
+    HEXFC_ERR_TIMEOUT = -5,   /* a bounded device-side wait ran out */
     HEXFC_ERR_MESH = -6,      /* the mesh is malformed (index out of range, non-finite vertex) */
-    HEXFC_ERR_STATE = -7      /* call out of order (no mesh, no view, no previous render) */
+    HEXFC_ERR_STATE = -7,     /* call out of order (no mesh, no view, no previous render) */
+    HEXFC_ERR_CHECK = -8      /* a device-side consistency check failed (list sizes of the count and
+                                 fill passes disagree, or an exact depth could not be confirmed) */
 };
 
 /* Longest per-pixel fragment list the sort/composite pass accepts. */
@@ -282,7 +284,10 @@ hexfc_status hexfc_set_style(hexfc_ctx* ctx, const hexfc_style* style);
  * the image is complete when `stream` reaches the end of the call.
  * stats (host, nullable) receives the frame statistics.
  * Errors: ARG, STATE (no view), OOM (fragments exceed the budget; stats still
- * filled), OVERFLOW (a list longer than HEXFC_MAX_LIST), CUDA.
+ * filled), OVERFLOW (a list longer than HEXFC_MAX_LIST), CUDA, and TIMEOUT or
+ * CHECK from the device-side checks of the fill and composite passes: those
+ * passes run after the call returns, so hexfc_render reports their failure
+ * on the context's next call (hexfc_render_host at the end of its own frame).
  */
 hexfc_status hexfc_render(hexfc_ctx* ctx, int32_t mesh, float* out_rgba, hexfc_frame_stats* stats,
                           void* stream);
@@ -376,6 +381,17 @@ hexfc_status hexfc_stage_times(hexfc_ctx* ctx, double* ms, uint64_t* frames, int
 
 /* Static string for a status code. Never NULL. */
 const char* hexfc_status_string(hexfc_status s);
+
+/*
+ * The CUDA runtime error code (cudaError_t) of the last CUDA call or kernel
+ * launch of the library that failed on the calling host thread, 0 if none
+ * has; a call that returns HEXFC_ERR_CUDA (or HEXFC_ERR_OOM from a failed
+ * allocation) sets it. Not reset by later successful calls.
+ */
+int32_t hexfc_last_cuda_error(void);
+
+/* Static name of a CUDA runtime error code (e.g. "cudaErrorIllegalAddress"). Never NULL. */
+const char* hexfc_cuda_error_name(int32_t code);
 
 /* Size of the fixed device scratch array used by hexfc_render_noalloc. */
 #define HEXFC_NOALLOC_SCRATCH_BYTES (32u << 20)

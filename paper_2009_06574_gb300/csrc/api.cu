@@ -65,11 +65,29 @@ struct hexfc_ctx {
 
 namespace {
 
+// The CUDA error of the last failed runtime call or launch made by the library
+// on this host thread (hexfc_last_cuda_error).
+thread_local int32_t t_last_cuda = 0;
+
+// Record a failed call's error and clear the runtime's (non-sticky) last error.
+inline void note_cuda(cudaError_t e)
+{
+    t_last_cuda = (int32_t)e;
+    (void)cudaGetLastError();
+}
+
+// Status for the device error bits of scal[5]: a bounded wait that ran out
+// (bits 1, 2), else a failed exactness or consistency check (bit 0).
+inline hexfc_status device_error_status(uint64_t bits)
+{
+    return (bits & 6ull) ? HEXFC_ERR_TIMEOUT : HEXFC_ERR_CHECK;
+}
+
 #define CK(x)                                   \
     do {                                        \
         cudaError_t e_ = (x);                   \
         if (e_ != cudaSuccess) {                \
-            (void)cudaGetLastError();           \
+            note_cuda(e_);                      \
             return HEXFC_ERR_CUDA;              \
         }                                       \
     } while (0)
@@ -94,7 +112,7 @@ hexfc_status dalloc(T** p, size_t n)
     if (n == 0) n = 1;
     cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
     if (e != cudaSuccess) {
-        (void)cudaGetLastError();
+        note_cuda(e);
         *p = nullptr;
         return e == cudaErrorMemoryAllocation ? HEXFC_ERR_OOM : HEXFC_ERR_CUDA;
     }
@@ -425,6 +443,7 @@ hexfc_status job_alloc(FrameJob& j)
     if (!fb.scal) {
         if ((st = dalloc(&fb.scal, 16)) != HEXFC_OK) return st;
         CK(cudaMallocHost((void**)&fb.h_scal, 16 * sizeof(uint64_t)));
+        fb.scal_fresh = true;   // contents undefined: phase 1 clears all of it
     }
     return HEXFC_OK;
 }
@@ -436,9 +455,15 @@ hexfc_status job_phase1(FrameJob& j, cudaStream_t s)
     CK(cudaMemsetAsync(fb.tile_cnt, 0, sizeof(uint32_t) * (size_t)j.n_tiles, s));
     CK(cudaMemsetAsync(fb.tile_cur, 0, sizeof(uint32_t) * (size_t)j.n_tiles, s));
     // scal[5] (device error bits) is kept across frames so that errors of the
-    // last passes of a frame are reported by the next call
-    CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * 5, s));
-    CK(cudaMemsetAsync(fb.scal + 6, 0, sizeof(uint64_t) * 10, s));
+    // last passes of a frame are reported by the next call (hexfc_render_host
+    // reads them at the end of its own frame)
+    if (fb.scal_fresh) {
+        CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * 16, s));
+        fb.scal_fresh = false;
+    } else {
+        CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * 5, s));
+        CK(cudaMemsetAsync(fb.scal + 6, 0, sizeof(uint64_t) * 10, s));
+    }
     CK(launch_vertex_setup(*j.m, j.cam, fb, s));
     job_mark(j, 1, s);
     CK(launch_face_setup(*j.m, j.cam, j.lod, j.delta, fb, j.tiles_x, j.tiles_y, s));
@@ -495,7 +520,7 @@ hexfc_status job_read2(FrameJob& j, cudaStream_t s)
     if (fb.h_scal[5] != 0) {  // a bounded device wait ran out, or an exactness check failed
         const uint64_t bits = fb.h_scal[5];
         CK(cudaMemsetAsync(fb.scal + 5, 0, sizeof(uint64_t), s));
-        return (bits & 6ull) ? HEXFC_ERR_TIMEOUT : HEXFC_ERR_CUDA;
+        return device_error_status(bits);
     }
     j.total = fb.h_scal[0];
     j.max_list = (uint32_t)fb.h_scal[1];
@@ -633,7 +658,7 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     if (fb.h_scal[5] != 0) {
         const uint64_t bits = fb.h_scal[5];
         CK(cudaMemsetAsync(fb.scal + 5, 0, sizeof(uint64_t), s));
-        return (bits & 6ull) ? HEXFC_ERR_TIMEOUT : HEXFC_ERR_CUDA;
+        return device_error_status(bits);
     }
     const uint32_t overflow = (uint32_t)fb.h_scal[6];
     const uint64_t capacity = fb.h_scal[11];
@@ -741,8 +766,8 @@ template <typename F>
 hexfc_status batch_graph(hexfc_ctx* ctx, int phase, const std::vector<int>& items, F&& body)
 {
     cudaStream_t o = ctx->origin;
-    if (cudaStreamBeginCapture(o, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        (void)cudaGetLastError();
+    if (const cudaError_t e = cudaStreamBeginCapture(o, cudaStreamCaptureModeThreadLocal); e != cudaSuccess) {
+        note_cuda(e);
         return HEXFC_ERR_CUDA;
     }
     hexfc_status st = HEXFC_OK;
@@ -757,7 +782,8 @@ hexfc_status batch_graph(hexfc_ctx* ctx, int phase, const std::vector<int>& item
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(o, &g);
     if (!ok || ec != cudaSuccess || st != HEXFC_OK || !g) {
-        (void)cudaGetLastError();
+        if (ec != cudaSuccess) note_cuda(ec);
+        else (void)cudaGetLastError();
         if (g) cudaGraphDestroy(g);
         return st != HEXFC_OK ? st : HEXFC_ERR_CUDA;
     }
@@ -773,8 +799,8 @@ hexfc_status batch_graph(hexfc_ctx* ctx, int phase, const std::vector<int>& item
         }
     }
     if (!ex) {
-        if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
-            (void)cudaGetLastError();
+        if (const cudaError_t e = cudaGraphInstantiate(&ex, g, 0); e != cudaSuccess) {
+            note_cuda(e);
             ex = nullptr;
             cudaGraphDestroy(g);
             return HEXFC_ERR_CUDA;
@@ -782,8 +808,8 @@ hexfc_status batch_graph(hexfc_ctx* ctx, int phase, const std::vector<int>& item
         ++ctx->graph_instantiations;
     }
     cudaGraphDestroy(g);
-    if (cudaGraphLaunch(ex, o) != cudaSuccess) {
-        (void)cudaGetLastError();
+    if (const cudaError_t e = cudaGraphLaunch(ex, o); e != cudaSuccess) {
+        note_cuda(e);
         return HEXFC_ERR_CUDA;
     }
     return HEXFC_OK;
@@ -818,8 +844,8 @@ hexfc_status hexfc_create(hexfc_ctx** out, int device, uint64_t frag_budget_byte
     if (!out) return HEXFC_ERR_ARG;
     *out = nullptr;
     int n = 0;
-    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
-        (void)cudaGetLastError();
+    if (const cudaError_t e = cudaGetDeviceCount(&n); e != cudaSuccess || device < 0 || device >= n) {
+        note_cuda(e != cudaSuccess ? e : cudaErrorInvalidDevice);
         return HEXFC_ERR_CUDA;
     }
     hexfc_ctx* c = new (std::nothrow) hexfc_ctx();
@@ -920,7 +946,7 @@ hexfc_status hexfc_upload_mesh(hexfc_ctx* ctx, const float* verts, int64_t n_ver
     if (e == cudaSuccess) e = launch_importance(*m, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
-        (void)cudaGetLastError();
+        note_cuda(e);
         free_mesh(m);
         return HEXFC_ERR_CUDA;
     }
@@ -1249,11 +1275,18 @@ hexfc_status hexfc_render_host(hexfc_ctx* ctx, int32_t mesh, float* out_rgba_hos
     float* d_out = ctx->d_out;
     st = ctx->predicted ? render_frame_predicted(ctx, m, d_out, stats, s) : render_frame(ctx, m, d_out, stats, s);
     if (st == HEXFC_OK) {
+        // the image and this frame's device error bits
+        FrameBufs& fb = ctx->fb;
         cudaError_t e = cudaMemcpyAsync(out_rgba_host, d_out, bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(fb.h_scal + 5, fb.scal + 5, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
-            (void)cudaGetLastError();
+            note_cuda(e);
             st = HEXFC_ERR_CUDA;
+        } else if (fb.h_scal[5] != 0) {
+            st = device_error_status(fb.h_scal[5]);
+            CK(cudaMemsetAsync(fb.scal + 5, 0, sizeof(uint64_t), s));
+            CK(cudaStreamSynchronize(s));
         }
     }
     return st;
@@ -1290,7 +1323,7 @@ hexfc_status hexfc_debug_pixels(hexfc_ctx* ctx, const int32_t* px, const int32_t
                                 nullptr, d_cnt, 0);
     if (e == cudaSuccess) e = cudaMemcpy(counts, d_cnt, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
-        (void)cudaGetLastError();
+        note_cuda(e);
         cleanup();
         return HEXFC_ERR_CUDA;
     }
@@ -1322,11 +1355,11 @@ hexfc_status hexfc_debug_pixels(hexfc_ctx* ctx, const int32_t* px, const int32_t
     if (e == cudaSuccess && fb.scal) {
         uint64_t errflag = 0;
         e = cudaMemcpy(&errflag, fb.scal + 5, sizeof(uint64_t), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess && errflag) st = HEXFC_ERR_CUDA;
+        if (e == cudaSuccess && errflag) st = device_error_status(errflag);
     }
     cleanup();
     if (e != cudaSuccess) {
-        (void)cudaGetLastError();
+        note_cuda(e);
         return HEXFC_ERR_CUDA;
     }
     return st;
@@ -1369,6 +1402,10 @@ hexfc_status hexfc_stage_times(hexfc_ctx* ctx, double* ms, uint64_t* frames, int
     return HEXFC_OK;
 }
 
+int32_t hexfc_last_cuda_error(void) { return t_last_cuda; }
+
+const char* hexfc_cuda_error_name(int32_t code) { return cudaGetErrorName((cudaError_t)code); }
+
 const char* hexfc_status_string(hexfc_status s)
 {
     switch (s) {
@@ -1378,6 +1415,7 @@ const char* hexfc_status_string(hexfc_status s)
     case HEXFC_ERR_OVERFLOW: return "per-pixel list or output capacity exceeded";
     case HEXFC_ERR_CUDA: return "CUDA error";
     case HEXFC_ERR_TIMEOUT: return "device wait timed out";
+    case HEXFC_ERR_CHECK: return "device-side consistency check failed";
     case HEXFC_ERR_MESH: return "malformed mesh";
     case HEXFC_ERR_STATE: return "call out of order";
     default: return "unknown status";

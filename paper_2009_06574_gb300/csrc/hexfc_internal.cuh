@@ -125,6 +125,7 @@ struct FrameBufs {
     int64_t t_cap = 0;
     uint32_t* bins = nullptr;       // face2tri ids grouped by tile, each tile padded to whole chunks
     uint32_t* bins_tmp = nullptr;   // scratch of the depth order of long tile lists (same layout)
+    bool scal_fresh = false;        // scal just allocated (undefined contents)
     int64_t bin_cap = 0;
     uint32_t* masks = nullptr;      // per chunk of a tile list: 256 per-pixel coverage masks
     int64_t mask_cap = 0;

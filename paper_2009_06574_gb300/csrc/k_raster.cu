@@ -440,24 +440,29 @@ __device__ __forceinline__ void stage_fast(CountWarp& me, int j)
     }
 }
 
-// Coverage of sample (rx, ry) of triangle j: decided in float when every edge
-// value is outside its error bound (or one is clearly negative), else exactly.
-__device__ __forceinline__ bool cover_fast(const CountWarp& me, int j, int rx, int ry)
+// Coverage of samples (rx, ry) and, if `second`, (rx + 1, ry) of triangle j
+// (bits 0 and 1): decided in float when every edge value is outside its error
+// bound (or one is clearly negative), else exactly. The two samples share the
+// inner product fmaf(fb, ry, e0f), so each is evaluated as in the bound.
+__device__ __forceinline__ uint32_t cover_pair(const CountWarp& me, int j, int rx, int ry, bool second)
 {
     const float frx = (float)rx, fry = (float)ry;
-    bool all_pos = true, any_neg = false;
+    bool pos0 = true, neg0 = false, pos1 = true, neg1 = false;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float4 f = me.ef[k][j];
-        const float e = fmaf(f.y, frx, fmaf(f.z, fry, f.x));
-        const float t = f.w;
-        all_pos = all_pos && e > t;
-        any_neg = any_neg || e < -t;
+        const float inner = fmaf(f.z, fry, f.x);
+        const float e0 = fmaf(f.y, frx, inner), e1 = fmaf(f.y, frx + 1.f, inner);
+        pos0 = pos0 && e0 > f.w;
+        neg0 = neg0 || e0 < -f.w;
+        pos1 = pos1 && e1 > f.w;
+        neg1 = neg1 || e1 < -f.w;
     }
-    if (all_pos) return true;
-    if (any_neg) return false;
     int64_t l[3];
-    return cover_at(me.c, j, rx, ry, l);
+    uint32_t r = 0;
+    if (pos0 || (!neg0 && cover_at(me.c, j, rx, ry, l))) r |= 1u;
+    if (second && (pos1 || (!neg1 && cover_at(me.c, j, rx + 1, ry, l)))) r |= 2u;
+    return r;
 }
 
 // Warp `warp` of a tile block rasterises chunks warp, warp + kConsumerWarps, ...
@@ -489,10 +494,12 @@ __device__ __forceinline__ void count_chunks(CountWarp* s_w, int warp, int lane,
             me.c.box[lane] = 0;
         }
         f2t = f2t_next;
-        // the box samples of the chunk's 32 triangles as one sequence, so that
-        // every round gives each lane a sample whatever the boxes' sizes
+        // the box samples of the chunk's 32 triangles, in horizontal pairs, as
+        // one sequence, so that every round gives each lane a pair whatever
+        // the boxes' sizes
         const int bx_l = me.c.box[lane];
-        const uint32_t area_l = (uint32_t)(box_bw(bx_l) * box_bh(bx_l));
+        const uint32_t pw_l = (uint32_t)(box_bw(bx_l) + 1) >> 1;   // pairs per box row
+        const uint32_t area_l = pw_l * (uint32_t)box_bh(bx_l);
         uint32_t incl = area_l;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -501,8 +508,8 @@ __device__ __forceinline__ void count_chunks(CountWarp* s_w, int warp, int lane,
         }
         const uint32_t start_l = incl - area_l, total = __shfl_sync(0xffffffffu, incl, 31);
         const unsigned nonempty = __ballot_sync(0xffffffffu, area_l != 0);
-        me.seq[lane] = make_uint4(start_l, __float_as_uint(area_l ? __frcp_rn((float)box_bw(bx_l)) : 0.f),
-                                  (uint32_t)bx_l, 0u);
+        me.seq[lane] = make_uint4(start_l, __float_as_uint(area_l ? __frcp_rn((float)pw_l) : 0.f), (uint32_t)bx_l,
+                                  pw_l);
         if (area_l) me.r2j[__popc(nonempty & ((1u << lane) - 1u))] = (uint8_t)lane;
         __syncwarp();
         for (uint32_t g = 0; g < total; g += 32) {
@@ -516,13 +523,14 @@ __device__ __forceinline__ void count_chunks(CountWarp* s_w, int warp, int lane,
                 const int j = me.r2j[c > 0 ? before + c - 1 : before - 1];
                 const uint4 sq = me.seq[j];
                 const int bx = (int)sq.z;
-                const int bw = box_bw(bx);
                 const int off = (int)(idx - sq.x);
-                // exact for off < 256, bw <= 16: the quotient is never within 1/32 of an integer
+                // exact for off < 128, pairs per row <= 8: the quotient is never within 1/16 of an integer
                 const int ry = (int)(((float)off + 0.5f) * __uint_as_float(sq.y));
-                const int rx = off - ry * bw;
-                if (cover_fast(me, j, rx, ry))
-                    atomicOr(&me.mask[(box_ly0(bx) + ry) * kTile + box_lx0(bx) + rx], 1u << j);
+                const int rx = 2 * (off - ry * (int)sq.w);
+                const uint32_t cov = cover_pair(me, j, rx, ry, rx + 1 < box_bw(bx));
+                uint32_t* mrow = &me.mask[(box_ly0(bx) + ry) * kTile + box_lx0(bx) + rx];
+                if (cov & 1u) atomicOr(mrow, 1u << j);
+                if (cov & 2u) atomicOr(mrow + 1, 1u << j);
             }
         }
         __syncwarp();

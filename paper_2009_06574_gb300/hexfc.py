@@ -25,6 +25,7 @@ HEXFC_ERR_CUDA = -4
 HEXFC_ERR_TIMEOUT = -5
 HEXFC_ERR_MESH = -6
 HEXFC_ERR_STATE = -7
+HEXFC_ERR_CHECK = -8
 HEXFC_MAX_LIST = 8192
 HEXFC_NOALLOC_SCRATCH_BYTES = 32 << 20
 HEXFC_LENS_SCREEN = 0
@@ -47,7 +48,7 @@ EXPORTS = ["hexfc_style_default", "hexfc_create", "hexfc_destroy", "hexfc_upload
            "hexfc_stage_times", "hexfc_status_string", "hexfc_render_noalloc", "hexfc_share_mesh",
            "hexfc_frame_memory", "hexfc_trim", "hexfc_render_batch", "hexfc_capacity_reset",
            "hexfc_capacity_set_weights", "hexfc_capacity_get_weights", "hexfc_capacity_grad",
-           "hexfc_capacity_train"]
+           "hexfc_capacity_train", "hexfc_last_cuda_error", "hexfc_cuda_error_name"]
 
 
 class HexfcError(RuntimeError):
@@ -132,6 +133,8 @@ def load():
                 "hexfc_capacity_get_weights": (i32, [vp, vp, i64]),
                 "hexfc_capacity_grad": (i32, [vp, vp, vp, i64, vp, vp]),
                 "hexfc_capacity_train": (i32, [vp, i32, C.c_float, vp, vp]),
+                "hexfc_last_cuda_error": (i32, []),
+                "hexfc_cuda_error_name": (C.c_char_p, [i32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -145,8 +148,18 @@ def status_string(s: int) -> str:
     return load().hexfc_status_string(int(s)).decode()
 
 
+def last_cuda_error():
+    """(code, name) of the last CUDA call of the library that failed on this thread."""
+    L = load()
+    code = int(L.hexfc_last_cuda_error())
+    return code, L.hexfc_cuda_error_name(code).decode()
+
+
 def _check(status: int, what: str):
     if status != HEXFC_OK:
+        if status == HEXFC_ERR_CUDA:
+            code, name = last_cuda_error()
+            what = f"{what} ({name}, {code})"
         raise HexfcError(status, what)
 
 
@@ -209,6 +222,10 @@ class Renderer:
         self.device = device
         self.view = None
         self.last_stats = None
+
+    def last_cuda_error(self) -> int:
+        """CUDA error code of the last failed CUDA call on the calling thread (0: none)."""
+        return last_cuda_error()[0]
 
     def close(self):
         if getattr(self, "_h", None) is not None and _lib is not None:

@@ -45,6 +45,7 @@ class Result:
     ticket: int
     request: Request
     status: int = 0
+    cuda_error: int = 0                  # CUDA error code behind a HEXFC_ERR_CUDA status
     image: Optional[np.ndarray] = None   # [H, W, 4] float32
     stats: Optional[dict] = None
     slot: int = -1
@@ -274,11 +275,14 @@ class Server:
                 status = slot.r.render_host(slot.mesh_ids[req.mesh], img, slot.stream, check=False)
             except Exception:   # an argument the library rejected
                 status = -1
+            lce = getattr(slot.r, "last_cuda_error", None)
+            cuda_error = lce() if status != 0 and lce is not None else 0
             if status != 0:
                 img = None
             held = slot.r.frame_memory()
             with self._cv:
                 res.status = int(status)
+                res.cuda_error = int(cuda_error)
                 res.image = img
                 res.stats = dict(slot.r.last_stats) if slot.r.last_stats else None
                 res.t_done = time.perf_counter()

@@ -36,6 +36,7 @@ def test_host_only_entry_points():
     L = hexfc.load()
     assert hexfc.status_string(0) == "ok"
     assert "mesh" in hexfc.status_string(hexfc.HEXFC_ERR_MESH)
+    assert "check" in hexfc.status_string(hexfc.HEXFC_ERR_CHECK)
     s = hexfc.hexfc_style()
     L.hexfc_style_default(ctypes.byref(s))
     assert s.w_base == 2.0 and s.s == 1.5 and s.lod == 1
@@ -52,3 +53,5 @@ def test_no_gpu_create_fails_cleanly():
     from paper_2009_06574_gb300 import hexfc
     h = ctypes.c_void_p()
     assert hexfc.load().hexfc_create(ctypes.byref(h), 0, 0) == hexfc.HEXFC_ERR_CUDA
+    code, name = hexfc.last_cuda_error()   # the failed device query, by name
+    assert code != 0 and name.startswith("cudaError")

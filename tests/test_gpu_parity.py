@@ -128,6 +128,30 @@ def test_tiles_past_shared_sort(hx):
     assert st["gpu_stats"]["bin_entries"] > 4 * (4096 + 32)
 
 
+def test_fresh_buffers_carry_no_stale_error_bits(hx):
+    """Frame buffers allocated over freed device memory full of set bits (as a
+    context allocating after others released theirs) start with clear
+    device error bits: the first frames of new and trimmed contexts succeed."""
+    mesh = synth.hex_grid(4, jitter=0.1, seed=1)
+    out = torch.zeros((48, 64, 4), device="cuda")
+    for _ in range(4):
+        junk = torch.full((32 << 20,), -1, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        del junk
+        torch.cuda.empty_cache()
+        r = hx.Renderer(0)
+        mid = r.upload_mesh(mesh.verts, mesh.cells)
+        r.set_view(synth.orbit_view(3, 120, 64, 48, radius=2.0))
+        r.set_lens(synth.Lens())
+        r.set_style(synth.Style())
+        r.render(mid, out)
+        r.trim()
+        r.render(mid, out)
+        img = np.empty((48, 64, 4), np.float32)
+        r.render_host(mid, img)
+        r.close()
+
+
 def test_without_depth_order(hx):
     """Lists in the faces' order (no per-tile depth order): most lists go
     through the warp-wide sort of the out-of-order pass; the result is the same."""
