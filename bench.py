@@ -36,11 +36,11 @@ FRAG_BYTES = 24          # 8 B key + 16 B premultiplied RGBA
 # DRAM traffic of one k_fill launch (ncu dram__bytes_read.sum + dram__bytes_write.sum,
 # one pass, on the 1920x1080 bench frame), per fragment drawn, and the fill kernel's
 # sources it was taken on: the roofline reports it only while those sources are unchanged.
-FILL_DRAM = {"bytes_per_fragment": 42.12,
-             "sha256": "299dd47dd2d2e36843d4e927eaf8a37a3bb10f07e678307f2f265c184c99ee80",
-             "profile": "profiles/k_fill_dram_grid64_orbit_1080p.md"}
-FILL_SOURCES = ("csrc/k_raster.cu", "csrc/shade.cuh", "csrc/raster_common.cuh", "csrc/pipeline.cuh",
-                "csrc/hexfc_internal.cuh")
+FILL_DRAM = {"bytes_per_fragment": 27.59,
+             "sha256": "dcaf03827a03eee00129d4760fb6dd52c227ec6dced0addbc6a6b973d1c941dd",
+             "profile": "profiles/dram_k_fill_k_count_k_composite_grid64_orbit_1080p.md"}
+FILL_SOURCES = ("csrc/k_fill.cu", "csrc/raster_tiles.cuh", "csrc/shade.cuh", "csrc/raster_common.cuh",
+                "csrc/pipeline.cuh", "csrc/hexfc_internal.cuh")
 
 
 def fill_sources_sha256() -> str:
@@ -50,6 +50,8 @@ def fill_sources_sha256() -> str:
         with open(os.path.join(ROOT, "paper_2009_06574_gb300", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
+
+
 FACE_FRAME_BYTES = 64    # per-frame half of a face record: X[4], Y[4], z24[4] + flags, eye depth[4]
 FACE_STATIC_BYTES = 64   # static half: corner importance[4], world position[4][3]
 

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libhexfc.so")
 
-SOURCES = ["api.cu", "k_quality.cu", "k_raster.cu", "k_scan.cu", "k_composite.cu", "k_capacity.cu", "mesh_host.cpp"]
+SOURCES = ["api.cu", "k_quality.cu", "k_raster.cu", "k_fill.cu", "k_scan.cu", "k_composite.cu", "k_capacity.cu", "mesh_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",
          "-I", INCLUDE, "-I", CSRC]

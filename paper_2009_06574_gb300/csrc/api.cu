@@ -857,7 +857,8 @@ hexfc_status hexfc_create(hexfc_ctx** out, int device, uint64_t frag_budget_byte
     c->lens.radius = 1.0;
     {
         DeviceGuard g(device);
-        if (prepare_raster_kernels() != cudaSuccess || prepare_composite_kernels() != cudaSuccess) {
+        if (prepare_raster_kernels() != cudaSuccess || prepare_fill_kernels() != cudaSuccess ||
+            prepare_composite_kernels() != cudaSuccess) {
             (void)cudaGetLastError();
             delete c;
             return HEXFC_ERR_CUDA;

@@ -159,6 +159,7 @@ cudaError_t launch_bin_fill(const DevMesh& m, FrameBufs& fb, int tiles_x, int W,
                             cudaStream_t s);
 // Kernel attributes (dynamic shared memory limits), once per device context.
 cudaError_t prepare_raster_kernels();
+cudaError_t prepare_fill_kernels();
 cudaError_t prepare_composite_kernels();
 
 cudaError_t launch_bin_sort(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int buckets,
