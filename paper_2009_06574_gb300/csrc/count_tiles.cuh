@@ -8,28 +8,34 @@ namespace hexfc {
 // Per tile: coverage of every chunk of 32 triangles as per-pixel bit masks;
 // the masks are kept for the fill pass and their bit counts are the
 // per-pixel list lengths. Warp w takes chunks w, w + 8, ... of the tile's list
-// on its own: its 32 lanes stage the chunk's triangles, then walk each
-// triangle's box (clipped to the tile) one sample per lane, setting bit j of
-// the covered pixels in the warp's private masks. No block barrier until the
-// per-pixel totals are summed at the end.
+// on its own: its 32 lanes stage the chunk's triangles, then take the
+// triangles' box rows (clipped to the tile) one per lane: a triangle covers
+// one run of samples in a row, found from its three edges' crossings of the
+// row, and the lane sets bit j of those pixels in the warp's private masks.
+// No block barrier until the per-pixel totals are summed at the end.
 struct CountWarp {
     CovSoA c;
-    // float copies of the edge functions, (e0f, fa, fb, tol) per edge: E ~ e0f +
-    // fa*rx + fb*ry, and a bound on the float error; outside the bound the
-    // float sign is the exact sign (one 16-byte load per edge and sample)
+    // per edge, float data of its crossing with a sample row: (e0f, fb, rfa,
+    // eps). The edge value at box column rx of row ry is E = e0f + fb*ry +
+    // fa*rx (fa = -256 dy, fb = 256 dx, e0f ~ e0), so it crosses 0 at column
+    // t = -(e0f + fb*ry) * rfa, rfa = 1 / fa; eps bounds |t - t_exact|. An
+    // edge parallel to the rows (dy = 0) has rfa = 0 and eps = the bound on
+    // the float error of its (constant) value.
     float4 ef[3][kChunk];
-    // the chunk's samples as one sequence: triangle j's box samples start at
-    // seq[j].x (seq[j] = start, 1 / box width, box); r2j maps the rank of a
-    // non-empty triangle to its index
+    // the chunk's rows as one sequence: triangle j's rows start at seq[j].x
+    // (seq[j] = start, -, box, -); r2j maps the rank of a non-empty triangle
+    // to its index
     uint4 seq[kChunk];
     uint8_t r2j[kChunk];
     uint32_t mask[kTilePix];   // coverage bits of the chunk; after the last chunk, the warp's per-pixel counts
 };
 
-// Float version of triangle j's edge functions in the warp's staging slot.
-// e0f is within 0.75 ulp of e0 and the float evaluation fmaf(fa, rx,
-// fmaf(fb, ry, e0f)) adds two roundings, all of magnitudes at most |e0| +
-// 15 (|fa| + |fb|): at most 3.5 units of 2^-24 of that, and tol allows 8.
+// Float crossing data of triangle j's edges in the warp's staging slot. e0f
+// is within 0.75 ulp of e0 and fmaf(fb, ry, e0f) adds one rounding, all of
+// magnitudes at most M = |e0| + 16 (|fa| + |fb|): within tol = 8 units of
+// 2^-24 M of the exact value. Dividing by fa (rfa within 0.5 ulp, one more
+// rounding of t) moves t by at most tol |rfa| + 2^-22 |t|, and |t| <= 17
+// wherever it matters (columns 0..15): eps = tol |rfa| (1 + 2^-10) + 2^-17.
 __device__ __forceinline__ void stage_fast(CountWarp& me, int j)
 {
 #pragma unroll
@@ -37,38 +43,76 @@ __device__ __forceinline__ void stage_fast(CountWarp& me, int j)
         const float e0 = i64_to_f32(me.c.e0[k][j]);
         const float fa = -256.f * (float)me.c.dy[k][j];   // exact: |dy| < 2^24
         const float fb = 256.f * (float)me.c.dx[k][j];
-        me.ef[k][j] = make_float4(e0, fa, fb, ldexpf(fabsf(e0) + 16.f * (fabsf(fa) + fabsf(fb)), -21));
+        const float tol = ldexpf(fabsf(e0) + 16.f * (fabsf(fa) + fabsf(fb)), -21);
+        const float rfa = fa != 0.f ? __frcp_rn(fa) : 0.f;
+        const float eps = fa != 0.f ? fmaf(tol * fabsf(rfa), 1.f + 0x1p-10f, 0x1p-17f) : tol;
+        me.ef[k][j] = make_float4(e0, fb, rfa, eps);
     }
 }
 
-// Coverage of samples (rx, ry) and, if `second`, (rx + 1, ry) of triangle j
-// (bits 0 and 1): decided in float when every edge value is outside its error
-// bound (or one is clearly negative), else exactly. The two samples share the
-// inner product fmaf(fb, ry, e0f), so each is evaluated as in the bound.
-__device__ __forceinline__ uint32_t cover_pair(const CountWarp& me, int j, int rx, int ry, bool second)
+// Exact: does edge k of triangle j own box column rx of the row whose edge
+// value at column 0 is A (edge function > 0, or 0 on an edge the top-left rule
+// gives to the triangle)?
+__device__ __forceinline__ bool edge_in(const CovSoA& c, int k, int j, int64_t A, int rx)
 {
-    const float frx = (float)rx, fry = (float)ry;
-    bool pos0 = true, neg0 = false, pos1 = true, neg1 = false;
+    const int64_t e = A - (int64_t)c.dy[k][j] * (int64_t)(rx << 8);
+    return e > 0 || (e == 0 && ((c.meta[j] >> k) & 1u));
+}
+
+// The covered box columns [lo, hi] of box row ry of triangle j (empty if lo >
+// hi): the intersection of its three edges' half-rows. Each edge's crossing
+// is taken from the float data where it is more than eps from an integer
+// column; near one (or if eps is not small), the column is decided by exact
+// integer tests (a binary search on the monotone edge test).
+__device__ __forceinline__ void row_span(const CountWarp& me, int j, int ry, int bw, int& lo, int& hi)
+{
+    lo = 0;
+    hi = bw - 1;
+    const float fry = (float)ry;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float4 f = me.ef[k][j];
-        const float inner = fmaf(f.z, fry, f.x);
-        const float e0 = fmaf(f.y, frx, inner), e1 = fmaf(f.y, frx + 1.f, inner);
-        pos0 = pos0 && e0 > f.w;
-        neg0 = neg0 || e0 < -f.w;
-        pos1 = pos1 && e1 > f.w;
-        neg1 = neg1 || e1 < -f.w;
+        const float af = fmaf(f.y, fry, f.x);   // edge value at column 0
+        if (f.z == 0.f) {   // parallel to the rows: the whole row or nothing
+            bool in = af > f.w;
+            if (!in && af >= -f.w)
+                in = edge_in(me.c, k, j, me.c.e0[k][j] + (int64_t)me.c.dx[k][j] * (int64_t)(ry << 8), 0);
+            if (!in) hi = -1;
+            continue;
+        }
+        const float t = -af * f.z;
+        const float rt = rintf(t);
+        const bool exact = f.w > 0.25f || (fabsf(t - rt) <= f.w && rt >= 0.f && rt <= (float)(bw - 1));
+        int b;
+        if (!exact) {
+            const float ft = floorf(t);
+            b = f.z > 0.f ? (int)fminf(fmaxf(ft + 1.f, 0.f), (float)bw)     // first column inside
+                          : (int)fminf(fmaxf(ft, -1.f), (float)(bw - 1));   // last column inside
+        } else {
+            const int64_t A = me.c.e0[k][j] + (int64_t)me.c.dx[k][j] * (int64_t)(ry << 8);
+            if (f.z > 0.f) {   // inside from the first column that passes: search [0, bw]
+                int a = 0, z = bw;
+                while (a < z) {
+                    const int m = (a + z) >> 1;
+                    if (edge_in(me.c, k, j, A, m)) z = m;
+                    else a = m + 1;
+                }
+                b = a;
+            } else {           // inside up to the last column that passes: search [-1, bw - 1]
+                int a = -1, z = bw - 1;
+                while (a < z) {
+                    const int m = (a + z + 1) >> 1;
+                    if (edge_in(me.c, k, j, A, m)) a = m;
+                    else z = m - 1;
+                }
+                b = a;
+            }
+        }
+        if (f.z > 0.f) lo = max(lo, b);
+        else hi = min(hi, b);
     }
-    int64_t l[3];
-    uint32_t r = 0;
-    if (pos0 || (!neg0 && cover_at(me.c, j, rx, ry, l))) r |= 1u;
-    if (second && (pos1 || (!neg1 && cover_at(me.c, j, rx + 1, ry, l)))) r |= 2u;
-    return r;
 }
 
-// Warp `warp` of a tile block rasterises chunks warp, warp + kConsumerWarps, ...
-// of the tile's list into masks (global, per chunk); its per-pixel counts are
-// left in s_w[warp].mask.
 __device__ __forceinline__ void count_chunks(CountWarp* s_w, int warp, int lane, const uint32_t* __restrict__ bins,
                                              const FaceFrame* __restrict__ fframe, uint64_t beg, uint32_t n_chunks,
                                              int px0, int py0, int W, int H, uint32_t* __restrict__ masks)
@@ -95,43 +139,37 @@ __device__ __forceinline__ void count_chunks(CountWarp* s_w, int warp, int lane,
             me.c.box[lane] = 0;
         }
         f2t = f2t_next;
-        // the box samples of the chunk's 32 triangles, in horizontal pairs, as
-        // one sequence, so that every round gives each lane a pair whatever
-        // the boxes' sizes
+        // the box rows of the chunk's 32 triangles as one sequence, so that
+        // every round gives each lane a row whatever the boxes' sizes
         const int bx_l = me.c.box[lane];
-        const uint32_t pw_l = (uint32_t)(box_bw(bx_l) + 1) >> 1;   // pairs per box row
-        const uint32_t area_l = pw_l * (uint32_t)box_bh(bx_l);
-        uint32_t incl = area_l;
+        const uint32_t rows_l = (uint32_t)box_bh(bx_l);
+        uint32_t incl = rows_l;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        const uint32_t start_l = incl - area_l, total = __shfl_sync(0xffffffffu, incl, 31);
-        const unsigned nonempty = __ballot_sync(0xffffffffu, area_l != 0);
-        me.seq[lane] = make_uint4(start_l, __float_as_uint(area_l ? __frcp_rn((float)pw_l) : 0.f), (uint32_t)bx_l,
-                                  pw_l);
-        if (area_l) me.r2j[__popc(nonempty & ((1u << lane) - 1u))] = (uint8_t)lane;
+        const uint32_t start_l = incl - rows_l, total = __shfl_sync(0xffffffffu, incl, 31);
+        const unsigned nonempty = __ballot_sync(0xffffffffu, rows_l != 0);
+        me.seq[lane] = make_uint4(start_l, 0u, (uint32_t)bx_l, 0u);
+        if (rows_l) me.r2j[__popc(nonempty & ((1u << lane) - 1u))] = (uint8_t)lane;
         __syncwarp();
         for (uint32_t g = 0; g < total; g += 32) {
             // triangles starting in [g, g + 32) (bit = offset) and those before g
-            const bool starts = area_l != 0 && start_l >= g && start_l < g + 32;
+            const bool starts = rows_l != 0 && start_l >= g && start_l < g + 32;
             const uint32_t smask = __reduce_or_sync(0xffffffffu, starts ? 1u << (start_l - g) : 0u);
-            const int before = __popc(__ballot_sync(0xffffffffu, area_l != 0 && start_l < g));
+            const int before = __popc(__ballot_sync(0xffffffffu, rows_l != 0 && start_l < g));
             const uint32_t idx = g + (uint32_t)lane;
             if (idx < total) {
                 const int c = __popc(smask & (0xffffffffu >> (31 - lane)));   // starts in [g, idx]
                 const int j = me.r2j[c > 0 ? before + c - 1 : before - 1];
                 const uint4 sq = me.seq[j];
                 const int bx = (int)sq.z;
-                const int off = (int)(idx - sq.x);
-                // exact for off < 128, pairs per row <= 8: the quotient is never within 1/16 of an integer
-                const int ry = (int)(((float)off + 0.5f) * __uint_as_float(sq.y));
-                const int rx = 2 * (off - ry * (int)sq.w);
-                const uint32_t cov = cover_pair(me, j, rx, ry, rx + 1 < box_bw(bx));
-                uint32_t* mrow = &me.mask[(box_ly0(bx) + ry) * kTile + box_lx0(bx) + rx];
-                if (cov & 1u) atomicOr(mrow, 1u << j);
-                if (cov & 2u) atomicOr(mrow + 1, 1u << j);
+                const int ry = (int)(idx - sq.x);
+                int lo, hi;
+                row_span(me, j, ry, box_bw(bx), lo, hi);
+                uint32_t* mrow = &me.mask[(box_ly0(bx) + ry) * kTile + box_lx0(bx)];
+                for (int rx = lo; rx <= hi; ++rx) atomicOr(mrow + rx, 1u << j);
             }
         }
         __syncwarp();

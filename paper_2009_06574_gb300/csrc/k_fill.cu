@@ -233,11 +233,19 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
         const uint32_t tag = ((uint32_t)p << 5) | ((uint32_t)s << 13) | (fits ? kCounted : 0u);
         for (uint32_t w0 = 0; w0 < total; w0 += kWQWin) {
             uint32_t m2 = mk, r = incl - h;
-            while (m2) {
-                const uint32_t j = __ffs(m2) - 1;
-                m2 &= m2 - 1;
-                if (r >= w0 && r < w0 + kWQWin) s_q[(tail + r - w0) & (kWQ - 1)] = j | tag;
-                ++r;
+            if (total <= (uint32_t)kWQWin) {   // one window: every entry is queued
+                uint32_t pos = tail + r;
+                while (m2) {
+                    s_q[pos++ & (kWQ - 1)] = (__ffs(m2) - 1) | tag;
+                    m2 &= m2 - 1;
+                }
+            } else {
+                while (m2) {
+                    const uint32_t j = __ffs(m2) - 1;
+                    m2 &= m2 - 1;
+                    if (r >= w0 && r < w0 + kWQWin) s_q[(tail + r - w0) & (kWQ - 1)] = j | tag;
+                    ++r;
+                }
             }
             __syncwarp();   // the window's entries are queued
             tail += min((uint32_t)kWQWin, total - w0);

@@ -29,9 +29,20 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
                  : "memory");
 }
 // Waits for the phase with parity `parity` to complete; false if the bound ran out.
+__device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity)
+{
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return done != 0;
+}
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
 {
     const unsigned a = smem_addr(bar);
+    if (mbar_try(a, parity)) return true;
     const long long t0 = clock64();
     for (uint32_t it = 0; it < kWaitPolls && clock64() - t0 < kWaitCycles; ++it) {
         unsigned done;

@@ -95,6 +95,22 @@ def test_axis_aligned_cube(hx):
     assert st["fragments"] == 2 * 32 * 32
 
 
+def test_edges_through_sample_centres(hx):
+    """A cube whose projected corners sit on sample centres (orthographic, 64x64):
+    its edges and face diagonals pass through samples, so the top-left rule
+    decides every edge sample (rows' crossings exactly at a column, edges
+    parallel to the rows); each of the two visible faces covers 31 x 31
+    samples, the diagonal's samples once."""
+    h = 0.5 - 1.0 / 64.0
+    v = (np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0], [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]],
+                  np.float32) - 0.5) * (2 * h)
+    mesh = synth.HexMesh(v, np.arange(8, dtype=np.int32).reshape(1, 8), np.array([0.5], np.float32),
+                         np.zeros((1, 12), np.uint8))
+    view = synth.View(eye=(0, 0, 5.0), fovy_deg=0.0, ortho_half_h=1.0, znear=1.0, zfar=9.0, width=64, height=64)
+    st, _ = render_both(hx, mesh, view, synth.Lens(mode=0, center=(32, 32, 0), radius=10.0), synth.Style())
+    assert st["fragments"] == 2 * 31 * 31
+
+
 @pytest.mark.parametrize("depth_order", [True, False])
 def test_long_lists(hx, depth_order):
     """A 1x1x300 column of cells seen along its axis: 301 fragments per pixel,
