@@ -142,7 +142,7 @@ __global__ void k_bin_fill(const FaceFrame* __restrict__ fframe, int64_t n_faces
         for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx) {
                 int tile = ty * tiles_x + tx;
-                uint32_t slot = atomicAdd(tile_cur + tile, 1u);
+                const uint32_t slot = atomicAdd(tile_cur + tile, 1u);
                 bins[tile_off[tile] + slot] = (uint32_t)(2 * f + tri);
             }
     }
@@ -163,8 +163,8 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
                                                   const uint32_t* __restrict__ tzsum, int nb,
                                                   float* __restrict__ tile_zr, uint32_t* __restrict__ tmp)
 {
+    constexpr int kItems = kBinSortMax / 256;   // entries per thread of a list held in registers
     __shared__ uint32_t s_hist[kDepthBucketsMax];
-    __shared__ uint16_t s_b[kBinSortMax];
     __shared__ uint32_t s_out[kBinSortMax];
     __shared__ uint32_t s_red[2][8];
     const int tile = blockIdx.x;
@@ -174,15 +174,34 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
         if (threadIdx.x == 0) tile_zr[tile] = 0.f;
         return;
     }
-    const bool big = n > (uint32_t)kBinSortMax;   // buckets recomputed, scatter through tmp
+    const bool big = n > (uint32_t)kBinSortMax;   // entries re-read, scatter through tmp
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    auto zsum = [&](uint32_t f2t) -> uint32_t { return tzsum[f2t]; };   // sum of the triangle's window depths
-    // depth range of the tile's triangles
+    // a list of up to kBinSortMax entries is read once: entry tid + 256 k of
+    // the list and its triangle's depth sum (sum of the three window depths)
+    // stay in this thread's registers
+    uint32_t f2t[kItems], zs[kItems];
     uint32_t zmin = 0xFFFFFFFFu, zmax = 0;
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const uint32_t zs = zsum(bins[beg + i]);
-        zmin = min(zmin, zs);
-        zmax = max(zmax, zs);
+    if (!big) {
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const uint32_t i = threadIdx.x + 256u * k;
+            f2t[k] = i < n ? bins[beg + i] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const uint32_t i = threadIdx.x + 256u * k;
+            zs[k] = i < n ? tzsum[f2t[k]] : 0u;
+            if (i < n) {
+                zmin = min(zmin, zs[k]);
+                zmax = max(zmax, zs[k]);
+            }
+        }
+    } else {
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t z = tzsum[bins[beg + i]];
+            zmin = min(zmin, z);
+            zmax = max(zmax, z);
+        }
     }
     for (int i = threadIdx.x; i < nb; i += blockDim.x) s_hist[i] = 0;
 #pragma unroll
@@ -197,12 +216,14 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
     for (int w = 1; w < 8; ++w) { zmin = min(zmin, s_red[0][w]); zmax = max(zmax, s_red[1][w]); }
     const float scale = (float)nb / (float)(zmax - zmin + 1);
     if (threadIdx.x == 0) tile_zr[tile] = (float)(zmax - zmin) * (1.f / 50331648.f);   // of 3 * 2^24
-    auto bucket = [&](uint32_t f2t) -> int { return min((int)((float)(zsum(f2t) - zmin) * scale), nb - 1); };
+    auto bucket = [&](uint32_t z) -> int { return min((int)((float)(z - zmin) * scale), nb - 1); };
     // histogram
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const int b = bucket(bins[beg + i]);
-        if (!big) s_b[i] = (uint16_t)b;
-        atomicAdd(&s_hist[b], 1u);
+    if (!big) {
+#pragma unroll
+        for (int k = 0; k < kItems; ++k)
+            if (threadIdx.x + 256u * k < n) atomicAdd(&s_hist[bucket(zs[k])], 1u);
+    } else {
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_hist[bucket(tzsum[bins[beg + i]])], 1u);
     }
     __syncthreads();
     // exclusive scan of the histogram: nb / 256 buckets per thread
@@ -233,14 +254,20 @@ __global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ t
     }
     __syncthreads();
     // scatter (arbitrary order inside a bucket), then write back
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const uint32_t f2t = bins[beg + i];
-        const uint32_t slot = atomicAdd(&s_hist[big ? bucket(f2t) : (int)s_b[i]], 1u);
-        if (big) tmp[beg + slot] = f2t;
-        else s_out[slot] = f2t;
+    if (!big) {
+#pragma unroll
+        for (int k = 0; k < kItems; ++k)
+            if (threadIdx.x + 256u * k < n) s_out[atomicAdd(&s_hist[bucket(zs[k])], 1u)] = f2t[k];
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) bins[beg + i] = s_out[i];
+    } else {
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t f = bins[beg + i];
+            tmp[beg + atomicAdd(&s_hist[bucket(tzsum[f])], 1u)] = f;
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) bins[beg + i] = tmp[beg + i];
     }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) bins[beg + i] = big ? tmp[beg + i] : s_out[i];
 }
 
 // ------------------------------------------------------------------ tile order
