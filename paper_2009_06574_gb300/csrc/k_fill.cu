@@ -275,7 +275,7 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
 // queue order into the warp's region (the 32 lists the count pass sized):
 // chunk by chunk, pixel by pixel within a chunk. The producer fetches the face
 // records of chunk c+1 with cp.async while it sets up chunk c.
-__global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __restrict__ tile_off,
+__global__ void __launch_bounds__(kPipeThreads, 4) k_fill(const uint64_t* __restrict__ tile_off,
                                                           const uint32_t* __restrict__ bins,
                                                           const uint32_t* __restrict__ masks,
                                                           const FaceFrame* __restrict__ fframe,
