@@ -151,7 +151,7 @@ void free_frame(FrameBufs& f)
 {
     dfree(f.vproj); dfree(f.ved); dfree(f.fframe); dfree(f.tzsum);
     dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.tile_order); dfree(f.tile_frag); dfree(f.tile_cap); dfree(f.cap_off); dfree(f.tile_over); dfree(f.tile_zr); dfree(f.cap_x);
-    dfree(f.bins); dfree(f.bins_tmp); dfree(f.masks); dfree(f.cnt);
+    dfree(f.bins); dfree(f.bins_tmp); dfree(f.masks); dfree(f.seg); dfree(f.cnt);
     dfree(f.off);
     dfree(f.part); dfree(f.part_max); dfree(f.long_q); dfree(f.fix_q); dfree(f.key); dfree(f.rgba); dfree(f.scal);
     if (f.h_scal) cudaFreeHost(f.h_scal);
@@ -489,6 +489,7 @@ hexfc_status job_read1(FrameJob& j)
         if ((st = ensure(&fb.bins_tmp, &c1, fb.bin_cap)) != HEXFC_OK) return st;
     }
     if ((st = ensure(&fb.masks, &fb.mask_cap, (int64_t)j.n_bins * (kTilePix / kChunk))) != HEXFC_OK) return st;
+    if ((st = ensure(&fb.seg, &fb.seg_cap, (int64_t)(j.n_bins / kChunk) * (kTilePix / 32))) != HEXFC_OK) return st;
     return HEXFC_OK;
 }
 
@@ -1142,7 +1143,8 @@ hexfc_status hexfc_frame_memory(const hexfc_ctx* ctx, uint64_t* bytes)
     b += (uint64_t)f.v_cap * (sizeof(int4) + sizeof(float));
     b += (uint64_t)f.f_cap * (sizeof(FaceFrame) + 2 * sizeof(uint32_t));
     b += (uint64_t)f.t_cap * (9 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t));
-    b += (uint64_t)f.bin_cap * 2 * sizeof(uint32_t) + (uint64_t)f.mask_cap * sizeof(uint32_t);
+    b += (uint64_t)f.bin_cap * 2 * sizeof(uint32_t) + (uint64_t)f.mask_cap * sizeof(uint32_t) +
+         (uint64_t)f.seg_cap * sizeof(uint64_t);
     b += (uint64_t)f.p_cap * (3 * sizeof(uint32_t) + sizeof(uint64_t));
     b += (uint64_t)f.part_cap * (sizeof(uint64_t) + sizeof(uint32_t));
     b += (uint64_t)f.frag_cap * (sizeof(uint64_t) + sizeof(float4));
@@ -1152,7 +1154,7 @@ hexfc_status hexfc_frame_memory(const hexfc_ctx* ctx, uint64_t* bytes)
         b += (uint64_t)g.v_cap * (sizeof(int4) + sizeof(float)) +
              (uint64_t)g.f_cap * (sizeof(FaceFrame) + 2 * sizeof(uint32_t)) +
              (uint64_t)g.t_cap * (9 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t)) +
-             (uint64_t)(2 * g.bin_cap + g.mask_cap) * sizeof(uint32_t) +
+             (uint64_t)(2 * g.bin_cap + g.mask_cap) * sizeof(uint32_t) + (uint64_t)g.seg_cap * sizeof(uint64_t) +
              (uint64_t)g.p_cap * (3 * sizeof(uint32_t) + sizeof(uint64_t)) +
              (uint64_t)g.part_cap * (sizeof(uint64_t) + sizeof(uint32_t)) +
              (uint64_t)g.frag_cap * (sizeof(uint64_t) + sizeof(float4));
@@ -1519,11 +1521,12 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fb.bins = a.take<uint32_t>((size_t)n_bins);
     fb.bins_tmp = a.take<uint32_t>((size_t)n_bins);
     fb.masks = a.take<uint32_t>((size_t)n_bins * (kTilePix / kChunk));
+    fb.seg = a.take<uint64_t>((size_t)(n_bins / kChunk) * (kTilePix / 32));
     hexfc_frame_stats fs{};
     fs.bin_entries = n_bins;
     fs.width = (uint32_t)W;
     fs.height = (uint32_t)H;
-    if (!fb.bins || !fb.bins_tmp || !fb.masks) {
+    if (!fb.bins || !fb.bins_tmp || !fb.masks || !fb.seg) {
         if (stats) *stats = fs;
         return HEXFC_ERR_OVERFLOW;
     }

@@ -36,17 +36,17 @@ struct CountWarp {
 // 2^-24 M of the exact value. Dividing by fa (rfa within 0.5 ulp, one more
 // rounding of t) moves t by at most tol |rfa| + 2^-22 |t|, and |t| <= 17
 // wherever it matters (columns 0..15): eps = tol |rfa| (1 + 2^-10) + 2^-17.
-__device__ __forceinline__ void stage_fast(CountWarp& me, int j)
+__device__ __forceinline__ void stage_rows(const CovSoA& c, float4 (*ef)[kChunk], int j)
 {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float e0 = i64_to_f32(me.c.e0[k][j]);
-        const float fa = -256.f * (float)me.c.dy[k][j];   // exact: |dy| < 2^24
-        const float fb = 256.f * (float)me.c.dx[k][j];
+        const float e0 = i64_to_f32(c.e0[k][j]);
+        const float fa = -256.f * (float)c.dy[k][j];   // exact: |dy| < 2^24
+        const float fb = 256.f * (float)c.dx[k][j];
         const float tol = ldexpf(fabsf(e0) + 16.f * (fabsf(fa) + fabsf(fb)), -21);
         const float rfa = fa != 0.f ? __frcp_rn(fa) : 0.f;
         const float eps = fa != 0.f ? fmaf(tol * fabsf(rfa), 1.f + 0x1p-10f, 0x1p-17f) : tol;
-        me.ef[k][j] = make_float4(e0, fb, rfa, eps);
+        ef[k][j] = make_float4(e0, fb, rfa, eps);
     }
 }
 
@@ -64,19 +64,20 @@ __device__ __forceinline__ bool edge_in(const CovSoA& c, int k, int j, int64_t A
 // is taken from the float data where it is more than eps from an integer
 // column; near one (or if eps is not small), the column is decided by exact
 // integer tests (a binary search on the monotone edge test).
-__device__ __forceinline__ void row_span(const CountWarp& me, int j, int ry, int bw, int& lo, int& hi)
+__device__ __forceinline__ void row_span(const CovSoA& c, const float4 (*ef)[kChunk], int j, int ry, int bw, int& lo,
+                                         int& hi)
 {
     lo = 0;
     hi = bw - 1;
     const float fry = (float)ry;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float4 f = me.ef[k][j];
+        const float4 f = ef[k][j];
         const float af = fmaf(f.y, fry, f.x);   // edge value at column 0
         if (f.z == 0.f) {   // parallel to the rows: the whole row or nothing
             bool in = af > f.w;
             if (!in && af >= -f.w)
-                in = edge_in(me.c, k, j, me.c.e0[k][j] + (int64_t)me.c.dx[k][j] * (int64_t)(ry << 8), 0);
+                in = edge_in(c, k, j, c.e0[k][j] + (int64_t)c.dx[k][j] * (int64_t)(ry << 8), 0);
             if (!in) hi = -1;
             continue;
         }
@@ -89,12 +90,12 @@ __device__ __forceinline__ void row_span(const CountWarp& me, int j, int ry, int
             b = f.z > 0.f ? (int)fminf(fmaxf(ft + 1.f, 0.f), (float)bw)     // first column inside
                           : (int)fminf(fmaxf(ft, -1.f), (float)(bw - 1));   // last column inside
         } else {
-            const int64_t A = me.c.e0[k][j] + (int64_t)me.c.dx[k][j] * (int64_t)(ry << 8);
+            const int64_t A = c.e0[k][j] + (int64_t)c.dx[k][j] * (int64_t)(ry << 8);
             if (f.z > 0.f) {   // inside from the first column that passes: search [0, bw]
                 int a = 0, z = bw;
                 while (a < z) {
                     const int m = (a + z) >> 1;
-                    if (edge_in(me.c, k, j, A, m)) z = m;
+                    if (edge_in(c, k, j, A, m)) z = m;
                     else a = m + 1;
                 }
                 b = a;
@@ -102,7 +103,7 @@ __device__ __forceinline__ void row_span(const CountWarp& me, int j, int ry, int
                 int a = -1, z = bw - 1;
                 while (a < z) {
                     const int m = (a + z + 1) >> 1;
-                    if (edge_in(me.c, k, j, A, m)) a = m;
+                    if (edge_in(c, k, j, A, m)) a = m;
                     else z = m - 1;
                 }
                 b = a;
@@ -134,7 +135,7 @@ __device__ __forceinline__ void count_chunks(CountWarp* s_w, int warp, int lane,
         if (f2t != kPadBin) {
             TriGeom t;
             stage_cov(a, b, f2t, W, H, px0, py0, me.c, lane, t);
-            if (me.c.box[lane] != 0) stage_fast(me, lane);
+            if (me.c.box[lane] != 0) stage_rows(me.c, me.ef, lane);
         } else {
             me.c.box[lane] = 0;
         }
@@ -167,7 +168,7 @@ __device__ __forceinline__ void count_chunks(CountWarp* s_w, int warp, int lane,
                 const int bx = (int)sq.z;
                 const int ry = (int)(idx - sq.x);
                 int lo, hi;
-                row_span(me, j, ry, box_bw(bx), lo, hi);
+                row_span(me.c, me.ef, j, ry, box_bw(bx), lo, hi);
                 uint32_t* mrow = &me.mask[(box_ly0(bx) + ry) * kTile + box_lx0(bx)];
                 for (int rx = lo; rx <= hi; ++rx) atomicOr(mrow + rx, 1u << j);
             }

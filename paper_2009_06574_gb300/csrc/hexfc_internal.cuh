@@ -128,6 +128,8 @@ struct FrameBufs {
     bool scal_fresh = false;        // scal just allocated (undefined contents)
     int64_t bin_cap = 0;
     uint32_t* masks = nullptr;      // per chunk of a tile list: 256 per-pixel coverage masks
+    uint64_t* seg = nullptr;        // per chunk and warp group of 32 pixels: the first fragment of its records
+    int64_t seg_cap = 0;
     int64_t mask_cap = 0;
     // pixels (tile-major)
     uint32_t* cnt = nullptr;        // [P]

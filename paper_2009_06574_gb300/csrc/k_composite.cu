@@ -5,13 +5,12 @@
 //
 // The paper sorts with a per-pixel priority queue. Here the fill pass visits
 // each tile's triangles in depth order, so every list arrives sorted or nearly
-// sorted. Layout: the lists of a warp's 32 pixels (tile-major pixel order)
-// share one region of the fragment arrays, starting at the offset of the
-// group's first pixel, stored chunk-major: for each chunk of 32 triangles of
-// the tile list, the group's fragments of that chunk, pixel by pixel, each
-// pixel's in list order. A pixel finds its fragments of a chunk from the
-// chunk's coverage masks: its own bit count, after those of the lower pixels
-// of its group. One thread per pixel walks the chunks and streams its list
+// sorted. Layout: for each chunk of 32 triangles of a tile's list and each
+// group of 32 pixels of the tile (a warp, tile-major pixel order), the
+// group's fragments of that chunk are one run of records, pixel by pixel,
+// each pixel's in list order; seg gives the run's first record. A pixel finds
+// its fragments of a chunk from the chunk's coverage masks: its own bit
+// count, after those of the lower pixels of its group. One thread per pixel walks the chunks and streams its list
 // front to back through a small sorted window in registers, checking the
 // order of what it blends; a list the window cannot sort is gathered and
 // resolved by a whole warp: a bitonic network over (key, index) in registers.
@@ -28,6 +27,7 @@ namespace hexfc {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kGroups = kTilePix / 32;   // warp groups of 32 pixels per tile
 constexpr int kWarpList = kWarpSortMax;   // longest list a warp resolves
 
 struct CT { float r, g, b, t; };  // premultiplied colour and transmittance
@@ -179,23 +179,22 @@ __device__ __forceinline__ void tile_pixel(int64_t q, int tiles_x, int& x, int& 
 // fragment index e. Elements past `limit` are skipped.
 template <class F>
 __device__ __forceinline__ void list_walk(const uint64_t* __restrict__ tile_off, const uint32_t* __restrict__ masks,
-                                          const uint64_t* __restrict__ off, uint32_t q, int lane, uint32_t limit,
+                                          const uint64_t* __restrict__ seg, uint32_t q, int lane, uint32_t limit,
                                           F&& f)
 {
-    const uint32_t tile = q / kTilePix, l = q & 31u, g0 = q - l;
+    const uint32_t tile = q / kTilePix, l = q & 31u, g0 = q - l, grp = (g0 % kTilePix) / 32;
     const uint64_t cb = tile_off[tile] / kChunk, ce = tile_off[tile + 1] / kChunk;
     const uint32_t* mp = masks + cb * kTilePix + (g0 % kTilePix) + lane;
-    uint64_t e = off[g0];
     uint32_t k = 0;
     for (uint64_t c = cb; c < ce; ++c, mp += kTilePix) {
         const uint32_t h = __popc(*mp);
         const uint32_t before = __reduce_add_sync(kFull, (uint32_t)lane < l ? h : 0u);
-        const uint32_t total = __reduce_add_sync(kFull, h);
         const uint32_t hl = __shfl_sync(kFull, h, l);
+        if (hl == 0) continue;
+        const uint64_t e = seg[c * kGroups + grp] + before;
         for (uint32_t t = lane; t < hl; t += 32)
-            if (k + t < limit) f(k + t, e + before + t);
+            if (k + t < limit) f(k + t, e + t);
         k += hl;
-        e += total;
     }
 }
 
@@ -210,9 +209,8 @@ __device__ __forceinline__ float4 finish(CT c, float bg0, float bg1, float bg2)
 }
 
 // One block per tile, one thread per pixel: the thread walks the tile's
-// chunks (its group's fragments of each chunk follow those of the chunks
-// before; its own come after those of the lower pixels of the group) and
-// streams its list through a sorted window of KW (key, colour) pairs in
+// chunks (its fragments of a chunk start at the group's run of that chunk,
+// after those of the lower pixels of the group) and streams its list through a sorted window of KW (key, colour) pairs in
 // registers, blending the smallest pair each time the window overflows, so a
 // list whose elements sit at most KW - 1 places from their sorted position
 // comes out sorted. The blend checks that the keys it consumes increase; a
@@ -242,7 +240,7 @@ __device__ __forceinline__ void blend_checked(CT& c, uint64_t& last, bool& ok, c
 
 template <int KW>
 __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ cnt,
-                                                   const uint64_t* __restrict__ off,
+                                                   const uint64_t* __restrict__ seg,
                                                    const uint64_t* __restrict__ tile_off,
                                                    const uint32_t* __restrict__ masks,
                                                    const uint64_t* __restrict__ key,
@@ -257,7 +255,7 @@ __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ 
     const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;
     const uint64_t cb = tile_off[tile] / kChunk;
     const uint32_t n_chunks = (uint32_t)(tile_off[tile + 1] / kChunk - cb);
-    uint64_t e0 = off[q - lane];   // the group's region
+    const uint64_t* sp = seg + cb * kGroups + (threadIdx.x >> 5);   // the group's record of each chunk
     const uint32_t n = cnt[q];
     CT c{0.f, 0.f, 0.f, 1.f};
     bool ok = true;
@@ -269,10 +267,15 @@ __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ 
     for (int k = 0; k < KW; ++k) w[k] = KC{kPad, {}};
     uint32_t seen = 0;
     const uint32_t* mp = masks + cb * kTilePix + threadIdx.x;
-    uint32_t mk_next = n_chunks > 0 ? mp[0] : 0u;
+    uint32_t mk_next = n_chunks > 0 ? mp[0] : 0u;   // the next chunk's mask and record are in flight
+    uint64_t sg_next = n_chunks > 0 ? sp[0] : 0u;
     for (uint32_t ch = 0; ch < n_chunks; ++ch) {
         const uint32_t m = mk_next;
-        if (ch + 1 < n_chunks) mk_next = mp[(uint64_t)(ch + 1) * kTilePix];
+        const uint64_t sg = sg_next;
+        if (ch + 1 < n_chunks) {
+            mk_next = mp[(uint64_t)(ch + 1) * kTilePix];
+            sg_next = sp[(uint64_t)(ch + 1) * kGroups];
+        }
         const uint32_t h = __popc(m);
         uint32_t incl = h;
 #pragma unroll
@@ -280,8 +283,8 @@ __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ 
             const uint32_t t = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += t;
         }
-        const uint64_t e = e0 + incl - h;
-        e0 += __shfl_sync(kFull, incl, 31);
+        if (h == 0) continue;
+        const uint64_t e = sg + incl - h;
         KC nx{};   // the next element is loaded while this one is placed
         if (h > 0) nx = KC{key[e], rgba[e]};
         for (uint32_t t = 0; t < h; ++t) {
@@ -324,7 +327,7 @@ __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ 
 // Out-of-order lists (n <= 256): one warp each, gathered into shared memory
 // and sorted in registers.
 __global__ void __launch_bounds__(256) k_composite_fix(const uint32_t* __restrict__ cnt,
-                                                       const uint64_t* __restrict__ off,
+                                                       const uint64_t* __restrict__ seg,
                                                        const uint64_t* __restrict__ tile_off,
                                                        const uint32_t* __restrict__ masks,
                                                        const uint64_t* __restrict__ key,
@@ -341,7 +344,7 @@ __global__ void __launch_bounds__(256) k_composite_fix(const uint32_t* __restric
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < n_fix; w += warps) {
         const uint32_t q = fix_q[w];
         const uint32_t n = min(cnt[q], (uint32_t)kWarpList);
-        list_walk(tile_off, masks, off, q, lane, n, [&](uint32_t i, uint64_t e) {
+        list_walk(tile_off, masks, seg, q, lane, n, [&](uint32_t i, uint64_t e) {
             b.key[i] = key[e];
             b.rgba[i] = rgba[e];
         });
@@ -383,18 +386,16 @@ __device__ void block_sort(uint64_t* s_k, uint32_t* s_v, uint32_t n, uint32_t np
 // elements' fragment indices (relative to the group's region) in s_e, then the
 // block sorts (key, element) pairs and the first warp composites.
 __device__ CT block_composite(const uint64_t* __restrict__ tile_off, const uint32_t* __restrict__ masks,
-                              const uint64_t* __restrict__ off, const uint64_t* __restrict__ key,
+                              const uint64_t* __restrict__ seg, const uint64_t* __restrict__ key,
                               const float4* __restrict__ rgba, uint32_t q, uint32_t n, uint64_t* s_k, uint32_t* s_v,
-                              uint32_t* s_e, uint64_t* out_key, float4* out_rgba)
+                              uint64_t* s_e, uint64_t* out_key, float4* out_rgba)
 {
     uint32_t np2 = 32;
     while (np2 < n) np2 <<= 1;
-    const uint64_t base = off[q - (q & 31u)];
     if (threadIdx.x < 32)
-        list_walk(tile_off, masks, off, q, (int)threadIdx.x, n,
-                  [&](uint32_t i, uint64_t e) { s_e[i] = (uint32_t)(e - base); });
+        list_walk(tile_off, masks, seg, q, (int)threadIdx.x, n, [&](uint32_t i, uint64_t e) { s_e[i] = e; });
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) { s_k[i] = key[base + s_e[i]]; s_v[i] = i; }
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) { s_k[i] = key[s_e[i]]; s_v[i] = i; }
     __syncthreads();
     block_sort(s_k, s_v, n, np2);
     // first warp: each lane composites a contiguous run of ranks, then an ordered reduction
@@ -405,7 +406,7 @@ __device__ CT block_composite(const uint64_t* __restrict__ tile_off, const uint3
         for (uint32_t j = 0; j < per; ++j) {
             uint32_t rank = lane * per + j;
             if (rank < n) {
-                float4 f = rgba[base + s_e[s_v[rank]]];
+                float4 f = rgba[s_e[s_v[rank]]];
                 c = ct_over(c, CT{f.x, f.y, f.z, 1.f - f.w});
                 if (out_key) { out_key[rank] = s_k[rank]; out_rgba[rank] = f; }
             }
@@ -419,7 +420,7 @@ __device__ CT block_composite(const uint64_t* __restrict__ tile_off, const uint3
 // length is read on the device, so the grid need not match it). A list above
 // HEXFC_MAX_LIST is never drawn; the frame reports it as an overflow.
 __global__ void __launch_bounds__(1024) k_composite_long(const uint32_t* __restrict__ cnt,
-                                                         const uint64_t* __restrict__ off,
+                                                         const uint64_t* __restrict__ seg,
                                                          const uint64_t* __restrict__ tile_off,
                                                          const uint32_t* __restrict__ masks,
                                                          const uint64_t* __restrict__ key,
@@ -431,8 +432,8 @@ __global__ void __launch_bounds__(1024) k_composite_long(const uint32_t* __restr
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* s_k = reinterpret_cast<uint64_t*>(smem);
-    uint32_t* s_v = reinterpret_cast<uint32_t*>(s_k + HEXFC_MAX_LIST);
-    uint32_t* s_e = s_v + HEXFC_MAX_LIST;
+    uint64_t* s_e = s_k + HEXFC_MAX_LIST;
+    uint32_t* s_v = reinterpret_cast<uint32_t*>(s_e + HEXFC_MAX_LIST);
     const unsigned long long total = *n_long;
     for (unsigned long long i = blockIdx.x; i < total; i += gridDim.x) {
         const uint32_t q = long_q[i];
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(1024) k_composite_long(const uint32_t* __restr
         if (n > (uint32_t)HEXFC_MAX_LIST) continue;
         int x, y;
         tile_pixel(q, tiles_x, x, y);
-        CT c = block_composite(tile_off, masks, off, key, rgba, q, n, s_k, s_v, s_e, nullptr, nullptr);
+        CT c = block_composite(tile_off, masks, seg, key, rgba, q, n, s_k, s_v, s_e, nullptr, nullptr);
         if (threadIdx.x == 0) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
         __syncthreads();   // the shared arrays are reused by the next list
     }
@@ -450,7 +451,7 @@ __global__ void __launch_bounds__(1024) k_composite_long(const uint32_t* __restr
 
 // Sorted lists of requested pixels written at dst_off[i], by the same resolve
 // routines as the composite (one warp per pixel for n <= 256).
-__global__ void __launch_bounds__(256) k_debug_short(const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ off,
+__global__ void __launch_bounds__(256) k_debug_short(const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ seg,
                                                      const uint64_t* __restrict__ tile_off,
                                                      const uint32_t* __restrict__ masks,
                                                      const uint64_t* __restrict__ key,
@@ -468,7 +469,7 @@ __global__ void __launch_bounds__(256) k_debug_short(const uint32_t* __restrict_
     int64_t q = ((int64_t)(y / kTile) * tiles_x + x / kTile) * kTilePix + (y % kTile) * kTile + (x % kTile);
     uint32_t n = cnt[q];
     if (n == 0 || n > (uint32_t)kWarpList) return;
-    list_walk(tile_off, masks, off, (uint32_t)q, lane, n, [&](uint32_t k, uint64_t e) {
+    list_walk(tile_off, masks, seg, (uint32_t)q, lane, n, [&](uint32_t k, uint64_t e) {
         b.key[k] = key[e];
         b.rgba[k] = rgba[e];
     });
@@ -476,7 +477,7 @@ __global__ void __launch_bounds__(256) k_debug_short(const uint32_t* __restrict_
     (void)warp_resolve(b.key, b.rgba, n, lane, out_key + dst_off[i], out_rgba + dst_off[i]);
 }
 
-__global__ void __launch_bounds__(1024) k_debug_long(const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ off,
+__global__ void __launch_bounds__(1024) k_debug_long(const uint32_t* __restrict__ cnt, const uint64_t* __restrict__ seg,
                                                      const uint64_t* __restrict__ tile_off,
                                                      const uint32_t* __restrict__ masks,
                                                      const uint64_t* __restrict__ key, const float4* __restrict__ rgba,
@@ -486,14 +487,14 @@ __global__ void __launch_bounds__(1024) k_debug_long(const uint32_t* __restrict_
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* s_k = reinterpret_cast<uint64_t*>(smem);
-    uint32_t* s_v = reinterpret_cast<uint32_t*>(s_k + HEXFC_MAX_LIST);
-    uint32_t* s_e = s_v + HEXFC_MAX_LIST;
+    uint64_t* s_e = s_k + HEXFC_MAX_LIST;
+    uint32_t* s_v = reinterpret_cast<uint32_t*>(s_e + HEXFC_MAX_LIST);
     int64_t i = blockIdx.x;
     int x = px[i], y = py[i];
     int64_t q = ((int64_t)(y / kTile) * tiles_x + x / kTile) * kTilePix + (y % kTile) * kTile + (x % kTile);
     uint32_t n = cnt[q];
     if (n <= (uint32_t)kWarpList || n > (uint32_t)HEXFC_MAX_LIST) return;
-    (void)block_composite(tile_off, masks, off, key, rgba, (uint32_t)q, n, s_k, s_v, s_e, out_key + dst_off[i],
+    (void)block_composite(tile_off, masks, seg, key, rgba, (uint32_t)q, n, s_k, s_v, s_e, out_key + dst_off[i],
                           out_rgba + dst_off[i]);
 }
 
@@ -508,7 +509,7 @@ __global__ void k_debug_counts(const uint32_t* __restrict__ cnt, const int32_t* 
     out[i] = cnt[q];
 }
 
-constexpr size_t kLongSmem = (size_t)HEXFC_MAX_LIST * (sizeof(uint64_t) + 2 * sizeof(uint32_t));
+constexpr size_t kLongSmem = (size_t)HEXFC_MAX_LIST * (2 * sizeof(uint64_t) + sizeof(uint32_t));
 constexpr size_t kFixSmem = 8 * sizeof(WarpList);
 constexpr unsigned kFixBlocks = 4 * 152;   // persistent: warps stride over the queue of out-of-order lists
 constexpr unsigned kLongGridMax = 2 * 152;  // persistent: blocks stride over the queue of long lists
@@ -524,19 +525,19 @@ cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, 
     unsigned long long* fix_cursor = reinterpret_cast<unsigned long long*>(fb.scal + 4);
     const unsigned grid = (unsigned)(n_pix / kTilePix);
     if (window == 8)
-        k_composite<8><<<grid, 256, 0, s>>>(fb.cnt, fb.off, fb.tile_off, fb.masks, fb.key, fb.rgba, tiles_x, W, H,
+        k_composite<8><<<grid, 256, 0, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba, tiles_x, W, H,
                                             sp.bg[0], sp.bg[1], sp.bg[2], o4, fb.long_q, long_cursor, fb.fix_q,
                                             fix_cursor);
     else
-        k_composite<4><<<grid, 256, 0, s>>>(fb.cnt, fb.off, fb.tile_off, fb.masks, fb.key, fb.rgba, tiles_x, W, H,
+        k_composite<4><<<grid, 256, 0, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba, tiles_x, W, H,
                                             sp.bg[0], sp.bg[1], sp.bg[2], o4, fb.long_q, long_cursor, fb.fix_q,
                                             fix_cursor);
-    k_composite_fix<<<kFixBlocks, 256, kFixSmem, s>>>(fb.cnt, fb.off, fb.tile_off, fb.masks, fb.key, fb.rgba,
+    k_composite_fix<<<kFixBlocks, 256, kFixSmem, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
                                                       tiles_x, W, sp.bg[0], sp.bg[1], sp.bg[2], o4, fb.fix_q,
                                                       fix_cursor);
     if (n_long > 0) {   // n_long: the number of long lists if known, else an upper bound on the useful grid
         const unsigned grid = n_long < kLongGridMax ? n_long : kLongGridMax;
-        k_composite_long<<<grid, 1024, kLongSmem, s>>>(fb.cnt, fb.off, fb.tile_off, fb.masks, fb.key, fb.rgba,
+        k_composite_long<<<grid, 1024, kLongSmem, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
                                                        fb.long_q, long_cursor, tiles_x, W, sp.bg[0], sp.bg[1],
                                                        sp.bg[2], o4);
     }
@@ -563,11 +564,11 @@ cudaError_t launch_debug_gather(FrameBufs& fb, const int32_t* d_px, const int32_
     }
     const size_t dsm = 8 * sizeof(WarpList);
     cudaFuncSetAttribute(k_debug_short, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
-    k_debug_short<<<(unsigned)((n * 32 + 255) / 256), 256, dsm, s>>>(fb.cnt, fb.off, fb.tile_off, fb.masks, fb.key,
+    k_debug_short<<<(unsigned)((n * 32 + 255) / 256), 256, dsm, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key,
                                                                     fb.rgba, d_px, d_py, n, d_dst_off, tiles_x,
                                                                     d_keys, d_rgba);
     cudaFuncSetAttribute(k_debug_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSmem);
-    k_debug_long<<<(unsigned)n, 1024, kLongSmem, s>>>(fb.cnt, fb.off, fb.tile_off, fb.masks, fb.key, fb.rgba, d_px,
+    k_debug_long<<<(unsigned)n, 1024, kLongSmem, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba, d_px,
                                                       d_py, d_dst_off, tiles_x, d_keys, d_rgba);
     return cudaGetLastError();
 }

@@ -121,7 +121,7 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
                                           const FaceStatic* __restrict__ fstat, uint64_t beg, uint32_t n_chunks,
                                           int px0, int py0, int W, int H, const ShadeParams& sp,
                                           uint64_t* __restrict__ key, float4* __restrict__ rgba,
-                                          unsigned long long* __restrict__ err)
+                                          uint64_t* __restrict__ seg, unsigned long long* __restrict__ err)
 {
     FillSlot* s_ring = reinterpret_cast<FillSlot*>(smem);                                    // [kRing]
     RawFace* s_raw = reinterpret_cast<RawFace*>(smem + kRawOff);                            // [2][kChunk]
@@ -131,8 +131,23 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
         uint32_t f2t_n = n_chunks > 1 ? bins[beg + kChunk + lane] : kPadBin;
         if (f2t_c != kPadBin) rec_fetch(s_raw[lane], fframe, fstat, f2t_c >> 1);
         cp_async_commit();
+        // the runs of records: lane g < 8 follows group g's region (offset of its
+        // first pixel) chunk by chunk, from the groups' bit counts of the masks
+        const uint32_t* mp = masks + (beg / kChunk) * kTilePix + lane;
+        uint64_t* sgp = seg + (beg / kChunk) * kConsumerWarps + lane;
+        uint64_t run = lane < kConsumerWarps ? s_base[lane * 32] : 0;
         for (uint32_t c = 0; c < n_chunks; ++c) {
             const int s = c % kRing;
+            uint32_t mine = 0;
+#pragma unroll
+            for (int g = 0; g < kConsumerWarps; ++g) {
+                const uint32_t t = __reduce_add_sync(0xffffffffu, __popc(mp[(size_t)c * kTilePix + 32 * g]));
+                mine = lane == g ? t : mine;
+            }
+            if (lane < kConsumerWarps) {
+                sgp[(size_t)c * kConsumerWarps] = run;
+                run += mine;
+            }
             uint32_t f2t_nn = kPadBin;
             if (c + 1 < n_chunks) {
                 if (f2t_n != kPadBin) rec_fetch(s_raw[((c + 1) & 1) * kChunk + lane], fframe, fstat, f2t_n >> 1);
@@ -172,15 +187,15 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
     // e of the warp's queue at region start + e), so every shading round
     // writes 32 consecutive records.
     const uint64_t w_beg = s_base[warp * 32];
-    const uint64_t w_end = w_beg + __reduce_add_sync(0xffffffffu, s_len[p]);
+    const uint32_t w_len = __reduce_add_sync(0xffffffffu, s_len[p]);
     // Queue positions are absolute counts (modulo kWQ): entries [head, tail) are
     // queued. Only whole rounds of 32 entries are shaded; the rest waits for
     // the next chunk unless it would keep an older chunk's slot (then it is
     // shaded as a partial round), so at most the newest chunk's slot is held.
     uint32_t head = 0, tail = 0, released = 0;
     auto shade_entry = [&](uint32_t qe, uint32_t e) {
+        if (!(qe & kCounted) || e >= w_len) return;
         const uint64_t o = w_beg + e;
-        if (!(qe & kCounted) || o >= w_end) return;
         const int j = (int)(qe & 31u);
         const uint32_t pl = (qe >> 5) & 255u;
         const FillSlot& S = s_ring[(qe >> 13) & 3u];
@@ -199,13 +214,14 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
         rgba[o] = col;
     };
     // masks of the next two chunks are in flight while this one is shaded
-    uint32_t mk_a = n_chunks > 0 ? masks[(beg / kChunk) * kTilePix + p] : 0u;
-    uint32_t mk_b = n_chunks > 1 ? masks[(beg / kChunk + 1) * kTilePix + p] : 0u;
+    const uint32_t* mp = masks + (beg / kChunk) * kTilePix + p;             // this pixel's mask of chunk 0
+    uint32_t mk_a = n_chunks > 0 ? mp[0] : 0u;
+    uint32_t mk_b = n_chunks > 1 ? mp[kTilePix] : 0u;
     for (uint32_t c = 0; c < n_chunks; ++c) {
         const int s = c % kRing;
         const uint32_t mk = mk_a;
         mk_a = mk_b;
-        if (c + 2 < n_chunks) mk_b = masks[(beg / kChunk + c + 2) * kTilePix + p];
+        if (c + 2 < n_chunks) mk_b = mp[(size_t)(c + 2) * kTilePix];
         // every entry of the chunks before c - 1 (and of c - 1 if nothing is
         // left over) has been shaded by the whole warp: release their slots
         __syncwarp();
@@ -284,6 +300,7 @@ __global__ void __launch_bounds__(kPipeThreads, 4) k_fill(const uint64_t* __rest
                                                           int H, ShadeParams sp, const uint64_t* __restrict__ off,
                                                           const uint32_t* __restrict__ cnt,
                                                           uint64_t* __restrict__ key, float4* __restrict__ rgba,
+                                                          uint64_t* __restrict__ seg,
                                                           unsigned long long* __restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char fill_smem[];
@@ -301,7 +318,7 @@ __global__ void __launch_bounds__(kPipeThreads, 4) k_fill(const uint64_t* __rest
     }
     pipe_init(s_full, s_empty);
     fill_tile(fill_smem, s_base, s_len, s_full, s_empty, bins, masks, fframe, fstat, beg, n_chunks, px0, py0,
-              W, H, sp, key, rgba, err);
+              W, H, sp, key, rgba, seg, err);
 }
 
 // Per tile, with no separate count pass: the consumer warps rasterise the
@@ -326,6 +343,7 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_count_fill(const uint64_t* 
                                                                uint32_t* __restrict__ tile_frag,
                                                                uint32_t* __restrict__ over,
                                                                uint64_t* __restrict__ key, float4* __restrict__ rgba,
+                                                               uint64_t* __restrict__ seg,
                                                                unsigned long long* __restrict__ scal)
 {
     extern __shared__ __align__(128) unsigned char cf_smem[];
@@ -393,7 +411,7 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_count_fill(const uint64_t* 
     if (!fits) return;
     pipe_init(s_full, s_empty);   // also orders the scan's shared reads before the fill reuses them
     fill_tile(cf_smem, s_base, s_len, s_full, s_empty, bins, masks, fframe, fstat, beg, n_chunks, px0, py0,
-              W, H, sp, key, rgba, scal + 5);
+              W, H, sp, key, rgba, seg, scal + 5);
 }
 
 // Regions for the tiles that did not fit their capacity: after `base`, in
@@ -470,7 +488,7 @@ cudaError_t launch_count_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams
 {
     k_count_fill<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, count_fill_smem_bytes(), s>>>(
         fb.tile_off, fb.bins, fb.masks, fb.fframe, m.fstat, fb.tile_order, tiles_x, W, H, sp, fb.cap_off,
-        (uint64_t)fb.frag_cap, fb.cnt, fb.off, fb.tile_frag, fb.tile_over, fb.key, fb.rgba,
+        (uint64_t)fb.frag_cap, fb.cnt, fb.off, fb.tile_frag, fb.tile_over, fb.key, fb.rgba, fb.seg,
         reinterpret_cast<unsigned long long*>(fb.scal));
     return cudaGetLastError();
 }
@@ -481,7 +499,8 @@ cudaError_t launch_overflow_fill(const DevMesh& m, FrameBufs& fb, const ShadePar
     k_overflow_offsets<<<n_over, kTilePix, 0, s>>>(fb.tile_over, n_over, fb.tile_frag, base, fb.cnt, fb.off);
     k_fill<<<n_over, kPipeThreads, fill_smem_bytes(), s>>>(fb.tile_off, fb.bins, fb.masks, fb.fframe, m.fstat,
                                                             fb.tile_over, tiles_x, W, H, sp, fb.off, fb.cnt, fb.key,
-                                                            fb.rgba, reinterpret_cast<unsigned long long*>(fb.scal + 5));
+                                                            fb.rgba, fb.seg,
+                                                            reinterpret_cast<unsigned long long*>(fb.scal + 5));
     return cudaGetLastError();
 }
 cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W,
@@ -490,7 +509,7 @@ cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, 
     const size_t smem = fill_smem_bytes();
     k_fill<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, smem, s>>>(
         fb.tile_off, fb.bins, fb.masks, fb.fframe, m.fstat, fb.tile_order, tiles_x, W, H, sp, fb.off, fb.cnt, fb.key,
-        fb.rgba, reinterpret_cast<unsigned long long*>(fb.scal + 5));
+        fb.rgba, fb.seg, reinterpret_cast<unsigned long long*>(fb.scal + 5));
     return cudaGetLastError();
 }
 
