@@ -122,7 +122,7 @@ typedef struct hexfc_frame_stats {
     uint32_t kernel_launches;  /* kernels this call launched */
     uint32_t covered_pixels;   /* reserved (0) */
     uint32_t predicted;        /* 1: drawn with chosen tile capacities and no count pass */
-    uint32_t overflow_tiles;   /* tiles above their chosen capacity (the frame was then drawn exactly) */
+    uint32_t overflow_tiles;   /* tiles above their chosen capacity (their lists in the pool) */
     uint64_t capacity;         /* sum of the chosen tile capacities (fragments), 0 if none */
 } hexfc_frame_stats;
 
@@ -325,14 +325,16 @@ hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value);
 /*
  * Predicted capacities (HEXFC_OPT_PREDICTED_CAPACITY != 0; no counterpart in
  * the paper, which sizes its buffers once): the fragment arrays are divided
- * into per-16x16-tile regions of a chosen capacity before the frame, and one
- * fused pass per tile counts the tile's coverage, lays out its lists inside
- * the region and draws them, so there is no separate count pass, no global
- * scan and no host wait between counting and drawing. Capacities come from
- * the previous frame's exact tile counts (mode 1: count * 1.15 + 256) or from
- * the capacity network (mode 2, see hexfc_capacity_*). A frame with a tile
- * above its capacity is drawn again by the exact count-then-fill path, so
- * the image is always exact; stats.overflow_tiles reports it. The first frame
+ * into per-16x16-tile regions of a chosen capacity before the frame,
+ * followed by a pool; after the count pass, the fill lays out each tile's
+ * lists in the tile's region itself (in the pool if they do not fit), so
+ * there is no pixel scan and no host wait between counting and drawing; the
+ * host waits once, at the end of the frame. Capacities come from the
+ * previous frame's exact tile counts (mode 1: count * 1.15 + 256) or from the
+ * capacity network (mode 2, see hexfc_capacity_*); the pool holds 35% of the
+ * previous frame's fragments. stats.overflow_tiles counts the tiles above
+ * their capacity. Only if the pool runs out is the frame drawn again by the
+ * exact count-then-fill path, so the image is always exact. The first frame
  * at a resolution, with no previous counts, is drawn exactly.
  */
 

@@ -150,7 +150,7 @@ void free_mesh(DevMesh* m)
 void free_frame(FrameBufs& f)
 {
     dfree(f.vproj); dfree(f.ved); dfree(f.fframe); dfree(f.tzsum);
-    dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.tile_order); dfree(f.tile_frag); dfree(f.tile_cap); dfree(f.cap_off); dfree(f.tile_over); dfree(f.tile_zr); dfree(f.cap_x);
+    dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.tile_order); dfree(f.tile_frag); dfree(f.tile_cap); dfree(f.cap_off); dfree(f.tile_zr); dfree(f.cap_x);
     dfree(f.bins); dfree(f.bins_tmp); dfree(f.masks); dfree(f.seg); dfree(f.cnt);
     dfree(f.off);
     dfree(f.part); dfree(f.part_max); dfree(f.long_q); dfree(f.fix_q); dfree(f.key); dfree(f.rgba); dfree(f.scal);
@@ -441,8 +441,8 @@ hexfc_status job_alloc(FrameJob& j)
         if ((st = ensure(&fb.part_max, &c1, fb.part_cap)) != HEXFC_OK) return st;
     }
     if (!fb.scal) {
-        if ((st = dalloc(&fb.scal, 16)) != HEXFC_OK) return st;
-        CK(cudaMallocHost((void**)&fb.h_scal, 16 * sizeof(uint64_t)));
+        if ((st = dalloc(&fb.scal, kScal)) != HEXFC_OK) return st;
+        CK(cudaMallocHost((void**)&fb.h_scal, kScal * sizeof(uint64_t)));
         fb.scal_fresh = true;   // contents undefined: phase 1 clears all of it
     }
     return HEXFC_OK;
@@ -458,11 +458,11 @@ hexfc_status job_phase1(FrameJob& j, cudaStream_t s)
     // last passes of a frame are reported by the next call (hexfc_render_host
     // reads them at the end of its own frame)
     if (fb.scal_fresh) {
-        CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * 16, s));
+        CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * kScal, s));
         fb.scal_fresh = false;
     } else {
         CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * 5, s));
-        CK(cudaMemsetAsync(fb.scal + 6, 0, sizeof(uint64_t) * 10, s));
+        CK(cudaMemsetAsync(fb.scal + 6, 0, sizeof(uint64_t) * (kScal - 6), s));
     }
     CK(launch_vertex_setup(*j.m, j.cam, fb, s));
     job_mark(j, 1, s);
@@ -550,7 +550,7 @@ hexfc_status job_phase3(FrameJob& j, cudaStream_t s)
 {
     FrameBufs& fb = *j.fb;
     job_mark(j, 8, s);
-    CK(launch_fill(*j.m, fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, s));
+    CK(launch_fill(*j.m, fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, false, s));
     job_mark(j, 9, s);
     CK(launch_composite(fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, j.out, j.n_long, j.window, s));
     job_mark(j, 10, s);
@@ -600,6 +600,8 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
 
 constexpr float kCapMargin = 0.15f;   // capacity = predicted count * (1 + margin) + pad
 constexpr uint32_t kCapPad = 256;
+constexpr double kCapPool = 0.35;        // pool after the regions, in previous-frame fragments
+constexpr uint64_t kErrPoolBit = 16;     // device error bit: no room for a tile's lists in the pool
 constexpr uint32_t kLongListsUnknown = 1u << 30;   // the long-list pass reads the queue length on the device
 
 // A frame with chosen tile capacities and the fused count-and-fill pass; on
@@ -615,14 +617,14 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     hexfc_status st;
     if ((st = job_alloc(j)) != HEXFC_OK) return st;
     if (!fb.tile_cap || fb.cap_cap < fb.t_cap) {   // capacity arrays follow the tile arrays
-        int64_t c1 = 0, c2 = 0;
-        dfree(fb.cap_off); dfree(fb.tile_over);
+        int64_t c1 = 0;
+        dfree(fb.cap_off);
         if ((st = ensure(&fb.tile_cap, &fb.cap_cap, fb.t_cap)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.cap_off, &c1, fb.cap_cap)) != HEXFC_OK) return st;
-        if ((st = ensure(&fb.tile_over, &c2, fb.cap_cap)) != HEXFC_OK) return st;
     }
-    // fragment arrays for the capacities of this frame (previous counts * margin + pad)
-    const uint64_t want = (uint64_t)((double)ctx->counts_total * (1.0 + kCapMargin) * 1.1) +
+    // fragment arrays for the regions of this frame (previous counts * margin + pad) and a pool
+    // after them for the tiles above their capacity
+    const uint64_t want = (uint64_t)((double)ctx->counts_total * (1.0 + kCapMargin + kCapPool)) +
                           (uint64_t)j.n_tiles * kCapPad;
     if (!fb.key || fb.frag_cap < (int64_t)want) {
         int64_t c1 = 0;
@@ -645,27 +647,34 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     CK(launch_bin_sort(*m, fb, j.tiles_x, j.tiles_y, j.buckets, s));
     CK(launch_tile_order(fb, j.n_tiles, s));
     if ((st = job_features(j, s)) != HEXFC_OK) return st;
-    job_mark(j, 5, s);
+    // stages: bin (with the features, the capacities and their scan), count,
+    // then no pixel scan and no host wait, fill, composite
     if (ctx->predicted == 2) CK(launch_cap_forward(ctx->cap, fb, j.n_tiles, kCapMargin, kCapPad, s));
     else CK(launch_capacity_from_previous(fb, j.n_tiles, kCapMargin, kCapPad, s));
-    job_mark(j, 6, s);
     CK(scan_u32_to_u64(fb.tile_cap, fb.cap_off, j.n_tiles, fb.part, fb.part_max, fb.scal + 11, 0xFFFFFFFFu, s));
+    job_mark(j, 5, s);
+    CK(launch_count(*m, fb, j.tiles_x, j.tiles_y, j.W, j.H, s));
+    job_mark(j, 6, s);
     job_mark(j, 7, s);
-    CK(launch_count_fill(*m, fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, s));
     job_mark(j, 8, s);
-    j.launches += 4 + 1 + 3 + 1;
-    CK(cudaMemcpyAsync(fb.h_scal, fb.scal, 16 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CK(launch_fill(*m, fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, true, s));
+    job_mark(j, 9, s);
+    CK(launch_composite(fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, out, kLongListsUnknown, j.window, s));
+    job_mark(j, 10, s);
+    j.launches += 4 + 1 + 3 + 1 + 1 + 3;
+    CK(cudaMemcpyAsync(fb.h_scal, fb.scal, kScal * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (fb.h_scal[5] != 0) {
-        const uint64_t bits = fb.h_scal[5];
+    const uint64_t bits = fb.h_scal[5];
+    const uint32_t overflow = (uint32_t)fb.h_scal[6];
+    const uint64_t capacity = fb.h_scal[11];
+    if (bits & ~kErrPoolBit) {
         CK(cudaMemsetAsync(fb.scal + 5, 0, sizeof(uint64_t), s));
         return device_error_status(bits);
     }
-    const uint32_t overflow = (uint32_t)fb.h_scal[6];
-    const uint64_t capacity = fb.h_scal[11];
-    if (fb.h_scal[1] > HEXFC_MAX_LIST || capacity + fb.h_scal[14] > (uint64_t)fb.frag_cap) {
-        // a list too long, or no room after the regions for the tiles that did not fit: exact path
-        // (fb.tile_frag already holds this frame's exact counts; k_count rewrites them)
+    if ((bits & kErrPoolBit) || fb.h_scal[17] > HEXFC_MAX_LIST) {
+        // the pool after the regions ran out, or a list is too long: the exact path
+        // draws the frame again (the image above is overwritten)
+        CK(cudaMemsetAsync(fb.scal + 5, 0, sizeof(uint64_t), s));
         st = render_frame(ctx, m, out, stats, s);
         ctx->last.overflow_tiles = overflow;
         ctx->last.capacity = capacity;
@@ -675,21 +684,13 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
         }
         return st;
     }
-    if (overflow > 0) {   // the tiles above their capacity, in regions after all others
-        CK(launch_overflow_fill(*m, fb, j.sp, overflow, capacity, j.tiles_x, j.W, j.H, s));
-        j.launches += 2;
-    }
-    job_mark(j, 9, s);
-    CK(launch_composite(fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, out, kLongListsUnknown, j.window, s));
-    job_mark(j, 10, s);
-    j.launches += 3;
     ctx->ev_pending[ctx->ev_cur] = ctx->timing;
     hexfc_frame_stats& fs = j.fs;
     fs = hexfc_frame_stats{};
-    fs.fragments = fb.h_scal[0];
+    fs.fragments = fb.h_scal[16];   // from the count pass (no pixel scan)
     fs.bin_entries = j.n_bins;
-    fs.max_list = (uint32_t)fb.h_scal[1];
-    fs.long_lists = (uint32_t)fb.h_scal[2];
+    fs.max_list = (uint32_t)fb.h_scal[17];
+    fs.long_lists = (uint32_t)fb.h_scal[18];
     fs.width = (uint32_t)j.W;
     fs.height = (uint32_t)j.H;
     fs.kernel_launches = j.launches;
@@ -1281,7 +1282,8 @@ hexfc_status hexfc_render_host(hexfc_ctx* ctx, int32_t mesh, float* out_rgba_hos
         // the image and this frame's device error bits
         FrameBufs& fb = ctx->fb;
         cudaError_t e = cudaMemcpyAsync(out_rgba_host, d_out, bytes, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(fb.h_scal + 5, fb.scal + 5, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(fb.h_scal + 5, fb.scal + 5, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
             note_cuda(e);
@@ -1501,7 +1503,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fb.fix_q = a.take<uint32_t>((size_t)n_pix + 1);
     fb.part = a.take<uint64_t>(2 * (size_t)nparts);
     fb.part_max = a.take<uint32_t>(2 * (size_t)nparts);
-    fb.scal = a.take<uint64_t>(16);
+    fb.scal = a.take<uint64_t>(kScal);
     if (!fb.vproj || !fb.ved || !fb.fframe || !fb.tzsum || !fb.tile_cnt ||
         !fb.tile_off || !fb.tile_cur || !fb.tile_order || !fb.tile_frag || !fb.tile_zr || !fb.cnt || !fb.off || !fb.long_q || !fb.fix_q || !fb.part || !fb.part_max ||
         !fb.scal)
@@ -1509,7 +1511,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     // the array keeps the previous call's contents: clear what must start at zero
     CK(cudaMemsetAsync(fb.tile_cnt, 0, sizeof(uint32_t) * (size_t)n_tiles, s));
     CK(cudaMemsetAsync(fb.tile_cur, 0, sizeof(uint32_t) * (size_t)n_tiles, s));
-    CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * 16, s));
+    CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * kScal, s));
     CK(launch_vertex_setup(*m, ctx->cam, fb, s));
     CK(launch_face_setup(*m, ctx->cam, ctx->style.lod, ctx->style.delta, fb, tiles_x, tiles_y, s));
     CK(scan_u32_to_u64(fb.tile_cnt, fb.tile_off, n_tiles, fb.part, fb.part_max, fb.scal + 8, 0xFFFFFFFFu, s,
@@ -1538,7 +1540,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     CK(scan_u32_to_u64(fb.cnt, fb.off, n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
     CK(cudaMemcpyAsync(h, fb.scal, 6 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (h[5] != 0) return (h[5] & 6ull) ? HEXFC_ERR_TIMEOUT : HEXFC_ERR_CUDA;
+    if (h[5] != 0) return device_error_status(h[5]);
     const uint64_t total = h[0];
     const uint32_t n_long = (uint32_t)h[2];
     fs.fragments = total;
@@ -1550,8 +1552,9 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fb.key = a.take<uint64_t>((size_t)total + 2);   // the composite widens key copies to 16-byte boundaries
     fb.rgba = a.take<float4>((size_t)total);
     if (!fb.key || !fb.rgba) return HEXFC_ERR_OVERFLOW;
+    fb.frag_cap = (int64_t)total;
     ShadeParams sp = make_shade(ctx);
-    CK(launch_fill(*m, fb, sp, tiles_x, tiles_y, W, H, s));
+    CK(launch_fill(*m, fb, sp, tiles_x, tiles_y, W, H, false, s));
     CK(launch_composite(fb, sp, tiles_x, tiles_y, W, H, out, n_long, ctx->window, s));
     return HEXFC_OK;
 }

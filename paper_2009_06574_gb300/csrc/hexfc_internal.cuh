@@ -58,6 +58,14 @@ struct __align__(64) FaceStatic {
 };
 static_assert(sizeof(FaceFrame) == 64 && sizeof(FaceStatic) == 64, "two sectors each");
 constexpr uint32_t kZ24 = 0xFFFFFFu;
+
+// Device scalars of a frame (FrameBufs::scal): 0-2 pixel scan (fragments,
+// longest list, lists above the warp sort), 3-4 resolve queue cursors (long,
+// out of order), 5 device error bits (kept across frames), 6 tiles above
+// their chosen capacity, 8-10 tile scan (bin entries, ...), 11-13 capacity
+// scan (regions' total, ...), 14 records taken from the pool, 16-18 count
+// pass statistics (fragments, longest list, lists above the warp sort).
+constexpr int kScal = 24;
 __host__ __device__ inline uint32_t face_edge_flags(const uint4& z) { return z.x >> 24; }
 __host__ __device__ inline uint32_t face_tris(const uint4& z) { return (z.y >> 24) & 3u; }
 
@@ -120,7 +128,6 @@ struct FrameBufs {
     float* cap_x = nullptr;         // [4T] capacity-network features of the frame
     uint32_t* tile_cap = nullptr;   // [T+1] chosen fragment capacity per tile (predicted frames)
     uint64_t* cap_off = nullptr;    // [T+1] its exclusive prefix
-    uint32_t* tile_over = nullptr;  // [T+1] tiles above their capacity (drawn after the fused pass)
     int64_t cap_cap = 0;
     int64_t t_cap = 0;
     uint32_t* bins = nullptr;       // face2tri ids grouped by tile, each tile padded to whole chunks
@@ -146,7 +153,7 @@ struct FrameBufs {
     int64_t frag_cap = 0;
     // small device scalars: [0] total fragments, [1] max list, [2] long lists, [3] long queue cursor,
     // [4] out-of-order queue cursor, [5] error bits (kept across frames), [8..10] tile scan totals
-    uint64_t* scal = nullptr;
+    uint64_t* scal = nullptr;       // kScal device scalars (slots: see kScal)
     uint64_t* h_scal = nullptr;     // pinned mirror
 };
 
@@ -171,10 +178,6 @@ cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles
                          cudaStream_t s);
 cudaError_t launch_capacity_from_previous(FrameBufs& fb, int64_t n_tiles, float margin, uint32_t pad,
                                           cudaStream_t s);
-cudaError_t launch_count_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y,
-                              int W, int H, cudaStream_t s);
-cudaError_t launch_overflow_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, uint32_t n_over,
-                                 uint64_t base, int tiles_x, int W, int H, cudaStream_t s);
 cudaError_t launch_cap_features(FrameBufs& fb, int64_t n_tiles, int tiles_x, float lens_x, float lens_y,
                                 float inv_diag, float motion, cudaStream_t s);
 cudaError_t launch_cap_forward(const CapNet& net, FrameBufs& fb, int64_t n_tiles, float margin, uint32_t pad,
@@ -182,8 +185,8 @@ cudaError_t launch_cap_forward(const CapNet& net, FrameBufs& fb, int64_t n_tiles
 cudaError_t launch_cap_grad(CapNet& net, const float* X, const uint32_t* counts, int64_t n, cudaStream_t s);
 cudaError_t launch_cap_adam(CapNet& net, float lr, cudaStream_t s);
 cudaError_t launch_cap_to_half(CapNet& net, cudaStream_t s);
-cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x,
-                        int tiles_y, int W, int H, cudaStream_t s);
+cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W,
+                        int H, bool regions, cudaStream_t s);
 cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W, int H,
                              float* out, uint32_t n_long, int window, cudaStream_t s);
 cudaError_t launch_debug_gather(FrameBufs& fb, const int32_t* d_px, const int32_t* d_py, int64_t n,

@@ -176,11 +176,12 @@ __device__ __forceinline__ void tile_pixel(int64_t q, int tiles_x, int& x, int& 
 
 // The fragments of pixel q, in list order, found by one whole warp (lane i
 // reads the masks of pixel i of q's group): f(i, e) for list element i at
-// fragment index e. Elements past `limit` are skipped.
+// fragment index e. Elements past `limit`, or at an index past frag_cap
+// (inconsistent runs), are skipped.
 template <class F>
 __device__ __forceinline__ void list_walk(const uint64_t* __restrict__ tile_off, const uint32_t* __restrict__ masks,
-                                          const uint64_t* __restrict__ seg, uint32_t q, int lane, uint32_t limit,
-                                          F&& f)
+                                          const uint64_t* __restrict__ seg, uint64_t frag_cap, uint32_t q, int lane,
+                                          uint32_t limit, F&& f)
 {
     const uint32_t tile = q / kTilePix, l = q & 31u, g0 = q - l, grp = (g0 % kTilePix) / 32;
     const uint64_t cb = tile_off[tile] / kChunk, ce = tile_off[tile + 1] / kChunk;
@@ -193,7 +194,7 @@ __device__ __forceinline__ void list_walk(const uint64_t* __restrict__ tile_off,
         if (hl == 0) continue;
         const uint64_t e = seg[c * kGroups + grp] + before;
         for (uint32_t t = lane; t < hl; t += 32)
-            if (k + t < limit) f(k + t, e + t);
+            if (k + t < limit && e + t < frag_cap) f(k + t, e + t);   // (records beyond the arrays: skipped)
         k += hl;
     }
 }
@@ -210,10 +211,10 @@ __device__ __forceinline__ float4 finish(CT c, float bg0, float bg1, float bg2)
 
 // One block per tile, one thread per pixel: the thread walks the tile's
 // chunks (its fragments of a chunk start at the group's run of that chunk,
-// after those of the lower pixels of the group) and streams its list through a sorted window of KW (key, colour) pairs in
-// registers, blending the smallest pair each time the window overflows, so a
-// list whose elements sit at most KW - 1 places from their sorted position
-// comes out sorted. The blend checks that the keys it consumes increase; a
+// after those of the lower pixels of the group) and streams its list through
+// a sorted window of KW (key, colour) pairs in registers, blending the
+// smallest pair each time the window overflows, so a list whose elements sit
+// at most KW - 1 places from their sorted position comes out sorted. The blend checks that the keys it consumes increase; a
 // list that breaks that is queued for the warp-wide resolve of
 // k_composite_fix, or, if longer than 256, for the block-wide sort of
 // k_composite_long. KW (4 or 8) trades registers for fewer queued lists; the
@@ -244,8 +245,9 @@ __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ 
                                                    const uint64_t* __restrict__ tile_off,
                                                    const uint32_t* __restrict__ masks,
                                                    const uint64_t* __restrict__ key,
-                                                   const float4* __restrict__ rgba, int tiles_x, int W, int H,
-                                                   float bg0, float bg1, float bg2, float4* __restrict__ out,
+                                                   const float4* __restrict__ rgba, uint64_t frag_cap, int tiles_x,
+                                                   int W, int H, float bg0, float bg1, float bg2,
+                                                   float4* __restrict__ out,
                                                    uint32_t* __restrict__ long_q,
                                                    unsigned long long* __restrict__ long_cursor,
                                                    uint32_t* __restrict__ fix_q,
@@ -285,6 +287,10 @@ __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ 
         }
         if (h == 0) continue;
         const uint64_t e = sg + incl - h;
+        if (e + h > frag_cap) {   // inconsistent run: not read (the list is sent to the checked resolve)
+            ok = false;
+            continue;
+        }
         KC nx{};   // the next element is loaded while this one is placed
         if (h > 0) nx = KC{key[e], rgba[e]};
         for (uint32_t t = 0; t < h; ++t) {
@@ -331,9 +337,9 @@ __global__ void __launch_bounds__(256) k_composite_fix(const uint32_t* __restric
                                                        const uint64_t* __restrict__ tile_off,
                                                        const uint32_t* __restrict__ masks,
                                                        const uint64_t* __restrict__ key,
-                                                       const float4* __restrict__ rgba, int tiles_x, int W,
-                                                       float bg0, float bg1, float bg2, float4* __restrict__ out,
-                                                       const uint32_t* __restrict__ fix_q,
+                                                       const float4* __restrict__ rgba, uint64_t frag_cap,
+                                                       int tiles_x, int W, float bg0, float bg1, float bg2,
+                                                       float4* __restrict__ out, const uint32_t* __restrict__ fix_q,
                                                        const unsigned long long* __restrict__ fix_cursor)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -344,7 +350,7 @@ __global__ void __launch_bounds__(256) k_composite_fix(const uint32_t* __restric
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; w < n_fix; w += warps) {
         const uint32_t q = fix_q[w];
         const uint32_t n = min(cnt[q], (uint32_t)kWarpList);
-        list_walk(tile_off, masks, seg, q, lane, n, [&](uint32_t i, uint64_t e) {
+        list_walk(tile_off, masks, seg, frag_cap, q, lane, n, [&](uint32_t i, uint64_t e) {
             b.key[i] = key[e];
             b.rgba[i] = rgba[e];
         });
@@ -386,14 +392,18 @@ __device__ void block_sort(uint64_t* s_k, uint32_t* s_v, uint32_t n, uint32_t np
 // elements' fragment indices (relative to the group's region) in s_e, then the
 // block sorts (key, element) pairs and the first warp composites.
 __device__ CT block_composite(const uint64_t* __restrict__ tile_off, const uint32_t* __restrict__ masks,
-                              const uint64_t* __restrict__ seg, const uint64_t* __restrict__ key,
+                              const uint64_t* __restrict__ seg, uint64_t frag_cap, const uint64_t* __restrict__ key,
                               const float4* __restrict__ rgba, uint32_t q, uint32_t n, uint64_t* s_k, uint32_t* s_v,
                               uint64_t* s_e, uint64_t* out_key, float4* out_rgba)
 {
     uint32_t np2 = 32;
     while (np2 < n) np2 <<= 1;
-    if (threadIdx.x < 32)
-        list_walk(tile_off, masks, seg, q, (int)threadIdx.x, n, [&](uint32_t i, uint64_t e) { s_e[i] = e; });
+    if (threadIdx.x < 32) {
+        for (uint32_t i = threadIdx.x; i < n; i += 32) s_e[i] = 0;   // elements a walk may skip
+        __syncwarp();
+        list_walk(tile_off, masks, seg, frag_cap, q, (int)threadIdx.x, n,
+                  [&](uint32_t i, uint64_t e) { s_e[i] = e; });
+    }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) { s_k[i] = key[s_e[i]]; s_v[i] = i; }
     __syncthreads();
@@ -424,7 +434,7 @@ __global__ void __launch_bounds__(1024) k_composite_long(const uint32_t* __restr
                                                          const uint64_t* __restrict__ tile_off,
                                                          const uint32_t* __restrict__ masks,
                                                          const uint64_t* __restrict__ key,
-                                                         const float4* __restrict__ rgba,
+                                                         const float4* __restrict__ rgba, uint64_t frag_cap,
                                                          const uint32_t* __restrict__ long_q,
                                                          const unsigned long long* __restrict__ n_long,
                                                          int tiles_x, int W, float bg0, float bg1, float bg2,
@@ -441,7 +451,7 @@ __global__ void __launch_bounds__(1024) k_composite_long(const uint32_t* __restr
         if (n > (uint32_t)HEXFC_MAX_LIST) continue;
         int x, y;
         tile_pixel(q, tiles_x, x, y);
-        CT c = block_composite(tile_off, masks, seg, key, rgba, q, n, s_k, s_v, s_e, nullptr, nullptr);
+        CT c = block_composite(tile_off, masks, seg, frag_cap, key, rgba, q, n, s_k, s_v, s_e, nullptr, nullptr);
         if (threadIdx.x == 0) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
         __syncthreads();   // the shared arrays are reused by the next list
     }
@@ -455,7 +465,8 @@ __global__ void __launch_bounds__(256) k_debug_short(const uint32_t* __restrict_
                                                      const uint64_t* __restrict__ tile_off,
                                                      const uint32_t* __restrict__ masks,
                                                      const uint64_t* __restrict__ key,
-                                                     const float4* __restrict__ rgba, const int32_t* __restrict__ px,
+                                                     const float4* __restrict__ rgba, uint64_t frag_cap,
+                                                     const int32_t* __restrict__ px,
                                                      const int32_t* __restrict__ py, int64_t n_req,
                                                      const uint64_t* __restrict__ dst_off, int tiles_x,
                                                      uint64_t* __restrict__ out_key, float4* __restrict__ out_rgba)
@@ -469,7 +480,7 @@ __global__ void __launch_bounds__(256) k_debug_short(const uint32_t* __restrict_
     int64_t q = ((int64_t)(y / kTile) * tiles_x + x / kTile) * kTilePix + (y % kTile) * kTile + (x % kTile);
     uint32_t n = cnt[q];
     if (n == 0 || n > (uint32_t)kWarpList) return;
-    list_walk(tile_off, masks, seg, (uint32_t)q, lane, n, [&](uint32_t k, uint64_t e) {
+    list_walk(tile_off, masks, seg, frag_cap, (uint32_t)q, lane, n, [&](uint32_t k, uint64_t e) {
         b.key[k] = key[e];
         b.rgba[k] = rgba[e];
     });
@@ -481,7 +492,8 @@ __global__ void __launch_bounds__(1024) k_debug_long(const uint32_t* __restrict_
                                                      const uint64_t* __restrict__ tile_off,
                                                      const uint32_t* __restrict__ masks,
                                                      const uint64_t* __restrict__ key, const float4* __restrict__ rgba,
-                                                     const int32_t* __restrict__ px, const int32_t* __restrict__ py,
+                                                     uint64_t frag_cap, const int32_t* __restrict__ px,
+                                                     const int32_t* __restrict__ py,
                                                      const uint64_t* __restrict__ dst_off, int tiles_x,
                                                      uint64_t* __restrict__ out_key, float4* __restrict__ out_rgba)
 {
@@ -494,8 +506,8 @@ __global__ void __launch_bounds__(1024) k_debug_long(const uint32_t* __restrict_
     int64_t q = ((int64_t)(y / kTile) * tiles_x + x / kTile) * kTilePix + (y % kTile) * kTile + (x % kTile);
     uint32_t n = cnt[q];
     if (n <= (uint32_t)kWarpList || n > (uint32_t)HEXFC_MAX_LIST) return;
-    (void)block_composite(tile_off, masks, seg, key, rgba, (uint32_t)q, n, s_k, s_v, s_e, out_key + dst_off[i],
-                          out_rgba + dst_off[i]);
+    (void)block_composite(tile_off, masks, seg, frag_cap, key, rgba, (uint32_t)q, n, s_k, s_v, s_e,
+                          out_key + dst_off[i], out_rgba + dst_off[i]);
 }
 
 __global__ void k_debug_counts(const uint32_t* __restrict__ cnt, const int32_t* __restrict__ px,
@@ -525,21 +537,21 @@ cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, 
     unsigned long long* fix_cursor = reinterpret_cast<unsigned long long*>(fb.scal + 4);
     const unsigned grid = (unsigned)(n_pix / kTilePix);
     if (window == 8)
-        k_composite<8><<<grid, 256, 0, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba, tiles_x, W, H,
-                                            sp.bg[0], sp.bg[1], sp.bg[2], o4, fb.long_q, long_cursor, fb.fix_q,
-                                            fix_cursor);
+        k_composite<8><<<grid, 256, 0, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
+                                            (uint64_t)fb.frag_cap, tiles_x, W, H, sp.bg[0], sp.bg[1], sp.bg[2], o4,
+                                            fb.long_q, long_cursor, fb.fix_q, fix_cursor);
     else
-        k_composite<4><<<grid, 256, 0, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba, tiles_x, W, H,
-                                            sp.bg[0], sp.bg[1], sp.bg[2], o4, fb.long_q, long_cursor, fb.fix_q,
-                                            fix_cursor);
+        k_composite<4><<<grid, 256, 0, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
+                                            (uint64_t)fb.frag_cap, tiles_x, W, H, sp.bg[0], sp.bg[1], sp.bg[2], o4,
+                                            fb.long_q, long_cursor, fb.fix_q, fix_cursor);
     k_composite_fix<<<kFixBlocks, 256, kFixSmem, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
-                                                      tiles_x, W, sp.bg[0], sp.bg[1], sp.bg[2], o4, fb.fix_q,
-                                                      fix_cursor);
+                                                      (uint64_t)fb.frag_cap, tiles_x, W, sp.bg[0], sp.bg[1],
+                                                      sp.bg[2], o4, fb.fix_q, fix_cursor);
     if (n_long > 0) {   // n_long: the number of long lists if known, else an upper bound on the useful grid
         const unsigned grid = n_long < kLongGridMax ? n_long : kLongGridMax;
         k_composite_long<<<grid, 1024, kLongSmem, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
-                                                       fb.long_q, long_cursor, tiles_x, W, sp.bg[0], sp.bg[1],
-                                                       sp.bg[2], o4);
+                                                       (uint64_t)fb.frag_cap, fb.long_q, long_cursor, tiles_x, W,
+                                                       sp.bg[0], sp.bg[1], sp.bg[2], o4);
     }
     return cudaGetLastError();
 }
@@ -565,10 +577,11 @@ cudaError_t launch_debug_gather(FrameBufs& fb, const int32_t* d_px, const int32_
     const size_t dsm = 8 * sizeof(WarpList);
     cudaFuncSetAttribute(k_debug_short, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
     k_debug_short<<<(unsigned)((n * 32 + 255) / 256), 256, dsm, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key,
-                                                                    fb.rgba, d_px, d_py, n, d_dst_off, tiles_x,
-                                                                    d_keys, d_rgba);
+                                                                    fb.rgba, (uint64_t)fb.frag_cap, d_px, d_py, n,
+                                                                    d_dst_off, tiles_x, d_keys, d_rgba);
     cudaFuncSetAttribute(k_debug_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSmem);
-    k_debug_long<<<(unsigned)n, 1024, kLongSmem, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba, d_px,
+    k_debug_long<<<(unsigned)n, 1024, kLongSmem, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
+                                                      (uint64_t)fb.frag_cap, d_px,
                                                       d_py, d_dst_off, tiles_x, d_keys, d_rgba);
     return cudaGetLastError();
 }

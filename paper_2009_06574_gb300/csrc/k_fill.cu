@@ -3,8 +3,9 @@
 //   k_fill          per tile: every covered sample (from the count pass's
 //                   masks) gets its exact depth, is shaded with Eqs. 1-4 and
 //                   written into its warp's region of the fragment arrays.
-//   k_count_fill    per tile, with capacities chosen before the frame: count
-//                   and fill in one pass (no separate count, no global scan).
+//                   With capacities chosen before the frame, k_fill lays
+//                   out each tile's lists in the tile's region itself (no
+//                   pixel scan, no host wait between count and fill).
 //
 // Each face is drawn as two triangles (Section "Method Overview"; Section "GPU
 // Implementation"), all covered samples are kept (per-pixel fragment lists,
@@ -102,6 +103,7 @@ struct FillSlot {
 constexpr int kWQ = 256;               // entries per consumer warp (a power of two)
 constexpr int kWQWin = kWQ - 32;       // entries queued per window: fewer than 32 leftovers + a window fit
 constexpr uint32_t kCounted = 1u << 15;  // the count pass sized the sample's list for it
+constexpr unsigned long long kErrPool = 16ull;   // error bit: no room for a tile's lists (chosen capacities)
 static_assert(kRing <= 4, "two bits of ring slot");
 
 constexpr size_t kRawOff = (kRing * sizeof(FillSlot) + 127) & ~(size_t)127;   // face records: 128-aligned
@@ -293,162 +295,86 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
 // records of chunk c+1 with cp.async while it sets up chunk c.
 __global__ void __launch_bounds__(kPipeThreads, 4) k_fill(const uint64_t* __restrict__ tile_off,
                                                           const uint32_t* __restrict__ bins,
-                                                          const uint32_t* __restrict__ masks,
+                                                          uint32_t* __restrict__ masks,
                                                           const FaceFrame* __restrict__ fframe,
                                                           const FaceStatic* __restrict__ fstat,
                                                           const uint32_t* __restrict__ order, int tiles_x, int W,
                                                           int H, ShadeParams sp, const uint64_t* __restrict__ off,
-                                                          const uint32_t* __restrict__ cnt,
+                                                          uint32_t* __restrict__ cnt,
                                                           uint64_t* __restrict__ key, float4* __restrict__ rgba,
                                                           uint64_t* __restrict__ seg,
-                                                          unsigned long long* __restrict__ err)
+                                                          unsigned long long* __restrict__ err,
+                                                          const uint64_t* __restrict__ cap_off, int n_tiles,
+                                                          uint64_t frag_cap, unsigned long long* __restrict__ scal)
 {
     extern __shared__ __align__(128) unsigned char fill_smem[];
     __shared__ uint64_t s_base[kTilePix];
     __shared__ uint32_t s_len[kTilePix];
+    __shared__ uint32_t s_wsum[kConsumerWarps];
+    __shared__ uint64_t s_tile_base;
     __shared__ __align__(8) uint64_t s_full[kRing], s_empty[kRing];
     const int tile = (int)order[blockIdx.x];
     const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
     const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
     const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
-    if (threadIdx.x < kTilePix) {
-        const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;
-        s_base[threadIdx.x] = off[q];
-        s_len[threadIdx.x] = cnt[q];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;
+    if (!cap_off) {   // offsets from the pixel scan
+        if (threadIdx.x < kTilePix) {
+            s_base[threadIdx.x] = off[q];
+            s_len[threadIdx.x] = cnt[q];
+        }
+    } else {
+        // capacities chosen before the frame: the tile's lists are laid out in its
+        // region [cap_off[t], cap_off[t+1]), or in the pool after all regions
+        // (scal[14] records taken, scal[6] tiles) if they do not fit; with no
+        // room left there the tile is not drawn (error bit kErrPool)
+        uint32_t n = 0, incl = 0;
+        if (threadIdx.x < kTilePix) {
+            n = cnt[q];
+            incl = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) s_wsum[warp] = incl;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint64_t total = 0;
+            for (int w = 0; w < kConsumerWarps; ++w) total += s_wsum[w];
+            const uint64_t region = cap_off[tile];
+            uint64_t b = region;
+            if (region + total > cap_off[tile + 1] || region + total > frag_cap) {
+                const uint64_t p = atomicAdd(&scal[14], (unsigned long long)total);
+                atomicAdd(&scal[6], 1ull);
+                b = cap_off[n_tiles] + p;
+                if (b + total > frag_cap) {
+                    atomicOr(err, kErrPool);
+                    b = ~0ull;
+                }
+            }
+            s_tile_base = b;
+        }
+        __syncthreads();
+        if (s_tile_base == ~0ull) {   // no room: the frame is drawn again exactly
+            // the resolve must find no fragment here: clear the tile's masks and counts
+            uint32_t* mt = masks + (beg / kChunk) * kTilePix;
+            for (uint32_t i = threadIdx.x; i < n_chunks * kTilePix; i += blockDim.x) mt[i] = 0u;
+            if (threadIdx.x < kTilePix) cnt[q] = 0u;
+            return;
+        }
+        if (threadIdx.x < kTilePix) {
+            uint32_t pre = 0;
+            for (int w = 0; w < warp; ++w) pre += s_wsum[w];
+            s_base[threadIdx.x] = s_tile_base + pre + incl - n;
+            s_len[threadIdx.x] = n;
+        }
     }
     pipe_init(s_full, s_empty);
     fill_tile(fill_smem, s_base, s_len, s_full, s_empty, bins, masks, fframe, fstat, beg, n_chunks, px0, py0,
               W, H, sp, key, rgba, seg, err);
-}
-
-// Per tile, with no separate count pass: the consumer warps rasterise the
-// tile's chunks into masks and per-pixel counts (as k_count), the block scans
-// the counts into offsets inside the tile's region [cap_off[t], cap_off[t+1])
-// of the fragment arrays (capacities chosen before the frame), and if the
-// tile fits, the fill pipeline draws it. A tile that does not fit draws
-// nothing: it appends itself to `over` (scal[6] tiles, scal[14] fragments)
-// with its exact counts and masks in place, for k_fill to draw once it has a
-// region. tile_frag = the tile's exact total; scal[0] += fragments, scal[1] =
-// max list, scal[2] += lists longer than kWarpSortMax.
-__global__ void __launch_bounds__(kPipeThreads, 3) k_count_fill(const uint64_t* __restrict__ tile_off,
-                                                               const uint32_t* __restrict__ bins,
-                                                               uint32_t* __restrict__ masks,
-                                                               const FaceFrame* __restrict__ fframe,
-                                                               const FaceStatic* __restrict__ fstat,
-                                                               const uint32_t* __restrict__ order, int tiles_x,
-                                                               int W, int H, ShadeParams sp,
-                                                               const uint64_t* __restrict__ cap_off,
-                                                               uint64_t frag_cap, uint32_t* __restrict__ cnt,
-                                                               uint64_t* __restrict__ off,
-                                                               uint32_t* __restrict__ tile_frag,
-                                                               uint32_t* __restrict__ over,
-                                                               uint64_t* __restrict__ key, float4* __restrict__ rgba,
-                                                               uint64_t* __restrict__ seg,
-                                                               unsigned long long* __restrict__ scal)
-{
-    extern __shared__ __align__(128) unsigned char cf_smem[];
-    __shared__ uint64_t s_base[kTilePix];
-    __shared__ uint32_t s_len[kTilePix];
-    __shared__ uint32_t s_wsum[kConsumerWarps];
-    __shared__ uint32_t s_wmax[kConsumerWarps], s_wlong[kConsumerWarps];
-    __shared__ __align__(8) uint64_t s_full[kRing], s_empty[kRing];
-    const int tile = (int)order[blockIdx.x];
-    const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
-    const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
-    const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    CountWarp* s_w = reinterpret_cast<CountWarp*>(cf_smem);
-    if (warp < kConsumerWarps) count_chunks(s_w, warp, lane, bins, fframe, beg, n_chunks, px0, py0, W, H, masks);
-    __syncthreads();
-    // the per-pixel counts, their block-wide exclusive scan, maximum and long lists
-    uint32_t n = 0;
-    if (warp < kConsumerWarps)
-#pragma unroll
-        for (int w = 0; w < kConsumerWarps; ++w) n += s_w[w].mask[threadIdx.x];
-    uint32_t incl = n, mx = n, lg = n > (uint32_t)kWarpSortMax ? 1u : 0u;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        lg += __shfl_xor_sync(0xffffffffu, lg, o);
-    }
-    if (lane == 31 && warp < kConsumerWarps) {
-        s_wsum[warp] = incl;
-        s_wmax[warp] = mx;
-        s_wlong[warp] = lg;
-    }
-    __syncthreads();
-    uint32_t base = 0, total = 0, tmax = 0, tlong = 0;
-#pragma unroll
-    for (int w = 0; w < kConsumerWarps; ++w) {
-        const uint32_t v = s_wsum[w];
-        base += w < warp ? v : 0u;
-        total += v;
-        tmax = max(tmax, s_wmax[w]);
-        tlong += s_wlong[w];
-    }
-    const uint64_t region = cap_off[tile], cap = cap_off[tile + 1] - region;
-    const bool fits = total <= cap && region + total <= frag_cap;   // the same on every thread
-    if (warp < kConsumerWarps) {
-        const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;
-        const uint64_t o = region + base + incl - n;
-        cnt[q] = n;        // also for a tile that does not fit: its lists are drawn later
-        off[q] = o;
-        s_base[threadIdx.x] = o;
-        s_len[threadIdx.x] = n;
-    }
-    if (threadIdx.x == 0) {
-        tile_frag[tile] = total;
-        atomicAdd(&scal[0], (unsigned long long)total);
-        atomicMax(&scal[1], (unsigned long long)tmax);
-        atomicAdd(&scal[2], (unsigned long long)tlong);
-        if (!fits) {
-            over[atomicAdd(&scal[6], 1ull)] = (uint32_t)tile;
-            atomicAdd(&scal[14], (unsigned long long)total);
-        }
-    }
-    if (!fits) return;
-    pipe_init(s_full, s_empty);   // also orders the scan's shared reads before the fill reuses them
-    fill_tile(cf_smem, s_base, s_len, s_full, s_empty, bins, masks, fframe, fstat, beg, n_chunks, px0, py0,
-              W, H, sp, key, rgba, seg, scal + 5);
-}
-
-// Regions for the tiles that did not fit their capacity: after `base`, in
-// the order of the list, sized by their exact totals; then the pixels' list
-// offsets inside them (one block per listed tile).
-__global__ void __launch_bounds__(kTilePix) k_overflow_offsets(const uint32_t* __restrict__ over, uint32_t n_over,
-                                                               const uint32_t* __restrict__ tile_frag, uint64_t base,
-                                                               const uint32_t* __restrict__ cnt,
-                                                               uint64_t* __restrict__ off)
-{
-    __shared__ uint32_t s_w[kConsumerWarps];
-    __shared__ unsigned long long s_region;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t i = blockIdx.x;
-    // the tile's region: base + the totals of the tiles listed before it
-    unsigned long long acc = 0;
-    for (uint32_t k = threadIdx.x; k < i; k += blockDim.x) acc += tile_frag[over[k]];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (threadIdx.x == 0) s_region = 0;
-    __syncthreads();
-    if (lane == 0) atomicAdd(&s_region, acc);
-    // the pixels' exclusive scan inside the tile
-    const uint32_t tile = over[i];
-    const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;
-    const uint32_t n = cnt[q];
-    uint32_t incl = n;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    uint32_t pre = incl - n;
-    for (int w = 0; w < warp; ++w) pre += s_w[w];
-    off[q] = base + s_region + pre;
 }
 
 // Capacities from the previous frame's exact tile counts: prev * (1 + margin) + pad.
@@ -460,21 +386,11 @@ __global__ void k_capacity_from_previous(const uint32_t* __restrict__ prev, int6
     cap[t] = (uint32_t)fminf((float)prev[t] * (1.f + margin) + (float)pad, 4.0e9f);
 }
 
-constexpr size_t count_fill_smem_bytes()
-{
-    return kConsumerWarps * sizeof(CountWarp) > fill_smem_bytes() ? kConsumerWarps * sizeof(CountWarp)
-                                                                     : fill_smem_bytes();
-}
-
 }  // namespace
 
 cudaError_t prepare_fill_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem_bytes());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_count_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)count_fill_smem_bytes());
-    return e;
+    return cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem_bytes());
 }
 
 cudaError_t launch_capacity_from_previous(FrameBufs& fb, int64_t n_tiles, float margin, uint32_t pad, cudaStream_t s)
@@ -483,33 +399,14 @@ cudaError_t launch_capacity_from_previous(FrameBufs& fb, int64_t n_tiles, float 
     return cudaGetLastError();
 }
 
-cudaError_t launch_count_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W,
-                              int H, cudaStream_t s)
-{
-    k_count_fill<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, count_fill_smem_bytes(), s>>>(
-        fb.tile_off, fb.bins, fb.masks, fb.fframe, m.fstat, fb.tile_order, tiles_x, W, H, sp, fb.cap_off,
-        (uint64_t)fb.frag_cap, fb.cnt, fb.off, fb.tile_frag, fb.tile_over, fb.key, fb.rgba, fb.seg,
-        reinterpret_cast<unsigned long long*>(fb.scal));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_overflow_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, uint32_t n_over,
-                                 uint64_t base, int tiles_x, int W, int H, cudaStream_t s)
-{
-    k_overflow_offsets<<<n_over, kTilePix, 0, s>>>(fb.tile_over, n_over, fb.tile_frag, base, fb.cnt, fb.off);
-    k_fill<<<n_over, kPipeThreads, fill_smem_bytes(), s>>>(fb.tile_off, fb.bins, fb.masks, fb.fframe, m.fstat,
-                                                            fb.tile_over, tiles_x, W, H, sp, fb.off, fb.cnt, fb.key,
-                                                            fb.rgba, fb.seg,
-                                                            reinterpret_cast<unsigned long long*>(fb.scal + 5));
-    return cudaGetLastError();
-}
 cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W,
-                        int H, cudaStream_t s)
+                        int H, bool regions, cudaStream_t s)
 {
     const size_t smem = fill_smem_bytes();
     k_fill<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, smem, s>>>(
         fb.tile_off, fb.bins, fb.masks, fb.fframe, m.fstat, fb.tile_order, tiles_x, W, H, sp, fb.off, fb.cnt, fb.key,
-        fb.rgba, fb.seg, reinterpret_cast<unsigned long long*>(fb.scal + 5));
+        fb.rgba, fb.seg, reinterpret_cast<unsigned long long*>(fb.scal + 5), regions ? fb.cap_off : nullptr,
+        tiles_x * tiles_y, (uint64_t)fb.frag_cap, reinterpret_cast<unsigned long long*>(fb.scal));
     return cudaGetLastError();
 }
 
