@@ -504,7 +504,7 @@ hexfc_status job_phase2(FrameJob& j, cudaStream_t s)
     hexfc_status fst = job_features(j, s);
     if (fst != HEXFC_OK) return fst;
     job_mark(j, 5, s);
-    CK(launch_count(*j.m, fb, j.tiles_x, j.tiles_y, j.W, j.H, s));
+    CK(launch_count(*j.m, fb, j.tiles_x, j.tiles_y, j.W, j.H, false, s));
     job_mark(j, 6, s);
     CK(scan_u32_to_u64(fb.cnt, fb.off, j.n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
     job_mark(j, 7, s);
@@ -653,7 +653,7 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     else CK(launch_capacity_from_previous(fb, j.n_tiles, kCapMargin, kCapPad, s));
     CK(scan_u32_to_u64(fb.tile_cap, fb.cap_off, j.n_tiles, fb.part, fb.part_max, fb.scal + 11, 0xFFFFFFFFu, s));
     job_mark(j, 5, s);
-    CK(launch_count(*m, fb, j.tiles_x, j.tiles_y, j.W, j.H, s));
+    CK(launch_count(*m, fb, j.tiles_x, j.tiles_y, j.W, j.H, true, s));
     job_mark(j, 6, s);
     job_mark(j, 7, s);
     job_mark(j, 8, s);
@@ -1536,7 +1536,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     CK(launch_bin_fill(*m, fb, tiles_x, W, H, ctx->reverse_bins, s));
     CK(launch_bin_sort(*m, fb, tiles_x, tiles_y, ctx->depth_buckets, s));
     CK(launch_tile_order(fb, n_tiles, s));
-    CK(launch_count(*m, fb, tiles_x, tiles_y, W, H, s));
+    CK(launch_count(*m, fb, tiles_x, tiles_y, W, H, false, s));
     CK(scan_u32_to_u64(fb.cnt, fb.off, n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
     CK(cudaMemcpyAsync(h, fb.scal, 6 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

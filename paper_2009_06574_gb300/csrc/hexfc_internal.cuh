@@ -174,7 +174,7 @@ cudaError_t prepare_composite_kernels();
 cudaError_t launch_bin_sort(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int buckets,
                             cudaStream_t s);
 cudaError_t launch_tile_order(FrameBufs& fb, int n_tiles, cudaStream_t s);
-cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int W, int H,
+cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, bool stats,
                          cudaStream_t s);
 cudaError_t launch_capacity_from_previous(FrameBufs& fb, int64_t n_tiles, float margin, uint32_t pad,
                                           cudaStream_t s);

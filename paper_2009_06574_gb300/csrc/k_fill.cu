@@ -205,12 +205,27 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
         const int bx = S.c.box[j];
         // exact weights of vertices 1 and 2 (edge functions opposite them)
         const int32_t sxr = (lx - box_lx0(bx)) << 8, syr = (ly - box_ly0(bx)) << 8;
-        const int64_t l1 = S.c.e0[1][j] + (int64_t)S.c.dx[1][j] * syr - (int64_t)S.c.dy[1][j] * sxr;
-        const int64_t l2 = S.c.e0[2][j] + (int64_t)S.c.dx[2][j] * syr - (int64_t)S.c.dy[2][j] * sxr;
         const float ia = S.sh.inv_area[j];
-        const float lam1 = u64_to_f32((uint64_t)l1) * ia, lam2 = u64_to_f32((uint64_t)l2) * ia;
-        const uint32_t z = sample_depth_lam(S.sh.z[0][j], S.sh.z[1][j], S.sh.z[2][j], l1, l2, S.sh.area[j], lam1,
-                                            lam2, S.sh.dz[0][j], S.sh.dz[1][j], bad);
+        const int64_t area = S.sh.area[j];
+        float lam1, lam2;
+        uint32_t z;
+        if (area < (1ll << 26)) {   // 0 <= l <= area < 2^26: the weights in 32-bit arithmetic (exact mod 2^32)
+            const uint32_t l1 = (uint32_t)S.c.e0[1][j] + (uint32_t)S.c.dx[1][j] * (uint32_t)syr -
+                                (uint32_t)S.c.dy[1][j] * (uint32_t)sxr;
+            const uint32_t l2 = (uint32_t)S.c.e0[2][j] + (uint32_t)S.c.dx[2][j] * (uint32_t)syr -
+                                (uint32_t)S.c.dy[2][j] * (uint32_t)sxr;
+            lam1 = (float)l1 * ia;
+            lam2 = (float)l2 * ia;
+            z = sample_depth_small(S.sh.z[0][j], S.sh.z[1][j], S.sh.z[2][j], l1, l2, (uint32_t)area, lam1, lam2,
+                                   S.sh.dz[0][j], S.sh.dz[1][j], bad);
+        } else {
+            const int64_t l1 = S.c.e0[1][j] + (int64_t)S.c.dx[1][j] * syr - (int64_t)S.c.dy[1][j] * sxr;
+            const int64_t l2 = S.c.e0[2][j] + (int64_t)S.c.dx[2][j] * syr - (int64_t)S.c.dy[2][j] * sxr;
+            lam1 = u64_to_f32((uint64_t)l1) * ia;
+            lam2 = u64_to_f32((uint64_t)l2) * ia;
+            z = sample_depth_lam(S.sh.z[0][j], S.sh.z[1][j], S.sh.z[2][j], l1, l2, area, lam1, lam2, S.sh.dz[0][j],
+                                 S.sh.dz[1][j], bad);
+        }
         const float4 col = shade_fragment(S.sh, j, lam1, lam2, px0 + lx, py0 + ly, sp);
         key[o] = ((uint64_t)z << 32) | (uint64_t)S.sh.f2t[j];
         rgba[o] = col;

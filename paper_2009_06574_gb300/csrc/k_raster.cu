@@ -358,8 +358,9 @@ __device__ __forceinline__ uint32_t tile_sum(uint32_t v, uint32_t* s_tmp)
 
 // Per tile: coverage of every chunk as per-pixel bit masks (kept for the
 // fill) and the per-pixel list lengths; the tile's total goes to tile_frag,
-// and stats[0] += fragments, stats[1] = longest list, stats[2] += lists
-// longer than kWarpSortMax (the frame's statistics without the pixel scan).
+// and, if stats is given, stats[0] += fragments, stats[1] = longest list,
+// stats[2] += lists longer than kWarpSortMax (the frame's statistics without
+// the pixel scan).
 __global__ void __launch_bounds__(kTilePix, 5) k_count(const uint64_t* __restrict__ tile_off,
                                                     const uint32_t* __restrict__ bins,
                                                     const FaceFrame* __restrict__ fframe,
@@ -382,16 +383,18 @@ __global__ void __launch_bounds__(kTilePix, 5) k_count(const uint64_t* __restric
 #pragma unroll
     for (int w = 0; w < kConsumerWarps; ++w) n += s_w[w].mask[threadIdx.x];
     cnt[(int64_t)tile * kTilePix + threadIdx.x] = n;
-    const uint32_t mx = __reduce_max_sync(0xffffffffu, n);
-    const uint32_t lg = __reduce_add_sync(0xffffffffu, n > (uint32_t)kWarpSortMax ? 1u : 0u);
-    if (lane == 0) {
-        atomicMax(&stats[1], (unsigned long long)mx);
-        if (lg) atomicAdd(&stats[2], (unsigned long long)lg);
+    if (stats) {   // (the pixel scan gives them otherwise)
+        const uint32_t mx = __reduce_max_sync(0xffffffffu, n);
+        const uint32_t lg = __reduce_add_sync(0xffffffffu, n > (uint32_t)kWarpSortMax ? 1u : 0u);
+        if (lane == 0) {
+            atomicMax(&stats[1], (unsigned long long)mx);
+            if (lg) atomicAdd(&stats[2], (unsigned long long)lg);
+        }
     }
     const uint32_t total = tile_sum(n, s_tmp);
     if (threadIdx.x == 0) {
         tile_frag[tile] = total;
-        atomicAdd(&stats[0], (unsigned long long)total);
+        if (stats) atomicAdd(&stats[0], (unsigned long long)total);
     }
 }
 
@@ -443,12 +446,14 @@ cudaError_t launch_tile_order(FrameBufs& fb, int n_tiles, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, cudaStream_t s)
+cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, bool stats,
+                         cudaStream_t s)
 {
     const size_t smem = kConsumerWarps * sizeof(CountWarp);
     k_count<<<(unsigned)(tiles_x * tiles_y), kTilePix, smem, s>>>(fb.tile_off, fb.bins, fb.fframe, fb.tile_order,
                                                                    tiles_x, W, H, fb.cnt, fb.masks, fb.tile_frag,
-                                                                   reinterpret_cast<unsigned long long*>(fb.scal + 16));
+                                                                   stats ? reinterpret_cast<unsigned long long*>(fb.scal + 16)
+                                                                         : nullptr);
     return cudaGetLastError();
 }
 

@@ -148,4 +148,23 @@ __device__ __forceinline__ uint32_t sample_depth_lam(uint32_t z0, uint32_t z1, u
     return (uint32_t)((int64_t)z0 + q);
 }
 
+// sample_depth_lam for a triangle with area < 2^26 (16.8 units squared: below
+// 512 square pixels), in 32-bit arithmetic: its weights satisfy 0 <= l <=
+// area < 2^26, the float estimate is within 8 of the quotient, so the exact
+// remainder l1 d1 + l2 d2 - q area lies within (-9, 9) areas, below 2^30 in
+// magnitude, and its value modulo 2^32 read as a signed integer is exact.
+__device__ __forceinline__ uint32_t sample_depth_small(uint32_t z0, uint32_t z1, uint32_t z2, uint32_t l1,
+                                                       uint32_t l2, uint32_t area, float lam1, float lam2, float dz1,
+                                                       float dz2, bool& bad)
+{
+    int32_t q = __float2int_rd(fmaf(lam1, dz1, lam2 * dz2));
+    int32_t r = (int32_t)(l1 * (z1 - z0) + l2 * (z2 - z0) - (uint32_t)q * area);
+#pragma unroll 1
+    for (int it = 0; it < 16 && r < 0; ++it) { --q; r += (int32_t)area; }
+#pragma unroll 1
+    for (int it = 0; it < 16 && r >= (int32_t)area; ++it) { ++q; r -= (int32_t)area; }
+    if (r < 0 || r >= (int32_t)area) bad = true;
+    return z0 + (uint32_t)q;
+}
+
 }  // namespace hexfc
