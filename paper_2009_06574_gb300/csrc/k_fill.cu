@@ -133,23 +133,8 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
         uint32_t f2t_n = n_chunks > 1 ? bins[beg + kChunk + lane] : kPadBin;
         if (f2t_c != kPadBin) rec_fetch(s_raw[lane], fframe, fstat, f2t_c >> 1);
         cp_async_commit();
-        // the runs of records: lane g < 8 follows group g's region (offset of its
-        // first pixel) chunk by chunk, from the groups' bit counts of the masks
-        const uint32_t* mp = masks + (beg / kChunk) * kTilePix + lane;
-        uint64_t* sgp = seg + (beg / kChunk) * kConsumerWarps + lane;
-        uint64_t run = lane < kConsumerWarps ? s_base[lane * 32] : 0;
         for (uint32_t c = 0; c < n_chunks; ++c) {
             const int s = c % kRing;
-            uint32_t mine = 0;
-#pragma unroll
-            for (int g = 0; g < kConsumerWarps; ++g) {
-                const uint32_t t = __reduce_add_sync(0xffffffffu, __popc(mp[(size_t)c * kTilePix + 32 * g]));
-                mine = lane == g ? t : mine;
-            }
-            if (lane < kConsumerWarps) {
-                sgp[(size_t)c * kConsumerWarps] = run;
-                run += mine;
-            }
             uint32_t f2t_nn = kPadBin;
             if (c + 1 < n_chunks) {
                 if (f2t_n != kPadBin) rec_fetch(s_raw[((c + 1) & 1) * kChunk + lane], fframe, fstat, f2t_n >> 1);
@@ -232,6 +217,7 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
     };
     // masks of the next two chunks are in flight while this one is shaded
     const uint32_t* mp = masks + (beg / kChunk) * kTilePix + p;             // this pixel's mask of chunk 0
+    uint64_t* sgp = seg + (beg / kChunk) * kConsumerWarps + warp;           // this group's run of chunk 0
     uint32_t mk_a = n_chunks > 0 ? mp[0] : 0u;
     uint32_t mk_b = n_chunks > 1 ? mp[kTilePix] : 0u;
     for (uint32_t c = 0; c < n_chunks; ++c) {
@@ -263,6 +249,7 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
         const bool fits = k_run + h <= s_len[p];   // the count pass sized this list
         bad = bad || !fits;
         const uint32_t chunk_start = tail;
+        if (lane == 0) sgp[(size_t)c * kConsumerWarps] = w_beg + chunk_start;
         const uint32_t tag = ((uint32_t)p << 5) | ((uint32_t)s << 13) | (fits ? kCounted : 0u);
         for (uint32_t w0 = 0; w0 < total; w0 += kWQWin) {
             uint32_t m2 = mk, r = incl - h;
