@@ -316,7 +316,8 @@ enum {
     HEXFC_OPT_DEPTH_BUCKETS = 3,     /* buckets of the per-tile depth order of the triangles: a power of
                                         two in 256..4096 (default 2048), or 0 for no depth order (lists
                                         in the faces' order: a test hook for the sorting passes) */
-    HEXFC_OPT_COMPOSITE_WINDOW = 4,  /* sorted window of the per-pixel resolve: 4 (default) or 8 */
+    HEXFC_OPT_COMPOSITE_WINDOW = 4,  /* sorted window of the per-pixel resolve: 2 (default), 4 or 8; the
+                                        image does not depend on it, bit for bit */
     HEXFC_OPT_PREDICTED_CAPACITY = 5 /* 0: count-then-fill (default); 1: capacities from the previous
                                         frame's tile counts; 2: from the capacity network. See below. */
 };

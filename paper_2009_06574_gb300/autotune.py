@@ -5,7 +5,7 @@ number of depth buckets of the per-tile triangle order
 (HEXFC_OPT_DEPTH_BUCKETS: more buckets give per-pixel lists closer to sorted,
 at a larger histogram per tile) and the sorted window of the per-pixel resolve
 (HEXFC_OPT_COMPOSITE_WINDOW: a wider window leaves fewer lists to the
-warp-sort pass, at more registers per thread). `tune` times every candidate on
+warp-sort pass, at more registers and moves per element). `tune` times every candidate on
 a few frames of the caller's own workload with CUDA events, keeps the
 fastest, applies it to the renderer, and caches the choice in a JSON file
 keyed by the GPU, the mesh size and the resolution, so that a workload is
@@ -18,8 +18,8 @@ import os
 import tempfile
 from typing import Callable, Iterable, Optional
 
-CANDIDATES = [{"depth_buckets": b, "composite_window": w} for b in (512, 1024, 2048, 4096) for w in (4, 8)]
-DEFAULT = {"depth_buckets": 2048, "composite_window": 4}
+CANDIDATES = [{"depth_buckets": b, "composite_window": w} for b in (512, 1024, 2048, 4096) for w in (2, 4, 8)]
+DEFAULT = {"depth_buckets": 2048, "composite_window": 2}
 
 
 def apply(renderer, cfg: dict):

@@ -26,7 +26,7 @@ struct hexfc_ctx {
     FrameBufs fb;
     int reverse_bins = 0;
     int depth_buckets = 2048;   // HEXFC_OPT_DEPTH_BUCKETS
-    int window = 4;             // HEXFC_OPT_COMPOSITE_WINDOW
+    int window = 2;             // HEXFC_OPT_COMPOSITE_WINDOW
     int predicted = 0;          // HEXFC_OPT_PREDICTED_CAPACITY
     // exact tile counts of the last frame (fb.tile_frag) are valid for this size
     int counts_W = 0, counts_H = 0;
@@ -1381,7 +1381,7 @@ hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value)
         ctx->depth_buckets = (int)value;
         return HEXFC_OK;
     case HEXFC_OPT_COMPOSITE_WINDOW:
-        if (value != 4 && value != 8) return HEXFC_ERR_ARG;
+        if (value != 2 && value != 4 && value != 8) return HEXFC_ERR_ARG;
         ctx->window = (int)value;
         return HEXFC_OK;
     case HEXFC_OPT_PREDICTED_CAPACITY:

@@ -17,9 +17,9 @@
 // Lists longer than 256 (up to HEXFC_MAX_LIST) are sorted by a whole block in
 // shared memory. Keys are unique within a pixel (depth, face, triangle), so
 // the order is unique.
-// The warp-wide resolve composites as an ordered reduction of (colour,
-// transmittance) pairs, (C1,T1)(C2,T2) = (C1 + T1 C2, T1 T2), equal to the
-// sequential front-to-back blend.
+// Every path blends a list front to back one element after the other (the
+// warp-wide paths pass the running colour from lane to lane), so the image
+// does not depend on which path resolved a list, bit for bit.
 #include "hexfc_internal.cuh"
 #include "pipeline.cuh"
 
@@ -37,16 +37,21 @@ __device__ __forceinline__ CT ct_over(CT a, CT b)  // a in front of b
     return CT{a.r + a.t * b.r, a.g + a.t * b.g, a.b + a.t * b.b, a.t * b.t};
 }
 
-__device__ __forceinline__ CT warp_ordered_reduce(CT c, int lane)
+// Front-to-back blend of a sorted list whose ranks are held by the lanes in
+// runs, lane 0's first: each lane in turn blends its run onto the running
+// colour, run(c) returning c after its elements. This is the same sequence of
+// ct_over steps as one thread blending the whole list, so every resolve path
+// gives the same image bit for bit, whichever path a list takes.
+template <class F>
+__device__ __forceinline__ CT warp_chain_blend(int lane, F&& run)
 {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        CT r;
-        r.r = __shfl_down_sync(kFull, c.r, o);
-        r.g = __shfl_down_sync(kFull, c.g, o);
-        r.b = __shfl_down_sync(kFull, c.b, o);
-        r.t = __shfl_down_sync(kFull, c.t, o);
-        if ((lane & (2 * o - 1)) == 0) c = ct_over(c, r);
+    CT c{0.f, 0.f, 0.f, 1.f};
+    for (int l = 0; l < 32; ++l) {
+        if (lane == l) c = run(c);
+        c.r = __shfl_sync(kFull, c.r, l);
+        c.g = __shfl_sync(kFull, c.g, l);
+        c.b = __shfl_sync(kFull, c.b, l);
+        c.t = __shfl_sync(kFull, c.t, l);
     }
     return c;
 }
@@ -115,20 +120,21 @@ __device__ __noinline__ CT warp_sort_resolve(const uint64_t* key, const float4* 
         v[j] = i;
     }
     warp_bitonic<M>(k, v, lane);
-    CT c{0.f, 0.f, 0.f, 1.f};
+    return warp_chain_blend(lane, [&](CT c) {
 #pragma unroll
-    for (int j = 0; j < M; ++j) {
-        uint32_t r = lane * M + j;
-        if (r < n) {
-            float4 f = rgba[v[j]];
-            c = ct_over(c, CT{f.x, f.y, f.z, 1.f - f.w});
-            if (out_key) {
-                out_key[r] = k[j];
-                out_rgba[r] = f;
+        for (int j = 0; j < M; ++j) {
+            const uint32_t r = lane * M + j;
+            if (r < n) {
+                const float4 f = rgba[v[j]];
+                c = ct_over(c, CT{f.x, f.y, f.z, 1.f - f.w});
+                if (out_key) {
+                    out_key[r] = k[j];
+                    out_rgba[r] = f;
+                }
             }
         }
-    }
-    return warp_ordered_reduce(c, lane);
+        return c;
+    });
 }
 
 // Resolve one list of n <= kWarpList fragments held in shared memory (key[i],
@@ -151,19 +157,20 @@ __device__ CT warp_resolve(const uint64_t* key, const float4* rgba, uint32_t n, 
         if (M <= 4) return warp_sort_resolve<4>(key, rgba, n, lane, out_key, out_rgba);
         return warp_sort_resolve<8>(key, rgba, n, lane, out_key, out_rgba);
     }
-    CT c{0.f, 0.f, 0.f, 1.f};
-    for (uint32_t j = 0; j < M; ++j) {
-        uint32_t r = i0 + j;
-        if (r < n) {
-            float4 f = rgba[r];
-            c = ct_over(c, CT{f.x, f.y, f.z, 1.f - f.w});
-            if (out_key) {
-                out_key[r] = key[r];
-                out_rgba[r] = f;
+    return warp_chain_blend(lane, [&](CT c) {
+        for (uint32_t j = 0; j < M; ++j) {
+            const uint32_t r = i0 + j;
+            if (r < n) {
+                const float4 f = rgba[r];
+                c = ct_over(c, CT{f.x, f.y, f.z, 1.f - f.w});
+                if (out_key) {
+                    out_key[r] = key[r];
+                    out_rgba[r] = f;
+                }
             }
         }
-    }
-    return warp_ordered_reduce(c, lane);
+        return c;
+    });
 }
 
 __device__ __forceinline__ void tile_pixel(int64_t q, int tiles_x, int& x, int& y)
@@ -217,8 +224,8 @@ __device__ __forceinline__ float4 finish(CT c, float bg0, float bg1, float bg2)
 // at most KW - 1 places from their sorted position comes out sorted. The blend checks that the keys it consumes increase; a
 // list that breaks that is queued for the warp-wide resolve of
 // k_composite_fix, or, if longer than 256, for the block-wide sort of
-// k_composite_long. KW (4 or 8) trades registers for fewer queued lists; the
-// result does not depend on it.
+// k_composite_long. KW (2, 4 or 8) trades registers and moves for fewer
+// queued lists; the result does not depend on it.
 struct KC {
     uint64_t k;
     float4 c;
@@ -408,20 +415,22 @@ __device__ CT block_composite(const uint64_t* __restrict__ tile_off, const uint3
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) { s_k[i] = key[s_e[i]]; s_v[i] = i; }
     __syncthreads();
     block_sort(s_k, s_v, n, np2);
-    // first warp: each lane composites a contiguous run of ranks, then an ordered reduction
+    // first warp: the lanes blend contiguous runs of ranks in turn
     CT c{0.f, 0.f, 0.f, 1.f};
     if (threadIdx.x < 32) {
-        int lane = threadIdx.x;
-        uint32_t per = np2 / 32;
-        for (uint32_t j = 0; j < per; ++j) {
-            uint32_t rank = lane * per + j;
-            if (rank < n) {
-                float4 f = rgba[s_e[s_v[rank]]];
-                c = ct_over(c, CT{f.x, f.y, f.z, 1.f - f.w});
-                if (out_key) { out_key[rank] = s_k[rank]; out_rgba[rank] = f; }
+        const int lane = threadIdx.x;
+        const uint32_t per = np2 / 32;
+        c = warp_chain_blend(lane, [&](CT a) {
+            for (uint32_t j = 0; j < per; ++j) {
+                const uint32_t rank = lane * per + j;
+                if (rank < n) {
+                    const float4 f = rgba[s_e[s_v[rank]]];
+                    a = ct_over(a, CT{f.x, f.y, f.z, 1.f - f.w});
+                    if (out_key) { out_key[rank] = s_k[rank]; out_rgba[rank] = f; }
+                }
             }
-        }
-        c = warp_ordered_reduce(c, lane);
+            return a;
+        });
     }
     return c;
 }
@@ -536,14 +545,14 @@ cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, 
     unsigned long long* long_cursor = reinterpret_cast<unsigned long long*>(fb.scal + 3);
     unsigned long long* fix_cursor = reinterpret_cast<unsigned long long*>(fb.scal + 4);
     const unsigned grid = (unsigned)(n_pix / kTilePix);
-    if (window == 8)
-        k_composite<8><<<grid, 256, 0, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
-                                            (uint64_t)fb.frag_cap, tiles_x, W, H, sp.bg[0], sp.bg[1], sp.bg[2], o4,
-                                            fb.long_q, long_cursor, fb.fix_q, fix_cursor);
-    else
-        k_composite<4><<<grid, 256, 0, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
-                                            (uint64_t)fb.frag_cap, tiles_x, W, H, sp.bg[0], sp.bg[1], sp.bg[2], o4,
-                                            fb.long_q, long_cursor, fb.fix_q, fix_cursor);
+    auto resolve = [&](auto kernel) {
+        kernel<<<grid, 256, 0, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba, (uint64_t)fb.frag_cap,
+                                    tiles_x, W, H, sp.bg[0], sp.bg[1], sp.bg[2], o4, fb.long_q, long_cursor, fb.fix_q,
+                                    fix_cursor);
+    };
+    if (window == 8) resolve(k_composite<8>);
+    else if (window == 4) resolve(k_composite<4>);
+    else resolve(k_composite<2>);
     k_composite_fix<<<kFixBlocks, 256, kFixSmem, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
                                                       (uint64_t)fb.frag_cap, tiles_x, W, sp.bg[0], sp.bg[1],
                                                       sp.bg[2], o4, fb.fix_q, fix_cursor);

@@ -168,6 +168,32 @@ def test_fresh_buffers_carry_no_stale_error_bits(hx):
         r.close()
 
 
+def test_image_independent_of_resolve_path(hx):
+    """The same frame with lists in depth order or not (so that lists take the
+    streaming window, the warp sort or the block sort) and with every window
+    size: the images are identical bit for bit, since every path blends a
+    list element after element in key order."""
+    mesh = synth.hex_grid(10, jitter=0.1, warp_amp=0.3, seed=4)
+    view = synth.orbit_view(17, 120, 192, 144, radius=1.3)
+    lens = synth.lissajous_lens(17, 120)
+    imgs = []
+    for buckets in (2048, 0):
+        for window in (2, 4, 8):
+            r = hx.Renderer(0)
+            r.set_option(hx.HEXFC_OPT_DEPTH_BUCKETS, buckets)
+            r.set_option(hx.HEXFC_OPT_COMPOSITE_WINDOW, window)
+            mid = r.upload_mesh(mesh.verts, mesh.cells, mesh.cell_scalar, mesh.edge_level)
+            r.set_view(view)
+            r.set_lens(lens)
+            r.set_style(synth.Style(w_base=1.5, lod=2))
+            out = torch.zeros((144, 192, 4), dtype=torch.float32, device="cuda")
+            r.render(mid, out)
+            imgs.append(out.cpu().numpy())
+            r.close()
+    for img in imgs[1:]:
+        np.testing.assert_array_equal(img, imgs[0])
+
+
 def test_without_depth_order(hx):
     """Lists in the faces' order (no per-tile depth order): most lists go
     through the warp-wide sort of the out-of-order pass; the result is the same."""
