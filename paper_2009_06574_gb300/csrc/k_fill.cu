@@ -22,11 +22,22 @@ inline unsigned grid_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b);
 
 // ------------------------------------------------------------------ fill + shade
 
-// Both records of a face, staged side by side by the producer.
-struct __align__(128) RawFace {
-    FaceFrame fr;
-    FaceStatic st;
+// Both records of a face as the producer stages them in shared memory: the
+// 64 bytes of FaceFrame, the 64 bytes of FaceStatic, and 16 bytes of padding
+// that make the stride 9 x 16 bytes. Each lane copies and reads its own
+// record 16 bytes at a time; with an odd stride in 16-byte units the lanes of
+// each quarter warp touch different banks (a 128-byte stride put all 32
+// lanes on the same four banks).
+struct RawFace {
+    int4 X, Y;      // FaceFrame
+    uint4 Z;
+    float4 ed;
+    float4 imp;     // FaceStatic
+    float4 px, py, pz;
+    int4 pad;
 };
+static_assert(sizeof(FaceFrame) == 64 && sizeof(FaceStatic) == 64, "face records of 4 x 16 bytes");
+static_assert(sizeof(RawFace) == 144, "record stride of 9 x 16 bytes");
 
 // Producer lane: fetch the records of face f into shared memory.
 __device__ __forceinline__ void rec_fetch(RawFace& r, const FaceFrame* __restrict__ fframe,
@@ -42,11 +53,9 @@ __device__ __forceinline__ void rec_fetch(RawFace& r, const FaceFrame* __restric
     }
 }
 
-__device__ __forceinline__ void stage_shade(const RawFace& rf, uint32_t f2t, const TriGeom& t, const ShadeParams& sp,
+__device__ __forceinline__ void stage_shade(const RawFace& r, uint32_t f2t, const TriGeom& t, const ShadeParams& sp,
                                             ShadeSoA& S, int j)
 {
-    const FaceFrame& r = rf.fr;
-    const FaceStatic& fs = rf.st;
     const int32_t FX[4] = {r.X.x, r.X.y, r.X.z, r.X.w}, FY[4] = {r.Y.x, r.Y.y, r.Y.z, r.Y.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -58,9 +67,9 @@ __device__ __forceinline__ void stage_shade(const RawFace& rf, uint32_t f2t, con
         S.inv_len2[k][j] = l2 > 0.f ? 1.f / l2 : 0.f;
     }
     const uint32_t zz[4] = {r.Z.x & kZ24, r.Z.y & kZ24, r.Z.z & kZ24, r.Z.w & kZ24};
-    const float ee[4] = {r.ed.x, r.ed.y, r.ed.z, r.ed.w}, ii[4] = {fs.imp.x, fs.imp.y, fs.imp.z, fs.imp.w};
-    const float xx[4] = {fs.px.x, fs.px.y, fs.px.z, fs.px.w}, yy[4] = {fs.py.x, fs.py.y, fs.py.z, fs.py.w};
-    const float ww[4] = {fs.pz.x, fs.pz.y, fs.pz.z, fs.pz.w};
+    const float ee[4] = {r.ed.x, r.ed.y, r.ed.z, r.ed.w}, ii[4] = {r.imp.x, r.imp.y, r.imp.z, r.imp.w};
+    const float xx[4] = {r.px.x, r.px.y, r.px.z, r.px.w}, yy[4] = {r.py.x, r.py.y, r.py.z, r.py.w};
+    const float ww[4] = {r.pz.x, r.pz.y, r.pz.z, r.pz.w};
     const bool ortho = sp.ortho != 0;
     float q[3], a[3], P[3][3];
 #pragma unroll
@@ -89,6 +98,7 @@ __device__ __forceinline__ void stage_shade(const RawFace& rf, uint32_t f2t, con
 #pragma unroll
     for (int d = 0; d < 3; ++d) S.p0[d][j] = P[0][d];
     S.area[j] = t.area;
+    S.area32[j] = t.area < (1ll << 26) ? (uint32_t)t.area : 0u;
     S.inv_area[j] = 1.f / u64_to_f32((uint64_t)t.area);
     S.f2t[j] = f2t;
     S.masks[j] = face_edge_flags(r.Z);
@@ -150,8 +160,12 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
             if (f2t_c != kPadBin) {
                 const RawFace& r = s_raw[(c & 1) * kChunk + lane];
                 TriGeom t;
-                stage_cov(r.fr.X, r.fr.Y, f2t_c, W, H, px0, py0, S.c, lane, t);
-                if (S.c.box[lane] != 0) stage_shade(r, f2t_c, t, sp, S.sh, lane);
+                stage_cov(r.X, r.Y, f2t_c, W, H, px0, py0, S.c, lane, t);
+                if (S.c.box[lane] != 0) {
+                    stage_shade(r, f2t_c, t, sp, S.sh, lane);
+                    S.sh.l0[0][lane] = (uint32_t)S.c.e0[1][lane];
+                    S.sh.l0[1][lane] = (uint32_t)S.c.e0[2][lane];
+                }
             } else {
                 S.c.box[lane] = 0;
             }
@@ -191,19 +205,20 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
         // exact weights of vertices 1 and 2 (edge functions opposite them)
         const int32_t sxr = (lx - box_lx0(bx)) << 8, syr = (ly - box_ly0(bx)) << 8;
         const float ia = S.sh.inv_area[j];
-        const int64_t area = S.sh.area[j];
+        const uint32_t area32 = S.sh.area32[j];
         float lam1, lam2;
         uint32_t z;
-        if (area < (1ll << 26)) {   // 0 <= l <= area < 2^26: the weights in 32-bit arithmetic (exact mod 2^32)
-            const uint32_t l1 = (uint32_t)S.c.e0[1][j] + (uint32_t)S.c.dx[1][j] * (uint32_t)syr -
+        if (area32 != 0) {   // 0 <= l <= area < 2^26: the weights in 32-bit arithmetic (exact mod 2^32)
+            const uint32_t l1 = S.sh.l0[0][j] + (uint32_t)S.c.dx[1][j] * (uint32_t)syr -
                                 (uint32_t)S.c.dy[1][j] * (uint32_t)sxr;
-            const uint32_t l2 = (uint32_t)S.c.e0[2][j] + (uint32_t)S.c.dx[2][j] * (uint32_t)syr -
+            const uint32_t l2 = S.sh.l0[1][j] + (uint32_t)S.c.dx[2][j] * (uint32_t)syr -
                                 (uint32_t)S.c.dy[2][j] * (uint32_t)sxr;
             lam1 = (float)l1 * ia;
             lam2 = (float)l2 * ia;
-            z = sample_depth_small(S.sh.z[0][j], S.sh.z[1][j], S.sh.z[2][j], l1, l2, (uint32_t)area, lam1, lam2,
+            z = sample_depth_small(S.sh.z[0][j], S.sh.z[1][j], S.sh.z[2][j], l1, l2, area32, lam1, lam2,
                                    S.sh.dz[0][j], S.sh.dz[1][j], bad);
         } else {
+            const int64_t area = S.sh.area[j];
             const int64_t l1 = S.c.e0[1][j] + (int64_t)S.c.dx[1][j] * syr - (int64_t)S.c.dy[1][j] * sxr;
             const int64_t l2 = S.c.e0[2][j] + (int64_t)S.c.dx[2][j] * syr - (int64_t)S.c.dy[2][j] * sxr;
             lam1 = u64_to_f32((uint64_t)l1) * ia;

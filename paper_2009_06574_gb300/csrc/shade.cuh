@@ -25,6 +25,8 @@ struct ShadeSoA {
     float a0[kChunk], da[2][kChunk];        // importance / eye depth
     float p0[3][kChunk], dp[2][3][kChunk];  // (world position - sphere lens centre) / eye depth
     int64_t area[kChunk];                   // twice the area (16.8 squared)
+    uint32_t area32[kChunk];                // the area below 2^26, else 0
+    uint32_t l0[2][kChunk];                 // low words of the edge functions of vertices 1, 2 at the box origin
     float inv_area[kChunk];
     uint32_t f2t[kChunk];
     uint32_t masks[kChunk];                 // bits 0-3 focus-visible, 4-7 context-visible face edges
