@@ -53,60 +53,61 @@ __device__ __forceinline__ void rec_fetch(RawFace& r, const FaceFrame* __restric
     }
 }
 
+// Producer lane j: the shading and depth inputs of triangle t (coverage setup
+// already in c) into its record.
 __device__ __forceinline__ void stage_shade(const RawFace& r, uint32_t f2t, const TriGeom& t, const ShadeParams& sp,
-                                            ShadeSoA& S, int j)
+                                            const CovSoA& c, ShadeRec& R, int j)
 {
     const int32_t FX[4] = {r.X.x, r.X.y, r.X.z, r.X.w}, FY[4] = {r.Y.x, r.Y.y, r.Y.z, r.Y.w};
+    float il[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int k1 = (k + 1) & 3;
-        S.FX[k][j] = (float)FX[k];   // |coordinate| <= 2^22: exact
-        S.FY[k][j] = (float)FY[k];
         const int32_t ex = FX[k1] - FX[k], ey = FY[k1] - FY[k];
         const float l2 = u64_to_f32((uint64_t)((int64_t)ex * ex + (int64_t)ey * ey));
-        S.inv_len2[k][j] = l2 > 0.f ? 1.f / l2 : 0.f;
+        il[k] = l2 > 0.f ? 1.f / l2 : 0.f;
     }
+    // |coordinate| <= 2^22: exact in float
+    R.fx = make_float4((float)FX[0], (float)FX[1], (float)FX[2], (float)FX[3]);
+    R.fy = make_float4((float)FY[0], (float)FY[1], (float)FY[2], (float)FY[3]);
+    R.il = make_float4(il[0], il[1], il[2], il[3]);
     const uint32_t zz[4] = {r.Z.x & kZ24, r.Z.y & kZ24, r.Z.z & kZ24, r.Z.w & kZ24};
     const float ee[4] = {r.ed.x, r.ed.y, r.ed.z, r.ed.w}, ii[4] = {r.imp.x, r.imp.y, r.imp.z, r.imp.w};
     const float xx[4] = {r.px.x, r.px.y, r.px.z, r.px.w}, yy[4] = {r.py.x, r.py.y, r.py.z, r.py.w};
     const float ww[4] = {r.pz.x, r.pz.y, r.pz.z, r.pz.w};
     const bool ortho = sp.ortho != 0;
+    uint32_t z[3];
     float q[3], a[3], P[3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const int c = t.vi[k];
-        // select corner c without dynamic register indexing
-        S.z[k][j] = c == 0 ? zz[0] : c == 1 ? zz[1] : c == 2 ? zz[2] : zz[3];
-        q[k] = ortho ? 1.f : 1.f / (c == 0 ? ee[0] : c == 1 ? ee[1] : c == 2 ? ee[2] : ee[3]);
-        a[k] = (c == 0 ? ii[0] : c == 1 ? ii[1] : c == 2 ? ii[2] : ii[3]) * q[k];
+        const int cc = t.vi[k];
+        // select corner cc without dynamic register indexing
+        z[k] = cc == 0 ? zz[0] : cc == 1 ? zz[1] : cc == 2 ? zz[2] : zz[3];
+        q[k] = ortho ? 1.f : 1.f / (cc == 0 ? ee[0] : cc == 1 ? ee[1] : cc == 2 ? ee[2] : ee[3]);
+        a[k] = (cc == 0 ? ii[0] : cc == 1 ? ii[1] : cc == 2 ? ii[2] : ii[3]) * q[k];
         // offset from the sphere lens centre (unused by the screen lens)
-        P[k][0] = ((c == 0 ? xx[0] : c == 1 ? xx[1] : c == 2 ? xx[2] : xx[3]) - sp.lens_c[0]) * q[k];
-        P[k][1] = ((c == 0 ? yy[0] : c == 1 ? yy[1] : c == 2 ? yy[2] : yy[3]) - sp.lens_c[1]) * q[k];
-        P[k][2] = ((c == 0 ? ww[0] : c == 1 ? ww[1] : c == 2 ? ww[2] : ww[3]) - sp.lens_c[2]) * q[k];
+        P[k][0] = ((cc == 0 ? xx[0] : cc == 1 ? xx[1] : cc == 2 ? xx[2] : xx[3]) - sp.lens_c[0]) * q[k];
+        P[k][1] = ((cc == 0 ? yy[0] : cc == 1 ? yy[1] : cc == 2 ? yy[2] : yy[3]) - sp.lens_c[1]) * q[k];
+        P[k][2] = ((cc == 0 ? ww[0] : cc == 1 ? ww[1] : cc == 2 ? ww[2] : ww[3]) - sp.lens_c[2]) * q[k];
     }
-    S.dz[0][j] = (float)(int32_t)(S.z[1][j] - S.z[0][j]);
-    S.dz[1][j] = (float)(int32_t)(S.z[2][j] - S.z[0][j]);
-    S.q0[j] = q[0];
-    S.a0[j] = a[0];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        S.dq[k][j] = q[k + 1] - q[0];
-        S.da[k][j] = a[k + 1] - a[0];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) S.dp[k][d][j] = P[k + 1][d] - P[0][d];
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d) S.p0[d][j] = P[0][d];
-    S.area[j] = t.area;
-    S.area32[j] = t.area < (1ll << 26) ? (uint32_t)t.area : 0u;
-    S.inv_area[j] = 1.f / u64_to_f32((uint64_t)t.area);
-    S.f2t[j] = f2t;
-    S.masks[j] = face_edge_flags(r.Z);
+    R.qa = make_float4(q[0], q[1] - q[0], q[2] - q[0], a[0]);
+    R.ap = make_float4(a[1] - a[0], a[2] - a[0], P[0][0], P[0][1]);
+    R.pp = make_float4(P[0][2], P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]);
+    R.pq = make_float4(P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2], 0.f);
+    R.zm = make_uint4(z[0], z[1], z[2], face_edge_flags(r.Z));
+    // depth differences below 2^24 in magnitude: exact in float
+    R.wd = make_uint4((uint32_t)c.e0[1][j], (uint32_t)c.e0[2][j], __float_as_uint((float)(int32_t)(z[1] - z[0])),
+                      __float_as_uint((float)(int32_t)(z[2] - z[0])));
+    R.ev = make_int4(c.dx[1][j], c.dy[1][j], c.dx[2][j], c.dy[2][j]);
+    R.hd = make_uint4((uint32_t)c.box[j], f2t, t.area < (1ll << 26) ? (uint32_t)t.area : 0u,
+                      __float_as_uint(1.f / u64_to_f32((uint64_t)t.area)));
 }
 
+// A ring slot: the coverage setup and the shading inputs of one chunk.
 struct FillSlot {
     CovSoA c;
-    ShadeSoA sh;
+    ShadeRec sh[kChunk];
+    int64_t area[kChunk];   // twice the area (16.8 squared)
 };
 
 // Warp queues of covered samples: entry = j | pixel << 5 | ring slot << 13 | counted << 15.
@@ -162,9 +163,8 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
                 TriGeom t;
                 stage_cov(r.X, r.Y, f2t_c, W, H, px0, py0, S.c, lane, t);
                 if (S.c.box[lane] != 0) {
-                    stage_shade(r, f2t_c, t, sp, S.sh, lane);
-                    S.sh.l0[0][lane] = (uint32_t)S.c.e0[1][lane];
-                    S.sh.l0[1][lane] = (uint32_t)S.c.e0[2][lane];
+                    stage_shade(r, f2t_c, t, sp, S.c, S.sh[lane], lane);
+                    S.area[lane] = t.area;
                 }
             } else {
                 S.c.box[lane] = 0;
@@ -201,33 +201,32 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
         const uint32_t pl = (qe >> 5) & 255u;
         const FillSlot& S = s_ring[(qe >> 13) & 3u];
         const int lx = (int)(pl & (kTile - 1)), ly = (int)(pl / kTile);
-        const int bx = S.c.box[j];
+        const ShadeRec& R = S.sh[j];
+        const uint4 hd = R.hd, zm = R.zm, wd = R.wd;
+        const int4 ev = R.ev;
+        const int bx = (int)hd.x;
         // exact weights of vertices 1 and 2 (edge functions opposite them)
         const int32_t sxr = (lx - box_lx0(bx)) << 8, syr = (ly - box_ly0(bx)) << 8;
-        const float ia = S.sh.inv_area[j];
-        const uint32_t area32 = S.sh.area32[j];
+        const float ia = __uint_as_float(hd.w);
+        const float dz1 = __uint_as_float(wd.z), dz2 = __uint_as_float(wd.w);
         float lam1, lam2;
         uint32_t z;
-        if (area32 != 0) {   // 0 <= l <= area < 2^26: the weights in 32-bit arithmetic (exact mod 2^32)
-            const uint32_t l1 = S.sh.l0[0][j] + (uint32_t)S.c.dx[1][j] * (uint32_t)syr -
-                                (uint32_t)S.c.dy[1][j] * (uint32_t)sxr;
-            const uint32_t l2 = S.sh.l0[1][j] + (uint32_t)S.c.dx[2][j] * (uint32_t)syr -
-                                (uint32_t)S.c.dy[2][j] * (uint32_t)sxr;
+        if (hd.z != 0) {   // 0 <= l <= area < 2^26: the weights in 32-bit arithmetic (exact mod 2^32)
+            const uint32_t l1 = wd.x + (uint32_t)ev.x * (uint32_t)syr - (uint32_t)ev.y * (uint32_t)sxr;
+            const uint32_t l2 = wd.y + (uint32_t)ev.z * (uint32_t)syr - (uint32_t)ev.w * (uint32_t)sxr;
             lam1 = (float)l1 * ia;
             lam2 = (float)l2 * ia;
-            z = sample_depth_small(S.sh.z[0][j], S.sh.z[1][j], S.sh.z[2][j], l1, l2, area32, lam1, lam2,
-                                   S.sh.dz[0][j], S.sh.dz[1][j], bad);
+            z = sample_depth_small(zm.x, zm.y, zm.z, l1, l2, hd.z, lam1, lam2, dz1, dz2, bad);
         } else {
-            const int64_t area = S.sh.area[j];
-            const int64_t l1 = S.c.e0[1][j] + (int64_t)S.c.dx[1][j] * syr - (int64_t)S.c.dy[1][j] * sxr;
-            const int64_t l2 = S.c.e0[2][j] + (int64_t)S.c.dx[2][j] * syr - (int64_t)S.c.dy[2][j] * sxr;
+            const int64_t area = S.area[j];
+            const int64_t l1 = S.c.e0[1][j] + (int64_t)ev.x * syr - (int64_t)ev.y * sxr;
+            const int64_t l2 = S.c.e0[2][j] + (int64_t)ev.z * syr - (int64_t)ev.w * sxr;
             lam1 = u64_to_f32((uint64_t)l1) * ia;
             lam2 = u64_to_f32((uint64_t)l2) * ia;
-            z = sample_depth_lam(S.sh.z[0][j], S.sh.z[1][j], S.sh.z[2][j], l1, l2, area, lam1, lam2, S.sh.dz[0][j],
-                                 S.sh.dz[1][j], bad);
+            z = sample_depth_lam(zm.x, zm.y, zm.z, l1, l2, area, lam1, lam2, dz1, dz2, bad);
         }
-        const float4 col = shade_fragment(S.sh, j, lam1, lam2, px0 + lx, py0 + ly, sp);
-        key[o] = ((uint64_t)z << 32) | (uint64_t)S.sh.f2t[j];
+        const float4 col = shade_fragment(R, zm.w, lam1, lam2, px0 + lx, py0 + ly, sp);
+        key[o] = ((uint64_t)z << 32) | (uint64_t)hd.y;
         rgba[o] = col;
     };
     // masks of the next two chunks are in flight while this one is shaded
@@ -309,8 +308,11 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
 // 32 samples at a time, so that every lane has work, writing the fragments in
 // queue order into the warp's region (the 32 lists the count pass sized):
 // chunk by chunk, pixel by pixel within a chunk. The producer fetches the face
-// records of chunk c+1 with cp.async while it sets up chunk c.
-__global__ void __launch_bounds__(kPipeThreads, 4) k_fill(const uint64_t* __restrict__ tile_off,
+// records of chunk c+1 with cp.async while it sets up chunk c. Three blocks
+// per SM leave 72 registers a thread: a sample's inputs arrive as eleven
+// 16-byte vectors, more values live at once than at four blocks (56
+// registers), where they spill.
+__global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __restrict__ tile_off,
                                                           const uint32_t* __restrict__ bins,
                                                           uint32_t* __restrict__ masks,
                                                           const FaceFrame* __restrict__ fframe,

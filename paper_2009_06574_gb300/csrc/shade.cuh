@@ -5,10 +5,12 @@
 
 namespace hexfc {
 
-// Shading inputs of the kChunk triangles of one chunk, structure of arrays
-// (element j = triangle j, vertices in wound order), so that lanes reading
-// different triangles touch different shared-memory banks. Coordinates are in
-// 1/256-pixel units; integers below 2^24 are exact in float.
+// Shading and depth inputs of one triangle of a chunk (vertices in wound
+// order), read by the consumer lanes 16 bytes at a time: eleven vectors, an
+// odd stride in 16-byte units, so the lanes of a quarter warp that read
+// different triangles of the chunk share banks only when the triangles'
+// indices agree modulo 8. Coordinates are in 1/256-pixel units; integers
+// below 2^24 are exact in float.
 //
 // Perspective-correct interpolation of an attribute a with vertex weights
 // lam_k (lam_0 = 1 - lam_1 - lam_2) is sum lam_k a_k / w_k over
@@ -16,21 +18,19 @@ namespace hexfc {
 // each is kept as its value at vertex 0 and two differences: with q_k = 1/w_k,
 // Q = q0 + lam_1 dq1 + lam_2 dq2 and sum lam_k a_k q_k = A0 + lam_1 dA1 + lam_2 dA2.
 // Orthographic views use q_k = 1.
-struct ShadeSoA {
-    float FX[4][kChunk], FY[4][kChunk];     // face corners
-    float inv_len2[4][kChunk];              // 1 / squared length of face edge k -> k+1 (0: degenerate)
-    uint32_t z[3][kChunk];                  // window depth of the triangle's vertices
-    float dz[2][kChunk];                    // z[1] - z[0], z[2] - z[0] (exact: |d| < 2^24)
-    float q0[kChunk], dq[2][kChunk];        // 1 / eye depth
-    float a0[kChunk], da[2][kChunk];        // importance / eye depth
-    float p0[3][kChunk], dp[2][3][kChunk];  // (world position - sphere lens centre) / eye depth
-    int64_t area[kChunk];                   // twice the area (16.8 squared)
-    uint32_t area32[kChunk];                // the area below 2^26, else 0
-    uint32_t l0[2][kChunk];                 // low words of the edge functions of vertices 1, 2 at the box origin
-    float inv_area[kChunk];
-    uint32_t f2t[kChunk];
-    uint32_t masks[kChunk];                 // bits 0-3 focus-visible, 4-7 context-visible face edges
+struct ShadeRec {
+    float4 fx, fy;   // face corners
+    float4 il;       // 1 / squared length of face edge k -> k+1 (0: degenerate)
+    float4 qa;       // q0, dq1, dq2 (1 / eye depth); a0 (importance / eye depth)
+    float4 ap;       // da1, da2; p0.x, p0.y  (p = (world position - sphere lens centre) / eye depth)
+    float4 pp;       // p0.z; dp1.x, dp1.y, dp1.z
+    float4 pq;       // dp2.x, dp2.y, dp2.z; unused
+    uint4 zm;        // window depth of the three vertices; face edge flags (bits 0-3 focus, 4-7 context)
+    uint4 wd;        // low words of the edge functions of vertices 1, 2 at the box origin; dz1, dz2 (float bits)
+    int4 ev;         // dx, dy of the edges opposite vertices 1 and 2 (16.8)
+    uint4 hd;        // box (as CovSoA::box), f2t, twice the area if below 2^26 else 0, 1 / twice the area (float bits)
 };
+static_assert(sizeof(ShadeRec) == 11 * 16, "eleven 16-byte vectors");
 
 // Square root of x >= 0 (0 at 0), the hardware approximation (a few units in
 // the last place).
@@ -41,16 +41,17 @@ __device__ __forceinline__ float sqrt_approx(float x)
     return r;
 }
 
-// Eqs. 1-4 for one fragment of triangle j at pixel (px, py); lam1, lam2 are
-// the screen-space barycentric weights of vertices 1 and 2. Returns the
-// premultiplied RGBA of Eq. 4.
-__device__ __forceinline__ float4 shade_fragment(const ShadeSoA& t, int j, float lam1, float lam2, int px, int py,
-                                                 const ShadeParams& sp)
+// Eqs. 1-4 for one fragment of triangle t at pixel (px, py); lam1, lam2 are
+// the screen-space barycentric weights of vertices 1 and 2, masks the face
+// edge flags (t.zm.w). Returns the premultiplied RGBA of Eq. 4.
+__device__ __forceinline__ float4 shade_fragment(const ShadeRec& t, uint32_t masks, float lam1, float lam2, int px,
+                                                 int py, const ShadeParams& sp)
 {
-    const float Q = fmaf(lam2, t.dq[1][j], fmaf(lam1, t.dq[0][j], t.q0[j]));   // 1 / eye depth of the fragment
+    const float4 qa = t.qa, ap = t.ap;
+    const float Q = fmaf(lam2, qa.z, fmaf(lam1, qa.y, qa.x));   // 1 / eye depth of the fragment
     const float iQ = __fdividef(1.f, Q);
     const float g = sp.ortho ? 1.f : fminf(fmaxf(sp.zref * Q, sp.g_min), sp.g_max);   // z_ref / z_eye
-    const float t_imp = fmaf(lam2, t.da[1][j], fmaf(lam1, t.da[0][j], t.a0[j])) * iQ;
+    const float t_imp = fmaf(lam2, ap.y, fmaf(lam1, ap.x, qa.w)) * iQ;
     // lens distance, normalised to 1 at the lens border
     float dist;
     if (sp.lens_mode == HEXFC_LENS_SCREEN) {
@@ -58,9 +59,10 @@ __device__ __forceinline__ float4 shade_fragment(const ShadeSoA& t, int j, float
         dist = sqrt_approx(dx * dx + dy * dy) * sp.lens_inv_r;
     } else {
         // the interpolated offset from the centre, P - C = D / Q (D affine in lam)
-        const float Dx = fmaf(lam2, t.dp[1][0][j], fmaf(lam1, t.dp[0][0][j], t.p0[0][j]));
-        const float Dy = fmaf(lam2, t.dp[1][1][j], fmaf(lam1, t.dp[0][1][j], t.p0[1][j]));
-        const float Dz = fmaf(lam2, t.dp[1][2][j], fmaf(lam1, t.dp[0][2][j], t.p0[2][j]));
+        const float4 pp = t.pp, pq = t.pq;
+        const float Dx = fmaf(lam2, pq.x, fmaf(lam1, pp.y, ap.z));
+        const float Dy = fmaf(lam2, pq.y, fmaf(lam1, pp.z, ap.w));
+        const float Dz = fmaf(lam2, pq.z, fmaf(lam1, pp.w, pp.x));
         dist = sqrt_approx(fmaf(Dx, Dx, fmaf(Dy, Dy, Dz * Dz))) * (iQ * sp.lens_inv_r);
     }
     // focus = 1 - smoothstep(0.7, 1, dist)
@@ -70,16 +72,18 @@ __device__ __forceinline__ float4 shade_fragment(const ShadeSoA& t, int j, float
     // is corner k + t e_k, t = clamp(v_k . e_k / |e_k|^2, 0, 1), with
     // v_k = sample - corner k and e_k = corner k+1 - corner k (both exact)
     const float sx = (float)(256 * px + 128), sy = (float)(256 * py + 128);
-    const float vx0 = sx - t.FX[0][j], vy0 = sy - t.FY[0][j];
+    const float4 fx = t.fx, fy = t.fy, il = t.il;
+    const float FX[4] = {fx.x, fx.y, fx.z, fx.w}, FY[4] = {fy.x, fy.y, fy.z, fy.w};
+    const float IL[4] = {il.x, il.y, il.z, il.w};
+    const float vx0 = sx - FX[0], vy0 = sy - FY[0];
     float vx = vx0, vy = vy0;   // corner k of the loop
-    const uint32_t masks = t.masks[j];
     float a2 = INFINITY, f2 = INFINITY, c2 = INFINITY;   // all edges, visible in focus, visible in context
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int k1 = (k + 1) & 3;
-        const float nx = k1 == 0 ? vx0 : sx - t.FX[k1][j], ny = k1 == 0 ? vy0 : sy - t.FY[k1][j];
+        const float nx = k1 == 0 ? vx0 : sx - FX[k1], ny = k1 == 0 ? vy0 : sy - FY[k1];
         const float ex = vx - nx, ey = vy - ny;
-        const float tp = __saturatef(fmaf(vx, ex, vy * ey) * t.inv_len2[k][j]);
+        const float tp = __saturatef(fmaf(vx, ex, vy * ey) * IL[k]);
         const float dx = fmaf(-tp, ex, vx), dy = fmaf(-tp, ey, vy);
         const float d2 = fmaf(dx, dx, dy * dy);
         a2 = fminf(a2, d2);
