@@ -85,6 +85,30 @@ def test_style_variants(hx, style_kw):
     st, _ = render_both(hx, mesh, view, synth.lissajous_lens(33, 120, radius=0.4), synth.Style(**style_kw))
 
 
+def test_both_weight_precisions(hx):
+    """The fill computes barycentric weights and depth in 32-bit arithmetic for
+    triangles of twice-area below 2^26 (16.8 units squared, 1024 square
+    pixels) and in 64-bit arithmetic above. A close-up 3^3 grid at 240x180
+    (ragged bottom tiles) draws faces of both kinds; the split is taken from
+    the oracle's own projection and the fragments' face ids."""
+    mesh = synth.hex_grid(3, jitter=0.1, warp_amp=0.2, seed=7)
+    view = synth.orbit_view(10, 120, 240, 180, radius=1.1)
+    om = oracle.Mesh(mesh.verts, mesh.cells, mesh.cell_scalar, mesh.edge_level)
+    _, X, Y, _ = om.project(view)
+    corners, _, _ = om.faces()
+    st, _ = render_both(hx, mesh, view, synth.lissajous_lens(10, 120), synth.Style())
+    keys = om.render(view, synth.lissajous_lens(10, 120), synth.Style())["keys"]
+    big = small = 0
+    for f in np.unique((keys & 0xFFFFFFFF) >> 1):
+        c = np.roll(corners[f], -int(np.argmin(corners[f])))   # the diagonal starts at the smallest vertex id
+        a2 = [abs(int(X[b] - X[a]) * int(Y[d] - Y[a]) - int(X[d] - X[a]) * int(Y[b] - Y[a]))
+              for a, b, d in ((c[0], c[1], c[2]), (c[0], c[2], c[3]))]
+        big += min(a2) >= 1 << 26
+        small += max(a2) < 1 << 26
+    assert big >= 20 and small >= 20, (big, small)
+    assert st["fragments"] > 100000
+
+
 def test_axis_aligned_cube(hx):
     v = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0], [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]],
                  np.float32) - 0.5
