@@ -233,11 +233,12 @@ def run_reference(args, rank, world):
 
 # ----------------------------------------------------------------------------- GPU arm
 
-def replica_frames(rank: int, world: int, n_frames: int, start: int, count: int) -> list:
+def replica_frames(rank: int, world: int, n_frames: int, start: int, count: int, stride: int = 1) -> list:
     """Frames of the orbit a replica renders: rank r starts r/world of the way
-    along the path, so the replicas draw different views (weak scaling)."""
+    along the path, so the replicas draw different views (weak scaling);
+    stride > 1 spreads fewer frames over the whole path."""
     f0 = (rank * n_frames) // max(world, 1)
-    return [(f0 + start + i) % n_frames for i in range(count)]
+    return [(f0 + start + i * stride) % n_frames for i in range(count)]
 
 
 def reduce_replicas(ms: float, frag_sum: float, e2e_s: float, device) -> tuple:
@@ -360,7 +361,8 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     t0 = time.perf_counter()
-    for f in replica_frames(rank, world, w.n_frames, 0, ne):
+    # spread over the whole orbit, as the device-timed frames are
+    for f in replica_frames(rank, world, w.n_frames, 0, ne, stride=max(1, w.n_frames // ne)):
         r.set_view(w.view(f))
         r.set_lens(w.lens(f))
         r.cell_quality(mid, hexfc.HEXFC_METRIC_IMPORTANCE, imp, stream)

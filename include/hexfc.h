@@ -292,8 +292,13 @@ hexfc_status hexfc_set_style(hexfc_ctx* ctx, const hexfc_style* style);
 hexfc_status hexfc_render(hexfc_ctx* ctx, int32_t mesh, float* out_rgba, hexfc_frame_stats* stats,
                           void* stream);
 
-/* As hexfc_render, with the image copied into out_rgba_host (host,
- * height*width*4 float) before the call returns. */
+/* As hexfc_render, with the image in out_rgba_host (host, height*width*4
+ * float) when the call returns, and the device-side checks of this frame
+ * reported by this call. If out_rgba_host is page-locked memory of the
+ * context's device (cudaHostAlloc, cudaHostRegister) and 16-byte aligned, the
+ * resolve kernels write the image into it directly through its device
+ * mapping; otherwise the image is rendered into a device buffer of the
+ * context and copied. On an error the buffer's contents are unspecified. */
 hexfc_status hexfc_render_host(hexfc_ctx* ctx, int32_t mesh, float* out_rgba_host,
                                hexfc_frame_stats* stats, void* stream);
 

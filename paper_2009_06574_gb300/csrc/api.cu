@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -1274,14 +1275,29 @@ hexfc_status hexfc_render_host(hexfc_ctx* ctx, int32_t mesh, float* out_rgba_hos
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     size_t bytes = sizeof(float) * 4 * (size_t)ctx->view.width * (size_t)ctx->view.height;
-    hexfc_status st = ensure(&ctx->d_out, &ctx->d_out_cap, (int64_t)(bytes / sizeof(float)));
-    if (st != HEXFC_OK) return st;
-    float* d_out = ctx->d_out;
+    // A page-locked buffer of this device, 16-byte aligned, is written by the
+    // resolve kernels through its device mapping: the image crosses to the
+    // host while they run rather than in a copy after them.
+    float* d_out = nullptr;
+    cudaPointerAttributes pa{};
+    const cudaError_t pe = cudaPointerGetAttributes(&pa, out_rgba_host);
+    if (pe != cudaSuccess) (void)cudaGetLastError();   // not a pointer CUDA knows: the copy path
+    else if (pa.type == cudaMemoryTypeHost && pa.device == ctx->device && pa.devicePointer != nullptr &&
+             ((uintptr_t)pa.devicePointer & 15u) == 0)
+        d_out = static_cast<float*>(pa.devicePointer);
+    const bool direct = d_out != nullptr;
+    hexfc_status st = HEXFC_OK;
+    if (!direct) {
+        st = ensure(&ctx->d_out, &ctx->d_out_cap, (int64_t)(bytes / sizeof(float)));
+        if (st != HEXFC_OK) return st;
+        d_out = ctx->d_out;
+    }
     st = ctx->predicted ? render_frame_predicted(ctx, m, d_out, stats, s) : render_frame(ctx, m, d_out, stats, s);
     if (st == HEXFC_OK) {
-        // the image and this frame's device error bits
+        // the image (unless written in place) and this frame's device error bits
         FrameBufs& fb = ctx->fb;
-        cudaError_t e = cudaMemcpyAsync(out_rgba_host, d_out, bytes, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = direct ? cudaSuccess
+                               : cudaMemcpyAsync(out_rgba_host, d_out, bytes, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(fb.h_scal + 5, fb.scal + 5, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -374,7 +374,8 @@ class Renderer:
         return r
 
     def render_host(self, mesh: int, out: np.ndarray, stream=None, check: bool = True):
-        """out: numpy float32 [H, W, 4] (ideally pinned)."""
+        """out: numpy float32 [H, W, 4]; if it is page-locked (pinned) and 16-byte
+        aligned, the resolve kernels write the image into it directly."""
         assert out.dtype == np.float32 and out.flags["C_CONTIGUOUS"]
         st = hexfc_frame_stats()
         r = load().hexfc_render_host(self._h, int(mesh), _np_ptr(out), C.byref(st), _stream_ptr(stream))

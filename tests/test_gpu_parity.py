@@ -328,9 +328,20 @@ def test_render_host_matches_device(hx):
     r.set_style(w.style)
     d = torch.zeros((256, 256, 4), device="cuda")
     r.render(mid, d)
-    h = np.zeros((256, 256, 4), np.float32)
+    ref = d.cpu().numpy()
+    h = np.zeros((256, 256, 4), np.float32)   # pageable: rendered on the device, then copied
     r.render_host(mid, h)
-    assert np.array_equal(d.cpu().numpy(), h)
+    assert np.array_equal(ref, h)
+    # page-locked and aligned: written in place by the resolve kernels
+    pinned = torch.zeros((256, 256, 4), dtype=torch.float32, pin_memory=True)
+    r.render_host(mid, pinned.numpy())
+    assert np.array_equal(ref, pinned.numpy())
+    # page-locked but 4 bytes off a 16-byte boundary: the copy path
+    raw = torch.zeros(256 * 256 * 4 + 4, dtype=torch.float32, pin_memory=True)
+    off = raw[1:1 + 256 * 256 * 4].view(256, 256, 4)
+    assert off.data_ptr() % 16 == 4
+    r.render_host(mid, off.numpy())
+    assert np.array_equal(ref, off.numpy())
     r.close()
 
 

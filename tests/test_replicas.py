@@ -60,3 +60,4 @@ def test_replica_frames_are_disjoint_and_cover_the_path():
         assert all(0 <= f < n for f in seen)
     # a replica walks the path from its own start, wrapping around
     assert bench.replica_frames(1, 2, 120, 58, 4) == [118, 119, 0, 1]
+    assert bench.replica_frames(0, 1, 120, 0, 60, stride=2) == list(range(0, 120, 2))
