@@ -299,7 +299,7 @@ struct FrameJob {
     int W = 0, H = 0, tiles_x = 0, tiles_y = 0;
     int64_t n_tiles = 0, n_pix = 0;
     int reverse = 0;
-    int buckets = 2048, window = 4;
+    int buckets = 2048, window = 2;
     float lens_x = 0.f, lens_y = 0.f, inv_diag = 0.f, motion = 0.f;   // capacity-network features
     bool prev_counts = false;   // fb.tile_frag holds the previous frame's counts for this tile grid
     uint64_t budget = 0;

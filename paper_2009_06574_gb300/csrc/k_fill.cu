@@ -110,12 +110,12 @@ struct FillSlot {
     int64_t area[kChunk];   // twice the area (16.8 squared)
 };
 
-// Warp queues of covered samples: entry = j | pixel << 5 | ring slot << 13 | counted << 15.
+// Warp queues of covered samples: entry = j | pixel << 5 | ring slot << 13 | counted << 16.
 constexpr int kWQ = 256;               // entries per consumer warp (a power of two)
 constexpr int kWQWin = kWQ - 32;       // entries queued per window: fewer than 32 leftovers + a window fit
-constexpr uint32_t kCounted = 1u << 15;  // the count pass sized the sample's list for it
+constexpr uint32_t kCounted = 1u << 16;  // the count pass sized the sample's list for it
 constexpr unsigned long long kErrPool = 16ull;   // error bit: no room for a tile's lists (chosen capacities)
-static_assert(kRing <= 4, "two bits of ring slot");
+static_assert(kRing <= 8, "three bits of ring slot");
 
 constexpr size_t kRawOff = (kRing * sizeof(FillSlot) + 127) & ~(size_t)127;   // face records: 128-aligned
 
@@ -199,7 +199,7 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
         const uint64_t o = w_beg + e;
         const int j = (int)(qe & 31u);
         const uint32_t pl = (qe >> 5) & 255u;
-        const FillSlot& S = s_ring[(qe >> 13) & 3u];
+        const FillSlot& S = s_ring[(qe >> 13) & 7u];
         const int lx = (int)(pl & (kTile - 1)), ly = (int)(pl / kTile);
         const ShadeRec& R = S.sh[j];
         const uint4 hd = R.hd, zm = R.zm, wd = R.wd;

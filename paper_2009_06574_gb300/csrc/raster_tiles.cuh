@@ -76,7 +76,7 @@ __device__ __forceinline__ bool cover_at(const CovSoA& c, int j, int rx, int ry,
 // producer runs up to kRing chunks ahead. Every wait is bounded; a wait that runs out sets an error bit
 // and ends the kernel's loops.
 
-constexpr int kRing = 4;
+constexpr int kRing = 6;
 constexpr int kConsumerWarps = kTilePix / 32;
 constexpr int kPipeThreads = kTilePix + 32;
 constexpr unsigned long long kErrWait = 4ull;
