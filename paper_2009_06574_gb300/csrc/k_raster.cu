@@ -303,9 +303,21 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint64_t* __restrict_
         const uint64_t nc = (tile_off[t + 1] - tile_off[t]) / kChunk;
         return (uint32_t)(kOrderBuckets - 1) - (uint32_t)min(nc, (uint64_t)(kOrderBuckets - 1));
     };
+    // the classes of tiles threadIdx.x + 1024 k, k < kReg, are read once, all
+    // loads in flight together, and kept in registers for both passes
+    constexpr int kReg = 16;
+    uint32_t cl[kReg];
+#pragma unroll
+    for (int k = 0; k < kReg; ++k) {
+        const int t = k * 1024 + threadIdx.x;
+        cl[k] = t < n_tiles ? cls(t) : 0u;
+    }
     for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) s_hist[i] = 0;
     __syncthreads();
-    for (int t0 = 0; t0 < n_tiles; t0 += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < kReg; ++k)
+        if (k * 1024 < n_tiles) warp_add_same(s_hist, cl[k], k * 1024 + (int)threadIdx.x < n_tiles);
+    for (int t0 = kReg * 1024; t0 < n_tiles; t0 += blockDim.x) {
         const int t = t0 + threadIdx.x;
         warp_add_same(s_hist, t < n_tiles ? cls(t) : 0u, t < n_tiles);
     }
@@ -334,7 +346,15 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint64_t* __restrict_
         base += v[k];
     }
     __syncthreads();
-    for (int t0 = 0; t0 < n_tiles; t0 += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < kReg; ++k) {
+        const int t = k * 1024 + threadIdx.x;
+        if (k * 1024 < n_tiles) {
+            const uint32_t slot = warp_add_same(s_hist, cl[k], t < n_tiles);
+            if (t < n_tiles) order[slot] = (uint32_t)t;
+        }
+    }
+    for (int t0 = kReg * 1024; t0 < n_tiles; t0 += blockDim.x) {
         const int t = t0 + threadIdx.x;
         const uint32_t slot = warp_add_same(s_hist, t < n_tiles ? cls(t) : 0u, t < n_tiles);
         if (t < n_tiles) order[slot] = (uint32_t)t;
