@@ -63,6 +63,20 @@ __global__ void k_vertex_setup(const float* __restrict__ verts, int64_t n, CamPa
 
 // ------------------------------------------------------------------ face stage
 
+// atomicAdd(ctr + idx, 1) for every calling lane, one atomic per distinct idx
+// among the lanes that call together; returns the value this lane's own
+// increment would have returned (lanes of one index in lane order).
+__device__ __forceinline__ uint32_t agg_inc(uint32_t* ctr, int idx)
+{
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, idx);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(ctr + idx, (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+}
+
 __device__ __forceinline__ void tile_range(const TriGeom& t, int& tx0, int& ty0, int& tx1, int& ty1)
 {
     tx0 = t.bx0 / kTile; tx1 = t.bx1 / kTile;
@@ -110,7 +124,7 @@ __global__ void k_face_setup(const int4* __restrict__ fverts, const int4* __rest
         int tx0, ty0, tx1, ty1;
         tile_range(t, tx0, ty0, tx1, ty1);
         for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(tile_cnt + ty * tiles_x + tx, 1u);
+            for (int tx = tx0; tx <= tx1; ++tx) agg_inc(tile_cnt, ty * tiles_x + tx);
     }
     FaceFrame& r = fframe[f];
     r.X = make_int4(X[0], X[1], X[2], X[3]);
@@ -142,7 +156,7 @@ __global__ void k_bin_fill(const FaceFrame* __restrict__ fframe, int64_t n_faces
         for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx) {
                 int tile = ty * tiles_x + tx;
-                const uint32_t slot = atomicAdd(tile_cur + tile, 1u);
+                const uint32_t slot = agg_inc(tile_cur, tile);
                 bins[tile_off[tile] + slot] = (uint32_t)(2 * f + tri);
             }
     }
