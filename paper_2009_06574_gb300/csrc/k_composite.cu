@@ -285,6 +285,18 @@ __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ 
             mk_next = mp[(uint64_t)(ch + 1) * kTilePix];
             sg_next = sp[(uint64_t)(ch + 1) * kGroups];
         }
+        // the group reads its region chunk after chunk (a run is about 75
+        // records at 1920x1080): the 128 records from 96 past this chunk's
+        // run start are brought into L2 while the chunk is placed (lanes 0-7
+        // a key line each, 8-23 a colour line each; wider or longer spans
+        // measured slower)
+        if (lane < 24) {
+            const uint64_t r = lane < 8 ? sg + 96 + 16 * (uint64_t)lane : sg + 96 + 8 * (uint64_t)(lane - 8);
+            if (r < frag_cap) {
+                const void* a = lane < 8 ? (const void*)(key + r) : (const void*)(rgba + r);
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+            }
+        }
         const uint32_t h = __popc(m);
         uint32_t incl = h;
 #pragma unroll
