@@ -194,15 +194,25 @@ __device__ __forceinline__ void list_walk(const uint64_t* __restrict__ tile_off,
     const uint64_t cb = tile_off[tile] / kChunk, ce = tile_off[tile + 1] / kChunk;
     const uint32_t* mp = masks + cb * kTilePix + (g0 % kTilePix) + lane;
     uint32_t k = 0;
-    for (uint64_t c = cb; c < ce; ++c, mp += kTilePix) {
-        const uint32_t h = __popc(*mp);
-        const uint32_t before = __reduce_add_sync(kFull, (uint32_t)lane < l ? h : 0u);
-        const uint32_t hl = __shfl_sync(kFull, h, l);
-        if (hl == 0) continue;
-        const uint64_t e = seg[c * kGroups + grp] + before;
-        for (uint32_t t = lane; t < hl; t += 32)
-            if (k + t < limit && e + t < frag_cap) f(k + t, e + t);   // (records beyond the arrays: skipped)
-        k += hl;
+    // eight chunks at a time: their masks and run starts are loaded together
+    for (uint64_t c0 = cb; c0 < ce; c0 += 8, mp += 8 * kTilePix) {
+        uint32_t mm[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) mm[i] = c0 + i < ce ? mp[i * kTilePix] : 0u;
+        const uint64_t cl = c0 + (uint64_t)(lane & 7);
+        const unsigned long long sgl = cl < ce ? seg[cl * kGroups + grp] : 0ull;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t h = __popc(mm[i]);
+            const uint32_t before = __reduce_add_sync(kFull, (uint32_t)lane < l ? h : 0u);
+            const uint32_t hl = __shfl_sync(kFull, h, l);
+            const uint64_t sg = __shfl_sync(kFull, sgl, i);
+            if (hl == 0) continue;
+            const uint64_t e = sg + before;
+            for (uint32_t t = lane; t < hl; t += 32)
+                if (k + t < limit && e + t < frag_cap) f(k + t, e + t);   // (records beyond the arrays: skipped)
+            k += hl;
+        }
     }
 }
 
