@@ -295,24 +295,27 @@ __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ 
             mk_next = mp[(uint64_t)(ch + 1) * kTilePix];
             sg_next = sp[(uint64_t)(ch + 1) * kGroups];
         }
-        // the group reads its region chunk after chunk (a run is about 75
-        // records at 1920x1080): the 128 records from 96 past this chunk's
-        // run start are brought into L2 while the chunk is placed (lanes 0-7
-        // a key line each, 8-23 a colour line each; wider or longer spans
-        // measured slower)
-        if (lane < 24) {
-            const uint64_t r = lane < 8 ? sg + 96 + 16 * (uint64_t)lane : sg + 96 + 8 * (uint64_t)(lane - 8);
-            if (r < frag_cap) {
-                const void* a = lane < 8 ? (const void*)(key + r) : (const void*)(rgba + r);
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
-            }
-        }
         const uint32_t h = __popc(m);
         uint32_t incl = h;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += t;
+        }
+        // The group reads its region chunk after chunk, each run right after
+        // the last: the 128 records from 24 past the end of this chunk's run
+        // are brought into L2 while the chunk is placed (lanes 0-7 a key line
+        // each, 8-23 a colour line each). Placing the span by the run start
+        // of the next chunk waits for that load; wider spans measured slower.
+        {
+            const uint64_t nb = sg + __shfl_sync(kFull, incl, 31) + 24;
+            if (lane < 24) {
+                const uint64_t r = lane < 8 ? nb + 16 * (uint64_t)lane : nb + 8 * (uint64_t)(lane - 8);
+                if (r < frag_cap) {
+                    const void* a = lane < 8 ? (const void*)(key + r) : (const void*)(rgba + r);
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+                }
+            }
         }
         if (h == 0) continue;
         const uint64_t e = sg + incl - h;
