@@ -37,7 +37,7 @@ FRAG_BYTES = 24          # 8 B key + 16 B premultiplied RGBA
 # one pass, on the 1920x1080 bench frame), per fragment drawn, and the fill kernel's
 # sources it was taken on: the roofline reports it only while those sources are unchanged.
 FILL_DRAM = {"bytes_per_fragment": 27.60,
-             "sha256": "bb4deeab2e438f719fa54e9a34dbbf7329d7b462b0e3982ea358b3c8bc79503f",
+             "sha256": "d30ba66788bc028bc5cb7dde76ece9b2c6703544e08696e880d0a9bc789c413e",
              "profile": "profiles/dram_k_fill_k_count_k_composite_grid64_orbit_1080p.md"}
 FILL_SOURCES = ("csrc/k_fill.cu", "csrc/raster_tiles.cuh", "csrc/shade.cuh", "csrc/raster_common.cuh",
                 "csrc/pipeline.cuh", "csrc/hexfc_internal.cuh")

@@ -23,11 +23,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
 }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
 // Waits for the phase with parity `parity` to complete; false if the bound ran out.
 __device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity)
 {
@@ -55,24 +50,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
     }
     return false;
 }
-// Bulk copy global -> shared (16-byte aligned, size a multiple of 16), completion on `bar`.
-__device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, unsigned bytes, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-            smem_addr(smem)),
-        "l"(gmem), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-// Per-thread asynchronous copies global -> shared (4, 8 or 16 bytes, naturally aligned).
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
-}
+// Per-thread asynchronous copy global -> shared (16 bytes, 16-byte aligned).
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
@@ -80,8 +58,5 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// Order earlier generic-proxy shared-memory accesses before later async-proxy writes.
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 }  // namespace hexfc

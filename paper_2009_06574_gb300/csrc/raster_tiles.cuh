@@ -49,22 +49,6 @@ __device__ __forceinline__ void stage_cov(int4 a, int4 b, uint32_t f2t, int W, i
     c.box[j] = (x0 - px0) | ((y0 - py0) << 8) | ((x1 - x0 + 1) << 16) | ((y1 - y0 + 1) << 24);
 }
 
-// Exact coverage of the sample (rx, ry) pixels from the box origin of
-// triangle j; l[k] = edge function k = weight of vertex k (sum = the area).
-__device__ __forceinline__ bool cover_at(const CovSoA& c, int j, int rx, int ry, int64_t l[3])
-{
-    const int32_t sx = rx << 8, sy = ry << 8;
-    const uint32_t meta = c.meta[j];
-    bool in = true;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        int64_t e = c.e0[k][j] + (int64_t)c.dx[k][j] * sy - (int64_t)c.dy[k][j] * sx;
-        l[k] = e;
-        in = in && (e > 0 || (e == 0 && ((meta >> k) & 1u)));
-    }
-    return in;
-}
-
 // ------------------------------------------------------------------ tile passes
 //
 // k_fill runs one block per tile as a pipeline: a producer warp stages each
