@@ -125,6 +125,13 @@ def lib():
             L.orc_smoothstep.argtypes = [C.c_double, C.c_double, C.c_double]
             L.orc_project_vertices.argtypes = [vp, C.POINTER(_View), vp, vp, vp, vp]
             L.orc_cover_raw.restype = C.c_int
+            L.orc_fragment_geometry.restype = C.c_int
+            L.orc_fragment_geometry.argtypes = [vp, C.POINTER(_View), C.POINTER(_Lens),
+                                                C.POINTER(_Style), C.c_int32, C.c_int32,
+                                                C.c_uint32, vp, vp]
+            L.orc_segment_distance.restype = C.c_double
+            L.orc_segment_distance.argtypes = [C.c_int64, C.c_int64, C.c_int32, C.c_int32,
+                                               C.c_int32, C.c_int32]
             L.orc_cover_raw.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int, C.c_int]
     return _lib
 
@@ -172,6 +179,14 @@ def cover_raw(X, Y, px, py, W=1 << 14, H=1 << 14) -> int:
     Xa = np.ascontiguousarray(X, dtype=np.int32)
     Ya = np.ascontiguousarray(Y, dtype=np.int32)
     return lib().orc_cover_raw(_ptr(Xa), _ptr(Ya), int(px), int(py), int(W), int(H))
+
+
+def segment_distance(sx, sy, ax, ay, bx, by) -> float:
+    """Pixel distance from a sample to a segment, all given in 1/256 pixel units."""
+    return lib().orc_segment_distance(int(sx), int(sy), int(ax), int(ay), int(bx), int(by))
+
+
+GEOMETRY_FIELDS = ("dist", "d_f", "d_c", "d_a", "g", "z_eye", "t_imp")
 
 
 class Mesh:
@@ -258,6 +273,24 @@ class Mesh:
         np.cumsum(counts, out=off[1:])
         return {"counts": counts, "offsets": off, "keys": keys[:tot], "rgba": rgba[:tot],
                 "tie": tie[:tot], "image": image}
+
+    def fragment_geometry(self, view, lens, style, px, py, face2tri):
+        """Inputs of the focus+context formulas for one fragment, or None if the
+        triangle does not cover the pixel: a dict with dist, d_f, d_c, d_a, g,
+        z_eye, t_imp, P (world position), b (vertex weights) and vi (face corner
+        index of each weighted vertex)."""
+        out = np.zeros(13, dtype=np.float64)
+        vi = np.zeros(3, dtype=np.int32)
+        v, l, s = _view(view), _lens(lens), _style(style)
+        ok = lib().orc_fragment_geometry(self._h, C.byref(v), C.byref(l), C.byref(s), int(px),
+                                         int(py), int(face2tri), _ptr(out), _ptr(vi))
+        if not ok:
+            return None
+        d = {k: float(out[i]) for i, k in enumerate(GEOMETRY_FIELDS)}
+        d["P"] = out[7:10].copy()
+        d["b"] = out[10:13].copy()
+        d["vi"] = vi
+        return d
 
     def shade(self, view, lens, style, px, py, face2tri, flip=0):
         """Shade one fragment with decisions in `flip` inverted; None if not covered."""

@@ -687,11 +687,24 @@ static void orc_frame_free(orc_frame* fr)
     free(fr->tri);
 }
 
-/* Shade the fragment of face f, triangle tri at pixel (px,py), whose exact
- * barycentric weights are l (Section "Focus+Context", readings R6-R11). */
-static void orc_shade_frag(const orc_mesh* m, const orc_frame* fr, const orc_lens* lens,
-                           const orc_style* st, int64_t f, int tri, int32_t px, int32_t py,
-                           const int64_t l[3], int flip, double rgba[4], int* tie)
+/* Geometric quantities of one fragment, the inputs of the focus+context
+ * formulas (Section "Focus+Context", readings R6, R8, R9, R10). */
+typedef struct {
+    double dist;           /* normalised lens distance (R6) */
+    double d_f, d_c, d_a;  /* edge distances per visibility class, pixels (R8) */
+    double g;              /* depth factor of the edge width (R9) */
+    double z_eye;          /* eye-space depth of the sample */
+    double t_imp;          /* interpolated vertex importance (R10) */
+    double P[3];           /* interpolated world position */
+    double b[3];           /* interpolation weights of the triangle's vertices */
+} orc_geom;
+
+/* Fragment geometry of face f, triangle tri at pixel (px,py), whose exact
+ * barycentric weights are l: perspective-correct weights, importance, world
+ * position and eye depth, lens distance, edge distances and depth factor. */
+static void orc_frag_geometry(const orc_mesh* m, const orc_frame* fr, const orc_lens* lens,
+                              const orc_style* st, int64_t f, int tri, int32_t px, int32_t py,
+                              const int64_t l[3], orc_geom* G)
 {
     const orc_tri* t = &fr->tri[2 * f + tri];
     const orc_face* F = &m->faces[f];
@@ -748,7 +761,28 @@ static void orc_shade_frag(const orc_mesh* m, const orc_frame* fr, const orc_len
         if (g < st->g_min) g = st->g_min;
         if (g > st->g_max) g = st->g_max;
     }
-    orc_fc_shade(st, dist, d_f, d_c, d_a, g, t_imp, flip, rgba, tie);
+    G->dist = dist;
+    G->d_f = d_f;
+    G->d_c = d_c;
+    G->d_a = d_a;
+    G->g = g;
+    G->z_eye = z_eye;
+    G->t_imp = t_imp;
+    for (int k = 0; k < 3; ++k) {
+        G->P[k] = P[k];
+        G->b[k] = b[k];
+    }
+}
+
+/* Shade the fragment of face f, triangle tri at pixel (px,py), whose exact
+ * barycentric weights are l (Section "Focus+Context", readings R6-R11). */
+static void orc_shade_frag(const orc_mesh* m, const orc_frame* fr, const orc_lens* lens,
+                           const orc_style* st, int64_t f, int tri, int32_t px, int32_t py,
+                           const int64_t l[3], int flip, double rgba[4], int* tie)
+{
+    orc_geom G;
+    orc_frag_geometry(m, fr, lens, st, f, tri, px, py, l, &G);
+    orc_fc_shade(st, G.dist, G.d_f, G.d_c, G.d_a, G.g, G.t_imp, flip, rgba, tie);
 }
 
 typedef struct {
@@ -842,6 +876,24 @@ int64_t orc_render(const orc_mesh* m, const orc_view* v, const orc_lens* lens, c
     return fits ? total : -1;
 }
 
+/* A frame holding only the four corners of face f and its triangle tri:
+ * enough to shade that face's fragments. */
+static int orc_face_frame(const orc_mesh* m, const orc_view* v, int64_t f, int tri, orc_frame* fr)
+{
+    if (f < 0 || f >= m->n_faces) return 0;
+    orc_camera(v, &fr->cam);
+    fr->pv = (orc_pv*)calloc((size_t)m->n_verts, sizeof(orc_pv));
+    for (int k = 0; k < 4; ++k) {
+        int32_t vid = m->faces[f].c[k];
+        orc_project(&fr->cam, &m->verts[3 * (int64_t)vid], &fr->pv[vid]);
+    }
+    fr->tri = (orc_tri*)calloc(2 * (size_t)m->n_faces, sizeof(orc_tri));
+    orc_pv pv[4];
+    for (int k = 0; k < 4; ++k) pv[k] = fr->pv[m->faces[f].c[k]];
+    orc_setup_tri(pv, tri, v->width, v->height, &fr->tri[2 * f + tri]);
+    return 1;
+}
+
 /*
  * Shade one fragment (face2tri = 2 face + tri at pixel px,py) with the
  * decisions in flip inverted. Returns 1 and fills rgba/tie if the triangle
@@ -852,27 +904,50 @@ int orc_shade(const orc_mesh* m, const orc_view* v, const orc_lens* lens, const 
 {
     int64_t f = face2tri / 2;
     int tri = (int)(face2tri % 2);
-    if (f >= m->n_faces) return 0;
-    orc_cam cam;
-    orc_camera(v, &cam);
     orc_frame fr;
-    fr.cam = cam;
-    /* only the four corners of this face are needed */
-    fr.pv = (orc_pv*)calloc((size_t)m->n_verts, sizeof(orc_pv));
-    for (int k = 0; k < 4; ++k) {
-        int32_t vid = m->faces[f].c[k];
-        orc_project(&cam, &m->verts[3 * (int64_t)vid], &fr.pv[vid]);
-    }
-    fr.tri = (orc_tri*)calloc(2 * (size_t)m->n_faces, sizeof(orc_tri));
-    orc_pv pv[4];
-    for (int k = 0; k < 4; ++k) pv[k] = fr.pv[m->faces[f].c[k]];
-    orc_setup_tri(pv, tri, v->width, v->height, &fr.tri[2 * f + tri]);
+    if (!orc_face_frame(m, v, f, tri, &fr)) return 0;
     int64_t l[3];
     int ok = orc_covers(&fr.tri[2 * f + tri], px, py, l);
     if (ok) orc_shade_frag(m, &fr, lens, st, f, tri, px, py, l, flip, rgba, tie);
-    free(fr.pv);
-    free(fr.tri);
+    orc_frame_free(&fr);
     return ok;
+}
+
+/*
+ * Test hook: the geometric inputs of the focus+context formulas for one
+ * fragment (face2tri at pixel px,py). out[0..13] = dist, d_f, d_c, d_a, g,
+ * z_eye, t_imp, P[3], b[3] (the weights of the triangle's vertices in the
+ * winding order of the coverage setup), and vi[0..2] = the face corner index
+ * (0..3) of each of those vertices. Returns 1 if the triangle covers the
+ * pixel, 0 otherwise.
+ */
+int orc_fragment_geometry(const orc_mesh* m, const orc_view* v, const orc_lens* lens,
+                          const orc_style* st, int32_t px, int32_t py, uint32_t face2tri,
+                          double out[13], int32_t vi[3])
+{
+    int64_t f = face2tri / 2;
+    int tri = (int)(face2tri % 2);
+    orc_frame fr;
+    if (!orc_face_frame(m, v, f, tri, &fr)) return 0;
+    int64_t l[3];
+    int ok = orc_covers(&fr.tri[2 * f + tri], px, py, l);
+    if (ok) {
+        orc_geom G;
+        orc_frag_geometry(m, &fr, lens, st, f, tri, px, py, l, &G);
+        double vals[13] = {G.dist, G.d_f, G.d_c, G.d_a, G.g, G.z_eye, G.t_imp,
+                           G.P[0], G.P[1], G.P[2], G.b[0], G.b[1], G.b[2]};
+        memcpy(out, vals, sizeof(vals));
+        for (int k = 0; k < 3; ++k) vi[k] = fr.tri[2 * f + tri].vi[k];
+    }
+    orc_frame_free(&fr);
+    return ok;
+}
+
+/* Test hook: pixel distance from sample (sx,sy) to the segment a-b, all in
+ * 1/256 pixel units (reading R8). */
+double orc_segment_distance(int64_t sx, int64_t sy, int32_t ax, int32_t ay, int32_t bx, int32_t by)
+{
+    return seg_dist(sx, sy, ax, ay, bx, by);
 }
 
 /* Front-to-back compositing of n premultiplied fragments (already sorted). */
