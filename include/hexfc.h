@@ -323,8 +323,13 @@ enum {
                                         in the faces' order: a test hook for the sorting passes) */
     HEXFC_OPT_COMPOSITE_WINDOW = 4,  /* sorted window of the per-pixel resolve: 2 (default), 4 or 8; the
                                         image does not depend on it, bit for bit */
-    HEXFC_OPT_PREDICTED_CAPACITY = 5 /* 0: count-then-fill (default); 1: capacities from the previous
+    HEXFC_OPT_PREDICTED_CAPACITY = 5, /* 0: count-then-fill (default); 1: capacities from the previous
                                         frame's tile counts; 2: from the capacity network. See below. */
+    HEXFC_OPT_DEBUG_ERROR_BITS = 6   /* test hook, bits 0..7: after the last kernel of the next
+                                        hexfc_render or hexfc_render_noalloc frame, these bits are set
+                                        in the device error word as a kernel of that frame would set
+                                        them (4: a bounded wait ran out, 1: a failed check); no wait
+                                        runs out and nothing faults. One frame only. */
 };
 hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value);
 
@@ -419,18 +424,24 @@ const char* hexfc_cuda_error_name(int32_t code);
  * cudaMallocHost; the mesh must already be uploaded, and out_rgba (device,
  * height*width*4 float) is the caller's.
  *
- * - The first call on a device looks up the array's device address (with that
- *   device current) and keeps it; make that first call before any stream
+ * - Every call looks up the array's device address on the current device
+ *   (ctx's device). The first call on a device loads the library's module
+ *   there, which creates the array: make that first call before any stream
  *   capture on that device.
  * - All calls share the one array and it keeps the last call's contents (the
  *   counters that must start at zero are cleared on the stream). Calls whose
  *   work overlaps on the GPU (other streams, other threads, other contexts of
  *   the same process on the same device) race on it: serialise them.
- * - It waits on `stream` twice, like hexfc_render; stage timing is not recorded
- *   and hexfc_debug_pixels keeps referring to the last hexfc_render* frame.
+ * - It waits on `stream` twice, like hexfc_render, and returns with the fill
+ *   and the composite still running. Their device error bits (a bounded wait
+ *   that ran out, a failed exactness check) stay in the array and are
+ *   reported, as TIMEOUT or CHECK, by the next hexfc_render_noalloc call on
+ *   the same device, as hexfc_render reports its previous frame's.
+ * - Stage timing is not recorded and hexfc_debug_pixels keeps referring to the
+ *   last hexfc_render* frame.
  * Errors: ARG, STATE (no view or bad mesh), OVERFLOW (the frame needs more
  * than HEXFC_NOALLOC_SCRATCH_BYTES, or a list longer than HEXFC_MAX_LIST;
- * nothing is drawn, stats is filled as far as known), CUDA.
+ * nothing is drawn, stats is filled as far as known), TIMEOUT, CHECK, CUDA.
  */
 hexfc_status hexfc_render_noalloc(hexfc_ctx* ctx, int32_t mesh, float* out_rgba, hexfc_frame_stats* stats,
                                   void* stream);

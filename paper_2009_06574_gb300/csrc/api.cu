@@ -29,6 +29,7 @@ struct hexfc_ctx {
     int depth_buckets = 2048;   // HEXFC_OPT_DEPTH_BUCKETS
     int window = 2;             // HEXFC_OPT_COMPOSITE_WINDOW
     int predicted = 0;          // HEXFC_OPT_PREDICTED_CAPACITY
+    uint64_t inject_bits = 0;   // HEXFC_OPT_DEBUG_ERROR_BITS: ORed into the error word after the next frame
     // exact tile counts of the last frame (fb.tile_frag) are valid for this size
     int counts_W = 0, counts_H = 0;
     uint64_t counts_total = 0;
@@ -82,6 +83,14 @@ inline void note_cuda(cudaError_t e)
 inline hexfc_status device_error_status(uint64_t bits)
 {
     return (bits & 6ull) ? HEXFC_ERR_TIMEOUT : HEXFC_ERR_CHECK;
+}
+
+// Test hook (HEXFC_OPT_DEBUG_ERROR_BITS): set error bits in the device word
+// as a kernel of the frame would, so that the host's reporting of them can be
+// tested without making any device wait run out.
+__global__ void k_or_error_bits(unsigned long long* word, unsigned long long bits)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(word, bits);
 }
 
 #define CK(x)                                   \
@@ -560,6 +569,20 @@ hexfc_status job_phase3(FrameJob& j, cudaStream_t s)
     return HEXFC_OK;
 }
 
+inline uint64_t* fb_of(FrameJob& j) { return j.fb->scal; }
+
+// HEXFC_OPT_DEBUG_ERROR_BITS: after the frame's last kernel, set the requested
+// bits in the device error word (one frame only).
+hexfc_status inject_error_bits(hexfc_ctx* ctx, uint64_t* scal, cudaStream_t s)
+{
+    if (!ctx->inject_bits) return HEXFC_OK;
+    k_or_error_bits<<<1, 32, 0, s>>>(reinterpret_cast<unsigned long long*>(scal + 5),
+                                     (unsigned long long)ctx->inject_bits);
+    ctx->inject_bits = 0;
+    CK(cudaGetLastError());
+    return HEXFC_OK;
+}
+
 // Bins, counts, scan, fill and composite of one frame (everything but the output copy).
 hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_stats* stats, cudaStream_t s)
 {
@@ -583,6 +606,7 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
     if (stats) *stats = j.fs;
     if (st != HEXFC_OK) return st;
     if ((st = job_phase3(j, s)) != HEXFC_OK) return st;
+    if ((st = inject_error_bits(ctx, fb_of(j), s)) != HEXFC_OK) return st;
     ctx->ev_pending[ctx->ev_cur] = ctx->timing;
     ctx->last.kernel_launches = j.launches;
     if (stats) stats->kernel_launches = j.launches;
@@ -1404,6 +1428,10 @@ hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value)
         if (value < 0 || value > 2) return HEXFC_ERR_ARG;
         ctx->predicted = (int)value;
         return HEXFC_OK;
+    case HEXFC_OPT_DEBUG_ERROR_BITS:
+        if (value < 0 || value > 7) return HEXFC_ERR_ARG;
+        ctx->inject_bits = (uint64_t)value;
+        return HEXFC_OK;
     default: return HEXFC_ERR_ARG;
     }
 }
@@ -1459,22 +1487,20 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[HEXFC_NOALLOC_S
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-void* g_noalloc_ptr[kMaxDevices] = {};
-
-// Device address of g_noalloc_scratch on `device` (current); nullptr on failure.
-void* noalloc_scratch(int device)
+// Device address of g_noalloc_scratch on the current device; nullptr on
+// failure. Looked up on every call (a table lookup in the runtime; nothing is
+// allocated), so that concurrent first calls from several host threads need no
+// lock and a context created after cudaDeviceReset gets the new address. The
+// first lookup on a device loads this file's module there, which creates the
+// array: that first call should come before any stream capture.
+void* noalloc_scratch()
 {
-    if (device < 0 || device >= kMaxDevices) return nullptr;
-    if (!g_noalloc_ptr[device]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
-            (void)cudaGetLastError();
-            return nullptr;
-        }
-        g_noalloc_ptr[device] = p;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
     }
-    return g_noalloc_ptr[device];
+    return p;
 }
 
 // Bump carving of the scratch array in 256-byte aligned pieces.
@@ -1494,7 +1520,7 @@ struct Arena {
 
 hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_stats* stats, cudaStream_t s)
 {
-    unsigned char* scratch = static_cast<unsigned char*>(noalloc_scratch(ctx->device));
+    unsigned char* scratch = static_cast<unsigned char*>(noalloc_scratch());
     if (!scratch) return HEXFC_ERR_CUDA;
     const int W = ctx->view.width, H = ctx->view.height;
     const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
@@ -1503,6 +1529,9 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     const int64_t nparts = scan_partials_needed(std::max<int64_t>(n_pix, n_tiles)) + 1;
     Arena a{scratch, 0, (size_t)HEXFC_NOALLOC_SCRATCH_BYTES};
     FrameBufs fb;
+    // the device scalars first, at the same place in every call: slot 5, the
+    // device error word, outlives the call (see below)
+    fb.scal = a.take<uint64_t>(kScal);
     fb.vproj = a.take<int4>((size_t)m->n_verts);
     fb.ved = a.take<float>((size_t)m->n_verts);
     fb.fframe = a.take<FaceFrame>((size_t)m->n_faces);
@@ -1519,7 +1548,6 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fb.fix_q = a.take<uint32_t>((size_t)n_pix + 1);
     fb.part = a.take<uint64_t>(2 * (size_t)nparts);
     fb.part_max = a.take<uint32_t>(2 * (size_t)nparts);
-    fb.scal = a.take<uint64_t>(kScal);
     if (!fb.vproj || !fb.ved || !fb.fframe || !fb.tzsum || !fb.tile_cnt ||
         !fb.tile_off || !fb.tile_cur || !fb.tile_order || !fb.tile_frag || !fb.tile_zr || !fb.cnt || !fb.off || !fb.long_q || !fb.fix_q || !fb.part || !fb.part_max ||
         !fb.scal)
@@ -1527,7 +1555,12 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     // the array keeps the previous call's contents: clear what must start at zero
     CK(cudaMemsetAsync(fb.tile_cnt, 0, sizeof(uint32_t) * (size_t)n_tiles, s));
     CK(cudaMemsetAsync(fb.tile_cur, 0, sizeof(uint32_t) * (size_t)n_tiles, s));
-    CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * kScal, s));
+    // all device scalars but the error word (slot 5): the fill and the composite
+    // of the previous call on this device may have set bits there after that
+    // call returned, and they are reported below, by this call (the array starts
+    // zeroed when the module is loaded)
+    CK(cudaMemsetAsync(fb.scal, 0, sizeof(uint64_t) * 5, s));
+    CK(cudaMemsetAsync(fb.scal + 6, 0, sizeof(uint64_t) * (kScal - 6), s));
     CK(launch_vertex_setup(*m, ctx->cam, fb, s));
     CK(launch_face_setup(*m, ctx->cam, ctx->style.lod, ctx->style.delta, fb, tiles_x, tiles_y, s));
     CK(scan_u32_to_u64(fb.tile_cnt, fb.tile_off, n_tiles, fb.part, fb.part_max, fb.scal + 8, 0xFFFFFFFFu, s,
@@ -1556,7 +1589,12 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     CK(scan_u32_to_u64(fb.cnt, fb.off, n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
     CK(cudaMemcpyAsync(h, fb.scal, 6 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (h[5] != 0) return device_error_status(h[5]);
+    if (h[5] != 0) {   // this call's count pass, or the previous call's fill or composite
+        CK(cudaMemsetAsync(fb.scal + 5, 0, sizeof(uint64_t), s));
+        CK(cudaStreamSynchronize(s));
+        if (stats) *stats = fs;
+        return device_error_status(h[5]);
+    }
     const uint64_t total = h[0];
     const uint32_t n_long = (uint32_t)h[2];
     fs.fragments = total;
@@ -1572,7 +1610,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     ShadeParams sp = make_shade(ctx);
     CK(launch_fill(*m, fb, sp, tiles_x, tiles_y, W, H, false, s));
     CK(launch_composite(fb, sp, tiles_x, tiles_y, W, H, out, n_long, ctx->window, s));
-    return HEXFC_OK;
+    return inject_error_bits(ctx, fb.scal, s);
 }
 
 }  // namespace

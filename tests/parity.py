@@ -74,3 +74,18 @@ def compare_lists(gpu: dict, orc: dict, om: "oracle.Mesh", view, lens, style, px
         assert stats["max_pixel_err"] <= tol, (f"pixel ({px[worst]},{py[worst]}) gpu {gpu_image[worst]} "
                                                f"oracle {exp[worst]} err {ie[worst]:.3g}")
     return stats
+
+
+def check_sampled(r, mesh, view, lens, style, image, n: int = 1500, seed: int = 0, lists_from=None):
+    """Sampled pixels of a GPU frame against the oracle. r: the Renderer whose
+    last hexfc_render* frame holds the fragment lists (lists_from overrides it
+    when the image came from a path without readable lists, e.g. a batch item
+    redrawn alone); image: that frame's [H, W, 4] image (numpy or torch)."""
+    rng = np.random.default_rng(seed)
+    px = rng.integers(0, view.width, n).astype(np.int32)
+    py = rng.integers(0, view.height, n).astype(np.int32)
+    g = (lists_from or r).debug_pixels(px, py)
+    om = oracle.Mesh(mesh.verts, mesh.cells, mesh.cell_scalar, mesh.edge_level)
+    o = om.render(view, lens, style, px, py)
+    img = image.cpu().numpy() if hasattr(image, "cpu") else np.asarray(image)
+    return compare_lists(g, o, om, view, lens, style, px, py, gpu_image=img[py, px])

@@ -8,6 +8,8 @@ import torch
 
 from paper_2009_06574_gb300 import synth
 
+from parity import check_sampled
+
 pytestmark = pytest.mark.gpu
 
 
@@ -48,19 +50,26 @@ def _alone(r, item):
 
 def test_batch_matches_frames_drawn_alone(hx):
     r = hx.Renderer(0)
-    ids = []
+    ids, meshes = [], {}
     for n, seed in ((5, 3), (7, 4)):
         m = synth.hex_grid(n, jitter=0.1, warp_amp=0.25, seed=seed)
         ids.append(r.upload_mesh(m.verts, m.cells, m.cell_scalar, m.edge_level))
+        meshes[ids[-1]] = m
+    checked = 0
     for seed, k in ((1, 6), (2, 6), (3, 4)):   # new views (graphs updated), then another size
         items = _items(ids, k, seed)
         st, per, stats = r.render_batch(items)
         torch.cuda.synchronize()
         assert st == 0 and all(p == 0 for p in per)
-        for it, s in zip(items, stats):
+        for i, (it, s) in enumerate(zip(items, stats)):
             img, alone_stats = _alone(r, it)
             np.testing.assert_array_equal(it[4].cpu().numpy(), img)
             assert s["fragments"] == alone_stats["fragments"] and s["bin_entries"] == alone_stats["bin_entries"]
+            if seed == 1:   # the batch images against the oracle (lists of the frame drawn alone)
+                mid, view, lens, style, out = it
+                check_sampled(r, meshes[mid], view, lens, style, out, n=600, seed=i)
+                checked += 1
+    assert checked == 6
     r.close()
 
 

@@ -9,6 +9,8 @@ import torch
 from oracle import capacity_mlp as mlp
 from paper_2009_06574_gb300 import synth
 
+from parity import check_sampled
+
 pytestmark = pytest.mark.gpu
 
 
@@ -88,6 +90,9 @@ def test_network_capacities_draw_exact_frames(hx):
             imgs.append(o.cpu().numpy())
         np.testing.assert_array_equal(imgs[1], imgs[0])
         n_pred += pr.last_stats["predicted"]
+        if f == 9 and pr.last_stats["predicted"]:   # network capacities, against the oracle
+            st = check_sampled(pr, m, view, lens, style, imgs[1], seed=f)
+            assert st["fragments"] > 1000
         pr.capacity_train(20, lr=3e-3)
     assert n_pred >= 5
     ex.close(); pr.close()

@@ -26,7 +26,7 @@ def hx():
     return hexfc
 
 
-def render_both(hx, mesh, view, lens, style, px=None, py=None, scalar=None, options=None):
+def render_both(hx, mesh, view, lens, style, px=None, py=None, scalar=None, options=None, cap_per_pixel=None):
     scalar = mesh.cell_scalar if scalar is None else scalar
     r = hx.Renderer(0)
     for opt, val in (options or {}).items():
@@ -44,7 +44,10 @@ def render_both(hx, mesh, view, lens, style, px=None, py=None, scalar=None, opti
     g = r.debug_pixels(px, py)
     img = out.cpu().numpy()[py, px]
     om = oracle.Mesh(mesh.verts, mesh.cells, scalar, mesh.edge_level)
-    o = om.render(view, lens, style, px, py)
+    # a capacity bound spares the oracle its separate counting pass (a full scan
+    # of all triangles per pixel); without one it counts first
+    cap = None if cap_per_pixel is None else int(cap_per_pixel) * len(px)
+    o = om.render(view, lens, style, px, py, cap=cap)
     stats = compare_lists(g, o, om, view, lens, style, px, py, gpu_image=img)
     stats["gpu_stats"] = r.last_stats
     r.close()
@@ -244,20 +247,48 @@ def test_tiny_viewport(hx):
     render_both(hx, mesh, view, synth.lissajous_lens(5, 120), synth.Style())
 
 
-def test_full_size_sampled(hx):
-    """64^3 warped grid at 1920x1080 (one orbit frame): sampled pixels and a
-    crop against the oracle, in the launch configuration of the benchmark."""
+def _sample_with_crops(rng, width, height, n, crops):
+    """n random pixels plus the pixels of each crop (x0, y0, w, h)."""
+    px = [rng.integers(0, width, n)]
+    py = [rng.integers(0, height, n)]
+    for (x0, y0, cw, ch) in crops:
+        cy, cx = np.meshgrid(np.arange(y0, y0 + ch), np.arange(x0, x0 + cw), indexing="ij")
+        px.append(cx.ravel())
+        py.append(cy.ravel())
+    return np.concatenate(px).astype(np.int32), np.concatenate(py).astype(np.int32)
+
+
+@pytest.mark.parametrize("frame", [7, 45, 93])
+def test_full_size_sampled(hx, frame):
+    """64^3 warped grid at 1920x1080, three orbit frames: 4,096 random pixels and
+    a 64x64 crop against the oracle, in the launch configuration of the
+    benchmark (the crop moves with the frame: centre, then near the right and
+    bottom edges of the mesh's footprint)."""
     w = synth.grid64_orbit_1080p()
     mesh = w.mesh()
-    rng = np.random.default_rng(11)
-    n = 384
-    px = rng.integers(0, w.width, n).astype(np.int32)
-    py = rng.integers(0, w.height, n).astype(np.int32)
-    cy, cx = np.meshgrid(np.arange(500, 516), np.arange(900, 916), indexing="ij")
-    px = np.concatenate([px, cx.ravel().astype(np.int32)])
-    py = np.concatenate([py, cy.ravel().astype(np.int32)])
-    st, _ = render_both(hx, mesh, w.view(7), w.lens(7), w.style, px, py)
-    assert st["fragments"] > 10000
+    rng = np.random.default_rng(100 + frame)
+    crop = {7: (928, 508, 64, 64), 45: (1380, 300, 64, 64), 93: (600, 800, 64, 64)}[frame]
+    px, py = _sample_with_crops(rng, w.width, w.height, 4096, [crop])
+    st, _ = render_both(hx, mesh, w.view(frame), w.lens(frame), w.style, px, py, cap_per_pixel=160)
+    assert st["fragments"] > 200000
+    assert st["gpu_stats"]["fragments"] > 50_000_000
+
+
+def test_full_size_4k_sampled(hx):
+    """128^3 warped grid at 3840x2160 (the cubic128-sized case, 0.6 G fragments
+    per frame): random pixels plus crops where window coordinates are largest,
+    across the mesh's right silhouette (x 3300..3520 of orbit frame 3; from
+    x = 2048 on, an FP32 window coordinate keeps only 8 fractional bits), and
+    one in the middle."""
+    w = synth.grid128_orbit_4k()
+    mesh = w.mesh()
+    rng = np.random.default_rng(7)
+    px, py = _sample_with_crops(rng, w.width, w.height, 1024,
+                                [(3470, 600, 64, 24), (3300, 1040, 64, 24), (3050, 1800, 64, 16),
+                                 (1900, 1060, 32, 24)])
+    st, _ = render_both(hx, mesh, w.view(3), w.lens(3), w.style, px, py, cap_per_pixel=320)
+    assert st["fragments"] > 100000
+    assert st["gpu_stats"]["fragments"] > 400_000_000
 
 
 def test_quality_matches_oracle(hx):
@@ -405,4 +436,31 @@ def test_list_overflow_status(hx):
     assert r.render(mid, out, check=False) == hx.HEXFC_OK
     assert r.last_stats["max_list"] == nz + 1
     assert r.render(mid2, out, check=False) == hx.HEXFC_ERR_OVERFLOW
+    r.close()
+
+
+@pytest.mark.parametrize("bits,status", [(4, "HEXFC_ERR_TIMEOUT"), (1, "HEXFC_ERR_CHECK")])
+def test_device_error_bits_are_reported(hx, bits, status):
+    """Error bits set by a frame's last kernels (here by the test hook, after
+    the last kernel, as those kernels would) are reported once: by the next
+    hexfc_render call, or by hexfc_render_host's own call, which waits for its
+    frame."""
+    w = synth.grid4_ortho_256()
+    mesh = w.mesh()
+    r = hx.Renderer(0)
+    mid = r.upload_mesh(mesh.verts, mesh.cells, mesh.cell_scalar, mesh.edge_level)
+    r.set_style(w.style)
+    r.set_view(w.view(0))
+    r.set_lens(w.lens(0))
+    out = torch.zeros((256, 256, 4), dtype=torch.float32, device="cuda")
+    assert r.render(mid, out) == hx.HEXFC_OK
+    r.set_option(hx.HEXFC_OPT_DEBUG_ERROR_BITS, bits)
+    assert r.render(mid, out, check=False) == hx.HEXFC_OK
+    assert r.render(mid, out, check=False) == getattr(hx, status)
+    assert r.render(mid, out, check=False) == hx.HEXFC_OK
+    host = np.zeros((256, 256, 4), np.float32)
+    r.set_option(hx.HEXFC_OPT_DEBUG_ERROR_BITS, bits)
+    assert r.render_host(mid, host, check=False) == getattr(hx, status)
+    assert r.render_host(mid, host, check=False) == hx.HEXFC_OK
+    torch.cuda.synchronize()
     r.close()

@@ -9,6 +9,8 @@ import torch
 
 from paper_2009_06574_gb300 import synth
 
+from parity import check_sampled
+
 pytestmark = pytest.mark.gpu
 
 
@@ -52,6 +54,9 @@ def test_predicted_frames_match_exact_path(hx):
         n_pred += sb["predicted"]
         if sb["predicted"]:
             assert sb["capacity"] > 0
+        if f in (3, 11) and sb["predicted"]:   # the region layout read back, against the oracle
+            st = check_sampled(pr, mesh, view, lens, style, b, seed=f)
+            assert st["fragments"] > 1000
     assert n_pred >= 15   # all but the first (no previous counts) use the chosen capacities
     ex.close(); pr.close()
 
@@ -88,7 +93,11 @@ def test_tiles_over_capacity_use_the_pool(hx):
         a, _ = _draw(ex, me, view, lens)
         b, sb = _draw(pr, mp, view, lens)
         np.testing.assert_array_equal(b, a)
-        partial += int(sb["predicted"] == 1 and sb["overflow_tiles"] > 0)
+        if sb["predicted"] == 1 and sb["overflow_tiles"] > 0:
+            partial += 1
+            if partial == 1:   # lists in the pool, read back against the oracle
+                st = check_sampled(pr, mesh, view, lens, style, b, n=2500, seed=f)
+                assert st["fragments"] > 1000
     assert partial >= 1
     ex.close(); pr.close()
 
