@@ -615,6 +615,11 @@ def run_learned(args, rank, world):
         r.render(mid, out, stream)
         return r.last_stats
 
+    def final_stats(done: dict, st: dict):
+        """Frames with predicted capacities are verified by the next call (or
+        finish): keep each frame's final statistics by its sequence number."""
+        done[st["frame"]] = st
+
     r.capacity_reset(1)
     t0 = time.perf_counter()
     losses = []
@@ -627,21 +632,25 @@ def run_learned(args, rank, world):
         r.set_option(hexfc.HEXFC_OPT_PREDICTED_CAPACITY, mode)
         frame(n_train - 2)
         frame(n_train - 1)
+        r.finish()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        stats = []
+        done, seqs = {}, []
         e0.record(stream)
         for f in range(n_train, n_frames):
-            stats.append(frame(f))
+            seqs.append(frame(f)["frame"])
+            final_stats(done, r.completed_stats())
+        final_stats(done, r.finish())   # the last frame verified (and drawn again if needed) inside the timing
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
+        stats = [done[q] for q in seqs]
         frags = sum(st["fragments"] for st in stats)
         pred = [st for st in stats if st["predicted"]]
         res[name] = {
             "frames_per_s": len(stats) / (ms / 1000.0), "ms_per_frame": ms / len(stats),
             "fragments_per_s": frags / (ms / 1000.0),
-            "predicted_frames": len(pred), "exact_redraws": sum(1 for st in stats if st["capacity"] and not st["predicted"]),
+            "predicted_frames": len(pred), "exact_redraws": sum(1 for st in stats if st["redrawn"]),
             "overflow_tiles_per_frame": float(np.mean([st["overflow_tiles"] for st in stats])),
             "capacity_over_fragments": (float(np.mean([st["capacity"] / max(st["fragments"], 1) for st in pred]))
                                         if pred else None),

@@ -121,9 +121,15 @@ typedef struct hexfc_frame_stats {
     uint32_t width, height;
     uint32_t kernel_launches;  /* kernels this call launched */
     uint32_t covered_pixels;   /* reserved (0) */
-    uint32_t predicted;        /* 1: drawn with chosen tile capacities and no count pass */
+    uint32_t predicted;        /* 1: drawn with chosen tile capacities (no pixel scan, no host wait
+                                  after the count pass) */
     uint32_t overflow_tiles;   /* tiles above their chosen capacity (their lists in the pool) */
     uint64_t capacity;         /* sum of the chosen tile capacities (fragments), 0 if none */
+    uint32_t pending;          /* 1: a frame with chosen capacities whose device statistics (fragments,
+                                  max_list, long_lists, overflow_tiles, capacity) are not known yet:
+                                  hexfc_finish or hexfc_completed_stats give them once it is verified */
+    uint32_t redrawn;          /* 1: its chosen capacities ran out and it was drawn again exactly */
+    uint64_t frame;            /* sequence number of the frame in its context (1, 2, ...) */
 } hexfc_frame_stats;
 
 /* Stages timed by HEXFC_OPT_STAGE_TIMING (CUDA events on the render stream).
@@ -332,6 +338,30 @@ enum {
                                         runs out and nothing faults. One frame only. */
 };
 hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value);
+
+/*
+ * Complete the context's last frame. With predicted capacities
+ * (HEXFC_OPT_PREDICTED_CAPACITY != 0) hexfc_render returns without waiting
+ * for its frame, which is verified by the next call on the context (at that
+ * call's first host wait, when the frame has completed) or by this one: if the
+ * frame needed more room than its chosen capacities and the pool left, it is
+ * drawn again exactly (count-then-fill) into its own output with the camera,
+ * lens and style it was drawn with, so that no frame keeps an overflow error.
+ * A predicted frame's image is final once the next hexfc_render* call or
+ * hexfc_finish on its context has returned (and the stream work it issued has
+ * run); its output buffer must stay valid until then. Waits for the last
+ * frame's stream. stats (host, nullable): the final statistics of the last
+ * frame (pending = 0; redrawn = 1 if it was drawn again). Errors: ARG,
+ * TIMEOUT/CHECK (device error bits of the verified frame), CUDA. Not in the
+ * paper, which sizes its fragment buffer once (Section "GPU Implementation").
+ */
+hexfc_status hexfc_finish(hexfc_ctx* ctx, hexfc_frame_stats* stats);
+
+/* Final statistics of the most recently verified frame of the context, without
+ * waiting (host `stats`). After hexfc_render of frame n with predicted
+ * capacities returns, these are frame n-1's (stats->frame says which).
+ * Errors: ARG. */
+hexfc_status hexfc_completed_stats(const hexfc_ctx* ctx, hexfc_frame_stats* stats);
 
 /*
  * Predicted capacities (HEXFC_OPT_PREDICTED_CAPACITY != 0; no counterpart in

@@ -30,6 +30,25 @@ struct hexfc_ctx {
     int window = 2;             // HEXFC_OPT_COMPOSITE_WINDOW
     int predicted = 0;          // HEXFC_OPT_PREDICTED_CAPACITY
     uint64_t inject_bits = 0;   // HEXFC_OPT_DEBUG_ERROR_BITS: ORed into the error word after the next frame
+    // A frame drawn with chosen capacities is verified by the next call on the
+    // context (or hexfc_finish), once it has completed: what is needed to draw
+    // it again exactly if its capacities ran out, and its device scalars and
+    // count statistics, copied into h_pend at its end.
+    struct Pending {
+        bool active = false;
+        std::shared_ptr<DevMesh> mesh;
+        float* out = nullptr;
+        cudaStream_t stream = nullptr;
+        hexfc_view view{};
+        CamParams cam{};
+        double zref = 1.0;
+        hexfc_lens lens{};
+        hexfc_style style{};
+        hexfc_frame_stats fs{};   // what was known when its call returned
+    } pend;
+    uint64_t* h_pend = nullptr;        // pinned [kScal + 4 kStatCopies]
+    hexfc_frame_stats completed{};     // final statistics of the last verified frame
+    uint64_t frame_seq = 0;            // frames drawn by this context
     // exact tile counts of the last frame (fb.tile_frag) are valid for this size
     int counts_W = 0, counts_H = 0;
     uint64_t counts_total = 0;
@@ -164,6 +183,7 @@ void free_frame(FrameBufs& f)
     dfree(f.bins); dfree(f.bins_tmp); dfree(f.masks); dfree(f.seg); dfree(f.cnt);
     dfree(f.off);
     dfree(f.part); dfree(f.part_max); dfree(f.long_q); dfree(f.fix_q); dfree(f.key); dfree(f.rgba); dfree(f.scal);
+    dfree(f.cstat);
     if (f.h_scal) cudaFreeHost(f.h_scal);
     f = FrameBufs{};
 }
@@ -571,6 +591,8 @@ hexfc_status job_phase3(FrameJob& j, cudaStream_t s)
 
 inline uint64_t* fb_of(FrameJob& j) { return j.fb->scal; }
 
+hexfc_status settle_pending(hexfc_ctx* ctx, cudaStream_t s, bool* redrawn);
+
 // HEXFC_OPT_DEBUG_ERROR_BITS: after the frame's last kernel, set the requested
 // bits in the device error word (one frame only).
 hexfc_status inject_error_bits(hexfc_ctx* ctx, uint64_t* scal, cudaStream_t s)
@@ -597,14 +619,24 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
     if ((st = job_phase1(j, s)) != HEXFC_OK) return st;
     CK(cudaStreamSynchronize(s));
     collect(ctx);
+    if (ctx->pend.active) {   // the previous frame (chosen capacities) has completed: verify it
+        bool redrawn = false;
+        if ((st = settle_pending(ctx, s, &redrawn)) != HEXFC_OK) return st;
+        if (redrawn) {   // it was drawn again in these buffers: this frame's first passes once more
+            if ((st = job_phase1(j, s)) != HEXFC_OK) return st;
+            CK(cudaStreamSynchronize(s));
+        }
+    }
     if ((st = job_read1(j)) != HEXFC_OK) return st;
     if ((st = job_phase2(j, s)) != HEXFC_OK) return st;
     CK(cudaStreamSynchronize(s));
     ctx->have_frame = false;
     st = job_read2(j, s);
+    j.fs.frame = ++ctx->frame_seq;
     ctx->last = j.fs;
     if (stats) *stats = j.fs;
     if (st != HEXFC_OK) return st;
+    ctx->completed = j.fs;
     if ((st = job_phase3(j, s)) != HEXFC_OK) return st;
     if ((st = inject_error_bits(ctx, fb_of(j), s)) != HEXFC_OK) return st;
     ctx->ev_pending[ctx->ev_cur] = ctx->timing;
@@ -629,8 +661,14 @@ constexpr double kCapPool = 0.35;        // pool after the regions, in previous-
 constexpr uint64_t kErrPoolBit = 16;     // device error bit: no room for a tile's lists in the pool
 constexpr uint32_t kLongListsUnknown = 1u << 30;   // the long-list pass reads the queue length on the device
 
-// A frame with chosen tile capacities and the fused count-and-fill pass; on
-// an overflow, the frame is drawn again by render_frame.
+// A frame with chosen tile capacities: capacities from the previous frame's
+// exact tile counts or from the capacity network, the count pass, then the fill
+// lays out each tile's lists in the tile's region (or the pool) itself, so
+// there is no pixel scan and no host wait after the count; and the call does
+// not wait at the end either. The frame is verified by the next call on the
+// context, at that call's first host wait (it has completed by then), or by
+// hexfc_finish: if its capacities ran out, it is drawn again exactly by
+// count-then-fill into its own output, before anything else.
 hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_stats* stats,
                                     cudaStream_t s)
 {
@@ -647,6 +685,26 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
         if ((st = ensure(&fb.tile_cap, &fb.cap_cap, fb.t_cap)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.cap_off, &c1, fb.cap_cap)) != HEXFC_OK) return st;
     }
+    if (!fb.cstat && (st = dalloc(&fb.cstat, 4 * kStatCopies)) != HEXFC_OK) return st;
+    if (!ctx->h_pend) CK(cudaMallocHost((void**)&ctx->h_pend, (kScal + 4 * kStatCopies) * sizeof(uint64_t)));
+    if (ctx->timing && !ctx->ev[0][0])
+        for (auto& set : ctx->ev)
+            for (auto& e : set) CK(cudaEventCreate(&e));
+    ctx->ev_cur ^= 1;
+    j.timing = ctx;
+    if ((st = job_phase1(j, s)) != HEXFC_OK) return st;
+    CK(cudaStreamSynchronize(s));
+    collect(ctx);
+    if (ctx->pend.active) {   // the previous frame has completed: verify it
+        bool redrawn = false;
+        if ((st = settle_pending(ctx, s, &redrawn)) != HEXFC_OK) return st;
+        if (redrawn) {
+            if (ctx->counts_W != j.W || ctx->counts_H != j.H) return render_frame(ctx, m, out, stats, s);
+            if ((st = job_phase1(j, s)) != HEXFC_OK) return st;
+            CK(cudaStreamSynchronize(s));
+        }
+    }
+    if ((st = job_read1(j)) != HEXFC_OK) return st;
     // fragment arrays for the regions of this frame (previous counts * margin + pad) and a pool
     // after them for the tiles above their capacity
     const uint64_t want = (uint64_t)((double)ctx->counts_total * (1.0 + kCapMargin + kCapPool)) +
@@ -657,15 +715,6 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
         if ((st = ensure(&fb.key, &fb.frag_cap, (int64_t)want)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.rgba, &c1, fb.frag_cap)) != HEXFC_OK) return st;
     }
-    if (ctx->timing && !ctx->ev[0][0])
-        for (auto& set : ctx->ev)
-            for (auto& e : set) CK(cudaEventCreate(&e));
-    ctx->ev_cur ^= 1;
-    j.timing = ctx;
-    if ((st = job_phase1(j, s)) != HEXFC_OK) return st;
-    CK(cudaStreamSynchronize(s));
-    collect(ctx);
-    if ((st = job_read1(j)) != HEXFC_OK) return st;
     job_mark(j, 4, s);
     CK(cudaMemsetAsync(fb.bins, 0xFF, sizeof(uint32_t) * (size_t)j.n_bins, s));   // padding slots = kPadBin
     CK(launch_bin_fill(*m, fb, j.tiles_x, j.W, j.H, j.reverse, s));
@@ -677,6 +726,7 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     if (ctx->predicted == 2) CK(launch_cap_forward(ctx->cap, fb, j.n_tiles, kCapMargin, kCapPad, s));
     else CK(launch_capacity_from_previous(fb, j.n_tiles, kCapMargin, kCapPad, s));
     CK(scan_u32_to_u64(fb.tile_cap, fb.cap_off, j.n_tiles, fb.part, fb.part_max, fb.scal + 11, 0xFFFFFFFFu, s));
+    CK(cudaMemsetAsync(fb.cstat, 0, sizeof(uint64_t) * 4 * kStatCopies, s));
     job_mark(j, 5, s);
     CK(launch_count(*m, fb, j.tiles_x, j.tiles_y, j.W, j.H, true, s));
     job_mark(j, 6, s);
@@ -687,41 +737,33 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     CK(launch_composite(fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, out, kLongListsUnknown, j.window, s));
     job_mark(j, 10, s);
     j.launches += 4 + 1 + 3 + 1 + 1 + 3;
-    CK(cudaMemcpyAsync(fb.h_scal, fb.scal, kScal * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    const uint64_t bits = fb.h_scal[5];
-    const uint32_t overflow = (uint32_t)fb.h_scal[6];
-    const uint64_t capacity = fb.h_scal[11];
-    if (bits & ~kErrPoolBit) {
-        CK(cudaMemsetAsync(fb.scal + 5, 0, sizeof(uint64_t), s));
-        return device_error_status(bits);
-    }
-    if ((bits & kErrPoolBit) || fb.h_scal[17] > HEXFC_MAX_LIST) {
-        // the pool after the regions ran out, or a list is too long: the exact path
-        // draws the frame again (the image above is overwritten)
-        CK(cudaMemsetAsync(fb.scal + 5, 0, sizeof(uint64_t), s));
-        st = render_frame(ctx, m, out, stats, s);
-        ctx->last.overflow_tiles = overflow;
-        ctx->last.capacity = capacity;
-        if (stats) {
-            stats->overflow_tiles = overflow;
-            stats->capacity = capacity;
-        }
-        return st;
-    }
+    // the frame's scalars and count statistics for its verification; no wait here
+    CK(cudaMemcpyAsync(ctx->h_pend, fb.scal, kScal * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_pend + kScal, fb.cstat, 4 * kStatCopies * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                       s));
     ctx->ev_pending[ctx->ev_cur] = ctx->timing;
     hexfc_frame_stats& fs = j.fs;
     fs = hexfc_frame_stats{};
-    fs.fragments = fb.h_scal[16];   // from the count pass (no pixel scan)
     fs.bin_entries = j.n_bins;
-    fs.max_list = (uint32_t)fb.h_scal[17];
-    fs.long_lists = (uint32_t)fb.h_scal[18];
     fs.width = (uint32_t)j.W;
     fs.height = (uint32_t)j.H;
     fs.kernel_launches = j.launches;
     fs.predicted = 1;
-    fs.overflow_tiles = overflow;
-    fs.capacity = capacity;
+    fs.pending = 1;   // fragments, longest list, tiles over capacity: known once verified
+    fs.frame = ++ctx->frame_seq;
+    hexfc_ctx::Pending& p = ctx->pend;
+    p.active = true;
+    p.mesh.reset();
+    for (const auto& sp_m : ctx->meshes)
+        if (sp_m.get() == m) p.mesh = sp_m;
+    p.out = out;
+    p.stream = s;
+    p.view = ctx->view;
+    p.cam = ctx->cam;
+    p.zref = ctx->zref;
+    p.lens = ctx->lens;
+    p.style = ctx->style;
+    p.fs = fs;
     ctx->last = fs;
     if (stats) *stats = fs;
     ctx->have_frame = true;
@@ -729,10 +771,88 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     ctx->last_H = j.H;
     ctx->last_tiles_x = j.tiles_x;
     ctx->last_tiles_y = j.tiles_y;
-    ctx->counts_total = fs.fragments;
+    ctx->counts_W = j.W;   // k_count leaves the exact tile counts in fb.tile_frag
+    ctx->counts_H = j.H;
     ctx->feat_tiles = j.n_tiles;
     remember_camera(ctx, j.cam);
     return HEXFC_OK;
+}
+
+// Verify the pending frame (drawn with chosen capacities), which must have
+// completed or be about to (its stream is waited for): its device scalars give
+// its statistics; device error bits are reported; if its pool ran out or a list
+// is too long for the resolve, it is drawn again exactly (count-then-fill) into
+// its output with its own camera, lens and style. s: the stream of the caller's
+// frame, on which the consumed error bits are cleared.
+hexfc_status settle_pending(hexfc_ctx* ctx, cudaStream_t s, bool* redrawn)
+{
+    *redrawn = false;
+    if (!ctx->pend.active) return HEXFC_OK;
+    hexfc_ctx::Pending p = ctx->pend;
+    ctx->pend.active = false;
+    ctx->pend.mesh.reset();
+    CK(cudaStreamSynchronize(p.stream));
+    const uint64_t* h = ctx->h_pend;
+    const uint64_t bits = h[5];
+    hexfc_frame_stats fs = p.fs;
+    fs.pending = 0;
+    fs.overflow_tiles = (uint32_t)h[6];
+    fs.capacity = h[11];
+    fs.fragments = 0;   // from the count pass (no pixel scan): the sums over its counter copies
+    fs.max_list = 0;
+    fs.long_lists = 0;
+    for (int c = 0; c < kStatCopies; ++c) {
+        const uint64_t* cs = h + kScal + 4 * c;
+        fs.fragments += cs[0];
+        fs.max_list = std::max(fs.max_list, (uint32_t)cs[1]);
+        fs.long_lists += (uint32_t)cs[2];
+    }
+    if (bits) CK(cudaMemsetAsync(ctx->fb.scal + 5, 0, sizeof(uint64_t), s));
+    if (bits & ~kErrPoolBit) {   // a bounded wait ran out or a check failed
+        ctx->completed = fs;
+        return device_error_status(bits);
+    }
+    if ((bits & kErrPoolBit) || fs.max_list > HEXFC_MAX_LIST) {
+        if (!p.mesh) return HEXFC_ERR_STATE;
+        // the pool after the regions ran out, or a list is too long: draw it
+        // again exactly, with the camera, lens and style it was drawn with
+        const hexfc_view v = ctx->view;
+        const CamParams cam = ctx->cam;
+        const double zref = ctx->zref;
+        const hexfc_lens lens = ctx->lens;
+        const hexfc_style style = ctx->style;
+        ctx->view = p.view;
+        ctx->cam = p.cam;
+        ctx->zref = p.zref;
+        ctx->lens = p.lens;
+        ctx->style = p.style;
+        hexfc_frame_stats ex{};
+        hexfc_status st = render_frame(ctx, p.mesh.get(), p.out, &ex, p.stream);
+        ctx->view = v;
+        ctx->cam = cam;
+        ctx->zref = zref;
+        ctx->lens = lens;
+        ctx->style = style;
+        CK(cudaStreamSynchronize(p.stream));   // its buffers are this context's: done before the next frame
+        ex.frame = fs.frame;
+        ex.redrawn = 1;
+        ex.overflow_tiles = fs.overflow_tiles;
+        ex.capacity = fs.capacity;
+        ctx->completed = ex;
+        *redrawn = true;
+        return st;
+    }
+    ctx->counts_total = fs.fragments;
+    ctx->completed = fs;
+    return HEXFC_OK;
+}
+
+// Wait for the context's last frame and verify it if it is pending.
+hexfc_status finish_pending(hexfc_ctx* ctx)
+{
+    if (!ctx->pend.active) return HEXFC_OK;
+    bool redrawn = false;
+    return settle_pending(ctx, ctx->pend.stream, &redrawn);
 }
 
 // Capture `body(i, stream_i)` for the listed items, each on its own stream
@@ -900,6 +1020,10 @@ void hexfc_destroy(hexfc_ctx* ctx)
     if (!ctx) return;
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
+    ctx->pend.active = false;
+    ctx->pend.mesh.reset();
+    if (ctx->h_pend) cudaFreeHost(ctx->h_pend);
+    ctx->h_pend = nullptr;
     ctx->meshes.clear();   // a mesh is freed with its last holder
     free_frame(ctx->fb);
     for (auto& b : ctx->batch) {
@@ -1193,6 +1317,10 @@ hexfc_status hexfc_trim(hexfc_ctx* ctx)
 {
     if (!ctx) return HEXFC_ERR_ARG;
     DeviceGuard g(ctx->device);
+    if (ctx->pend.active) {
+        const hexfc_status st = finish_pending(ctx);
+        if (st != HEXFC_OK) return st;
+    }
     uint64_t* pinned = ctx->fb.h_scal;
     ctx->fb.h_scal = nullptr;   // the pinned mirror is small: keep it
     free_frame(ctx->fb);
@@ -1317,6 +1445,10 @@ hexfc_status hexfc_render_host(hexfc_ctx* ctx, int32_t mesh, float* out_rgba_hos
         d_out = ctx->d_out;
     }
     st = ctx->predicted ? render_frame_predicted(ctx, m, d_out, stats, s) : render_frame(ctx, m, d_out, stats, s);
+    if (st == HEXFC_OK && ctx->pend.active) {   // this call waits anyway: verify the frame now
+        st = finish_pending(ctx);
+        if (stats) *stats = ctx->completed;
+    }
     if (st == HEXFC_OK) {
         // the image (unless written in place) and this frame's device error bits
         FrameBufs& fb = ctx->fb;
@@ -1342,6 +1474,11 @@ hexfc_status hexfc_debug_pixels(hexfc_ctx* ctx, const int32_t* px, const int32_t
 {
     if (!ctx || !px || !py || !counts || n < 0) return HEXFC_ERR_ARG;
     if (!ctx->have_frame) return HEXFC_ERR_STATE;
+    if (ctx->pend.active) {
+        DeviceGuard g0(ctx->device);
+        const hexfc_status st0 = finish_pending(ctx);
+        if (st0 != HEXFC_OK) return st0;
+    }
     for (int64_t i = 0; i < n; ++i)
         if (px[i] < 0 || py[i] < 0 || px[i] >= ctx->last_W || py[i] >= ctx->last_H) return HEXFC_ERR_ARG;
     if (n == 0) return HEXFC_OK;
@@ -1434,6 +1571,22 @@ hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value)
         return HEXFC_OK;
     default: return HEXFC_ERR_ARG;
     }
+}
+
+hexfc_status hexfc_finish(hexfc_ctx* ctx, hexfc_frame_stats* stats)
+{
+    if (!ctx) return HEXFC_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    hexfc_status st = finish_pending(ctx);
+    if (stats) *stats = ctx->completed;
+    return st;
+}
+
+hexfc_status hexfc_completed_stats(const hexfc_ctx* ctx, hexfc_frame_stats* stats)
+{
+    if (!ctx || !stats) return HEXFC_ERR_ARG;
+    *stats = ctx->completed;
+    return HEXFC_OK;
 }
 
 hexfc_status hexfc_stage_times(hexfc_ctx* ctx, double* ms, uint64_t* frames, int32_t reset)
@@ -1622,5 +1775,9 @@ extern "C" hexfc_status hexfc_render_noalloc(hexfc_ctx* ctx, int32_t mesh, float
     DevMesh* m = get_mesh(ctx, mesh);
     if (!m || !ctx->have_view) return HEXFC_ERR_STATE;
     DeviceGuard g(ctx->device);
+    if (ctx->pend.active) {
+        const hexfc_status st = finish_pending(ctx);
+        if (st != HEXFC_OK) return st;
+    }
     return render_frame_noalloc(ctx, m, out_rgba, stats, (cudaStream_t)stream);
 }

@@ -66,6 +66,10 @@ constexpr uint32_t kZ24 = 0xFFFFFFu;
 // scan (regions' total, ...), 14 records taken from the pool, 16-18 count
 // pass statistics (fragments, longest list, lists above the warp sort).
 constexpr int kScal = 24;
+// Copies of the count pass's frame statistics (fragments, longest list, long
+// lists, unused), one per tile % kStatCopies, summed on the host: tiles
+// adding into one address would queue on it.
+constexpr int kStatCopies = 32;
 __host__ __device__ inline uint32_t face_edge_flags(const uint4& z) { return z.x >> 24; }
 __host__ __device__ inline uint32_t face_tris(const uint4& z) { return (z.y >> 24) & 3u; }
 
@@ -154,6 +158,7 @@ struct FrameBufs {
     // small device scalars: [0] total fragments, [1] max list, [2] long lists, [3] long queue cursor,
     // [4] out-of-order queue cursor, [5] error bits (kept across frames), [8..10] tile scan totals
     uint64_t* scal = nullptr;       // kScal device scalars (slots: see kScal)
+    uint64_t* cstat = nullptr;      // [4 * kStatCopies] count pass statistics (predicted frames)
     uint64_t* h_scal = nullptr;     // pinned mirror
 };
 

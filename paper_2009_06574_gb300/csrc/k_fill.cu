@@ -323,7 +323,8 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __rest
                                                           uint64_t* __restrict__ key, float4* __restrict__ rgba,
                                                           uint64_t* __restrict__ seg,
                                                           unsigned long long* __restrict__ err,
-                                                          const uint64_t* __restrict__ cap_off, int n_tiles,
+                                                          const uint64_t* __restrict__ cap_off,
+                                                          const uint32_t* __restrict__ tile_frag, int n_tiles,
                                                           uint64_t frag_cap, unsigned long long* __restrict__ scal)
 {
     extern __shared__ __align__(128) unsigned char fill_smem[];
@@ -343,40 +344,28 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __rest
             s_base[threadIdx.x] = off[q];
             s_len[threadIdx.x] = cnt[q];
         }
-    } else {
+    } else if (threadIdx.x == 0) {
         // capacities chosen before the frame: the tile's lists are laid out in its
         // region [cap_off[t], cap_off[t+1]), or in the pool after all regions
-        // (scal[14] records taken, scal[6] tiles) if they do not fit; with no
-        // room left there the tile is not drawn (error bit kErrPool)
-        uint32_t n = 0, incl = 0;
-        if (threadIdx.x < kTilePix) {
-            n = cnt[q];
-            incl = n;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+        // (scal[14] records taken, scal[6] tiles) if they do not fit (the tile's
+        // exact total is the count pass's); with no room left there the tile is
+        // not drawn (error bit kErrPool)
+        const uint64_t total = tile_frag[tile];
+        const uint64_t region = cap_off[tile];
+        uint64_t b = region;
+        if (region + total > cap_off[tile + 1] || region + total > frag_cap) {
+            const uint64_t p = atomicAdd(&scal[14], (unsigned long long)total);
+            atomicAdd(&scal[6], 1ull);
+            b = cap_off[n_tiles] + p;
+            if (b + total > frag_cap) {
+                atomicOr(err, kErrPool);
+                b = ~0ull;
             }
-            if (lane == 31) s_wsum[warp] = incl;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint64_t total = 0;
-            for (int w = 0; w < kConsumerWarps; ++w) total += s_wsum[w];
-            const uint64_t region = cap_off[tile];
-            uint64_t b = region;
-            if (region + total > cap_off[tile + 1] || region + total > frag_cap) {
-                const uint64_t p = atomicAdd(&scal[14], (unsigned long long)total);
-                atomicAdd(&scal[6], 1ull);
-                b = cap_off[n_tiles] + p;
-                if (b + total > frag_cap) {
-                    atomicOr(err, kErrPool);
-                    b = ~0ull;
-                }
-            }
-            s_tile_base = b;
-        }
-        __syncthreads();
+        s_tile_base = b;
+    }
+    pipe_init(s_full, s_empty);   // (its block barrier publishes s_tile_base, s_base, s_len)
+    if (cap_off) {
         if (s_tile_base == ~0ull) {   // no room: the frame is drawn again exactly
             // the resolve must find no fragment here: clear the tile's masks and counts
             uint32_t* mt = masks + (beg / kChunk) * kTilePix;
@@ -385,13 +374,25 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __rest
             return;
         }
         if (threadIdx.x < kTilePix) {
+            // the consumers lay out the tile's lists (a scan of the counts over the
+            // 256 pixels, consumer warps only: named barrier 1) while the producer
+            // starts on the first chunks
+            const uint32_t n = cnt[q];
+            uint32_t incl = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) s_wsum[warp] = incl;
+            asm volatile("bar.sync 1, %0;" ::"n"(kTilePix) : "memory");
             uint32_t pre = 0;
             for (int w = 0; w < warp; ++w) pre += s_wsum[w];
             s_base[threadIdx.x] = s_tile_base + pre + incl - n;
             s_len[threadIdx.x] = n;
+            __syncwarp();
         }
     }
-    pipe_init(s_full, s_empty);
     fill_tile(fill_smem, s_base, s_len, s_full, s_empty, bins, masks, fframe, fstat, beg, n_chunks, px0, py0,
               W, H, sp, key, rgba, seg, err);
 }
@@ -425,7 +426,7 @@ cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, 
     k_fill<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, smem, s>>>(
         fb.tile_off, fb.bins, fb.masks, fb.fframe, m.fstat, fb.tile_order, tiles_x, W, H, sp, fb.off, fb.cnt, fb.key,
         fb.rgba, fb.seg, reinterpret_cast<unsigned long long*>(fb.scal + 5), regions ? fb.cap_off : nullptr,
-        tiles_x * tiles_y, (uint64_t)fb.frag_cap, reinterpret_cast<unsigned long long*>(fb.scal));
+        fb.tile_frag, tiles_x * tiles_y, (uint64_t)fb.frag_cap, reinterpret_cast<unsigned long long*>(fb.scal));
     return cudaGetLastError();
 }
 

@@ -392,8 +392,9 @@ __device__ __forceinline__ uint32_t tile_sum(uint32_t v, uint32_t* s_tmp)
 
 // Per tile: coverage of every chunk as per-pixel bit masks (kept for the
 // fill) and the per-pixel list lengths; the tile's total goes to tile_frag,
-// and, if stats is given, stats[0] += fragments, stats[1] = longest list,
-// stats[2] += lists longer than kWarpSortMax (the frame's statistics without
+// and, if stats is given, into copy tile % kStatCopies of the counters
+// (stats + 4 copy): [0] += fragments, [1] = longest list, [2] += lists longer
+// than kWarpSortMax (the frame's statistics without
 // the pixel scan).
 __global__ void __launch_bounds__(kTilePix, 5) k_count(const uint64_t* __restrict__ tile_off,
                                                     const uint32_t* __restrict__ bins,
@@ -417,18 +418,30 @@ __global__ void __launch_bounds__(kTilePix, 5) k_count(const uint64_t* __restric
 #pragma unroll
     for (int w = 0; w < kConsumerWarps; ++w) n += s_w[w].mask[threadIdx.x];
     cnt[(int64_t)tile * kTilePix + threadIdx.x] = n;
+    __shared__ uint32_t s_mx[kConsumerWarps], s_lg[kConsumerWarps];
     if (stats) {   // (the pixel scan gives them otherwise)
         const uint32_t mx = __reduce_max_sync(0xffffffffu, n);
         const uint32_t lg = __reduce_add_sync(0xffffffffu, n > (uint32_t)kWarpSortMax ? 1u : 0u);
         if (lane == 0) {
-            atomicMax(&stats[1], (unsigned long long)mx);
-            if (lg) atomicAdd(&stats[2], (unsigned long long)lg);
+            s_mx[warp] = mx;
+            s_lg[warp] = lg;
         }
     }
-    const uint32_t total = tile_sum(n, s_tmp);
+    const uint32_t total = tile_sum(n, s_tmp);   // (its block barrier also publishes s_mx, s_lg)
     if (threadIdx.x == 0) {
         tile_frag[tile] = total;
-        if (stats) atomicAdd(&stats[0], (unsigned long long)total);
+        if (stats) {   // one copy of the counters per tile % kStatCopies: no queue on one address
+            uint32_t mx = 0, lg = 0;
+#pragma unroll
+            for (int w = 0; w < kConsumerWarps; ++w) {
+                mx = max(mx, s_mx[w]);
+                lg += s_lg[w];
+            }
+            unsigned long long* st = stats + (tile % kStatCopies) * 4;
+            if (total) atomicAdd(&st[0], (unsigned long long)total);
+            if (mx) atomicMax(&st[1], (unsigned long long)mx);
+            if (lg) atomicAdd(&st[2], (unsigned long long)lg);
+        }
     }
 }
 
@@ -486,7 +499,7 @@ cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles
     const size_t smem = kConsumerWarps * sizeof(CountWarp);
     k_count<<<(unsigned)(tiles_x * tiles_y), kTilePix, smem, s>>>(fb.tile_off, fb.bins, fb.fframe, fb.tile_order,
                                                                    tiles_x, W, H, fb.cnt, fb.masks, fb.tile_frag,
-                                                                   stats ? reinterpret_cast<unsigned long long*>(fb.scal + 16)
+                                                                   stats ? reinterpret_cast<unsigned long long*>(fb.cstat)
                                                                          : nullptr);
     return cudaGetLastError();
 }

@@ -49,7 +49,8 @@ EXPORTS = ["hexfc_style_default", "hexfc_create", "hexfc_destroy", "hexfc_upload
            "hexfc_stage_times", "hexfc_status_string", "hexfc_render_noalloc", "hexfc_share_mesh",
            "hexfc_frame_memory", "hexfc_trim", "hexfc_render_batch", "hexfc_capacity_reset",
            "hexfc_capacity_set_weights", "hexfc_capacity_get_weights", "hexfc_capacity_grad",
-           "hexfc_capacity_train", "hexfc_last_cuda_error", "hexfc_cuda_error_name"]
+           "hexfc_capacity_train", "hexfc_last_cuda_error", "hexfc_cuda_error_name", "hexfc_finish",
+           "hexfc_completed_stats"]
 
 
 class HexfcError(RuntimeError):
@@ -80,7 +81,8 @@ class hexfc_frame_stats(C.Structure):
     _fields_ = [("fragments", C.c_uint64), ("bin_entries", C.c_uint64), ("max_list", C.c_uint32),
                 ("long_lists", C.c_uint32), ("width", C.c_uint32), ("height", C.c_uint32),
                 ("kernel_launches", C.c_uint32), ("covered_pixels", C.c_uint32), ("predicted", C.c_uint32),
-                ("overflow_tiles", C.c_uint32), ("capacity", C.c_uint64)]
+                ("overflow_tiles", C.c_uint32), ("capacity", C.c_uint64), ("pending", C.c_uint32),
+                ("redrawn", C.c_uint32), ("frame", C.c_uint64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -125,6 +127,8 @@ def load():
                 "hexfc_stage_times": (i32, [vp, vp, C.POINTER(u64), i32]),
                 "hexfc_status_string": (C.c_char_p, [i32]),
                 "hexfc_render_noalloc": (i32, [vp, i32, vp, C.POINTER(hexfc_frame_stats), vp]),
+                "hexfc_finish": (i32, [vp, C.POINTER(hexfc_frame_stats)]),
+                "hexfc_completed_stats": (i32, [vp, C.POINTER(hexfc_frame_stats)]),
                 "hexfc_share_mesh": (i32, [vp, vp, i32, C.POINTER(i32)]),
                 "hexfc_frame_memory": (i32, [vp, C.POINTER(u64)]),
                 "hexfc_trim": (i32, [vp]),
@@ -362,6 +366,21 @@ class Renderer:
         _check(load().hexfc_capacity_train(self._h, int(steps), float(lr), C.byref(loss) if want_loss else None,
                                            _stream_ptr(stream)), "hexfc_capacity_train")
         return float(loss.value) if want_loss else None
+
+    def finish(self, check: bool = True) -> dict:
+        """Complete the last frame (verify a frame drawn with predicted capacities,
+        drawing it again exactly if they ran out); its final statistics."""
+        st = hexfc_frame_stats()
+        r = load().hexfc_finish(self._h, C.byref(st))
+        if check:
+            _check(r, "hexfc_finish")
+        return st.as_dict()
+
+    def completed_stats(self) -> dict:
+        """Final statistics of the most recently verified frame (no wait)."""
+        st = hexfc_frame_stats()
+        _check(load().hexfc_completed_stats(self._h, C.byref(st)), "hexfc_completed_stats")
+        return st.as_dict()
 
     def render_noalloc(self, mesh: int, out, stream=None, check: bool = True):
         """Like render, with every per-frame buffer in the library's fixed scratch

@@ -87,6 +87,7 @@ def test_network_capacities_draw_exact_frames(hx):
             r.set_lens(lens)
             o = torch.empty((150, 200, 4), device="cuda")
             r.render(mid, o)
+            r.finish()   # a predicted frame is verified (and drawn again if it overflowed)
             imgs.append(o.cpu().numpy())
         np.testing.assert_array_equal(imgs[1], imgs[0])
         n_pred += pr.last_stats["predicted"]
