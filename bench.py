@@ -36,9 +36,9 @@ FRAG_BYTES = 24          # 8 B key + 16 B premultiplied RGBA
 # DRAM traffic of one k_fill launch (ncu dram__bytes_read.sum + dram__bytes_write.sum,
 # one pass, on the 1920x1080 bench frame), per fragment drawn, and the fill kernel's
 # sources it was taken on: the roofline reports it only while those sources are unchanged.
-FILL_DRAM = {"bytes_per_fragment": 27.60,
-             "sha256": "d30ba66788bc028bc5cb7dde76ece9b2c6703544e08696e880d0a9bc789c413e",
-             "profile": "profiles/dram_k_fill_k_count_k_composite_grid64_orbit_1080p.md"}
+FILL_DRAM = {"bytes_per_fragment": 27.66,
+             "sha256": "107f2655669b4d04289e10c1fb9d1b519ebe33fb365ea99d30bc784fca585e4f",
+             "profile": "profiles/dram_k_fill_grid64_orbit_1080p.md"}
 FILL_SOURCES = ("csrc/k_fill.cu", "csrc/raster_tiles.cuh", "csrc/shade.cuh", "csrc/raster_common.cuh",
                 "csrc/pipeline.cuh", "csrc/hexfc_internal.cuh")
 
@@ -52,8 +52,8 @@ def fill_sources_sha256() -> str:
     return h.hexdigest()
 
 
-FACE_FRAME_BYTES = 64    # per-frame half of a face record: X[4], Y[4], z24[4] + flags, eye depth[4]
-FACE_STATIC_BYTES = 64   # static half: corner importance[4], world position[4][3]
+GEOM_FACE_BYTES = 48     # a face: 4 corner ids, 4 edge levels and importances (16 + 16 + 16 B)
+GEOM_VERTEX_BYTES = 12   # a vertex: its position (3 floats)
 
 
 def parse_args():
@@ -67,6 +67,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-steps", type=int, default=60)
     ap.add_argument("--no-4k", action="store_true", help="skip the secondary 3840x2160 measurement")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the learned-capacity, batch and serving measurements after the main line")
     ap.add_argument("--predicted", type=int, default=0,
                     help="tile capacities: 0 count-then-fill, 1 previous frame's counts, 2 capacity network")
     # serving mode (--workload serving): Poisson request stream over resident meshes
@@ -385,10 +387,17 @@ def run_ours(args, rank, world, local_rank):
     P = tiles * 256
     st = r.last_stats
     bins = st["bin_entries"]
+    # what an A-buffer must move (each datum once): the geometry (48 B per face,
+    # 12 B per vertex) read by the count and the fill, a 24 B record per
+    # fragment written by the fill and read by the composite, per pixel a count
+    # written (4 B), an offset and a cursor (8 B) in the fill, an offset (4 B)
+    # and the 16 B image in the composite
+    n_pix = w.width * w.height
+    geometry = n_faces * GEOM_FACE_BYTES + mesh.n_verts * GEOM_VERTEX_BYTES
     algo = {
-        "fill": F * FRAG_BYTES + P * 8 + bins * 4 + n_faces * (FACE_FRAME_BYTES + FACE_STATIC_BYTES),
-        "composite": F * FRAG_BYTES + P * 12 + w.width * w.height * 16,
-        "count": bins * 4 + n_faces * 32 + P * 4,
+        "fill": F * FRAG_BYTES + n_pix * 8 + geometry,
+        "composite": F * FRAG_BYTES + n_pix * 4 + n_pix * 16,
+        "count": geometry + n_pix * 4,
     }
     kernel_stages = {k: per_frame[k] for k in ("vertex", "face", "tile_scan", "bin", "count", "scan", "fill",
                                                "composite")}
@@ -404,6 +413,25 @@ def run_ours(args, rank, world, local_rank):
             sec = secondary_4k(args, hexfc, torch, stream)
         except Exception as e:   # the main line stands on its own
             sec = {"workload": "grid128_orbit_4k", "failed": str(e)}
+    # the metric's other parts, each measured after the main line with its own
+    # clock record: learned capacity against count-then-fill (128^3, 3840x2160),
+    # batched views against one by one, the serving loop (rank 0 at N = 1)
+    secondaries = {}
+    if not args.no_secondary and rank == 0 and world == 1:
+        legs = (("secondary_learned", lambda: run_learned(args, rank, world)),
+                ("secondary_batch", lambda: run_batch(args, rank, world, steps=10, warmup=3)),
+                ("secondary_serving", lambda: run_serving(args, rank, world)))
+        for key, fn in legs:
+            sampler = ClockSampler(uuid)
+            sampler.start()
+            try:
+                leg = fn()
+            except Exception as e:   # the main line stands on its own
+                leg = {"failed": str(e)}
+            leg_clocks = sampler.stop()
+            if leg is not None:
+                leg["clocks"] = leg_clocks
+                secondaries[key] = leg
     cpu = None
     if not args.no_cpu_baseline:
         try:
@@ -433,6 +461,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak_kind": peak_kind, "algorithmic_bytes": algo[dom]},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         "secondary_4k": sec,
+        **secondaries,
     }
     print(json.dumps(line), flush=True)
 
@@ -452,7 +481,7 @@ def run_serving(args, rank, world):
     from paper_2009_06574_gb300 import serve, synth
 
     if rank != 0:
-        return
+        return None
     sizes = [int(x) for x in args.serve_sizes.split(",")]
     res = [(1280, 720), (1920, 1080), (3840, 2160)]
     rng = np.random.default_rng(5)
@@ -516,10 +545,10 @@ def run_serving(args, rank, world):
         "fragments_per_s": frags / wall, "failed": len(out) - len(ok), "max_in_flight": in_flight,
         "peak_admitted_gb": peak / (1 << 30), "mesh_upload_s": upload_s, "wall_s": wall,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
-def run_batch(args, rank, world):
+def run_batch(args, rank, world, steps=None, warmup=None):
     """Many views of several meshes in one call: warped N^3 grids (N = 32, 64,
     96) x 16 orbit views each at 1280x720, drawn as one batch per step (each
     frame phase of all 48 views captured as one CUDA graph), with the tuning
@@ -530,7 +559,9 @@ def run_batch(args, rank, world):
     from paper_2009_06574_gb300 import autotune, hexfc, synth
 
     if rank != 0:
-        return
+        return None
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     sizes, n_views, (W, H) = [32, 64, 96], 16, (1280, 720)
     r = hexfc.Renderer(0)
     style = synth.Style(w_base=2.0, lod=4, delta=0.08, tf_hi=0.15)
@@ -562,45 +593,47 @@ def run_batch(args, rank, world):
 
     res = {}
     for name, fn in (("batched", batched), ("one_by_one", one_by_one)):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         frags = 0
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             frags += sum(s["fragments"] for s in fn())
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        res[name] = {"frames_per_s": args.steps * len(items) / (ms / 1000.0), "ms_per_batch": ms / args.steps,
+        res[name] = {"frames_per_s": steps * len(items) / (ms / 1000.0), "ms_per_batch": ms / steps,
                      "fragments_per_s": frags / (ms / 1000.0)}
     line = {
         "metric": "frames/s, batched views (3 meshes x 16 views, 1280x720)",
-        "value": res["batched"]["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "higher_is_better": True, "impl": "ours", "dtype": "f32", "data": "synthetic",
+        "value": res["batched"]["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "steps": steps,
+        "warmup": warmup, "higher_is_better": True, "impl": "ours", "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch_grids32-64-96_x16views_1280x720", "items": len(items),
                    "tuned": tuned["config"]},
         "batched": res["batched"], "one_by_one": res["one_by_one"],
         "speedup": res["batched"]["frames_per_s"] / res["one_by_one"]["frames_per_s"],
     }
-    print(json.dumps(line), flush=True)
     r.close()
+    return line
 
 
 def run_learned(args, rank, world):
     """Learned tile capacities: a warped 128^3 grid at 3840x2160 along a
     500-frame camera and lens path. Frames 0-399 are drawn by count-then-fill
     and the capacity network trains on each frame's exact tile counts; frames
-    400-499 are then drawn (timed) by count-then-fill, by the fused pass with
-    the network's capacities, and by the fused pass with the previous frame's
-    counts as capacities."""
+    400-499 are then drawn (timed) by count-then-fill and with chosen tile
+    capacities (no pixel scan, no host wait after the count, each frame
+    verified by the next call and drawn again exactly if they ran out): the
+    network's, the previous frame's counts, and the previous total spread
+    evenly over the tiles."""
     import numpy as np
     import torch
     from paper_2009_06574_gb300 import hexfc, synth
 
     if rank != 0:
-        return
+        return None
     n, (W, H), n_frames, n_train = args.learned_n, (3840, 2160), 500, 400
     r = hexfc.Renderer(0)
     m = synth.hex_grid(n, jitter=0.1, warp_amp=0.3, seed=100 + n)
@@ -628,7 +661,7 @@ def run_learned(args, rank, world):
         losses.append(r.capacity_train(args.train_steps, lr=2e-3, stream=stream))
     train_s = time.perf_counter() - t0
     res = {}
-    for name, mode in (("count_then_fill", 0), ("network", 2), ("previous_frame", 1)):
+    for name, mode in (("count_then_fill", 0), ("network", 2), ("previous_frame", 1), ("uniform", 3)):
         r.set_option(hexfc.HEXFC_OPT_PREDICTED_CAPACITY, mode)
         frame(n_train - 2)
         frame(n_train - 1)
@@ -639,7 +672,9 @@ def run_learned(args, rank, world):
         e0.record(stream)
         for f in range(n_train, n_frames):
             seqs.append(frame(f)["frame"])
-            final_stats(done, r.completed_stats())
+            prev = r.completed_stats(seqs[-2]) if len(seqs) > 1 else None
+            if prev is not None:
+                final_stats(done, prev)
         final_stats(done, r.finish())   # the last frame verified (and drawn again if needed) inside the timing
         e1.record(stream)
         torch.cuda.synchronize()
@@ -667,8 +702,8 @@ def run_learned(args, rank, world):
         "train_loss": {"first": losses[0], "after_100": losses[min(99, len(losses) - 1)], "last": losses[-1]},
         "train_seconds": train_s,
     }
-    print(json.dumps(line), flush=True)
     r.close()
+    return line
 
 
 def main():
@@ -679,14 +714,11 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.workload == "serving":
-        run_serving(args, rank, world)
-        return
-    if args.workload == "batch":
-        run_batch(args, rank, world)
-        return
-    if args.workload == "learned":
-        run_learned(args, rank, world)
+    standalone = {"serving": run_serving, "batch": run_batch, "learned": run_learned}
+    if args.workload in standalone:
+        line = standalone[args.workload](args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
         return
     if world > 1:
         import torch

@@ -330,7 +330,9 @@ enum {
     HEXFC_OPT_COMPOSITE_WINDOW = 4,  /* sorted window of the per-pixel resolve: 2 (default), 4 or 8; the
                                         image does not depend on it, bit for bit */
     HEXFC_OPT_PREDICTED_CAPACITY = 5, /* 0: count-then-fill (default); 1: capacities from the previous
-                                        frame's tile counts; 2: from the capacity network. See below. */
+                                        frame's tile counts; 2: from the capacity network; 3: the previous
+                                        frame's total spread evenly over the tiles (the baseline without
+                                        any per-tile knowledge). See below. */
     HEXFC_OPT_DEBUG_ERROR_BITS = 6   /* test hook, bits 0..7: after the last kernel of the next
                                         hexfc_render or hexfc_render_noalloc frame, these bits are set
                                         in the device error word as a kernel of that frame would set
@@ -357,11 +359,12 @@ hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value);
  */
 hexfc_status hexfc_finish(hexfc_ctx* ctx, hexfc_frame_stats* stats);
 
-/* Final statistics of the most recently verified frame of the context, without
- * waiting (host `stats`). After hexfc_render of frame n with predicted
- * capacities returns, these are frame n-1's (stats->frame says which).
- * Errors: ARG. */
-hexfc_status hexfc_completed_stats(const hexfc_ctx* ctx, hexfc_frame_stats* stats);
+/* Final statistics of frame `frame` of the context (its sequence number,
+ * hexfc_frame_stats.frame), or of the most recently verified frame if frame
+ * is 0, without waiting (host `stats`). After hexfc_render of frame n with
+ * predicted capacities returns, frame n-1 is verified. The last 16 frames are
+ * kept. Errors: ARG, STATE (that frame is not verified yet or no longer kept). */
+hexfc_status hexfc_completed_stats(const hexfc_ctx* ctx, uint64_t frame, hexfc_frame_stats* stats);
 
 /*
  * Predicted capacities (HEXFC_OPT_PREDICTED_CAPACITY != 0; no counterpart in

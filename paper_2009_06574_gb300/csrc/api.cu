@@ -48,6 +48,7 @@ struct hexfc_ctx {
     } pend;
     uint64_t* h_pend = nullptr;        // pinned [kScal + 4 kStatCopies]
     hexfc_frame_stats completed{};     // final statistics of the last verified frame
+    hexfc_frame_stats history[16]{};   // final statistics of recent frames, at frame % 16
     uint64_t frame_seq = 0;            // frames drawn by this context
     // exact tile counts of the last frame (fb.tile_frag) are valid for this size
     int counts_W = 0, counts_H = 0;
@@ -593,6 +594,13 @@ inline uint64_t* fb_of(FrameJob& j) { return j.fb->scal; }
 
 hexfc_status settle_pending(hexfc_ctx* ctx, cudaStream_t s, bool* redrawn);
 
+// A frame's final statistics: the latest verified, and kept by sequence number.
+inline void record_final(hexfc_ctx* ctx, const hexfc_frame_stats& fs)
+{
+    ctx->completed = fs;
+    ctx->history[fs.frame % 16] = fs;
+}
+
 // HEXFC_OPT_DEBUG_ERROR_BITS: after the frame's last kernel, set the requested
 // bits in the device error word (one frame only).
 hexfc_status inject_error_bits(hexfc_ctx* ctx, uint64_t* scal, cudaStream_t s)
@@ -636,7 +644,7 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
     ctx->last = j.fs;
     if (stats) *stats = j.fs;
     if (st != HEXFC_OK) return st;
-    ctx->completed = j.fs;
+    record_final(ctx, j.fs);
     if ((st = job_phase3(j, s)) != HEXFC_OK) return st;
     if ((st = inject_error_bits(ctx, fb_of(j), s)) != HEXFC_OK) return st;
     ctx->ev_pending[ctx->ev_cur] = ctx->timing;
@@ -673,8 +681,12 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
                                     cudaStream_t s)
 {
     if (ctx->predicted == 2 && !ctx->cap.ready) return HEXFC_ERR_STATE;   // no network weights
-    if (ctx->counts_W != ctx->view.width || ctx->counts_H != ctx->view.height)
-        return render_frame(ctx, m, out, stats, s);   // no tile counts for this size yet
+    // previous-frame capacities need the tile counts of a frame of this size; the
+    // network (that feature is then 0) and the uniform capacity need only some
+    // earlier frame, for the size of the pool
+    const bool same_size = ctx->counts_W == ctx->view.width && ctx->counts_H == ctx->view.height;
+    if (ctx->counts_W == 0 || (ctx->predicted == 1 && !same_size))
+        return render_frame(ctx, m, out, stats, s);
     FrameJob j = make_job(ctx, &ctx->fb, m, out);
     FrameBufs& fb = ctx->fb;
     hexfc_status st;
@@ -698,8 +710,9 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     if (ctx->pend.active) {   // the previous frame has completed: verify it
         bool redrawn = false;
         if ((st = settle_pending(ctx, s, &redrawn)) != HEXFC_OK) return st;
-        if (redrawn) {
-            if (ctx->counts_W != j.W || ctx->counts_H != j.H) return render_frame(ctx, m, out, stats, s);
+        if (redrawn) {   // its exact redraw reused these buffers: this frame's first passes once more
+            if (ctx->predicted == 1 && (ctx->counts_W != j.W || ctx->counts_H != j.H))
+                return render_frame(ctx, m, out, stats, s);
             if ((st = job_phase1(j, s)) != HEXFC_OK) return st;
             CK(cudaStreamSynchronize(s));
         }
@@ -707,8 +720,10 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     if ((st = job_read1(j)) != HEXFC_OK) return st;
     // fragment arrays for the regions of this frame (previous counts * margin + pad) and a pool
     // after them for the tiles above their capacity
-    const uint64_t want = (uint64_t)((double)ctx->counts_total * (1.0 + kCapMargin + kCapPool)) +
-                          (uint64_t)j.n_tiles * kCapPad;
+    // (the previous frame's fragment total, now verified, scaled to this frame's pixels)
+    const double prev_total = (double)ctx->counts_total * ((double)j.W * j.H) /
+                              ((double)ctx->counts_W * (double)ctx->counts_H);
+    const uint64_t want = (uint64_t)(prev_total * (1.0 + kCapMargin + kCapPool)) + (uint64_t)j.n_tiles * kCapPad;
     if (!fb.key || fb.frag_cap < (int64_t)want) {
         int64_t c1 = 0;
         dfree(fb.rgba);
@@ -723,8 +738,13 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     if ((st = job_features(j, s)) != HEXFC_OK) return st;
     // stages: bin (with the features, the capacities and their scan), count,
     // then no pixel scan and no host wait, fill, composite
-    if (ctx->predicted == 2) CK(launch_cap_forward(ctx->cap, fb, j.n_tiles, kCapMargin, kCapPad, s));
-    else CK(launch_capacity_from_previous(fb, j.n_tiles, kCapMargin, kCapPad, s));
+    if (ctx->predicted == 2) {
+        CK(launch_cap_forward(ctx->cap, fb, j.n_tiles, kCapMargin, kCapPad, s));
+    } else {   // previous-frame counts, or (mode 3) the previous total spread evenly over the tiles
+        const uint32_t uniform =
+            ctx->predicted == 3 ? (uint32_t)std::max(1.0, std::ceil(prev_total / (double)j.n_tiles)) : 0u;
+        CK(launch_capacity_from_previous(fb, j.n_tiles, kCapMargin, kCapPad, uniform, s));
+    }
     CK(scan_u32_to_u64(fb.tile_cap, fb.cap_off, j.n_tiles, fb.part, fb.part_max, fb.scal + 11, 0xFFFFFFFFu, s));
     CK(cudaMemsetAsync(fb.cstat, 0, sizeof(uint64_t) * 4 * kStatCopies, s));
     job_mark(j, 5, s);
@@ -809,7 +829,7 @@ hexfc_status settle_pending(hexfc_ctx* ctx, cudaStream_t s, bool* redrawn)
     }
     if (bits) CK(cudaMemsetAsync(ctx->fb.scal + 5, 0, sizeof(uint64_t), s));
     if (bits & ~kErrPoolBit) {   // a bounded wait ran out or a check failed
-        ctx->completed = fs;
+        record_final(ctx, fs);
         return device_error_status(bits);
     }
     if ((bits & kErrPoolBit) || fs.max_list > HEXFC_MAX_LIST) {
@@ -838,12 +858,12 @@ hexfc_status settle_pending(hexfc_ctx* ctx, cudaStream_t s, bool* redrawn)
         ex.redrawn = 1;
         ex.overflow_tiles = fs.overflow_tiles;
         ex.capacity = fs.capacity;
-        ctx->completed = ex;
+        record_final(ctx, ex);
         *redrawn = true;
         return st;
     }
     ctx->counts_total = fs.fragments;
-    ctx->completed = fs;
+    record_final(ctx, fs);
     return HEXFC_OK;
 }
 
@@ -1562,7 +1582,7 @@ hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value)
         ctx->window = (int)value;
         return HEXFC_OK;
     case HEXFC_OPT_PREDICTED_CAPACITY:
-        if (value < 0 || value > 2) return HEXFC_ERR_ARG;
+        if (value < 0 || value > 3) return HEXFC_ERR_ARG;
         ctx->predicted = (int)value;
         return HEXFC_OK;
     case HEXFC_OPT_DEBUG_ERROR_BITS:
@@ -1582,10 +1602,16 @@ hexfc_status hexfc_finish(hexfc_ctx* ctx, hexfc_frame_stats* stats)
     return st;
 }
 
-hexfc_status hexfc_completed_stats(const hexfc_ctx* ctx, hexfc_frame_stats* stats)
+hexfc_status hexfc_completed_stats(const hexfc_ctx* ctx, uint64_t frame, hexfc_frame_stats* stats)
 {
     if (!ctx || !stats) return HEXFC_ERR_ARG;
-    *stats = ctx->completed;
+    if (frame == 0) {
+        *stats = ctx->completed;
+        return HEXFC_OK;
+    }
+    const hexfc_frame_stats& h = ctx->history[frame % 16];
+    if (h.frame != frame) return HEXFC_ERR_STATE;   // not verified yet, or no longer kept
+    *stats = h;
     return HEXFC_OK;
 }
 

@@ -181,8 +181,9 @@ cudaError_t launch_bin_sort(const DevMesh& m, FrameBufs& fb, int tiles_x, int ti
 cudaError_t launch_tile_order(FrameBufs& fb, int n_tiles, cudaStream_t s);
 cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, bool stats,
                          cudaStream_t s);
+// Tile capacities from the previous frame's exact counts, or `uniform` (> 0) per tile.
 cudaError_t launch_capacity_from_previous(FrameBufs& fb, int64_t n_tiles, float margin, uint32_t pad,
-                                          cudaStream_t s);
+                                          uint32_t uniform, cudaStream_t s);
 cudaError_t launch_cap_features(FrameBufs& fb, int64_t n_tiles, int tiles_x, float lens_x, float lens_y,
                                 float inv_diag, float motion, cudaStream_t s);
 cudaError_t launch_cap_forward(const CapNet& net, FrameBufs& fb, int64_t n_tiles, float margin, uint32_t pad,

@@ -397,13 +397,15 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __rest
               W, H, sp, key, rgba, seg, err);
 }
 
-// Capacities from the previous frame's exact tile counts: prev * (1 + margin) + pad.
+// Capacities from the previous frame's exact tile counts: prev * (1 + margin)
+// + pad; or, given a uniform count (> 0), that count for every tile instead.
 __global__ void k_capacity_from_previous(const uint32_t* __restrict__ prev, int64_t n_tiles, float margin,
-                                         uint32_t pad, uint32_t* __restrict__ cap)
+                                         uint32_t pad, uint32_t uniform, uint32_t* __restrict__ cap)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
-    cap[t] = (uint32_t)fminf((float)prev[t] * (1.f + margin) + (float)pad, 4.0e9f);
+    const float c = uniform ? (float)uniform : (float)prev[t];
+    cap[t] = (uint32_t)fminf(c * (1.f + margin) + (float)pad, 4.0e9f);
 }
 
 }  // namespace
@@ -413,9 +415,11 @@ cudaError_t prepare_fill_kernels()
     return cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem_bytes());
 }
 
-cudaError_t launch_capacity_from_previous(FrameBufs& fb, int64_t n_tiles, float margin, uint32_t pad, cudaStream_t s)
+cudaError_t launch_capacity_from_previous(FrameBufs& fb, int64_t n_tiles, float margin, uint32_t pad, uint32_t uniform,
+                                          cudaStream_t s)
 {
-    k_capacity_from_previous<<<grid_for(n_tiles, 256), 256, 0, s>>>(fb.tile_frag, n_tiles, margin, pad, fb.tile_cap);
+    k_capacity_from_previous<<<grid_for(n_tiles, 256), 256, 0, s>>>(fb.tile_frag, n_tiles, margin, pad, uniform,
+                                                                     fb.tile_cap);
     return cudaGetLastError();
 }
 

@@ -128,7 +128,7 @@ def load():
                 "hexfc_status_string": (C.c_char_p, [i32]),
                 "hexfc_render_noalloc": (i32, [vp, i32, vp, C.POINTER(hexfc_frame_stats), vp]),
                 "hexfc_finish": (i32, [vp, C.POINTER(hexfc_frame_stats)]),
-                "hexfc_completed_stats": (i32, [vp, C.POINTER(hexfc_frame_stats)]),
+                "hexfc_completed_stats": (i32, [vp, C.c_uint64, C.POINTER(hexfc_frame_stats)]),
                 "hexfc_share_mesh": (i32, [vp, vp, i32, C.POINTER(i32)]),
                 "hexfc_frame_memory": (i32, [vp, C.POINTER(u64)]),
                 "hexfc_trim": (i32, [vp]),
@@ -376,10 +376,15 @@ class Renderer:
             _check(r, "hexfc_finish")
         return st.as_dict()
 
-    def completed_stats(self) -> dict:
-        """Final statistics of the most recently verified frame (no wait)."""
+    def completed_stats(self, frame: int = 0):
+        """Final statistics of frame `frame` (sequence number), or of the most
+        recently verified frame if 0; None if that frame is not verified yet or
+        no longer kept (no wait)."""
         st = hexfc_frame_stats()
-        _check(load().hexfc_completed_stats(self._h, C.byref(st)), "hexfc_completed_stats")
+        r = load().hexfc_completed_stats(self._h, int(frame), C.byref(st))
+        if r == HEXFC_ERR_STATE:
+            return None
+        _check(r, "hexfc_completed_stats")
         return st.as_dict()
 
     def render_noalloc(self, mesh: int, out, stream=None, check: bool = True):

@@ -97,3 +97,81 @@ def test_network_capacities_draw_exact_frames(hx):
         pr.capacity_train(20, lr=3e-3)
     assert n_pred >= 5
     ex.close(); pr.close()
+
+
+def _cut_path(seed, n_seg, seg_len, sizes):
+    """Orbit segments with a cut between them (new azimuth and distance), each
+    segment at sizes[segment % len(sizes)]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_seg):
+        az0, rad = float(rng.uniform(0, 360)), float(rng.uniform(1.2, 2.6))
+        w, h = sizes[k % len(sizes)]
+        for i in range(seg_len):
+            out.append((synth.orbit_view(i, 240, w, h, radius=rad, azimuth0_deg=az0),
+                        synth.lissajous_lens(int(az0) + i, 240)))
+    return out
+
+
+def test_network_gain_over_uniform_and_previous_capacities(hx):
+    """What the trained capacity network gains: on a held-out path with camera
+    cuts and a resolution change, its capacities put far fewer tiles over
+    capacity than the same total spread evenly over the tiles (no per-tile
+    knowledge), and they predict after the resolution change, where the
+    previous frame's counts cannot (those frames are drawn count-then-fill).
+    Every frame of every mode equals the count-then-fill image. The numbers of
+    each mode (tiles over capacity, frames drawn with predicted capacities,
+    exact redraws) are returned in the assertion messages."""
+    m = synth.hex_grid(12, jitter=0.1, warp_amp=0.3, seed=11)
+    style = synth.Style(w_base=1.5, lod=2)
+    ex, pr = hx.Renderer(0), hx.Renderer(0)
+    me = ex.upload_mesh(m.verts, m.cells, m.cell_scalar, m.edge_level)
+    mp = pr.upload_mesh(m.verts, m.cells, m.cell_scalar, m.edge_level)
+    ex.set_style(style)
+    pr.set_style(style)
+
+    def draw(r, mid, v, l):
+        r.set_view(v)
+        r.set_lens(l)
+        o = torch.empty((v.height, v.width, 4), device="cuda")
+        r.render(mid, o)
+        return o, r.last_stats["frame"]
+
+    pr.capacity_reset(3)
+    for v, l in _cut_path(1, 24, 8, [(256, 192)]):   # training: cuts, one size
+        draw(pr, mp, v, l)
+        pr.capacity_train(10, lr=3e-3)
+    ev = _cut_path(2, 8, 6, [(256, 192)] * 4 + [(320, 224)] * 4)
+    ref = [draw(ex, me, v, l)[0].cpu().numpy() for v, l in ev]
+    res = {}
+    for name, mode in (("uniform", 3), ("previous", 1), ("network", 2)):
+        pr.set_option(hx.HEXFC_OPT_PREDICTED_CAPACITY, mode)
+        draw(pr, mp, *ev[0])
+        pr.finish()
+        outs, seqs, final = [], [], {}
+        for v, l in ev:
+            o, q = draw(pr, mp, v, l)
+            outs.append(o)
+            seqs.append(q)
+            for q0 in seqs[-2:]:   # this frame if drawn exactly, else the previous one, now verified
+                st = pr.completed_stats(q0)
+                if st is not None:
+                    final[q0] = st
+        last = pr.finish()
+        final[last["frame"]] = last
+        stats = [final[q] for q in seqs]
+        for o, a in zip(outs, ref):
+            np.testing.assert_array_equal(o.cpu().numpy(), a)
+        res[name] = {"over": sum(st["overflow_tiles"] for st in stats),
+                     "predicted": sum(st["predicted"] for st in stats),
+                     "redrawn": sum(st["redrawn"] for st in stats),
+                     "after_resize": sum(st["predicted"] for st in stats[24:25])}
+    pr.set_option(hx.HEXFC_OPT_PREDICTED_CAPACITY, 0)
+    # per-tile knowledge: fewer tiles over capacity, and no more frames whose pool
+    # ran out, than capacities without it
+    assert res["network"]["over"] < 0.7 * res["uniform"]["over"], res
+    assert res["network"]["redrawn"] <= res["uniform"]["redrawn"], res
+    # after the resolution change only the network predicts; previous-frame
+    # counts of that size do not exist, that frame is drawn count-then-fill
+    assert res["network"]["after_resize"] == 1 and res["previous"]["after_resize"] == 0, res
+    ex.close(); pr.close()

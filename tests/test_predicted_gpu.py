@@ -82,7 +82,7 @@ def test_overflow_falls_back_to_exact(hx):
     assert sc["predicted"] == 1 and sc["overflow_tiles"] == 0
     np.testing.assert_array_equal(c, a)
     with pytest.raises(hx.HexfcError):
-        pr.set_option(hx.HEXFC_OPT_PREDICTED_CAPACITY, 3)
+        pr.set_option(hx.HEXFC_OPT_PREDICTED_CAPACITY, 4)
     ex.close(); pr.close()
 
 
@@ -130,8 +130,9 @@ def test_frames_are_verified_by_the_next_call(hx):
         if k >= 2:   # the first two frames have no previous counts of this size / are exact
             assert st["predicted"] == 1 and st["pending"] == 1
         if k >= 3:
-            done = pr.completed_stats()
-            assert done["frame"] == frames[k - 1] and done["pending"] == 0
+            done = pr.completed_stats(frames[k - 1])
+            assert done is not None and done["frame"] == frames[k - 1] and done["pending"] == 0
+            assert pr.completed_stats(frames[k]) is None   # this frame is still pending
             if k == 4:   # frame 3 jumped much closer: its pool ran out
                 assert done["redrawn"] == 1 and done["overflow_tiles"] > 0
         outs.append(o)
