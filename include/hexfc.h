@@ -159,8 +159,11 @@ enum {
  * g 0.5..2). Never fails. */
 void hexfc_style_default(hexfc_style* style);
 
-/* Create a context on CUDA device `device`. frag_budget_bytes caps the
- * fragment buffers (24 bytes per fragment); 0 means no cap beyond free memory.
+/* Create a context on CUDA device `device`. frag_budget_bytes caps the device
+ * memory of the context's frame buffers (hexfc_frame_memory), fragment arrays
+ * (24 bytes per fragment) included: a count-then-fill frame that would need
+ * more is refused with OOM before its fragment arrays grow; 0 means no cap
+ * beyond free memory. HEXFC_OPT_FRAG_BUDGET changes it between frames.
  * Errors: ARG (out == NULL), CUDA (bad device). */
 hexfc_status hexfc_create(hexfc_ctx** out, int device, uint64_t frag_budget_bytes);
 
@@ -269,8 +272,22 @@ hexfc_status hexfc_set_cell_importance(hexfc_ctx* ctx, int32_t mesh, const float
 hexfc_status hexfc_mesh_info(hexfc_ctx* ctx, int32_t mesh, int64_t* n_faces, int64_t* n_edges);
 
 /* Set the camera. Errors: ARG (NULL, width/height outside 1..16384,
- * znear >= zfar, degenerate basis). */
+ * znear >= zfar, degenerate basis). Draws the whole frame (see
+ * hexfc_set_subrect). */
 hexfc_status hexfc_set_view(hexfc_ctx* ctx, const hexfc_view* view);
+
+/*
+ * Draw only the rectangle [x0, x0 + w) x [y0, y0 + h) of the view's
+ * width x height frame: the next frames' outputs are w x h images (row-major,
+ * row 0 = frame row y0) equal, bit for bit, to those pixels of the whole frame
+ * (vertices are snapped in frame coordinates, then moved by whole pixels; the
+ * screen lens is placed in frame pixels). A frame whose fragment lists do not
+ * fit the memory budget is drawn in parts this way (Section "Results and
+ * Analysis": subdividing the screen and rendering each part separately).
+ * (0, 0, 0, 0) selects the whole frame again; hexfc_set_view does too.
+ * Errors: ARG (rectangle not inside the frame, w or h < 1), STATE (no view).
+ */
+hexfc_status hexfc_set_subrect(hexfc_ctx* ctx, int32_t x0, int32_t y0, int32_t w, int32_t h);
 
 /* Set the focus lens (radius > 0). Errors: ARG. */
 hexfc_status hexfc_set_lens(hexfc_ctx* ctx, const hexfc_lens* lens);
@@ -289,8 +306,8 @@ hexfc_status hexfc_set_style(hexfc_ctx* ctx, const hexfc_style* style);
  * composite. The call waits once for the fragment total (to size the buffers);
  * the image is complete when `stream` reaches the end of the call.
  * stats (host, nullable) receives the frame statistics.
- * Errors: ARG, STATE (no view), OOM (fragments exceed the budget; stats still
- * filled), OVERFLOW (a list longer than HEXFC_MAX_LIST), CUDA, and TIMEOUT or
+ * Errors: ARG, STATE (no view), OOM (the frame's buffers would exceed the
+ * budget; stats still filled: fragments tells how far), OVERFLOW (a list longer than HEXFC_MAX_LIST), CUDA, and TIMEOUT or
  * CHECK from the device-side checks of the fill and composite passes: those
  * passes run after the call returns, so hexfc_render reports their failure
  * on the context's next call (hexfc_render_host at the end of its own frame).
@@ -333,11 +350,14 @@ enum {
                                         frame's tile counts; 2: from the capacity network; 3: the previous
                                         frame's total spread evenly over the tiles (the baseline without
                                         any per-tile knowledge). See below. */
-    HEXFC_OPT_DEBUG_ERROR_BITS = 6   /* test hook, bits 0..7: after the last kernel of the next
+    HEXFC_OPT_DEBUG_ERROR_BITS = 6,  /* test hook, bits 0..7: after the last kernel of the next
                                         hexfc_render or hexfc_render_noalloc frame, these bits are set
                                         in the device error word as a kernel of that frame would set
                                         them (4: a bounded wait ran out, 1: a failed check); no wait
                                         runs out and nothing faults. One frame only. */
+    HEXFC_OPT_FRAG_BUDGET = 7        /* bytes: the cap of hexfc_create's frag_budget_bytes, per frame
+                                        (0: none); a serving loop sets it to what the other frames in
+                                        flight leave */
 };
 hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value);
 

@@ -29,6 +29,7 @@ struct hexfc_ctx {
     int depth_buckets = 2048;   // HEXFC_OPT_DEPTH_BUCKETS
     int window = 2;             // HEXFC_OPT_COMPOSITE_WINDOW
     int predicted = 0;          // HEXFC_OPT_PREDICTED_CAPACITY
+    int sub_x0 = 0, sub_y0 = 0, sub_w = 0, sub_h = 0;   // hexfc_set_subrect (sub_w 0: the whole frame)
     uint64_t inject_bits = 0;   // HEXFC_OPT_DEBUG_ERROR_BITS: ORed into the error word after the next frame
     // A frame drawn with chosen capacities is verified by the next call on the
     // context (or hexfc_finish), once it has completed: what is needed to draw
@@ -289,14 +290,22 @@ ShadeParams make_shade_params(const hexfc_lens& lens, const hexfc_style& s, doub
 
 ShadeParams make_shade(const hexfc_ctx* ctx)
 {
-    return make_shade_params(ctx->lens, ctx->style, ctx->zref, ctx->cam.ortho);
+    ShadeParams sp = make_shade_params(ctx->lens, ctx->style, ctx->zref, ctx->cam.ortho);
+    sp.px_off = ctx->cam.ox;
+    sp.py_off = ctx->cam.oy;
+    return sp;
 }
+
+// Size of the drawn rectangle (the whole frame unless hexfc_set_subrect chose one).
+inline int draw_w(const hexfc_ctx* ctx) { return ctx->sub_w ? ctx->sub_w : ctx->view.width; }
+inline int draw_h(const hexfc_ctx* ctx) { return ctx->sub_w ? ctx->sub_h : ctx->view.height; }
 
 bool valid_view(const hexfc_view* v, CamParams& c, double& zref)
 {
     if (v->width < 1 || v->height < 1 || v->width > 16384 || v->height > 16384) return false;
     if (!(v->znear < v->zfar) || !std::isfinite(v->znear) || !std::isfinite(v->zfar)) return false;
     if (!(v->fovy_deg >= 0.0)) return false;
+    c.ox = c.oy = 0;
     return make_camera(v, c, zref);
 }
 
@@ -367,8 +376,8 @@ void feature_constants(const hexfc_ctx* ctx, const hexfc_view& v, const hexfc_le
             lx = ly = 1e9;   // behind the camera: far from every tile
         }
     }
-    j.lens_x = (float)lx;
-    j.lens_y = (float)ly;
+    j.lens_x = (float)(lx - c.ox);   // tiles are placed in the drawn rectangle
+    j.lens_y = (float)(ly - c.oy);
     j.inv_diag = (float)(1.0 / std::sqrt((double)v.width * v.width + (double)v.height * v.height));
     double motion = 0.0;
     if (ctx->have_prev_cam) {
@@ -400,8 +409,8 @@ FrameJob make_job(hexfc_ctx* ctx, FrameBufs* fb, DevMesh* m, float* out)
     j.sp = make_shade(ctx);
     j.lod = ctx->style.lod;
     j.delta = ctx->style.delta;
-    j.W = ctx->view.width;
-    j.H = ctx->view.height;
+    j.W = draw_w(ctx);
+    j.H = draw_h(ctx);
     j.tiles_x = (j.W + kTile - 1) / kTile;
     j.tiles_y = (j.H + kTile - 1) / kTile;
     j.n_tiles = (int64_t)j.tiles_x * j.tiles_y;
@@ -545,6 +554,21 @@ hexfc_status job_phase2(FrameJob& j, cudaStream_t s)
 }
 
 // After phase 2 has completed: device error bits, totals, limits, fragment buffers.
+// Device memory of a context's frame buffers, with fragment arrays of `frags` records.
+uint64_t frame_bytes(const FrameBufs& f, int64_t frags)
+{
+    uint64_t b = 0;
+    b += (uint64_t)f.v_cap * (sizeof(int4) + sizeof(float));
+    b += (uint64_t)f.f_cap * (sizeof(FaceFrame) + 2 * sizeof(uint32_t));
+    b += (uint64_t)f.t_cap * (9 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t));
+    b += (uint64_t)f.bin_cap * 2 * sizeof(uint32_t) + (uint64_t)f.mask_cap * sizeof(uint32_t) +
+         (uint64_t)f.seg_cap * sizeof(uint64_t);
+    b += (uint64_t)f.p_cap * (3 * sizeof(uint32_t) + sizeof(uint64_t));
+    b += (uint64_t)f.part_cap * (sizeof(uint64_t) + sizeof(uint32_t));
+    b += (uint64_t)frags * (sizeof(uint64_t) + sizeof(float4));
+    return b;
+}
+
 hexfc_status job_read2(FrameJob& j, cudaStream_t s)
 {
     FrameBufs& fb = *j.fb;
@@ -567,12 +591,23 @@ hexfc_status job_read2(FrameJob& j, cudaStream_t s)
     fs.height = (uint32_t)j.H;
     fs.kernel_launches = j.launches;
     if (j.max_list > HEXFC_MAX_LIST) return HEXFC_ERR_OVERFLOW;
-    if (j.budget && j.total * 24ull > j.budget) return HEXFC_ERR_OOM;
     if (!fb.key || fb.frag_cap < (int64_t)j.total) {
-        int64_t c1 = 0;
+        // the fragment arrays must grow: with a budget, the frame's buffers once
+        // they hold it must fit (refused before anything grows), and their
+        // headroom is what the budget leaves
+        int64_t want = (int64_t)j.total + (int64_t)j.total / 4 + 1024;
+        if (j.budget) {
+            const uint64_t per = sizeof(uint64_t) + sizeof(float4);
+            const uint64_t base = frame_bytes(fb, 0);
+            if (base + j.total * per > j.budget) return HEXFC_ERR_OOM;
+            want = std::min<int64_t>(want, (int64_t)((j.budget - base) / per));
+        }
+        dfree(fb.key);
         dfree(fb.rgba);
-        if ((st = ensure(&fb.key, &fb.frag_cap, (int64_t)j.total)) != HEXFC_OK) return st;
-        if ((st = ensure(&fb.rgba, &c1, fb.frag_cap)) != HEXFC_OK) return st;
+        fb.frag_cap = 0;
+        if ((st = dalloc(&fb.key, (size_t)want)) != HEXFC_OK) return st;
+        if ((st = dalloc(&fb.rgba, (size_t)want)) != HEXFC_OK) return st;
+        fb.frag_cap = want;
     }
     return HEXFC_OK;
 }
@@ -684,7 +719,7 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     // previous-frame capacities need the tile counts of a frame of this size; the
     // network (that feature is then 0) and the uniform capacity need only some
     // earlier frame, for the size of the pool
-    const bool same_size = ctx->counts_W == ctx->view.width && ctx->counts_H == ctx->view.height;
+    const bool same_size = ctx->counts_W == draw_w(ctx) && ctx->counts_H == draw_h(ctx);
     if (ctx->counts_W == 0 || (ctx->predicted == 1 && !same_size))
         return render_frame(ctx, m, out, stats, s);
     FrameJob j = make_job(ctx, &ctx->fb, m, out);
@@ -1308,16 +1343,7 @@ hexfc_status hexfc_capacity_train(hexfc_ctx* ctx, int32_t steps, float lr, float
 hexfc_status hexfc_frame_memory(const hexfc_ctx* ctx, uint64_t* bytes)
 {
     if (!ctx || !bytes) return HEXFC_ERR_ARG;
-    const FrameBufs& f = ctx->fb;
-    uint64_t b = 0;
-    b += (uint64_t)f.v_cap * (sizeof(int4) + sizeof(float));
-    b += (uint64_t)f.f_cap * (sizeof(FaceFrame) + 2 * sizeof(uint32_t));
-    b += (uint64_t)f.t_cap * (9 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t));
-    b += (uint64_t)f.bin_cap * 2 * sizeof(uint32_t) + (uint64_t)f.mask_cap * sizeof(uint32_t) +
-         (uint64_t)f.seg_cap * sizeof(uint64_t);
-    b += (uint64_t)f.p_cap * (3 * sizeof(uint32_t) + sizeof(uint64_t));
-    b += (uint64_t)f.part_cap * (sizeof(uint64_t) + sizeof(uint32_t));
-    b += (uint64_t)f.frag_cap * (sizeof(uint64_t) + sizeof(float4));
+    uint64_t b = frame_bytes(ctx->fb, ctx->fb.frag_cap);
     b += (uint64_t)ctx->d_out_cap * sizeof(float);
     for (const auto& bs : ctx->batch) {
         const FrameBufs& g = bs->fb;
@@ -1411,6 +1437,32 @@ hexfc_status hexfc_set_view(hexfc_ctx* ctx, const hexfc_view* v)
     ctx->cam = c;
     ctx->zref = zref;
     ctx->have_view = true;
+    ctx->sub_x0 = ctx->sub_y0 = ctx->sub_w = ctx->sub_h = 0;   // the whole frame
+    return HEXFC_OK;
+}
+
+hexfc_status hexfc_set_subrect(hexfc_ctx* ctx, int32_t x0, int32_t y0, int32_t w, int32_t h)
+{
+    if (!ctx) return HEXFC_ERR_ARG;
+    if (!ctx->have_view) return HEXFC_ERR_STATE;
+    const hexfc_view& v = ctx->view;
+    if (w == 0 && h == 0 && x0 == 0 && y0 == 0) {
+        ctx->sub_x0 = ctx->sub_y0 = ctx->sub_w = ctx->sub_h = 0;
+    } else {
+        if (x0 < 0 || y0 < 0 || w < 1 || h < 1 || (int64_t)x0 + w > v.width || (int64_t)y0 + h > v.height)
+            return HEXFC_ERR_ARG;
+        ctx->sub_x0 = x0;
+        ctx->sub_y0 = y0;
+        ctx->sub_w = w;
+        ctx->sub_h = h;
+    }
+    // the face stage clamps triangle boxes to the drawn rectangle (its tiles),
+    // like every later stage: W, H are the rectangle's, the projection keeps the
+    // frame's centre
+    ctx->cam.ox = ctx->sub_x0;
+    ctx->cam.oy = ctx->sub_y0;
+    ctx->cam.W = draw_w(ctx);
+    ctx->cam.H = draw_h(ctx);
     return HEXFC_OK;
 }
 
@@ -1446,7 +1498,7 @@ hexfc_status hexfc_render_host(hexfc_ctx* ctx, int32_t mesh, float* out_rgba_hos
     if (!m || !ctx->have_view) return HEXFC_ERR_STATE;
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    size_t bytes = sizeof(float) * 4 * (size_t)ctx->view.width * (size_t)ctx->view.height;
+    size_t bytes = sizeof(float) * 4 * (size_t)draw_w(ctx) * (size_t)draw_h(ctx);
     // A page-locked buffer of this device, 16-byte aligned, is written by the
     // resolve kernels through its device mapping: the image crosses to the
     // host while they run rather than in a copy after them.
@@ -1585,6 +1637,10 @@ hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value)
         if (value < 0 || value > 3) return HEXFC_ERR_ARG;
         ctx->predicted = (int)value;
         return HEXFC_OK;
+    case HEXFC_OPT_FRAG_BUDGET:
+        if (value < 0) return HEXFC_ERR_ARG;
+        ctx->budget = (uint64_t)value;
+        return HEXFC_OK;
     case HEXFC_OPT_DEBUG_ERROR_BITS:
         if (value < 0 || value > 7) return HEXFC_ERR_ARG;
         ctx->inject_bits = (uint64_t)value;
@@ -1701,7 +1757,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
 {
     unsigned char* scratch = static_cast<unsigned char*>(noalloc_scratch());
     if (!scratch) return HEXFC_ERR_CUDA;
-    const int W = ctx->view.width, H = ctx->view.height;
+    const int W = draw_w(ctx), H = draw_h(ctx);
     const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
     const int64_t n_tiles = (int64_t)tiles_x * tiles_y;
     const int64_t n_pix = n_tiles * kTilePix;
@@ -1782,7 +1838,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fs.kernel_launches = 15 + (n_long > 0 ? 1u : 0u);
     if (stats) *stats = fs;
     if (fs.max_list > HEXFC_MAX_LIST) return HEXFC_ERR_OVERFLOW;
-    fb.key = a.take<uint64_t>((size_t)total + 2);   // the composite widens key copies to 16-byte boundaries
+    fb.key = a.take<uint64_t>((size_t)total);
     fb.rgba = a.take<float4>((size_t)total);
     if (!fb.key || !fb.rgba) return HEXFC_ERR_OVERFLOW;
     fb.frag_cap = (int64_t)total;

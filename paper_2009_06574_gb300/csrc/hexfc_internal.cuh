@@ -19,7 +19,8 @@ constexpr uint32_t kPadBin = 0xFFFFFFFFu; // empty slot: tile lists are padded t
 struct CamParams {
     double eye[3], R[3], U[3], F[3];
     double focal, scale, cx, cy, znear, zfar, zf_over;
-    int ortho, W, H;
+    int ortho, W, H;   // W, H: size of the drawn rectangle (the frame's unless a sub-rectangle is drawn)
+    int ox, oy;   // drawn rectangle's offset in the frame (pixels): window positions are shifted by it
 };
 
 // Focus+context constants of the fragment stage (float).
@@ -38,6 +39,7 @@ struct ShadeParams {
     int ortho;
     float accent_r2;   // (256 * 2/3 * w_base)^2: accentuation radius squared, 1/256-pixel units
     float desat;       // depth cue strength (0 = off)
+    int px_off, py_off;   // drawn rectangle's offset in the frame: pixel (x, y) is frame pixel (x + px_off, ...)
 };
 
 // A face as two 64-byte records: the per-frame one (window corners, depths,

@@ -52,8 +52,10 @@ __global__ void k_vertex_setup(const float* __restrict__ verts, int64_t n, CamPa
     int4 o = make_int4(0, 0, 0, 0);
     if (valid) {
         z = fmin(fmax(z, 0.0), 1.0);
-        o.x = (int32_t)rint(__dmul_rn(xw, 256.0));
-        o.y = (int32_t)rint(__dmul_rn(yw, 256.0));
+        // snapped in frame coordinates, then moved by whole pixels into the drawn
+        // rectangle: coverage, depth and edge distances are those of the frame
+        o.x = (int32_t)rint(__dmul_rn(xw, 256.0)) - 256 * cam.ox;
+        o.y = (int32_t)rint(__dmul_rn(yw, 256.0)) - 256 * cam.oy;
         o.z = (int32_t)(uint32_t)rint(__dmul_rn(z, 16777215.0));
         o.w = 1;
     }

@@ -55,7 +55,9 @@ __device__ __forceinline__ float4 shade_fragment(const ShadeRec& t, uint32_t mas
     // lens distance, normalised to 1 at the lens border
     float dist;
     if (sp.lens_mode == HEXFC_LENS_SCREEN) {
-        const float dx = ((float)px + 0.5f) - sp.lens_c[0], dy = ((float)py + 0.5f) - sp.lens_c[1];
+        // (frame pixel coordinates, so that a drawn rectangle shades as the frame does)
+        const float dx = ((float)(px + sp.px_off) + 0.5f) - sp.lens_c[0];
+        const float dy = ((float)(py + sp.py_off) + 0.5f) - sp.lens_c[1];
         dist = sqrt_approx(dx * dx + dy * dy) * sp.lens_inv_r;
     } else {
         // the interpolated offset from the centre, P - C = D / Q (D affine in lam)

@@ -39,6 +39,7 @@ HEXFC_OPT_DEPTH_BUCKETS = 3
 HEXFC_OPT_COMPOSITE_WINDOW = 4
 HEXFC_OPT_PREDICTED_CAPACITY = 5
 HEXFC_OPT_DEBUG_ERROR_BITS = 6
+HEXFC_OPT_FRAG_BUDGET = 7
 HEXFC_CAPACITY_PARAMS = 4545
 STAGES = ["vertex", "face", "tile_scan", "gap1", "bin", "count", "scan", "gap2", "fill", "composite"]
 
@@ -50,7 +51,7 @@ EXPORTS = ["hexfc_style_default", "hexfc_create", "hexfc_destroy", "hexfc_upload
            "hexfc_frame_memory", "hexfc_trim", "hexfc_render_batch", "hexfc_capacity_reset",
            "hexfc_capacity_set_weights", "hexfc_capacity_get_weights", "hexfc_capacity_grad",
            "hexfc_capacity_train", "hexfc_last_cuda_error", "hexfc_cuda_error_name", "hexfc_finish",
-           "hexfc_completed_stats"]
+           "hexfc_completed_stats", "hexfc_set_subrect"]
 
 
 class HexfcError(RuntimeError):
@@ -128,6 +129,7 @@ def load():
                 "hexfc_status_string": (C.c_char_p, [i32]),
                 "hexfc_render_noalloc": (i32, [vp, i32, vp, C.POINTER(hexfc_frame_stats), vp]),
                 "hexfc_finish": (i32, [vp, C.POINTER(hexfc_frame_stats)]),
+                "hexfc_set_subrect": (i32, [vp, i32, i32, i32, i32]),
                 "hexfc_completed_stats": (i32, [vp, C.c_uint64, C.POINTER(hexfc_frame_stats)]),
                 "hexfc_share_mesh": (i32, [vp, vp, i32, C.POINTER(i32)]),
                 "hexfc_frame_memory": (i32, [vp, C.POINTER(u64)]),
@@ -366,6 +368,15 @@ class Renderer:
         _check(load().hexfc_capacity_train(self._h, int(steps), float(lr), C.byref(loss) if want_loss else None,
                                            _stream_ptr(stream)), "hexfc_capacity_train")
         return float(loss.value) if want_loss else None
+
+    def set_subrect(self, x0: int = 0, y0: int = 0, w: int = 0, h: int = 0):
+        """Draw only the rectangle [x0, x0 + w) x [y0, y0 + h) of the view's frame
+        (the outputs are then w x h); all zeros: the whole frame again."""
+        _check(load().hexfc_set_subrect(self._h, int(x0), int(y0), int(w), int(h)), "hexfc_set_subrect")
+
+    def set_budget(self, nbytes: int):
+        """Cap of the context's frame buffers for the next frames (0: none)."""
+        self.set_option(HEXFC_OPT_FRAG_BUDGET, int(nbytes))
 
     def finish(self, check: bool = True) -> dict:
         """Complete the last frame (verify a frame drawn with predicted capacities,

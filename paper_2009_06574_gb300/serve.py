@@ -17,6 +17,14 @@ buffers (largest first) if that makes room (freeing device memory synchronises
 the device, so it is not done under running frames). Requests start in
 arrival order (no overtaking).
 
+Each frame is drawn with a budget of its own: what the other slots hold or
+have reserved leaves of the total. A frame that needs more (a new pose of a
+known kind can) is refused by the renderer before its buffers grow, and is
+then drawn in horizontal bands of the screen, each a separate rendering into
+its rows of the image (the paper's subdivision of the screen into parts,
+Section "Results and Analysis"); a band that still does not fit is halved.
+The bands give the frame's pixels bit for bit.
+
 The renderer is injected (`renderer_factory`), so the scheduling logic is
 tested on the CPU with a stand-in; the default is `hexfc.Renderer`.
 """
@@ -89,6 +97,10 @@ class _BufferPool:
             self._free.setdefault(n, []).append(raw)
 
 
+HEXFC_ERR_OOM = -2
+BAND_ROWS = 16   # bands start and end on the renderer's tile rows
+
+
 class _Slot:
     def __init__(self, index: int, renderer, stream):
         self.index = index
@@ -97,8 +109,15 @@ class _Slot:
         self.busy = False
         self.held = 0          # bytes of per-frame buffers the slot holds now
         self.reserved = 0      # bytes admitted for the frame in flight
+        self.budget = 0        # bytes the frame in flight may use (the others' share taken out)
         self.mesh_ids = {}     # mesh name -> id in this slot's context
         self.job = None
+
+
+def _bands(height: int, parts: int):
+    """`parts` row ranges (y0, h) covering [0, height), cut on multiples of BAND_ROWS."""
+    step = max(BAND_ROWS, -(-height // parts // BAND_ROWS) * BAND_ROWS)
+    return [(y, min(step, height - y)) for y in range(0, height, step)]
 
 
 class Server:
@@ -209,6 +228,7 @@ class Server:
             self._queue.popleft()
             slot.busy = True
             slot.reserved = max(slot.held, need or 0)
+            slot.budget = max(0, self.budget - self._others(slot))
             slot.job = t
             if need is None:
                 self._alone = slot
@@ -268,11 +288,15 @@ class Server:
             res.slot = slot.index
             img = self._pool.take((int(req.view.height), int(req.view.width), 4))
             status = 0
+            bands, band_stats = 1, None
             try:
                 slot.r.set_view(req.view)
                 slot.r.set_lens(req.lens)
                 slot.r.set_style(req.style)
+                slot.r.set_budget(slot.budget)
                 status = slot.r.render_host(slot.mesh_ids[req.mesh], img, slot.stream, check=False)
+                if status == HEXFC_ERR_OOM:
+                    status, bands, band_stats = _render_bands(slot, req, img, slot.mesh_ids[req.mesh])
             except Exception:   # an argument the library rejected
                 status = -1
             lce = getattr(slot.r, "last_cuda_error", None)
@@ -284,7 +308,12 @@ class Server:
                 res.status = int(status)
                 res.cuda_error = int(cuda_error)
                 res.image = img
-                res.stats = dict(slot.r.last_stats) if slot.r.last_stats else None
+                if band_stats is not None and status == 0:
+                    res.stats = band_stats
+                else:
+                    res.stats = dict(slot.r.last_stats) if slot.r.last_stats else None
+                if res.stats is not None:
+                    res.stats["bands"] = bands
                 res.t_done = time.perf_counter()
                 key = self._key(req)
                 if status == 0:
@@ -297,6 +326,38 @@ class Server:
                     self._alone = None
                 self._admit()
                 self._cv.notify_all()
+
+
+def _render_bands(slot, req, img, mid):
+    """Draw the frame of `req` into `img` in horizontal bands that fit the
+    slot's budget; returns (status, number of bands, summed statistics)."""
+    H = int(req.view.height)
+    W = int(req.view.width)
+    frags = int((slot.r.last_stats or {}).get("fragments", 0))
+    # the fragment records dominate a frame's buffers: parts for 60% of the budget
+    parts = max(2, -(-frags * 24 // max(1, int(0.6 * slot.budget)))) if slot.budget else 2
+    todo = list(reversed(_bands(H, parts)))
+    done, total = 0, {"fragments": 0, "max_list": 0, "long_lists": 0, "bin_entries": 0,
+                      "width": W, "height": H}
+    status = 0
+    while todo:
+        y0, h = todo.pop()
+        slot.r.set_subrect(0, y0, W, h)
+        st = slot.r.render_host(mid, img[y0:y0 + h], slot.stream, check=False)
+        if st == HEXFC_ERR_OOM and h > BAND_ROWS:   # this band is still too large: halve it
+            todo.extend(reversed([(y0 + a, b) for a, b in _bands(h, 2)]))
+            continue
+        if st != 0:
+            status = st
+            break
+        done += 1
+        ls = slot.r.last_stats or {}
+        total["fragments"] += int(ls.get("fragments", 0))
+        total["bin_entries"] += int(ls.get("bin_entries", 0))
+        total["long_lists"] += int(ls.get("long_lists", 0))
+        total["max_list"] = max(total["max_list"], int(ls.get("max_list", 0)))
+    slot.r.set_subrect(0, 0, 0, 0)
+    return status, done, total
 
 
 def percentile(values, q: float) -> float:

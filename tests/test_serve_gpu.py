@@ -98,3 +98,81 @@ def test_shared_mesh_trim_and_memory(hx):
         b.share_mesh(b, 99)
     assert e.value.status == hx.HEXFC_ERR_STATE
     b.close()
+
+
+@pytest.mark.parametrize("lens_mode", [synth.LENS_SCREEN, synth.LENS_SPHERE])
+def test_subrect_pixels_equal_the_whole_frame(hx, lens_mode):
+    """A rectangle of the frame drawn alone (hexfc_set_subrect) is those pixels
+    of the whole frame bit for bit: full-width bands, and an inner rectangle at
+    odd offsets; the screen lens stays where it is in the frame."""
+    import torch
+    m = synth.hex_grid(9, jitter=0.1, warp_amp=0.3, seed=6)
+    W, H = 200, 150
+    view = synth.orbit_view(33, 120, W, H)
+    lens = (synth.Lens(mode=synth.LENS_SCREEN, center=(83.3, 61.7, 0.0), radius=45.0)
+            if lens_mode == synth.LENS_SCREEN else synth.lissajous_lens(33, 120))
+    r = hx.Renderer(0)
+    mid = r.upload_mesh(m.verts, m.cells, m.cell_scalar, m.edge_level)
+    r.set_view(view)
+    r.set_lens(lens)
+    r.set_style(synth.Style(w_base=1.5, lod=2))
+    full = torch.zeros((H, W, 4), device="cuda")
+    r.render(mid, full)
+    whole = r.last_stats["fragments"]
+    frags = 0
+    for (x0, y0, w, h) in [(0, 0, W, 48), (0, 48, W, 64), (0, 112, W, 38), (37, 21, 50, 33), (199, 149, 1, 1)]:
+        r.set_subrect(x0, y0, w, h)
+        part = torch.full((h, w, 4), -1.0, device="cuda")
+        r.render(mid, part)
+        torch.cuda.synchronize()
+        assert torch.equal(part, full[y0:y0 + h, x0:x0 + w]), (x0, y0, w, h)
+        if w == W:
+            frags += r.last_stats["fragments"]
+    assert frags == whole
+    r.set_subrect()
+    again = torch.zeros((H, W, 4), device="cuda")
+    r.render(mid, again)
+    assert torch.equal(again, full)
+    with pytest.raises(hx.HexfcError):
+        r.set_subrect(150, 0, 60, 10)
+    r.close()
+
+
+def test_frame_above_the_budget_is_drawn_in_bands(hx):
+    """A frame whose buffers exceed the server's whole budget is refused by the
+    renderer and drawn in horizontal bands that fit: its image equals the
+    frame drawn whole without a budget, and matches the oracle on sampled
+    pixels."""
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from parity import compare_lists
+    import oracle
+    from paper_2009_06574_gb300 import serve
+    m = synth.hex_grid(16, jitter=0.1, warp_amp=0.3, seed=8)
+    W, H = 320, 240
+    req = serve.Request(mesh="g16", view=synth.orbit_view(7, 120, W, H, radius=1.4),
+                        lens=synth.lissajous_lens(7, 120), style=synth.Style(w_base=1.5, lod=2))
+    r = hx.Renderer(0)   # the frame drawn whole, no budget: its need and its image
+    mid = r.upload_mesh(m.verts, m.cells, m.cell_scalar, m.edge_level)
+    r.set_view(req.view)
+    r.set_lens(req.lens)
+    r.set_style(req.style)
+    ref = np.zeros((H, W, 4), np.float32)
+    r.render_host(mid, ref)
+    need = r.frame_memory()
+    rng = np.random.default_rng(3)
+    px = rng.integers(0, W, 800).astype(np.int32)
+    py = rng.integers(0, H, 800).astype(np.int32)
+    g = r.debug_pixels(px, py)
+    r.close()
+    with serve.Server(0, slots=2, mem_budget_bytes=int(0.55 * need)) as srv:
+        srv.add_mesh("g16", m.verts, m.cells, m.cell_scalar, m.edge_level)
+        res = srv.result(srv.submit(req), timeout=120)
+        assert res.status == 0
+        assert res.stats["bands"] >= 2
+        np.testing.assert_array_equal(res.image, ref)
+        om = oracle.Mesh(m.verts, m.cells, m.cell_scalar, m.edge_level)
+        o = om.render(req.view, req.lens, req.style, px, py)
+        compare_lists(g, o, om, req.view, req.lens, req.style, px, py, gpu_image=np.asarray(res.image)[py, px])
+        assert srv.peak_reserved <= int(0.55 * need)

@@ -25,12 +25,18 @@ class Ledger:
 
 class FakeRenderer:
     """Draws a deterministic image; holds `footprint` bytes after its first
-    frame of a kind, like a context whose buffers grow and are reused."""
+    frame of a kind, like a context whose buffers grow and are reused. Like the
+    library, it refuses (OOM) a frame whose footprint exceeds its per-frame
+    budget before holding more, and draws a band of the frame when given a
+    sub-rectangle (footprint in proportion to the band's rows)."""
 
     def __init__(self, device, ledger, footprint, duration):
         self.ledger, self.footprint, self.duration = ledger, footprint, duration
         self.meshes, self.last_stats, self.view = [], None, None
         self.held = 0
+        self.budget = 0
+        self.sub = None
+        self.refused = 0
 
     def upload_mesh(self, verts, cells, scalar=None, levels=None):
         self.meshes.append(("own", int(np.asarray(cells).shape[0])))
@@ -40,13 +46,30 @@ class FakeRenderer:
         self.meshes.append(src.meshes[mid])
         return len(self.meshes) - 1
 
-    def set_view(self, v): self.view = v
+    def set_view(self, v):
+        self.view = v
+        self.sub = None
+
     def set_lens(self, l): self.lens = l
     def set_style(self, s): self.style = s
+    def set_budget(self, b): self.budget = b
+
+    def set_subrect(self, x0=0, y0=0, w=0, h=0):
+        self.sub = None if w == 0 else (x0, y0, w, h)
 
     def render_host(self, mid, img, stream=None, check=False):
-        key = (self.meshes[mid][1], img.shape[1], img.shape[0])
+        W, H = int(self.view.width), int(self.view.height)
+        key = (self.meshes[mid][1], W, H)
         need = self.footprint(key)
+        if callable(need):   # a footprint that depends on the pose
+            need = need(self.view)
+        x0, y0, w, h = self.sub or (0, 0, W, H)
+        assert img.shape[:2] == (h, w)
+        need = need * h // H
+        if self.budget and need > self.budget:
+            self.refused += 1
+            self.last_stats = {"fragments": need // 24}
+            return serve.HEXFC_ERR_OOM
         L = self.ledger
         with L.lock:
             self.held = max(self.held, need)
@@ -56,9 +79,8 @@ class FakeRenderer:
             L.peak_running = max(L.peak_running, L.running)
             L.log.append(("start", key, L.running))
         time.sleep(self.duration(key))
-        h, w = img.shape[:2]
-        img[...] = (key[0] * 1e-3 + np.arange(w)[None, :, None] * 1e-4 + self.view.eye[0]
-                    + np.arange(h)[:, None, None] * 1e-5)
+        img[...] = (key[0] * 1e-3 + (x0 + np.arange(w))[None, :, None] * 1e-4 + self.view.eye[0]
+                    + (y0 + np.arange(h))[:, None, None] * 1e-5)
         self.last_stats = {"fragments": key[0] * w * h}
         with L.lock:
             L.running -= 1
@@ -166,6 +188,40 @@ def test_idle_buffers_are_released_to_admit_a_large_frame():
     srv.close()
     assert r.status == 0
     assert L.peak <= 1000 * MB
+
+
+def test_new_pose_of_a_known_kind_is_drawn_in_bands_within_the_budget():
+    """A second pose of a kind already measured needs more than was reserved
+    for it: the frame is refused at its own budget (what the other slots
+    leave) instead of growing its buffers, then drawn in horizontal bands that
+    fit; the image equals the frame drawn whole, and the budget holds."""
+    L = Ledger()
+
+    def fp(key):
+        if key[0] != 7:
+            return 300 * MB
+        return lambda view: (400 if view.eye[0] > 0.5 else 1500) * MB   # the second pose: far more
+
+    srv = make_server(3, 1000 * MB, fp, lambda k: 0.02, L)
+    srv.add_mesh("m2", *grid(2))
+    srv.add_mesh("m7", *grid(7))
+    first = srv.result(srv.submit(request(7, 64, 64, 10)), timeout=30)   # eye x > 0.5: 400 MB
+    assert first.status == 0 and first.stats["bands"] == 1
+    busy = [srv.submit(request(2, 64, 64, i)) for i in range(2)]          # 300 MB frames beside it
+    second = srv.result(srv.submit(request(7, 64, 64, 60)), timeout=30)  # eye x < 0: 1500 MB whole
+    for t in busy:
+        assert srv.result(t, timeout=30).status == 0
+    srv.close()
+    assert second.status == 0 and second.stats["bands"] >= 2
+    np.testing.assert_array_equal(second.image, expected_image(7, 64, 64, 60))
+    assert L.peak <= 1000 * MB
+    assert any(s.r.refused for s in srv._slots)
+
+
+def test_band_rows():
+    assert serve._bands(100, 2) == [(0, 64), (64, 36)]
+    assert serve._bands(1080, 3) == [(0, 368), (368, 368), (736, 344)]
+    assert serve._bands(20, 8) == [(0, 16), (16, 4)]
 
 
 def test_percentile():
