@@ -56,7 +56,8 @@ class _Style(C.Structure):
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("tf_lo", C.c_float),
                 ("tf_hi", C.c_float), ("bg", C.c_float * 3), ("accent_beta", C.c_float),
                 ("halo_scale", C.c_float), ("darken", C.c_float), ("g_min", C.c_float),
-                ("g_max", C.c_float), ("desat", C.c_float)]
+                ("g_max", C.c_float), ("desat", C.c_float), ("sil_alpha", C.c_float),
+                ("sil_threshold", C.c_float)]
 
 
 def _view(v) -> _View:
@@ -114,7 +115,7 @@ def lib():
             L.orc_mesh_vertex_importance.argtypes = [vp, vp]
             L.orc_render.restype = C.c_int64
             L.orc_render.argtypes = [vp, C.POINTER(_View), C.POINTER(_Lens), C.POINTER(_Style),
-                                     vp, vp, C.c_int64, C.c_int64, vp, vp, vp, vp, vp]
+                                     vp, vp, C.c_int64, C.c_int64, vp, vp, vp, vp, vp, vp]
             L.orc_shade.restype = C.c_int
             L.orc_shade.argtypes = [vp, C.POINTER(_View), C.POINTER(_Lens), C.POINTER(_Style),
                                     C.c_int32, C.c_int32, C.c_uint32, C.c_int, vp, vp]
@@ -129,6 +130,8 @@ def lib():
             L.orc_fragment_geometry.argtypes = [vp, C.POINTER(_View), C.POINTER(_Lens),
                                                 C.POINTER(_Style), C.c_int32, C.c_int32,
                                                 C.c_uint32, vp, vp]
+            L.orc_boundary_depth_at.restype = C.c_int
+            L.orc_boundary_depth_at.argtypes = [vp, C.POINTER(_View), C.c_int32, C.c_int32, vp]
             L.orc_segment_distance.restype = C.c_double
             L.orc_segment_distance.argtypes = [C.c_int64, C.c_int64, C.c_int32, C.c_int32,
                                                C.c_int32, C.c_int32]
@@ -243,8 +246,9 @@ class Mesh:
 
     def render(self, view, lens, style, px=None, py=None, cap=None, fragments=True):
         """Render the listed pixels (default: all, row-major). Returns a dict with
-        counts, offsets, keys, rgba (float64 [F,4]), tie (uint8 [F]) and image
-        (float64 [npix,4])."""
+        counts, offsets, keys, rgba (float64 [F,4]), tie (uint8 [F]), image
+        (float64 [npix,4], with the silhouette overlay) and sil (uint8 [npix], 1
+        for a silhouette pixel)."""
         if px is None:
             yy, xx = np.meshgrid(np.arange(view.height), np.arange(view.width), indexing="ij")
             px, py = xx.ravel(), yy.ravel()
@@ -253,26 +257,27 @@ class Mesh:
         n = px.shape[0]
         counts = np.zeros(n, dtype=np.uint32)
         image = np.zeros((n, 4), dtype=np.float64)
+        sil = np.zeros(n, dtype=np.uint8)
         v, l, s = _view(view), _lens(lens), _style(style)
         L = lib()
         if cap is None:
             # counting pass first so that the fragment arrays are sized exactly
             tot = L.orc_render(self._h, C.byref(v), C.byref(l), C.byref(s), _ptr(px), _ptr(py), n, 0,
-                               _ptr(counts), None, None, None, _ptr(image))
+                               _ptr(counts), None, None, None, _ptr(image), _ptr(sil))
             cap = int(counts.sum(dtype=np.int64))
             if not fragments:
-                return {"counts": counts, "image": image}
+                return {"counts": counts, "image": image, "sil": sil}
         keys = np.zeros(cap, dtype=np.uint64)
         rgba = np.zeros((cap, 4), dtype=np.float64)
         tie = np.zeros(cap, dtype=np.uint8)
         tot = L.orc_render(self._h, C.byref(v), C.byref(l), C.byref(s), _ptr(px), _ptr(py), n, cap,
-                           _ptr(counts), _ptr(keys), _ptr(rgba), _ptr(tie), _ptr(image))
+                           _ptr(counts), _ptr(keys), _ptr(rgba), _ptr(tie), _ptr(image), _ptr(sil))
         if tot < 0:
             raise RuntimeError("fragment capacity exceeded")
         off = np.zeros(n + 1, dtype=np.int64)
         np.cumsum(counts, out=off[1:])
         return {"counts": counts, "offsets": off, "keys": keys[:tot], "rgba": rgba[:tot],
-                "tie": tie[:tot], "image": image}
+                "tie": tie[:tot], "image": image, "sil": sil}
 
     def fragment_geometry(self, view, lens, style, px, py, face2tri):
         """Inputs of the focus+context formulas for one fragment, or None if the
@@ -291,6 +296,13 @@ class Mesh:
         d["b"] = out[10:13].copy()
         d["vi"] = vi
         return d
+
+    def boundary_depth(self, view, px, py):
+        """24-bit depth of the nearest boundary-face fragment at the pixel, or None."""
+        z = np.zeros(1, np.uint32)
+        v = _view(view)
+        ok = lib().orc_boundary_depth_at(self._h, C.byref(v), int(px), int(py), _ptr(z))
+        return int(z[0]) if ok else None
 
     def shade(self, view, lens, style, px, py, face2tri, flip=0):
         """Shade one fragment with decisions in `flip` inverted; None if not covered."""

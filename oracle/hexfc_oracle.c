@@ -65,6 +65,18 @@
  *      the Eq. 4 colour moves towards its luma y = 0.299 R + 0.587 G +
  *      0.114 B by k; opacity unchanged.
  *
+ *   R17 silhouettes (Section "Blending Focus and Context": white exterior and
+ *      interior screen-space silhouettes; the boundary surface is rendered and
+ *      fragments along sharp edges of its depth buffer are emphasised): D(p)
+ *      = 24-bit depth of the nearest fragment of a boundary face (a face of
+ *      one cell) at pixel p. p is a silhouette pixel iff D(p) exists and a
+ *      4-neighbour inside the frame has none (exterior), or for a neighbour q
+ *      and the opposite neighbour q' (both with D), D(q) - D(p) > T and
+ *      |D(q) - 2 D(p) + D(q')| > T (interior: the near side of a jump in
+ *      depth; a plane, however steep, has no second difference), T =
+ *      sil_threshold. A silhouette pixel's image moves towards white by
+ *      sil_alpha: RGB' = RGB + a (1 - RGB), A' = A + a (1 - A).
+ *
  * Near-tie bookkeeping: a discrete decision of R8/R9 whose two sides differ by
  * less than ORC_TIE_MARGIN pixels is reported in a per-fragment bit mask, and
  * orc_shade() can evaluate a fragment with any of those decisions flipped, so
@@ -107,6 +119,8 @@ typedef struct {
     float bg[3];
     float accent_beta, halo_scale, darken, g_min, g_max;
     float desat;          /* depth cue strength (R16), 0 = off */
+    float sil_alpha;      /* silhouette opacity (R17), 0 = off */
+    float sil_threshold;  /* silhouette depth threshold T, 24-bit depth units (R17) */
 } orc_style;
 
 /* ----------------------------------------------------------------- quality */
@@ -192,6 +206,7 @@ void orc_cell_quality(const float* verts, const int32_t* cells, int64_t n_cells,
 typedef struct {
     int32_t c[4];  /* canonical cyclic corners */
     int32_t s[4];  /* sorted ids: the identity of the face */
+    int32_t ncell; /* cells sharing the face: 1 on the boundary surface */
 } orc_face;
 
 typedef struct {
@@ -207,6 +222,8 @@ typedef struct {
     orc_face* faces;     /* unique faces sorted by s */
     orc_edge* edges;     /* unique edges sorted by (a,b) */
     int32_t* face_edge;  /* n_faces*4: edge index of local edge k = (c_k, c_k+1) */
+    int64_t* bfaces;     /* ids of the boundary faces (R17) */
+    int64_t n_bfaces;
     double bbox_c[3];
 } orc_mesh;
 
@@ -303,10 +320,21 @@ orc_mesh* orc_mesh_build(const float* verts, int64_t n_verts, const int32_t* cel
         }
     qsort(all, 6 * (size_t)n_cells, sizeof(orc_face), cmp_face);
     int64_t nf = 0;
-    for (int64_t i = 0; i < 6 * n_cells; ++i)
-        if (nf == 0 || cmp_face(&all[nf - 1], &all[i]) != 0) all[nf++] = all[i];
+    for (int64_t i = 0; i < 6 * n_cells; ++i) {
+        if (nf == 0 || cmp_face(&all[nf - 1], &all[i]) != 0) {
+            all[nf] = all[i];
+            all[nf].ncell = 1;
+            ++nf;
+        } else {
+            all[nf - 1].ncell += 1;
+        }
+    }
     m->faces = all;
     m->n_faces = nf;
+    m->bfaces = (int64_t*)malloc(sizeof(int64_t) * ((size_t)nf + 1));
+    m->n_bfaces = 0;
+    for (int64_t f = 0; f < nf; ++f)
+        if (all[f].ncell == 1) m->bfaces[m->n_bfaces++] = f;
 
     /* unique edges with level and importance */
     orc_edge* E = (orc_edge*)malloc(sizeof(orc_edge) * 12 * (size_t)n_cells);
@@ -356,6 +384,7 @@ void orc_mesh_free(orc_mesh* m)
     free(m->faces);
     free(m->edges);
     free(m->face_edge);
+    free(m->bfaces);
     free(m);
 }
 
@@ -791,17 +820,68 @@ typedef struct {
     int tie;
 } orc_frag;
 
+/* Depth (24-bit) of the nearest fragment of a boundary face at pixel (px,py);
+ * 0 if no boundary face covers it (reading R17). */
+static int orc_boundary_depth(const orc_mesh* m, const orc_frame* fr, int32_t px, int32_t py, uint32_t* z)
+{
+    int found = 0;
+    uint32_t best = 0;
+    for (int64_t b = 0; b < m->n_bfaces; ++b) {
+        const int64_t f = m->bfaces[b];
+        for (int tri = 0; tri < 2; ++tri) {
+            const orc_tri* t = &fr->tri[2 * f + tri];
+            int64_t l[3];
+            if (!orc_covers(t, px, py, l)) continue;
+            orc_pv pv[4];
+            for (int k = 0; k < 4; ++k) pv[k] = fr->pv[m->faces[f].c[k]];
+            const uint32_t d = orc_depth(t, pv, l);
+            if (!found || d < best) best = d;
+            found = 1;
+        }
+    }
+    *z = best;
+    return found;
+}
+
+/* Is (px,py) a silhouette pixel of the boundary surface's depth image (R17)? */
+static int orc_silhouette(const orc_mesh* m, const orc_frame* fr, const orc_style* st, int32_t px, int32_t py,
+                          int W, int H)
+{
+    uint32_t zp;
+    if (!orc_boundary_depth(m, fr, px, py, &zp)) return 0;
+    static const int dx[4] = {1, -1, 0, 0}, dy[4] = {0, 0, 1, -1};   /* k ^ 1 is the opposite side */
+    int inside[4], has[4];
+    uint32_t zq[4];
+    for (int k = 0; k < 4; ++k) {
+        const int32_t qx = px + dx[k], qy = py + dy[k];
+        inside[k] = qx >= 0 && qy >= 0 && qx < W && qy < H;
+        has[k] = inside[k] && orc_boundary_depth(m, fr, qx, qy, &zq[k]);
+        if (inside[k] && !has[k]) return 1;   /* exterior: the surface ends here */
+    }
+    const int64_t T = (int64_t)st->sil_threshold;
+    for (int k = 0; k < 4; ++k) {
+        const int o = k ^ 1;
+        if (!has[k] || !has[o]) continue;
+        const int64_t d1 = (int64_t)zq[k] - (int64_t)zp;
+        const int64_t d2 = (int64_t)zq[k] - 2 * (int64_t)zp + (int64_t)zq[o];
+        if (d1 > T && (d2 > T || -d2 > T)) return 1;   /* interior: the near side of a depth jump */
+    }
+    return 0;
+}
+
 /*
  * Render the listed pixels. For pixel i: counts[i] fragments, written in
  * sorted order at the running offset into keys (uint64), frag_rgba (4 doubles
  * each) and frag_tie (bit mask of near-tie decisions); image[4 i..] gets the
- * composited RGBA. Any output pointer may be NULL. Returns the total number of
- * fragments, or -1 if it exceeds cap (counts and image are still complete).
+ * composited RGBA (with the silhouette overlay of R17) and sil[i] 1 if the
+ * pixel is a silhouette pixel (computed only if st->sil_alpha > 0). Any output
+ * pointer may be NULL. Returns the total number of fragments, or -1 if it
+ * exceeds cap (counts and image are still complete).
  */
 int64_t orc_render(const orc_mesh* m, const orc_view* v, const orc_lens* lens, const orc_style* st,
                    const int32_t* pxs, const int32_t* pys, int64_t npix, int64_t cap,
                    uint32_t* counts, uint64_t* keys, double* frag_rgba, uint8_t* frag_tie,
-                   double* image)
+                   double* image, uint8_t* sil)
 {
     orc_frame fr;
     orc_frame_setup(m, v, &fr);
@@ -855,9 +935,16 @@ int64_t orc_render(const orc_mesh* m, const orc_view* v, const orc_lens* lens, c
             A += tr * L[a].rgba[3];
         }
         if (counts) counts[i] = n;
+        const int is_sil = st->sil_alpha > 0.0f &&
+                           orc_silhouette(m, &fr, st, pxs[i], pys[i], v->width, v->height);
+        if (sil) sil[i] = (uint8_t)is_sil;
         if (image) {
             for (int k = 0; k < 3; ++k) image[4 * i + k] = C[k] + (1.0 - A) * (double)st->bg[k];
             image[4 * i + 3] = A;
+            if (is_sil) { /* white silhouette over the pixel (R17) */
+                const double a = st->sil_alpha;
+                for (int k = 0; k < 4; ++k) image[4 * i + k] = image[4 * i + k] + a * (1.0 - image[4 * i + k]);
+            }
         }
         if (fits) {
             for (uint32_t a = 0; a < n; ++a) {
@@ -939,6 +1026,18 @@ int orc_fragment_geometry(const orc_mesh* m, const orc_view* v, const orc_lens* 
         memcpy(out, vals, sizeof(vals));
         for (int k = 0; k < 3; ++k) vi[k] = fr.tri[2 * f + tri].vi[k];
     }
+    orc_frame_free(&fr);
+    return ok;
+}
+
+/* Test hook: the boundary surface's depth at pixel (px,py) (reading R17):
+ * returns 1 and *z (24-bit depth of the nearest boundary-face fragment), or 0
+ * if no boundary face covers the pixel. */
+int orc_boundary_depth_at(const orc_mesh* m, const orc_view* v, int32_t px, int32_t py, uint32_t* z)
+{
+    orc_frame fr;
+    orc_frame_setup(m, v, &fr);
+    const int ok = orc_boundary_depth(m, &fr, px, py, z);
     orc_frame_free(&fr);
     return ok;
 }

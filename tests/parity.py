@@ -66,8 +66,11 @@ def compare_lists(gpu: dict, orc: dict, om: "oracle.Mesh", view, lens, style, px
         exp = orc["image"].copy()
         if n_alt:
             touched = np.unique(pix_of[np.nonzero(err > tol)[0]])
+            a = float(getattr(style, "sil_alpha", 0.0))
             for i in touched:
                 exp[i] = oracle.composite(ro[off[i]:off[i + 1]], style.bg)
+                if a > 0 and orc.get("sil") is not None and orc["sil"][i]:   # the white silhouette on top
+                    exp[i] = exp[i] + a * (1.0 - exp[i])
         ie = np.abs(gpu_image.astype(np.float64) - exp).max(axis=1)
         worst = int(np.argmax(ie)) if len(ie) else 0
         stats["max_pixel_err"] = float(ie.max()) if len(ie) else 0.0

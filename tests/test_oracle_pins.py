@@ -127,8 +127,8 @@ def _golden_rows():
 @pytest.mark.parametrize("name,inp,exp", _golden_rows(), ids=[r[0] for r in _golden_rows()])
 def test_fc_closed_forms(name, inp, exp):
     dist, d_f, d_c, d_a, g, t_imp, s = inp
-    st = synth.Style(w_base=2.0, s=s, alpha_min=0.1, alpha_max=0.6, tf_lo=0.0, tf_hi=1.0,
-                     accent_beta=0.2, halo_scale=0.5, darken=0.25)
+    st = synth.plain(synth.Style(w_base=2.0, s=s, alpha_min=0.1, alpha_max=0.6, tf_lo=0.0, tf_hi=1.0,
+                                 accent_beta=0.2, halo_scale=0.5, darken=0.25))
     rgba, _ = oracle.fc_shade(st, dist, d_f, d_c, d_a, g, t_imp)
     assert np.allclose(rgba, exp, atol=1e-12), (name, rgba, exp)
 
@@ -167,7 +167,7 @@ def test_depth_cue_invariants():
         d_f, d_c, d_a = rng.uniform(0, 6, 3)
         d_c = max(d_c, d_f)
         d_a = min(d_a, d_f)
-        base, _ = oracle.fc_shade(synth.Style(), dist, d_f, d_c, d_a, g, t)
+        base, _ = oracle.fc_shade(synth.plain(synth.Style()), dist, d_f, d_c, d_a, g, t)
         cued, _ = oracle.fc_shade(synth.Style(desat=rng.uniform(0.1, 1.0)), dist, d_f, d_c, d_a, g, t)
         assert cued[3] == base[3]
         assert float(luma @ cued[:3]) == pytest.approx(float(luma @ base[:3]), abs=1e-14)
@@ -452,7 +452,7 @@ def test_opaque_limit_is_a_zbuffer():
     w = synth.grid4_ortho_256()
     mesh = w.mesh()
     m = oracle.Mesh(mesh.verts, mesh.cells, mesh.cell_scalar, mesh.edge_level)
-    st = synth.Style(alpha_min=1.0, alpha_max=1.0, s=1.0, **NO_EDGES)
+    st = synth.plain(synth.Style(alpha_min=1.0, alpha_max=1.0, s=1.0, **NO_EDGES))
     lens = synth.Lens(mode=synth.LENS_SPHERE, center=(50.0, 0.0, 0.0), radius=0.1)
     r = m.render(w.view(0), lens, st)
     off = r["offsets"]
@@ -468,7 +468,7 @@ def test_transparent_limit_is_background():
     mesh = w.mesh()
     m = oracle.Mesh(mesh.verts, mesh.cells, mesh.cell_scalar, mesh.edge_level)
     bg = (0.2, 0.3, 0.4)
-    st0 = synth.Style(alpha_min=0.0, alpha_max=0.0, bg=bg, **NO_EDGES)
+    st0 = synth.plain(synth.Style(alpha_min=0.0, alpha_max=0.0, bg=bg, **NO_EDGES))
     r0 = m.render(w.view(0), w.lens(0), st0, fragments=False)
     r1 = m.render(w.view(0), w.lens(0), w.style, fragments=False)
     assert (r0["counts"] == r1["counts"]).all()
@@ -483,7 +483,7 @@ def test_single_fragment_over_background():
     m = oracle.Mesh(v, c, np.array([0.8], np.float32), np.full((1, 12), 3, np.uint8))
     bg = (0.1, 0.5, 0.9)
     view = ortho_view(64, 64, 1.0, znear=1.0, zfar=5.2)  # back face at ed 5.5 is culled
-    st = synth.Style(bg=bg, lod=1)
+    st = synth.plain(synth.Style(bg=bg, lod=1))
     r = m.render(view, synth.Lens(mode=0, center=(20.0, 30.0, 0), radius=25.0), st)
     one = np.nonzero(r["counts"] == 1)[0]
     assert len(one) == 32 * 32
