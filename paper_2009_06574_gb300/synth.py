@@ -216,7 +216,16 @@ class Style:
     darken: float = 0.25
     g_min: float = 0.5
     g_max: float = 2.0
-    desat: float = 0.0
+    desat: float = 0.35            # depth cue strength (0: off)
+    sil_alpha: float = 1.0         # white silhouettes of the boundary surface (0: off)
+    sil_threshold: float = 32768.0 # depth jump of an interior silhouette (24-bit depth units)
+
+
+def plain(style: "Style") -> "Style":
+    """The style without the depth cue and the silhouettes (the plain method)."""
+    style.desat = 0.0
+    style.sil_alpha = 0.0
+    return style
 
 
 def orbit_view(frame: int, n_frames: int, width: int, height: int, radius: float = 1.2,
@@ -285,10 +294,10 @@ def grid4_ortho_256() -> Workload:
 
 def grid64_orbit_1080p() -> Workload:
     """64^3 warped+jittered grid (262,144 cells), 1920x1080, 60 deg FOV, 120-frame
-    orbit with a Lissajous sphere lens, face alpha 0.1-0.6."""
+    orbit with a Lissajous sphere lens, face alpha 0.1-0.6, the plain method."""
     return Workload("grid64_warp0.3_jitter0.1_orbit120_1920x1080", 64, 0.1, 0.3, 2, 1920, 1080,
-                    120, Style(w_base=2.0, lod=4, delta=0.08, alpha_min=0.1, alpha_max=0.6, tf_lo=0.0,
-                               tf_hi=0.15))
+                    120, plain(Style(w_base=2.0, lod=4, delta=0.08, alpha_min=0.1, alpha_max=0.6, tf_lo=0.0,
+                                     tf_hi=0.15)))
 
 
 def grid64_orbit_540p() -> Workload:
@@ -302,5 +311,5 @@ def grid64_orbit_540p() -> Workload:
 def grid128_orbit_4k() -> Workload:
     """128^3 warped grid (2.1M cells) at 3840x2160 (the cubic128-sized case)."""
     return Workload("grid128_warp0.3_jitter0.1_orbit500_3840x2160", 128, 0.1, 0.3, 4, 3840, 2160,
-                    500, Style(w_base=2.0, lod=5, delta=0.08, alpha_min=0.1, alpha_max=0.6, tf_lo=0.0,
-                               tf_hi=0.15))
+                    500, plain(Style(w_base=2.0, lod=5, delta=0.08, alpha_min=0.1, alpha_max=0.6, tf_lo=0.0,
+                                     tf_hi=0.15)))
