@@ -417,7 +417,7 @@ def run_ours(args, rank, world, local_rank):
     # clock record: learned capacity against count-then-fill (128^3, 3840x2160),
     # batched views against one by one, the serving loop (rank 0 at N = 1)
     secondaries = {}
-    if not args.no_secondary and rank == 0 and world == 1:
+    if not args.no_secondary and rank == 0 and world == 1 and args.workload == "grid64_orbit_1080p":
         legs = (("secondary_learned", lambda: run_learned(args, rank, world)),
                 ("secondary_batch", lambda: run_batch(args, rank, world, steps=10, warmup=3)),
                 ("secondary_serving", lambda: run_serving(args, rank, world)))

@@ -110,6 +110,8 @@ typedef struct hexfc_style {
     float darken;
     float g_min, g_max;
     float desat;
+    float sil_alpha;       /* opacity of the white silhouettes of the boundary surface, 0 = off */
+    float sil_threshold;   /* depth jump (24-bit window depth units) of an interior silhouette */
 } hexfc_style;
 
 /* Per-frame statistics of the last hexfc_render* call. */

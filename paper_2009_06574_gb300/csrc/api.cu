@@ -30,6 +30,7 @@ struct hexfc_ctx {
     int window = 2;             // HEXFC_OPT_COMPOSITE_WINDOW
     int predicted = 0;          // HEXFC_OPT_PREDICTED_CAPACITY
     int sub_x0 = 0, sub_y0 = 0, sub_w = 0, sub_h = 0;   // hexfc_set_subrect (sub_w 0: the whole frame)
+    OutWin last_win{};          // output window of the last frame, in its drawn rectangle
     uint64_t inject_bits = 0;   // HEXFC_OPT_DEBUG_ERROR_BITS: ORed into the error word after the next frame
     // A frame drawn with chosen capacities is verified by the next call on the
     // context (or hexfc_finish), once it has completed: what is needed to draw
@@ -174,7 +175,7 @@ void free_mesh(DevMesh* m)
     if (!m) return;
     dfree(m->verts); dfree(m->cells); dfree(m->cell_edges); dfree(m->cell_imp);
     dfree(m->vkey); dfree(m->ekey); dfree(m->vimp); dfree(m->eattr); dfree(m->elevel);
-    dfree(m->fverts); dfree(m->fedges); dfree(m->fstat);
+    dfree(m->fverts); dfree(m->fedges); dfree(m->fstat); dfree(m->fbound);
     delete m;
 }
 
@@ -183,7 +184,7 @@ void free_frame(FrameBufs& f)
     dfree(f.vproj); dfree(f.ved); dfree(f.fframe); dfree(f.tzsum);
     dfree(f.tile_cnt); dfree(f.tile_off); dfree(f.tile_cur); dfree(f.tile_order); dfree(f.tile_frag); dfree(f.tile_cap); dfree(f.cap_off); dfree(f.tile_zr); dfree(f.cap_x);
     dfree(f.bins); dfree(f.bins_tmp); dfree(f.masks); dfree(f.seg); dfree(f.cnt);
-    dfree(f.off);
+    dfree(f.off); dfree(f.zsil);
     dfree(f.part); dfree(f.part_max); dfree(f.long_q); dfree(f.fix_q); dfree(f.key); dfree(f.rgba); dfree(f.scal);
     dfree(f.cstat);
     if (f.h_scal) cudaFreeHost(f.h_scal);
@@ -296,9 +297,19 @@ ShadeParams make_shade(const hexfc_ctx* ctx)
     return sp;
 }
 
-// Size of the drawn rectangle (the whole frame unless hexfc_set_subrect chose one).
+// Size of the output image (the whole frame unless hexfc_set_subrect chose a
+// rectangle of it).
 inline int draw_w(const hexfc_ctx* ctx) { return ctx->sub_w ? ctx->sub_w : ctx->view.width; }
 inline int draw_h(const hexfc_ctx* ctx) { return ctx->sub_w ? ctx->sub_h : ctx->view.height; }
+
+// A sub-rectangle is drawn with an apron of one pixel (inside the frame): the
+// silhouettes of its border pixels read their neighbours' depths, as in the
+// whole frame. The camera's rectangle (cam.ox, cam.oy, cam.W, cam.H) is the
+// one drawn; the window selects the output pixels in it.
+OutWin output_window(const hexfc_ctx* ctx)
+{
+    return OutWin{ctx->sub_x0 - ctx->cam.ox, ctx->sub_y0 - ctx->cam.oy, draw_w(ctx), draw_h(ctx)};
+}
 
 bool valid_view(const hexfc_view* v, CamParams& c, double& zref)
 {
@@ -319,6 +330,7 @@ bool valid_style(const hexfc_style* s)
 {
     if (!(s->w_base >= 0.f) || s->tf_hi == s->tf_lo || !(s->g_min >= 0.f) || !(s->g_min <= s->g_max)) return false;
     if (!(s->halo_scale >= 0.f)) return false;
+    if (!(s->sil_alpha >= 0.f && s->sil_alpha <= 1.f) || !(s->sil_threshold >= 0.f)) return false;
     return s->desat >= 0.f && s->desat <= 1.f;
 }
 
@@ -343,6 +355,9 @@ struct FrameJob {
     bool prev_counts = false;   // fb.tile_frag holds the previous frame's counts for this tile grid
     uint64_t budget = 0;
     float* out = nullptr;
+    OutWin win{};                  // output pixels of the drawn rectangle (the rest: the apron)
+    float sil_alpha = 0.f, sil_threshold = 0.f;   // silhouettes (off at alpha 0)
+    int frame_w = 0, frame_h = 0;  // the view's frame, which the drawn rectangle is a part of
     hexfc_ctx* timing = nullptr;   // stage events of the single-frame path
     uint32_t launches = 0;
     uint64_t n_bins = 0, total = 0;
@@ -409,8 +424,13 @@ FrameJob make_job(hexfc_ctx* ctx, FrameBufs* fb, DevMesh* m, float* out)
     j.sp = make_shade(ctx);
     j.lod = ctx->style.lod;
     j.delta = ctx->style.delta;
-    j.W = draw_w(ctx);
-    j.H = draw_h(ctx);
+    j.W = ctx->cam.W;   // the drawn rectangle (the frame, or a sub-rectangle and its apron)
+    j.H = ctx->cam.H;
+    j.win = output_window(ctx);
+    j.sil_alpha = ctx->style.sil_alpha;
+    j.sil_threshold = ctx->style.sil_threshold;
+    j.frame_w = ctx->view.width;
+    j.frame_h = ctx->view.height;
     j.tiles_x = (j.W + kTile - 1) / kTile;
     j.tiles_y = (j.H + kTile - 1) / kTile;
     j.n_tiles = (int64_t)j.tiles_x * j.tiles_y;
@@ -467,11 +487,13 @@ hexfc_status job_alloc(FrameJob& j)
     }
     if (!fb.cnt || fb.p_cap < j.n_pix + 1) {
         int64_t c1 = 0, c2 = 0, c3 = 0;
-        dfree(fb.off); dfree(fb.long_q); dfree(fb.fix_q);
+        dfree(fb.off); dfree(fb.long_q); dfree(fb.fix_q); dfree(fb.zsil);
         if ((st = ensure(&fb.cnt, &fb.p_cap, j.n_pix + 1)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.off, &c1, fb.p_cap)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.long_q, &c2, fb.p_cap)) != HEXFC_OK) return st;
         if ((st = ensure(&fb.fix_q, &c3, fb.p_cap)) != HEXFC_OK) return st;
+        int64_t c4 = 0;
+        if ((st = ensure(&fb.zsil, &c4, fb.p_cap)) != HEXFC_OK) return st;
     }
     const int64_t nparts = scan_partials_needed(std::max<int64_t>(j.n_pix, j.n_tiles)) + 1;
     if (!fb.part || fb.part_cap < 2 * nparts) {
@@ -563,7 +585,7 @@ uint64_t frame_bytes(const FrameBufs& f, int64_t frags)
     b += (uint64_t)f.t_cap * (9 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t));
     b += (uint64_t)f.bin_cap * 2 * sizeof(uint32_t) + (uint64_t)f.mask_cap * sizeof(uint32_t) +
          (uint64_t)f.seg_cap * sizeof(uint64_t);
-    b += (uint64_t)f.p_cap * (3 * sizeof(uint32_t) + sizeof(uint64_t));
+    b += (uint64_t)f.p_cap * (4 * sizeof(uint32_t) + sizeof(uint64_t));
     b += (uint64_t)f.part_cap * (sizeof(uint64_t) + sizeof(uint32_t));
     b += (uint64_t)frags * (sizeof(uint64_t) + sizeof(float4));
     return b;
@@ -612,13 +634,33 @@ hexfc_status job_read2(FrameJob& j, cudaStream_t s)
     return HEXFC_OK;
 }
 
+// With silhouettes: the depth image of the boundary surface starts empty.
+hexfc_status job_sil_clear(const FrameJob& j, cudaStream_t s)
+{
+    if (j.sil_alpha > 0.f) CK(cudaMemsetAsync(j.fb->zsil, 0xFF, sizeof(uint32_t) * (size_t)j.n_pix, s));
+    return HEXFC_OK;
+}
+
+// After the composite: the white silhouettes over the output window.
+hexfc_status job_silhouette(FrameJob& j, float* out, cudaStream_t s)
+{
+    if (j.sil_alpha <= 0.f) return HEXFC_OK;
+    CK(launch_silhouette(*j.fb, j.tiles_x, j.cam.ox, j.cam.oy, j.frame_w, j.frame_h, j.sil_alpha, j.sil_threshold,
+                         out, j.win, s));
+    j.launches += 2;
+    return HEXFC_OK;
+}
+
 hexfc_status job_phase3(FrameJob& j, cudaStream_t s)
 {
     FrameBufs& fb = *j.fb;
     job_mark(j, 8, s);
-    CK(launch_fill(*j.m, fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, false, s));
+    hexfc_status st;
+    if ((st = job_sil_clear(j, s)) != HEXFC_OK) return st;
+    CK(launch_fill(*j.m, fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, false, j.sil_alpha > 0.f, s));
     job_mark(j, 9, s);
-    CK(launch_composite(fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, j.out, j.n_long, j.window, s));
+    CK(launch_composite(fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, j.out, j.n_long, j.window, j.win, s));
+    if ((st = job_silhouette(j, j.out, s)) != HEXFC_OK) return st;
     job_mark(j, 10, s);
     j.launches += 3 + (j.n_long > 0 ? 1 : 0);
     j.fs.kernel_launches = j.launches;
@@ -687,6 +729,7 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
     if (stats) stats->kernel_launches = j.launches;
     ctx->have_frame = true;
     ctx->last_W = j.W;
+    ctx->last_win = j.win;
     ctx->last_H = j.H;
     ctx->last_tiles_x = j.tiles_x;
     ctx->last_tiles_y = j.tiles_y;
@@ -787,9 +830,11 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     job_mark(j, 6, s);
     job_mark(j, 7, s);
     job_mark(j, 8, s);
-    CK(launch_fill(*m, fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, true, s));
+    if ((st = job_sil_clear(j, s)) != HEXFC_OK) return st;
+    CK(launch_fill(*m, fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, true, j.sil_alpha > 0.f, s));
     job_mark(j, 9, s);
-    CK(launch_composite(fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, out, kLongListsUnknown, j.window, s));
+    CK(launch_composite(fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, out, kLongListsUnknown, j.window, j.win, s));
+    if ((st = job_silhouette(j, out, s)) != HEXFC_OK) return st;
     job_mark(j, 10, s);
     j.launches += 4 + 1 + 3 + 1 + 1 + 3;
     // the frame's scalars and count statistics for its verification; no wait here
@@ -823,6 +868,7 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     if (stats) *stats = fs;
     ctx->have_frame = true;
     ctx->last_W = j.W;
+    ctx->last_win = j.win;
     ctx->last_H = j.H;
     ctx->last_tiles_x = j.tiles_x;
     ctx->last_tiles_y = j.tiles_y;
@@ -1038,7 +1084,9 @@ void hexfc_style_default(hexfc_style* s)
     s->darken = 0.25f;
     s->g_min = 0.5f;
     s->g_max = 2.f;
-    s->desat = 0.f;
+    s->desat = 0.35f;          // the depth cue and the silhouettes of the paper's final look
+    s->sil_alpha = 1.f;
+    s->sil_threshold = 32768.f;
 }
 
 hexfc_status hexfc_create(hexfc_ctx** out, int device, uint64_t frag_budget_bytes)
@@ -1134,6 +1182,7 @@ hexfc_status hexfc_upload_mesh(hexfc_ctx* ctx, const float* verts, int64_t n_ver
     A(dalloc(&m->fverts, (size_t)t.n_faces));
     A(dalloc(&m->fedges, (size_t)t.n_faces));
     A(dalloc(&m->fstat, (size_t)t.n_faces));
+    A(dalloc(&m->fbound, (size_t)t.n_faces));
     if (st != HEXFC_OK) {
         free_mesh(m);
         return st;
@@ -1148,6 +1197,7 @@ hexfc_status hexfc_upload_mesh(hexfc_ctx* ctx, const float* verts, int64_t n_ver
     H2D(m->elevel, t.elevel.data(), t.elevel.size());
     H2D(m->fverts, t.fverts.data(), sizeof(int32_t) * t.fverts.size());
     H2D(m->fedges, t.fedges.data(), sizeof(int32_t) * t.fedges.size());
+    H2D(m->fbound, t.fbound.data(), t.fbound.size());
     if (cell_scalar) H2D(m->cell_imp, cell_scalar, sizeof(float) * (size_t)n_cells);
     if (e == cudaSuccess && !cell_scalar) e = launch_cell_quality(*m, HEXFC_METRIC_IMPORTANCE, m->cell_imp, 0);
     if (e == cudaSuccess) e = launch_importance(*m, 0);
@@ -1222,6 +1272,11 @@ hexfc_status hexfc_render_batch(hexfc_ctx* ctx, int32_t n, const hexfc_batch_ite
         j.window = ctx->window;
         j.budget = ctx->budget;
         j.out = it.out_rgba;
+        j.win = OutWin{0, 0, j.W, j.H};   // whole frames
+        j.sil_alpha = it.style.sil_alpha;
+        j.sil_threshold = it.style.sil_threshold;
+        j.frame_w = j.W;
+        j.frame_h = j.H;
         if ((st = job_alloc(j)) != HEXFC_OK) return st;
         live.push_back(i);
     }
@@ -1456,13 +1511,21 @@ hexfc_status hexfc_set_subrect(hexfc_ctx* ctx, int32_t x0, int32_t y0, int32_t w
         ctx->sub_w = w;
         ctx->sub_h = h;
     }
-    // the face stage clamps triangle boxes to the drawn rectangle (its tiles),
-    // like every later stage: W, H are the rectangle's, the projection keeps the
-    // frame's centre
-    ctx->cam.ox = ctx->sub_x0;
-    ctx->cam.oy = ctx->sub_y0;
-    ctx->cam.W = draw_w(ctx);
-    ctx->cam.H = draw_h(ctx);
+    // drawn: the rectangle and an apron of one pixel inside the frame. The face
+    // stage clamps triangle boxes to it (its tiles), like every later stage:
+    // W, H are its own, the projection keeps the frame's centre
+    if (ctx->sub_w == 0) {
+        ctx->cam.ox = ctx->cam.oy = 0;
+        ctx->cam.W = v.width;
+        ctx->cam.H = v.height;
+    } else {
+        const int x0a = std::max(0, x0 - 1), y0a = std::max(0, y0 - 1);
+        const int x1a = std::min(v.width, x0 + w + 1), y1a = std::min(v.height, y0 + h + 1);
+        ctx->cam.ox = x0a;
+        ctx->cam.oy = y0a;
+        ctx->cam.W = x1a - x0a;
+        ctx->cam.H = y1a - y0a;
+    }
     return HEXFC_OK;
 }
 
@@ -1551,9 +1614,17 @@ hexfc_status hexfc_debug_pixels(hexfc_ctx* ctx, const int32_t* px, const int32_t
         const hexfc_status st0 = finish_pending(ctx);
         if (st0 != HEXFC_OK) return st0;
     }
+    const OutWin win = ctx->last_win;   // pixels of the output image, placed in the drawn rectangle
     for (int64_t i = 0; i < n; ++i)
-        if (px[i] < 0 || py[i] < 0 || px[i] >= ctx->last_W || py[i] >= ctx->last_H) return HEXFC_ERR_ARG;
+        if (px[i] < 0 || py[i] < 0 || px[i] >= win.w || py[i] >= win.h) return HEXFC_ERR_ARG;
     if (n == 0) return HEXFC_OK;
+    std::vector<int32_t> qx((size_t)n), qy((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        qx[(size_t)i] = px[i] + win.x0;
+        qy[(size_t)i] = py[i] + win.y0;
+    }
+    px = qx.data();
+    py = qy.data();
     DeviceGuard g(ctx->device);
     FrameBufs& fb = ctx->fb;
     int32_t *d_px = nullptr, *d_py = nullptr;
@@ -1757,7 +1828,9 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
 {
     unsigned char* scratch = static_cast<unsigned char*>(noalloc_scratch());
     if (!scratch) return HEXFC_ERR_CUDA;
-    const int W = draw_w(ctx), H = draw_h(ctx);
+    const int W = ctx->cam.W, H = ctx->cam.H;   // the drawn rectangle (with its apron)
+    const OutWin win = output_window(ctx);
+    const bool sil = ctx->style.sil_alpha > 0.f;
     const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
     const int64_t n_tiles = (int64_t)tiles_x * tiles_y;
     const int64_t n_pix = n_tiles * kTilePix;
@@ -1781,10 +1854,11 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fb.off = a.take<uint64_t>((size_t)n_pix + 1);
     fb.long_q = a.take<uint32_t>((size_t)n_pix + 1);
     fb.fix_q = a.take<uint32_t>((size_t)n_pix + 1);
+    fb.zsil = sil ? a.take<uint32_t>((size_t)n_pix) : nullptr;
     fb.part = a.take<uint64_t>(2 * (size_t)nparts);
     fb.part_max = a.take<uint32_t>(2 * (size_t)nparts);
     if (!fb.vproj || !fb.ved || !fb.fframe || !fb.tzsum || !fb.tile_cnt ||
-        !fb.tile_off || !fb.tile_cur || !fb.tile_order || !fb.tile_frag || !fb.tile_zr || !fb.cnt || !fb.off || !fb.long_q || !fb.fix_q || !fb.part || !fb.part_max ||
+        !fb.tile_off || !fb.tile_cur || !fb.tile_order || !fb.tile_frag || !fb.tile_zr || !fb.cnt || !fb.off || !fb.long_q || !fb.fix_q || (sil && !fb.zsil) || !fb.part || !fb.part_max ||
         !fb.scal)
         return HEXFC_ERR_OVERFLOW;
     // the array keeps the previous call's contents: clear what must start at zero
@@ -1810,8 +1884,8 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fb.seg = a.take<uint64_t>((size_t)(n_bins / kChunk) * (kTilePix / 32));
     hexfc_frame_stats fs{};
     fs.bin_entries = n_bins;
-    fs.width = (uint32_t)W;
-    fs.height = (uint32_t)H;
+    fs.width = (uint32_t)win.w;
+    fs.height = (uint32_t)win.h;
     if (!fb.bins || !fb.bins_tmp || !fb.masks || !fb.seg) {
         if (stats) *stats = fs;
         return HEXFC_ERR_OVERFLOW;
@@ -1835,7 +1909,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     fs.fragments = total;
     fs.max_list = (uint32_t)h[1];
     fs.long_lists = n_long;
-    fs.kernel_launches = 15 + (n_long > 0 ? 1u : 0u);
+    fs.kernel_launches = 15 + (n_long > 0 ? 1u : 0u) + (sil ? 2u : 0u);
     if (stats) *stats = fs;
     if (fs.max_list > HEXFC_MAX_LIST) return HEXFC_ERR_OVERFLOW;
     fb.key = a.take<uint64_t>((size_t)total);
@@ -1843,8 +1917,12 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     if (!fb.key || !fb.rgba) return HEXFC_ERR_OVERFLOW;
     fb.frag_cap = (int64_t)total;
     ShadeParams sp = make_shade(ctx);
-    CK(launch_fill(*m, fb, sp, tiles_x, tiles_y, W, H, false, s));
-    CK(launch_composite(fb, sp, tiles_x, tiles_y, W, H, out, n_long, ctx->window, s));
+    if (sil) CK(cudaMemsetAsync(fb.zsil, 0xFF, sizeof(uint32_t) * (size_t)n_pix, s));
+    CK(launch_fill(*m, fb, sp, tiles_x, tiles_y, W, H, false, sil, s));
+    CK(launch_composite(fb, sp, tiles_x, tiles_y, W, H, out, n_long, ctx->window, win, s));
+    if (sil)
+        CK(launch_silhouette(fb, tiles_x, ctx->cam.ox, ctx->cam.oy, ctx->view.width, ctx->view.height,
+                             ctx->style.sil_alpha, ctx->style.sil_threshold, out, win, s));
     return inject_error_bits(ctx, fb.scal, s);
 }
 

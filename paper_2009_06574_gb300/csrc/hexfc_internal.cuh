@@ -51,7 +51,7 @@ struct __align__(64) FaceFrame {
     int4 X, Y;            // corner window position, 16.8 fixed point
     uint4 Z;              // bits 0-23: corner window depth (z24); Z.x bits 24-31: edge flags
                           // (bits 0-3 visible in focus, 4-7 visible in context); Z.y bits 24-25:
-                          // triangle 0 / 1 drawn
+                          // triangle 0 / 1 drawn, bit 26: a boundary face (of one cell)
     float4 ed;            // corner eye depth
 };
 struct __align__(64) FaceStatic {
@@ -74,6 +74,8 @@ constexpr int kScal = 24;
 constexpr int kStatCopies = 32;
 __host__ __device__ inline uint32_t face_edge_flags(const uint4& z) { return z.x >> 24; }
 __host__ __device__ inline uint32_t face_tris(const uint4& z) { return (z.y >> 24) & 3u; }
+__host__ __device__ inline uint32_t face_boundary(const uint4& z) { return (z.y >> 26) & 1u; }
+constexpr uint32_t kNoDepth = 0xFFFFFFFFu;   // no boundary fragment at a pixel
 
 // Resident mesh (device pointers), see hexfc_upload_mesh.
 struct DevMesh {
@@ -89,6 +91,7 @@ struct DevMesh {
     uint8_t* elevel = nullptr;     // [E]
     int4* fverts = nullptr;        // [F] canonical corners
     int4* fedges = nullptr;        // [F] unique edge id of local edge k = (c_k, c_k+1)
+    uint8_t* fbound = nullptr;     // [F] 1: a boundary face (one cell)
     FaceStatic* fstat = nullptr;   // [F] static face records
 };
 
@@ -153,6 +156,7 @@ struct FrameBufs {
     int64_t part_cap = 0;
     uint32_t* long_q = nullptr;     // queue of pixels with long lists
     uint32_t* fix_q = nullptr;      // queue of pixels whose list arrived out of order
+    uint32_t* zsil = nullptr;       // [P] depth of the nearest boundary fragment (silhouettes), kNoDepth if none
     // fragments
     uint64_t* key = nullptr;
     float4* rgba = nullptr;
@@ -193,10 +197,22 @@ cudaError_t launch_cap_forward(const CapNet& net, FrameBufs& fb, int64_t n_tiles
 cudaError_t launch_cap_grad(CapNet& net, const float* X, const uint32_t* counts, int64_t n, cudaStream_t s);
 cudaError_t launch_cap_adam(CapNet& net, float lr, cudaStream_t s);
 cudaError_t launch_cap_to_half(CapNet& net, cudaStream_t s);
+// sil: record each pixel's nearest boundary-fragment depth into fb.zsil.
 cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W,
-                        int H, bool regions, cudaStream_t s);
+                        int H, bool regions, bool sil, cudaStream_t s);
+// The pixels of the drawn rectangle that go to the output image: [x0, x0 + w) x
+// [y0, y0 + h), written at out[(y - y0) w + (x - x0)] (the rest is an apron whose
+// depths the silhouettes read).
+struct OutWin {
+    int x0, y0, w, h;
+};
 cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W, int H,
-                             float* out, uint32_t n_long, int window, cudaStream_t s);
+                             float* out, uint32_t n_long, int window, OutWin win, cudaStream_t s);
+// White silhouettes over the output (Section "Blending Focus and Context"):
+// from the boundary surface's depths fb.zsil of the drawn rectangle, which sits
+// at (fx0, fy0) of a frame_w x frame_h frame.
+cudaError_t launch_silhouette(FrameBufs& fb, int tiles_x, int fx0, int fy0, int frame_w, int frame_h, float alpha,
+                              float threshold, float* out, OutWin win, cudaStream_t s);
 cudaError_t launch_debug_gather(FrameBufs& fb, const int32_t* d_px, const int32_t* d_py, int64_t n,
                                 const uint64_t* d_dst_off, int tiles_x, int W, int H,
                                 uint64_t* d_keys, float4* d_rgba, uint32_t* d_counts,

@@ -256,6 +256,15 @@ __device__ __forceinline__ void blend_checked(CT& c, uint64_t& last, bool& ok, c
     c = ct_over(c, CT{e.c.x, e.c.y, e.c.z, 1.f - e.c.w});
 }
 
+// Output index of drawn pixel (x, y), if it belongs to the output window.
+__device__ __forceinline__ bool out_index(const OutWin& w, int x, int y, int64_t& o)
+{
+    const int u = x - w.x0, v = y - w.y0;
+    if (u < 0 || v < 0 || u >= w.w || v >= w.h) return false;
+    o = (int64_t)v * w.w + u;
+    return true;
+}
+
 template <int KW>
 __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ cnt,
                                                    const uint64_t* __restrict__ seg,
@@ -264,7 +273,7 @@ __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ 
                                                    const uint64_t* __restrict__ key,
                                                    const float4* __restrict__ rgba, uint64_t frag_cap, int tiles_x,
                                                    int W, int H, float bg0, float bg1, float bg2,
-                                                   float4* __restrict__ out,
+                                                   float4* __restrict__ out, OutWin win,
                                                    uint32_t* __restrict__ long_q,
                                                    unsigned long long* __restrict__ long_cursor,
                                                    uint32_t* __restrict__ fix_q,
@@ -357,7 +366,9 @@ __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ 
     int x, y;
     tile_pixel(q, tiles_x, x, y);
     if (x >= W || y >= H) return;
-    if (ok) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
+    int64_t o;
+    if (!out_index(win, x, y, o)) return;   // an apron pixel: only its depth is used
+    if (ok) out[o] = finish(c, bg0, bg1, bg2);
     else if (n > (uint32_t)kWarpList) long_q[atomicAdd(long_cursor, 1ull)] = (uint32_t)q;
     else fix_q[atomicAdd(fix_cursor, 1ull)] = (uint32_t)q;
 }
@@ -370,8 +381,9 @@ __global__ void __launch_bounds__(256) k_composite_fix(const uint32_t* __restric
                                                        const uint32_t* __restrict__ masks,
                                                        const uint64_t* __restrict__ key,
                                                        const float4* __restrict__ rgba, uint64_t frag_cap,
-                                                       int tiles_x, int W, float bg0, float bg1, float bg2,
-                                                       float4* __restrict__ out, const uint32_t* __restrict__ fix_q,
+                                                       int tiles_x, float bg0, float bg1, float bg2,
+                                                       float4* __restrict__ out, OutWin win,
+                                                       const uint32_t* __restrict__ fix_q,
                                                        const unsigned long long* __restrict__ fix_cursor)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -390,7 +402,8 @@ __global__ void __launch_bounds__(256) k_composite_fix(const uint32_t* __restric
         int x, y;
         tile_pixel(q, tiles_x, x, y);
         CT c = warp_resolve(b.key, b.rgba, n, lane, nullptr, nullptr);
-        if (lane == 0) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
+        int64_t o;
+        if (lane == 0 && out_index(win, x, y, o)) out[o] = finish(c, bg0, bg1, bg2);
         __syncwarp();   // the staging is reused by the warp's next list
     }
 }
@@ -471,8 +484,8 @@ __global__ void __launch_bounds__(1024) k_composite_long(const uint32_t* __restr
                                                          const float4* __restrict__ rgba, uint64_t frag_cap,
                                                          const uint32_t* __restrict__ long_q,
                                                          const unsigned long long* __restrict__ n_long,
-                                                         int tiles_x, int W, float bg0, float bg1, float bg2,
-                                                         float4* __restrict__ out)
+                                                         int tiles_x, float bg0, float bg1, float bg2,
+                                                         float4* __restrict__ out, OutWin win)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* s_k = reinterpret_cast<uint64_t*>(smem);
@@ -486,9 +499,68 @@ __global__ void __launch_bounds__(1024) k_composite_long(const uint32_t* __restr
         int x, y;
         tile_pixel(q, tiles_x, x, y);
         CT c = block_composite(tile_off, masks, seg, frag_cap, key, rgba, q, n, s_k, s_v, s_e, nullptr, nullptr);
-        if (threadIdx.x == 0) out[(int64_t)y * W + x] = finish(c, bg0, bg1, bg2);
+        int64_t o;
+        if (threadIdx.x == 0 && out_index(win, x, y, o)) out[o] = finish(c, bg0, bg1, bg2);
         __syncthreads();   // the shared arrays are reused by the next list
     }
+}
+
+// ---------------------------------------------------------------- silhouettes
+
+// White silhouettes of the boundary surface (Section "Blending Focus and
+// Context": the boundary surface is rendered and fragments along sharp edges
+// of its depth buffer are emphasised). zsil holds, per drawn pixel (tile-major),
+// the 24-bit depth of its nearest boundary-face fragment (kNoDepth: none). An
+// output pixel p with a depth is a silhouette pixel if a 4-neighbour inside the
+// frame has none (exterior), or if for a neighbour q and the opposite q' (both
+// with depths) D(q) - D(p) > T and |D(q) - 2 D(p) + D(q')| > T (interior: the
+// near side of a depth jump; a plane, however steep, has no second
+// difference); its colour and opacity move towards white by alpha. The drawn
+// rectangle starts at frame pixel (fx0, fy0) and holds every in-frame
+// neighbour of the output window (an apron around a sub-rectangle).
+__device__ __forceinline__ uint32_t zsil_at(const uint32_t* __restrict__ zsil, int tiles_x, int x, int y)
+{
+    const int64_t t = (int64_t)(y / kTile) * tiles_x + x / kTile;
+    return zsil[t * kTilePix + (y % kTile) * kTile + (x % kTile)];
+}
+
+__global__ void __launch_bounds__(256) k_silhouette(const uint32_t* __restrict__ zsil, int tiles_x, int fx0, int fy0,
+                                                    int frame_w, int frame_h, float alpha, int64_t T,
+                                                    float4* __restrict__ out, OutWin win)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)win.w * win.h) return;
+    const int x = win.x0 + (int)(i % win.w), y = win.y0 + (int)(i / win.w);
+    const uint32_t zp = zsil_at(zsil, tiles_x, x, y);
+    if (zp == kNoDepth) return;
+    const int dx[4] = {1, -1, 0, 0}, dy[4] = {0, 0, 1, -1};   // k ^ 1: the opposite side
+    int64_t zq[4];
+    bool has[4];
+    bool sil = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int qx = x + dx[k], qy = y + dy[k];
+        const bool inside = qx + fx0 >= 0 && qy + fy0 >= 0 && qx + fx0 < frame_w && qy + fy0 < frame_h;
+        const uint32_t z = inside ? zsil_at(zsil, tiles_x, qx, qy) : kNoDepth;
+        has[k] = z != kNoDepth;
+        zq[k] = (int64_t)z;
+        sil = sil || (inside && !has[k]);   // exterior: the surface ends here
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int o = k ^ 1;
+        if (has[k] && has[o]) {
+            const int64_t d1 = zq[k] - (int64_t)zp, d2 = zq[k] - 2 * (int64_t)zp + zq[o];
+            sil = sil || (d1 > T && (d2 > T || -d2 > T));   // interior: the near side of a jump
+        }
+    }
+    if (!sil) return;
+    float4 c = out[i];
+    c.x = fmaf(alpha, 1.f - c.x, c.x);
+    c.y = fmaf(alpha, 1.f - c.y, c.y);
+    c.z = fmaf(alpha, 1.f - c.z, c.z);
+    c.w = fmaf(alpha, 1.f - c.w, c.w);
+    out[i] = c;
 }
 
 // ---------------------------------------------------------------- debug gather
@@ -563,7 +635,7 @@ constexpr unsigned kLongGridMax = 2 * 152;  // persistent: blocks stride over th
 }  // namespace
 
 cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W, int H, float* out,
-                             uint32_t n_long, int window, cudaStream_t s)
+                             uint32_t n_long, int window, OutWin win, cudaStream_t s)
 {
     float4* o4 = reinterpret_cast<float4*>(out);
     const int64_t n_pix = (int64_t)tiles_x * tiles_y * kTilePix;
@@ -572,21 +644,31 @@ cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, 
     const unsigned grid = (unsigned)(n_pix / kTilePix);
     auto resolve = [&](auto kernel) {
         kernel<<<grid, 256, 0, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba, (uint64_t)fb.frag_cap,
-                                    tiles_x, W, H, sp.bg[0], sp.bg[1], sp.bg[2], o4, fb.long_q, long_cursor, fb.fix_q,
-                                    fix_cursor);
+                                    tiles_x, W, H, sp.bg[0], sp.bg[1], sp.bg[2], o4, win, fb.long_q, long_cursor,
+                                    fb.fix_q, fix_cursor);
     };
     if (window == 8) resolve(k_composite<8>);
     else if (window == 4) resolve(k_composite<4>);
     else resolve(k_composite<2>);
     k_composite_fix<<<kFixBlocks, 256, kFixSmem, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
-                                                      (uint64_t)fb.frag_cap, tiles_x, W, sp.bg[0], sp.bg[1],
-                                                      sp.bg[2], o4, fb.fix_q, fix_cursor);
+                                                      (uint64_t)fb.frag_cap, tiles_x, sp.bg[0], sp.bg[1],
+                                                      sp.bg[2], o4, win, fb.fix_q, fix_cursor);
     if (n_long > 0) {   // n_long: the number of long lists if known, else an upper bound on the useful grid
         const unsigned grid = n_long < kLongGridMax ? n_long : kLongGridMax;
         k_composite_long<<<grid, 1024, kLongSmem, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
-                                                       (uint64_t)fb.frag_cap, fb.long_q, long_cursor, tiles_x, W,
-                                                       sp.bg[0], sp.bg[1], sp.bg[2], o4);
+                                                       (uint64_t)fb.frag_cap, fb.long_q, long_cursor, tiles_x,
+                                                       sp.bg[0], sp.bg[1], sp.bg[2], o4, win);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_silhouette(FrameBufs& fb, int tiles_x, int fx0, int fy0, int frame_w, int frame_h, float alpha,
+                              float threshold, float* out, OutWin win, cudaStream_t s)
+{
+    const int64_t n = (int64_t)win.w * win.h;
+    if (n == 0) return cudaSuccess;
+    k_silhouette<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(fb.zsil, tiles_x, fx0, fy0, frame_w, frame_h, alpha,
+                                                             (int64_t)threshold, reinterpret_cast<float4*>(out), win);
     return cudaGetLastError();
 }
 

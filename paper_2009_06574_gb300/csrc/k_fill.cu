@@ -94,7 +94,7 @@ __device__ __forceinline__ void stage_shade(const RawFace& r, uint32_t f2t, cons
     R.ap = make_float4(a[1] - a[0], a[2] - a[0], P[0][0], P[0][1]);
     R.pp = make_float4(P[0][2], P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]);
     R.pq = make_float4(P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2], 0.f);
-    R.zm = make_uint4(z[0], z[1], z[2], face_edge_flags(r.Z));
+    R.zm = make_uint4(z[0], z[1], z[2], face_edge_flags(r.Z) | (face_boundary(r.Z) << 8));
     // depth differences below 2^24 in magnitude: exact in float
     R.wd = make_uint4((uint32_t)c.e0[1][j], (uint32_t)c.e0[2][j], __float_as_uint((float)(int32_t)(z[1] - z[0])),
                       __float_as_uint((float)(int32_t)(z[2] - z[0])));
@@ -127,6 +127,7 @@ __host__ __device__ constexpr size_t fill_smem_bytes()
 // The fill pipeline of one tile block: s_base / s_len hold the offsets and
 // lengths of the tile's 256 lists, the ring barriers are initialised, and
 // `smem` is the dynamic shared memory (fill_smem_bytes()).
+template <bool kSil>
 __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s_base, const uint32_t* s_len,
                                           uint64_t* s_full, uint64_t* s_empty,
                                           const uint32_t* __restrict__ bins, const uint32_t* __restrict__ masks,
@@ -134,7 +135,8 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
                                           const FaceStatic* __restrict__ fstat, uint64_t beg, uint32_t n_chunks,
                                           int px0, int py0, int W, int H, const ShadeParams& sp,
                                           uint64_t* __restrict__ key, float4* __restrict__ rgba,
-                                          uint64_t* __restrict__ seg, unsigned long long* __restrict__ err)
+                                          uint64_t* __restrict__ seg, unsigned long long* __restrict__ err,
+                                          uint32_t* __restrict__ zsil_t)
 {
     FillSlot* s_ring = reinterpret_cast<FillSlot*>(smem);                                    // [kRing]
     RawFace* s_raw = reinterpret_cast<RawFace*>(smem + kRawOff);                            // [2][kChunk]
@@ -228,6 +230,10 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
         const float4 col = shade_fragment(R, zm.w, lam1, lam2, px0 + lx, py0 + ly, sp);
         key[o] = ((uint64_t)z << 32) | (uint64_t)hd.y;
         rgba[o] = col;
+        // the boundary surface's depth image (silhouettes): nearest boundary fragment
+        if constexpr (kSil) {
+            if (zm.w & 0x100u) atomicMin(zsil_t + pl, z);
+        }
     };
     // masks of the next two chunks are in flight while this one is shaded
     const uint32_t* mp = masks + (beg / kChunk) * kTilePix + p;             // this pixel's mask of chunk 0
@@ -312,6 +318,7 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
 // per SM leave 72 registers a thread: a sample's inputs arrive as eleven
 // 16-byte vectors, more values live at once than at four blocks (56
 // registers), where they spill.
+template <bool kSil>
 __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __restrict__ tile_off,
                                                           const uint32_t* __restrict__ bins,
                                                           uint32_t* __restrict__ masks,
@@ -325,7 +332,8 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __rest
                                                           unsigned long long* __restrict__ err,
                                                           const uint64_t* __restrict__ cap_off,
                                                           const uint32_t* __restrict__ tile_frag, int n_tiles,
-                                                          uint64_t frag_cap, unsigned long long* __restrict__ scal)
+                                                          uint64_t frag_cap, unsigned long long* __restrict__ scal,
+                                                          uint32_t* __restrict__ zsil)
 {
     extern __shared__ __align__(128) unsigned char fill_smem[];
     __shared__ uint64_t s_base[kTilePix];
@@ -393,8 +401,8 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __rest
             __syncwarp();
         }
     }
-    fill_tile(fill_smem, s_base, s_len, s_full, s_empty, bins, masks, fframe, fstat, beg, n_chunks, px0, py0,
-              W, H, sp, key, rgba, seg, err);
+    fill_tile<kSil>(fill_smem, s_base, s_len, s_full, s_empty, bins, masks, fframe, fstat, beg, n_chunks, px0, py0,
+                    W, H, sp, key, rgba, seg, err, kSil ? zsil + (int64_t)tile * kTilePix : nullptr);
 }
 
 // Capacities from the previous frame's exact tile counts: prev * (1 + margin)
@@ -412,7 +420,11 @@ __global__ void k_capacity_from_previous(const uint32_t* __restrict__ prev, int6
 
 cudaError_t prepare_fill_kernels()
 {
-    return cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem_bytes());
+    cudaError_t e = cudaFuncSetAttribute(k_fill<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fill_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem_bytes());
+    return e;
 }
 
 cudaError_t launch_capacity_from_previous(FrameBufs& fb, int64_t n_tiles, float margin, uint32_t pad, uint32_t uniform,
@@ -424,13 +436,18 @@ cudaError_t launch_capacity_from_previous(FrameBufs& fb, int64_t n_tiles, float 
 }
 
 cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W,
-                        int H, bool regions, cudaStream_t s)
+                        int H, bool regions, bool sil, cudaStream_t s)
 {
     const size_t smem = fill_smem_bytes();
-    k_fill<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, smem, s>>>(
-        fb.tile_off, fb.bins, fb.masks, fb.fframe, m.fstat, fb.tile_order, tiles_x, W, H, sp, fb.off, fb.cnt, fb.key,
-        fb.rgba, fb.seg, reinterpret_cast<unsigned long long*>(fb.scal + 5), regions ? fb.cap_off : nullptr,
-        fb.tile_frag, tiles_x * tiles_y, (uint64_t)fb.frag_cap, reinterpret_cast<unsigned long long*>(fb.scal));
+    auto go = [&](auto kernel) {   // with silhouettes, the variant that records the boundary depths
+        kernel<<<(unsigned)(tiles_x * tiles_y), kPipeThreads, smem, s>>>(
+            fb.tile_off, fb.bins, fb.masks, fb.fframe, m.fstat, fb.tile_order, tiles_x, W, H, sp, fb.off, fb.cnt,
+            fb.key, fb.rgba, fb.seg, reinterpret_cast<unsigned long long*>(fb.scal + 5),
+            regions ? fb.cap_off : nullptr, fb.tile_frag, tiles_x * tiles_y, (uint64_t)fb.frag_cap,
+            reinterpret_cast<unsigned long long*>(fb.scal), sil ? fb.zsil : nullptr);
+    };
+    if (sil) go(k_fill<true>);
+    else go(k_fill<false>);
     return cudaGetLastError();
 }
 

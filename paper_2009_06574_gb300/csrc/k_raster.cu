@@ -86,6 +86,7 @@ __device__ __forceinline__ void tile_range(const TriGeom& t, int& tx0, int& ty0,
 }
 
 __global__ void k_face_setup(const int4* __restrict__ fverts, const int4* __restrict__ fedges,
+                             const uint8_t* __restrict__ fbound,
                              const uint8_t* __restrict__ elevel, const float* __restrict__ eattr,
                              const int4* __restrict__ vproj, const float* __restrict__ ved, int64_t n_faces,
                              int lod, float delta, int W, int H, int tiles_x, FaceFrame* __restrict__ fframe,
@@ -131,7 +132,9 @@ __global__ void k_face_setup(const int4* __restrict__ fverts, const int4* __rest
     FaceFrame& r = fframe[f];
     r.X = make_int4(X[0], X[1], X[2], X[3]);
     r.Y = make_int4(Y[0], Y[1], Y[2], Y[3]);
-    r.Z = make_uint4((Z[0] & kZ24) | (flags << 24), (Z[1] & kZ24) | (tris << 24), Z[2] & kZ24, Z[3] & kZ24);
+    const uint32_t bnd = fbound[f] ? 1u : 0u;
+    r.Z = make_uint4((Z[0] & kZ24) | (flags << 24), (Z[1] & kZ24) | (tris << 24) | (bnd << 26), Z[2] & kZ24,
+                     Z[3] & kZ24);
     r.ed = make_float4(E[0], E[1], E[2], E[3]);
     const uint32_t z0 = Z[0] & kZ24, z1 = Z[1] & kZ24, z2 = Z[2] & kZ24, z3 = Z[3] & kZ24;
     reinterpret_cast<uint2*>(tzsum)[f] = make_uint2(z0 + z1 + z2, z0 + z2 + z3);   // < 3 * 2^24
@@ -465,7 +468,7 @@ cudaError_t launch_face_setup(const DevMesh& m, const CamParams& cam, int lod, f
                               int tiles_x, int tiles_y, cudaStream_t s)
 {
     (void)tiles_y;
-    k_face_setup<<<grid_for(m.n_faces, 256), 256, 0, s>>>(m.fverts, m.fedges, m.elevel, m.eattr, fb.vproj,
+    k_face_setup<<<grid_for(m.n_faces, 256), 256, 0, s>>>(m.fverts, m.fedges, m.fbound, m.elevel, m.eattr, fb.vproj,
                                                            fb.ved, m.n_faces, lod, delta, cam.W, cam.H, tiles_x,
                                                            fb.fframe, fb.tzsum, fb.tile_cnt);
     return cudaGetLastError();

@@ -8,7 +8,8 @@
 // and the same diagonal (corner 0 to corner 2). Edges are unique vertex pairs;
 // an edge's LoD level is the largest of the levels given for it by its cells
 // (Section "Level of Detail Structure": an edge carries the highest level at
-// which it still exists).
+// which it still exists). A face of one cell is on the boundary surface, whose
+// depth image gives the silhouettes (Section "Blending Focus and Context").
 #include "mesh_host.h"
 
 #include <algorithm>
@@ -64,9 +65,19 @@ int build_host_tables(const float* verts, int64_t n_verts, const int32_t* cells,
         return a.k0 != b.k0 ? a.k0 < b.k0 : a.k1 < b.k1;
     });
     size_t nf = 0;
-    for (size_t i = 0; i < fr.size(); ++i)
-        if (nf == 0 || fr[i].k0 != fr[nf - 1].k0 || fr[i].k1 != fr[nf - 1].k1) fr[nf++] = fr[i];
+    std::vector<uint32_t> ncell;   // cells sharing each unique face
+    ncell.reserve(fr.size());
+    for (size_t i = 0; i < fr.size(); ++i) {
+        if (nf == 0 || fr[i].k0 != fr[nf - 1].k0 || fr[i].k1 != fr[nf - 1].k1) {
+            fr[nf++] = fr[i];
+            ncell.push_back(1);
+        } else {
+            ++ncell.back();
+        }
+    }
     fr.resize(nf);
+    out.fbound.resize(nf);
+    for (size_t f = 0; f < nf; ++f) out.fbound[f] = ncell[f] == 1 ? 1 : 0;
 
     // ---- edges
     size_t ne_all = (size_t)(12 * n_cells);

@@ -11,6 +11,7 @@ struct HostTables {
     std::vector<int32_t> fedges;     // [F*4] unique edge id of local edge k = (c_k, c_k+1)
     std::vector<int32_t> cell_edges; // [C*12] unique edge id of each cell edge
     std::vector<uint8_t> elevel;     // [E] LoD level of each unique edge
+    std::vector<uint8_t> fbound;     // [F] 1: the face belongs to one cell (the boundary surface)
     int64_t n_faces = 0, n_edges = 0;
 };
 

@@ -75,7 +75,7 @@ class hexfc_style(C.Structure):
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("tf_lo", C.c_float), ("tf_hi", C.c_float),
                 ("bg", C.c_float * 3), ("accent_beta", C.c_float), ("halo_scale", C.c_float),
                 ("darken", C.c_float), ("g_min", C.c_float), ("g_max", C.c_float),
-                ("desat", C.c_float)]
+                ("desat", C.c_float), ("sil_alpha", C.c_float), ("sil_threshold", C.c_float)]
 
 
 class hexfc_frame_stats(C.Structure):

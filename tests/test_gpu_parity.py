@@ -464,3 +464,35 @@ def test_device_error_bits_are_reported(hx, bits, status):
     assert r.render_host(mid, host, check=False) == hx.HEXFC_OK
     torch.cuda.synchronize()
     r.close()
+
+
+@pytest.mark.parametrize("lens_mode", [synth.LENS_SPHERE, synth.LENS_SCREEN])
+def test_silhouettes_match_oracle(hx, lens_mode):
+    """White exterior and interior silhouettes (Section "Blending Focus and
+    Context"): a small box in front of a larger slab under a perspective view,
+    every pixel against the oracle; then a sub-rectangle cutting through the
+    inner silhouette, equal to those pixels of the whole frame."""
+    from test_oracle_geometry_pins import box_cells
+    verts, cells = box_cells([((-0.6, 0.6), (-0.5, 0.5), (-0.5, -0.3)),
+                              ((-0.25, 0.3), (-0.2, 0.25), (0.1, 0.45))])
+    mesh = synth.HexMesh(verts=verts, cells=cells, cell_scalar=np.array([0.3, 0.8], np.float32),
+                         edge_level=np.zeros((2, 12), np.uint8))
+    view = synth.orbit_view(9, 120, 150, 110, radius=2.2)
+    lens = (synth.lissajous_lens(9, 120) if lens_mode == synth.LENS_SPHERE
+            else synth.Lens(mode=synth.LENS_SCREEN, center=(70.0, 50.0, 0.0), radius=40.0))
+    style = synth.Style(w_base=1.5, lod=1, sil_alpha=0.8, sil_threshold=4096.0)
+    st, out = render_both(hx, mesh, view, lens, style)
+    om = oracle.Mesh(mesh.verts, mesh.cells, mesh.cell_scalar, mesh.edge_level)
+    sil = om.render(view, lens, style, fragments=False)["sil"]
+    assert sil.sum() > 150   # the outline and the small box's ring
+    r = hx.Renderer(0)
+    mid = r.upload_mesh(mesh.verts, mesh.cells, mesh.cell_scalar, mesh.edge_level)
+    r.set_view(view)
+    r.set_lens(lens)
+    r.set_style(style)
+    r.set_subrect(40, 30, 60, 41)
+    part = torch.zeros((41, 60, 4), dtype=torch.float32, device="cuda")
+    r.render(mid, part)
+    torch.cuda.synchronize()
+    assert torch.equal(part, out[30:71, 40:100])
+    r.close()

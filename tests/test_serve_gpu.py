@@ -128,7 +128,9 @@ def test_subrect_pixels_equal_the_whole_frame(hx, lens_mode):
         assert torch.equal(part, full[y0:y0 + h, x0:x0 + w]), (x0, y0, w, h)
         if w == W:
             frags += r.last_stats["fragments"]
-    assert frags == whole
+    # each band is drawn with an apron row above and below it (their depths give
+    # the border pixels' silhouettes): its count includes those rows
+    assert whole <= frags <= whole * 1.1
     r.set_subrect()
     again = torch.zeros((H, W, 4), device="cuda")
     r.render(mid, again)
