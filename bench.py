@@ -16,6 +16,7 @@ Prints one JSON line (rank 0). --impl reference times the CPU oracle instead
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -551,9 +552,11 @@ def run_serving(args, rank, world):
 def run_batch(args, rank, world, steps=None, warmup=None):
     """Many views of several meshes in one call: warped N^3 grids (N = 32, 64,
     96) x 16 orbit views each at 1280x720, drawn as one batch per step (each
-    frame phase of all 48 views captured as one CUDA graph), with the tuning
-    options chosen by the autotuner; against the same 48 frames drawn one by
-    one."""
+    frame phase of all 48 views captured as one CUDA graph, every view its own
+    launches on parallel branches), with the tuning options chosen by the
+    autotuner; against the same batch with the count, fill and resolve of all
+    views each one launch, and against the 48 frames drawn one by one. The
+    same three ways are timed again on 320x180 thumbnails of the same views."""
     import numpy as np
     import torch
     from paper_2009_06574_gb300 import autotune, hexfc, synth
@@ -573,47 +576,59 @@ def run_batch(args, rank, world, steps=None, warmup=None):
               for k in range(n_views)]
     cache = os.path.join(tempfile.gettempdir(), "hexfc_autotune.json")
     tuned = autotune.tune(r, mids[1], frames[::4], style, cache_path=cache)
-    items = [(mid, v, l, style, torch.empty((H, W, 4), dtype=torch.float32, device="cuda"))
-             for mid in mids for (v, l) in frames]
     stream = torch.cuda.current_stream()
 
-    def batched():
-        st, per, stats = r.render_batch(items, stream)
-        return stats
+    def arms(items):
+        def batched(single):
+            def go():
+                r.set_option(hexfc.HEXFC_OPT_BATCH_LAUNCH, single)
+                st, per, stats = r.render_batch(items, stream)
+                return stats
+            return go
 
-    def one_by_one():
-        stats = []
-        for mid, v, l, sty, out in items:
-            r.set_view(v)
-            r.set_lens(l)
-            r.set_style(sty)
-            r.render(mid, out, stream)
-            stats.append(r.last_stats)
-        return stats
+        def one_by_one():
+            stats = []
+            for mid, v, l, sty, out in items:
+                r.set_view(v)
+                r.set_lens(l)
+                r.set_style(sty)
+                r.render(mid, out, stream)
+                stats.append(r.last_stats)
+            return stats
 
-    res = {}
-    for name, fn in (("batched", batched), ("one_by_one", one_by_one)):
-        for _ in range(warmup):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        frags = 0
-        e0.record(stream)
-        for _ in range(steps):
-            frags += sum(s["fragments"] for s in fn())
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        res[name] = {"frames_per_s": steps * len(items) / (ms / 1000.0), "ms_per_batch": ms / steps,
-                     "fragments_per_s": frags / (ms / 1000.0)}
+        res = {}
+        for name, fn in (("batched", batched(0)), ("single_launch", batched(1)), ("one_by_one", one_by_one)):
+            for _ in range(warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            frags = 0
+            e0.record(stream)
+            for _ in range(steps):
+                frags += sum(s["fragments"] for s in fn())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            res[name] = {"frames_per_s": steps * len(items) / (ms / 1000.0), "ms_per_batch": ms / steps,
+                         "fragments_per_s": frags / (ms / 1000.0)}
+        r.set_option(hexfc.HEXFC_OPT_BATCH_LAUNCH, 0)
+        return res
+
+    def views(w, h):
+        return [(mid, dataclasses.replace(v, width=w, height=h), l, style,
+                 torch.empty((h, w, 4), dtype=torch.float32, device="cuda")) for mid in mids for (v, l) in frames]
+
+    res = arms(views(W, H))
+    small = arms(views(320, 180))
     line = {
         "metric": "frames/s, batched views (3 meshes x 16 views, 1280x720)",
         "value": res["batched"]["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "steps": steps,
         "warmup": warmup, "higher_is_better": True, "impl": "ours", "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "batch_grids32-64-96_x16views_1280x720", "items": len(items),
+        "config": {"workload": "batch_grids32-64-96_x16views_1280x720", "items": len(mids) * len(frames),
                    "tuned": tuned["config"]},
-        "batched": res["batched"], "one_by_one": res["one_by_one"],
+        "batched": res["batched"], "single_launch": res["single_launch"], "one_by_one": res["one_by_one"],
         "speedup": res["batched"]["frames_per_s"] / res["one_by_one"]["frames_per_s"],
+        "thumbnails_320x180": {k: v["frames_per_s"] for k, v in small.items()},
     }
     r.close()
     return line

@@ -225,8 +225,10 @@ hexfc_status hexfc_share_mesh(hexfc_ctx* dst, const hexfc_ctx* src, int32_t mesh
  * depth order and coverage count up to the fragment total; fill and
  * composite) run for all items at once: each phase is captured as one CUDA
  * graph with the items on their own streams, and the executable graph of a
- * phase is reused (updated in place) when only parameters changed. The host
- * waits twice per batch instead of twice per frame.
+ * phase is reused (updated in place) when only parameters changed; with
+ * HEXFC_OPT_BATCH_LAUNCH 1 the coverage count, the fill and the main resolve
+ * pass of all items are instead each one launch over the tiles of every item.
+ * The host waits twice per batch instead of twice per frame.
  *   items[i].mesh      mesh handle of ctx
  *   items[i].view, .lens, .style   as for hexfc_set_view / _lens / _style
  *                      (the context's own view, lens and style are unchanged)
@@ -357,9 +359,14 @@ enum {
                                         in the device error word as a kernel of that frame would set
                                         them (4: a bounded wait ran out, 1: a failed check); no wait
                                         runs out and nothing faults. One frame only. */
-    HEXFC_OPT_FRAG_BUDGET = 7        /* bytes: the cap of hexfc_create's frag_budget_bytes, per frame
+    HEXFC_OPT_FRAG_BUDGET = 7,       /* bytes: the cap of hexfc_create's frag_budget_bytes, per frame
                                         (0: none); a serving loop sets it to what the other frames in
                                         flight leave */
+    HEXFC_OPT_BATCH_LAUNCH = 8       /* hexfc_render_batch: 0 (default): every item its own launches,
+                                        the items as parallel branches of each phase's graph; 1: the
+                                        coverage count, the fill and the main resolve pass of all items
+                                        each one kernel launch over every item's tiles (groups of 64
+                                        items). The images do not depend on it, bit for bit */
 };
 hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value);
 

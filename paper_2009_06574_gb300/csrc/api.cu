@@ -28,6 +28,7 @@ struct hexfc_ctx {
     int reverse_bins = 0;
     int depth_buckets = 2048;   // HEXFC_OPT_DEPTH_BUCKETS
     int window = 2;             // HEXFC_OPT_COMPOSITE_WINDOW
+    bool batch_launch = false;  // HEXFC_OPT_BATCH_LAUNCH
     int predicted = 0;          // HEXFC_OPT_PREDICTED_CAPACITY
     int sub_x0 = 0, sub_y0 = 0, sub_w = 0, sub_h = 0;   // hexfc_set_subrect (sub_w 0: the whole frame)
     OutWin last_win{};          // output window of the last frame, in its drawn rectangle
@@ -555,7 +556,8 @@ hexfc_status job_read1(FrameJob& j)
     return HEXFC_OK;
 }
 
-hexfc_status job_phase2(FrameJob& j, cudaStream_t s)
+// Phase 2 up to the count: the bins in depth order, the tile order, the capacity features.
+hexfc_status job_phase2_bins(FrameJob& j, cudaStream_t s)
 {
     FrameBufs& fb = *j.fb;
     job_mark(j, 4, s);
@@ -563,16 +565,31 @@ hexfc_status job_phase2(FrameJob& j, cudaStream_t s)
     CK(launch_bin_fill(*j.m, fb, j.tiles_x, j.W, j.H, j.reverse, s));
     CK(launch_bin_sort(*j.m, fb, j.tiles_x, j.tiles_y, j.buckets, s));
     CK(launch_tile_order(fb, j.n_tiles, s));
+    j.launches += 3;
     hexfc_status fst = job_features(j, s);
     if (fst != HEXFC_OK) return fst;
     job_mark(j, 5, s);
-    CK(launch_count(*j.m, fb, j.tiles_x, j.tiles_y, j.W, j.H, false, s));
+    return HEXFC_OK;
+}
+
+// Phase 2 after the count: the pixel scan, its totals to the host.
+hexfc_status job_phase2_scan(FrameJob& j, cudaStream_t s)
+{
+    FrameBufs& fb = *j.fb;
     job_mark(j, 6, s);
     CK(scan_u32_to_u64(fb.cnt, fb.off, j.n_pix, fb.part, fb.part_max, fb.scal, (uint32_t)kWarpSortMax, s));
     job_mark(j, 7, s);
-    j.launches += 7;
+    j.launches += 4;   // the count and the three scan passes
     CK(cudaMemcpyAsync(fb.h_scal, fb.scal, 6 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     return HEXFC_OK;
+}
+
+hexfc_status job_phase2(FrameJob& j, cudaStream_t s)
+{
+    hexfc_status st;
+    if ((st = job_phase2_bins(j, s)) != HEXFC_OK) return st;
+    CK(launch_count(*j.m, *j.fb, j.tiles_x, j.tiles_y, j.W, j.H, false, s));
+    return job_phase2_scan(j, s);
 }
 
 // After phase 2 has completed: device error bits, totals, limits, fragment buffers.
@@ -664,6 +681,79 @@ hexfc_status job_phase3(FrameJob& j, cudaStream_t s)
     job_mark(j, 10, s);
     j.launches += 3 + (j.n_long > 0 ? 1 : 0);
     j.fs.kernel_launches = j.launches;
+    return HEXFC_OK;
+}
+
+// A frame's entries in the batched count, fill and main resolve launches.
+CountItem count_item(const FrameJob& j)
+{
+    const FrameBufs& fb = *j.fb;
+    return CountItem{fb.tile_off, fb.bins, fb.fframe, fb.tile_order, fb.cnt, fb.masks, fb.tile_frag,
+                     j.tiles_x,   j.W,     j.H};
+}
+
+FillItem fill_item(const FrameJob& j)
+{
+    const FrameBufs& fb = *j.fb;
+    FillItem it{};
+    it.tile_off = fb.tile_off;
+    it.bins = fb.bins;
+    it.masks = fb.masks;
+    it.fframe = fb.fframe;
+    it.fstat = j.m->fstat;
+    it.order = fb.tile_order;
+    it.off = fb.off;
+    it.cnt = fb.cnt;
+    it.key = fb.key;
+    it.rgba = fb.rgba;
+    it.seg = fb.seg;
+    it.err = reinterpret_cast<unsigned long long*>(fb.scal + 5);
+    it.zsil = j.sil_alpha > 0.f ? fb.zsil : nullptr;
+    it.sp = j.sp;
+    it.tiles_x = j.tiles_x;
+    it.W = j.W;
+    it.H = j.H;
+    return it;
+}
+
+CompositeItem composite_item(const FrameJob& j)
+{
+    const FrameBufs& fb = *j.fb;
+    CompositeItem it{};
+    it.cnt = fb.cnt;
+    it.seg = fb.seg;
+    it.tile_off = fb.tile_off;
+    it.masks = fb.masks;
+    it.key = fb.key;
+    it.rgba = fb.rgba;
+    it.out = reinterpret_cast<float4*>(j.out);
+    it.long_q = fb.long_q;
+    it.long_cursor = reinterpret_cast<unsigned long long*>(fb.scal + 3);
+    it.fix_q = fb.fix_q;
+    it.fix_cursor = reinterpret_cast<unsigned long long*>(fb.scal + 4);
+    it.frag_cap = (uint64_t)fb.frag_cap;
+    for (int c = 0; c < 3; ++c) it.bg[c] = j.sp.bg[c];
+    it.win = j.win;
+    it.tiles_x = j.tiles_x;
+    it.W = j.W;
+    it.H = j.H;
+    return it;
+}
+
+// One batched launch per group of at most kBatchLaunchMax frames: `add` puts
+// frame i in the batch, `go` launches it.
+template <typename B, typename Add, typename Go>
+hexfc_status batched(B& b, const std::vector<int>& items, Add&& add, Go&& go)
+{
+    b.n = 0;
+    b.tile_begin[0] = 0;
+    for (size_t k = 0; k < items.size(); ++k) {
+        add(b, items[k]);   // sets b.it[b.n] and b.tile_begin[b.n + 1], advances b.n
+        if (b.n == kBatchLaunchMax || k + 1 == items.size()) {
+            CK(go(b));
+            b.n = 0;
+        }
+    }
     return HEXFC_OK;
 }
 
@@ -1010,8 +1100,13 @@ struct NormalStream {
     }
 };
 
-template <typename F>
-hexfc_status batch_graph(hexfc_ctx* ctx, int phase, const std::vector<int>& items, F&& body)
+// One phase of a batch as one graph: `pre` of every frame on the frame's own
+// stream (branches that run side by side), then `mid` on the origin stream
+// after all of them (the batched launches over every frame's tiles), then
+// `post` of every frame on its stream again; `mid` and `post` may be empty.
+template <typename Pre, typename Mid, typename Post>
+hexfc_status batch_graph(hexfc_ctx* ctx, int phase, const std::vector<int>& items, Pre&& pre, Mid&& mid,
+                         Post&& post, bool has_mid)
 {
     cudaStream_t o = ctx->origin;
     if (const cudaError_t e = cudaStreamBeginCapture(o, cudaStreamCaptureModeThreadLocal); e != cudaSuccess) {
@@ -1019,13 +1114,21 @@ hexfc_status batch_graph(hexfc_ctx* ctx, int phase, const std::vector<int>& item
         return HEXFC_ERR_CUDA;
     }
     hexfc_status st = HEXFC_OK;
-    bool ok = cudaEventRecord(ctx->ev_in, o) == cudaSuccess;
-    for (int i : items) {
-        auto& b = *ctx->batch[(size_t)i];
-        ok = ok && cudaStreamWaitEvent(b.stream, ctx->ev_in, 0) == cudaSuccess;
-        if (ok && st == HEXFC_OK) st = body(i, b.stream);
-        ok = ok && cudaEventRecord(b.done, b.stream) == cudaSuccess;   // join, also after a failure
-        ok = ok && cudaStreamWaitEvent(o, b.done, 0) == cudaSuccess;
+    bool ok = true;
+    auto branches = [&](auto&& body) {   // fork from the origin stream, run body per frame, join
+        ok = ok && cudaEventRecord(ctx->ev_in, o) == cudaSuccess;
+        for (int i : items) {
+            auto& b = *ctx->batch[(size_t)i];
+            ok = ok && cudaStreamWaitEvent(b.stream, ctx->ev_in, 0) == cudaSuccess;
+            if (ok && st == HEXFC_OK) st = body(i, b.stream);
+            ok = ok && cudaEventRecord(b.done, b.stream) == cudaSuccess;   // join, also after a failure
+            ok = ok && cudaStreamWaitEvent(o, b.done, 0) == cudaSuccess;
+        }
+    };
+    branches(pre);
+    if (has_mid) {
+        if (ok && st == HEXFC_OK) st = mid(o);
+        branches(post);
     }
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(o, &g);
@@ -1283,24 +1386,91 @@ hexfc_status hexfc_render_batch(hexfc_ctx* ctx, int32_t n, const hexfc_batch_ite
     // the batch starts after the caller's earlier work on its stream
     CK(cudaEventRecord(ctx->ev_out, s));
     CK(cudaStreamWaitEvent(ctx->origin, ctx->ev_out, 0));
-    if ((st = batch_graph(ctx, 0, live, [&](int i, cudaStream_t si) { return job_phase1(jobs[(size_t)i], si); })) !=
-        HEXFC_OK)
+    auto none = [](int, cudaStream_t) -> hexfc_status { return HEXFC_OK; };
+    auto no_mid = [](cudaStream_t) -> hexfc_status { return HEXFC_OK; };
+    if ((st = batch_graph(
+             ctx, 0, live, [&](int i, cudaStream_t si) { return job_phase1(jobs[(size_t)i], si); }, no_mid, none,
+             false)) != HEXFC_OK)
         return st;
     CK(cudaStreamSynchronize(ctx->origin));
     for (int i : live)
         if ((st = job_read1(jobs[(size_t)i])) != HEXFC_OK) return st;
-    if ((st = batch_graph(ctx, 1, live, [&](int i, cudaStream_t si) { return job_phase2(jobs[(size_t)i], si); })) !=
-        HEXFC_OK)
+    // the count of every frame in one launch (per group of kBatchLaunchMax frames)
+    auto count_all = [&](cudaStream_t o) -> hexfc_status {
+        CountBatch b;
+        return batched(
+            b, live,
+            [&](CountBatch& cb, int i) {
+                const FrameJob& j = jobs[(size_t)i];
+                cb.it[cb.n] = count_item(j);
+                cb.tile_begin[cb.n + 1] = cb.tile_begin[cb.n] + (uint32_t)j.n_tiles;
+                ++cb.n;
+            },
+            [&](CountBatch& cb) { return launch_count_batch(cb, o); });
+    };
+    const bool one = ctx->batch_launch;
+    if (one && (st = batch_graph(
+                    ctx, 1, live, [&](int i, cudaStream_t si) { return job_phase2_bins(jobs[(size_t)i], si); },
+                    count_all, [&](int i, cudaStream_t si) { return job_phase2_scan(jobs[(size_t)i], si); }, true)) !=
+                   HEXFC_OK)
+        return st;
+    if (!one && (st = batch_graph(
+                     ctx, 1, live, [&](int i, cudaStream_t si) { return job_phase2(jobs[(size_t)i], si); }, no_mid,
+                     none, false)) != HEXFC_OK)
         return st;
     CK(cudaStreamSynchronize(ctx->origin));
-    std::vector<int> draw;
+    std::vector<int> draw, draw_sil, draw_plain;
     for (int i : live) {
         res[(size_t)i] = job_read2(jobs[(size_t)i], ctx->batch[(size_t)i]->stream);
-        if (res[(size_t)i] == HEXFC_OK) draw.push_back(i);
+        if (res[(size_t)i] != HEXFC_OK) continue;
+        draw.push_back(i);
+        (jobs[(size_t)i].sil_alpha > 0.f ? draw_sil : draw_plain).push_back(i);
     }
-    if (!draw.empty() &&
-        (st = batch_graph(ctx, 2, draw, [&](int i, cudaStream_t si) { return job_phase3(jobs[(size_t)i], si); })) !=
-            HEXFC_OK)
+    // the fill of every frame in one launch (one per fill variant), then the
+    // main resolve pass of every frame in one launch
+    auto fill_composite_all = [&](cudaStream_t o) -> hexfc_status {
+        hexfc_status r = HEXFC_OK;
+        for (int variant = 0; variant < 2 && r == HEXFC_OK; ++variant) {
+            FillBatch b;
+            r = batched(
+                b, variant ? draw_sil : draw_plain,
+                [&](FillBatch& fbt, int i) {
+                    const FrameJob& j = jobs[(size_t)i];
+                    fbt.it[fbt.n] = fill_item(j);
+                    fbt.tile_begin[fbt.n + 1] = fbt.tile_begin[fbt.n] + (uint32_t)j.n_tiles;
+                    ++fbt.n;
+                },
+                [&](FillBatch& fbt) { return launch_fill_batch(fbt, variant == 1, o); });
+        }
+        if (r != HEXFC_OK) return r;
+        CompositeBatch cb;
+        return batched(
+            cb, draw,
+            [&](CompositeBatch& c, int i) {
+                const FrameJob& j = jobs[(size_t)i];
+                c.it[c.n] = composite_item(j);
+                c.tile_begin[c.n + 1] = c.tile_begin[c.n] + (uint32_t)j.n_tiles;
+                ++c.n;
+            },
+            [&](CompositeBatch& c) { return launch_composite_batch(c, ctx->window, o); });
+    };
+    auto tail = [&](int i, cudaStream_t si) -> hexfc_status {   // short lists past the window, long lists, silhouettes
+        FrameJob& j = jobs[(size_t)i];
+        CK(launch_composite_tail(*j.fb, j.sp, j.tiles_x, j.out, j.n_long, j.win, si));
+        hexfc_status r = job_silhouette(j, j.out, si);
+        j.launches += 3 + (j.n_long > 0 ? 1 : 0);
+        j.fs.kernel_launches = j.launches;
+        return r;
+    };
+    if (one && !draw.empty() &&
+        (st = batch_graph(
+             ctx, 2, draw, [&](int i, cudaStream_t si) { return job_sil_clear(jobs[(size_t)i], si); },
+             fill_composite_all, tail, true)) != HEXFC_OK)
+        return st;
+    if (!one && !draw.empty() &&
+        (st = batch_graph(
+             ctx, 2, draw, [&](int i, cudaStream_t si) { return job_phase3(jobs[(size_t)i], si); }, no_mid, none,
+             false)) != HEXFC_OK)
         return st;
     // the caller's stream continues after the batch
     CK(cudaEventRecord(ctx->ev_out, ctx->origin));
@@ -1711,6 +1881,10 @@ hexfc_status hexfc_set_option(hexfc_ctx* ctx, int32_t option, int64_t value)
     case HEXFC_OPT_FRAG_BUDGET:
         if (value < 0) return HEXFC_ERR_ARG;
         ctx->budget = (uint64_t)value;
+        return HEXFC_OK;
+    case HEXFC_OPT_BATCH_LAUNCH:
+        if (value != 0 && value != 1) return HEXFC_ERR_ARG;
+        ctx->batch_launch = value != 0;
         return HEXFC_OK;
     case HEXFC_OPT_DEBUG_ERROR_BITS:
         if (value < 0 || value > 7) return HEXFC_ERR_ARG;

@@ -168,6 +168,90 @@ struct FrameBufs {
     uint64_t* h_scal = nullptr;     // pinned mirror
 };
 
+// The pixels of the drawn rectangle that go to the output image: [x0, x0 + w) x
+// [y0, y0 + h), written at out[(y - y0) w + (x - x0)] (the rest is an apron whose
+// depths the silhouettes read).
+struct OutWin {
+    int x0, y0, w, h;
+};
+
+// ---- batched launches: the tiles of up to kBatchLaunchMax frames in one grid ------------
+// Each block finds its frame from the frames' first tile (tile_begin, in the
+// kernel's parameters) and takes that frame's tile in its tile order.
+constexpr int kBatchLaunchMax = 64;
+struct CountItem {
+    const uint64_t* tile_off;
+    const uint32_t* bins;
+    const FaceFrame* fframe;
+    const uint32_t* order;
+    uint32_t* cnt;
+    uint32_t* masks;
+    uint32_t* tile_frag;
+    int tiles_x, W, H;
+};
+struct CountBatch {
+    CountItem it[kBatchLaunchMax];
+    uint32_t tile_begin[kBatchLaunchMax + 1];
+    int n;
+};
+struct FillItem {
+    const uint64_t* tile_off;
+    const uint32_t* bins;
+    const uint32_t* masks;
+    const FaceFrame* fframe;
+    const FaceStatic* fstat;
+    const uint32_t* order;
+    const uint64_t* off;
+    const uint32_t* cnt;
+    uint64_t* key;
+    float4* rgba;
+    uint64_t* seg;
+    unsigned long long* err;
+    uint32_t* zsil;   // nullptr: no silhouettes
+    ShadeParams sp;
+    int tiles_x, W, H;
+};
+struct FillBatch {
+    FillItem it[kBatchLaunchMax];
+    uint32_t tile_begin[kBatchLaunchMax + 1];
+    int n;
+};
+struct CompositeItem {
+    const uint32_t* cnt;
+    const uint64_t* seg;
+    const uint64_t* tile_off;
+    const uint32_t* masks;
+    const uint64_t* key;
+    const float4* rgba;
+    float4* out;
+    uint32_t* long_q;
+    unsigned long long* long_cursor;
+    uint32_t* fix_q;
+    unsigned long long* fix_cursor;
+    uint64_t frag_cap;
+    float bg[3];
+    OutWin win;
+    int tiles_x, W, H;
+};
+struct CompositeBatch {
+    CompositeItem it[kBatchLaunchMax];
+    uint32_t tile_begin[kBatchLaunchMax + 1];
+    int n;
+};
+// The frame of block b in a batched launch: the last with begin[i] <= b.
+__device__ __forceinline__ int batch_item(const uint32_t* begin, int n, uint32_t b)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+static_assert(sizeof(FillBatch) < 30000 && sizeof(CompositeBatch) < 30000 && sizeof(CountBatch) < 30000,
+              "a batch's parameters fit a kernel's parameter space");
+
 // ---- launches (each returns cudaGetLastError()) -----------------------------------------
 cudaError_t launch_cell_quality(const DevMesh& m, int metric, float* out, cudaStream_t s);
 cudaError_t launch_importance(const DevMesh& m, cudaStream_t s);
@@ -187,6 +271,13 @@ cudaError_t launch_bin_sort(const DevMesh& m, FrameBufs& fb, int tiles_x, int ti
 cudaError_t launch_tile_order(FrameBufs& fb, int n_tiles, cudaStream_t s);
 cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles_y, int W, int H, bool stats,
                          cudaStream_t s);
+// The count, fill and main resolve pass of several frames, each one launch.
+cudaError_t launch_count_batch(const CountBatch& b, cudaStream_t s);
+cudaError_t launch_fill_batch(const FillBatch& b, bool sil, cudaStream_t s);
+cudaError_t launch_composite_batch(const CompositeBatch& b, int window, cudaStream_t s);
+// The second passes of one frame's resolve (out-of-order and long lists).
+cudaError_t launch_composite_tail(FrameBufs& fb, const ShadeParams& sp, int tiles_x, float* out, uint32_t n_long,
+                                  OutWin win, cudaStream_t s);
 // Tile capacities from the previous frame's exact counts, or `uniform` (> 0) per tile.
 cudaError_t launch_capacity_from_previous(FrameBufs& fb, int64_t n_tiles, float margin, uint32_t pad,
                                           uint32_t uniform, cudaStream_t s);
@@ -200,12 +291,6 @@ cudaError_t launch_cap_to_half(CapNet& net, cudaStream_t s);
 // sil: record each pixel's nearest boundary-fragment depth into fb.zsil.
 cudaError_t launch_fill(const DevMesh& m, FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W,
                         int H, bool regions, bool sil, cudaStream_t s);
-// The pixels of the drawn rectangle that go to the output image: [x0, x0 + w) x
-// [y0, y0 + h), written at out[(y - y0) w + (x - x0)] (the rest is an apron whose
-// depths the silhouettes read).
-struct OutWin {
-    int x0, y0, w, h;
-};
 cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W, int H,
                              float* out, uint32_t n_long, int window, OutWin win, cudaStream_t s);
 // White silhouettes over the output (Section "Blending Focus and Context"):

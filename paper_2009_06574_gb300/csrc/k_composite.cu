@@ -265,21 +265,22 @@ __device__ __forceinline__ bool out_index(const OutWin& w, int x, int y, int64_t
     return true;
 }
 
+// The main resolve pass of one tile (the body of k_composite and k_composite_batch).
 template <int KW>
-__global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ cnt,
-                                                   const uint64_t* __restrict__ seg,
-                                                   const uint64_t* __restrict__ tile_off,
-                                                   const uint32_t* __restrict__ masks,
-                                                   const uint64_t* __restrict__ key,
-                                                   const float4* __restrict__ rgba, uint64_t frag_cap, int tiles_x,
-                                                   int W, int H, float bg0, float bg1, float bg2,
-                                                   float4* __restrict__ out, OutWin win,
-                                                   uint32_t* __restrict__ long_q,
-                                                   unsigned long long* __restrict__ long_cursor,
-                                                   uint32_t* __restrict__ fix_q,
-                                                   unsigned long long* __restrict__ fix_cursor)
+__device__ __forceinline__ void composite_tile(int tile, const uint32_t* __restrict__ cnt,
+                                               const uint64_t* __restrict__ seg,
+                                               const uint64_t* __restrict__ tile_off,
+                                               const uint32_t* __restrict__ masks,
+                                               const uint64_t* __restrict__ key,
+                                               const float4* __restrict__ rgba, uint64_t frag_cap, int tiles_x,
+                                               int W, int H, float bg0, float bg1, float bg2,
+                                               float4* __restrict__ out, const OutWin& win,
+                                               uint32_t* __restrict__ long_q,
+                                               unsigned long long* __restrict__ long_cursor,
+                                               uint32_t* __restrict__ fix_q,
+                                               unsigned long long* __restrict__ fix_cursor)
 {
-    const int tile = blockIdx.x, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
     const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;
     const uint64_t cb = tile_off[tile] / kChunk;
     const uint32_t n_chunks = (uint32_t)(tile_off[tile + 1] / kChunk - cb);
@@ -371,6 +372,40 @@ __global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ 
     if (ok) out[o] = finish(c, bg0, bg1, bg2);
     else if (n > (uint32_t)kWarpList) long_q[atomicAdd(long_cursor, 1ull)] = (uint32_t)q;
     else fix_q[atomicAdd(fix_cursor, 1ull)] = (uint32_t)q;
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) k_composite(const uint32_t* __restrict__ cnt,
+                                                   const uint64_t* __restrict__ seg,
+                                                   const uint64_t* __restrict__ tile_off,
+                                                   const uint32_t* __restrict__ masks,
+                                                   const uint64_t* __restrict__ key,
+                                                   const float4* __restrict__ rgba, uint64_t frag_cap, int tiles_x,
+                                                   int W, int H, float bg0, float bg1, float bg2,
+                                                   float4* __restrict__ out, OutWin win,
+                                                   uint32_t* __restrict__ long_q,
+                                                   unsigned long long* __restrict__ long_cursor,
+                                                   uint32_t* __restrict__ fix_q,
+                                                   unsigned long long* __restrict__ fix_cursor)
+{
+    composite_tile<KW>(blockIdx.x, cnt, seg, tile_off, masks, key, rgba, frag_cap, tiles_x, W, H, bg0, bg1, bg2, out,
+                       win, long_q, long_cursor, fix_q, fix_cursor);
+}
+
+// The main resolve pass of several frames in one grid (a batch); tiles in
+// index order within a frame, as k_composite takes them.
+template <int KW>
+__global__ void __launch_bounds__(256, KW == 2 ? 4 : (KW == 4 ? 3 : 2))
+k_composite_batch(const __grid_constant__ CompositeBatch b)
+{
+    __shared__ CompositeItem s_it;   // the frame's pointers and constants, read from shared memory
+    const int i = batch_item(b.tile_begin, b.n, blockIdx.x);
+    if (threadIdx.x == 0) s_it = b.it[i];
+    __syncthreads();
+    const CompositeItem& it = s_it;
+    composite_tile<KW>((int)(blockIdx.x - b.tile_begin[i]), it.cnt, it.seg, it.tile_off, it.masks, it.key, it.rgba,
+                       it.frag_cap, it.tiles_x, it.W, it.H, it.bg[0], it.bg[1], it.bg[2], it.out, it.win, it.long_q,
+                       it.long_cursor, it.fix_q, it.fix_cursor);
 }
 
 // Out-of-order lists (n <= 256): one warp each, gathered into shared memory
@@ -634,6 +669,24 @@ constexpr unsigned kLongGridMax = 2 * 152;  // persistent: blocks stride over th
 
 }  // namespace
 
+cudaError_t launch_composite_tail(FrameBufs& fb, const ShadeParams& sp, int tiles_x, float* out, uint32_t n_long,
+                                  OutWin win, cudaStream_t s)
+{
+    float4* o4 = reinterpret_cast<float4*>(out);
+    unsigned long long* long_cursor = reinterpret_cast<unsigned long long*>(fb.scal + 3);
+    unsigned long long* fix_cursor = reinterpret_cast<unsigned long long*>(fb.scal + 4);
+    k_composite_fix<<<kFixBlocks, 256, kFixSmem, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
+                                                      (uint64_t)fb.frag_cap, tiles_x, sp.bg[0], sp.bg[1],
+                                                      sp.bg[2], o4, win, fb.fix_q, fix_cursor);
+    if (n_long > 0) {   // n_long: the number of long lists if known, else an upper bound on the useful grid
+        const unsigned grid = n_long < kLongGridMax ? n_long : kLongGridMax;
+        k_composite_long<<<grid, 1024, kLongSmem, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
+                                                       (uint64_t)fb.frag_cap, fb.long_q, long_cursor, tiles_x,
+                                                       sp.bg[0], sp.bg[1], sp.bg[2], o4, win);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, int tiles_y, int W, int H, float* out,
                              uint32_t n_long, int window, OutWin win, cudaStream_t s)
 {
@@ -650,15 +703,18 @@ cudaError_t launch_composite(FrameBufs& fb, const ShadeParams& sp, int tiles_x, 
     if (window == 8) resolve(k_composite<8>);
     else if (window == 4) resolve(k_composite<4>);
     else resolve(k_composite<2>);
-    k_composite_fix<<<kFixBlocks, 256, kFixSmem, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
-                                                      (uint64_t)fb.frag_cap, tiles_x, sp.bg[0], sp.bg[1],
-                                                      sp.bg[2], o4, win, fb.fix_q, fix_cursor);
-    if (n_long > 0) {   // n_long: the number of long lists if known, else an upper bound on the useful grid
-        const unsigned grid = n_long < kLongGridMax ? n_long : kLongGridMax;
-        k_composite_long<<<grid, 1024, kLongSmem, s>>>(fb.cnt, fb.seg, fb.tile_off, fb.masks, fb.key, fb.rgba,
-                                                       (uint64_t)fb.frag_cap, fb.long_q, long_cursor, tiles_x,
-                                                       sp.bg[0], sp.bg[1], sp.bg[2], o4, win);
-    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_composite_tail(fb, sp, tiles_x, out, n_long, win, s);
+}
+
+cudaError_t launch_composite_batch(const CompositeBatch& b, int window, cudaStream_t s)
+{
+    if (b.n == 0 || b.tile_begin[b.n] == 0) return cudaSuccess;
+    const unsigned grid = b.tile_begin[b.n];
+    if (window == 8) k_composite_batch<8><<<grid, 256, 0, s>>>(b);
+    else if (window == 4) k_composite_batch<4><<<grid, 256, 0, s>>>(b);
+    else k_composite_batch<2><<<grid, 256, 0, s>>>(b);
     return cudaGetLastError();
 }
 

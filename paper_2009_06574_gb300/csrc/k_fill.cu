@@ -405,6 +405,35 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __rest
                     W, H, sp, key, rgba, seg, err, kSil ? zsil + (int64_t)tile * kTilePix : nullptr);
 }
 
+// The fill of several frames in one grid (a batch; offsets from each frame's
+// pixel scan).
+template <bool kSil>
+__global__ void __launch_bounds__(kPipeThreads, 3) k_fill_batch(const __grid_constant__ FillBatch b)
+{
+    extern __shared__ __align__(128) unsigned char fill_smem[];
+    __shared__ uint64_t s_base[kTilePix];
+    __shared__ uint32_t s_len[kTilePix];
+    __shared__ __align__(8) uint64_t s_full[kRing], s_empty[kRing];
+    __shared__ FillItem s_it;   // the frame's pointers and constants, read from shared memory
+    const int i = batch_item(b.tile_begin, b.n, blockIdx.x);
+    const int tile = (int)b.it[i].order[blockIdx.x - b.tile_begin[i]];
+    if (threadIdx.x == 0) s_it = b.it[i];
+    __syncthreads();
+    const FillItem& it = s_it;
+    const int px0 = (tile % it.tiles_x) * kTile, py0 = (tile / it.tiles_x) * kTile;
+    const uint64_t beg = it.tile_off[tile], end = it.tile_off[tile + 1];
+    const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
+    const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;
+    if (threadIdx.x < kTilePix) {
+        s_base[threadIdx.x] = it.off[q];
+        s_len[threadIdx.x] = it.cnt[q];
+    }
+    pipe_init(s_full, s_empty);
+    fill_tile<kSil>(fill_smem, s_base, s_len, s_full, s_empty, it.bins, it.masks, it.fframe, it.fstat, beg, n_chunks,
+                    px0, py0, it.W, it.H, it.sp, it.key, it.rgba, it.seg, it.err,
+                    kSil ? it.zsil + (int64_t)tile * kTilePix : nullptr);
+}
+
 // Capacities from the previous frame's exact tile counts: prev * (1 + margin)
 // + pad; or, given a uniform count (> 0), that count for every tile instead.
 __global__ void k_capacity_from_previous(const uint32_t* __restrict__ prev, int64_t n_tiles, float margin,
@@ -424,7 +453,21 @@ cudaError_t prepare_fill_kernels()
                                          (int)fill_smem_bytes());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fill<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fill_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fill_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fill_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fill_smem_bytes());
     return e;
+}
+
+cudaError_t launch_fill_batch(const FillBatch& b, bool sil, cudaStream_t s)
+{
+    if (b.n == 0 || b.tile_begin[b.n] == 0) return cudaSuccess;
+    if (sil) k_fill_batch<true><<<b.tile_begin[b.n], kPipeThreads, fill_smem_bytes(), s>>>(b);
+    else k_fill_batch<false><<<b.tile_begin[b.n], kPipeThreads, fill_smem_bytes(), s>>>(b);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_capacity_from_previous(FrameBufs& fb, int64_t n_tiles, float margin, uint32_t pad, uint32_t uniform,

@@ -401,18 +401,16 @@ __device__ __forceinline__ uint32_t tile_sum(uint32_t v, uint32_t* s_tmp)
 // (stats + 4 copy): [0] += fragments, [1] = longest list, [2] += lists longer
 // than kWarpSortMax (the frame's statistics without
 // the pixel scan).
-__global__ void __launch_bounds__(kTilePix, 5) k_count(const uint64_t* __restrict__ tile_off,
-                                                    const uint32_t* __restrict__ bins,
-                                                    const FaceFrame* __restrict__ fframe,
-                                                    const uint32_t* __restrict__ order, int tiles_x, int W, int H,
-                                                    uint32_t* __restrict__ cnt, uint32_t* __restrict__ masks,
-                                                    uint32_t* __restrict__ tile_frag,
-                                                    unsigned long long* __restrict__ stats)
+// The count of one tile (the body of k_count and k_count_batch).
+__device__ __forceinline__ void count_tile(int tile, const uint64_t* __restrict__ tile_off,
+                                           const uint32_t* __restrict__ bins, const FaceFrame* __restrict__ fframe,
+                                           int tiles_x, int W, int H, uint32_t* __restrict__ cnt,
+                                           uint32_t* __restrict__ masks, uint32_t* __restrict__ tile_frag,
+                                           unsigned long long* __restrict__ stats)
 {
     extern __shared__ __align__(16) unsigned char count_smem[];
     CountWarp* s_w = reinterpret_cast<CountWarp*>(count_smem);   // [kConsumerWarps]
     __shared__ uint32_t s_tmp[kConsumerWarps];
-    const int tile = (int)order[blockIdx.x];
     const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
     const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
     const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
@@ -450,12 +448,37 @@ __global__ void __launch_bounds__(kTilePix, 5) k_count(const uint64_t* __restric
     }
 }
 
+__global__ void __launch_bounds__(kTilePix, 5) k_count(const uint64_t* __restrict__ tile_off,
+                                                    const uint32_t* __restrict__ bins,
+                                                    const FaceFrame* __restrict__ fframe,
+                                                    const uint32_t* __restrict__ order, int tiles_x, int W, int H,
+                                                    uint32_t* __restrict__ cnt, uint32_t* __restrict__ masks,
+                                                    uint32_t* __restrict__ tile_frag,
+                                                    unsigned long long* __restrict__ stats)
+{
+    count_tile((int)order[blockIdx.x], tile_off, bins, fframe, tiles_x, W, H, cnt, masks, tile_frag, stats);
+}
+
+// The count of several frames in one grid (a batch).
+__global__ void __launch_bounds__(kTilePix, 5) k_count_batch(const __grid_constant__ CountBatch b)
+{
+    const int i = batch_item(b.tile_begin, b.n, blockIdx.x);
+    const CountItem& it = b.it[i];
+    const int tile = (int)it.order[blockIdx.x - b.tile_begin[i]];
+    count_tile(tile, it.tile_off, it.bins, it.fframe, it.tiles_x, it.W, it.H, it.cnt, it.masks, it.tile_frag,
+               nullptr);
+}
+
 }  // namespace
 
 cudaError_t prepare_raster_kernels()
 {
-    return cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(kConsumerWarps * sizeof(CountWarp)));
+    cudaError_t e = cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kConsumerWarps * sizeof(CountWarp)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_count_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kConsumerWarps * sizeof(CountWarp)));
+    return e;
 }
 
 cudaError_t launch_vertex_setup(const DevMesh& m, const CamParams& cam, FrameBufs& fb, cudaStream_t s)
@@ -506,6 +529,14 @@ cudaError_t launch_count(const DevMesh& m, FrameBufs& fb, int tiles_x, int tiles
                                                                    tiles_x, W, H, fb.cnt, fb.masks, fb.tile_frag,
                                                                    stats ? reinterpret_cast<unsigned long long*>(fb.cstat)
                                                                          : nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_batch(const CountBatch& b, cudaStream_t s)
+{
+    const size_t smem = kConsumerWarps * sizeof(CountWarp);
+    if (b.n == 0 || b.tile_begin[b.n] == 0) return cudaSuccess;
+    k_count_batch<<<b.tile_begin[b.n], kTilePix, smem, s>>>(b);
     return cudaGetLastError();
 }
 

@@ -40,6 +40,7 @@ HEXFC_OPT_COMPOSITE_WINDOW = 4
 HEXFC_OPT_PREDICTED_CAPACITY = 5
 HEXFC_OPT_DEBUG_ERROR_BITS = 6
 HEXFC_OPT_FRAG_BUDGET = 7
+HEXFC_OPT_BATCH_LAUNCH = 8
 HEXFC_CAPACITY_PARAMS = 4545
 STAGES = ["vertex", "face", "tile_scan", "gap1", "bin", "count", "scan", "gap2", "fill", "composite"]
 
