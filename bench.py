@@ -451,7 +451,8 @@ def run_ours(args, rank, world, local_rank):
                    "height": w.height, "frames": w.n_frames,
                    "l2": "not flushed: per-frame working set (fragment lists) far larger than L2",
                    "parallelism": f"replicas x{world}",
-                   "tile_capacity": ["count pass", "previous frame", "capacity network"][args.predicted]},
+                   "tile_capacity": ["count pass", "previous frame", "capacity network"][args.predicted],
+                   "raster_tile": "%dx%d" % hexfc.raster_tile()},
         "fragments_per_s": F * fps, "fragments_per_frame": F, "bins_per_frame": bins,
         "predicted_frames": int(sum(predicted_frames[-args.steps:])),
         "kernels_gbs": {k: round(algo[k] / (kernel_stages[k] / 1000.0) / 1e9, 1) for k in algo},

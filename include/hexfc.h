@@ -468,6 +468,15 @@ int32_t hexfc_last_cuda_error(void);
 /* Static name of a CUDA runtime error code (e.g. "cudaErrorIllegalAddress"). Never NULL. */
 const char* hexfc_cuda_error_name(int32_t code);
 
+/*
+ * The raster tile of this build, in pixels: 16 x 16 by default, 32 x 8 or
+ * 8 x 32 in a library built for those (always 256 pixels). Tiles are the
+ * units of binning (Section "GPU Implementation" draws the faces into
+ * per-pixel lists; the tiling is this implementation's). width, height: host
+ * pointers, each may be NULL.
+ */
+void hexfc_raster_tile(int32_t* width, int32_t* height);
+
 /* Size of the fixed device scratch array used by hexfc_render_noalloc. */
 #define HEXFC_NOALLOC_SCRATCH_BYTES (32u << 20)
 

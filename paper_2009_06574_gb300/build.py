@@ -39,19 +39,40 @@ def _inputs():
     return files
 
 
-def stale() -> bool:
+STAMP = os.path.join(OUT, "config.txt")
+
+
+def tile_defines(tile_w: int | None = None) -> list[str]:
+    """The raster tile is a build-time choice: 16x16 (default), 32x8 or 8x32
+    pixels (always 256 pixels, one per thread of a tile's block); the
+    environment variable HEXFC_TILE_W sets the width when no argument does."""
+    w = int(tile_w if tile_w is not None else os.environ.get("HEXFC_TILE_W", "16"))
+    if w not in (8, 16, 32):
+        raise ValueError(f"tile width {w}: 8, 16 or 32")
+    return [f"-DHEXFC_TILE_W={w}"]
+
+
+def stale(defines: list[str] | None = None) -> bool:
     if not os.path.exists(LIB):
+        return True
+    try:
+        with open(STAMP) as f:
+            if f.read() != " ".join(defines or tile_defines()):
+                return True
+    except OSError:
         return True
     t = os.path.getmtime(LIB)
     return any(os.path.getmtime(f) > t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if not force and not stale():
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          tile_w: int | None = None) -> str:
+    defines = tile_defines(tile_w)
+    if not force and not stale(defines):
         return LIB
     os.makedirs(OUT, exist_ok=True)
     cc = nvcc()
-    extra = list(extra or [])
+    extra = list(extra or []) + defines
 
     def compile_one(src):
         obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
@@ -73,10 +94,13 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(defines))
     return LIB
 
 
 if __name__ == "__main__":
     v = "-v" in sys.argv
+    tw = int(sys.argv[sys.argv.index("--tile-w") + 1]) if "--tile-w" in sys.argv else None
     print(build(force="-f" in sys.argv, verbose=v,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None, tile_w=tw))

@@ -432,8 +432,8 @@ FrameJob make_job(hexfc_ctx* ctx, FrameBufs* fb, DevMesh* m, float* out)
     j.sil_threshold = ctx->style.sil_threshold;
     j.frame_w = ctx->view.width;
     j.frame_h = ctx->view.height;
-    j.tiles_x = (j.W + kTile - 1) / kTile;
-    j.tiles_y = (j.H + kTile - 1) / kTile;
+    j.tiles_x = (j.W + kTileW - 1) / kTileW;
+    j.tiles_y = (j.H + kTileH - 1) / kTileH;
     j.n_tiles = (int64_t)j.tiles_x * j.tiles_y;
     j.n_pix = j.n_tiles * kTilePix;
     j.reverse = ctx->reverse_bins;
@@ -1366,8 +1366,8 @@ hexfc_status hexfc_render_batch(hexfc_ctx* ctx, int32_t n, const hexfc_batch_ite
         j.delta = it.style.delta;
         j.W = it.view.width;
         j.H = it.view.height;
-        j.tiles_x = (j.W + kTile - 1) / kTile;
-        j.tiles_y = (j.H + kTile - 1) / kTile;
+        j.tiles_x = (j.W + kTileW - 1) / kTileW;
+        j.tiles_y = (j.H + kTileH - 1) / kTileH;
         j.n_tiles = (int64_t)j.tiles_x * j.tiles_y;
         j.n_pix = j.n_tiles * kTilePix;
         j.reverse = ctx->reverse_bins;
@@ -1933,6 +1933,12 @@ hexfc_status hexfc_stage_times(hexfc_ctx* ctx, double* ms, uint64_t* frames, int
 
 int32_t hexfc_last_cuda_error(void) { return t_last_cuda; }
 
+void hexfc_raster_tile(int32_t* width, int32_t* height)
+{
+    if (width) *width = kTileW;
+    if (height) *height = kTileH;
+}
+
 const char* hexfc_cuda_error_name(int32_t code) { return cudaGetErrorName((cudaError_t)code); }
 
 const char* hexfc_status_string(hexfc_status s)
@@ -2005,7 +2011,7 @@ hexfc_status render_frame_noalloc(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_
     const int W = ctx->cam.W, H = ctx->cam.H;   // the drawn rectangle (with its apron)
     const OutWin win = output_window(ctx);
     const bool sil = ctx->style.sil_alpha > 0.f;
-    const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
+    const int tiles_x = (W + kTileW - 1) / kTileW, tiles_y = (H + kTileH - 1) / kTileH;
     const int64_t n_tiles = (int64_t)tiles_x * tiles_y;
     const int64_t n_pix = n_tiles * kTilePix;
     const int64_t nparts = scan_partials_needed(std::max<int64_t>(n_pix, n_tiles)) + 1;

@@ -32,10 +32,11 @@ struct CountWarp {
 
 // Float crossing data of triangle j's edges in the warp's staging slot. e0f
 // is within 0.75 ulp of e0 and fmaf(fb, ry, e0f) adds one rounding, all of
-// magnitudes at most M = |e0| + 16 (|fa| + |fb|): within tol = 8 units of
-// 2^-24 M of the exact value. Dividing by fa (rfa within 0.5 ulp, one more
-// rounding of t) moves t by at most tol |rfa| + 2^-22 |t|, and |t| <= 17
-// wherever it matters (columns 0..15): eps = tol |rfa| (1 + 2^-10) + 2^-17.
+// magnitudes at most M = |e0| + TW |fa| + TH |fb| (tile TW x TH): within
+// tol = 8 units of 2^-24 M of the exact value. Dividing by fa (rfa within 0.5
+// ulp, one more rounding of t) moves t by at most tol |rfa| + 2^-22 |t|, and
+// |t| <= TW + 1 wherever it matters (columns 0..TW-1): eps = tol |rfa|
+// (1 + 2^-10) + 2^-17 for TW <= 16 (17 * 2^-22 < 2^-17), + 2^-16 for TW = 32.
 __device__ __forceinline__ void stage_rows(const CovSoA& c, float4 (*ef)[kChunk], int j)
 {
 #pragma unroll
@@ -43,9 +44,10 @@ __device__ __forceinline__ void stage_rows(const CovSoA& c, float4 (*ef)[kChunk]
         const float e0 = i64_to_f32(c.e0[k][j]);
         const float fa = -256.f * (float)c.dy[k][j];   // exact: |dy| < 2^24
         const float fb = 256.f * (float)c.dx[k][j];
-        const float tol = ldexpf(fabsf(e0) + 16.f * (fabsf(fa) + fabsf(fb)), -21);
+        const float tol = ldexpf(fabsf(e0) + (float)kTileW * fabsf(fa) + (float)kTileH * fabsf(fb), -21);
         const float rfa = fa != 0.f ? __frcp_rn(fa) : 0.f;
-        const float eps = fa != 0.f ? fmaf(tol * fabsf(rfa), 1.f + 0x1p-10f, 0x1p-17f) : tol;
+        constexpr float kTabs = kTileW <= 16 ? 0x1p-17f : 0x1p-16f;
+        const float eps = fa != 0.f ? fmaf(tol * fabsf(rfa), 1.f + 0x1p-10f, kTabs) : tol;
         ef[k][j] = make_float4(e0, fb, rfa, eps);
     }
 }
@@ -169,7 +171,7 @@ __device__ __forceinline__ void count_chunks(CountWarp* s_w, int warp, int lane,
                 const int ry = (int)(idx - sq.x);
                 int lo, hi;
                 row_span(me.c, me.ef, j, ry, box_bw(bx), lo, hi);
-                uint32_t* mrow = &me.mask[(box_ly0(bx) + ry) * kTile + box_lx0(bx)];
+                uint32_t* mrow = &me.mask[(box_ly0(bx) + ry) * kTileW + box_lx0(bx)];
                 for (int rx = lo; rx <= hi; ++rx) atomicOr(mrow + rx, 1u << j);
             }
         }

@@ -8,8 +8,13 @@
 
 namespace hexfc {
 
-constexpr int kTile = 16;                 // raster tile edge in pixels
-constexpr int kTilePix = kTile * kTile;   // pixels (= threads) per tile CTA
+#ifndef HEXFC_TILE_W
+#define HEXFC_TILE_W 16
+#endif
+constexpr int kTilePix = 256;                  // pixels (= threads) per tile CTA
+constexpr int kTileW = HEXFC_TILE_W;           // raster tile width in pixels (a build-time choice)
+constexpr int kTileH = kTilePix / kTileW;      // raster tile height
+static_assert(kTileW == 8 || kTileW == 16 || kTileW == 32, "tiles of 8x32, 16x16 or 32x8 pixels");
 constexpr int kWarpSortMax = 256;         // longest list sorted in registers by one warp
 constexpr uint64_t kPadKey = ~0ull;
 constexpr int kChunk = 32;                // triangles per raster chunk (one coverage bit each)

@@ -1,4 +1,4 @@
-// Tile-capacity network: per 16x16 tile, a 4 -> 64 -> 64 -> 1 ReLU network
+// Tile-capacity network: per raster tile, a 4 -> 64 -> 64 -> 1 ReLU network
 // predicts y ~ log(1 + fragments of the tile) from four features, so that
 // fragment storage can be divided among the tiles before a frame is counted.
 // Weights are used in FP16 (staged in shared memory), sums in FP32; training
@@ -43,7 +43,8 @@ __global__ void k_cap_features(int64_t n_tiles, int tiles_x, const uint32_t* __r
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
-    const float cx = (float)((t % tiles_x) * kTile) + 0.5f * kTile, cy = (float)((t / tiles_x) * kTile) + 0.5f * kTile;
+    const float cx = (float)((t % tiles_x) * kTileW) + 0.5f * kTileW;
+    const float cy = (float)((t / tiles_x) * kTileH) + 0.5f * kTileH;
     const float dx = cx - lens_x, dy = cy - lens_y;
     X[4 * t + 0] = log1pf((float)prev[t]) * (1.f / 12.f);
     X[4 * t + 1] = zr[t];

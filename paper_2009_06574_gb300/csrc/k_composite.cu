@@ -177,8 +177,8 @@ __device__ __forceinline__ void tile_pixel(int64_t q, int tiles_x, int& x, int& 
 {
     int64_t tile = q / kTilePix;
     int local = (int)(q % kTilePix);
-    x = (int)(tile % tiles_x) * kTile + (local & (kTile - 1));
-    y = (int)(tile / tiles_x) * kTile + local / kTile;
+    x = (int)(tile % tiles_x) * kTileW + local % kTileW;
+    y = (int)(tile / tiles_x) * kTileH + local / kTileW;
 }
 
 // The fragments of pixel q, in list order, found by one whole warp (lane i
@@ -555,8 +555,8 @@ __global__ void __launch_bounds__(1024) k_composite_long(const uint32_t* __restr
 // neighbour of the output window (an apron around a sub-rectangle).
 __device__ __forceinline__ uint32_t zsil_at(const uint32_t* __restrict__ zsil, int tiles_x, int x, int y)
 {
-    const int64_t t = (int64_t)(y / kTile) * tiles_x + x / kTile;
-    return zsil[t * kTilePix + (y % kTile) * kTile + (x % kTile)];
+    const int64_t t = (int64_t)(y / kTileH) * tiles_x + x / kTileW;
+    return zsil[t * kTilePix + (y % kTileH) * kTileW + (x % kTileW)];
 }
 
 __global__ void __launch_bounds__(256) k_silhouette(const uint32_t* __restrict__ zsil, int tiles_x, int fx0, int fy0,
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(256) k_debug_short(const uint32_t* __restrict_
     int lane = threadIdx.x & 31;
     if (i >= n_req) return;
     int x = px[i], y = py[i];
-    int64_t q = ((int64_t)(y / kTile) * tiles_x + x / kTile) * kTilePix + (y % kTile) * kTile + (x % kTile);
+    int64_t q = ((int64_t)(y / kTileH) * tiles_x + x / kTileW) * kTilePix + (y % kTileH) * kTileW + (x % kTileW);
     uint32_t n = cnt[q];
     if (n == 0 || n > (uint32_t)kWarpList) return;
     list_walk(tile_off, masks, seg, frag_cap, (uint32_t)q, lane, n, [&](uint32_t k, uint64_t e) {
@@ -644,7 +644,7 @@ __global__ void __launch_bounds__(1024) k_debug_long(const uint32_t* __restrict_
     uint32_t* s_v = reinterpret_cast<uint32_t*>(s_e + HEXFC_MAX_LIST);
     int64_t i = blockIdx.x;
     int x = px[i], y = py[i];
-    int64_t q = ((int64_t)(y / kTile) * tiles_x + x / kTile) * kTilePix + (y % kTile) * kTile + (x % kTile);
+    int64_t q = ((int64_t)(y / kTileH) * tiles_x + x / kTileW) * kTilePix + (y % kTileH) * kTileW + (x % kTileW);
     uint32_t n = cnt[q];
     if (n <= (uint32_t)kWarpList || n > (uint32_t)HEXFC_MAX_LIST) return;
     (void)block_composite(tile_off, masks, seg, frag_cap, key, rgba, (uint32_t)q, n, s_k, s_v, s_e,
@@ -658,7 +658,7 @@ __global__ void k_debug_counts(const uint32_t* __restrict__ cnt, const int32_t* 
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_req) return;
     int x = px[i], y = py[i];
-    int64_t q = ((int64_t)(y / kTile) * tiles_x + x / kTile) * kTilePix + (y % kTile) * kTile + (x % kTile);
+    int64_t q = ((int64_t)(y / kTileH) * tiles_x + x / kTileW) * kTilePix + (y % kTileH) * kTileW + (x % kTileW);
     out[i] = cnt[q];
 }
 

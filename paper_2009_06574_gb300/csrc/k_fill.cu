@@ -202,7 +202,7 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
         const int j = (int)(qe & 31u);
         const uint32_t pl = (qe >> 5) & 255u;
         const FillSlot& S = s_ring[(qe >> 13) & 7u];
-        const int lx = (int)(pl & (kTile - 1)), ly = (int)(pl / kTile);
+        const int lx = (int)(pl % kTileW), ly = (int)(pl / kTileW);
         const ShadeRec& R = S.sh[j];
         const uint4 hd = R.hd, zm = R.zm, wd = R.wd;
         const int4 ev = R.ev;
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill(const uint64_t* __rest
     __shared__ uint64_t s_tile_base;
     __shared__ __align__(8) uint64_t s_full[kRing], s_empty[kRing];
     const int tile = (int)order[blockIdx.x];
-    const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
+    const int px0 = (tile % tiles_x) * kTileW, py0 = (tile / tiles_x) * kTileH;
     const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
     const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kPipeThreads, 3) k_fill_batch(const __grid_con
     if (threadIdx.x == 0) s_it = b.it[i];
     __syncthreads();
     const FillItem& it = s_it;
-    const int px0 = (tile % it.tiles_x) * kTile, py0 = (tile / it.tiles_x) * kTile;
+    const int px0 = (tile % it.tiles_x) * kTileW, py0 = (tile / it.tiles_x) * kTileH;
     const uint64_t beg = it.tile_off[tile], end = it.tile_off[tile + 1];
     const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
     const int64_t q = (int64_t)tile * kTilePix + threadIdx.x;

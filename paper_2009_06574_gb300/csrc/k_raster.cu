@@ -4,7 +4,7 @@
 //                   position snapped to 16.8 fixed point, 24-bit window depth.
 //   k_face_setup    per unique face: gather the 4 projected corners, edge
 //                   visibility masks of Eq. 1, triangle validity, and the
-//                   number of 16x16 tiles each triangle's box touches.
+//                   number of raster tiles each triangle's box touches.
 //   k_bin_fill      per face: append 2*face+tri to the list of every touched tile.
 //   k_bin_sort      per tile: counting sort of the tile's triangles by depth.
 //   k_tile_order    the tiles by decreasing work (for count and fill).
@@ -81,8 +81,8 @@ __device__ __forceinline__ uint32_t agg_inc(uint32_t* ctr, int idx)
 
 __device__ __forceinline__ void tile_range(const TriGeom& t, int& tx0, int& ty0, int& tx1, int& ty1)
 {
-    tx0 = t.bx0 / kTile; tx1 = t.bx1 / kTile;
-    ty0 = t.by0 / kTile; ty1 = t.by1 / kTile;
+    tx0 = t.bx0 / kTileW; tx1 = t.bx1 / kTileW;
+    ty0 = t.by0 / kTileH; ty1 = t.by1 / kTileH;
 }
 
 __global__ void k_face_setup(const int4* __restrict__ fverts, const int4* __restrict__ fedges,
@@ -411,7 +411,7 @@ __device__ __forceinline__ void count_tile(int tile, const uint64_t* __restrict_
     extern __shared__ __align__(16) unsigned char count_smem[];
     CountWarp* s_w = reinterpret_cast<CountWarp*>(count_smem);   // [kConsumerWarps]
     __shared__ uint32_t s_tmp[kConsumerWarps];
-    const int px0 = (tile % tiles_x) * kTile, py0 = (tile / tiles_x) * kTile;
+    const int px0 = (tile % tiles_x) * kTileW, py0 = (tile / tiles_x) * kTileH;
     const uint64_t beg = tile_off[tile], end = tile_off[tile + 1];  // multiples of kChunk
     const uint32_t n_chunks = (uint32_t)((end - beg) / kChunk);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

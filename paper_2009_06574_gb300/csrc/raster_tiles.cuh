@@ -29,8 +29,8 @@ __device__ __forceinline__ void stage_cov(int4 a, int4 b, uint32_t f2t, int W, i
 {
     int32_t X[4] = {a.x, a.y, a.z, a.w}, Y[4] = {b.x, b.y, b.z, b.w};
     tri_setup(X, Y, (int)(f2t & 1), W, H, t);
-    int x0 = max(t.bx0, px0), x1 = min(t.bx1, px0 + kTile - 1);
-    int y0 = max(t.by0, py0), y1 = min(t.by1, py0 + kTile - 1);
+    int x0 = max(t.bx0, px0), x1 = min(t.bx1, px0 + kTileW - 1);
+    int y0 = max(t.by0, py0), y1 = min(t.by1, py0 + kTileH - 1);
     if (!t.valid || x0 > x1 || y0 > y1) {
         c.box[j] = 0;
         return;

@@ -51,7 +51,7 @@ EXPORTS = ["hexfc_style_default", "hexfc_create", "hexfc_destroy", "hexfc_upload
            "hexfc_stage_times", "hexfc_status_string", "hexfc_render_noalloc", "hexfc_share_mesh",
            "hexfc_frame_memory", "hexfc_trim", "hexfc_render_batch", "hexfc_capacity_reset",
            "hexfc_capacity_set_weights", "hexfc_capacity_get_weights", "hexfc_capacity_grad",
-           "hexfc_capacity_train", "hexfc_last_cuda_error", "hexfc_cuda_error_name", "hexfc_finish",
+           "hexfc_capacity_train", "hexfc_last_cuda_error", "hexfc_cuda_error_name", "hexfc_raster_tile", "hexfc_finish",
            "hexfc_completed_stats", "hexfc_set_subrect"]
 
 
@@ -142,6 +142,7 @@ def load():
                 "hexfc_capacity_grad": (i32, [vp, vp, vp, i64, vp, vp]),
                 "hexfc_capacity_train": (i32, [vp, i32, C.c_float, vp, vp]),
                 "hexfc_last_cuda_error": (i32, []),
+                "hexfc_raster_tile": (None, [C.POINTER(i32), C.POINTER(i32)]),
                 "hexfc_cuda_error_name": (C.c_char_p, [i32]),
             }
             for name, (res, args) in sig.items():
@@ -161,6 +162,14 @@ def last_cuda_error():
     L = load()
     code = int(L.hexfc_last_cuda_error())
     return code, L.hexfc_cuda_error_name(code).decode()
+
+
+def raster_tile():
+    """(width, height) in pixels of the loaded library's raster tile."""
+    L = load()
+    w, h = C.c_int32(0), C.c_int32(0)
+    L.hexfc_raster_tile(C.byref(w), C.byref(h))
+    return w.value, h.value
 
 
 def _check(status: int, what: str):

@@ -44,6 +44,9 @@ def test_host_only_entry_points():
     assert L.hexfc_create(None, 0, 0) == hexfc.HEXFC_ERR_ARG
     assert L.hexfc_set_view(None, None) == hexfc.HEXFC_ERR_ARG
     assert L.hexfc_render(None, 0, None, None, None) == hexfc.HEXFC_ERR_ARG
+    w, h = hexfc.raster_tile()   # the build-time tile: 256 pixels
+    assert w * h == 256 and w in (8, 16, 32)
+    L.hexfc_raster_tile(None, None)
 
 
 def test_no_gpu_create_fails_cleanly():
