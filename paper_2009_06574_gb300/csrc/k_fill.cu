@@ -95,9 +95,15 @@ __device__ __forceinline__ void stage_shade(const RawFace& r, uint32_t f2t, cons
     R.pp = make_float4(P[0][2], P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]);
     R.pq = make_float4(P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2], 0.f);
     R.zm = make_uint4(z[0], z[1], z[2], face_edge_flags(r.Z) | (face_boundary(r.Z) << 8));
-    // depth differences below 2^24 in magnitude: exact in float
-    R.wd = make_uint4((uint32_t)c.e0[1][j], (uint32_t)c.e0[2][j], __float_as_uint((float)(int32_t)(z[1] - z[0])),
-                      __float_as_uint((float)(int32_t)(z[2] - z[0])));
+    // the edge functions of vertices 1 and 2 moved from the box origin to the
+    // tile's first sample (low words: exact modulo 2^32, and at a covered
+    // sample of a small triangle the value itself lies in [0, area]); depth
+    // differences below 2^24 in magnitude: exact in float
+    const int bx = c.box[j];
+    const uint32_t ox = (uint32_t)box_lx0(bx) << 8, oy = (uint32_t)box_ly0(bx) << 8;
+    const uint32_t w1 = (uint32_t)c.e0[1][j] - (uint32_t)c.dx[1][j] * oy + (uint32_t)c.dy[1][j] * ox;
+    const uint32_t w2 = (uint32_t)c.e0[2][j] - (uint32_t)c.dx[2][j] * oy + (uint32_t)c.dy[2][j] * ox;
+    R.wd = make_uint4(w1, w2, __float_as_uint((float)(int32_t)(z[1] - z[0])), __float_as_uint((float)(int32_t)(z[2] - z[0])));
     R.ev = make_int4(c.dx[1][j], c.dy[1][j], c.dx[2][j], c.dy[2][j]);
     R.hd = make_uint4((uint32_t)c.box[j], f2t, t.area < (1ll << 26) ? (uint32_t)t.area : 0u,
                       __float_as_uint(1.f / u64_to_f32((uint64_t)t.area)));
@@ -198,7 +204,6 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
     uint32_t head = 0, tail = 0, released = 0;
     auto shade_entry = [&](uint32_t qe, uint32_t e) {
         if (!(qe & kCounted) || e >= w_len) return;
-        const uint64_t o = w_beg + e;
         const int j = (int)(qe & 31u);
         const uint32_t pl = (qe >> 5) & 255u;
         const FillSlot& S = s_ring[(qe >> 13) & 7u];
@@ -206,21 +211,22 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
         const ShadeRec& R = S.sh[j];
         const uint4 hd = R.hd, zm = R.zm, wd = R.wd;
         const int4 ev = R.ev;
-        const int bx = (int)hd.x;
         // exact weights of vertices 1 and 2 (edge functions opposite them)
-        const int32_t sxr = (lx - box_lx0(bx)) << 8, syr = (ly - box_ly0(bx)) << 8;
+        const uint32_t sx8 = (uint32_t)lx << 8, sy8 = (uint32_t)ly << 8;
         const float ia = __uint_as_float(hd.w);
         const float dz1 = __uint_as_float(wd.z), dz2 = __uint_as_float(wd.w);
         float lam1, lam2;
         uint32_t z;
         if (hd.z != 0) {   // 0 <= l <= area < 2^26: the weights in 32-bit arithmetic (exact mod 2^32)
-            const uint32_t l1 = wd.x + (uint32_t)ev.x * (uint32_t)syr - (uint32_t)ev.y * (uint32_t)sxr;
-            const uint32_t l2 = wd.y + (uint32_t)ev.z * (uint32_t)syr - (uint32_t)ev.w * (uint32_t)sxr;
+            const uint32_t l1 = wd.x + (uint32_t)ev.x * sy8 - (uint32_t)ev.y * sx8;
+            const uint32_t l2 = wd.y + (uint32_t)ev.z * sy8 - (uint32_t)ev.w * sx8;
             lam1 = (float)l1 * ia;
             lam2 = (float)l2 * ia;
             z = sample_depth_small(zm.x, zm.y, zm.z, l1, l2, hd.z, lam1, lam2, dz1, dz2, bad);
         } else {
             const int64_t area = S.area[j];
+            const int bx = (int)hd.x;
+            const int32_t sxr = (lx - box_lx0(bx)) << 8, syr = (ly - box_ly0(bx)) << 8;
             const int64_t l1 = S.c.e0[1][j] + (int64_t)ev.x * syr - (int64_t)ev.y * sxr;
             const int64_t l2 = S.c.e0[2][j] + (int64_t)ev.z * syr - (int64_t)ev.w * sxr;
             lam1 = u64_to_f32((uint64_t)l1) * ia;
@@ -228,6 +234,7 @@ __device__ __forceinline__ void fill_tile(unsigned char* smem, const uint64_t* s
             z = sample_depth_lam(zm.x, zm.y, zm.z, l1, l2, area, lam1, lam2, dz1, dz2, bad);
         }
         const float4 col = shade_fragment(R, zm.w, lam1, lam2, px0 + lx, py0 + ly, sp);
+        const uint64_t o = w_beg + e;
         key[o] = ((uint64_t)z << 32) | (uint64_t)hd.y;
         rgba[o] = col;
         // the boundary surface's depth image (silhouettes): nearest boundary fragment

@@ -26,7 +26,7 @@ struct ShadeRec {
     float4 pp;       // p0.z; dp1.x, dp1.y, dp1.z
     float4 pq;       // dp2.x, dp2.y, dp2.z; unused
     uint4 zm;        // window depth of the three vertices; face edge flags (bits 0-3 focus, 4-7 context)
-    uint4 wd;        // low words of the edge functions of vertices 1, 2 at the box origin; dz1, dz2 (float bits)
+    uint4 wd;        // low words of the edge functions of vertices 1, 2 at the tile's first sample; dz1, dz2 (float bits)
     int4 ev;         // dx, dy of the edges opposite vertices 1 and 2 (16.8)
     uint4 hd;        // box (as CovSoA::box), f2t, twice the area if below 2^26 else 0, 1 / twice the area (float bits)
 };
