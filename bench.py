@@ -37,7 +37,7 @@ FRAG_BYTES = 24          # 8 B key + 16 B premultiplied RGBA
 # DRAM traffic of one k_fill launch (ncu dram__bytes_read.sum + dram__bytes_write.sum,
 # one pass, on the 1920x1080 bench frame), per fragment drawn, and the fill kernel's
 # sources it was taken on: the roofline reports it only while those sources are unchanged.
-FILL_DRAM = {"bytes_per_fragment": 27.62,
+FILL_DRAM = {"bytes_per_fragment": 27.64,
              "sha256": "d1b7416779726e2792f33809a681b10d03af9899d76a6013a4ad950d9f41a3eb",
              "profile": "profiles/dram_k_fill_grid64_orbit_1080p.md"}
 FILL_SOURCES = ("csrc/k_fill.cu", "csrc/raster_tiles.cuh", "csrc/shade.cuh", "csrc/raster_common.cuh",
