@@ -84,6 +84,7 @@ struct hexfc_ctx {
     std::vector<std::unique_ptr<BatchSlot>> batch;
     cudaStream_t origin = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_p1 = nullptr;   // a single frame's phase 1: bin total copied (FrameJob::p1_done)
     cudaGraphExec_t graph_exec[3] = {nullptr, nullptr, nullptr};
     uint64_t graph_instantiations = 0, graph_updates = 0;
 };
@@ -360,6 +361,11 @@ struct FrameJob {
     float sil_alpha = 0.f, sil_threshold = 0.f;   // silhouettes (off at alpha 0)
     int frame_w = 0, frame_h = 0;  // the view's frame, which the drawn rectangle is a part of
     hexfc_ctx* timing = nullptr;   // stage events of the single-frame path
+    // single-frame path: phase 1 records this event once its bin total is on the
+    // way to the host and then orders the tiles (which needs only the tile
+    // offsets), so that the tile order runs while the host waits and allocates
+    cudaEvent_t p1_done = nullptr;
+    bool order_done = false;
     uint32_t launches = 0;
     uint64_t n_bins = 0, total = 0;
     uint32_t max_list = 0, n_long = 0;
@@ -536,6 +542,23 @@ hexfc_status job_phase1(FrameJob& j, cudaStream_t s)
     job_mark(j, 3, s);
     j.launches = 5;
     CK(cudaMemcpyAsync(fb.h_scal + 8, fb.scal + 8, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    j.order_done = false;
+    if (j.p1_done) {
+        CK(cudaEventRecord(j.p1_done, s));
+        CK(launch_tile_order(fb, j.n_tiles, s));
+        j.order_done = true;
+        j.launches += 1;
+    }
+    return HEXFC_OK;
+}
+
+// The host's wait for phase 1: for its bin total only (the tile order may
+// still run), unless a pending frame is to be verified and perhaps drawn again
+// in the same buffers first.
+hexfc_status job_wait1(const hexfc_ctx* ctx, const FrameJob& j, cudaStream_t s)
+{
+    if (j.p1_done && !ctx->pend.active) CK(cudaEventSynchronize(j.p1_done));
+    else CK(cudaStreamSynchronize(s));
     return HEXFC_OK;
 }
 
@@ -564,8 +587,11 @@ hexfc_status job_phase2_bins(FrameJob& j, cudaStream_t s)
     CK(cudaMemsetAsync(fb.bins, 0xFF, sizeof(uint32_t) * (size_t)j.n_bins, s));   // padding slots = kPadBin
     CK(launch_bin_fill(*j.m, fb, j.tiles_x, j.W, j.H, j.reverse, s));
     CK(launch_bin_sort(*j.m, fb, j.tiles_x, j.tiles_y, j.buckets, s));
-    CK(launch_tile_order(fb, j.n_tiles, s));
-    j.launches += 3;
+    if (!j.order_done) {
+        CK(launch_tile_order(fb, j.n_tiles, s));
+        j.launches += 1;
+    }
+    j.launches += 2;
     hexfc_status fst = job_features(j, s);
     if (fst != HEXFC_OK) return fst;
     job_mark(j, 5, s);
@@ -791,15 +817,17 @@ hexfc_status render_frame(hexfc_ctx* ctx, DevMesh* m, float* out, hexfc_frame_st
             for (auto& e : set) CK(cudaEventCreate(&e));
     ctx->ev_cur ^= 1;
     j.timing = ctx;
+    if (!ctx->ev_p1) CK(cudaEventCreateWithFlags(&ctx->ev_p1, cudaEventDisableTiming));
+    j.p1_done = ctx->ev_p1;
     if ((st = job_phase1(j, s)) != HEXFC_OK) return st;
-    CK(cudaStreamSynchronize(s));
+    if ((st = job_wait1(ctx, j, s)) != HEXFC_OK) return st;
     collect(ctx);
     if (ctx->pend.active) {   // the previous frame (chosen capacities) has completed: verify it
         bool redrawn = false;
         if ((st = settle_pending(ctx, s, &redrawn)) != HEXFC_OK) return st;
         if (redrawn) {   // it was drawn again in these buffers: this frame's first passes once more
             if ((st = job_phase1(j, s)) != HEXFC_OK) return st;
-            CK(cudaStreamSynchronize(s));
+            if ((st = job_wait1(ctx, j, s)) != HEXFC_OK) return st;
         }
     }
     if ((st = job_read1(j)) != HEXFC_OK) return st;
@@ -872,8 +900,10 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
             for (auto& e : set) CK(cudaEventCreate(&e));
     ctx->ev_cur ^= 1;
     j.timing = ctx;
+    if (!ctx->ev_p1) CK(cudaEventCreateWithFlags(&ctx->ev_p1, cudaEventDisableTiming));
+    j.p1_done = ctx->ev_p1;
     if ((st = job_phase1(j, s)) != HEXFC_OK) return st;
-    CK(cudaStreamSynchronize(s));
+    if ((st = job_wait1(ctx, j, s)) != HEXFC_OK) return st;
     collect(ctx);
     if (ctx->pend.active) {   // the previous frame has completed: verify it
         bool redrawn = false;
@@ -882,7 +912,7 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
             if (ctx->predicted == 1 && (ctx->counts_W != j.W || ctx->counts_H != j.H))
                 return render_frame(ctx, m, out, stats, s);
             if ((st = job_phase1(j, s)) != HEXFC_OK) return st;
-            CK(cudaStreamSynchronize(s));
+            if ((st = job_wait1(ctx, j, s)) != HEXFC_OK) return st;
         }
     }
     if ((st = job_read1(j)) != HEXFC_OK) return st;
@@ -902,7 +932,7 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     CK(cudaMemsetAsync(fb.bins, 0xFF, sizeof(uint32_t) * (size_t)j.n_bins, s));   // padding slots = kPadBin
     CK(launch_bin_fill(*m, fb, j.tiles_x, j.W, j.H, j.reverse, s));
     CK(launch_bin_sort(*m, fb, j.tiles_x, j.tiles_y, j.buckets, s));
-    CK(launch_tile_order(fb, j.n_tiles, s));
+    if (!j.order_done) CK(launch_tile_order(fb, j.n_tiles, s));
     if ((st = job_features(j, s)) != HEXFC_OK) return st;
     // stages: bin (with the features, the capacities and their scan), count,
     // then no pixel scan and no host wait, fill, composite
@@ -926,7 +956,7 @@ hexfc_status render_frame_predicted(hexfc_ctx* ctx, DevMesh* m, float* out, hexf
     CK(launch_composite(fb, j.sp, j.tiles_x, j.tiles_y, j.W, j.H, out, kLongListsUnknown, j.window, j.win, s));
     if ((st = job_silhouette(j, out, s)) != HEXFC_OK) return st;
     job_mark(j, 10, s);
-    j.launches += 4 + 1 + 3 + 1 + 1 + 3;
+    j.launches += (j.order_done ? 3 : 4) + 1 + 3 + 1 + 1 + 3;   // (the tile order counted by phase 1)
     // the frame's scalars and count statistics for its verification; no wait here
     CK(cudaMemcpyAsync(ctx->h_pend, fb.scal, kScal * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(ctx->h_pend + kScal, fb.cstat, 4 * kStatCopies * sizeof(uint64_t), cudaMemcpyDeviceToHost,
@@ -1247,6 +1277,7 @@ void hexfc_destroy(hexfc_ctx* ctx)
     if (ctx->origin) cudaStreamDestroy(ctx->origin);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+    if (ctx->ev_p1) cudaEventDestroy(ctx->ev_p1);
     dfree(ctx->d_out);
     for (auto& set : ctx->ev)
         for (auto& e : set)
