@@ -423,6 +423,9 @@ def run_ours(args, rank, world, local_rank):
                 ("secondary_batch", lambda: run_batch(args, rank, world, steps=10, warmup=3)),
                 ("secondary_serving", lambda: run_serving(args, rank, world)))
         for key, fn in legs:
+            import gc
+            gc.collect()
+            torch.cuda.empty_cache()   # the cached blocks of the legs before go back to the driver
             sampler = ClockSampler(uuid)
             sampler.start()
             try:
