@@ -19,6 +19,17 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libhexfc.so")
 
+
+def out_dir() -> str:
+    """Where the library is built: in-tree, unless HEXFC_BUILD_DIR names
+    another folder (a second build, e.g. of another raster tile, beside the
+    in-tree one)."""
+    return os.environ.get("HEXFC_BUILD_DIR") or OUT
+
+
+def lib_file() -> str:
+    return os.path.join(out_dir(), "libhexfc.so")
+
 SOURCES = ["api.cu", "k_quality.cu", "k_raster.cu", "k_fill.cu", "k_scan.cu", "k_composite.cu", "k_capacity.cu", "mesh_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",
@@ -39,7 +50,8 @@ def _inputs():
     return files
 
 
-STAMP = os.path.join(OUT, "config.txt")
+def stamp_file() -> str:
+    return os.path.join(out_dir(), "config.txt")
 
 
 def tile_defines(tile_w: int | None = None) -> list[str]:
@@ -53,29 +65,31 @@ def tile_defines(tile_w: int | None = None) -> list[str]:
 
 
 def stale(defines: list[str] | None = None) -> bool:
-    if not os.path.exists(LIB):
+    lib = lib_file()
+    if not os.path.exists(lib):
         return True
     try:
-        with open(STAMP) as f:
+        with open(stamp_file()) as f:
             if f.read() != " ".join(defines or tile_defines()):
                 return True
     except OSError:
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _inputs())
 
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
           tile_w: int | None = None) -> str:
     defines = tile_defines(tile_w)
+    out, lib = out_dir(), lib_file()
     if not force and not stale(defines):
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+        return lib
+    os.makedirs(out, exist_ok=True)
     cc = nvcc()
     extra = list(extra or []) + defines
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(out, os.path.splitext(src)[0] + ".o")
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -88,15 +102,15 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    with open(STAMP, "w") as f:
+    os.replace(tmp, lib)
+    with open(stamp_file(), "w") as f:
         f.write(" ".join(defines))
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

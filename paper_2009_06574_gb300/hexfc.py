@@ -100,7 +100,7 @@ _lock = threading.Lock()
 
 
 def lib_path() -> str:
-    return _build.LIB
+    return _build.lib_file()
 
 
 def load():
