@@ -496,3 +496,30 @@ def test_silhouettes_match_oracle(hx, lens_mode):
     torch.cuda.synchronize()
     assert torch.equal(part, out[30:71, 40:100])
     r.close()
+
+
+def test_camera_inside_the_mesh(hx):
+    """The eye inside a warped grid, looking across it with a wide lens: many
+    triangles have a corner behind the near plane and are culled (no clipping),
+    the rest cover the frame; every pixel against the oracle."""
+    mesh = synth.hex_grid(6, jitter=0.1, warp_amp=0.25, seed=21)
+    view = synth.View(eye=(0.04, 0.03, 0.12), target=(0.35, -0.1, -0.45), up=(0.0, 1.0, 0.0), fovy_deg=75.0,
+                      znear=0.02, zfar=4.0, width=120, height=90)
+    for lens in (synth.Lens(mode=synth.LENS_SPHERE, center=(0.2, 0.0, -0.2), radius=0.25),
+                 synth.Lens(mode=synth.LENS_SCREEN, center=(60.0, 45.0, 0.0), radius=30.0)):
+        st, _ = render_both(hx, mesh, view, lens, synth.Style(w_base=1.5, lod=2))
+        assert st["fragments"] > 20000
+
+
+def test_guard_band_culling(hx):
+    """A long lens (0.1 degree) on a grid: corners off the axis project beyond
+    the 2^14-pixel guard band, and every triangle with such a corner is culled
+    on both sides, even where part of it would be on screen."""
+    mesh = synth.hex_grid(4, jitter=0.1, warp_amp=0.2, seed=22)
+    # 85 of the 125 corners are beyond the guard band; of the cells whose
+    # corners' box meets the frame, 2 have such a corner and 6 do not
+    view = synth.View(eye=(0.9, 0.7, 2.6), target=(0.03, 0.02, 0.0), up=(0.0, 1.0, 0.0), fovy_deg=0.03,
+                      znear=0.5, zfar=6.0, width=96, height=72)
+    st, _ = render_both(hx, mesh, view, synth.Lens(mode=synth.LENS_SCREEN, center=(48.0, 36.0, 0.0), radius=20.0),
+                        synth.Style(w_base=1.5, lod=1))
+    assert st["fragments"] > 0
