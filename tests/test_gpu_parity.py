@@ -523,3 +523,24 @@ def test_guard_band_culling(hx):
     st, _ = render_both(hx, mesh, view, synth.Lens(mode=synth.LENS_SCREEN, center=(48.0, 36.0, 0.0), radius=20.0),
                         synth.Style(w_base=1.5, lod=1))
     assert st["fragments"] > 0
+
+
+@pytest.mark.parametrize("shape", [(16384, 24), (24, 16384)])
+def test_maximum_frame_size(hx, shape):
+    """The widest and the tallest frame a view allows (16384 pixels): a long
+    lens makes a warped 32^3 grid span the frame, and sampled pixels plus the
+    last 24 columns or rows (16.8 coordinates near 2^22, float sample offsets
+    still exact) match the oracle."""
+    W, H = shape
+    mesh = synth.hex_grid(32, jitter=0.1, warp_amp=0.25, seed=23)
+    # 40000 pixels per unit at distance 1: the grid runs past the far end of the
+    # frame, where the triangles with every corner inside the guard band still
+    # cover some of the last 24 columns or rows (about 300-400 of their pixels)
+    fovy = math.degrees(2.0 * math.atan((H / 2.0) / 40000.0))
+    view = synth.View(eye=(0.35, 0.25, 2.0), target=(0.0, 0.0, 0.0), up=(0.0, 1.0, 0.0), fovy_deg=fovy,
+                      znear=0.5, zfar=5.0, width=W, height=H)
+    rng = np.random.default_rng(5)
+    edge = (W - 24, 0, 24, H) if W > H else (0, H - 24, W, 24)
+    px, py = _sample_with_crops(rng, W, H, 1500, [edge])
+    st, _ = render_both(hx, mesh, view, synth.lissajous_lens(3, 120), synth.Style(w_base=1.5, lod=2), px=px, py=py)
+    assert st["fragments"] > 2000
