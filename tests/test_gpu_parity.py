@@ -544,3 +544,25 @@ def test_maximum_frame_size(hx, shape):
     px, py = _sample_with_crops(rng, W, H, 1500, [edge])
     st, _ = render_both(hx, mesh, view, synth.lissajous_lens(3, 120), synth.Style(w_base=1.5, lod=2), px=px, py=py)
     assert st["fragments"] > 2000
+
+
+def test_degenerate_cells(hx):
+    """Collapsed geometry: in half of a 5^3 grid the vertex layer k = 3 is moved
+    onto layer k = 2 (flat cells: their side faces have zero area, and two
+    distinct faces lie exactly on top of each other, so equal depths are
+    ordered by face id), and some vertices of layer k = 1 onto a neighbour
+    (faces with two coincident corners, one triangle of zero area); every pixel
+    against the oracle."""
+    n = 5
+    mesh = synth.hex_grid(n, jitter=0.1, warp_amp=0.2, seed=24)
+    v = mesh.verts.copy()
+    n1 = n + 1
+    for j in range(n1):
+        for i in range(n1 // 2 + 1):
+            v[i + n1 * (j + n1 * 3)] = v[i + n1 * (j + n1 * 2)]
+    for j in range(0, n1, 2):
+        v[1 + n1 * (j + n1 * 1)] = v[2 + n1 * (j + n1 * 1)]
+    flat = synth.HexMesh(v, mesh.cells, mesh.cell_scalar, mesh.edge_level)
+    for view in (synth.orbit_view(17, 120, 110, 90, radius=1.7), synth.orbit_view(70, 120, 110, 90, radius=1.7)):
+        st, _ = render_both(hx, flat, view, synth.lissajous_lens(17, 120), synth.Style(w_base=1.5, lod=1))
+        assert st["fragments"] > 10000
