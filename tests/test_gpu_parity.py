@@ -566,3 +566,17 @@ def test_degenerate_cells(hx):
     for view in (synth.orbit_view(17, 120, 110, 90, radius=1.7), synth.orbit_view(70, 120, 110, 90, radius=1.7)):
         st, _ = render_both(hx, flat, view, synth.lissajous_lens(17, 120), synth.Style(w_base=1.5, lod=1))
         assert st["fragments"] > 10000
+
+
+@pytest.mark.parametrize("fovy", [0.0, 40.0])
+def test_near_and_far_planes_cut_the_mesh(hx, fovy):
+    """Near and far planes through the grid (orthographic and perspective):
+    a triangle with a corner outside [near, far] is culled on both sides
+    (no clipping), so the frame shows the middle slab of the grid's faces and
+    the faces that straddle a plane vanish; every pixel against the oracle."""
+    mesh = synth.hex_grid(6, jitter=0.1, warp_amp=0.25, seed=25)
+    view = synth.View(eye=(0.6, 0.5, 1.8), target=(0.0, 0.0, 0.0), up=(0.0, 1.0, 0.0), fovy_deg=fovy,
+                      ortho_half_h=0.8, znear=1.9, zfar=2.5, width=100, height=80)
+    st, _ = render_both(hx, mesh, view, synth.Lens(mode=synth.LENS_SPHERE, center=(0.1, 0.0, 0.1), radius=0.35),
+                        synth.Style(w_base=1.5, lod=2))
+    assert st["fragments"] > 5000
