@@ -92,3 +92,23 @@ def check_sampled(r, mesh, view, lens, style, image, n: int = 1500, seed: int = 
     o = om.render(view, lens, style, px, py)
     img = image.cpu().numpy() if hasattr(image, "cpu") else np.asarray(image)
     return compare_lists(g, o, om, view, lens, style, px, py, gpu_image=img[py, px])
+
+
+def hex_rotations():
+    """The 24 proper rotations of a hexahedron as permutations of its VTK
+    corners (new corner i = old corner s[i]) and of its local edges."""
+    pos = [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0), (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]
+    edges = [(0, 1), (1, 2), (2, 3), (3, 0), (4, 5), (5, 6), (6, 7), (7, 4), (0, 4), (1, 5), (2, 6), (3, 7)]
+    out = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product([1, -1], repeat=3):
+            m = np.zeros((3, 3), int)
+            for row, (col, sg) in enumerate(zip(perm, signs)):
+                m[row, col] = sg
+            if round(np.linalg.det(m)) != 1:
+                continue
+            s = [pos.index(tuple(((m @ (2 * np.array(p) - 1) + 1) // 2).tolist())) for p in pos]
+            e = [next(k for k, (x, y) in enumerate(edges) if {x, y} == {s[a], s[b]}) for (a, b) in edges]
+            out.append((s, e))
+    assert len(out) == 24
+    return out

@@ -11,7 +11,7 @@ import pytest
 import oracle
 from paper_2009_06574_gb300 import synth
 
-from parity import TOL, compare_lists
+from parity import TOL, compare_lists, hex_rotations
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -580,3 +580,36 @@ def test_near_and_far_planes_cut_the_mesh(hx, fovy):
     st, _ = render_both(hx, mesh, view, synth.Lens(mode=synth.LENS_SPHERE, center=(0.1, 0.0, 0.1), radius=0.35),
                         synth.Style(w_base=1.5, lod=2))
     assert st["fragments"] > 5000
+
+
+def test_cell_corner_order_invariance(hx):
+    """Every cell's corners listed in another of the hexahedron's 24 proper
+    orders (its edge levels permuted to match): the same unique faces, split on
+    the same diagonals, so keys and image are bit-identical, and the oracle
+    agrees on the rotated mesh."""
+    mesh = synth.hex_grid(6, jitter=0.15, warp_amp=0.25, seed=26)
+    rots = hex_rotations()
+    pick = np.random.default_rng(7).integers(0, 24, mesh.n_cells)
+    s = np.array([rots[k][0] for k in pick])
+    e = np.array([rots[k][1] for k in pick])
+    rows = np.arange(mesh.n_cells)[:, None]
+    rotated = synth.HexMesh(mesh.verts, mesh.cells[rows, s], mesh.cell_scalar, mesh.edge_level[rows, e])
+    view, lens = synth.orbit_view(33, 120, 112, 84), synth.lissajous_lens(33, 120)
+    style = synth.Style(w_base=1.5, lod=2)
+    keys, imgs = [], []
+    for m in (mesh, rotated):
+        r = hx.Renderer(0)
+        mid = r.upload_mesh(m.verts, m.cells, m.cell_scalar, m.edge_level)
+        r.set_view(view)
+        r.set_lens(lens)
+        r.set_style(style)
+        o = torch.zeros((84, 112, 4), device="cuda")
+        r.render(mid, o)
+        torch.cuda.synchronize()
+        yy, xx = np.meshgrid(np.arange(84), np.arange(112), indexing="ij")
+        keys.append(r.debug_pixels(xx.ravel(), yy.ravel())["keys"])
+        imgs.append(o.cpu().numpy())
+        r.close()
+    assert np.array_equal(keys[0], keys[1])
+    assert np.array_equal(imgs[0], imgs[1])
+    render_both(hx, rotated, view, lens, style)
