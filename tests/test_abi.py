@@ -58,3 +58,23 @@ def test_no_gpu_create_fails_cleanly():
     assert hexfc.load().hexfc_create(ctypes.byref(h), 0, 0) == hexfc.HEXFC_ERR_CUDA
     code, name = hexfc.last_cuda_error()   # the failed device query, by name
     assert code != 0 and name.startswith("cudaError")
+
+
+def test_tile_build_options(tmp_path, monkeypatch):
+    """The raster tile is chosen at build time: 8, 16 (default) or 32 pixels
+    wide (always 256 pixels); anything else is refused before nvcc runs, and a
+    build folder of its own keeps another tile's library apart."""
+    from paper_2009_06574_gb300 import build
+    monkeypatch.delenv("HEXFC_TILE_W", raising=False)
+    monkeypatch.delenv("HEXFC_BUILD_DIR", raising=False)
+    assert build.tile_defines() == ["-DHEXFC_TILE_W=16"]
+    assert build.tile_defines(32) == ["-DHEXFC_TILE_W=32"]
+    monkeypatch.setenv("HEXFC_TILE_W", "8")
+    assert build.tile_defines() == ["-DHEXFC_TILE_W=8"]
+    for bad in (4, 12, 64):
+        with pytest.raises(ValueError):
+            build.tile_defines(bad)
+    assert build.lib_file() == build.LIB
+    monkeypatch.setenv("HEXFC_BUILD_DIR", str(tmp_path))
+    assert build.lib_file() == str(tmp_path / "libhexfc.so")
+    assert build.stale()   # nothing built there yet
