@@ -40,6 +40,12 @@ FRAG_BYTES = 24          # 8 B key + 16 B premultiplied RGBA
 FILL_DRAM = {"bytes_per_fragment": 27.64,
              "sha256": "d1b7416779726e2792f33809a681b10d03af9899d76a6013a4ad950d9f41a3eb",
              "profile": "profiles/dram_k_fill_grid64_orbit_1080p.md"}
+# Warp instructions the fill executes per fragment (ncu smsp__inst_executed.sum on
+# the same frames and sources): its issue roofline, beside the HBM one.
+FILL_ISSUE = {"warp_instructions_per_fragment": 11.126,
+              "sha256": FILL_DRAM["sha256"],
+              "profile": "profiles/issue_k_fill_grid64_orbit_1080p.md"}
+SCHEDULERS_PER_SM = 4    # warp schedulers (issue slots per cycle) of a Blackwell SM
 FILL_SOURCES = ("csrc/k_fill.cu", "csrc/raster_tiles.cuh", "csrc/shade.cuh", "csrc/raster_common.cuh",
                 "csrc/pipeline.cuh", "csrc/hexfc_internal.cuh")
 
@@ -446,6 +452,18 @@ def run_ours(args, rank, world, local_rank):
         except Exception as e:  # the GPU number stands on its own
             cpu = {"value": None, "unit": "frames/s", "cores": omp_threads(), "kind": "oracle",
                    "sample": f"failed: {e}"}
+    # the fill's issue roofline: the warp instructions it executes (an ncu count
+    # on the same sources) over one per scheduler and cycle at the sampled clock
+    fill_issue = None
+    if fill_sources_sha256() == FILL_ISSUE["sha256"]:
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        inst = FILL_ISSUE["warp_instructions_per_fragment"] * F
+        rate = inst / (kernel_stages["fill"] / 1000.0)
+        limit = n_sm * SCHEDULERS_PER_SM * sm_mhz * 1e6
+        fill_issue = {"bound": "issue", "kernel": "k_fill", "achieved": rate, "peak": limit,
+                      "unit": "warp instructions/s", "frac": rate / limit, "instructions_per_frame": inst,
+                      "source": FILL_ISSUE["profile"]}
     line = {
         "metric": "frames/s", "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -464,6 +482,7 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / peak, "traffic": traffic,
                      "traffic_source": FILL_DRAM["profile"] if traffic else None,
                      "peak_kind": peak_kind, "algorithmic_bytes": algo[dom]},
+        "fill_issue": fill_issue,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         "secondary_4k": sec,
         **secondaries,
