@@ -210,14 +210,25 @@ def run_reference(args, rank, world):
     om = oracle.Mesh(mesh.verts, mesh.cells, mesh.cell_scalar, mesh.edge_level)
     npx = w.width * w.height
     rng = np.random.default_rng(1)
-    # calibrate the per-step sample so that the whole run stays within ~2 minutes
+    # a call costs a per-frame setup (projecting the vertices, setting up the
+    # triangles) plus a cost per pixel: both are calibrated, and the per-step
+    # sample is sized so that the whole run stays within ~2 minutes
     budget = 120.0 / max(1, args.steps + args.warmup)
     view, lens = w.view(0), w.lens(0)
-    t0 = time.perf_counter()
-    om.render(view, lens, w.style, np.array([1], np.int32), np.array([1], np.int32), fragments=False)
-    per_px = max(time.perf_counter() - t0, 1e-4)
-    n = max(1, int(budget / per_px))
-    tot_px, tot_t = 0, 0.0
+
+    def timed(n_px):
+        px = rng.integers(0, w.width, n_px).astype(np.int32)
+        py = rng.integers(0, w.height, n_px).astype(np.int32)
+        t0 = time.perf_counter()
+        om.render(view, lens, w.style, px, py, fragments=False)
+        return time.perf_counter() - t0
+
+    t1 = timed(1)
+    t64 = timed(64)
+    per_px = max((t64 - t1) / 63.0, 1e-6)
+    setup = max(t1 - per_px, 0.0)
+    n = max(1, int(max(budget - setup, per_px) / per_px))
+    tot_px, tot_t, steps = 0, 0.0, 0
     for i in range(args.warmup + args.steps):
         f = i % w.n_frames
         px = rng.integers(0, w.width, n).astype(np.int32)
@@ -228,8 +239,13 @@ def run_reference(args, rank, world):
         if i >= args.warmup:
             tot_px += n
             tot_t += dt
-    fps = (tot_px / npx) / tot_t
-    sample = f"{n} random pixels of each orbit frame per step (brute force over all triangles)"
+            steps += 1
+    # a whole frame: one setup and every pixel (the per-pixel cost from the
+    # timed steps, less their setups)
+    per_px_run = max((tot_t - steps * setup) / max(tot_px, 1), per_px * 0.5)
+    fps = 1.0 / (setup + npx * per_px_run)
+    sample = (f"{n} random pixels of each orbit frame per step (brute force over all triangles); "
+              f"a frame = one setup ({setup * 1e3:.1f} ms) + {npx} pixels at {per_px_run * 1e3:.3f} ms")
     line = {"impl": "reference", "metric": "frames/s", "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
