@@ -38,7 +38,7 @@ FRAG_BYTES = 24          # 8 B key + 16 B premultiplied RGBA
 # one pass, on the 1920x1080 bench frame), per fragment drawn, and the fill kernel's
 # sources it was taken on: the roofline reports it only while those sources are unchanged.
 FILL_DRAM = {"bytes_per_fragment": 27.64,
-             "sha256": "d1b7416779726e2792f33809a681b10d03af9899d76a6013a4ad950d9f41a3eb",
+             "sha256": "97e08b9a25a9387f9f365102441d5c877818a94eeb32062b8886111206668b41",
              "profile": "profiles/dram_k_fill_grid64_orbit_1080p.md"}
 # Warp instructions the fill executes per fragment (ncu smsp__inst_executed.sum on
 # the same frames and sources): its issue roofline, beside the HBM one.

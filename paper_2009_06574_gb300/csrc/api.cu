@@ -1334,7 +1334,7 @@ hexfc_status hexfc_upload_mesh(hexfc_ctx* ctx, const float* verts, int64_t n_ver
     H2D(m->fbound, t.fbound.data(), t.fbound.size());
     if (cell_scalar) H2D(m->cell_imp, cell_scalar, sizeof(float) * (size_t)n_cells);
     if (e == cudaSuccess && !cell_scalar) e = launch_cell_quality(*m, HEXFC_METRIC_IMPORTANCE, m->cell_imp, 0);
-    if (e == cudaSuccess) e = launch_importance(*m, 0);
+    if (e == cudaSuccess) e = launch_importance(*m, true, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         note_cuda(e);
@@ -1670,7 +1670,7 @@ hexfc_status hexfc_set_cell_importance(hexfc_ctx* ctx, int32_t mesh, const float
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(m->cell_imp, cell_importance, sizeof(float) * (size_t)m->n_cells, cudaMemcpyDeviceToDevice, s));
-    CK(launch_importance(*m, s));
+    CK(launch_importance(*m, false, s));   // positions unchanged since the upload
     return HEXFC_OK;
 }
 

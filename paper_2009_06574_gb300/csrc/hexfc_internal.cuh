@@ -259,7 +259,9 @@ static_assert(sizeof(FillBatch) < 30000 && sizeof(CompositeBatch) < 30000 && siz
 
 // ---- launches (each returns cudaGetLastError()) -----------------------------------------
 cudaError_t launch_cell_quality(const DevMesh& m, int metric, float* out, cudaStream_t s);
-cudaError_t launch_importance(const DevMesh& m, cudaStream_t s);
+// Vertex and edge importance (max over cells) and the faces' static records;
+// positions: also the corners' world positions (once, at the upload).
+cudaError_t launch_importance(const DevMesh& m, bool positions, cudaStream_t s);
 
 cudaError_t launch_vertex_setup(const DevMesh& m, const CamParams& cam, FrameBufs& fb, cudaStream_t s);
 cudaError_t launch_face_setup(const DevMesh& m, const CamParams& cam, int lod, float delta,

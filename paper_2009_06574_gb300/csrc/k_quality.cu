@@ -80,10 +80,12 @@ __device__ __forceinline__ int32_t f2key(float f)
 }
 __device__ __forceinline__ float key2f(int32_t k) { return __int_as_float(k >= 0 ? k : (k ^ 0x7FFFFFFF)); }
 
-__global__ void k_init_keys(int32_t* p, int64_t n, int32_t v)
+// Both key arrays (vertices, then edges) to v in one launch.
+__global__ void k_init_keys(int32_t* __restrict__ a, int64_t na, int32_t* __restrict__ b, int64_t nb, int32_t v)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) p[i] = v;
+    if (i < na) a[i] = v;
+    else if (i - na < nb) b[i - na] = v;
 }
 
 __global__ void k_importance_scatter(const int32_t* __restrict__ cells, const int32_t* __restrict__ cell_edges,
@@ -99,32 +101,42 @@ __global__ void k_importance_scatter(const int32_t* __restrict__ cells, const in
     for (int j = 0; j < 12; ++j) atomicMax(ekey + cell_edges[12 * c + j], k);
 }
 
-__global__ void k_key_to_float(const int32_t* __restrict__ key, float* __restrict__ out, int64_t n)
+// Both key arrays back to floats in one launch (vertices, then edges); an
+// unreferenced vertex or edge gets 0.
+__global__ void k_key_to_float(const int32_t* __restrict__ ka, float* __restrict__ oa, int64_t na,
+                               const int32_t* __restrict__ kb, float* __restrict__ ob, int64_t nb)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int32_t k = key[i];
-    out[i] = (k == INT32_MIN) ? 0.f : key2f(k);   // an unreferenced vertex gets 0
+    if (i < na) {
+        const int32_t k = ka[i];
+        oa[i] = (k == INT32_MIN) ? 0.f : key2f(k);
+    } else if (i - na < nb) {
+        const int32_t k = kb[i - na];
+        ob[i - na] = (k == INT32_MIN) ? 0.f : key2f(k);
+    }
 }
 
-// Static face records: importance and world position of the 4 corners.
+// Static face records: importance and world position of the 4 corners. The
+// positions do not change after the upload: with positions false only the
+// importances are written.
 __global__ void k_face_static(const int4* __restrict__ fverts, const float* __restrict__ vimp,
-                              const float* __restrict__ verts, int64_t n_faces, FaceStatic* __restrict__ fstat)
+                              const float* __restrict__ verts, int64_t n_faces, bool positions,
+                              FaceStatic* __restrict__ fstat)
 {
     int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= n_faces) return;
     int4 c = fverts[f];
     int id[4] = {c.x, c.y, c.z, c.w};
-    float im[4], x[4], y[4], z[4];
+    FaceStatic& r = fstat[f];
+    r.imp = make_float4(vimp[id[0]], vimp[id[1]], vimp[id[2]], vimp[id[3]]);
+    if (!positions) return;
+    float x[4], y[4], z[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        im[k] = vimp[id[k]];
         x[k] = verts[3 * (int64_t)id[k]];
         y[k] = verts[3 * (int64_t)id[k] + 1];
         z[k] = verts[3 * (int64_t)id[k] + 2];
     }
-    FaceStatic& r = fstat[f];
-    r.imp = make_float4(im[0], im[1], im[2], im[3]);
     r.px = make_float4(x[0], x[1], x[2], x[3]);
     r.py = make_float4(y[0], y[1], y[2], y[3]);
     r.pz = make_float4(z[0], z[1], z[2], z[3]);
@@ -141,15 +153,15 @@ cudaError_t launch_cell_quality(const DevMesh& m, int metric, float* out, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_importance(const DevMesh& m, cudaStream_t s)
+cudaError_t launch_importance(const DevMesh& m, bool positions, cudaStream_t s)
 {
-    k_init_keys<<<grid_for(m.n_verts, 256), 256, 0, s>>>(m.vkey, m.n_verts, INT32_MIN);
-    k_init_keys<<<grid_for(m.n_edges, 256), 256, 0, s>>>(m.ekey, m.n_edges, INT32_MIN);
+    const int64_t nk = m.n_verts + m.n_edges;
+    k_init_keys<<<grid_for(nk, 256), 256, 0, s>>>(m.vkey, m.n_verts, m.ekey, m.n_edges, INT32_MIN);
     k_importance_scatter<<<grid_for(m.n_cells, 256), 256, 0, s>>>(m.cells, m.cell_edges, m.cell_imp,
                                                                    m.n_cells, m.vkey, m.ekey);
-    k_key_to_float<<<grid_for(m.n_verts, 256), 256, 0, s>>>(m.vkey, m.vimp, m.n_verts);
-    k_key_to_float<<<grid_for(m.n_edges, 256), 256, 0, s>>>(m.ekey, m.eattr, m.n_edges);
-    k_face_static<<<grid_for(m.n_faces, 256), 256, 0, s>>>(m.fverts, m.vimp, m.verts, m.n_faces, m.fstat);
+    k_key_to_float<<<grid_for(nk, 256), 256, 0, s>>>(m.vkey, m.vimp, m.n_verts, m.ekey, m.eattr, m.n_edges);
+    k_face_static<<<grid_for(m.n_faces, 256), 256, 0, s>>>(m.fverts, m.vimp, m.verts, m.n_faces, positions,
+                                                           m.fstat);
     return cudaGetLastError();
 }
 
