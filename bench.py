@@ -364,7 +364,7 @@ def run_ours(args, rank, world, local_rank):
     ev0.record(stream)
     for i in range(args.steps):
         st = step(args.warmup + i)
-        launches += 1 + 6 + st["kernel_launches"]
+        launches += 1 + 4 + st["kernel_launches"]   # quality, importance (4 kernels), the frame
     ev1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
